@@ -1,0 +1,202 @@
+"""ctypes binding of the FP64 C oracle (oracle/pmf_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Arrays are converted to contiguous float64 here; the
+C code does all of the arithmetic.  Grids are passed as (nx, ny, nz, vx, vy, vz)
+tuples or any object with those attributes.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+_D = ct.POINTER(ct.c_double)
+_I64 = ct.POINTER(ct.c_int64)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ct.CDLL(path)
+            L.orc_threads.restype = ct.c_int
+            L.orc_set_threads.argtypes = [ct.c_int]
+            L.orc_quat_to_rot.argtypes = [_D, _D]
+            L.orc_voxelize.argtypes = [_I64, _D, ct.c_int64, ct.c_int, _D, _D, _D, _D, ct.c_double, ct.c_int, _D]
+            L.orc_voxelize.restype = ct.c_int
+            L.orc_voxelize_backward.argtypes = [_I64, _D, ct.c_int64, ct.c_int, _D, _D, _D, _D, ct.c_double,
+                                                _D, _D, _D, _D, _D]
+            L.orc_voxelize_backward.restype = ct.c_int
+            L.orc_combine.argtypes = [ct.c_int64, ct.c_int, ct.c_int, _D, _D, _D]
+            L.orc_combine_backward.argtypes = [ct.c_int64, ct.c_int, ct.c_int, _D, _D, _D, _D, _D]
+            L.orc_warp.argtypes = [_I64, _D, ct.c_int, _D, _D, _D]
+            L.orc_warp_backward.argtypes = [_I64, _D, ct.c_int, _D, _D, _D, _D, _D]
+            L.orc_project.argtypes = [_I64, _D, ct.c_int, ct.c_int, ct.c_double, ct.c_int, _D, _D, ct.c_int64, _D]
+            L.orc_project_backward.argtypes = [_I64, _D, ct.c_int, ct.c_int, ct.c_double, ct.c_int, _D, _D, _D,
+                                               ct.c_int64]
+            L.orc_project_gaussians.argtypes = [ct.c_int, ct.c_int, ct.c_double, ct.c_int, _D, ct.c_int64,
+                                                _D, _D, _D, _D, ct.c_int64, ct.c_int64, _D]
+            L.orc_loss.argtypes = [ct.c_int, ct.c_int64, _D, _D, _D]
+            L.orc_loss.restype = ct.c_double
+            _lib = L
+    return _lib
+
+
+def threads() -> int:
+    return int(lib().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _p(a):
+    return a.ctypes.data_as(_D)
+
+
+def _grid(grid):
+    if hasattr(grid, "nx"):
+        dims = (grid.nx, grid.ny, grid.nz)
+        vox = (grid.vx, grid.vy, grid.vz)
+    else:
+        dims, vox = tuple(grid[:3]), tuple(grid[3:6])
+    d = np.array(dims, dtype=np.int64)
+    v = np.array(vox, dtype=np.float64)
+    return d, v, int(d[0] * d[1] * d[2])
+
+
+def quat_to_rot(q) -> np.ndarray:
+    q = _f64(q)
+    R = np.zeros(9)
+    lib().orc_quat_to_rot(_p(q), _p(R))
+    return R.reshape(3, 3)
+
+
+def voxelize(grid, mean, scale, quat, value, kappa=3.0, cull=True) -> np.ndarray:
+    """Eq. 4-5 voxelization; returns out[C][nz][ny][nx] (float64)."""
+    d, v, n = _grid(grid)
+    mean, scale, quat = _f64(mean).reshape(-1, 3), _f64(scale).reshape(-1, 3), _f64(quat).reshape(-1, 4)
+    value = _f64(value)
+    if value.ndim == 1:
+        value = value[:, None]
+    g, c = value.shape
+    out = np.zeros(n * c)
+    rc = lib().orc_voxelize(d.ctypes.data_as(_I64), _p(v), g, c, _p(mean), _p(scale), _p(quat), _p(value),
+                            float(kappa), int(bool(cull)), _p(out))
+    if rc != 0:
+        raise ValueError("oracle voxelize rejected its arguments")
+    return out.reshape(c, d[2], d[1], d[0])
+
+
+def voxelize_backward(grid, mean, scale, quat, value, d_out, kappa=3.0):
+    """Adjoint of `voxelize`; returns (d_mean, d_scale, d_quat, d_value)."""
+    d, v, n = _grid(grid)
+    mean, scale, quat = _f64(mean).reshape(-1, 3), _f64(scale).reshape(-1, 3), _f64(quat).reshape(-1, 4)
+    value = _f64(value)
+    if value.ndim == 1:
+        value = value[:, None]
+    g, c = value.shape
+    dout = _f64(d_out).reshape(-1)
+    assert dout.size == n * c
+    dm, ds, dq, dv = np.zeros((g, 3)), np.zeros((g, 3)), np.zeros((g, 4)), np.zeros((g, c))
+    rc = lib().orc_voxelize_backward(d.ctypes.data_as(_I64), _p(v), g, c, _p(mean), _p(scale), _p(quat), _p(value),
+                                     float(kappa), _p(dout), _p(dm), _p(ds), _p(dq), _p(dv))
+    if rc != 0:
+        raise ValueError("oracle voxelize_backward rejected its arguments")
+    return dm, ds, dq, dv
+
+
+def combine(E, w) -> np.ndarray:
+    """Eq. 3: E[L][3][N...], w[P][L][3] -> D[P][3][N...]."""
+    E = _f64(E)
+    w = _f64(w)
+    L = E.shape[0]
+    n = E[0, 0].size
+    P = w.shape[0]
+    D = np.zeros((P, 3) + E.shape[2:])
+    lib().orc_combine(n, L, P, _p(E), _p(w), _p(D))
+    return D
+
+
+def combine_backward(E, w, dD):
+    E, w, dD = _f64(E), _f64(w), _f64(dD)
+    L, P, n = E.shape[0], w.shape[0], E[0, 0].size
+    dE = np.zeros_like(E)
+    dw = np.zeros_like(w)
+    lib().orc_combine_backward(n, L, P, _p(E), _p(w), _p(dD), _p(dE), _p(dw))
+    return dE, dw
+
+
+def warp(grid, V, D) -> np.ndarray:
+    """Eq. 2: V[N...], D[P][3][N...] (mm) -> W[P][N...]."""
+    d, v, n = _grid(grid)
+    V, D = _f64(V), _f64(D)
+    P = D.shape[0]
+    W = np.zeros((P,) + tuple(d[::-1]))
+    lib().orc_warp(d.ctypes.data_as(_I64), _p(v), P, _p(V), _p(D), _p(W))
+    return W
+
+
+def warp_backward(grid, V, D, dW):
+    d, v, n = _grid(grid)
+    V, D, dW = _f64(V), _f64(D), _f64(dW)
+    P = D.shape[0]
+    dV = np.zeros(n)
+    dD = np.zeros(D.shape)
+    lib().orc_warp_backward(d.ctypes.data_as(_I64), _p(v), P, _p(V), _p(D), _p(dW), _p(dV), _p(dD))
+    return dV.reshape(tuple(d[::-1])), dD
+
+
+def project(grid, nu, nv, step, views, vol, shared=None) -> np.ndarray:
+    """Eq. 6 ray sum; vol is [N...] (shared by every view) or [P][N...]."""
+    d, v, n = _grid(grid)
+    views = _f64(views).reshape(-1, 12)
+    P = views.shape[0]
+    vol = _f64(vol)
+    if shared is None:
+        shared = vol.size == n
+    Y = np.zeros((P, nv, nu))
+    lib().orc_project(d.ctypes.data_as(_I64), _p(v), int(nu), int(nv), float(step), P, _p(views), _p(vol),
+                      0 if shared else n, _p(Y))
+    return Y
+
+
+def project_backward(grid, nu, nv, step, views, dY, shared=False) -> np.ndarray:
+    d, v, n = _grid(grid)
+    views = _f64(views).reshape(-1, 12)
+    P = views.shape[0]
+    dY = _f64(dY)
+    out = np.zeros(n if shared else P * n)
+    lib().orc_project_backward(d.ctypes.data_as(_I64), _p(v), int(nu), int(nv), float(step), P, _p(views),
+                               _p(dY), _p(out), 0 if shared else n)
+    return out.reshape(tuple(d[::-1]) if shared else (P,) + tuple(d[::-1]))
+
+
+def project_gaussians(nu, nv, step, views, mean, scale, quat, value, m_lo, m_hi) -> np.ndarray:
+    views = _f64(views).reshape(-1, 12)
+    P = views.shape[0]
+    mean, scale, quat = _f64(mean).reshape(-1, 3), _f64(scale).reshape(-1, 3), _f64(quat).reshape(-1, 4)
+    value = _f64(value).reshape(-1)
+    Y = np.zeros((P, nv, nu))
+    lib().orc_project_gaussians(int(nu), int(nv), float(step), P, _p(views), mean.shape[0], _p(mean), _p(scale),
+                                _p(quat), _p(value), int(m_lo), int(m_hi), _p(Y))
+    return Y
+
+
+def loss(kind, pred, meas, with_grad=True):
+    """kind 1 = L1, 2 = L2, both averaged over all pixels; returns (loss, d_pred)."""
+    pred, meas = _f64(pred), _f64(meas)
+    g = np.zeros_like(pred) if with_grad else None
+    val = lib().orc_loss(int(kind), pred.size, _p(pred), _p(meas), _p(g) if with_grad else None)
+    return float(val), g

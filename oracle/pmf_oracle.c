@@ -1,0 +1,495 @@
+/*
+ * FP64 CPU oracle for the PMF-STGR forward model and its adjoint.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is read by the tests, by the smoke check
+ * and by the benchmark's CPU-baseline leg; the library under test never links,
+ * loads or calls it.  It shares no code, header, table or constant with the
+ * CUDA path.  Every loop is the plain definition from the paper, in double
+ * precision, with no tiling, fusion or reordering beyond skipping terms that are
+ * exactly zero by the definition (voxels outside a Gaussian's truncation
+ * ellipsoid, ray samples outside the zero-padded volume).
+ *
+ * Passages followed (PMF-STGR, Xie, Shao & Zhang):
+ *   Eq. 4  G(x) = rho exp(-1/2 (x-p)^T Sigma^-1 (x-p))            voxelize
+ *   Eq. 5  sigma(x) = sum_i G_i(x)                                 voxelize
+ *   Sec. 2.3.1  negative-permitting voxelizer for signed MBC values  voxelize, C=3
+ *   Eq. 3  d(x,p) = sum_i w_i(p) x e_i(x)  (per Cartesian component) combine
+ *   Eq. 2  I(x,p) = I_ref(x + d(x,p))                              warp
+ *   Eq. 6  I(r) = integral of sigma along the ray                   project
+ *   Eq. 10/12  mean L1 over the batch; Eq. 1 squared-norm form      loss
+ * Readings where the paper is silent (all listed in the design notes):
+ *   Sigma = R(q/|q|) diag(s^2) R^T with q = (w,x,y,z) and s in mm; hard
+ *   truncation q_form <= kappa^2 (kappa = +inf disables it); values are sampled
+ *   at voxel centres (i + 1/2 - n/2) v; interpolation is trilinear with zero
+ *   padding outside [0, n-1]; the DVF is in mm and applied in index space
+ *   (u = i + d/v); the line integral is the source-anchored sum
+ *   step * sum_{m >= 0} Trilin(W, idx(src + m step r)) with r the unit
+ *   source-to-pixel-centre direction.
+ *
+ * Parity: pinned by closed forms, invariants, finite differences and a NumPy
+ * brute force in the oracle tests; there is no worked example in the paper to
+ * match ("parity unpinned" against the paper's own numbers only).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ---------------------------------------------------------------- geometry */
+
+/* Voxel centre coordinate along one axis (mm): (i + 1/2 - n/2) v. */
+static double centre(int64_t i, int64_t n, double v) { return ((double)i + 0.5 - 0.5 * (double)n) * v; }
+
+/* Continuous voxel index of a coordinate: x / v + n/2 - 1/2 (inverse of centre). */
+static double to_index(double x, int64_t n, double v) { return x / v + 0.5 * (double)n - 0.5; }
+
+/* Rotation matrix of the unit quaternion q/|q|, q = (w, x, y, z); row-major R[3*i+j].
+ * The columns of R are the Gaussian's principal axes: Sigma = R diag(s^2) R^T. */
+static void quat_to_rot(const double q_in[4], double R[9], double qn[4], double* norm) {
+    double n = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+    double w = q_in[0] / n, x = q_in[1] / n, y = q_in[2] / n, z = q_in[3] / n;
+    if (qn) { qn[0] = w; qn[1] = x; qn[2] = y; qn[3] = z; }
+    if (norm) *norm = n;
+    R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - w * z);       R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);       R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);       R[7] = 2.0 * (y * z + w * x);       R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+void orc_quat_to_rot(const double* q, double* R) { quat_to_rot(q, R, NULL, NULL); }
+
+/* Index range [lo, hi] along one axis that can hold voxel centres of the
+ * truncation ellipsoid: the ellipsoid {d : d^T Sigma^-1 d <= k^2} extends
+ * k sqrt(Sigma_aa) from its centre along axis a.  One voxel of slack on each
+ * side; the per-voxel test decides. */
+static void axis_range(double mu, double half, int64_t n, double v, int64_t* lo, int64_t* hi) {
+    double a = to_index(mu - half, n, v), b = to_index(mu + half, n, v);
+    double l = ceil(a) - 1.0, h = floor(b) + 1.0;
+    if (l < 0.0) l = 0.0;
+    if (h > (double)(n - 1)) h = (double)(n - 1);
+    *lo = (int64_t)l; *hi = (int64_t)h;
+    if (!(a == a) || !(b == b)) { *lo = 0; *hi = n - 1; }
+}
+
+typedef struct {
+    double mu[3], s[3], R[9], qn[4], qnorm;
+    int64_t lo[3], hi[3];
+} gauss_t;
+
+static void prepare(gauss_t* g, const double* mean, const double* scale, const double* quat,
+                    double kappa, int cull, const int64_t dims[3], const double vox[3]) {
+    for (int a = 0; a < 3; a++) { g->mu[a] = mean[a]; g->s[a] = scale[a]; }
+    quat_to_rot(quat, g->R, g->qn, &g->qnorm);
+    for (int a = 0; a < 3; a++) {
+        if (!cull || isinf(kappa)) { g->lo[a] = 0; g->hi[a] = dims[a] - 1; continue; }
+        double var = 0.0;
+        for (int j = 0; j < 3; j++) var += g->R[3 * a + j] * g->R[3 * a + j] * g->s[j] * g->s[j];
+        axis_range(g->mu[a], kappa * sqrt(var), dims[a], vox[a], &g->lo[a], &g->hi[a]);
+    }
+}
+
+/* Quadratic form q = (x-mu)^T Sigma^-1 (x-mu) = sum_j (r_j / s_j)^2, r = R^T (x-mu). */
+static double qform(const gauss_t* g, const double d[3], double r[3]) {
+    double q = 0.0;
+    for (int j = 0; j < 3; j++) {
+        r[j] = g->R[0 * 3 + j] * d[0] + g->R[1 * 3 + j] * d[1] + g->R[2 * 3 + j] * d[2];
+        q += (r[j] / g->s[j]) * (r[j] / g->s[j]);
+    }
+    return q;
+}
+
+/* ------------------------------------------------------------ voxelization */
+
+/* Eq. 4-5: out[c][v] = sum_g value[g][c] exp(-q_g(x_v)/2) [q_g(x_v) <= kappa^2].
+ * kappa = +inf: no truncation.  cull = 0 visits every voxel for every Gaussian
+ * (used to check the culled loop).  Per voxel the sum runs in Gaussian order. */
+int orc_voxelize(const int64_t dims[3], const double vox[3], int64_t G, int C,
+                 const double* mean, const double* scale, const double* quat, const double* value,
+                 double kappa, int cull, double* out) {
+    if (!(kappa > 0.0) || C < 1) return -1;
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2], N = nx * ny * nz;
+    const double k2 = isinf(kappa) ? INFINITY : kappa * kappa;
+    gauss_t* gs = (gauss_t*)malloc(sizeof(gauss_t) * (size_t)(G > 0 ? G : 1));
+    for (int64_t g = 0; g < G; g++) prepare(&gs[g], mean + 3 * g, scale + 3 * g, quat + 4 * g, kappa, cull, dims, vox);
+    memset(out, 0, sizeof(double) * (size_t)(N * C));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nz; k++) {
+        for (int64_t g = 0; g < G; g++) {
+            const gauss_t* ga = &gs[g];
+            if (k < ga->lo[2] || k > ga->hi[2]) continue;
+            for (int64_t j = ga->lo[1]; j <= ga->hi[1]; j++)
+                for (int64_t i = ga->lo[0]; i <= ga->hi[0]; i++) {
+                    double d[3] = {centre(i, nx, vox[0]) - ga->mu[0], centre(j, ny, vox[1]) - ga->mu[1],
+                                   centre(k, nz, vox[2]) - ga->mu[2]};
+                    double r[3];
+                    double q = qform(ga, d, r);
+                    if (!(q <= k2)) continue;
+                    double e = exp(-0.5 * q);
+                    int64_t v = (k * ny + j) * nx + i;
+                    for (int c = 0; c < C; c++) out[c * N + v] += value[g * C + c] * e;
+                }
+        }
+    }
+    free(gs);
+    return 0;
+}
+
+/* d R / d (w, x, y, z) for the rotation matrix written in quat_to_rot (treating
+ * the normalised components as free variables); dR[comp][9]. */
+static void drot_dq(const double q[4], double dR[4][9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double t[4][9] = {
+        /* d/dw */ {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0},
+        /* d/dx */ {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x},
+        /* d/dy */ {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y},
+        /* d/dz */ {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0},
+    };
+    memcpy(dR, t, sizeof(t));
+}
+
+/* Adjoint of orc_voxelize with respect to every Gaussian parameter (the
+ * truncation indicator has zero derivative).  Gradients overwrite the outputs.
+ * Chain rule per voxel: with e = exp(-q/2) and s = sum_c value_c dL/dout_c,
+ *   dL/dvalue_c += dL/dout_c e,   dL/dq = -s e / 2,
+ *   dq/dmu = -2 R (r / s^2),  dq/ds_j = -2 r_j^2 / s_j^3,  dq/dR_ij = 2 d_i r_j / s_j^2,
+ * then dR -> d(unit quaternion) -> d(raw quaternion) through (I - qq^T)/|q|. */
+int orc_voxelize_backward(const int64_t dims[3], const double vox[3], int64_t G, int C,
+                          const double* mean, const double* scale, const double* quat, const double* value,
+                          double kappa, const double* d_out,
+                          double* d_mean, double* d_scale, double* d_quat, double* d_value) {
+    if (!(kappa > 0.0) || C < 1 || C > 16) return -1;
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2], N = nx * ny * nz;
+    const double k2 = isinf(kappa) ? INFINITY : kappa * kappa;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t g = 0; g < G; g++) {
+        gauss_t ga;
+        prepare(&ga, mean + 3 * g, scale + 3 * g, quat + 4 * g, kappa, 1, dims, vox);
+        double gmu[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gR[9] = {0};
+        double gval[16];
+        for (int c = 0; c < C && c < 16; c++) gval[c] = 0.0;
+        for (int64_t k = ga.lo[2]; k <= ga.hi[2]; k++)
+            for (int64_t j = ga.lo[1]; j <= ga.hi[1]; j++)
+                for (int64_t i = ga.lo[0]; i <= ga.hi[0]; i++) {
+                    double d[3] = {centre(i, nx, vox[0]) - ga.mu[0], centre(j, ny, vox[1]) - ga.mu[1],
+                                   centre(k, nz, vox[2]) - ga.mu[2]};
+                    double r[3];
+                    double q = qform(&ga, d, r);
+                    if (!(q <= k2)) continue;
+                    double e = exp(-0.5 * q);
+                    int64_t v = (k * ny + j) * nx + i;
+                    double s = 0.0;
+                    for (int c = 0; c < C; c++) {
+                        gval[c] += d_out[c * N + v] * e;
+                        s += value[g * C + c] * d_out[c * N + v];
+                    }
+                    double gq = -0.5 * s * e;
+                    for (int a = 0; a < 3; a++) {
+                        double Ad = 0.0;
+                        for (int jj = 0; jj < 3; jj++) Ad += ga.R[3 * a + jj] * r[jj] / (ga.s[jj] * ga.s[jj]);
+                        gmu[a] += gq * (-2.0 * Ad);
+                    }
+                    for (int jj = 0; jj < 3; jj++) gs[jj] += gq * (-2.0 * r[jj] * r[jj] / (ga.s[jj] * ga.s[jj] * ga.s[jj]));
+                    for (int a = 0; a < 3; a++)
+                        for (int jj = 0; jj < 3; jj++) gR[3 * a + jj] += gq * (2.0 * d[a] * r[jj] / (ga.s[jj] * ga.s[jj]));
+                }
+        double dR[4][9], gqn[4];
+        drot_dq(ga.qn, dR);
+        for (int c4 = 0; c4 < 4; c4++) {
+            gqn[c4] = 0.0;
+            for (int t = 0; t < 9; t++) gqn[c4] += gR[t] * dR[c4][t];
+        }
+        double dot = gqn[0] * ga.qn[0] + gqn[1] * ga.qn[1] + gqn[2] * ga.qn[2] + gqn[3] * ga.qn[3];
+        for (int c4 = 0; c4 < 4; c4++) d_quat[4 * g + c4] = (gqn[c4] - ga.qn[c4] * dot) / ga.qnorm;
+        for (int a = 0; a < 3; a++) { d_mean[3 * g + a] = gmu[a]; d_scale[3 * g + a] = gs[a]; }
+        for (int c = 0; c < C; c++) d_value[g * C + c] = gval[c];
+    }
+    return 0;
+}
+
+/* ----------------------------------------------------------------- combine */
+
+/* Eq. 3, per Cartesian component k: D[p][k][v] = sum_l w[p][l][k] E[l][k][v]. */
+void orc_combine(int64_t N, int L, int P, const double* E, const double* w, double* D) {
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < N; v++)
+        for (int p = 0; p < P; p++)
+            for (int k = 0; k < 3; k++) {
+                double acc = 0.0;
+                for (int l = 0; l < L; l++) acc += w[(p * L + l) * 3 + k] * E[((int64_t)l * 3 + k) * N + v];
+                D[((int64_t)p * 3 + k) * N + v] = acc;
+            }
+}
+
+/* Adjoint of orc_combine: dE[l][k][v] = sum_p dD[p][k][v] w[p][l][k];
+ * dw[p][l][k] = sum_v dD[p][k][v] E[l][k][v]. */
+void orc_combine_backward(int64_t N, int L, int P, const double* E, const double* w, const double* dD,
+                          double* dE, double* dw) {
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < N; v++)
+        for (int l = 0; l < L; l++)
+            for (int k = 0; k < 3; k++) {
+                double acc = 0.0;
+                for (int p = 0; p < P; p++) acc += dD[((int64_t)p * 3 + k) * N + v] * w[(p * L + l) * 3 + k];
+                dE[((int64_t)l * 3 + k) * N + v] = acc;
+            }
+    for (int p = 0; p < P; p++)
+        for (int l = 0; l < L; l++)
+            for (int k = 0; k < 3; k++) {
+                double acc = 0.0;
+                const double* a = dD + ((int64_t)p * 3 + k) * N;
+                const double* b = E + ((int64_t)l * 3 + k) * N;
+#pragma omp parallel for reduction(+ : acc) schedule(static)
+                for (int64_t v = 0; v < N; v++) acc += a[v] * b[v];
+                dw[(p * L + l) * 3 + k] = acc;
+            }
+}
+
+/* ------------------------------------------------------------- trilinear */
+
+static double vox_at(const double* V, const int64_t dims[3], int64_t i, int64_t j, int64_t k) {
+    if (i < 0 || j < 0 || k < 0 || i >= dims[0] || j >= dims[1] || k >= dims[2]) return 0.0;
+    return V[(k * dims[1] + j) * dims[0] + i];
+}
+
+/* Trilinear interpolation at continuous index u with zero padding: corners
+ * floor(u) and floor(u)+1 per axis, weights (1-f, f), f = u - floor(u). */
+static double trilin(const double* V, const int64_t dims[3], const double u[3]) {
+    double fl[3], f[3];
+    for (int a = 0; a < 3; a++) { fl[a] = floor(u[a]); f[a] = u[a] - fl[a]; }
+    int64_t i0 = (int64_t)fl[0], j0 = (int64_t)fl[1], k0 = (int64_t)fl[2];
+    double acc = 0.0;
+    for (int c = 0; c < 8; c++) {
+        int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+        double wgt = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) * (dk ? f[2] : 1.0 - f[2]);
+        acc += wgt * vox_at(V, dims, i0 + di, j0 + dj, k0 + dk);
+    }
+    return acc;
+}
+
+/* Scatter g * weight to the 8 corners (adjoint of trilin with respect to V). */
+static void trilin_adj(double* dV, const int64_t dims[3], const double u[3], double g) {
+    double fl[3], f[3];
+    for (int a = 0; a < 3; a++) { fl[a] = floor(u[a]); f[a] = u[a] - fl[a]; }
+    int64_t i0 = (int64_t)fl[0], j0 = (int64_t)fl[1], k0 = (int64_t)fl[2];
+    for (int c = 0; c < 8; c++) {
+        int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+        int64_t i = i0 + di, j = j0 + dj, k = k0 + dk;
+        if (i < 0 || j < 0 || k < 0 || i >= dims[0] || j >= dims[1] || k >= dims[2]) continue;
+        double wgt = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) * (dk ? f[2] : 1.0 - f[2]);
+        dV[(k * dims[1] + j) * dims[0] + i] += g * wgt;
+    }
+}
+
+/* Gradient of trilin with respect to u (derivative of the weights inside the
+ * floor cell; at an exact integer u this is the one-sided derivative from the
+ * cell [u, u+1]). */
+static void trilin_grad(const double* V, const int64_t dims[3], const double u[3], double gu[3]) {
+    double fl[3], f[3];
+    for (int a = 0; a < 3; a++) { fl[a] = floor(u[a]); f[a] = u[a] - fl[a]; }
+    int64_t i0 = (int64_t)fl[0], j0 = (int64_t)fl[1], k0 = (int64_t)fl[2];
+    gu[0] = gu[1] = gu[2] = 0.0;
+    for (int c = 0; c < 8; c++) {
+        int dd[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        double val = vox_at(V, dims, i0 + dd[0], j0 + dd[1], k0 + dd[2]);
+        double wv[3], dw[3];
+        for (int a = 0; a < 3; a++) { wv[a] = dd[a] ? f[a] : 1.0 - f[a]; dw[a] = dd[a] ? 1.0 : -1.0; }
+        gu[0] += val * dw[0] * wv[1] * wv[2];
+        gu[1] += val * wv[0] * dw[1] * wv[2];
+        gu[2] += val * wv[0] * wv[1] * dw[2];
+    }
+}
+
+/* -------------------------------------------------------------------- warp */
+
+/* Eq. 2 (pull warp): W[p][v] = Trilin(V, (i,j,k) + D[p][:,v] / vox). */
+void orc_warp(const int64_t dims[3], const double vox[3], int P, const double* V, const double* D, double* W) {
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2], N = nx * ny * nz;
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < N; v++) {
+        int64_t i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
+        for (int p = 0; p < P; p++) {
+            const double* Dp = D + (int64_t)p * 3 * N;
+            double u[3] = {(double)i + Dp[v] / vox[0], (double)j + Dp[N + v] / vox[1], (double)k + Dp[2 * N + v] / vox[2]};
+            W[(int64_t)p * N + v] = trilin(V, dims, u);
+        }
+    }
+}
+
+/* Adjoint of orc_warp: dV = sum_p scatter of dW (overwrites dV);
+ * dD[p][k][v] = dW[p][v] dTrilin/du_k / vox_k (overwrites dD). */
+void orc_warp_backward(const int64_t dims[3], const double vox[3], int P, const double* V, const double* D,
+                       const double* dW, double* dV, double* dD) {
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2], N = nx * ny * nz;
+    memset(dV, 0, sizeof(double) * (size_t)N);
+    for (int p = 0; p < P; p++) {
+        const double* Dp = D + (int64_t)p * 3 * N;
+#pragma omp parallel for schedule(static)
+        for (int64_t v = 0; v < N; v++) {
+            int64_t i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
+            double u[3] = {(double)i + Dp[v] / vox[0], (double)j + Dp[N + v] / vox[1], (double)k + Dp[2 * N + v] / vox[2]};
+            double gu[3];
+            trilin_grad(V, dims, u, gu);
+            double g = dW[(int64_t)p * N + v];
+            for (int a = 0; a < 3; a++) dD[((int64_t)p * 3 + a) * N + v] = g * gu[a] / vox[a];
+        }
+        for (int64_t v = 0; v < N; v++) {
+            int64_t i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
+            double u[3] = {(double)i + Dp[v] / vox[0], (double)j + Dp[N + v] / vox[1], (double)k + Dp[2 * N + v] / vox[2]};
+            trilin_adj(dV, dims, u, dW[(int64_t)p * N + v]);
+        }
+    }
+}
+
+/* --------------------------------------------------------------- projector */
+
+typedef struct { double src[3], dir[3]; int64_t m_lo, m_hi; } ray_t;
+
+/* Ray from the source through the centre of pixel (a, b) and the range of
+ * sample indices m that can touch the zero-padded volume.  A sample at x
+ * contributes only if |x_a| < (n_a + 1) v_a / 2 on every axis, so every such
+ * sample lies inside the sphere of radius |((n+1) v / 2)| about the origin. */
+static void make_ray(const double* view, int nu, int nv, int a, int b, const int64_t dims[3], const double vox[3],
+                     double step, ray_t* r) {
+    const double *src = view, *det = view + 3, *du = view + 6, *dv = view + 9;
+    double ca = (double)a + 0.5 - 0.5 * (double)nu, cb = (double)b + 0.5 - 0.5 * (double)nv;
+    double len = 0.0;
+    for (int t = 0; t < 3; t++) {
+        r->src[t] = src[t];
+        r->dir[t] = det[t] + ca * du[t] + cb * dv[t] - src[t];
+        len += r->dir[t] * r->dir[t];
+    }
+    len = sqrt(len);
+    for (int t = 0; t < 3; t++) r->dir[t] /= len;
+    double rad2 = 0.0, tc = 0.0, d2 = 0.0;
+    for (int t = 0; t < 3; t++) {
+        double h = 0.5 * (double)(dims[t] + 1) * vox[t];
+        rad2 += h * h;
+        tc -= src[t] * r->dir[t];
+        d2 += src[t] * src[t];
+    }
+    double perp2 = d2 - tc * tc;
+    if (perp2 >= rad2) { r->m_lo = 1; r->m_hi = 0; return; }
+    double half = sqrt(rad2 - perp2);
+    double lo = floor((tc - half) / step) - 1.0, hi = ceil((tc + half) / step) + 1.0;
+    if (lo < 0.0) lo = 0.0;
+    r->m_lo = (int64_t)lo; r->m_hi = (int64_t)hi;
+}
+
+/* Eq. 6, discretised: Y[p][b][a] = step * sum_{m >= 0} Trilin(vol_p, idx(src + m step r)).
+ * views: [P][12] = src, detector centre, du, dv.  vol_stride = 0 shares one
+ * volume between all views; otherwise view p reads vol + p * vol_stride. */
+void orc_project(const int64_t dims[3], const double vox[3], int nu, int nv, double step, int P,
+                 const double* views, const double* vol, int64_t vol_stride, double* Y) {
+#pragma omp parallel for collapse(2) schedule(dynamic, 4)
+    for (int p = 0; p < P; p++)
+        for (int b = 0; b < nv; b++) {
+            const double* W = vol + (int64_t)p * vol_stride;
+            for (int a = 0; a < nu; a++) {
+                ray_t r;
+                make_ray(views + 12 * p, nu, nv, a, b, dims, vox, step, &r);
+                double acc = 0.0;
+                for (int64_t m = r.m_lo; m <= r.m_hi; m++) {
+                    double t = (double)m * step, u[3];
+                    for (int ax = 0; ax < 3; ax++) u[ax] = to_index(r.src[ax] + t * r.dir[ax], dims[ax], vox[ax]);
+                    acc += trilin(W, dims, u);
+                }
+                Y[((int64_t)p * nv + b) * nu + a] = step * acc;
+            }
+        }
+}
+
+/* Adjoint of orc_project: dvol (overwritten) = step * sum over rays and samples
+ * of dY times the trilinear weights.  vol_stride = 0: one shared dvol[N];
+ * otherwise dvol[P][N]. */
+void orc_project_backward(const int64_t dims[3], const double vox[3], int nu, int nv, double step, int P,
+                          const double* views, const double* dY, double* dvol, int64_t vol_stride) {
+    const int64_t N = dims[0] * dims[1] * dims[2];
+    memset(dvol, 0, sizeof(double) * (size_t)(vol_stride ? (int64_t)P * N : N));
+#pragma omp parallel for schedule(dynamic, 1) if (vol_stride != 0)
+    for (int p = 0; p < P; p++) {
+        double* dW = dvol + (int64_t)p * vol_stride;
+        for (int b = 0; b < nv; b++)
+            for (int a = 0; a < nu; a++) {
+                ray_t r;
+                make_ray(views + 12 * p, nu, nv, a, b, dims, vox, step, &r);
+                double g = step * dY[((int64_t)p * nv + b) * nu + a];
+                for (int64_t m = r.m_lo; m <= r.m_hi; m++) {
+                    double t = (double)m * step, u[3];
+                    for (int ax = 0; ax < 3; ax++) u[ax] = to_index(r.src[ax] + t * r.dir[ax], dims[ax], vox[ax]);
+                    trilin_adj(dW, dims, u, g);
+                }
+            }
+    }
+}
+
+/* Test mode (no voxelization): step * sum_{m in [m_lo, m_hi]} sigma(src + m step r)
+ * with sigma the untruncated Gaussian mixture of Eq. 5, for pinning the
+ * quadrature against the closed-form line integral of Eq. 7. */
+void orc_project_gaussians(int nu, int nv, double step, int P, const double* views, int64_t G,
+                           const double* mean, const double* scale, const double* quat, const double* value,
+                           int64_t m_lo, int64_t m_hi, double* Y) {
+    gauss_t* gs = (gauss_t*)malloc(sizeof(gauss_t) * (size_t)(G > 0 ? G : 1));
+    int64_t dims1[3] = {1, 1, 1};
+    double vox1[3] = {1, 1, 1};
+    for (int64_t g = 0; g < G; g++) prepare(&gs[g], mean + 3 * g, scale + 3 * g, quat + 4 * g, INFINITY, 0, dims1, vox1);
+#pragma omp parallel for collapse(2) schedule(dynamic, 4)
+    for (int p = 0; p < P; p++)
+        for (int b = 0; b < nv; b++)
+            for (int a = 0; a < nu; a++) {
+                const double* view = views + 12 * p;
+                double ca = (double)a + 0.5 - 0.5 * (double)nu, cb = (double)b + 0.5 - 0.5 * (double)nv;
+                double dir[3], len = 0.0;
+                for (int t = 0; t < 3; t++) { dir[t] = view[3 + t] + ca * view[6 + t] + cb * view[9 + t] - view[t]; len += dir[t] * dir[t]; }
+                len = sqrt(len);
+                for (int t = 0; t < 3; t++) dir[t] /= len;
+                double acc = 0.0;
+                for (int64_t m = m_lo; m <= m_hi; m++) {
+                    double x[3];
+                    for (int t = 0; t < 3; t++) x[t] = view[t] + (double)m * step * dir[t];
+                    for (int64_t g = 0; g < G; g++) {
+                        double d[3] = {x[0] - gs[g].mu[0], x[1] - gs[g].mu[1], x[2] - gs[g].mu[2]}, r[3];
+                        acc += value[g] * exp(-0.5 * qform(&gs[g], d, r));
+                    }
+                }
+                Y[((int64_t)p * nv + b) * nu + a] = step * acc;
+            }
+    free(gs);
+}
+
+/* -------------------------------------------------------------------- loss */
+
+/* Eq. 10/12 (L1, kind 1) and the squared form of Eq. 1 (L2, kind 2), averaged
+ * over all n = B * Q pixels of the batch.  d_pred (nullable) receives
+ * sign(pred - meas) / n (sign(0) = 0) or 2 (pred - meas) / n. */
+double orc_loss(int kind, int64_t n, const double* pred, const double* meas, double* d_pred) {
+    double acc = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double r = pred[i] - meas[i];
+        if (kind == 1) {
+            acc += fabs(r);
+            if (d_pred) d_pred[i] = (r > 0.0 ? 1.0 : (r < 0.0 ? -1.0 : 0.0)) / (double)n;
+        } else {
+            acc += r * r;
+            if (d_pred) d_pred[i] = 2.0 * r / (double)n;
+        }
+    }
+    return acc / (double)n;
+}

@@ -1,0 +1,40 @@
+"""The whole forward model and its adjoint, composed from oracle stages (test
+infrastructure): voxelize (Eq. 4-5) -> combine (Eq. 3) -> warp (Eq. 2) ->
+project (Eq. 6) -> loss (Eq. 10/12), then the exact adjoint chain."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+
+def forward(wl, views=None, coeff=None, kappa=None):
+    kappa = wl.kappa if kappa is None else kappa
+    views = wl.views if views is None else views
+    coeff = wl.coeff if coeff is None else coeff
+    g = wl.grid
+    V = oracle.voxelize(g, wl.ref.mean, wl.ref.scale, wl.ref.quat, wl.ref.value, kappa)[0]
+    E = np.stack([oracle.voxelize(g, m.mean, m.scale, m.quat, m.value, kappa) for m in wl.mbc])
+    D = oracle.combine(E, coeff)
+    W = oracle.warp(g, V, D)
+    Y = oracle.project(g, wl.det.nu, wl.det.nv, wl.det.step_mm, views, W, shared=False)
+    return dict(V=V, E=E, D=D, W=W, Y=Y)
+
+
+def step(wl, meas, kind=2, views=None, coeff=None, kappa=None):
+    """Loss and gradients with respect to every Gaussian parameter and the
+    temporal coefficients (float64)."""
+    kappa = wl.kappa if kappa is None else kappa
+    views = wl.views if views is None else views
+    coeff = wl.coeff if coeff is None else coeff
+    g = wl.grid
+    f = forward(wl, views, coeff, kappa)
+    loss, dY = oracle.loss(kind, f["Y"], meas)
+    dW = oracle.project_backward(g, wl.det.nu, wl.det.nv, wl.det.step_mm, views, dY, shared=False)
+    dV, dD = oracle.warp_backward(g, f["V"], f["D"], dW)
+    dE, dw = oracle.combine_backward(f["E"], coeff, dD)
+    grads = {"coeff": dw, "dV": dV, "dE": dE, "dW": dW, "dY": dY}
+    grads["ref"] = oracle.voxelize_backward(g, wl.ref.mean, wl.ref.scale, wl.ref.quat, wl.ref.value, dV, kappa)
+    grads["mbc"] = [oracle.voxelize_backward(g, m.mean, m.scale, m.quat, m.value, dE[l], kappa)
+                    for l, m in enumerate(wl.mbc)]
+    return loss, grads, f

@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Throughput of the PMF-STGR forward model + adjoint on GB300.
+
+One step = one training batch (default 32 projections, the paper's Stage-2
+batch, Sec. 2.3.2) of the paper-scale workload (200x200x100 at 2 mm, 100,000
+reference Gaussians, three MBC levels of 500/2,000/8,000 Gaussians, 512x384
+detector, 660 views over 360 degrees): voxelize the reference and MBC
+Gaussians, combine + warp, cone-beam project, loss, and the full adjoint down
+to every Gaussian parameter and temporal coefficient.  Metric: projections/s
+(forward + adjoint).  Inputs are seeded synthetic stand-ins for the XCAT and
+patient scans.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f32|bf16|f16]
+    python bench.py --impl reference ...    # FP64 CPU oracle on host cores
+
+Under torchrun every rank runs independent batches (no data-path collective);
+the timed region is bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "projections/s fwd+adjoint at 1 GB300; batched BF16 vs plain FP32; % HBM roofline"
+UNIT = "projections/s"
+WORKLOAD = "PMF-STGR fwd+adjoint, 200x200x100 @2mm, 100k ref Gaussians, MBC 500/2000/8000, 512x384 det, 660 views"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="f32")
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--kind", type=int, default=2, help="1 = L1 loss, 2 = L2 loss")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--small", action="store_true", help="the 64^3 / 2k-Gaussian / 128^2 case (for profiling)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, enabled: bool = True):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+        self.enabled = enabled
+
+    def start(self):
+        if not self.enabled:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        maxmhz = max(r[1] for r in rows)
+        load = [r[0] for r in rows if r[2] > 0.25 * max(x[2] for x in rows)] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": maxmhz, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel)
+    if not d or d.get("workload") != workload:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d.get("source_sha"):
+        return None
+    return float(d["dram_bytes_per_launch"])
+
+
+def build_workload(small: bool):
+    import numpy as np
+    import synth
+    if small:
+        wl = synth.config0(with_measured=True)
+        return wl, wl.measured
+    wl = synth.config1(p=660)
+    meas = synth.measured_projections(np.random.default_rng(synth.seeds_for(1)["measured"]), wl.p, wl.det.nu,
+                                      wl.det.nv, 400.0)
+    return wl, meas
+
+
+def algorithmic_bytes(stage: str, B: int, n: int, q: int, L: int, esz: int) -> float:
+    """Bytes each stage must move at least once per launch (B projections)."""
+    if stage == "conebeam_project":
+        return B * (n * esz + q * 4 + 96)
+    if stage == "conebeam_project_backward":
+        return B * (q * 4 + n * 4 + 96)
+    if stage == "warp_combine":
+        return L * 3 * n * esz + n * esz + B * n * esz
+    if stage == "warp_combine_backward":
+        return B * n * 4 + L * 3 * n * esz + n * esz + n * 4 + L * 3 * n * 4
+    if stage == "projection_loss":
+        return B * q * 12
+    return 0.0
+
+
+# ------------------------------------------------------------ native arm
+
+def run_native(a):
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    import paper_2503_22139_gb300 as pmf
+    from paper_2503_22139_gb300 import ops
+    from paper_2503_22139_gb300.pipeline import ForwardAdjoint
+    import synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
+    wl, meas_np = build_workload(a.small)
+    B = min(a.batch, wl.p)
+    perm = synth.select_batch(wl.p, wl.p, 0)  # one permutation of the scan; batches are its slices
+    nbatch = wl.p // B
+
+    def d(x, t=torch.float32):
+        return torch.as_tensor(np.ascontiguousarray(x), dtype=t, device="cuda")
+
+    views_all = d(wl.views[perm], torch.float64)
+    coeff_all = d(wl.coeff[perm])
+    meas_all = d(meas_np[perm])
+
+    def gset(s):
+        return pmf.Gaussians(d(s.mean), d(s.scale), d(s.quat), d(s.value), wl.kappa)
+
+    ref = gset(wl.ref)
+    mbc = [gset(m) for m in wl.mbc]
+    step = ForwardAdjoint(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind)
+
+    stage_names = ["gs_voxelize", "warp_combine", "conebeam_project", "projection_loss",
+                   "conebeam_project_backward", "warp_combine_backward", "gs_voxelize_backward"]
+
+    def batch(k):
+        s = ((rank * 7919 + k) % nbatch) * B
+        return views_all[s:s + B], coeff_all[s:s + B], meas_all[s:s + B]
+
+    # warm-up
+    for k in range(a.warmup):
+        step.run(*batch(k))
+    torch.cuda.synchronize()
+
+    # per-stage events on the launching stream, over the timed steps
+    stream = torch.cuda.current_stream()
+    ev = {s: [] for s in stage_names}
+    orig = {s: getattr(ops, s) for s in stage_names}
+
+    def timed(name):
+        f = orig[name]
+
+        def w(*args, **kw):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = f(*args, **kw)
+            e1.record(stream)
+            ev[name].append((e0, e1))
+            return r
+        return w
+
+    clocks = ClockSampler(local, enabled=not a.no_clocks)
+    clocks.start()
+    for s in stage_names:
+        setattr(ops, s, timed(s))
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(a.steps):
+        loss = step.run(*batch(a.warmup + k))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
+    for s in stage_names:
+        setattr(ops, s, orig[s])
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    if world > 1:
+        tt = torch.tensor([elapsed], device="cuda")
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    total_proj = B * a.steps * world
+    value = total_proj / elapsed
+    stage_ms = {s: sum(e0.elapsed_time(e1) for e0, e1 in ev[s]) / a.steps for s in stage_names if ev[s]}
+
+    # roofline of the dominant stage
+    n, q, L = wl.grid.n, wl.det.q, wl.levels
+    esz = torch.tensor([], dtype=dt).element_size()
+    dom = max(stage_ms, key=stage_ms.get)
+    per_launch_ms = stage_ms[dom] / max(1, len(ev[dom]) // a.steps)
+    alg = algorithmic_bytes(dom, B, n, q, L, esz)
+    peak, src = peaks()
+    achieved = alg / (per_launch_ms / 1e3) / 1e9 if alg else 0.0
+    workload_tag = f"{'small' if a.small else 'config1'}-{a.dtype}-B{B}"
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 5), "peak_source": f"{src} hbm_gbs",
+            "traffic": traffic_for(dom, workload_tag), "algorithmic_bytes": alg,
+            "avg_launch_ms": round(per_launch_ms, 4)}
+
+    # end to end: pinned host inputs -> device -> step -> gradients back to pinned host
+    e2e = None
+    if not a.no_e2e:
+        h_ref = [t.cpu().pin_memory() for t in (ref.mean, ref.scale, ref.quat, ref.value)]
+        h_mbc = [[t.cpu().pin_memory() for t in (m.mean, m.scale, m.quat, m.value)] for m in mbc]
+        h_views = views_all.cpu().pin_memory()
+        h_coeff = coeff_all.cpu().pin_memory()
+        h_meas = meas_all.cpu().pin_memory()
+        outs = [step.g_ref, *step.g_mbc, (step.g_wc[2],)]
+        h_out = [[torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in grp] for grp in outs]
+        h_loss = torch.empty(1).pin_memory()
+        bv = torch.empty((B, 12), dtype=torch.float64, device="cuda")
+        bc = torch.empty((B, L, 3), device="cuda")
+        bm = torch.empty((B, wl.det.nv, wl.det.nu), device="cuda")
+        h2d = sum(t.numel() * t.element_size() for t in h_ref) + sum(
+            t.numel() * t.element_size() for g in h_mbc for t in g)
+        h2d += B * (12 * 8 + L * 3 * 4 + wl.det.q * 4)
+        d2h = sum(t.numel() * t.element_size() for g in h_out for t in g) + 4
+
+        def e2e_step(k):
+            s = ((rank * 7919 + k) % nbatch) * B
+            for dst, src_ in zip((ref.mean, ref.scale, ref.quat, ref.value), h_ref):
+                dst.copy_(src_, non_blocking=True)
+            for m, hm in zip(mbc, h_mbc):
+                for dst, src_ in zip((m.mean, m.scale, m.quat, m.value), hm):
+                    dst.copy_(src_, non_blocking=True)
+            bv.copy_(h_views[s:s + B], non_blocking=True)
+            bc.copy_(h_coeff[s:s + B], non_blocking=True)
+            bm.copy_(h_meas[s:s + B], non_blocking=True)
+            lo = step.run(bv, bc, bm)
+            for grp, hgrp in zip(outs, h_out):
+                for t, h in zip(grp, hgrp):
+                    h.copy_(t, non_blocking=True)
+            h_loss.copy_(lo, non_blocking=True)
+
+        for k in range(a.warmup):
+            e2e_step(k)
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(a.steps):
+            e2e_step(a.warmup + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1) / 1e3
+        if world > 1:
+            tt = torch.tensor([te], device="cuda")
+            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": round(total_proj / te, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(wl, meas_np, small=a.small)
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(elapsed * 1e3 / a.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD if not a.small else "small: 64^3 @4mm, 2k Gaussians, 128^2 det, 8 views",
+                   "batch_projections": B, "loss": "L2" if a.kind == 2 else "L1", "storage_dtype": a.dtype,
+                   "accumulate_dtype": "f32", "l2_policy": "working set > L2 (E 144 MB, W and dW 512 MB each)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": roof, "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": step.launches_per_step * a.steps,
+        "loss": float(loss.item()),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_sample(wl, meas_np, view_idx, kind=2):
+    """One projection's forward + adjoint of the workload with the FP64 oracle,
+    voxelization of all Gaussians and its adjoint included; returns seconds."""
+    import numpy as np
+    import oracle
+    g, det = wl.grid, wl.det
+    t = time.perf_counter()
+    V = oracle.voxelize(g, wl.ref.mean, wl.ref.scale, wl.ref.quat, wl.ref.value, wl.kappa)[0]
+    E = np.stack([oracle.voxelize(g, m.mean, m.scale, m.quat, m.value, wl.kappa) for m in wl.mbc])
+    w = wl.coeff[view_idx:view_idx + 1].astype(np.float64)
+    vw = wl.views[view_idx:view_idx + 1]
+    D = oracle.combine(E, w)
+    W = oracle.warp(g, V, D)
+    Y = oracle.project(g, det.nu, det.nv, det.step_mm, vw, W, shared=False)
+    _, dY = oracle.loss(kind, Y, meas_np[view_idx:view_idx + 1])
+    dW = oracle.project_backward(g, det.nu, det.nv, det.step_mm, vw, dY, shared=False)
+    dV, dD = oracle.warp_backward(g, V, D, dW)
+    dE, dw = oracle.combine_backward(E, w, dD)
+    oracle.voxelize_backward(g, wl.ref.mean, wl.ref.scale, wl.ref.quat, wl.ref.value, dV, wl.kappa)
+    for l, m in enumerate(wl.mbc):
+        oracle.voxelize_backward(g, m.mean, m.scale, m.quat, m.value, dE[l], wl.kappa)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(wl, meas_np, small=False):
+    import oracle
+    secs = oracle_sample(wl, meas_np, 0)
+    return {"value": round(1.0 / secs, 5), "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"1 projection fwd+adjoint incl. voxelization of all Gaussians and its adjoint "
+                      f"({'small' if small else 'paper-scale'} workload), FP64 C oracle, {secs:.1f} s"}
+
+
+def run_reference(a):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    wl, meas_np = build_workload(a.small)
+    for k in range(a.warmup):
+        oracle_sample(wl, meas_np, k % wl.p, a.kind)
+    t = time.perf_counter()
+    for k in range(a.steps):
+        oracle_sample(wl, meas_np, (a.warmup + k) % wl.p, a.kind)
+    el = time.perf_counter() - t
+    value = a.steps / el
+    sample = ("each step: 1 projection fwd+adjoint incl. voxelization of all Gaussians and its adjoint, "
+              "FP64 C oracle (the path's plain definition), host cores")
+    line = {"metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(el * 1e3 / a.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD if not a.small else "small", "batch_projections": 1},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "kind": "oracle", "cores": oracle.threads(),
+                             "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_native(a)
+
+
+if __name__ == "__main__":
+    main()

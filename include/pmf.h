@@ -1,0 +1,219 @@
+/*
+ * pmf.h -- C ABI of the GB300 (sm_103a) library for the PMF-STGR forward model
+ * and its adjoint (Xie, Shao & Zhang, "Time-resolved dynamic CBCT reconstruction
+ * using prior-model-free spatiotemporal Gaussian representation").
+ *
+ * The model (Sec. 2.1-2.3): a reference volume voxelized from 3-D Gaussians
+ * (Eq. 4-5), motion-basis components (MBCs) voxelized from signed Gaussians
+ * (Sec. 2.3.1), per-projection DVFs d = sum_l w_l(p) x e_l (Eq. 3), the warped
+ * volume I(x,p) = I_ref(x + d(x,p)) (Eq. 2), and cone-beam line integrals of it
+ * (Eq. 6) compared with the measured projection under an L1 (Eq. 10/12) or L2
+ * (Eq. 1) loss.
+ *
+ * Conventions (every call):
+ *  - Pointers named d_* or marked "device" are CUDA device pointers; host
+ *    structs (pmf_grid, pmf_detector, pmf_gaussians) are read on the host
+ *    during the call and may be freed on return.  The caller owns every buffer;
+ *    the library never allocates or frees device memory.
+ *  - All device work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) and is asynchronous: inputs must stay alive and unchanged
+ *    until the stream reaches the work.  No call synchronizes.
+ *  - Volumes are [nz][ny][nx], x fastest, centred on the isocentre: voxel
+ *    (i,j,k) sits at ((i + 1/2 - nx/2) vx, (j + 1/2 - ny/2) vy, (k + 1/2 - nz/2) vz) mm.
+ *    Trilinear interpolation reads voxels outside [0, n-1] as zero.
+ *  - A DVF is SoA [P][3][N] in mm; MBC grids are [L][3][N]; temporal
+ *    coefficients are float [P][L][3]; projections are float [P][nv][nu].
+ *  - `dtype` is the storage type of volumes, MBC grids, DVFs and warped
+ *    volumes (fp32, bf16 or fp16, round-to-nearest-even on store).  Every
+ *    interpolation, ray sum and reduction runs in fp32; gradients are fp32.
+ *  - Gradient outputs: accumulate = 0 overwrites, accumulate = 1 adds.
+ *  - Scatter-type adjoints (back-projection, warp transpose) accumulate in
+ *    64-bit fixed point with a power-of-two scale chosen per call from the
+ *    largest input magnitude, so results are bit-reproducible run to run.
+ *  - Errors: host-side validation happens before any launch and returns
+ *    PMF_EINVAL / PMF_EWORKSPACE with nothing enqueued; a failed launch returns
+ *    PMF_ECUDA.  pmf_last_error() gives a message for the calling thread.
+ *  - `ws`/`ws_bytes`: caller-provided device scratch of at least the size the
+ *    matching *_workspace() query returns, 256-byte aligned; its contents on
+ *    entry do not matter and are clobbered.
+ */
+#ifndef PMF_H_
+#define PMF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* pmf_stream; /* same object as cudaStream_t */
+
+typedef enum {
+    PMF_OK = 0,
+    PMF_EINVAL = -1,      /* bad argument (null pointer, size, geometry) */
+    PMF_ECUDA = -2,       /* a CUDA launch or call failed */
+    PMF_EWORKSPACE = -3,  /* ws too small or misaligned */
+    PMF_ETIMEOUT = -4,    /* reserved: a bounded device wait gave up */
+    PMF_EUNSUPPORTED = -5 /* valid but not implemented (e.g. channels > 4) */
+} pmf_status;
+
+typedef enum { PMF_F32 = 0, PMF_BF16 = 1, PMF_F16 = 2 } pmf_dtype;
+
+/* Voxel grid: sizes and voxel spacing in mm (Sec. 2.3.3: 200x200x100 at 2 mm). */
+typedef struct {
+    int32_t nx, ny, nz;
+    float vx, vy, vz;
+} pmf_grid;
+
+/* One cone-beam view (flat detector).  src: x-ray source; det: detector
+ * centre; du/dv: one-pixel step vectors (mm).  Pixel (a, b) is centred at
+ * det + (a + 1/2 - nu/2) du + (b + 1/2 - nv/2) dv.  Double precision so that
+ * the ray directions (source ~1 m away) keep sub-micron accuracy. */
+typedef struct {
+    double src[3], det[3], du[3], dv[3];
+} pmf_view;
+
+/* Detector size and the ray-march step (mm): a ray from src with unit
+ * direction r is sampled at src + m * step * r for every integer m >= 0. */
+typedef struct {
+    int32_t nu, nv;
+    float step_mm;
+} pmf_detector;
+
+/* A Gaussian set (Eq. 4): G(x) = value * exp(-q/2),
+ * q = (x - mean)^T Sigma^-1 (x - mean), Sigma = R(quat/|quat|) diag(scale^2) R^T,
+ * truncated to q <= kappa^2 (kappa = +INFINITY: no truncation).
+ * mean [n][3] mm, scale [n][3] mm (standard deviations, > 0), quat [n][4]
+ * (w,x,y,z; need not be unit length, must be non-zero), value [n][channels]
+ * (channels = 1 for the reference densities, 3 for MBC vectors; signed values
+ * are allowed: the negative-permitting voxelizer of Sec. 2.3.1).  All device. */
+typedef struct {
+    int64_t n;
+    int32_t channels;
+    float kappa;
+    const float* mean;
+    const float* scale;
+    const float* quat;
+    const float* value;
+} pmf_gaussians;
+
+/* ----------------------------------------------------------------- status */
+
+const char* pmf_version(void);
+/* Message for the last non-OK status returned on the calling thread. */
+const char* pmf_last_error(void);
+const char* pmf_status_string(pmf_status status);
+
+/* ------------------------------------------------------ voxelizer (Eq. 4-5) */
+
+/* Bytes of scratch gs_voxelize needs for a set of n Gaussians with room for
+ * `pair_capacity` (Gaussian, 8x8x8-tile) overlaps.  Host-only. */
+pmf_status gs_voxelize_workspace(const pmf_grid* grid, int64_t n, int64_t pair_capacity, size_t* bytes);
+
+/* Exact number of (Gaussian, tile) overlaps, written to *d_pairs (device
+ * int64).  ws as for gs_voxelize with pair_capacity 0. */
+pmf_status gs_voxelize_count(const pmf_grid* grid, const pmf_gaussians* g, int64_t* d_pairs,
+                             void* ws, size_t ws_bytes, pmf_stream stream);
+
+/* Eq. 5 (channels = 1) and the signed MBC voxelizer (channels = 3):
+ * out[c][v] = sum_i value[i][c] exp(-q_i(x_v)/2) [q_i(x_v) <= kappa^2], point
+ * samples at voxel centres.  out: device [channels][N] of `dtype`.
+ * Overlaps beyond the workspace's pair capacity are still handled (slower). */
+pmf_status gs_voxelize(const pmf_grid* grid, const pmf_gaussians* g, pmf_dtype dtype, void* out,
+                       void* ws, size_t ws_bytes, pmf_stream stream);
+
+/* Adjoint of gs_voxelize with respect to every Gaussian parameter, given
+ * d_out = dL/dout (device fp32 [channels][N]).  Outputs device fp32:
+ * d_mean [n][3], d_scale [n][3], d_quat [n][4] (gradient with respect to the
+ * raw, unnormalised quaternion), d_value [n][channels].  The truncation
+ * indicator has zero derivative.  Needs no scratch. */
+pmf_status gs_voxelize_backward(const pmf_grid* grid, const pmf_gaussians* g, const float* d_out,
+                                float* d_mean, float* d_scale, float* d_quat, float* d_value,
+                                int accumulate, pmf_stream stream);
+
+/* --------------------------------------------------- DVF combine (Eq. 3) */
+
+/* dvf[p][k][v] = sum_l coeff[p][l][k] * mbc[l][k][v].  mbc [L][3][N], dvf
+ * [P][3][N] (both `dtype`, device); coeff device fp32 [P][L][3]. */
+pmf_status mbc_combine(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* mbc,
+                       const float* coeff, void* dvf, pmf_stream stream);
+
+pmf_status mbc_combine_backward_workspace(const pmf_grid* grid, int32_t L, int32_t P, size_t* bytes);
+
+/* Adjoint of mbc_combine: d_mbc[l][k][v] = sum_p d_dvf[p][k][v] coeff[p][l][k];
+ * d_coeff[p][l][k] = sum_v d_dvf[p][k][v] mbc[l][k][v] (fixed-order tree
+ * reduction).  d_dvf, d_mbc, d_coeff device fp32. */
+pmf_status mbc_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* mbc,
+                                const float* coeff, const float* d_dvf, float* d_mbc, float* d_coeff,
+                                int accumulate, void* ws, size_t ws_bytes, pmf_stream stream);
+
+/* -------------------------------------------------------- warp (Eq. 2) */
+
+/* out[p][v] = Trilin(ref, (i,j,k) + dvf[p][:,v] / (vx,vy,vz)) (pull warp; the
+ * DVF is applied in index space, so dvf = 0 returns ref exactly).
+ * ref [N], dvf [P][3][N], out [P][N]: device, `dtype`. */
+pmf_status warp_volume(const pmf_grid* grid, int32_t P, pmf_dtype dtype, const void* ref, const void* dvf,
+                       void* out, pmf_stream stream);
+
+pmf_status warp_volume_backward_workspace(const pmf_grid* grid, int32_t P, size_t* bytes);
+
+/* Adjoint of warp_volume given d_out [P][N] (fp32): d_ref [N] receives the
+ * trilinear-weight scatter summed over all P; d_dvf [P][3][N] (nullable) gets
+ * d_out * dTrilin/du / voxel (one-sided at exact integer positions). */
+pmf_status warp_volume_backward(const pmf_grid* grid, int32_t P, pmf_dtype dtype, const void* ref,
+                                const void* dvf, const float* d_out, float* d_ref, float* d_dvf,
+                                int accumulate, void* ws, size_t ws_bytes, pmf_stream stream);
+
+/* Fused Eq. 3 + Eq. 2: out[p][v] = Trilin(ref, v + sum_l coeff[p][l][:] * mbc[l][:][v] / voxel).
+ * The DVF is never stored; each voxel's MBC vectors are read once for all P. */
+pmf_status warp_combine(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
+                        const void* mbc, const float* coeff, void* out, pmf_stream stream);
+
+pmf_status warp_combine_backward_workspace(const pmf_grid* grid, int32_t L, int32_t P, size_t* bytes);
+
+/* Adjoint of warp_combine with the DVF recomputed from (mbc, coeff):
+ * d_ref [N], d_mbc [L][3][N], d_coeff [P][L][3] (device fp32). */
+pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
+                                 const void* mbc, const float* coeff, const float* d_out, float* d_ref,
+                                 float* d_mbc, float* d_coeff, int accumulate, void* ws, size_t ws_bytes,
+                                 pmf_stream stream);
+
+/* ------------------------------------------- cone-beam projector (Eq. 6) */
+
+/* proj[p][b][a] = step * sum_{m >= 0} Trilin(vol_p, idx(src_p + m step r_pab)),
+ * r_pab the unit direction from src_p to the centre of pixel (a, b), idx(x) =
+ * x / voxel + n/2 - 1/2.  views: device pmf_view[P].  vol: `dtype`, device;
+ * view p reads vol + p * vol_stride elements (vol_stride = 0: one volume
+ * shared by all views).  proj: device fp32 [P][nv][nu]. */
+pmf_status conebeam_project(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
+                            pmf_dtype dtype, const void* vol, int64_t vol_stride, float* proj,
+                            pmf_stream stream);
+
+pmf_status conebeam_project_backward_workspace(const pmf_grid* grid, int32_t P, int64_t vol_stride,
+                                               size_t* bytes);
+
+/* Exact adjoint of conebeam_project: d_vol (fp32, device; [P][N] with
+ * vol_stride = N, or [N] with vol_stride = 0 summed over views) receives
+ * step * sum over rays and samples of d_proj times the trilinear weights. */
+pmf_status conebeam_project_backward(const pmf_grid* grid, const pmf_detector* det, int32_t P,
+                                     const pmf_view* views, const float* d_proj, float* d_vol,
+                                     int64_t vol_stride, int accumulate, void* ws, size_t ws_bytes,
+                                     pmf_stream stream);
+
+/* -------------------------------------------------------- loss (Eq. 10/12) */
+
+pmf_status projection_loss_workspace(int64_t count, size_t* bytes);
+
+/* kind 1: L = mean |pred - meas| (Eq. 10/12); kind 2: L = mean (pred - meas)^2
+ * (Eq. 1), the mean over all P * Q pixels.  loss: device fp32 scalar.
+ * d_pred (nullable): sign(pred - meas)/(PQ) with sign(0) = 0, or
+ * 2 (pred - meas)/(PQ).  Fixed-order reduction. */
+pmf_status projection_loss(int32_t kind, int32_t P, int64_t Q, const float* pred, const float* meas,
+                           float* loss, float* d_pred, void* ws, size_t ws_bytes, pmf_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMF_H_ */

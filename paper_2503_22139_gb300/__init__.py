@@ -1,0 +1,21 @@
+"""GB300-native (sm_103a) forward model of PMF-STGR and its adjoint.
+
+Stages (Xie, Shao & Zhang, Sec. 2): Gaussian voxelization of the reference
+volume (Eq. 4-5) and of the signed motion-basis components, the DVF combine
+(Eq. 3), the pull warp (Eq. 2), and the cone-beam line integrals (Eq. 6) with
+an L1/L2 projection loss -- each with a hand-written adjoint.  The compute lives
+in the C-ABI library built from csrc/ (see include/pmf.h); this package is its
+argument-marshalling binding.
+"""
+from . import ops  # noqa: F401
+from .ops import (  # noqa: F401
+    Gaussians, conebeam_project, conebeam_project_backward, gs_voxelize, gs_voxelize_backward,
+    gs_voxelize_count, mbc_combine, mbc_combine_backward, projection_loss, views_tensor, warp_combine,
+    warp_combine_backward, warp_volume, warp_volume_backward,
+)
+
+__all__ = [
+    "Gaussians", "conebeam_project", "conebeam_project_backward", "gs_voxelize", "gs_voxelize_backward",
+    "gs_voxelize_count", "mbc_combine", "mbc_combine_backward", "projection_loss", "views_tensor",
+    "warp_combine", "warp_combine_backward", "warp_volume", "warp_volume_backward",
+]

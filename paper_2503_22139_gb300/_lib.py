@@ -1,0 +1,102 @@
+"""ctypes loader for the in-tree sm_103a library (libpmf.so) and its C structs.
+
+There is no fallback: if the library cannot be built or loaded, every entry
+point raises.  The structs mirror include/pmf.h field for field.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PmfGrid(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32),
+                ("vx", ct.c_float), ("vy", ct.c_float), ("vz", ct.c_float)]
+
+
+class PmfView(ct.Structure):
+    _fields_ = [("src", ct.c_double * 3), ("det", ct.c_double * 3), ("du", ct.c_double * 3), ("dv", ct.c_double * 3)]
+
+
+class PmfDetector(ct.Structure):
+    _fields_ = [("nu", ct.c_int32), ("nv", ct.c_int32), ("step_mm", ct.c_float)]
+
+
+class PmfGaussians(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("channels", ct.c_int32), ("kappa", ct.c_float),
+                ("mean", ct.c_void_p), ("scale", ct.c_void_p), ("quat", ct.c_void_p), ("value", ct.c_void_p)]
+
+
+PMF_OK = 0
+STATUS = {0: "PMF_OK", -1: "PMF_EINVAL", -2: "PMF_ECUDA", -3: "PMF_EWORKSPACE", -4: "PMF_ETIMEOUT",
+          -5: "PMF_EUNSUPPORTED"}
+DTYPE_CODES = {"f32": 0, "bf16": 1, "f16": 2}
+
+_P = ct.c_void_p
+_G = ct.POINTER(PmfGrid)
+_SZ = ct.POINTER(ct.c_size_t)
+_I32 = ct.c_int32
+_I64 = ct.c_int64
+
+# name -> argtypes (every entry point returns pmf_status as int)
+SIGNATURES = {
+    "gs_voxelize_workspace": [_G, _I64, _I64, _SZ],
+    "gs_voxelize_count": [_G, ct.POINTER(PmfGaussians), _P, _P, ct.c_size_t, _P],
+    "gs_voxelize": [_G, ct.POINTER(PmfGaussians), ct.c_int, _P, _P, ct.c_size_t, _P],
+    "gs_voxelize_backward": [_G, ct.POINTER(PmfGaussians), _P, _P, _P, _P, _P, ct.c_int, _P],
+    "mbc_combine": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P],
+    "mbc_combine_backward_workspace": [_G, _I32, _I32, _SZ],
+    "mbc_combine_backward": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
+    "warp_volume": [_G, _I32, ct.c_int, _P, _P, _P, _P],
+    "warp_volume_backward_workspace": [_G, _I32, _SZ],
+    "warp_volume_backward": [_G, _I32, ct.c_int, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
+    "warp_combine": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P],
+    "warp_combine_backward_workspace": [_G, _I32, _I32, _SZ],
+    "warp_combine_backward": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
+    "conebeam_project": [_G, ct.POINTER(PmfDetector), _I32, _P, ct.c_int, _P, _I64, _P, _P],
+    "conebeam_project_backward_workspace": [_G, _I32, _I64, _SZ],
+    "conebeam_project_backward": [_G, ct.POINTER(PmfDetector), _I32, _P, _P, _P, _I64, ct.c_int, _P, ct.c_size_t, _P],
+    "projection_loss_workspace": [_I64, _SZ],
+    "projection_loss": [_I32, _I32, _I64, _P, _P, _P, _P, _P, ct.c_size_t, _P],
+}
+
+
+class PmfError(RuntimeError):
+    pass
+
+
+def load():
+    """Build (if stale) and load libpmf.so; raises if either fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise PmfError(f"libpmf.so missing at {path}")
+            L = ct.CDLL(path)
+            for name, args in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ct.c_int
+            L.pmf_version.restype = ct.c_char_p
+            L.pmf_last_error.restype = ct.c_char_p
+            L.pmf_status_string.restype = ct.c_char_p
+            L.pmf_status_string.argtypes = [ct.c_int]
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str) -> None:
+    if status != PMF_OK:
+        msg = load().pmf_last_error().decode(errors="replace")
+        raise PmfError(f"{what}: {STATUS.get(status, status)}: {msg}")
+
+
+def library_path() -> str:
+    return _build.LIB

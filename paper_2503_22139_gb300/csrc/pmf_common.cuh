@@ -1,0 +1,157 @@
+// Shared device helpers for the PMF-STGR sm_103a kernels: storage-type loads
+// and stores, grid geometry, zero-padded trilinear interpolation, 64-bit fixed
+// point for reproducible scatters, and host-side status plumbing.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pmf.h"
+
+namespace pmf {
+
+// ------------------------------------------------------------ host status
+
+pmf_status set_error(pmf_status st, const char* fmt, ...);
+pmf_status check_launch(const char* what);
+
+#define PMF_REQUIRE(cond, ...)                                 \
+    do {                                                       \
+        if (!(cond)) return ::pmf::set_error(PMF_EINVAL, __VA_ARGS__); \
+    } while (0)
+
+pmf_status validate_grid(const pmf_grid* g);
+pmf_status validate_dtype(pmf_dtype dt);
+pmf_status validate_ws(const void* ws, size_t ws_bytes, size_t need);
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Fixed launch width for grid-stride kernels whose reductions must not depend
+// on the device: 4 x 152 SMs.
+constexpr int kStreamBlocks = 608;
+
+// ------------------------------------------------------- storage dtypes
+
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float* p, int64_t i) { return __ldg(p + i); }
+    static __device__ __forceinline__ void st(float* p, int64_t i, float v) { p[i] = v; }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i) {
+        return __bfloat162float(__ldg(p + i));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, int64_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
+    static __device__ __forceinline__ void st(__half* p, int64_t i, float v) { p[i] = __float2half_rn(v); }
+};
+
+#define PMF_DISPATCH_DTYPE(dt, T, ...)                          \
+    switch (dt) {                                               \
+        case PMF_F32: { using T = float; __VA_ARGS__; break; }  \
+        case PMF_BF16: { using T = __nv_bfloat16; __VA_ARGS__; break; } \
+        case PMF_F16: { using T = __half; __VA_ARGS__; break; } \
+        default: return ::pmf::set_error(PMF_EINVAL, "unknown dtype %d", (int)dt); \
+    }
+
+// ------------------------------------------------------------- geometry
+
+struct GridD {
+    int nx, ny, nz;
+    float vx, vy, vz;       // voxel size, mm
+    float ivx, ivy, ivz;    // 1 / voxel size
+    int64_t n;
+};
+
+inline GridD make_grid(const pmf_grid* g) {
+    GridD d;
+    d.nx = g->nx; d.ny = g->ny; d.nz = g->nz;
+    d.vx = g->vx; d.vy = g->vy; d.vz = g->vz;
+    d.ivx = 1.0f / g->vx; d.ivy = 1.0f / g->vy; d.ivz = 1.0f / g->vz;
+    d.n = (int64_t)g->nx * g->ny * g->nz;
+    return d;
+}
+
+// ---------------------------------------------------- trilinear helpers
+
+// Value of vol at integer (i,j,k), zero outside the grid.
+template <typename T>
+__device__ __forceinline__ float vox_or_zero(const T* vol, const GridD& g, int i, int j, int k) {
+    bool in = (unsigned)i < (unsigned)g.nx && (unsigned)j < (unsigned)g.ny && (unsigned)k < (unsigned)g.nz;
+    return in ? Store<T>::ld(vol, ((int64_t)k * g.ny + j) * g.nx + i) : 0.0f;
+}
+
+// Zero-padded trilinear interpolation at cell (i0,j0,k0) with fractions f.
+template <typename T>
+__device__ __forceinline__ float trilin_cell(const T* vol, const GridD& g, int i0, int j0, int k0, float fx,
+                                             float fy, float fz) {
+    float c000 = vox_or_zero(vol, g, i0, j0, k0), c100 = vox_or_zero(vol, g, i0 + 1, j0, k0);
+    float c010 = vox_or_zero(vol, g, i0, j0 + 1, k0), c110 = vox_or_zero(vol, g, i0 + 1, j0 + 1, k0);
+    float c001 = vox_or_zero(vol, g, i0, j0, k0 + 1), c101 = vox_or_zero(vol, g, i0 + 1, j0, k0 + 1);
+    float c011 = vox_or_zero(vol, g, i0, j0 + 1, k0 + 1), c111 = vox_or_zero(vol, g, i0 + 1, j0 + 1, k0 + 1);
+    float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
+    float a01 = fmaf(fx, c101 - c001, c001), a11 = fmaf(fx, c111 - c011, c011);
+    float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
+    return fmaf(fz, b1 - b0, b0);
+}
+
+// Split a small offset t (in voxels) into floor and fraction exactly.
+__device__ __forceinline__ void split_offset(float t, int& fl, float& f) {
+    float ft = floorf(t);
+    fl = (int)ft;
+    f = t - ft;
+}
+
+// ------------------------------------------------------- fixed point
+//
+// Reproducible scatter: every contribution is rounded to an integer multiple of
+// 2^-e and added with 64-bit integer atomics, which are order independent.
+// e is chosen per call so that `bound` (a provable bound on the magnitude of
+// any accumulated sum) stays below 2^62.
+
+__device__ __forceinline__ int fixed_exponent(float bound) {
+    if (!(bound > 0.0f) || !isfinite(bound)) return 0;
+    int e;
+    frexpf(bound, &e);  // bound < 2^e
+    int k = 62 - e;
+    return k > 126 ? 126 : (k < -126 ? -126 : k);
+}
+
+__device__ __forceinline__ unsigned long long to_fixed(float x, float scale) {
+    return (unsigned long long)__float2ll_rn(x * scale);
+}
+
+__device__ __forceinline__ float from_fixed(unsigned long long a, float inv_scale) {
+    return __ll2float_rn((long long)a) * inv_scale;
+}
+
+__device__ __forceinline__ void red_add(unsigned long long* p, unsigned long long v) {
+    if (v) atomicAdd(p, v);
+}
+
+// Non-negative float max via the order-preserving bit pattern.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned int* p, float v) {
+    if (v > 0.0f) atomicMax(p, __float_as_uint(v));
+}
+
+// --------------------------------------------------- block reductions
+
+template <int NT>
+__device__ __forceinline__ float block_sum(float v, float* smem) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem[w] = v;
+    __syncthreads();
+    float r = 0.0f;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NT / 32; i++) r += smem[i];
+    }
+    return r;  // valid in thread 0
+}
+
+}  // namespace pmf

@@ -1,0 +1,537 @@
+// Tile-binned Gaussian voxelizer (Eq. 4-5 and the signed MBC variant of
+// Sec. 2.3.1) and its adjoint, for sm_103a.
+//
+// Forward: (1) per Gaussian, the inverse covariance and the voxel box of its
+// truncation ellipsoid; count the 8x8x8 tiles it overlaps; (2) exclusive scan
+// of the per-tile counts; (3) fill per-tile Gaussian lists; (4) one CTA per
+// tile stages its list in shared memory and sums every entry at its 512 voxel
+// centres.  Sums are kept in 64-bit fixed point (scale 2^k with
+// G * max|value| * 2^k < 2^62), so the unordered list fill cannot change a bit
+// of the result.
+//
+// Backward: one CTA per Gaussian walks its voxel box, accumulates
+// sum_v dL/dout_c * e, and the moments S1 = sum w d, S2 = sum w d d^T
+// (w = e * sum_c value_c dL/dout_c), reduces them in a fixed order, and turns
+// them into d mean = A S1, d scale_j = (R^T S2 R)_jj / s_j^3,
+// dR = -S2 R diag(1/s^2), then d quaternion through R(q/|q|).
+#include "pmf_common.cuh"
+
+namespace pmf {
+namespace {
+
+constexpr int kTile = 8;              // tile edge (voxels)
+constexpr int kRenderThreads = 256;   // 2 voxels per thread
+constexpr int kMaxC = 4;
+constexpr float kNegHalfLog2e = -0.72134752044448170368f;  // -log2(e)/2
+
+struct VoxHeader {
+    unsigned int max_abs_bits;  // max |value| over all Gaussians and channels (float bits)
+    unsigned int pad;
+    long long total_pairs;
+};
+
+struct VoxWs {
+    VoxHeader* hdr;
+    float* prm;        // [10][G]: mx my mz a00 a11 a22 b01 b02 b12 (b = 2 a) and k2
+    int* box;          // [6][G]: voxel lo xyz, hi xyz (lo > hi: empty)
+    unsigned* tcount;  // [T]
+    unsigned* toff;    // [T+1]
+    unsigned* cursor;  // [T]
+    unsigned* list;    // [capacity]
+    int64_t capacity;
+};
+
+struct TileGeom {
+    int tx, ty, tz;
+    int64_t t;
+};
+
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+size_t vox_ws_layout(const GridD& g, int64_t G, int64_t capacity, VoxWs* w, char* base) {
+    int tx = ceil_div(g.nx, kTile), ty = ceil_div(g.ny, kTile), tz = ceil_div(g.nz, kTile);
+    int64_t T = (int64_t)tx * ty * tz;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return base ? base + o : nullptr; };
+    VoxWs x;
+    x.hdr = (VoxHeader*)take(sizeof(VoxHeader));
+    x.prm = (float*)take(sizeof(float) * 10 * (size_t)(G > 0 ? G : 1));
+    x.box = (int*)take(sizeof(int) * 6 * (size_t)(G > 0 ? G : 1));
+    x.tcount = (unsigned*)take(sizeof(unsigned) * (size_t)T);
+    x.toff = (unsigned*)take(sizeof(unsigned) * (size_t)(T + 1));
+    x.cursor = (unsigned*)take(sizeof(unsigned) * (size_t)T);
+    x.list = (unsigned*)take(sizeof(unsigned) * (size_t)(capacity > 0 ? capacity : 1));
+    x.capacity = capacity;
+    if (w) *w = x;
+    return off;
+}
+
+// Per-Gaussian setup shared by forward and backward so that both take the
+// same truncation decisions: rotation of the normalised quaternion, inverse
+// covariance A = R diag(1/s^2) R^T, and the voxel box of {q <= kappa^2}.
+struct GaussSetup {
+    float mu[3], s[3], qn[4], qnorm, R[9];
+    float a00, a11, a22, b01, b02, b12;  // q = a00 dx^2 + a11 dy^2 + a22 dz^2 + b01 dx dy + b02 dx dz + b12 dy dz
+    int lo[3], hi[3];
+};
+
+__device__ __forceinline__ void gauss_setup(const pmf_gaussians& G, int64_t i, const GridD& g, float kappa,
+                                            GaussSetup& o) {
+    o.mu[0] = __ldg(G.mean + 3 * i); o.mu[1] = __ldg(G.mean + 3 * i + 1); o.mu[2] = __ldg(G.mean + 3 * i + 2);
+    o.s[0] = __ldg(G.scale + 3 * i); o.s[1] = __ldg(G.scale + 3 * i + 1); o.s[2] = __ldg(G.scale + 3 * i + 2);
+    float qw = __ldg(G.quat + 4 * i), qx = __ldg(G.quat + 4 * i + 1), qy = __ldg(G.quat + 4 * i + 2),
+          qz = __ldg(G.quat + 4 * i + 3);
+    float nrm = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    float inv = 1.0f / nrm;
+    float w = qw * inv, x = qx * inv, y = qy * inv, z = qz * inv;
+    o.qn[0] = w; o.qn[1] = x; o.qn[2] = y; o.qn[3] = z; o.qnorm = nrm;
+    float* R = o.R;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+    float is2[3] = {1.f / (o.s[0] * o.s[0]), 1.f / (o.s[1] * o.s[1]), 1.f / (o.s[2] * o.s[2])};
+    float A[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            A[a][b] = R[3 * a] * R[3 * b] * is2[0] + R[3 * a + 1] * R[3 * b + 1] * is2[1] +
+                      R[3 * a + 2] * R[3 * b + 2] * is2[2];
+    o.a00 = A[0][0]; o.a11 = A[1][1]; o.a22 = A[2][2];
+    o.b01 = A[0][1] + A[1][0]; o.b02 = A[0][2] + A[2][0]; o.b12 = A[1][2] + A[2][1];
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const float iv[3] = {g.ivx, g.ivy, g.ivz};
+    for (int a = 0; a < 3; a++) {
+        float var = R[3 * a] * R[3 * a] * o.s[0] * o.s[0] + R[3 * a + 1] * R[3 * a + 1] * o.s[1] * o.s[1] +
+                    R[3 * a + 2] * R[3 * a + 2] * o.s[2] * o.s[2];
+        float half = kappa * sqrtf(var);
+        float c = o.mu[a] * iv[a] + 0.5f * (float)n[a] - 0.5f;
+        float l = floorf(c - half * iv[a]) - 1.0f, h = ceilf(c + half * iv[a]) + 1.0f;
+        // clamp to the grid; fmaxf/fminf drop a NaN operand, so a NaN box comes out empty
+        l = fminf(fmaxf(l, 0.0f), (float)n[a]);
+        h = fminf(fmaxf(h, -1.0f), (float)(n[a] - 1));
+        o.lo[a] = (int)l;
+        o.hi[a] = (int)h;
+    }
+}
+
+// The quadratic form, written with explicit fused multiply-adds so every
+// kernel that calls it rounds identically.
+__device__ __forceinline__ float qform(float dx, float dy, float dz, float a00, float a11, float a22, float b01,
+                                       float b02, float b12) {
+    float tx = __fmaf_rn(a00, dx, __fmaf_rn(b01, dy, __fmul_rn(b02, dz)));
+    float ty = __fmaf_rn(a11, dy, __fmul_rn(b12, dz));
+    return __fmaf_rn(dx, tx, __fmaf_rn(dy, ty, __fmul_rn(__fmul_rn(a22, dz), dz)));
+}
+
+// Voxel-centre coordinate (i + 1/2 - n/2) v, rounded the same way everywhere.
+__device__ __forceinline__ float centre(int i, int n, float v) {
+    return __fmul_rn(__fsub_rn(__fadd_rn((float)i, 0.5f), __fmul_rn(0.5f, (float)n)), v);
+}
+
+// ------------------------------------------------------------- forward
+
+// One warp per Gaussian: lane 0 stores the setup, all lanes count tiles.
+__global__ void k_prep(pmf_gaussians G, GridD g, float kappa, VoxWs w, int ntx, int nty) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= G.n) return;
+    GaussSetup s;
+    gauss_setup(G, i, g, kappa, s);
+    const int64_t n = G.n;
+    if (lane == 0) {
+        float k2 = isinf(kappa) ? INFINITY : kappa * kappa;
+        float* p = w.prm;
+        p[0 * n + i] = s.mu[0]; p[1 * n + i] = s.mu[1]; p[2 * n + i] = s.mu[2];
+        p[3 * n + i] = s.a00; p[4 * n + i] = s.a11; p[5 * n + i] = s.a22;
+        p[6 * n + i] = s.b01; p[7 * n + i] = s.b02; p[8 * n + i] = s.b12; p[9 * n + i] = k2;
+        for (int a = 0; a < 3; a++) { w.box[a * n + i] = s.lo[a]; w.box[(3 + a) * n + i] = s.hi[a]; }
+        float m = 0.0f;
+        for (int c = 0; c < G.channels; c++) m = fmaxf(m, fabsf(__ldg(G.value + i * G.channels + c)));
+        atomic_max_nonneg(&w.hdr->max_abs_bits, m);
+    }
+    if (s.lo[0] > s.hi[0] || s.lo[1] > s.hi[1] || s.lo[2] > s.hi[2]) return;
+    const int t0x = s.lo[0] / kTile, t1x = s.hi[0] / kTile, t0y = s.lo[1] / kTile, t1y = s.hi[1] / kTile,
+              t0z = s.lo[2] / kTile, t1z = s.hi[2] / kTile;
+    const int ex = t1x - t0x + 1, ey = t1y - t0y + 1, ez = t1z - t0z + 1;
+    const int cnt = ex * ey * ez;
+    for (int c = lane; c < cnt; c += 32) {
+        int x = t0x + c % ex, y = t0y + (c / ex) % ey, z = t0z + c / (ex * ey);
+        atomicAdd(&w.tcount[((int64_t)z * nty + y) * ntx + x], 1u);
+    }
+}
+
+// Exclusive scan of the tile counts in one CTA (T is at most a few 1e5).
+__global__ void k_scan(VoxWs w, int64_t T) {
+    __shared__ unsigned long long part[1024];
+    const int tid = threadIdx.x;
+    const int64_t per = (T + 1023) / 1024;
+    const int64_t b = tid * per, e = b + per < T ? b + per : T;
+    unsigned long long s = 0;
+    for (int64_t i = b; i < e; i++) s += w.tcount[i];
+    part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long run = 0;
+        for (int i = 0; i < 1024; i++) { unsigned long long v = part[i]; part[i] = run; run += v; }
+        w.hdr->total_pairs = (long long)run;
+    }
+    __syncthreads();
+    unsigned long long run = part[tid];
+    for (int64_t i = b; i < e; i++) {
+        w.toff[i] = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
+        run += w.tcount[i];
+    }
+    if (tid == 1023) w.toff[T] = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
+}
+
+__global__ void k_fill(int64_t n, VoxWs w, int ntx, int nty) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; a++) { lo[a] = w.box[a * n + i]; hi[a] = w.box[(3 + a) * n + i]; }
+    if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2]) return;
+    const int t0x = lo[0] / kTile, t0y = lo[1] / kTile, t0z = lo[2] / kTile;
+    const int ex = hi[0] / kTile - t0x + 1, ey = hi[1] / kTile - t0y + 1, ez = hi[2] / kTile - t0z + 1;
+    const int cnt = ex * ey * ez;
+    for (int c = lane; c < cnt; c += 32) {
+        int x = t0x + c % ex, y = t0y + (c / ex) % ey, z = t0z + c / (ex * ey);
+        int64_t t = ((int64_t)z * nty + y) * ntx + x;
+        unsigned pos = atomicAdd(&w.cursor[t], 1u);
+        unsigned long long at = (unsigned long long)w.toff[t] + pos;
+        if ((long long)at < w.capacity) w.list[at] = (unsigned)i;
+    }
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, GridD g, VoxWs w, T* out, int ntx,
+                                                           int nty) {
+    __shared__ float sm[10][kRenderThreads];
+    __shared__ float sv[C][kRenderThreads];
+    __shared__ unsigned sidx[kRenderThreads];
+    __shared__ int scount;
+    const int tid = threadIdx.x;
+    const int64_t t = blockIdx.x;
+    const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((int64_t)ntx * nty));
+    const int ix = tx * kTile + (tid & 7), iy = ty * kTile + ((tid >> 3) & 7);
+    const int iz0 = tz * kTile + (tid >> 6), iz1 = iz0 + 4;
+    const float cx = centre(ix, g.nx, g.vx), cy = centre(iy, g.ny, g.vy);
+    const float cz0 = centre(iz0, g.nz, g.vz), cz1 = centre(iz1, g.nz, g.vz);
+
+    const float maxabs = __uint_as_float(w.hdr->max_abs_bits);
+    const int kexp = fixed_exponent(maxabs * (float)(G.n > 0 ? G.n : 1));
+    const float scale = ldexpf(1.0f, kexp), inv_scale = ldexpf(1.0f, -kexp);
+
+    long long acc0[C], acc1[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) { acc0[c] = 0; acc1[c] = 0; }
+
+    const int64_t n = G.n;
+    const unsigned cnt = w.tcount[t];
+    const unsigned long long off = w.toff[t];
+    const bool listed = (long long)(off + cnt) <= w.capacity && w.toff[t] != 0xffffffffu;
+    // Listed tiles walk their own list; overflowed tiles scan every Gaussian's box.
+    const int64_t total = listed ? (int64_t)cnt : n;
+    const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
+    for (int64_t base = 0; base < total; base += kRenderThreads) {
+        __syncthreads();
+        if (tid == 0) scount = 0;
+        __syncthreads();
+        const int64_t k = base + tid;
+        if (k < total) {
+            unsigned gi;
+            bool take;
+            if (listed) {
+                gi = w.list[off + k];
+                take = true;
+            } else {
+                gi = (unsigned)k;
+                int lx = w.box[k], ly = w.box[n + k], lz = w.box[2 * n + k];
+                int hx = w.box[3 * n + k], hy = w.box[4 * n + k], hz = w.box[5 * n + k];
+                take = lx <= hx && ly <= hy && lz <= hz && lx <= x0 + kTile - 1 && hx >= x0 && ly <= y0 + kTile - 1 &&
+                       hy >= y0 && lz <= z0 + kTile - 1 && hz >= z0;
+            }
+            if (take) {
+                int slot = listed ? tid : atomicAdd(&scount, 1);
+                sidx[slot] = gi;
+            }
+        }
+        if (listed) {
+            if (tid == 0) scount = (int)((total - base) < kRenderThreads ? (total - base) : kRenderThreads);
+        }
+        __syncthreads();
+        const int m = scount;
+        if (tid < m) {
+            unsigned gi = sidx[tid];
+#pragma unroll
+            for (int f = 0; f < 10; f++) sm[f][tid] = w.prm[(int64_t)f * n + gi];
+#pragma unroll
+            for (int c = 0; c < C; c++) sv[c][tid] = __ldg(G.value + (int64_t)gi * C + c) * scale;
+        }
+        __syncthreads();
+        for (int j = 0; j < m; j++) {
+            const float dx = cx - sm[0][j], dy = cy - sm[1][j];
+            const float a00 = sm[3][j], a11 = sm[4][j], a22 = sm[5][j], b01 = sm[6][j], b02 = sm[7][j],
+                        b12 = sm[8][j], k2 = sm[9][j];
+            const float dz0 = cz0 - sm[2][j], dz1 = cz1 - sm[2][j];
+            const float q0 = qform(dx, dy, dz0, a00, a11, a22, b01, b02, b12);
+            const float q1 = qform(dx, dy, dz1, a00, a11, a22, b01, b02, b12);
+            if (q0 <= k2) {
+                const float e = exp2f(q0 * kNegHalfLog2e);
+#pragma unroll
+                for (int c = 0; c < C; c++) acc0[c] += __float2ll_rn(sv[c][j] * e);
+            }
+            if (q1 <= k2) {
+                const float e = exp2f(q1 * kNegHalfLog2e);
+#pragma unroll
+                for (int c = 0; c < C; c++) acc1[c] += __float2ll_rn(sv[c][j] * e);
+            }
+        }
+    }
+    const int64_t N = g.n;
+    if (ix < g.nx && iy < g.ny) {
+        if (iz0 < g.nz) {
+            const int64_t v = ((int64_t)iz0 * g.ny + iy) * g.nx + ix;
+#pragma unroll
+            for (int c = 0; c < C; c++) Store<T>::st(out, c * N + v, __ll2float_rn(acc0[c]) * inv_scale);
+        }
+        if (iz1 < g.nz) {
+            const int64_t v = ((int64_t)iz1 * g.ny + iy) * g.nx + ix;
+#pragma unroll
+            for (int c = 0; c < C; c++) Store<T>::st(out, c * N + v, __ll2float_rn(acc1[c]) * inv_scale);
+        }
+    }
+}
+
+__global__ void k_copy_total(const VoxWs w, int64_t* d_pairs) { *d_pairs = w.hdr->total_pairs; }
+
+// ------------------------------------------------------------ backward
+
+constexpr int kBwdThreads = 128;
+
+template <int C>
+__global__ void __launch_bounds__(kBwdThreads) k_vox_bwd(pmf_gaussians G, GridD g, const float* __restrict__ dout,
+                                                         float* d_mean, float* d_scale, float* d_quat,
+                                                         float* d_value, int accumulate) {
+    __shared__ float red[kBwdThreads / 32][C + 9];
+    const int64_t i = blockIdx.x;
+    GaussSetup s;
+    gauss_setup(G, i, g, G.kappa, s);
+    const float k2 = isinf(G.kappa) ? INFINITY : G.kappa * G.kappa;
+    float val[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) val[c] = __ldg(G.value + i * C + c);
+    float gv[C], S1[3] = {0.f, 0.f, 0.f}, S2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < C; c++) gv[c] = 0.f;
+    const int64_t N = g.n;
+    if (s.lo[0] <= s.hi[0] && s.lo[1] <= s.hi[1] && s.lo[2] <= s.hi[2]) {
+        const int ex = s.hi[0] - s.lo[0] + 1, ey = s.hi[1] - s.lo[1] + 1, ez = s.hi[2] - s.lo[2] + 1;
+        const int64_t cnt = (int64_t)ex * ey * ez;
+        for (int64_t c0 = threadIdx.x; c0 < cnt; c0 += kBwdThreads) {
+            const int x = s.lo[0] + (int)(c0 % ex);
+            const int y = s.lo[1] + (int)((c0 / ex) % ey);
+            const int z = s.lo[2] + (int)(c0 / ((int64_t)ex * ey));
+            const float dx = centre(x, g.nx, g.vx) - s.mu[0];
+            const float dy = centre(y, g.ny, g.vy) - s.mu[1];
+            const float dz = centre(z, g.nz, g.vz) - s.mu[2];
+            const float q = qform(dx, dy, dz, s.a00, s.a11, s.a22, s.b01, s.b02, s.b12);
+            if (!(q <= k2)) continue;
+            const float e = exp2f(q * kNegHalfLog2e);
+            const int64_t v = ((int64_t)z * g.ny + y) * g.nx + x;
+            float sw = 0.f;
+#pragma unroll
+            for (int c = 0; c < C; c++) {
+                const float go = __ldg(dout + c * N + v);
+                gv[c] = fmaf(go, e, gv[c]);
+                sw = fmaf(val[c], go, sw);
+            }
+            const float wgt = sw * e;
+            S1[0] = fmaf(wgt, dx, S1[0]); S1[1] = fmaf(wgt, dy, S1[1]); S1[2] = fmaf(wgt, dz, S1[2]);
+            const float wx = wgt * dx, wy = wgt * dy;
+            S2[0] = fmaf(wx, dx, S2[0]); S2[1] = fmaf(wx, dy, S2[1]); S2[2] = fmaf(wx, dz, S2[2]);
+            S2[3] = fmaf(wy, dy, S2[3]); S2[4] = fmaf(wy, dz, S2[4]); S2[5] = fmaf(wgt * dz, dz, S2[5]);
+        }
+    }
+    // fixed-order reduction: butterfly within warps, then warps in order
+    float r[C + 9];
+#pragma unroll
+    for (int c = 0; c < C; c++) r[c] = gv[c];
+#pragma unroll
+    for (int a = 0; a < 3; a++) r[C + a] = S1[a];
+#pragma unroll
+    for (int a = 0; a < 6; a++) r[C + 3 + a] = S2[a];
+#pragma unroll
+    for (int k = 0; k < C + 9; k++)
+        for (int o = 16; o > 0; o >>= 1) r[k] += __shfl_xor_sync(0xffffffffu, r[k], o);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < C + 9; k++) red[threadIdx.x >> 5][k] = r[k];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int k = 0; k < C + 9; k++) {
+        float t = 0.f;
+        for (int wi = 0; wi < kBwdThreads / 32; wi++) t += red[wi][k];
+        r[k] = t;
+    }
+    const float* s1 = r + C;
+    const float* s2v = r + C + 3;
+    const float S2m[3][3] = {{s2v[0], s2v[1], s2v[2]}, {s2v[1], s2v[3], s2v[4]}, {s2v[2], s2v[4], s2v[5]}};
+    const float A[3][3] = {{s.a00, 0.5f * s.b01, 0.5f * s.b02},
+                           {0.5f * s.b01, s.a11, 0.5f * s.b12},
+                           {0.5f * s.b02, 0.5f * s.b12, s.a22}};
+    float gmu[3], gs[3], gR[9];
+    for (int a = 0; a < 3; a++) gmu[a] = A[a][0] * s1[0] + A[a][1] * s1[1] + A[a][2] * s1[2];
+    float S2R[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int j = 0; j < 3; j++)
+            S2R[a][j] = S2m[a][0] * s.R[0 * 3 + j] + S2m[a][1] * s.R[1 * 3 + j] + S2m[a][2] * s.R[2 * 3 + j];
+    for (int j = 0; j < 3; j++) {
+        float d = s.R[0 * 3 + j] * S2R[0][j] + s.R[1 * 3 + j] * S2R[1][j] + s.R[2 * 3 + j] * S2R[2][j];
+        gs[j] = d / (s.s[j] * s.s[j] * s.s[j]);
+        for (int a = 0; a < 3; a++) gR[3 * a + j] = -S2R[a][j] / (s.s[j] * s.s[j]);
+    }
+    // dR/d(w,x,y,z) of R(q/|q|), then the normalisation Jacobian (I - qq^T)/|q|
+    const float w = s.qn[0], x = s.qn[1], y = s.qn[2], z = s.qn[3];
+    const float dRw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+    const float dRx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+    const float dRy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+    const float dRz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+    float gq[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t = 0; t < 9; t++) {
+        gq[0] += gR[t] * dRw[t]; gq[1] += gR[t] * dRx[t]; gq[2] += gR[t] * dRy[t]; gq[3] += gR[t] * dRz[t];
+    }
+    const float dot = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    const float qn[4] = {w, x, y, z};
+    const float inv = 1.0f / s.qnorm;
+    for (int c = 0; c < 4; c++) {
+        float v = (gq[c] - qn[c] * dot) * inv;
+        d_quat[4 * i + c] = accumulate ? d_quat[4 * i + c] + v : v;
+    }
+    for (int a = 0; a < 3; a++) {
+        d_mean[3 * i + a] = accumulate ? d_mean[3 * i + a] + gmu[a] : gmu[a];
+        d_scale[3 * i + a] = accumulate ? d_scale[3 * i + a] + gs[a] : gs[a];
+    }
+    for (int c = 0; c < C; c++) d_value[i * C + c] = accumulate ? d_value[i * C + c] + r[c] : r[c];
+}
+
+pmf_status validate_gaussians(const pmf_gaussians* g) {
+    PMF_REQUIRE(g != nullptr, "gaussians is null");
+    PMF_REQUIRE(g->n >= 0 && g->n < ((int64_t)1 << 31), "gaussian count %lld out of range", (long long)g->n);
+    PMF_REQUIRE(g->channels >= 1, "channels must be >= 1");
+    if (g->channels > kMaxC) return set_error(PMF_EUNSUPPORTED, "channels > %d not supported", kMaxC);
+    PMF_REQUIRE(g->kappa > 0.0f, "kappa must be > 0 (use INFINITY for no truncation)");
+    if (g->n > 0)
+        PMF_REQUIRE(g->mean && g->scale && g->quat && g->value, "gaussian arrays must be non-null");
+    return PMF_OK;
+}
+
+pmf_status run_prep_scan(const pmf_grid* grid, const pmf_gaussians* gs, const VoxWs& w, const GridD& g,
+                         cudaStream_t st, int ntx, int nty, int64_t T) {
+    cudaMemsetAsync(w.hdr, 0, sizeof(VoxHeader), st);
+    cudaMemsetAsync(w.tcount, 0, sizeof(unsigned) * (size_t)T, st);
+    cudaMemsetAsync(w.cursor, 0, sizeof(unsigned) * (size_t)T, st);
+    if (gs->n > 0) {
+        int64_t threads = gs->n * 32;
+        k_prep<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(*gs, g, gs->kappa, w, ntx, nty);
+    }
+    k_scan<<<1, 1024, 0, st>>>(w, T);
+    (void)grid;
+    return check_launch("gs_voxelize prep");
+}
+
+}  // namespace
+}  // namespace pmf
+
+using namespace pmf;
+
+extern "C" {
+
+pmf_status gs_voxelize_workspace(const pmf_grid* grid, int64_t n, int64_t pair_capacity, size_t* bytes) {
+    pmf_status st = validate_grid(grid);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(bytes != nullptr, "bytes is null");
+    PMF_REQUIRE(n >= 0 && pair_capacity >= 0 && pair_capacity < ((int64_t)1 << 32), "bad sizes");
+    GridD g = make_grid(grid);
+    *bytes = vox_ws_layout(g, n, pair_capacity, nullptr, nullptr);
+    return PMF_OK;
+}
+
+pmf_status gs_voxelize_count(const pmf_grid* grid, const pmf_gaussians* gs, int64_t* d_pairs, void* ws,
+                             size_t ws_bytes, pmf_stream stream) {
+    pmf_status st = validate_grid(grid);
+    if (st != PMF_OK) return st;
+    if ((st = validate_gaussians(gs)) != PMF_OK) return st;
+    PMF_REQUIRE(d_pairs != nullptr, "d_pairs is null");
+    GridD g = make_grid(grid);
+    size_t need = vox_ws_layout(g, gs->n, 0, nullptr, nullptr);
+    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
+    VoxWs w;
+    vox_ws_layout(g, gs->n, 0, &w, (char*)ws);
+    const int ntx = (g.nx + kTile - 1) / kTile, nty = (g.ny + kTile - 1) / kTile, ntz = (g.nz + kTile - 1) / kTile;
+    const int64_t T = (int64_t)ntx * nty * ntz;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = run_prep_scan(grid, gs, w, g, s, ntx, nty, T)) != PMF_OK) return st;
+    k_copy_total<<<1, 1, 0, s>>>(w, d_pairs);
+    return check_launch("gs_voxelize_count");
+}
+
+pmf_status gs_voxelize(const pmf_grid* grid, const pmf_gaussians* gs, pmf_dtype dtype, void* out, void* ws,
+                       size_t ws_bytes, pmf_stream stream) {
+    pmf_status st = validate_grid(grid);
+    if (st != PMF_OK) return st;
+    if ((st = validate_gaussians(gs)) != PMF_OK) return st;
+    if ((st = validate_dtype(dtype)) != PMF_OK) return st;
+    PMF_REQUIRE(out != nullptr, "out is null");
+    GridD g = make_grid(grid);
+    size_t fixed = vox_ws_layout(g, gs->n, 0, nullptr, nullptr);
+    if ((st = validate_ws(ws, ws_bytes, fixed)) != PMF_OK) return st;
+    // whatever is left after the fixed part holds the pair list
+    int64_t cap = (int64_t)((ws_bytes - fixed) / sizeof(unsigned)) + 1;
+    while (cap > 0 && vox_ws_layout(g, gs->n, cap, nullptr, nullptr) > ws_bytes) cap -= 64;
+    if (cap < 0) cap = 0;
+    if (cap > 0xfffffff0ll) cap = 0xfffffff0ll;
+    VoxWs w;
+    vox_ws_layout(g, gs->n, cap, &w, (char*)ws);
+    const int ntx = (g.nx + kTile - 1) / kTile, nty = (g.ny + kTile - 1) / kTile, ntz = (g.nz + kTile - 1) / kTile;
+    const int64_t T = (int64_t)ntx * nty * ntz;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = run_prep_scan(grid, gs, w, g, s, ntx, nty, T)) != PMF_OK) return st;
+    if (gs->n > 0) {
+        int64_t threads = gs->n * 32;
+        k_fill<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(gs->n, w, ntx, nty);
+    }
+    PMF_DISPATCH_DTYPE(dtype, T_, {
+        T_* o = (T_*)out;
+        switch (gs->channels) {
+            case 1: k_render<T_, 1><<<(unsigned)T, kRenderThreads, 0, s>>>(*gs, g, w, o, ntx, nty); break;
+            case 2: k_render<T_, 2><<<(unsigned)T, kRenderThreads, 0, s>>>(*gs, g, w, o, ntx, nty); break;
+            case 3: k_render<T_, 3><<<(unsigned)T, kRenderThreads, 0, s>>>(*gs, g, w, o, ntx, nty); break;
+            default: k_render<T_, 4><<<(unsigned)T, kRenderThreads, 0, s>>>(*gs, g, w, o, ntx, nty); break;
+        }
+    });
+    return check_launch("gs_voxelize");
+}
+
+pmf_status gs_voxelize_backward(const pmf_grid* grid, const pmf_gaussians* gs, const float* d_out, float* d_mean,
+                                float* d_scale, float* d_quat, float* d_value, int accumulate, pmf_stream stream) {
+    pmf_status st = validate_grid(grid);
+    if (st != PMF_OK) return st;
+    if ((st = validate_gaussians(gs)) != PMF_OK) return st;
+    if (gs->n == 0) return PMF_OK;
+    PMF_REQUIRE(d_out && d_mean && d_scale && d_quat && d_value, "null gradient pointer");
+    PMF_REQUIRE(gs->n <= 0x7fffffffll, "too many gaussians for one launch");
+    GridD g = make_grid(grid);
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned nb = (unsigned)gs->n;
+    switch (gs->channels) {
+        case 1: k_vox_bwd<1><<<nb, kBwdThreads, 0, s>>>(*gs, g, d_out, d_mean, d_scale, d_quat, d_value, accumulate); break;
+        case 2: k_vox_bwd<2><<<nb, kBwdThreads, 0, s>>>(*gs, g, d_out, d_mean, d_scale, d_quat, d_value, accumulate); break;
+        case 3: k_vox_bwd<3><<<nb, kBwdThreads, 0, s>>>(*gs, g, d_out, d_mean, d_scale, d_quat, d_value, accumulate); break;
+        default: k_vox_bwd<4><<<nb, kBwdThreads, 0, s>>>(*gs, g, d_out, d_mean, d_scale, d_quat, d_value, accumulate); break;
+    }
+    return check_launch("gs_voxelize_backward");
+}
+
+}  // extern "C"

@@ -1,0 +1,499 @@
+// DVF combine (Eq. 3), pull warp (Eq. 2), their fusion, and the adjoints, for
+// sm_103a.  All streaming kernels are grid-stride loops over voxels with a fixed
+// grid (so reductions do not depend on the device); coefficient tables are read
+// through the read-only cache as warp-uniform broadcasts.
+//
+// Reproducibility: the warp transpose scatters into d_ref with 64-bit
+// fixed-point atomics (scale chosen from max |d_out| * P * N < 2^62); the
+// coefficient gradients are block partials reduced in a fixed order.
+#include "pmf_common.cuh"
+
+namespace pmf {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxL = 8;
+
+// Corner weights of a trilinear cell and their derivatives with respect to
+// the fractional position.
+struct Cell {
+    int i0, j0, k0;
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ Cell make_cell(int i, int j, int k, float tx, float ty, float tz) {
+    Cell c;
+    int ox, oy, oz;
+    split_offset(tx, ox, c.fx);
+    split_offset(ty, oy, c.fy);
+    split_offset(tz, oz, c.fz);
+    c.i0 = i + ox; c.j0 = j + oy; c.k0 = k + oz;
+    return c;
+}
+
+// Trilinear value and gradient (with respect to the continuous index) of vol
+// at a cell; zero padding outside the grid.
+template <typename T>
+__device__ __forceinline__ float trilin_grad(const T* vol, const GridD& g, const Cell& c, float& gx, float& gy,
+                                             float& gz) {
+    float v000 = vox_or_zero(vol, g, c.i0, c.j0, c.k0), v100 = vox_or_zero(vol, g, c.i0 + 1, c.j0, c.k0);
+    float v010 = vox_or_zero(vol, g, c.i0, c.j0 + 1, c.k0), v110 = vox_or_zero(vol, g, c.i0 + 1, c.j0 + 1, c.k0);
+    float v001 = vox_or_zero(vol, g, c.i0, c.j0, c.k0 + 1), v101 = vox_or_zero(vol, g, c.i0 + 1, c.j0, c.k0 + 1);
+    float v011 = vox_or_zero(vol, g, c.i0, c.j0 + 1, c.k0 + 1), v111 = vox_or_zero(vol, g, c.i0 + 1, c.j0 + 1, c.k0 + 1);
+    float a00 = fmaf(c.fx, v100 - v000, v000), a10 = fmaf(c.fx, v110 - v010, v010);
+    float a01 = fmaf(c.fx, v101 - v001, v001), a11 = fmaf(c.fx, v111 - v011, v011);
+    float b0 = fmaf(c.fy, a10 - a00, a00), b1 = fmaf(c.fy, a11 - a01, a01);
+    gz = b1 - b0;
+    gy = fmaf(c.fz, (a11 - a01) - (a10 - a00), a10 - a00);
+    float ex0 = fmaf(c.fy, (v110 - v010) - (v100 - v000), v100 - v000);
+    float ex1 = fmaf(c.fy, (v111 - v011) - (v101 - v001), v101 - v001);
+    gx = fmaf(c.fz, ex1 - ex0, ex0);
+    return fmaf(c.fz, b1 - b0, b0);
+}
+
+__device__ __forceinline__ void scatter_cell(unsigned long long* acc, const GridD& g, const Cell& c, float val,
+                                             float scale) {
+    const float wx[2] = {1.f - c.fx, c.fx}, wy[2] = {1.f - c.fy, c.fy}, wz[2] = {1.f - c.fz, c.fz};
+#pragma unroll
+    for (int dz = 0; dz < 2; dz++) {
+        const int k = c.k0 + dz;
+        if ((unsigned)k >= (unsigned)g.nz) continue;
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++) {
+            const int j = c.j0 + dy;
+            if ((unsigned)j >= (unsigned)g.ny) continue;
+#pragma unroll
+            for (int dx = 0; dx < 2; dx++) {
+                const int i = c.i0 + dx;
+                if ((unsigned)i >= (unsigned)g.nx) continue;
+                const float w = wx[dx] * wy[dy] * wz[dz];
+                red_add(acc + ((int64_t)k * g.ny + j) * g.nx + i, to_fixed(val * w, scale));
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void voxel_ijk(int64_t v, const GridD& g, int& i, int& j, int& k) {
+    i = (int)(v % g.nx);
+    int64_t r = v / g.nx;
+    j = (int)(r % g.ny);
+    k = (int)(r / g.ny);
+}
+
+// ----------------------------------------------------------- combine
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_combine(GridD g, int L, int P, const T* __restrict__ E,
+                                                      const float* __restrict__ w, T* __restrict__ D) {
+    const int64_t N = g.n;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        float e[kMaxL][3];
+        for (int l = 0; l < L; l++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) e[l][k] = Store<T>::ld(E, ((int64_t)l * 3 + k) * N + v);
+        for (int p = 0; p < P; p++) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                float acc = 0.f;
+                for (int l = 0; l < L; l++) acc = fmaf(__ldg(w + (p * L + l) * 3 + k), e[l][k], acc);
+                Store<T>::st(D, ((int64_t)p * 3 + k) * N + v, acc);
+            }
+        }
+    }
+}
+
+// d_mbc[l][k][v] = sum_p d_dvf[p][k][v] coeff[p][l][k]
+__global__ void __launch_bounds__(kThreads) k_combine_bwd_mbc(GridD g, int L, int P, const float* __restrict__ w,
+                                                              const float* __restrict__ dD, float* dE, int accumulate) {
+    const int64_t N = g.n;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        for (int l = 0; l < L; l++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                float acc = 0.f;
+                for (int p = 0; p < P; p++) acc = fmaf(__ldg(dD + ((int64_t)p * 3 + k) * N + v), __ldg(w + (p * L + l) * 3 + k), acc);
+                const int64_t o = ((int64_t)l * 3 + k) * N + v;
+                dE[o] = accumulate ? dE[o] + acc : acc;
+            }
+    }
+}
+
+// Block partials of d_coeff[p][l][k] = sum_v d_dvf[p][k][v] mbc[l][k][v]:
+// gridDim.y = P*3 (one (p,k) per y), gridDim.x = fixed voxel split.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_combine_bwd_coeff(GridD g, int L, int P, const T* __restrict__ E,
+                                                                const float* __restrict__ dD, float* part) {
+    __shared__ float red[kThreads / 32][kMaxL];
+    const int64_t N = g.n;
+    const int pk = blockIdx.y, p = pk / 3, k = pk % 3;
+    float acc[kMaxL];
+    for (int l = 0; l < kMaxL; l++) acc[l] = 0.f;
+    const float* d = dD + ((int64_t)p * 3 + k) * N;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        const float dv = __ldg(d + v);
+        for (int l = 0; l < L; l++) acc[l] = fmaf(dv, Store<T>::ld(E, ((int64_t)l * 3 + k) * N + v), acc[l]);
+    }
+    for (int l = 0; l < L; l++) {
+        float r = acc[l];
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][l] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < L) {
+        float r = 0.f;
+        for (int wi = 0; wi < kThreads / 32; wi++) r += red[wi][threadIdx.x];
+        // part[(p*L + l)*3 + k][block]
+        part[(((int64_t)p * L + threadIdx.x) * 3 + k) * gridDim.x + blockIdx.x] = r;
+    }
+}
+
+// Sum `nb` block partials per output in index order.
+__global__ void k_reduce_partials(const float* part, int64_t nout, int nb, float* out, int accumulate) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nout) return;
+    float r = 0.f;
+    for (int b = 0; b < nb; b++) r += part[o * nb + b];
+    out[o] = accumulate ? out[o] + r : r;
+}
+
+// --------------------------------------------------------------- warp
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_warp(GridD g, int P, const T* __restrict__ ref, const T* __restrict__ D,
+                                                   T* __restrict__ W) {
+    const int64_t N = g.n, total = N * P;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / N, v = t - p * N;
+        int i, j, k;
+        voxel_ijk(v, g, i, j, k);
+        const T* Dp = D + p * 3 * N;
+        const Cell c = make_cell(i, j, k, Store<T>::ld(Dp, v) * g.ivx, Store<T>::ld(Dp, N + v) * g.ivy,
+                                 Store<T>::ld(Dp, 2 * N + v) * g.ivz);
+        Store<T>::st(W, t, trilin_cell(ref, g, c.i0, c.j0, c.k0, c.fx, c.fy, c.fz));
+    }
+}
+
+__global__ void k_absmax(const float* __restrict__ x, int64_t n, unsigned* out) {
+    float m = 0.f;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(__ldg(x + t)));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_warp_bwd(GridD g, int P, const T* __restrict__ ref,
+                                                       const T* __restrict__ D, const float* __restrict__ dW,
+                                                       float* d_dvf, unsigned long long* acc, const unsigned* maxbits,
+                                                       int accumulate) {
+    const int64_t N = g.n, total = N * P;
+    const int kexp = fixed_exponent(__uint_as_float(*maxbits) * (float)total);
+    const float scale = ldexpf(1.0f, kexp);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / N, v = t - p * N;
+        int i, j, k;
+        voxel_ijk(v, g, i, j, k);
+        const T* Dp = D + p * 3 * N;
+        const Cell c = make_cell(i, j, k, Store<T>::ld(Dp, v) * g.ivx, Store<T>::ld(Dp, N + v) * g.ivy,
+                                 Store<T>::ld(Dp, 2 * N + v) * g.ivz);
+        const float gw = __ldg(dW + t);
+        if (d_dvf) {
+            float gx, gy, gz;
+            trilin_grad(ref, g, c, gx, gy, gz);
+            float* o = d_dvf + p * 3 * N + v;
+            const float r0 = gw * gx * g.ivx, r1 = gw * gy * g.ivy, r2 = gw * gz * g.ivz;
+            o[0] = accumulate ? o[0] + r0 : r0;
+            o[N] = accumulate ? o[N] + r1 : r1;
+            o[2 * N] = accumulate ? o[2 * N] + r2 : r2;
+        }
+        if (gw != 0.f) scatter_cell(acc, g, c, gw, scale);
+    }
+}
+
+// d_ref (=/+=) fixed-point accumulator * 2^-k, k from the same bound.
+__global__ void k_fixed_to_float(const unsigned long long* __restrict__ acc, int64_t n, const unsigned* maxbits,
+                                 float bound_mult, float* out, int accumulate) {
+    const float bound = __uint_as_float(*maxbits) * bound_mult;
+    const int kexp = fixed_exponent(bound);
+    const float inv = ldexpf(1.0f, -kexp);
+    const bool bad = !isfinite(bound);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        float r = bad ? __int_as_float(0x7fc00000) : from_fixed(acc[t], inv);
+        out[t] = accumulate ? out[t] + r : r;
+    }
+}
+
+// ----------------------------------------------------- fused combine + warp
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_warp_combine(GridD g, int L, int P, const T* __restrict__ ref,
+                                                           const T* __restrict__ E, const float* __restrict__ w,
+                                                           T* __restrict__ W) {
+    const int64_t N = g.n;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        voxel_ijk(v, g, i, j, k);
+        float e[kMaxL][3];
+        for (int l = 0; l < L; l++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) e[l][a] = Store<T>::ld(E, ((int64_t)l * 3 + a) * N + v);
+        for (int p = 0; p < P; p++) {
+            float d[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                float acc = 0.f;
+                for (int l = 0; l < L; l++) acc = fmaf(__ldg(w + (p * L + l) * 3 + a), e[l][a], acc);
+                d[a] = acc;
+            }
+            const Cell c = make_cell(i, j, k, d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
+            Store<T>::st(W, (int64_t)p * N + v, trilin_cell(ref, g, c.i0, c.j0, c.k0, c.fx, c.fy, c.fz));
+        }
+    }
+}
+
+// Fused adjoint with the DVF recomputed.  Per voxel, loops over p in order:
+// d_mbc accumulates in registers (fixed order), d_ref scatters in fixed point,
+// d_coeff contributions are reduced per warp and kept per warp in shared
+// memory, then per block, then across blocks in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_warp_combine_bwd(GridD g, int L, int P, const T* __restrict__ ref,
+                                                               const T* __restrict__ E, const float* __restrict__ w,
+                                                               const float* __restrict__ dW, float* d_mbc,
+                                                               unsigned long long* acc, const unsigned* maxbits,
+                                                               float* part, int accumulate) {
+    extern __shared__ float swarp[];  // [kThreads/32][P*L*3]
+    const int PL3 = P * L * 3;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < (kThreads / 32) * PL3; t += kThreads) swarp[t] = 0.f;
+    __syncthreads();
+    const int64_t N = g.n;
+    const int kexp = fixed_exponent(__uint_as_float(*maxbits) * (float)(N * P));
+    const float scale = ldexpf(1.0f, kexp);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of iterations so the
+    // shuffles below stay converged
+    const int64_t vbeg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t iters = (N + stride - 1) / stride;
+    for (int64_t it = 0; it < iters; it++) {
+        const int64_t v = vbeg + it * stride;
+        const bool live = v < N;
+        int i = 0, j = 0, k = 0;
+        float e[kMaxL][3], gE[kMaxL][3];
+        for (int l = 0; l < L; l++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) { e[l][a] = live ? Store<T>::ld(E, ((int64_t)l * 3 + a) * N + v) : 0.f; gE[l][a] = 0.f; }
+        if (live) voxel_ijk(v, g, i, j, k);
+        for (int p = 0; p < P; p++) {
+            float gd[3] = {0.f, 0.f, 0.f};
+            if (live) {
+                float d[3];
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    float s = 0.f;
+                    for (int l = 0; l < L; l++) s = fmaf(__ldg(w + (p * L + l) * 3 + a), e[l][a], s);
+                    d[a] = s;
+                }
+                const Cell c = make_cell(i, j, k, d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
+                const float gw = __ldg(dW + (int64_t)p * N + v);
+                if (gw != 0.f) {
+                    float gx, gy, gz;
+                    trilin_grad(ref, g, c, gx, gy, gz);
+                    gd[0] = gw * gx * g.ivx; gd[1] = gw * gy * g.ivy; gd[2] = gw * gz * g.ivz;
+                    scatter_cell(acc, g, c, gw, scale);
+                }
+            }
+            for (int l = 0; l < L; l++) {
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    gE[l][a] = fmaf(gd[a], __ldg(w + (p * L + l) * 3 + a), gE[l][a]);
+                    float r = gd[a] * e[l][a];
+                    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+                    if (lane == 0) swarp[wid * PL3 + (p * L + l) * 3 + a] += r;
+                }
+            }
+        }
+        if (live) {
+            for (int l = 0; l < L; l++)
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    float* o = d_mbc + ((int64_t)l * 3 + a) * N + v;
+                    *o = accumulate ? *o + gE[l][a] : gE[l][a];
+                }
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < PL3; t += kThreads) {
+        float r = 0.f;
+        for (int wi = 0; wi < kThreads / 32; wi++) r += swarp[wi * PL3 + t];
+        part[(int64_t)t * gridDim.x + blockIdx.x] = r;
+    }
+}
+
+unsigned stream_blocks(int64_t work) {
+    int64_t b = (work + kThreads - 1) / kThreads;
+    return (unsigned)(b < kStreamBlocks ? (b > 0 ? b : 1) : kStreamBlocks);
+}
+
+pmf_status check_common(const pmf_grid* grid, int32_t P, pmf_dtype dtype) {
+    pmf_status st = validate_grid(grid);
+    if (st != PMF_OK) return st;
+    if ((st = validate_dtype(dtype)) != PMF_OK) return st;
+    PMF_REQUIRE(P >= 0, "P must be >= 0");
+    return PMF_OK;
+}
+
+}  // namespace
+}  // namespace pmf
+
+using namespace pmf;
+
+extern "C" {
+
+pmf_status mbc_combine(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* mbc,
+                       const float* coeff, void* dvf, pmf_stream stream) {
+    pmf_status st = check_common(grid, P, dtype);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(L >= 1 && L <= kMaxL, "L must be in [1, %d]", kMaxL);
+    if (P == 0) return PMF_OK;
+    PMF_REQUIRE(mbc && coeff && dvf, "null pointer");
+    GridD g = make_grid(grid);
+    cudaStream_t s = (cudaStream_t)stream;
+    PMF_DISPATCH_DTYPE(dtype, T, k_combine<T><<<stream_blocks(g.n), kThreads, 0, s>>>(g, L, P, (const T*)mbc, coeff, (T*)dvf));
+    return check_launch("mbc_combine");
+}
+
+pmf_status mbc_combine_backward_workspace(const pmf_grid* grid, int32_t L, int32_t P, size_t* bytes) {
+    pmf_status st = validate_grid(grid);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(bytes != nullptr, "bytes is null");
+    PMF_REQUIRE(L >= 1 && L <= kMaxL && P >= 0, "bad L/P");
+    *bytes = align_up(sizeof(float) * (size_t)P * L * 3 * kStreamBlocks);
+    return PMF_OK;
+}
+
+pmf_status mbc_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* mbc,
+                                const float* coeff, const float* d_dvf, float* d_mbc, float* d_coeff, int accumulate,
+                                void* ws, size_t ws_bytes, pmf_stream stream) {
+    pmf_status st = check_common(grid, P, dtype);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(L >= 1 && L <= kMaxL, "L must be in [1, %d]", kMaxL);
+    size_t need;
+    mbc_combine_backward_workspace(grid, L, P, &need);
+    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
+    GridD g = make_grid(grid);
+    cudaStream_t s = (cudaStream_t)stream;
+    PMF_REQUIRE(mbc && d_mbc && (P == 0 || (coeff && d_dvf && d_coeff)), "null pointer");
+    if (P == 0) {
+        if (!accumulate) cudaMemsetAsync(d_mbc, 0, sizeof(float) * (size_t)(L * 3 * g.n), s);
+        return check_launch("mbc_combine_backward");
+    }
+    k_combine_bwd_mbc<<<stream_blocks(g.n), kThreads, 0, s>>>(g, L, P, coeff, d_dvf, d_mbc, accumulate);
+    dim3 gr(kStreamBlocks, (unsigned)(P * 3));
+    float* part = (float*)ws;
+    PMF_DISPATCH_DTYPE(dtype, T, k_combine_bwd_coeff<T><<<gr, kThreads, 0, s>>>(g, L, P, (const T*)mbc, d_dvf, part));
+    int64_t nout = (int64_t)P * L * 3;
+    k_reduce_partials<<<(unsigned)((nout + 255) / 256), 256, 0, s>>>(part, nout, kStreamBlocks, d_coeff, accumulate);
+    return check_launch("mbc_combine_backward");
+}
+
+pmf_status warp_volume(const pmf_grid* grid, int32_t P, pmf_dtype dtype, const void* ref, const void* dvf, void* out,
+                       pmf_stream stream) {
+    pmf_status st = check_common(grid, P, dtype);
+    if (st != PMF_OK) return st;
+    if (P == 0) return PMF_OK;
+    PMF_REQUIRE(ref && dvf && out, "null pointer");
+    GridD g = make_grid(grid);
+    cudaStream_t s = (cudaStream_t)stream;
+    PMF_DISPATCH_DTYPE(dtype, T, k_warp<T><<<stream_blocks(g.n * P), kThreads, 0, s>>>(g, P, (const T*)ref, (const T*)dvf, (T*)out));
+    return check_launch("warp_volume");
+}
+
+pmf_status warp_volume_backward_workspace(const pmf_grid* grid, int32_t P, size_t* bytes) {
+    pmf_status st = validate_grid(grid);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(bytes != nullptr && P >= 0, "bad arguments");
+    GridD g = make_grid(grid);
+    *bytes = align_up(256) + align_up(sizeof(unsigned long long) * (size_t)g.n);
+    return PMF_OK;
+}
+
+pmf_status warp_volume_backward(const pmf_grid* grid, int32_t P, pmf_dtype dtype, const void* ref, const void* dvf,
+                                const float* d_out, float* d_ref, float* d_dvf, int accumulate, void* ws,
+                                size_t ws_bytes, pmf_stream stream) {
+    pmf_status st = check_common(grid, P, dtype);
+    if (st != PMF_OK) return st;
+    size_t need;
+    warp_volume_backward_workspace(grid, P, &need);
+    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
+    PMF_REQUIRE(ref && d_ref && (P == 0 || (dvf && d_out)), "null pointer");
+    GridD g = make_grid(grid);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* maxbits = (unsigned*)ws;
+    unsigned long long* acc = (unsigned long long*)((char*)ws + align_up(256));
+    cudaMemsetAsync(ws, 0, need, s);
+    if (P > 0) {
+        k_absmax<<<stream_blocks(g.n * P), kThreads, 0, s>>>(d_out, g.n * P, maxbits);
+        PMF_DISPATCH_DTYPE(dtype, T, k_warp_bwd<T><<<stream_blocks(g.n * P), kThreads, 0, s>>>(g, P, (const T*)ref, (const T*)dvf, d_out, d_dvf, acc, maxbits, accumulate));
+    }
+    k_fixed_to_float<<<stream_blocks(g.n), kThreads, 0, s>>>(acc, g.n, maxbits, (float)(g.n * (int64_t)P), d_ref, accumulate);
+    return check_launch("warp_volume_backward");
+}
+
+pmf_status warp_combine(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref, const void* mbc,
+                        const float* coeff, void* out, pmf_stream stream) {
+    pmf_status st = check_common(grid, P, dtype);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(L >= 1 && L <= kMaxL, "L must be in [1, %d]", kMaxL);
+    if (P == 0) return PMF_OK;
+    PMF_REQUIRE(ref && mbc && coeff && out, "null pointer");
+    GridD g = make_grid(grid);
+    cudaStream_t s = (cudaStream_t)stream;
+    PMF_DISPATCH_DTYPE(dtype, T, k_warp_combine<T><<<stream_blocks(g.n), kThreads, 0, s>>>(g, L, P, (const T*)ref, (const T*)mbc, coeff, (T*)out));
+    return check_launch("warp_combine");
+}
+
+pmf_status warp_combine_backward_workspace(const pmf_grid* grid, int32_t L, int32_t P, size_t* bytes) {
+    pmf_status st = validate_grid(grid);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(bytes != nullptr && P >= 0 && L >= 1 && L <= kMaxL, "bad arguments");
+    GridD g = make_grid(grid);
+    *bytes = align_up(256) + align_up(sizeof(unsigned long long) * (size_t)g.n) +
+             align_up(sizeof(float) * (size_t)P * L * 3 * kStreamBlocks);
+    return PMF_OK;
+}
+
+pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
+                                 const void* mbc, const float* coeff, const float* d_out, float* d_ref, float* d_mbc,
+                                 float* d_coeff, int accumulate, void* ws, size_t ws_bytes, pmf_stream stream) {
+    pmf_status st = check_common(grid, P, dtype);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(L >= 1 && L <= kMaxL, "L must be in [1, %d]", kMaxL);
+    size_t need;
+    warp_combine_backward_workspace(grid, L, P, &need);
+    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
+    PMF_REQUIRE(ref && mbc && d_ref && d_mbc && (P == 0 || (coeff && d_out && d_coeff)), "null pointer");
+    const size_t smem = sizeof(float) * (kThreads / 32) * (size_t)P * L * 3;
+    if (smem > 200 * 1024) return set_error(PMF_EUNSUPPORTED, "P*L too large for the fused adjoint (P*L <= %d)", (int)(200 * 1024 / (4 * 8 * 3)));
+    GridD g = make_grid(grid);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* maxbits = (unsigned*)ws;
+    unsigned long long* acc = (unsigned long long*)((char*)ws + align_up(256));
+    float* part = (float*)((char*)acc + align_up(sizeof(unsigned long long) * (size_t)g.n));
+    cudaMemsetAsync(ws, 0, align_up(256) + align_up(sizeof(unsigned long long) * (size_t)g.n), s);
+    if (P == 0) {
+        if (!accumulate) cudaMemsetAsync(d_mbc, 0, sizeof(float) * (size_t)(L * 3 * g.n), s);
+    } else {
+        k_absmax<<<stream_blocks(g.n * P), kThreads, 0, s>>>(d_out, g.n * P, maxbits);
+        const unsigned nb = stream_blocks(g.n);
+        PMF_DISPATCH_DTYPE(dtype, T, {
+            if (smem > 48 * 1024) cudaFuncSetAttribute(k_warp_combine_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_warp_combine_bwd<T><<<nb, kThreads, smem, s>>>(g, L, P, (const T*)ref, (const T*)mbc, coeff, d_out, d_mbc, acc, maxbits, part, accumulate);
+        });
+        int64_t nout = (int64_t)P * L * 3;
+        k_reduce_partials<<<(unsigned)((nout + 255) / 256), 256, 0, s>>>(part, nout, (int)nb, d_coeff, accumulate);
+    }
+    k_fixed_to_float<<<stream_blocks(g.n), kThreads, 0, s>>>(acc, g.n, maxbits, (float)(g.n * (int64_t)P), d_ref, accumulate);
+    return check_launch("warp_combine_backward");
+}
+
+}  // extern "C"

@@ -1,0 +1,304 @@
+"""Python binding of the C ABI (include/pmf.h), one function per entry point
+with the same name.  Argument marshalling only: tensors are checked, outputs
+and scratch are allocated with torch on the tensors' device, and the call is
+enqueued on torch's current CUDA stream.  Every step of the computation runs
+in libpmf.so; nothing here falls back to PyTorch math.
+
+Grids are any object with nx, ny, nz, vx, vy, vz (or a 6-tuple); detectors any
+object with nu, nv, step_mm (or a 3-tuple).  Views are float64 [P, 12] tensors
+(src, detector centre, du, dv) on the device -- the pmf_view layout.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import PmfDetector, PmfGaussians, PmfGrid, check
+
+_DT = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
+
+
+def _grid(g) -> PmfGrid:
+    if hasattr(g, "nx"):
+        return PmfGrid(int(g.nx), int(g.ny), int(g.nz), float(g.vx), float(g.vy), float(g.vz))
+    nx, ny, nz, vx, vy, vz = g
+    return PmfGrid(int(nx), int(ny), int(nz), float(vx), float(vy), float(vz))
+
+
+def _det(d) -> PmfDetector:
+    if hasattr(d, "nu"):
+        return PmfDetector(int(d.nu), int(d.nv), float(d.step_mm))
+    nu, nv, step = d
+    return PmfDetector(int(nu), int(nv), float(step))
+
+
+def _shape(g):
+    gr = _grid(g)
+    return (gr.nz, gr.ny, gr.nx), gr.nx * gr.ny * gr.nz
+
+
+def _stream():
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _p(t: Optional[torch.Tensor]):
+    return ct.c_void_p(t.data_ptr()) if t is not None else ct.c_void_p(0)
+
+
+def _need(t: torch.Tensor, name: str, dtype=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if dtype is None and t.dtype not in _DT:
+        raise ValueError(f"{name} must be float32, bfloat16 or float16")
+    return t.contiguous()
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _size(fn, *args) -> int:
+    n = ct.c_size_t(0)
+    check(fn(*args, ct.byref(n)), fn.__name__)
+    return int(n.value)
+
+
+class Gaussians:
+    """Device views of a Gaussian set (Eq. 4) kept alive for a call."""
+
+    def __init__(self, mean, scale, quat, value, kappa: float = 3.0):
+        self.mean = _need(mean, "mean", torch.float32)
+        self.scale = _need(scale, "scale", torch.float32)
+        self.quat = _need(quat, "quat", torch.float32)
+        v = _need(value, "value", torch.float32)
+        self.value = v.reshape(v.shape[0], -1) if v.dim() == 1 else v
+        self.n = int(self.mean.shape[0])
+        self.channels = int(self.value.shape[1]) if self.value.dim() == 2 else 1
+        self.kappa = float(kappa)
+        if not (self.mean.shape == (self.n, 3) and self.scale.shape == (self.n, 3) and self.quat.shape == (self.n, 4)
+                and self.value.shape[0] == self.n):
+            raise ValueError("gaussian arrays must be mean[G,3], scale[G,3], quat[G,4], value[G,C]")
+
+    def c_struct(self) -> PmfGaussians:
+        k = self.kappa if math.isfinite(self.kappa) else float("inf")
+        return PmfGaussians(self.n, self.channels, k, self.mean.data_ptr(), self.scale.data_ptr(),
+                            self.quat.data_ptr(), self.value.data_ptr())
+
+
+def _gs(*args) -> Gaussians:
+    return args[0] if isinstance(args[0], Gaussians) else Gaussians(*args)
+
+
+# ----------------------------------------------------------- voxelizer
+
+def gs_voxelize_workspace(grid, n: int, pair_capacity: int) -> int:
+    L = _lib.load()
+    return _size(L.gs_voxelize_workspace, ct.byref(_grid(grid)), int(n), int(pair_capacity))
+
+
+def gs_voxelize_count(grid, gs: Gaussians) -> int:
+    """Exact number of (Gaussian, 8^3-tile) overlaps (synchronizes)."""
+    L = _lib.load()
+    g = _grid(grid)
+    ws = _ws(gs_voxelize_workspace(grid, gs.n, 0), gs.mean.device)
+    out = torch.zeros(1, dtype=torch.int64, device=gs.mean.device)
+    s = gs.c_struct()
+    check(L.gs_voxelize_count(ct.byref(g), ct.byref(s), _p(out), _p(ws), ws.numel(), _stream()), "gs_voxelize_count")
+    return int(out.item())
+
+
+def gs_voxelize(grid, gs: Gaussians, dtype=torch.float32, pair_capacity: Optional[int] = None,
+                out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Eq. 5 / signed MBC voxelization -> [C, nz, ny, nx] of `dtype`."""
+    L = _lib.load()
+    g = _grid(grid)
+    shape, n = _shape(grid)
+    dev = gs.mean.device
+    if out is None:
+        out = torch.empty((gs.channels,) + shape, dtype=dtype, device=dev)
+    if ws is None:
+        cap = gs_voxelize_count(grid, gs) if pair_capacity is None else int(pair_capacity)
+        ws = _ws(gs_voxelize_workspace(grid, gs.n, cap), dev)
+    s = gs.c_struct()
+    check(L.gs_voxelize(ct.byref(g), ct.byref(s), _DT[out.dtype], _p(out), _p(ws), ws.numel(), _stream()),
+          "gs_voxelize")
+    return out
+
+
+def gs_voxelize_backward(grid, gs: Gaussians, d_out: torch.Tensor, grads=None, accumulate: bool = False):
+    """Adjoint of gs_voxelize -> (d_mean, d_scale, d_quat, d_value), fp32."""
+    L = _lib.load()
+    g = _grid(grid)
+    d_out = _need(d_out, "d_out", torch.float32)
+    dev = gs.mean.device
+    if grads is None:
+        grads = (torch.empty((gs.n, 3), device=dev), torch.empty((gs.n, 3), device=dev),
+                 torch.empty((gs.n, 4), device=dev), torch.empty((gs.n, gs.channels), device=dev))
+    s = gs.c_struct()
+    check(L.gs_voxelize_backward(ct.byref(g), ct.byref(s), _p(d_out), *[_p(t) for t in grads], int(accumulate),
+                                 _stream()), "gs_voxelize_backward")
+    return grads
+
+
+# ------------------------------------------------------- combine / warp
+
+def mbc_combine(grid, mbc: torch.Tensor, coeff: torch.Tensor, out=None) -> torch.Tensor:
+    L = _lib.load()
+    mbc = _need(mbc, "mbc")
+    coeff = _need(coeff, "coeff", torch.float32)
+    P, Lv = int(coeff.shape[0]), int(coeff.shape[1])
+    shape, n = _shape(grid)
+    if out is None:
+        out = torch.empty((P, 3) + shape, dtype=mbc.dtype, device=mbc.device)
+    check(L.mbc_combine(ct.byref(_grid(grid)), Lv, P, _DT[mbc.dtype], _p(mbc), _p(coeff), _p(out), _stream()),
+          "mbc_combine")
+    return out
+
+
+def mbc_combine_backward(grid, mbc, coeff, d_dvf, accumulate=False, grads=None):
+    L = _lib.load()
+    mbc = _need(mbc, "mbc")
+    coeff = _need(coeff, "coeff", torch.float32)
+    d_dvf = _need(d_dvf, "d_dvf", torch.float32)
+    P, Lv = int(coeff.shape[0]), int(coeff.shape[1])
+    g = _grid(grid)
+    ws = _ws(_size(L.mbc_combine_backward_workspace, ct.byref(g), Lv, P), mbc.device)
+    if grads is None:
+        grads = (torch.empty(mbc.shape, dtype=torch.float32, device=mbc.device),
+                 torch.empty(coeff.shape, dtype=torch.float32, device=mbc.device))
+    check(L.mbc_combine_backward(ct.byref(g), Lv, P, _DT[mbc.dtype], _p(mbc), _p(coeff), _p(d_dvf), _p(grads[0]),
+                                 _p(grads[1]), int(accumulate), _p(ws), ws.numel(), _stream()), "mbc_combine_backward")
+    return grads
+
+
+def warp_volume(grid, ref, dvf, out=None) -> torch.Tensor:
+    L = _lib.load()
+    ref, dvf = _need(ref, "ref"), _need(dvf, "dvf")
+    P = int(dvf.shape[0])
+    shape, _ = _shape(grid)
+    if out is None:
+        out = torch.empty((P,) + shape, dtype=ref.dtype, device=ref.device)
+    check(L.warp_volume(ct.byref(_grid(grid)), P, _DT[ref.dtype], _p(ref), _p(dvf), _p(out), _stream()), "warp_volume")
+    return out
+
+
+def warp_volume_backward(grid, ref, dvf, d_out, need_dvf=True, accumulate=False, grads=None):
+    L = _lib.load()
+    ref, dvf = _need(ref, "ref"), _need(dvf, "dvf")
+    d_out = _need(d_out, "d_out", torch.float32)
+    P = int(dvf.shape[0])
+    g = _grid(grid)
+    ws = _ws(_size(L.warp_volume_backward_workspace, ct.byref(g), P), ref.device)
+    if grads is None:
+        grads = (torch.empty(ref.shape, dtype=torch.float32, device=ref.device),
+                 torch.empty(dvf.shape, dtype=torch.float32, device=ref.device) if need_dvf else None)
+    check(L.warp_volume_backward(ct.byref(g), P, _DT[ref.dtype], _p(ref), _p(dvf), _p(d_out), _p(grads[0]),
+                                 _p(grads[1]), int(accumulate), _p(ws), ws.numel(), _stream()), "warp_volume_backward")
+    return grads
+
+
+def warp_combine(grid, ref, mbc, coeff, out=None) -> torch.Tensor:
+    L = _lib.load()
+    ref, mbc = _need(ref, "ref"), _need(mbc, "mbc")
+    coeff = _need(coeff, "coeff", torch.float32)
+    P, Lv = int(coeff.shape[0]), int(coeff.shape[1])
+    shape, _ = _shape(grid)
+    if out is None:
+        out = torch.empty((P,) + shape, dtype=ref.dtype, device=ref.device)
+    check(L.warp_combine(ct.byref(_grid(grid)), Lv, P, _DT[ref.dtype], _p(ref), _p(mbc), _p(coeff), _p(out),
+                         _stream()), "warp_combine")
+    return out
+
+
+def warp_combine_backward(grid, ref, mbc, coeff, d_out, accumulate=False, grads=None, ws=None):
+    L = _lib.load()
+    ref, mbc = _need(ref, "ref"), _need(mbc, "mbc")
+    coeff = _need(coeff, "coeff", torch.float32)
+    d_out = _need(d_out, "d_out", torch.float32)
+    P, Lv = int(coeff.shape[0]), int(coeff.shape[1])
+    g = _grid(grid)
+    if ws is None:
+        ws = _ws(_size(L.warp_combine_backward_workspace, ct.byref(g), Lv, P), ref.device)
+    if grads is None:
+        grads = (torch.empty(ref.shape, dtype=torch.float32, device=ref.device),
+                 torch.empty(mbc.shape, dtype=torch.float32, device=ref.device),
+                 torch.empty(coeff.shape, dtype=torch.float32, device=ref.device))
+    check(L.warp_combine_backward(ct.byref(g), Lv, P, _DT[ref.dtype], _p(ref), _p(mbc), _p(coeff), _p(d_out),
+                                  _p(grads[0]), _p(grads[1]), _p(grads[2]), int(accumulate), _p(ws), ws.numel(),
+                                  _stream()), "warp_combine_backward")
+    return grads
+
+
+# ----------------------------------------------------------- projector
+
+def views_tensor(views, device) -> torch.Tensor:
+    """float64 [P, 12] on `device` (the pmf_view layout)."""
+    t = torch.as_tensor(views, dtype=torch.float64)
+    return t.reshape(-1, 12).contiguous().to(device)
+
+
+def conebeam_project(grid, det, views: torch.Tensor, vol: torch.Tensor, shared: Optional[bool] = None,
+                     out=None) -> torch.Tensor:
+    """Eq. 6 ray sums -> [P, nv, nu] fp32.  vol is [nz,ny,nx] (shared by all
+    views) or [P,nz,ny,nx]."""
+    L = _lib.load()
+    vol = _need(vol, "vol")
+    views = _need(views, "views", torch.float64)
+    P = int(views.shape[0])
+    d = _det(det)
+    _, n = _shape(grid)
+    if shared is None:
+        shared = vol.numel() == n
+    if out is None:
+        out = torch.empty((P, d.nv, d.nu), dtype=torch.float32, device=vol.device)
+    check(L.conebeam_project(ct.byref(_grid(grid)), ct.byref(d), P, _p(views), _DT[vol.dtype], _p(vol),
+                             0 if shared else n, _p(out), _stream()), "conebeam_project")
+    return out
+
+
+def conebeam_project_backward(grid, det, views, d_proj, shared: bool = False, accumulate=False, out=None,
+                              ws=None) -> torch.Tensor:
+    L = _lib.load()
+    views = _need(views, "views", torch.float64)
+    d_proj = _need(d_proj, "d_proj", torch.float32)
+    P = int(views.shape[0])
+    d = _det(det)
+    g = _grid(grid)
+    shape, n = _shape(grid)
+    stride = 0 if shared else n
+    if ws is None:
+        ws = _ws(_size(L.conebeam_project_backward_workspace, ct.byref(g), P, stride), d_proj.device)
+    if out is None:
+        out = torch.empty(shape if shared else (P,) + shape, dtype=torch.float32, device=d_proj.device)
+    check(L.conebeam_project_backward(ct.byref(g), ct.byref(d), P, _p(views), _p(d_proj), _p(out), stride,
+                                      int(accumulate), _p(ws), ws.numel(), _stream()), "conebeam_project_backward")
+    return out
+
+
+def projection_loss(kind: int, pred: torch.Tensor, meas: torch.Tensor, with_grad: bool = True, ws=None):
+    """kind 1 = L1 (Eq. 10/12), 2 = L2 (Eq. 1); mean over all pixels -> (loss[1], d_pred)."""
+    L = _lib.load()
+    pred = _need(pred, "pred", torch.float32)
+    meas = _need(meas, "meas", torch.float32)
+    if pred.shape != meas.shape:
+        raise ValueError("pred and meas shapes differ")
+    P = int(pred.shape[0])
+    Q = pred.numel() // max(P, 1)
+    if ws is None:
+        ws = _ws(_size(L.projection_loss_workspace, P * Q), pred.device)
+    loss = torch.empty(1, dtype=torch.float32, device=pred.device)
+    d_pred = torch.empty_like(pred) if with_grad else None
+    check(L.projection_loss(int(kind), P, Q, _p(pred), _p(meas), _p(loss), _p(d_pred), _p(ws), ws.numel(),
+                            _stream()), "projection_loss")
+    return loss, d_pred
+
+
+def library_info() -> dict:
+    L = _lib.load()
+    return {"version": L.pmf_version().decode(), "path": _lib.library_path()}

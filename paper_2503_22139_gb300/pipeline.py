@@ -1,0 +1,86 @@
+"""One forward + adjoint pass of the PMF-STGR model over a batch of projections
+(Sec. 2.3.2, Stages 2-3): every stage is a C-ABI call, buffers are allocated
+once and reused, and nothing runs outside libpmf.so's kernels.
+
+    V  = gs_voxelize(reference Gaussians)                  Eq. 4-5
+    E_l = gs_voxelize(MBC Gaussians of level l)            Sec. 2.3.1
+    W_p = warp_combine(V, E, w_p)                          Eq. 3 + Eq. 2 (DVF never stored)
+    Y_p = conebeam_project(W_p)                            Eq. 6
+    L, dY = projection_loss(Y, M)                          Eq. 10/12 (L1) or Eq. 1 (L2)
+    dW = conebeam_project_backward(dY)
+    dV, dE, dw = warp_combine_backward(dW)                 DVF recomputed
+    d(ref Gaussians), d(MBC Gaussians) = gs_voxelize_backward(...)
+"""
+from __future__ import annotations
+
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import ops
+from .ops import Gaussians
+
+# kernels each entry point launches (memsets excluded): used for the launch count
+KERNELS = {
+    "gs_voxelize": 4, "gs_voxelize_backward": 1, "warp_combine": 1, "conebeam_project": 1,
+    "projection_loss": 2, "conebeam_project_backward": 3, "warp_combine_backward": 4,
+}
+
+
+class ForwardAdjoint:
+    def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
+                 dtype: torch.dtype = torch.float32, kind: int = 2, pair_headroom: float = 1.25):
+        self.grid, self.det, self.ref, self.mbc = grid, det, ref, list(mbc)
+        self.B, self.dtype, self.kind = int(batch), dtype, int(kind)
+        dev = ref.mean.device
+        shape, n = ops._shape(grid)
+        L = len(self.mbc)
+        self.L = L
+        # buffers
+        self.V = torch.empty((1,) + shape, dtype=dtype, device=dev)
+        self.E = torch.empty((L, 3) + shape, dtype=dtype, device=dev)
+        self.W = torch.empty((self.B,) + shape, dtype=dtype, device=dev)
+        self.Y = torch.empty((self.B, det.nv, det.nu), dtype=torch.float32, device=dev)
+        self.dW = torch.empty((self.B,) + shape, dtype=torch.float32, device=dev)
+        self.g_ref = (torch.empty((ref.n, 3), device=dev), torch.empty((ref.n, 3), device=dev),
+                      torch.empty((ref.n, 4), device=dev), torch.empty((ref.n, ref.channels), device=dev))
+        self.g_mbc = [(torch.empty((m.n, 3), device=dev), torch.empty((m.n, 3), device=dev),
+                       torch.empty((m.n, 4), device=dev), torch.empty((m.n, m.channels), device=dev))
+                      for m in self.mbc]
+        self.g_wc = (torch.empty(shape, dtype=torch.float32, device=dev),
+                     torch.empty((L, 3) + shape, dtype=torch.float32, device=dev),
+                     torch.empty((self.B, L, 3), dtype=torch.float32, device=dev))
+        # scratch, sized once
+        self.vox_ws = []
+        for gs in [ref] + self.mbc:
+            cap = int(ops.gs_voxelize_count(grid, gs) * pair_headroom) + 4096
+            self.vox_ws.append(ops._ws(ops.gs_voxelize_workspace(grid, gs.n, cap), dev))
+        Lb = ops._lib.load()
+        g = ops._grid(grid)
+        self.bp_ws = ops._ws(ops._size(Lb.conebeam_project_backward_workspace, ops.ct.byref(g), self.B, n), dev)
+        self.wc_ws = ops._ws(ops._size(Lb.warp_combine_backward_workspace, ops.ct.byref(g), L, self.B), dev)
+        self.loss_ws = ops._ws(ops._size(Lb.projection_loss_workspace, self.B * det.nu * det.nv), dev)
+
+    @property
+    def launches_per_step(self) -> int:
+        k = KERNELS
+        return ((1 + self.L) * (k["gs_voxelize"] + k["gs_voxelize_backward"]) + k["warp_combine"]
+                + k["conebeam_project"] + k["projection_loss"] + k["conebeam_project_backward"]
+                + k["warp_combine_backward"])
+
+    def run(self, views: torch.Tensor, coeff: torch.Tensor, meas: torch.Tensor):
+        """views [B,12] f64, coeff [B,L,3] f32, meas [B,nv,nu] f32 (device).
+        Returns the loss (device [1]); gradients land in g_ref, g_mbc, g_wc."""
+        g, det = self.grid, self.det
+        ops.gs_voxelize(g, self.ref, out=self.V, ws=self.vox_ws[0])
+        for l, m in enumerate(self.mbc):
+            ops.gs_voxelize(g, m, out=self.E[l], ws=self.vox_ws[1 + l])
+        ops.warp_combine(g, self.V[0], self.E, coeff, out=self.W)
+        ops.conebeam_project(g, det, views, self.W, shared=False, out=self.Y)
+        loss, dY = ops.projection_loss(self.kind, self.Y, meas, ws=self.loss_ws)
+        ops.conebeam_project_backward(g, det, views, dY, shared=False, out=self.dW, ws=self.bp_ws)
+        ops.warp_combine_backward(g, self.V[0], self.E, coeff, self.dW, grads=self.g_wc, ws=self.wc_ws)
+        ops.gs_voxelize_backward(g, self.ref, self.g_wc[0].reshape((1,) + self.g_wc[0].shape), grads=self.g_ref)
+        for l, m in enumerate(self.mbc):
+            ops.gs_voxelize_backward(g, m, self.g_wc[1][l], grads=self.g_mbc[l])
+        return loss

@@ -1,0 +1,104 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point include/pmf.h declares, its structs match the header, and
+host-side validation rejects bad arguments before any device work."""
+import ctypes as ct
+import math
+import os
+import re
+
+import pytest
+
+from paper_2503_22139_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pmf.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(", src, re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ["gs_voxelize", "gs_voxelize_backward", "mbc_combine", "mbc_combine_backward", "warp_volume",
+                 "warp_volume_backward", "conebeam_project", "conebeam_project_backward", "projection_loss",
+                 "warp_combine", "warp_combine_backward"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.load()
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+    assert b"sm_103a" in L.pmf_version()
+
+
+def test_struct_layouts_match_header():
+    assert ct.sizeof(_lib.PmfGrid) == 24
+    assert ct.sizeof(_lib.PmfView) == 96
+    assert ct.sizeof(_lib.PmfDetector) == 12
+    assert ct.sizeof(_lib.PmfGaussians) == 48
+    assert _lib.PmfGaussians.mean.offset == 16
+
+
+def test_every_symbol_has_a_python_binding_of_the_same_name():
+    import paper_2503_22139_gb300.ops as ops
+    for n in _declared():
+        if n.startswith("pmf_") or n.endswith("_workspace"):
+            continue
+        assert hasattr(ops, n), n
+
+
+def _status(name, *args):
+    L = _lib.load()
+    return getattr(L, name)(*args)
+
+
+def test_workspace_queries_are_host_only():
+    g = _lib.PmfGrid(200, 200, 100, 2.0, 2.0, 2.0)
+    n = ct.c_size_t(0)
+    assert _status("gs_voxelize_workspace", ct.byref(g), 100000, 10**6, ct.byref(n)) == 0
+    assert n.value >= 4 * 10**6
+    assert _status("conebeam_project_backward_workspace", ct.byref(g), 32, 4_000_000, ct.byref(n)) == 0
+    assert n.value >= 8 * 32 * 4_000_000
+    assert _status("warp_combine_backward_workspace", ct.byref(g), 3, 32, ct.byref(n)) == 0
+    assert _status("projection_loss_workspace", 1000, ct.byref(n)) == 0
+
+
+@pytest.mark.parametrize("grid", [(0, 4, 4, 1, 1, 1), (4, 4, 4, 0, 1, 1), (4, -1, 4, 1, 1, 1)])
+def test_bad_grids_are_rejected_before_launch(grid):
+    g = _lib.PmfGrid(*grid)
+    d = _lib.PmfDetector(8, 8, 1.0)
+    rc = _status("conebeam_project", ct.byref(g), ct.byref(d), 1, ct.c_void_p(16), 0, ct.c_void_p(16), 0,
+                 ct.c_void_p(16), None)
+    assert rc == -1
+    assert b"grid" in _lib.load().pmf_last_error() or b"voxel" in _lib.load().pmf_last_error()
+
+
+def test_bad_arguments_are_rejected_before_launch():
+    g = _lib.PmfGrid(8, 8, 8, 1.0, 1.0, 1.0)
+    d = _lib.PmfDetector(8, 8, -1.0)
+    assert _status("conebeam_project", ct.byref(g), ct.byref(d), 1, ct.c_void_p(16), 0, ct.c_void_p(16), 0,
+                   ct.c_void_p(16), None) == -1
+    d = _lib.PmfDetector(8, 8, 1.0)
+    assert _status("conebeam_project", ct.byref(g), ct.byref(d), 1, ct.c_void_p(16), 7, ct.c_void_p(16), 0,
+                   ct.c_void_p(16), None) == -1
+    gs = _lib.PmfGaussians(10, 1, 0.0, 16, 16, 16, 16)  # kappa = 0
+    assert _status("gs_voxelize", ct.byref(g), ct.byref(gs), 0, ct.c_void_p(16), ct.c_void_p(256), 1 << 20,
+                   None) == -1
+    gs = _lib.PmfGaussians(10, 9, 3.0, 16, 16, 16, 16)  # too many channels
+    assert _status("gs_voxelize", ct.byref(g), ct.byref(gs), 0, ct.c_void_p(16), ct.c_void_p(256), 1 << 20,
+                   None) == -5
+    gs = _lib.PmfGaussians(10, 1, math.inf, 16, 16, 16, 16)
+    # workspace far too small
+    assert _status("gs_voxelize", ct.byref(g), ct.byref(gs), 0, ct.c_void_p(16), ct.c_void_p(256), 16, None) == -3
+    # misaligned workspace
+    assert _status("gs_voxelize", ct.byref(g), ct.byref(gs), 0, ct.c_void_p(16), ct.c_void_p(264), 1 << 20,
+                   None) == -3
+    assert _status("projection_loss", 3, 1, 4, ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(16), None,
+                   ct.c_void_p(256), 1 << 16, None) == -1
+    assert _status("mbc_combine", ct.byref(g), 9, 1, 0, ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(16),
+                   None) == -1

@@ -1,0 +1,263 @@
+"""GPU parity: every stage of the CUDA path (called through the C ABI) against
+the FP64 oracle on the same seeded inputs.  FP32 bar: relative L2 <= 1e-5
+(tighter where the arithmetic allows); gradients <= 1e-3 relative."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2503_22139_gb300 as pmf
+from synth import Detector, Grid, circular_views, config0, fd_subproblem, gaussian_set, mbc_levels
+from tests import oracle_chain
+from tests.gpu_util import dev, gset, host, pixel_views, rel_l2, views
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib_loaded(gpu_lib):
+    return gpu_lib
+
+
+def _rand_gaussians(seed, grid, G, lo, hi, C, std=None):
+    return gaussian_set(np.random.default_rng(seed), grid, G, lo, hi, channels=C, value_std=std)
+
+
+# ------------------------------------------------------------- voxelizer
+
+@pytest.mark.parametrize("kappa", [3.0, float("inf")])
+def test_voxelize_ragged_grid(kappa):
+    grid = Grid(13, 11, 9, 2.0, 2.5, 3.0)  # several 8^3 tiles with ragged edges
+    gs = _rand_gaussians(1, grid, 60, 0.7, 3.0, 1)
+    got = host(pmf.gs_voxelize(grid, gset(gs, kappa)))
+    ref = oracle.voxelize(grid, gs.mean, gs.scale, gs.quat, gs.value, kappa)
+    assert rel_l2(got, ref) <= TOL32
+
+
+def test_voxelize_config0_reference_and_mbc():
+    wl = config0(with_measured=False)
+    got = host(pmf.gs_voxelize(wl.grid, gset(wl.ref, wl.kappa)))
+    ref = oracle.voxelize(wl.grid, wl.ref.mean, wl.ref.scale, wl.ref.quat, wl.ref.value, wl.kappa)
+    assert rel_l2(got, ref) <= TOL32
+    m = wl.mbc[0]
+    got = host(pmf.gs_voxelize(wl.grid, gset(m, wl.kappa)))
+    ref = oracle.voxelize(wl.grid, m.mean, m.scale, m.quat, m.value, wl.kappa)
+    assert got.shape == (3,) + wl.grid.shape
+    assert rel_l2(got, ref) <= TOL32
+
+
+def test_voxelize_list_overflow_falls_back_correctly():
+    """A pair capacity far below the overlap count routes tiles through the
+    scan-everything path; the result must not change by a bit."""
+    grid = Grid(24, 20, 17, 2.0, 2.0, 2.0)
+    gs = gset(_rand_gaussians(2, grid, 300, 0.7, 4.0, 3, 2.0), 3.0)
+    full = pmf.gs_voxelize(grid, gs)
+    small = pmf.gs_voxelize(grid, gs, pair_capacity=37)
+    zero = pmf.gs_voxelize(grid, gs, pair_capacity=0)
+    torch.testing.assert_close(full, small, rtol=0, atol=0)
+    torch.testing.assert_close(full, zero, rtol=0, atol=0)
+
+
+def test_voxelize_edge_cases():
+    grid = Grid(9, 8, 7, 2.0, 2.0, 2.0)
+    empty = pmf.Gaussians(dev(np.zeros((0, 3))), dev(np.ones((0, 3))), dev(np.ones((0, 4))), dev(np.zeros((0, 1))))
+    assert float(pmf.gs_voxelize(grid, empty).abs().max()) == 0.0
+    # entirely outside the volume
+    far = pmf.Gaussians(dev([[500.0, 0, 0]]), dev([[1.0, 1, 1]]), dev([[1.0, 0, 0, 0]]), dev([[1.0]]), 3.0)
+    assert float(pmf.gs_voxelize(grid, far).abs().max()) == 0.0
+    # one voxel grid
+    g1 = Grid(1, 1, 1, 1.0, 1.0, 1.0)
+    one = pmf.Gaussians(dev([[0.0, 0, 0]]), dev([[1.0, 1, 1]]), dev([[1.0, 0, 0, 0]]), dev([[2.0]]), 3.0)
+    assert float(pmf.gs_voxelize(g1, one).item()) == pytest.approx(2.0, rel=1e-7)
+
+
+def test_voxelize_is_bit_reproducible():
+    wl = config0(with_measured=False)
+    gs = gset(wl.mbc[0], wl.kappa)
+    a = pmf.gs_voxelize(wl.grid, gs)
+    b = pmf.gs_voxelize(wl.grid, gs)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("C,kappa", [(1, float("inf")), (3, float("inf")), (1, 3.0), (3, 2.5)])
+def test_voxelize_backward_matches_oracle(C, kappa):
+    grid = Grid(12, 10, 11, 2.0, 2.0, 2.0)
+    gs = _rand_gaussians(3 + C, grid, 40, 0.8, 3.0, C, 2.0 if C == 3 else None)
+    rng = np.random.default_rng(7)
+    d_out = rng.normal(size=(C,) + grid.shape).astype(np.float32)
+    got = pmf.gs_voxelize_backward(grid, gset(gs, kappa), dev(d_out))
+    ref = oracle.voxelize_backward(grid, gs.mean, gs.scale, gs.quat, gs.value, d_out, kappa)
+    for name, g_, r_ in zip(("mean", "scale", "quat", "value"), got, ref):
+        assert rel_l2(host(g_), r_) <= 1e-4, name
+
+
+def test_voxelize_backward_accumulates():
+    grid = Grid(8, 8, 8, 2.0, 2.0, 2.0)
+    gs = gset(_rand_gaussians(9, grid, 10, 1.0, 2.0, 1), 3.0)
+    d_out = dev(np.random.default_rng(1).normal(size=(1,) + grid.shape))
+    a = pmf.gs_voxelize_backward(grid, gs, d_out)
+    b = pmf.gs_voxelize_backward(grid, gs, d_out, grads=tuple(t.clone() for t in a), accumulate=True)
+    for x, y in zip(a, b):
+        torch.testing.assert_close(2 * x, y, rtol=1e-6, atol=1e-6)
+
+
+# --------------------------------------------------- combine and warp
+
+def _mbc_and_ref(grid, seed, L=3, P=5):
+    rng = np.random.default_rng(seed)
+    V = rng.random(grid.shape).astype(np.float32)
+    E = rng.normal(0, 2.0, (L, 3) + grid.shape).astype(np.float32)
+    w = rng.uniform(-1, 1, (P, L, 3)).astype(np.float32)
+    return V, E, w
+
+
+def test_combine_and_warp_match_oracle():
+    grid = Grid(21, 17, 13, 2.0, 2.0, 2.0)
+    V, E, w = _mbc_and_ref(grid, 11)
+    D = pmf.mbc_combine(grid, dev(E), dev(w))
+    Dref = oracle.combine(E, w)
+    assert rel_l2(host(D), Dref) <= 1e-6
+    W = pmf.warp_volume(grid, dev(V), D)
+    Wref = oracle.warp(grid, V, host(D))
+    assert rel_l2(host(W), Wref) <= TOL32
+    Wf = pmf.warp_combine(grid, dev(V), dev(E), dev(w))
+    assert rel_l2(host(Wf), oracle.warp(grid, V, Dref)) <= TOL32
+
+
+def test_zero_dvf_warp_is_bitwise_identity():
+    grid = Grid(9, 8, 7, 2.0, 2.0, 2.0)
+    V = dev(np.random.default_rng(3).random(grid.shape))
+    W = pmf.warp_volume(grid, V, torch.zeros((2, 3) + grid.shape, device="cuda"))
+    assert torch.equal(W[0], V) and torch.equal(W[1], V)
+
+
+def test_combine_and_warp_backward_match_oracle():
+    grid = Grid(19, 15, 12, 2.0, 2.0, 2.0)
+    V, E, w = _mbc_and_ref(grid, 12, L=3, P=4)
+    rng = np.random.default_rng(13)
+    dW = rng.normal(size=(4,) + grid.shape).astype(np.float32)
+    Dref = oracle.combine(E, w)
+    dV_ref, dD_ref = oracle.warp_backward(grid, V, Dref, dW)
+    dE_ref, dw_ref = oracle.combine_backward(E, w, dD_ref)
+    D = pmf.mbc_combine(grid, dev(E), dev(w))
+    dV, dD = pmf.warp_volume_backward(grid, dev(V), D, dev(dW))
+    assert rel_l2(host(dV), dV_ref) <= TOL32
+    assert rel_l2(host(dD), dD_ref) <= 1e-4
+    dE, dw = pmf.mbc_combine_backward(grid, dev(E), dev(w), dev(dD_ref.astype(np.float32)))
+    dE_r2, dw_r2 = oracle.combine_backward(E, w, dD_ref.astype(np.float32))
+    assert rel_l2(host(dE), dE_r2) <= 1e-6
+    assert rel_l2(host(dw), dw_r2) <= 1e-5
+    fdV, fdE, fdw = pmf.warp_combine_backward(grid, dev(V), dev(E), dev(w), dev(dW))
+    assert rel_l2(host(fdV), dV_ref) <= TOL32
+    assert rel_l2(host(fdE), dE_ref) <= 1e-4
+    assert rel_l2(host(fdw), dw_ref) <= 1e-4
+
+
+def test_warp_backward_is_bit_reproducible():
+    grid = Grid(19, 15, 12, 2.0, 2.0, 2.0)
+    V, E, w = _mbc_and_ref(grid, 14, L=3, P=4)
+    dW = dev(np.random.default_rng(15).normal(size=(4,) + grid.shape))
+    a = pmf.warp_combine_backward(grid, dev(V), dev(E), dev(w), dW)
+    b = pmf.warp_combine_backward(grid, dev(V), dev(E), dev(w), dW)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+# ------------------------------------------------------------ projector
+
+@pytest.mark.parametrize("nu,nv", [(37, 23), (16, 16)])
+def test_project_ragged_detector(nu, nv):
+    grid = Grid(20, 18, 14, 2.0, 2.0, 2.5)
+    rng = np.random.default_rng(21)
+    vol = rng.random((3,) + grid.shape).astype(np.float32)
+    vw = circular_views(3, 400.0, 600.0, nu, nv, 1.8, 1.9, start=0.37)
+    got = host(pmf.conebeam_project(grid, Detector(nu, nv, 1.0), views(vw), dev(vol)))
+    ref = oracle.project(grid, nu, nv, 1.0, vw, vol)
+    assert rel_l2(got, ref) <= TOL32
+
+
+def test_project_config0_voxelized_reference():
+    wl = config0(with_measured=False)
+    V = pmf.gs_voxelize(wl.grid, gset(wl.ref, wl.kappa))[0]
+    Vh = host(V)
+    got = host(pmf.conebeam_project(wl.grid, wl.det, views(wl.views), V, shared=True))
+    ref = oracle.project(wl.grid, wl.det.nu, wl.det.nv, wl.det.step_mm, wl.views, Vh)
+    assert rel_l2(got, ref) <= TOL32
+
+
+def test_project_shared_volume_and_rays_that_miss():
+    grid = Grid(16, 16, 16, 2.0, 2.0, 2.0)
+    vol = np.random.default_rng(4).random(grid.shape).astype(np.float32)
+    vw = circular_views(2, 300.0, 450.0, 40, 40, 2.0, 2.0)  # outer pixels miss the volume
+    got = host(pmf.conebeam_project(grid, Detector(40, 40, 1.0), views(vw), dev(vol), shared=True))
+    ref = oracle.project(grid, 40, 40, 1.0, vw, vol)
+    assert rel_l2(got, ref) <= TOL32
+    assert np.all(got[ref == 0] == 0)
+
+
+@pytest.mark.parametrize("shared", [False, True])
+def test_backproject_matches_oracle_and_is_reproducible(shared):
+    grid = Grid(20, 18, 14, 2.0, 2.0, 2.5)
+    rng = np.random.default_rng(22)
+    vw = circular_views(3, 400.0, 600.0, 29, 21, 1.8, 1.9, start=0.1)
+    dY = rng.normal(size=(3, 21, 29)).astype(np.float32)
+    det = Detector(29, 21, 1.0)
+    got = pmf.conebeam_project_backward(grid, det, views(vw), dev(dY), shared=shared)
+    again = pmf.conebeam_project_backward(grid, det, views(vw), dev(dY), shared=shared)
+    assert torch.equal(got, again)
+    ref = oracle.project_backward(grid, 29, 21, 1.0, vw, dY, shared=shared)
+    assert rel_l2(host(got), ref) <= TOL32
+
+
+def test_loss_matches_oracle():
+    rng = np.random.default_rng(5)
+    a, b = rng.normal(size=(3, 17, 29)).astype(np.float32), rng.normal(size=(3, 17, 29)).astype(np.float32)
+    for kind in (1, 2):
+        loss, g = pmf.projection_loss(kind, dev(a), dev(b))
+        lref, gref = oracle.loss(kind, a, b)
+        assert float(loss.item()) == pytest.approx(lref, rel=1e-6)
+        assert rel_l2(host(g), gref) <= 1e-6
+
+
+# ------------------------------------------------------------- the chain
+
+def _gpu_step(wl, meas, kind=2):
+    g, det = wl.grid, wl.det
+    ref = gset(wl.ref, wl.kappa)
+    mbcs = [gset(m, wl.kappa) for m in wl.mbc]
+    V = pmf.gs_voxelize(g, ref)[0]
+    E = torch.stack([pmf.gs_voxelize(g, m) for m in mbcs])
+    w = dev(wl.coeff)
+    vt = views(wl.views)
+    W = pmf.warp_combine(g, V, E, w)
+    Y = pmf.conebeam_project(g, det, vt, W, shared=False)
+    loss, dY = pmf.projection_loss(kind, Y, dev(meas))
+    dW = pmf.conebeam_project_backward(g, det, vt, dY, shared=False)
+    dV, dE, dw = pmf.warp_combine_backward(g, V, E, w, dW)
+    gref = pmf.gs_voxelize_backward(g, ref, dV.reshape(1, *g.shape))
+    gmbc = [pmf.gs_voxelize_backward(g, m, dE[l]) for l, m in enumerate(mbcs)]
+    return loss, Y, dict(coeff=dw, ref=gref, mbc=gmbc, dV=dV, dE=dE, dW=dW)
+
+
+@pytest.mark.parametrize("kind", [2, 1])
+def test_full_chain_forward_and_gradients_match_oracle(kind):
+    wl = fd_subproblem()
+    meas = wl.measured
+    loss, Y, grads = _gpu_step(wl, meas, kind)
+    lref, gref, fref = oracle_chain.step(wl, meas, kind=kind)
+    assert rel_l2(host(Y), fref["Y"]) <= TOL32
+    assert float(loss.item()) == pytest.approx(lref, rel=1e-5)
+    assert rel_l2(host(grads["coeff"]), gref["coeff"]) <= 1e-3
+    for i in range(4):
+        assert rel_l2(host(grads["ref"][i]), gref["ref"][i]) <= 1e-3
+        for l in range(3):
+            assert rel_l2(host(grads["mbc"][l][i]), gref["mbc"][l][i]) <= 1e-3
+
+
+def test_config0_chain_forward_matches_oracle():
+    wl = config0()
+    loss, Y, _ = _gpu_step(wl, wl.measured)
+    f = oracle_chain.forward(wl)
+    assert rel_l2(host(Y), f["Y"]) <= TOL32

@@ -31,6 +31,9 @@ def lib():
             L.orc_quat_to_rot.argtypes = [_D, _D]
             L.orc_voxelize.argtypes = [_I64, _D, ct.c_int64, ct.c_int, _D, _D, _D, _D, ct.c_double, ct.c_int, _D]
             L.orc_voxelize.restype = ct.c_int
+            L.orc_voxelize_ambiguity.argtypes = [_I64, _D, ct.c_int64, ct.c_int, _D, _D, _D, _D, ct.c_double,
+                                                 ct.c_double, _D]
+            L.orc_voxelize_ambiguity.restype = ct.c_int
             L.orc_voxelize_backward.argtypes = [_I64, _D, ct.c_int64, ct.c_int, _D, _D, _D, _D, ct.c_double,
                                                 _D, _D, _D, _D, _D]
             L.orc_voxelize_backward.restype = ct.c_int
@@ -97,6 +100,23 @@ def voxelize(grid, mean, scale, quat, value, kappa=3.0, cull=True) -> np.ndarray
     if rc != 0:
         raise ValueError("oracle voxelize rejected its arguments")
     return out.reshape(c, d[2], d[1], d[0])
+
+
+def voxelize_ambiguity(grid, mean, scale, quat, value, kappa=3.0, eps=1e-4) -> np.ndarray:
+    """Per-voxel mass of truncation decisions within eps*kappa^2 of the cutoff
+    ([nz][ny][nx]); voxel values are unique only up to this mass."""
+    d, v, n = _grid(grid)
+    mean, scale, quat = _f64(mean).reshape(-1, 3), _f64(scale).reshape(-1, 3), _f64(quat).reshape(-1, 4)
+    value = _f64(value)
+    if value.ndim == 1:
+        value = value[:, None]
+    g, c = value.shape
+    out = np.zeros(n)
+    rc = lib().orc_voxelize_ambiguity(d.ctypes.data_as(_I64), _p(v), g, c, _p(mean), _p(scale), _p(quat),
+                                      _p(value), float(kappa), float(eps), _p(out))
+    if rc != 0:
+        raise ValueError("oracle voxelize_ambiguity rejected its arguments")
+    return out.reshape(d[2], d[1], d[0])
 
 
 def voxelize_backward(grid, mean, scale, quat, value, d_out, kappa=3.0):

@@ -152,6 +152,43 @@ int orc_voxelize(const int64_t dims[3], const double vox[3], int64_t G, int C,
     return 0;
 }
 
+/* Per-voxel mass of the truncation decisions that rounding can flip:
+ * amb[v] = sum_g max_c |value[g][c]| exp(-q/2) over the pairs whose q lies in
+ * the band |q - kappa^2| <= eps kappa^2.  An implementation that evaluates q in
+ * lower precision may keep or drop exactly these terms, so a voxel's value is
+ * unique only up to amb[v].  kappa = +inf: no band, amb = 0. */
+int orc_voxelize_ambiguity(const int64_t dims[3], const double vox[3], int64_t G, int C,
+                           const double* mean, const double* scale, const double* quat, const double* value,
+                           double kappa, double eps, double* amb) {
+    if (!(kappa > 0.0) || C < 1 || !(eps >= 0.0)) return -1;
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2], N = nx * ny * nz;
+    memset(amb, 0, sizeof(double) * (size_t)N);
+    if (isinf(kappa)) return 0;
+    const double lo2 = kappa * kappa * (1.0 - eps), hi2 = kappa * kappa * (1.0 + eps);
+    gauss_t* gs = (gauss_t*)malloc(sizeof(gauss_t) * (size_t)(G > 0 ? G : 1));
+    for (int64_t g = 0; g < G; g++)
+        prepare(&gs[g], mean + 3 * g, scale + 3 * g, quat + 4 * g, kappa * sqrt(1.0 + eps), 1, dims, vox);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nz; k++) {
+        for (int64_t g = 0; g < G; g++) {
+            const gauss_t* ga = &gs[g];
+            if (k < ga->lo[2] || k > ga->hi[2]) continue;
+            double vmax = 0.0;
+            for (int c = 0; c < C; c++) vmax = fmax(vmax, fabs(value[g * C + c]));
+            for (int64_t j = ga->lo[1]; j <= ga->hi[1]; j++)
+                for (int64_t i = ga->lo[0]; i <= ga->hi[0]; i++) {
+                    double d[3] = {centre(i, nx, vox[0]) - ga->mu[0], centre(j, ny, vox[1]) - ga->mu[1],
+                                   centre(k, nz, vox[2]) - ga->mu[2]};
+                    double r[3];
+                    double q = qform(ga, d, r);
+                    if (q >= lo2 && q <= hi2) amb[(k * ny + j) * nx + i] += vmax * exp(-0.5 * q);
+                }
+        }
+    }
+    free(gs);
+    return 0;
+}
+
 /* d R / d (w, x, y, z) for the rotation matrix written in quat_to_rot (treating
  * the normalised components as free variables); dR[comp][9]. */
 static void drot_dq(const double q[4], double dR[4][9]) {

@@ -3,20 +3,25 @@
 // sm_103a.
 //
 // Precision: the source sits ~1 m from the volume, so a ray's direction and
-// start are set up in double precision, then carried as float-float (hi + lo)
-// pairs in voxel-index space.  Samples are taken in runs of 32 from an anchor
+// start are set up in double precision and then carried as float-float (hi + lo)
+// pairs in voxel-index space.  Each chunk of 32 samples starts from an anchor
 // whose integer part is exact and whose fraction is float, so every sample
-// position is accurate to ~1e-6 voxel while the inner loop is plain fp32.
+// position is good to ~1e-6 voxel while the inner loop is plain fp32.
 //
-// Threads: one ray per thread; a 256-thread CTA covers a 16x16 pixel tile and
-// each warp an 8x4 patch, so the 32 rays of a warp sample neighbouring voxels
-// at each step and their gathers share cache lines.
-//
-// Adjoint: the same march scatters step * dL/dY * (trilinear weights) into a
-// 64-bit fixed-point accumulator (scale 2^k chosen per call from a provable
-// bound), merging consecutive samples that fall in the same cell before each
-// atomic.  Integer atomics are order independent, so the result is
-// bit-reproducible.
+// Work split: one ray per thread; a 256-thread CTA covers a 16x16 pixel tile
+// (each warp an 8x4 patch).  The tile's rays all leave the same source, so
+// sample m of every ray lies at the same distance m*step from it: the CTA
+// marches its rays in lock-step chunks of 32 samples, and the voxels one chunk
+// touches form a small box (about 16x16x7 at the paper's geometry).
+//  - Forward: the box is staged in shared memory with coalesced loads (zero
+//    outside the grid), and the 8-corner trilinear gathers read shared memory.
+//  - Adjoint: samples accumulate into a shared-memory box in 32-bit fixed point
+//    (per-CTA scale), each ray first merging consecutive samples in a sliding
+//    2x2x2 corner window; the box is then flushed with one 64-bit fixed-point
+//    atomic per touched voxel (global scale 2^k from a provable bound).  Integer
+//    sums are order independent, so the result is bit-reproducible.
+// A chunk whose box does not fit in shared memory falls back to direct
+// (bounds-checked) global gathers or atomics.
 #include <climits>
 
 #include "pmf_common.cuh"
@@ -24,27 +29,27 @@
 namespace pmf {
 namespace {
 
-constexpr int kRay = 256;  // threads per CTA (16 x 16 pixels)
-constexpr int kRun = 32;   // samples per float anchor
+constexpr int kRay = 256;     // threads per CTA (16 x 16 pixels)
+constexpr int kChunk = 32;    // samples per chunk
+constexpr int kBox = 4096;    // shared-memory box capacity (voxels)
+constexpr unsigned kFull = 0xffffffffu;
 
-struct RayMarch {
-    int nsamp;       // number of samples (0: the ray misses the padded volume)
-    float hi[3];     // index-space position of the first sample, float-float
-    float lo[3];
-    float dhi[3];    // index-space step, float-float
-    float dlo[3];
+struct Ray {
+    float uh[3], ul[3];  // index-space position of sample m = 0 (the source), float-float
+    float dh[3], dl[3];  // index-space step, float-float
+    int mlo, mhi;        // samples that can touch the zero-padded volume (mhi < mlo: none)
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = a + b;
-    float bb = s - a;
+    const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
 
-// Pixel (a, b) of `view`: direction, sample range and float-float start.
-__device__ __forceinline__ RayMarch ray_setup(const pmf_view& vw, int nu, int nv, int a, int b, const GridD& g,
-                                              double step) {
-    RayMarch r;
+// Ray through the centre of pixel (a, b) of view `vw`.
+__device__ __forceinline__ Ray ray_init(const pmf_view& vw, int nu, int nv, int a, int b, const GridD& g,
+                                        double step) {
+    Ray r;
     const double ca = (double)a + 0.5 - 0.5 * (double)nu, cb = (double)b + 0.5 - 0.5 * (double)nv;
     double d[3];
     double len2 = 0.0;
@@ -53,20 +58,24 @@ __device__ __forceinline__ RayMarch ray_setup(const pmf_view& vw, int nu, int nv
         d[t] = fma(cb, vw.dv[t], fma(ca, vw.du[t], vw.det[t] - vw.src[t]));
         len2 = fma(d[t], d[t], len2);
     }
-    // 1/sqrt(len2): fp32 seed, two Newton steps in double (~1e-16 relative)
+    // 1/sqrt(len2): fp32 seed, two Newton steps in double
     double y = (double)rsqrtf((float)len2);
     y = y * (1.5 - 0.5 * len2 * y * y);
     y = y * (1.5 - 0.5 * len2 * y * y);
     const int n[3] = {g.nx, g.ny, g.nz};
     const double iv[3] = {1.0 / (double)g.vx, 1.0 / (double)g.vy, 1.0 / (double)g.vz};
-    double us[3], du[3];
     float tlo = 0.0f, thi = 3.0e38f;
     bool miss = false;
 #pragma unroll
     for (int t = 0; t < 3; t++) {
-        us[t] = fma(vw.src[t], iv[t], 0.5 * (double)n[t] - 0.5);
-        du[t] = step * (d[t] * y) * iv[t];
-        const float usf = (float)us[t], duf = (float)du[t];
+        const double us = fma(vw.src[t], iv[t], 0.5 * (double)n[t] - 0.5);
+        const double du = step * (d[t] * y) * iv[t];
+        r.uh[t] = (float)us;
+        r.ul[t] = (float)(us - (double)r.uh[t]);
+        r.dh[t] = (float)du;
+        r.dl[t] = (float)(du - (double)r.dh[t]);
+        const float usf = r.uh[t], duf = r.dh[t];
+        // the padded volume is u in (-1, n) on every axis
         if (duf != 0.0f) {
             const float inv = 1.0f / duf;
             const float t1 = (-1.0f - usf) * inv, t2 = ((float)n[t] - usf) * inv;
@@ -79,33 +88,34 @@ __device__ __forceinline__ RayMarch ray_setup(const pmf_view& vw, int nu, int nv
     // one sample of slack each side: samples outside the padded box read zeros
     const float mlo = fmaxf(floorf(tlo) - 1.0f, 0.0f), mhi = ceilf(thi) + 1.0f;
     if (miss || !(mhi >= mlo) || !(mhi < 1.0e8f)) {
-        r.nsamp = 0;
+        r.mlo = 1;
+        r.mhi = 0;
     } else {
-        r.nsamp = (int)(mhi - mlo) + 1;
-    }
-    const double m0 = (double)mlo;
-#pragma unroll
-    for (int t = 0; t < 3; t++) {
-        const double u0 = fma(m0, du[t], us[t]);
-        r.hi[t] = (float)u0;
-        r.lo[t] = (float)(u0 - (double)r.hi[t]);
-        r.dhi[t] = (float)du[t];
-        r.dlo[t] = (float)(du[t] - (double)r.dhi[t]);
+        r.mlo = (int)mlo;
+        r.mhi = (int)mhi;
     }
     return r;
 }
 
-// Advance the float-float start by kRun steps (exact up to the lo word).
-__device__ __forceinline__ void advance(RayMarch& r) {
+// Integer part and fraction of the position of sample m0 (float-float).
+__device__ __forceinline__ void anchor(const Ray& r, int m0, int ib[3], float fb[3]) {
+    const float m = (float)m0;
 #pragma unroll
     for (int t = 0; t < 3; t++) {
+        const float p = m * r.dh[t];
+        const float pe = fmaf(m, r.dh[t], -p);
         float s, e;
-        two_sum(r.hi[t], (float)kRun * r.dhi[t], s, e);
-        float lo = r.lo[t] + (float)kRun * r.dlo[t] + e;
-        float s2 = s + lo;
-        r.lo[t] = lo - (s2 - s);
-        r.hi[t] = s2;
+        two_sum(r.uh[t], p, s, e);
+        const float lo = ((r.ul[t] + pe) + m * r.dl[t]) + e;
+        const float fl = floorf(s);
+        ib[t] = (int)fl;
+        fb[t] = (s - fl) + lo;
     }
+}
+
+// Sample j of a chunk, relative to the anchor.
+__device__ __forceinline__ float at(const Ray& r, int t, float jf, const float fb[3]) {
+    return fmaf(jf, r.dh[t], fmaf(jf, r.dl[t], fb[t]));
 }
 
 __device__ __forceinline__ void pixel_of(int tile, int ntu, int& a, int& b) {
@@ -118,15 +128,14 @@ __device__ __forceinline__ void pixel_of(int tile, int ntu, int& a, int& b) {
 template <typename T>
 __device__ __forceinline__ float gather8(const T* vol, const GridD& g, int ix, int iy, int iz, float fx, float fy,
                                          float fz) {
-    // interior cells skip the per-corner bounds checks
     if ((unsigned)ix < (unsigned)(g.nx - 1) && (unsigned)iy < (unsigned)(g.ny - 1) &&
         (unsigned)iz < (unsigned)(g.nz - 1)) {
-        const int64_t sx = 1, sy = g.nx, sz = (int64_t)g.nx * g.ny;
+        const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
         const T* p = vol + iz * sz + iy * sy + ix;
-        const float c000 = Store<T>::ld(p, 0), c100 = Store<T>::ld(p, sx);
-        const float c010 = Store<T>::ld(p, sy), c110 = Store<T>::ld(p, sy + sx);
-        const float c001 = Store<T>::ld(p, sz), c101 = Store<T>::ld(p, sz + sx);
-        const float c011 = Store<T>::ld(p, sz + sy), c111 = Store<T>::ld(p, sz + sy + sx);
+        const float c000 = Store<T>::ld(p, 0), c100 = Store<T>::ld(p, 1);
+        const float c010 = Store<T>::ld(p, sy), c110 = Store<T>::ld(p, sy + 1);
+        const float c001 = Store<T>::ld(p, sz), c101 = Store<T>::ld(p, sz + 1);
+        const float c011 = Store<T>::ld(p, sz + sy), c111 = Store<T>::ld(p, sz + sy + 1);
         const float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
         const float a01 = fmaf(fx, c101 - c001, c001), a11 = fmaf(fx, c111 - c011, c011);
         const float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
@@ -135,39 +144,168 @@ __device__ __forceinline__ float gather8(const T* vol, const GridD& g, int ix, i
     return trilin_cell(vol, g, ix, iy, iz, fx, fy, fz);
 }
 
+// Shared block state for the lock-step march.
+struct BoxState {
+    int range[2];   // min mlo, max mhi over the CTA's rays
+    int box[2][6];  // double-buffered cell bounds of the current chunk: lo xyz, hi xyz
+};
+
+__device__ __forceinline__ void reset_box(int* b) {
+    b[0] = b[1] = b[2] = INT_MAX;
+    b[3] = b[4] = b[5] = INT_MIN;
+}
+
+// CTA-wide [min mlo, max mhi] over rays with samples.
+__device__ __forceinline__ void block_range(BoxState& bs, const Ray& r, bool act) {
+    if (threadIdx.x == 0) {
+        bs.range[0] = INT_MAX;
+        bs.range[1] = INT_MIN;
+        reset_box(bs.box[0]);
+        reset_box(bs.box[1]);
+    }
+    __syncthreads();
+    int lo = act ? r.mlo : INT_MAX, hi = act ? r.mhi : INT_MIN;
+    lo = __reduce_min_sync(kFull, lo);
+    hi = __reduce_max_sync(kFull, hi);
+    if ((threadIdx.x & 31) == 0 && lo != INT_MAX) {
+        atomicMin(&bs.range[0], lo);
+        atomicMax(&bs.range[1], hi);
+    }
+    __syncthreads();
+}
+
+// This thread's sample range in the chunk starting at M0, its anchor, and its
+// contribution to the chunk's cell box (reduced per warp).
+__device__ __forceinline__ bool chunk_begin(BoxState& bs, int sel, const Ray& r, bool live, int M0, int& j0,
+                                            int& j1, int ib[3], float fb[3]) {
+    j0 = max(r.mlo, M0) - M0;
+    j1 = min(r.mhi, M0 + kChunk - 1) - M0;
+    const bool act = live && j0 <= j1;
+    int clo[3] = {INT_MAX, INT_MAX, INT_MAX}, chi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    if (act) {
+        anchor(r, M0, ib, fb);
+#pragma unroll
+        for (int t = 0; t < 3; t++) {
+            const int f0 = ib[t] + (int)floorf(at(r, t, (float)j0, fb));
+            const int f1 = ib[t] + (int)floorf(at(r, t, (float)j1, fb));
+            clo[t] = min(f0, f1);
+            chi[t] = max(f0, f1);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 3; t++) {
+        clo[t] = __reduce_min_sync(kFull, clo[t]);
+        chi[t] = __reduce_max_sync(kFull, chi[t]);
+    }
+    if ((threadIdx.x & 31) == 0 && clo[0] != INT_MAX) {
+#pragma unroll
+        for (int t = 0; t < 3; t++) {
+            atomicMin(&bs.box[sel][t], clo[t]);
+            atomicMax(&bs.box[sel][3 + t], chi[t]);
+        }
+    }
+    if (threadIdx.x == 0) reset_box(bs.box[sel ^ 1]);
+    return act;
+}
+
+// Box geometry after the reduction: corners of cells [lo, hi] are [lo, hi + 1].
+struct Box {
+    int lx, ly, lz, bx, by, bz;
+    long long vol;
+};
+
+__device__ __forceinline__ Box read_box(const BoxState& bs, int sel) {
+    Box b;
+    b.lx = bs.box[sel][0]; b.ly = bs.box[sel][1]; b.lz = bs.box[sel][2];
+    if (b.lx == INT_MAX) {
+        b.bx = b.by = b.bz = 0;
+        b.vol = 0;
+        return b;
+    }
+    b.bx = bs.box[sel][3] - b.lx + 2;
+    b.by = bs.box[sel][4] - b.ly + 2;
+    b.bz = bs.box[sel][5] - b.lz + 2;
+    b.vol = (long long)b.bx * b.by * b.bz;
+    return b;
+}
+
+// ----------------------------------------------------------------- forward
+
 template <typename T>
 __global__ void __launch_bounds__(kRay) k_project(GridD g, int nu, int nv, int ntu, float step,
                                                   const pmf_view* __restrict__ views, const T* __restrict__ vol,
                                                   int64_t vol_stride, float* __restrict__ proj) {
+    __shared__ float box[kBox];
+    __shared__ BoxState bs;
     const int p = blockIdx.y;
     int a, b;
     pixel_of(blockIdx.x, ntu, a, b);
-    if (a >= nu || b >= nv) return;
-    const pmf_view vw = views[p];
-    RayMarch r = ray_setup(vw, nu, nv, a, b, g, (double)step);
-    const T* V = vol + (int64_t)p * vol_stride;
-    float acc = 0.0f;
-    for (int jb = 0; jb < r.nsamp; jb += kRun) {
-        int ib[3];
-        float fb[3];
-#pragma unroll
-        for (int t = 0; t < 3; t++) {
-            const float fl = floorf(r.hi[t]);
-            ib[t] = (int)fl;
-            fb[t] = (r.hi[t] - fl) + r.lo[t];
-        }
-        const int jn = min(kRun, r.nsamp - jb);
-        for (int j = 0; j < jn; j++) {
-            const float jf = (float)j;
-            const float ux = fmaf(jf, r.dhi[0], fmaf(jf, r.dlo[0], fb[0]));
-            const float uy = fmaf(jf, r.dhi[1], fmaf(jf, r.dlo[1], fb[1]));
-            const float uz = fmaf(jf, r.dhi[2], fmaf(jf, r.dlo[2], fb[2]));
-            const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
-            acc += gather8(V, g, ib[0] + (int)flx, ib[1] + (int)fly, ib[2] + (int)flz, ux - flx, uy - fly, uz - flz);
-        }
-        advance(r);
+    const bool in = a < nu && b < nv;
+    Ray r;
+    if (in) {
+        r = ray_init(views[p], nu, nv, a, b, g, (double)step);
+    } else {
+        r.mlo = 1; r.mhi = 0;
     }
-    proj[((int64_t)p * nv + b) * nu + a] = step * acc;
+    const bool live = in && r.mlo <= r.mhi;
+    const T* V = vol + (int64_t)p * vol_stride;
+    block_range(bs, r, live);
+    const int Mlo = bs.range[0], Mhi = bs.range[1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float acc = 0.0f;
+    int sel = 0;
+    for (int M0 = Mlo; M0 <= Mhi; M0 += kChunk, sel ^= 1) {
+        int j0, j1, ib[3];
+        float fb[3];
+        const bool act = chunk_begin(bs, sel, r, live, M0, j0, j1, ib, fb);
+        __syncthreads();
+        const Box bx = read_box(bs, sel);
+        if (bx.vol > 0 && bx.vol <= kBox) {
+            // stage the box: one warp per x-row, zero outside the grid
+            const int rows = bx.by * bx.bz;
+            for (int row = warp; row < rows; row += kRay / 32) {
+                const int y = bx.ly + row % bx.by, z = bx.lz + row / bx.by;
+                for (int x0 = lane; x0 < bx.bx; x0 += 32)
+                    box[row * bx.bx + x0] = vox_or_zero(V, g, bx.lx + x0, y, z);
+            }
+            __syncthreads();
+            if (act) {
+                // box-relative positions; cells are clamped into the box, which
+                // only moves a sample that rounding put a hair past the box edge
+                // onto the neighbouring cell with a fraction a hair outside [0, 1]
+                const float syf = (float)bx.bx, szf = (float)(bx.bx * bx.by);
+                const int sy = bx.bx, sz = bx.bx * bx.by;
+                const float ox = (float)(ib[0] - bx.lx) + fb[0], oy = (float)(ib[1] - bx.ly) + fb[1],
+                            oz = (float)(ib[2] - bx.lz) + fb[2];
+                const float mx = (float)(bx.bx - 2), my = (float)(bx.by - 2), mz = (float)(bx.bz - 2);
+                float jf = (float)j0;
+                for (int j = j0; j <= j1; j++, jf += 1.0f) {
+                    const float ux = fmaf(jf, r.dh[0], ox), uy = fmaf(jf, r.dh[1], oy), uz = fmaf(jf, r.dh[2], oz);
+                    const float flx = fminf(fmaxf(floorf(ux), 0.0f), mx);
+                    const float fly = fminf(fmaxf(floorf(uy), 0.0f), my);
+                    const float flz = fminf(fmaxf(floorf(uz), 0.0f), mz);
+                    const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
+                    const float* q = box + (int)fmaf(flz, szf, fmaf(fly, syf, flx));
+                    const float c000 = q[0], c100 = q[1], c010 = q[sy], c110 = q[sy + 1];
+                    const float c001 = q[sz], c101 = q[sz + 1], c011 = q[sz + sy], c111 = q[sz + sy + 1];
+                    const float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
+                    const float a01 = fmaf(fx, c101 - c001, c001), a11 = fmaf(fx, c111 - c011, c011);
+                    const float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
+                    acc += fmaf(fz, b1 - b0, b0);
+                }
+            }
+        } else if (act) {
+            for (int j = j0; j <= j1; j++) {
+                const float jf = (float)j;
+                const float ux = at(r, 0, jf, fb), uy = at(r, 1, jf, fb), uz = at(r, 2, jf, fb);
+                const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
+                acc += gather8(V, g, ib[0] + (int)flx, ib[1] + (int)fly, ib[2] + (int)flz, ux - flx, uy - fly,
+                               uz - flz);
+            }
+        }
+        __syncthreads();
+    }
+    if (in) proj[((int64_t)p * nv + b) * nu + a] = step * acc;
 }
 
 __global__ void k_absmax_f(const float* __restrict__ x, int64_t n, unsigned* out) {
@@ -178,69 +316,292 @@ __global__ void k_absmax_f(const float* __restrict__ x, int64_t n, unsigned* out
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
-// Scatter the 8 corner weights of one cell times g.
-__device__ __forceinline__ void flush_cell(unsigned long long* acc, const GridD& g, int ix, int iy, int iz,
-                                           const float* w, float gs) {
+// ----------------------------------------------------------------- adjoint
+
+// 2x2x2 corner weights of the cell a ray is in, slot c = dx + 2 dy + 4 dz.
+struct Window {
+    int cx, cy, cz;
+    float w[8];
+};
+
+__device__ __forceinline__ void win_clear(Window& W) {
 #pragma unroll
-    for (int c = 0; c < 8; c++) {
-        if (w[c] == 0.0f) continue;
-        const int i = ix + (c & 1), j = iy + ((c >> 1) & 1), k = iz + (c >> 2);
-        if ((unsigned)i >= (unsigned)g.nx || (unsigned)j >= (unsigned)g.ny || (unsigned)k >= (unsigned)g.nz) continue;
-        red_add(acc + ((int64_t)k * g.ny + j) * g.nx + i, to_fixed(w[c] * gs, 1.0f));
+    for (int c = 0; c < 8; c++) W.w[c] = 0.0f;
+}
+
+// Direct global sink (chunks whose box does not fit in shared memory).
+struct GlobalSink {
+    unsigned long long* acc;
+    GridD g;
+    float scale;  // step * g * 2^kg
+    __device__ __forceinline__ void put(int x, int y, int z, float w) const {
+        if (w == 0.0f) return;
+        if ((unsigned)x >= (unsigned)g.nx || (unsigned)y >= (unsigned)g.ny || (unsigned)z >= (unsigned)g.nz) return;
+        red_add(acc + ((int64_t)z * g.ny + y) * g.nx + x, to_fixed(w, scale));
     }
+};
+
+template <class S>
+__device__ __forceinline__ void win_flush_all(Window& W, const S& s) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) s.put(W.cx + (c & 1), W.cy + ((c >> 1) & 1), W.cz + (c >> 2), W.w[c]);
+    win_clear(W);
+}
+
+// Move the window to cell (x, y, z): corners shared by the old and new cell
+// keep their weights, the others are flushed.
+template <class S>
+__device__ __forceinline__ void win_move(Window& W, int x, int y, int z, const S& s) {
+    const int dx = x - W.cx, dy = y - W.cy, dz = z - W.cz;
+    if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) {
+        win_flush_all(W, s);
+        W.cx = x; W.cy = y; W.cz = z;
+        return;
+    }
+    if (dx == 1) {
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+            s.put(W.cx, W.cy + ((c >> 1) & 1), W.cz + (c >> 2), W.w[c]);
+            W.w[c] = W.w[c + 1];
+            W.w[c + 1] = 0.0f;
+        }
+        W.cx += 1;
+    } else if (dx == -1) {
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+            s.put(W.cx + 1, W.cy + ((c >> 1) & 1), W.cz + (c >> 2), W.w[c + 1]);
+            W.w[c + 1] = W.w[c];
+            W.w[c] = 0.0f;
+        }
+        W.cx -= 1;
+    }
+    if (dy == 1) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            if (c & 2) continue;
+            s.put(W.cx + (c & 1), W.cy, W.cz + (c >> 2), W.w[c]);
+            W.w[c] = W.w[c + 2];
+            W.w[c + 2] = 0.0f;
+        }
+        W.cy += 1;
+    } else if (dy == -1) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            if (c & 2) continue;
+            s.put(W.cx + (c & 1), W.cy + 1, W.cz + (c >> 2), W.w[c + 2]);
+            W.w[c + 2] = W.w[c];
+            W.w[c] = 0.0f;
+        }
+        W.cy -= 1;
+    }
+    if (dz == 1) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            s.put(W.cx + (c & 1), W.cy + ((c >> 1) & 1), W.cz, W.w[c]);
+            W.w[c] = W.w[c + 4];
+            W.w[c + 4] = 0.0f;
+        }
+        W.cz += 1;
+    } else if (dz == -1) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            s.put(W.cx + (c & 1), W.cy + ((c >> 1) & 1), W.cz + 1, W.w[c + 4]);
+            W.w[c + 4] = W.w[c];
+            W.w[c] = 0.0f;
+        }
+        W.cz -= 1;
+    }
+}
+
+__device__ __forceinline__ void win_add(Window& W, float fx, float fy, float fz) {
+    const float ex = 1.0f - fx, ey = 1.0f - fy, ez = 1.0f - fz;
+    const float a0 = ey * ez, a1 = fy * ez, a2 = ey * fz, a3 = fy * fz;
+    W.w[0] = fmaf(ex, a0, W.w[0]); W.w[1] = fmaf(fx, a0, W.w[1]);
+    W.w[2] = fmaf(ex, a1, W.w[2]); W.w[3] = fmaf(fx, a1, W.w[3]);
+    W.w[4] = fmaf(ex, a2, W.w[4]); W.w[5] = fmaf(fx, a2, W.w[5]);
+    W.w[6] = fmaf(ex, a3, W.w[6]); W.w[7] = fmaf(fx, a3, W.w[7]);
+}
+
+// Round-to-nearest float -> int for |x| < 2^22 without the conversion pipe:
+// adding 1.5 * 2^23 leaves round(x) in the low mantissa bits.
+__device__ __forceinline__ int round_small(float x) {
+    return __float_as_int(x + 12582912.0f) - 0x4b400000;
+}
+
+// Add the 8 corner weights (already scaled to the CTA's fixed point) of the
+// cell whose corner 000 is box[ci], then clear them.
+__device__ __forceinline__ void corner_add8(int* box, int ci, int sy, int sz, float* w) {
+    atomicAdd(box + ci, round_small(w[0]));
+    atomicAdd(box + ci + 1, round_small(w[1]));
+    atomicAdd(box + ci + sy, round_small(w[2]));
+    atomicAdd(box + ci + sy + 1, round_small(w[3]));
+    atomicAdd(box + ci + sz, round_small(w[4]));
+    atomicAdd(box + ci + sz + 1, round_small(w[5]));
+    atomicAdd(box + ci + sz + sy, round_small(w[6]));
+    atomicAdd(box + ci + sz + sy + 1, round_small(w[7]));
+#pragma unroll
+    for (int c = 0; c < 8; c++) w[c] = 0.0f;
+}
+
+// w += sc * (trilinear corner weights of fractions f)
+__device__ __forceinline__ void win_add8(float* w, float fx, float fy, float fz, float sc) {
+    const float ex = 1.0f - fx, ey = 1.0f - fy, ez = (1.0f - fz) * sc, fzs = fz * sc;
+    const float a0 = ey * ez, a1 = fy * ez, a2 = ey * fzs, a3 = fy * fzs;
+    w[0] = fmaf(ex, a0, w[0]); w[1] = fmaf(fx, a0, w[1]);
+    w[2] = fmaf(ex, a1, w[2]); w[3] = fmaf(fx, a1, w[3]);
+    w[4] = fmaf(ex, a2, w[4]); w[5] = fmaf(fx, a2, w[5]);
+    w[6] = fmaf(ex, a3, w[6]); w[7] = fmaf(fx, a3, w[7]);
+}
+
+// 2^k so that a bound b < 2^(bits) after scaling.
+__device__ __forceinline__ int exp_for(float bound, int bits) {
+    if (!(bound > 0.0f) || !isfinite(bound)) return 0;
+    int e;
+    frexpf(bound, &e);
+    const int k = bits - e;
+    return k > 126 ? 126 : (k < -126 ? -126 : k);
+}
+
+// Adjoint lane layout: lane l = g + 8 q of warp w takes pixel
+// (g + 8 (q & 1), w + 8 (q >> 1)) of the 16x16 tile, so the four lanes of
+// phase group g are 8 pixels apart.
+__device__ __forceinline__ void pixel_of_spread(int tile, int ntu, int& a, int& b) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, g = l & 7, q = l >> 3;
+    const int tu = tile % ntu, tv = tile / ntu;
+    a = tu * 16 + g + 8 * (q & 1);
+    b = tv * 16 + w + 8 * (q >> 1);
 }
 
 __global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, int ntu, float step,
                                                       const pmf_view* __restrict__ views,
                                                       const float* __restrict__ dproj, int64_t vol_stride,
                                                       unsigned long long* __restrict__ acc, const unsigned* maxbits,
-                                                      float bound_mult) {
+                                                      float bound_mult, float samples_per_voxel) {
+    __shared__ int box[kBox];
+    __shared__ BoxState bs;
+    __shared__ unsigned sgmax;
+    __shared__ float gsum[kRay / 32];
     const int p = blockIdx.y;
     int a, b;
-    pixel_of(blockIdx.x, ntu, a, b);
-    if (a >= nu || b >= nv) return;
-    const float gy = __ldg(dproj + ((int64_t)p * nv + b) * nu + a);
-    if (gy == 0.0f) return;
-    const int kexp = fixed_exponent(__uint_as_float(*maxbits) * bound_mult);
-    const float gs = step * gy * ldexpf(1.0f, kexp);  // scaled contribution per unit weight
-    const pmf_view vw = views[p];
-    RayMarch r = ray_setup(vw, nu, nv, a, b, g, (double)step);
-    unsigned long long* A = acc + (int64_t)p * vol_stride;
-    int cx = INT_MIN, cy = 0, cz = 0;
-    float w[8];
-#pragma unroll
-    for (int c = 0; c < 8; c++) w[c] = 0.0f;
-    for (int jb = 0; jb < r.nsamp; jb += kRun) {
-        int ib[3];
-        float fb[3];
-#pragma unroll
-        for (int t = 0; t < 3; t++) {
-            const float fl = floorf(r.hi[t]);
-            ib[t] = (int)fl;
-            fb[t] = (r.hi[t] - fl) + r.lo[t];
+    pixel_of_spread(blockIdx.x, ntu, a, b);
+    const bool in = a < nu && b < nv;
+    const float gy = in ? __ldg(dproj + ((int64_t)p * nv + b) * nu + a) : 0.0f;
+    Ray r;
+    if (in && gy != 0.0f) {
+        r = ray_init(views[p], nu, nv, a, b, g, (double)step);
+    } else {
+        r.mlo = 1; r.mhi = 0;
+    }
+    const bool live = r.mlo <= r.mhi;
+    // scales: global 2^kg (all views, provable bound) and CTA 2^kb <= 2^kg.
+    // Within one chunk a voxel receives at most step * S * sum_r |g_r| from the
+    // CTA's rays, where S bounds the trilinear weight one ray's samples put in
+    // one voxel (a hat function sampled at spacing h sums to at most 1/h + 1).
+    if (threadIdx.x == 0) sgmax = 0u;
+    for (int i = threadIdx.x; i < kBox; i += kRay) box[i] = 0;
+    __syncthreads();
+    {
+        float a = live ? fabsf(gy) : 0.0f;
+        unsigned m = __reduce_max_sync(kFull, __float_as_uint(a));
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+        if ((threadIdx.x & 31) == 0) {
+            gsum[threadIdx.x >> 5] = a;
+            if (m) atomicMax(&sgmax, m);
         }
-        const int jn = min(kRun, r.nsamp - jb);
-        for (int j = 0; j < jn; j++) {
-            const float jf = (float)j;
-            const float ux = fmaf(jf, r.dhi[0], fmaf(jf, r.dlo[0], fb[0]));
-            const float uy = fmaf(jf, r.dhi[1], fmaf(jf, r.dlo[1], fb[1]));
-            const float uz = fmaf(jf, r.dhi[2], fmaf(jf, r.dlo[2], fb[2]));
-            const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
-            const int ix = ib[0] + (int)flx, iy = ib[1] + (int)fly, iz = ib[2] + (int)flz;
-            const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
-            if (ix != cx || iy != cy || iz != cz) {
-                if (cx != INT_MIN) flush_cell(A, g, cx, cy, cz, w, gs);
-                cx = ix; cy = iy; cz = iz;
+    }
+    __syncthreads();
+    float gtot = 0.0f;
+    for (int i = 0; i < kRay / 32; i++) gtot += gsum[i];  // fixed order, same in every thread
+    const int kg = fixed_exponent(__uint_as_float(*maxbits) * bound_mult);
+    const float bcta = gtot * step * samples_per_voxel;
+    const float bray = __uint_as_float(sgmax) * step * samples_per_voxel;
+    // box sums < 2^29 and every single addend < 2^21 (round_small needs < 2^22)
+    const int kb = min(min(exp_for(bcta, 29), exp_for(bray, 21)), kg);
+    const int shift = kg - kb;
+    const float gsb = step * gy * ldexpf(1.0f, kb), gsg = step * gy * ldexpf(1.0f, kg);
+    unsigned long long* A = acc + (int64_t)p * vol_stride;
+    const GlobalSink gsink{A, g, gsg};
+
+    block_range(bs, r, live);
+    const int Mlo = bs.range[0], Mhi = bs.range[1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int sel = 0;
+    for (int M0 = Mlo; M0 <= Mhi; M0 += kChunk, sel ^= 1) {
+        int j0, j1, ib[3];
+        float fb[3];
+        const bool act = chunk_begin(bs, sel, r, live, M0, j0, j1, ib, fb);
+        __syncthreads();
+        const Box bx = read_box(bs, sel);
+        if (bx.vol > 0 && bx.vol <= kBox) {
+            if (act) {
+                const int sy = bx.bx, sz = bx.bx * bx.by;
+                const float syf = (float)sy, szf = (float)sz;
+                const float ox = (float)(ib[0] - bx.lx) + fb[0], oy = (float)(ib[1] - bx.ly) + fb[1],
+                            oz = (float)(ib[2] - bx.lz) + fb[2];
+                const float mx = (float)(bx.bx - 2), my = (float)(bx.by - 2), mz = (float)(bx.bz - 2);
+                // convergent scatter: every lane adds its current cell's 8 corner
+                // weights when it leaves the cell (consecutive samples in one
+                // cell are merged in registers); lanes of one phase group start
+                // 4 samples (2 voxels) after the previous group so a warp's
+                // simultaneous atomics mostly land on different voxels
+                const int phase = threadIdx.x & 7;
+                int ci = -1;
+                float w[8];
 #pragma unroll
                 for (int c = 0; c < 8; c++) w[c] = 0.0f;
+                for (int k = 0; k < kChunk; k++) {
+                    const int j = (k + 4 * phase) & (kChunk - 1);
+                    const bool on = j >= j0 && j <= j1;
+                    const float jf = (float)j;
+                    const float ux = fmaf(jf, r.dh[0], ox), uy = fmaf(jf, r.dh[1], oy), uz = fmaf(jf, r.dh[2], oz);
+                    const float flx = fminf(fmaxf(floorf(ux), 0.0f), mx);
+                    const float fly = fminf(fmaxf(floorf(uy), 0.0f), my);
+                    const float flz = fminf(fmaxf(floorf(uz), 0.0f), mz);
+                    const int idx = on ? (int)fmaf(flz, szf, fmaf(fly, syf, flx)) : ci;
+                    if (idx != ci) {
+                        if (ci >= 0) corner_add8(box, ci, sy, sz, w);
+                        ci = idx;
+                    }
+                    if (on) win_add8(w, ux - flx, uy - fly, uz - flz, gsb);
+                }
+                if (ci >= 0) corner_add8(box, ci, sy, sz, w);
             }
-            const float ex = 1.0f - fx, ey = 1.0f - fy, ez = 1.0f - fz;
-            w[0] += ex * ey * ez; w[1] += fx * ey * ez; w[2] += ex * fy * ez; w[3] += fx * fy * ez;
-            w[4] += ex * ey * fz; w[5] += fx * ey * fz; w[6] += ex * fy * fz; w[7] += fx * fy * fz;
+            __syncthreads();
+            // flush the box: one 64-bit atomic per touched in-grid voxel, and re-zero it
+            const int rows = bx.by * bx.bz;
+            for (int row = warp; row < rows; row += kRay / 32) {
+                const int y = bx.ly + row % bx.by, z = bx.lz + row / bx.by;
+                for (int x0 = lane; x0 < bx.bx; x0 += 32) {
+                    const int i = row * bx.bx + x0;
+                    const int v = box[i];
+                    if (v == 0) continue;
+                    box[i] = 0;
+                    const int x = bx.lx + x0;
+                    if ((unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz)
+                        atomicAdd(A + ((int64_t)z * g.ny + y) * g.nx + x,
+                                  (unsigned long long)((long long)v * (1ll << shift)));
+                }
+            }
+        } else if (act) {
+            Window W;
+            W.cx = INT_MIN;
+            win_clear(W);
+            for (int j = j0; j <= j1; j++) {
+                const float jf = (float)j;
+                const float ux = at(r, 0, jf, fb), uy = at(r, 1, jf, fb), uz = at(r, 2, jf, fb);
+                const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
+                const int cx = ib[0] + (int)flx, cy = ib[1] + (int)fly, cz = ib[2] + (int)flz;
+                if (W.cx == INT_MIN) {
+                    W.cx = cx; W.cy = cy; W.cz = cz;
+                } else if (cx != W.cx || cy != W.cy || cz != W.cz) {
+                    win_move(W, cx, cy, cz, gsink);
+                }
+                win_add(W, ux - flx, uy - fly, uz - flz);
+            }
+            if (W.cx != INT_MIN) win_flush_all(W, gsink);
         }
-        advance(r);
+        __syncthreads();
     }
-    if (cx != INT_MIN) flush_cell(A, g, cx, cy, cz, w, gs);
 }
 
 __global__ void k_fixed_to_float_f(const unsigned long long* __restrict__ acc, int64_t n, const unsigned* maxbits,
@@ -295,6 +656,17 @@ pmf_status check_proj(const pmf_grid* grid, const pmf_detector* det, int32_t P, 
     const int64_t n = (int64_t)grid->nx * grid->ny * grid->nz;
     PMF_REQUIRE(n < ((int64_t)1 << 31), "volume too large for the projector (N < 2^31)");
     return PMF_OK;
+}
+
+// Bound on the trilinear weight one ray's samples within one chunk can give a
+// single voxel: along the axis where the ray moves fastest in index space the
+// samples are at least h = step / (sqrt(3) v_max) apart, and a unit hat
+// function sampled at spacing h sums to at most 1/h + 1; each sample adds at
+// most 1 and a chunk holds kChunk samples.
+float chunk_samples_per_voxel(const pmf_grid* grid, float step) {
+    const double vmax = fmax(fmax((double)grid->vx, (double)grid->vy), (double)grid->vz);
+    const double s = sqrt(3.0) * vmax / (double)step + 1.0;
+    return (float)fmin(s, (double)kChunk);
 }
 
 int max_samples_per_voxel(const pmf_grid* grid, float step) {
@@ -363,7 +735,7 @@ pmf_status conebeam_project_backward(const pmf_grid* grid, const pmf_detector* d
         const int ntu = (det->nu + 15) / 16, ntv = (det->nv + 15) / 16;
         dim3 gr((unsigned)(ntu * ntv), (unsigned)P);
         k_backproject<<<gr, kRay, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, d_proj, vol_stride, acc,
-                                          maxbits, bound_mult);
+                                          maxbits, bound_mult, chunk_samples_per_voxel(grid, det->step_mm));
     }
     int64_t nb = (cells + 255) / 256;
     k_fixed_to_float_f<<<(unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks), 256, 0, s>>>(

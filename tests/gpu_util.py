@@ -44,3 +44,17 @@ def pixel_views(views_np, nu, nv, pixels):
         v[3:6] = v[3:6] + ca * v[6:9] + cb * v[9:12]
         out.append(v)
     return np.array(out)
+
+
+def assert_voxels_match(got, ref, amb, tol):
+    """Voxelization parity that respects truncation ties: voxels with no pair
+    near q = kappa^2 (amb == 0) must match to relative L2 <= tol; voxels with
+    such pairs may differ by at most their ambiguity mass (plus rounding)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    amb = np.broadcast_to(np.asarray(amb, dtype=np.float64), ref.shape)
+    sure = amb == 0
+    assert rel_l2(got[sure], ref[sure]) <= tol
+    slack = amb + 4 * tol * np.abs(ref).max()
+    assert np.all(np.abs(got - ref)[~sure] <= slack[~sure])
+    return float(sure.mean())

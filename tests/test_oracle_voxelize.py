@@ -118,3 +118,24 @@ def test_negative_values_are_permitted():
     b = oracle.voxelize(grid, m, s, q, -val)
     np.testing.assert_array_equal(a, -b)
     assert a.min() < 0 < a.max()
+
+
+def test_ambiguity_mass_is_the_band_between_two_cutoffs():
+    """For positive values, voxelize(kappa sqrt(1+eps)) - voxelize(kappa sqrt(1-eps))
+    keeps exactly the pairs in the band |q - kappa^2| <= eps kappa^2, which is
+    what the ambiguity mass sums; with kappa = inf there is no band."""
+    grid = Grid(16, 14, 12, 2.0, 2.0, 2.0)
+    rng = np.random.default_rng(41)
+    G = 30
+    m = (rng.random((G, 3)) - 0.5) * np.array([32, 28, 24])
+    s = rng.uniform(1.0, 5.0, (G, 3))
+    q, val = rng.normal(size=(G, 4)), rng.random((G, 1))
+    eps = 0.05
+    amb = oracle.voxelize_ambiguity(grid, m, s, q, val, 3.0, eps)
+    hi = oracle.voxelize(grid, m, s, q, val, kappa=3.0 * np.sqrt(1 + eps))[0]
+    lo = oracle.voxelize(grid, m, s, q, val, kappa=3.0 * np.sqrt(1 - eps))[0]
+    # the band's upper edge is inclusive on both sides; the lower cutoff keeps q <= lo2
+    # exactly, so the difference is the band minus pairs sitting exactly on lo2 (none here)
+    np.testing.assert_allclose(hi - lo, amb, rtol=1e-12, atol=1e-15)
+    assert amb.max() > 0
+    assert oracle.voxelize_ambiguity(grid, m, s, q, val, np.inf, eps).max() == 0.0

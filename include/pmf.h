@@ -148,6 +148,25 @@ pmf_status mbc_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf_
                                 const float* coeff, const float* d_dvf, float* d_mbc, float* d_coeff,
                                 int accumulate, void* ws, size_t ws_bytes, pmf_stream stream);
 
+/* The same computation as mbc_combine_backward without a caller workspace, for
+ * callers that cannot allocate device memory on the call path (their device
+ * memory is handed out up front by their own pool, or they must avoid the
+ * device-wide synchronization that allocating and freeing can cause).  The
+ * paper has no counterpart: this is an interface convenience only.
+ * Scratch: a fixed array of P*L*3*608 floats compiled into the library
+ * (about 0.9 MB; every GPU that loads the library holds it until the process
+ * exits), so P*L must be <= 128, else PMF_EWORKSPACE with nothing enqueued.
+ * It allocates nothing (no cudaMalloc/cudaFree or allocating library call).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (every slot read is rewritten first), so calls that overlap
+ * on the GPU -- on different streams, or from different threads -- race;
+ * serialize them. */
+pmf_status mbc_combine_backward_noalloc(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype,
+                                        const void* mbc, const float* coeff, const float* d_dvf, float* d_mbc,
+                                        float* d_coeff, int accumulate, pmf_stream stream);
+
 /* -------------------------------------------------------- warp (Eq. 2) */
 
 /* out[p][v] = Trilin(ref, (i,j,k) + dvf[p][:,v] / (vx,vy,vz)) (pull warp; the

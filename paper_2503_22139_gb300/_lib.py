@@ -53,6 +53,7 @@ SIGNATURES = {
     "mbc_combine": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P],
     "mbc_combine_backward_workspace": [_G, _I32, _I32, _SZ],
     "mbc_combine_backward": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
+    "mbc_combine_backward_noalloc": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P, ct.c_int, _P],
     "warp_volume": [_G, _I32, ct.c_int, _P, _P, _P, _P],
     "warp_volume_backward_workspace": [_G, _I32, _SZ],
     "warp_volume_backward": [_G, _I32, ct.c_int, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],

@@ -497,3 +497,76 @@ pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf
 }
 
 }  // extern "C"
+
+// ------------------------------------------- no-allocation adjoint variant
+//
+// mbc_combine_backward_noalloc: the same computation as mbc_combine_backward
+// for callers that cannot allocate device memory on the call path (for
+// example code whose device memory is all handed out up front by its own
+// pool, or code that must not risk the implicit device-wide synchronization
+// that allocating and freeing can cause).  Its scratch -- the per-block
+// partial sums of d_coeff -- lives in one fixed array in the library's device
+// image instead of a caller-supplied workspace.
+
+#include <mutex>
+
+namespace pmf {
+namespace {
+
+constexpr int kNoAllocMaxPL = 128;  // P * L limit: 128 * 3 * 608 floats, about 0.9 MB per device
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) float g_noalloc_part[kNoAllocMaxPL * 3 * kStreamBlocks];
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_part on the current device, looked up once per
+// device (the host-side symbol is only a stand-in, never a device address).
+pmf_status noalloc_scratch(float** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(PMF_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(PMF_EUNSUPPORTED, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_part);
+        if (e != cudaSuccess || p == nullptr)
+            return set_error(PMF_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (float*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return PMF_OK;
+}
+
+}  // namespace
+}  // namespace pmf
+
+extern "C" pmf_status mbc_combine_backward_noalloc(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype,
+                                                   const void* mbc, const float* coeff, const float* d_dvf,
+                                                   float* d_mbc, float* d_coeff, int accumulate, pmf_stream stream) {
+    pmf_status st = check_common(grid, P, dtype);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(L >= 1 && L <= kMaxL, "L must be in [1, %d]", kMaxL);
+    if ((int64_t)P * L > kNoAllocMaxPL)
+        return set_error(PMF_EWORKSPACE, "P*L = %lld exceeds the fixed scratch of the no-allocation variant (P*L <= %d)",
+                         (long long)P * L, kNoAllocMaxPL);
+    PMF_REQUIRE(mbc && d_mbc && (P == 0 || (coeff && d_dvf && d_coeff)), "null pointer");
+    GridD g = make_grid(grid);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (P == 0) {
+        if (!accumulate) cudaMemsetAsync(d_mbc, 0, sizeof(float) * (size_t)(L * 3 * g.n), s);
+        return check_launch("mbc_combine_backward_noalloc");
+    }
+    float* part = nullptr;
+    if ((st = noalloc_scratch(&part)) != PMF_OK) return st;
+    // every partial slot the reduction reads is written by k_combine_bwd_coeff
+    // first, so the array needs no clearing between calls
+    k_combine_bwd_mbc<<<stream_blocks(g.n), kThreads, 0, s>>>(g, L, P, coeff, d_dvf, d_mbc, accumulate);
+    dim3 gr(kStreamBlocks, (unsigned)(P * 3));
+    PMF_DISPATCH_DTYPE(dtype, T, k_combine_bwd_coeff<T><<<gr, kThreads, 0, s>>>(g, L, P, (const T*)mbc, d_dvf, part));
+    const int64_t nout = (int64_t)P * L * 3;
+    k_reduce_partials<<<(unsigned)((nout + 255) / 256), 256, 0, s>>>(part, nout, kStreamBlocks, d_coeff, accumulate);
+    return check_launch("mbc_combine_backward_noalloc");
+}

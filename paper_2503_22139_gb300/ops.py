@@ -177,6 +177,24 @@ def mbc_combine_backward(grid, mbc, coeff, d_dvf, accumulate=False, grads=None):
     return grads
 
 
+def mbc_combine_backward_noalloc(grid, mbc, coeff, d_dvf, accumulate=False, grads=None):
+    """mbc_combine_backward without a workspace: the library's fixed device
+    scratch is used instead (P * L <= 128; calls must not overlap on the GPU).
+    The output tensors are still allocated here unless `grads` is given."""
+    L = _lib.load()
+    mbc = _need(mbc, "mbc")
+    coeff = _need(coeff, "coeff", torch.float32)
+    d_dvf = _need(d_dvf, "d_dvf", torch.float32)
+    P, Lv = int(coeff.shape[0]), int(coeff.shape[1])
+    if grads is None:
+        grads = (torch.empty(mbc.shape, dtype=torch.float32, device=mbc.device),
+                 torch.empty(coeff.shape, dtype=torch.float32, device=mbc.device))
+    check(L.mbc_combine_backward_noalloc(ct.byref(_grid(grid)), Lv, P, _DT[mbc.dtype], _p(mbc), _p(coeff), _p(d_dvf),
+                                         _p(grads[0]), _p(grads[1]), int(accumulate), _stream()),
+          "mbc_combine_backward_noalloc")
+    return grads
+
+
 def warp_volume(grid, ref, dvf, out=None) -> torch.Tensor:
     L = _lib.load()
     ref, dvf = _need(ref, "ref"), _need(dvf, "dvf")

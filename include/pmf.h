@@ -123,14 +123,19 @@ pmf_status gs_voxelize_count(const pmf_grid* grid, const pmf_gaussians* g, int64
 pmf_status gs_voxelize(const pmf_grid* grid, const pmf_gaussians* g, pmf_dtype dtype, void* out,
                        void* ws, size_t ws_bytes, pmf_stream stream);
 
+/* Bytes of scratch gs_voxelize_backward needs for n Gaussians of `channels`
+ * channels (0 when n is large enough that no Gaussian is split).  Host-only. */
+pmf_status gs_voxelize_backward_workspace(const pmf_grid* grid, int64_t n, int32_t channels, size_t* bytes);
+
 /* Adjoint of gs_voxelize with respect to every Gaussian parameter, given
  * d_out = dL/dout (device fp32 [channels][N]).  Outputs device fp32:
  * d_mean [n][3], d_scale [n][3], d_quat [n][4] (gradient with respect to the
  * raw, unnormalised quaternion), d_value [n][channels].  The truncation
- * indicator has zero derivative.  Needs no scratch. */
+ * indicator has zero derivative.  Large Gaussians are split over several
+ * warps whose partial sums are added in a fixed order (ws holds them). */
 pmf_status gs_voxelize_backward(const pmf_grid* grid, const pmf_gaussians* g, const float* d_out,
                                 float* d_mean, float* d_scale, float* d_quat, float* d_value,
-                                int accumulate, pmf_stream stream);
+                                int accumulate, void* ws, size_t ws_bytes, pmf_stream stream);
 
 /* --------------------------------------------------- DVF combine (Eq. 3) */
 

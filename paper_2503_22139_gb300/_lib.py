@@ -49,7 +49,8 @@ SIGNATURES = {
     "gs_voxelize_workspace": [_G, _I64, _I64, _SZ],
     "gs_voxelize_count": [_G, ct.POINTER(PmfGaussians), _P, _P, ct.c_size_t, _P],
     "gs_voxelize": [_G, ct.POINTER(PmfGaussians), ct.c_int, _P, _P, ct.c_size_t, _P],
-    "gs_voxelize_backward": [_G, ct.POINTER(PmfGaussians), _P, _P, _P, _P, _P, ct.c_int, _P],
+    "gs_voxelize_backward_workspace": [_G, _I64, _I32, _SZ],
+    "gs_voxelize_backward": [_G, ct.POINTER(PmfGaussians), _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
     "mbc_combine": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P],
     "mbc_combine_backward_workspace": [_G, _I32, _I32, _SZ],
     "mbc_combine_backward": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],

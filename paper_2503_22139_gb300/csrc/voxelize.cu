@@ -305,76 +305,104 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
 __global__ void k_copy_total(const VoxWs w, int64_t* d_pairs) { *d_pairs = w.hdr->total_pairs; }
 
 // ------------------------------------------------------------ backward
+//
+// Work item = one warp on (Gaussian g, slab s): the warp takes the rows (y, z)
+// of g's voxel box with row index = s (mod S), one row per lane, and on each
+// row only the x span
+// where the quadratic form can be <= kappa^2 (solved analytically, with one
+// voxel of slack; the per-voxel test is the forward's).  It accumulates the
+// C + 9 moments, reduces them over the warp in a fixed tree, and writes either
+// the gradient (S = 1) or a partial that a second pass sums in slab order.
 
-constexpr int kBwdThreads = 128;
+constexpr int kBwdWarps = 8;   // warps per CTA
+constexpr int kMom = 9;        // S1 (3) + S2 (6)
 
 template <int C>
-__global__ void __launch_bounds__(kBwdThreads) k_vox_bwd(pmf_gaussians G, GridD g, const float* __restrict__ dout,
-                                                         float* d_mean, float* d_scale, float* d_quat,
-                                                         float* d_value, int accumulate) {
-    __shared__ float red[kBwdThreads / 32][C + 9];
-    const int64_t i = blockIdx.x;
-    GaussSetup s;
-    gauss_setup(G, i, g, G.kappa, s);
+struct Moments {
+    float gv[C], s1[3], s2[6];
+};
+
+// Row x-span of {q <= k2} for fixed (dy, dz), as voxel indices clamped to [lo, hi].
+__device__ __forceinline__ bool row_span(const GaussSetup& s, float k2, float dy, float dz, const GridD& g, int& xlo,
+                                         int& xhi) {
+    xlo = s.lo[0];
+    xhi = s.hi[0];
+    if (isinf(k2)) return true;
+    const float B = s.b01 * dy + s.b02 * dz;
+    const float C0 = s.a11 * dy * dy + s.b12 * dy * dz + s.a22 * dz * dz - k2;
+    const float disc = B * B - 4.0f * s.a00 * C0;
+    // skip only rows that are clearly empty; near-tangent rows keep their
+    // candidates and the exact per-voxel test decides
+    if (disc < -1e-4f * (B * B + fabsf(4.0f * s.a00 * C0))) return false;
+    const float r = sqrtf(fmaxf(disc, 0.0f));
+    const float inv2a = 0.5f / s.a00;
+    const float d0 = (-B - r) * inv2a, d1 = (-B + r) * inv2a;
+    const float c = s.mu[0] * g.ivx + 0.5f * (float)g.nx - 0.5f;
+    const float f0 = floorf(c + d0 * g.ivx) - 1.0f, f1 = ceilf(c + d1 * g.ivx) + 1.0f;
+    xlo = max(xlo, (int)fmaxf(f0, -1.0f));
+    xhi = min(xhi, (int)fminf(f1, (float)g.nx));
+    return xlo <= xhi;
+}
+
+template <int C>
+__device__ __forceinline__ void warp_moments(const pmf_gaussians& G, int64_t i, const GaussSetup& s, const GridD& g,
+                                             const float* __restrict__ dout, int slab, int S, Moments<C>& m) {
+    const int lane = threadIdx.x & 31;
     const float k2 = isinf(G.kappa) ? INFINITY : G.kappa * G.kappa;
     float val[C];
 #pragma unroll
-    for (int c = 0; c < C; c++) val[c] = __ldg(G.value + i * C + c);
-    float gv[C], S1[3] = {0.f, 0.f, 0.f}, S2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int c = 0; c < C; c++) {
+        val[c] = __ldg(G.value + i * C + c);
+        m.gv[c] = 0.f;
+    }
 #pragma unroll
-    for (int c = 0; c < C; c++) gv[c] = 0.f;
+    for (int a = 0; a < 3; a++) m.s1[a] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 6; a++) m.s2[a] = 0.f;
+    if (s.lo[0] > s.hi[0] || s.lo[1] > s.hi[1] || s.lo[2] > s.hi[2]) return;
+    const int ey = s.hi[1] - s.lo[1] + 1, ez = s.hi[2] - s.lo[2] + 1;
+    const int rows = ey * ez;
     const int64_t N = g.n;
-    if (s.lo[0] <= s.hi[0] && s.lo[1] <= s.hi[1] && s.lo[2] <= s.hi[2]) {
-        const int ex = s.hi[0] - s.lo[0] + 1, ey = s.hi[1] - s.lo[1] + 1, ez = s.hi[2] - s.lo[2] + 1;
-        const int64_t cnt = (int64_t)ex * ey * ez;
-        for (int64_t c0 = threadIdx.x; c0 < cnt; c0 += kBwdThreads) {
-            const int x = s.lo[0] + (int)(c0 % ex);
-            const int y = s.lo[1] + (int)((c0 / ex) % ey);
-            const int z = s.lo[2] + (int)(c0 / ((int64_t)ex * ey));
+    // one box row per lane (rows slab, slab + S, ... are this warp's), each
+    // lane walking its row's x span
+    for (int row = slab + S * lane; row < rows; row += 32 * S) {
+        const int y = s.lo[1] + row % ey, z = s.lo[2] + row / ey;
+        const float dy = centre(y, g.ny, g.vy) - s.mu[1];
+        const float dz = centre(z, g.nz, g.vz) - s.mu[2];
+        int xlo, xhi;
+        if (!row_span(s, k2, dy, dz, g, xlo, xhi)) continue;
+        const int64_t rowbase = ((int64_t)z * g.ny + y) * g.nx;
+        for (int x = xlo; x <= xhi; x++) {
             const float dx = centre(x, g.nx, g.vx) - s.mu[0];
-            const float dy = centre(y, g.ny, g.vy) - s.mu[1];
-            const float dz = centre(z, g.nz, g.vz) - s.mu[2];
             const float q = qform(dx, dy, dz, s.a00, s.a11, s.a22, s.b01, s.b02, s.b12);
             if (!(q <= k2)) continue;
             const float e = exp2f(q * kNegHalfLog2e);
-            const int64_t v = ((int64_t)z * g.ny + y) * g.nx + x;
+            const int64_t v = rowbase + x;
             float sw = 0.f;
 #pragma unroll
             for (int c = 0; c < C; c++) {
                 const float go = __ldg(dout + c * N + v);
-                gv[c] = fmaf(go, e, gv[c]);
+                m.gv[c] = fmaf(go, e, m.gv[c]);
                 sw = fmaf(val[c], go, sw);
             }
             const float wgt = sw * e;
-            S1[0] = fmaf(wgt, dx, S1[0]); S1[1] = fmaf(wgt, dy, S1[1]); S1[2] = fmaf(wgt, dz, S1[2]);
+            m.s1[0] = fmaf(wgt, dx, m.s1[0]); m.s1[1] = fmaf(wgt, dy, m.s1[1]); m.s1[2] = fmaf(wgt, dz, m.s1[2]);
             const float wx = wgt * dx, wy = wgt * dy;
-            S2[0] = fmaf(wx, dx, S2[0]); S2[1] = fmaf(wx, dy, S2[1]); S2[2] = fmaf(wx, dz, S2[2]);
-            S2[3] = fmaf(wy, dy, S2[3]); S2[4] = fmaf(wy, dz, S2[4]); S2[5] = fmaf(wgt * dz, dz, S2[5]);
+            m.s2[0] = fmaf(wx, dx, m.s2[0]); m.s2[1] = fmaf(wx, dy, m.s2[1]); m.s2[2] = fmaf(wx, dz, m.s2[2]);
+            m.s2[3] = fmaf(wy, dy, m.s2[3]); m.s2[4] = fmaf(wy, dz, m.s2[4]); m.s2[5] = fmaf(wgt * dz, dz, m.s2[5]);
         }
     }
-    // fixed-order reduction: butterfly within warps, then warps in order
-    float r[C + 9];
-#pragma unroll
-    for (int c = 0; c < C; c++) r[c] = gv[c];
-#pragma unroll
-    for (int a = 0; a < 3; a++) r[C + a] = S1[a];
-#pragma unroll
-    for (int a = 0; a < 6; a++) r[C + 3 + a] = S2[a];
-#pragma unroll
-    for (int k = 0; k < C + 9; k++)
-        for (int o = 16; o > 0; o >>= 1) r[k] += __shfl_xor_sync(0xffffffffu, r[k], o);
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int k = 0; k < C + 9; k++) red[threadIdx.x >> 5][k] = r[k];
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-#pragma unroll
-    for (int k = 0; k < C + 9; k++) {
-        float t = 0.f;
-        for (int wi = 0; wi < kBwdThreads / 32; wi++) t += red[wi][k];
-        r[k] = t;
-    }
+}
+
+__device__ __forceinline__ float warp_sum(float r) {
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
+// Gradients of one Gaussian from its summed moments (thread-local).
+template <int C>
+__device__ void moments_to_grad(const GaussSetup& s, const float* r, int64_t i, float* d_mean, float* d_scale,
+                                float* d_quat, float* d_value, int accumulate) {
     const float* s1 = r + C;
     const float* s2v = r + C + 3;
     const float S2m[3][3] = {{s2v[0], s2v[1], s2v[2]}, {s2v[1], s2v[3], s2v[4]}, {s2v[2], s2v[4], s2v[5]}};
@@ -406,7 +434,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_vox_bwd(pmf_gaussians G, GridD 
     const float qn[4] = {w, x, y, z};
     const float inv = 1.0f / s.qnorm;
     for (int c = 0; c < 4; c++) {
-        float v = (gq[c] - qn[c] * dot) * inv;
+        const float v = (gq[c] - qn[c] * dot) * inv;
         d_quat[4 * i + c] = accumulate ? d_quat[4 * i + c] + v : v;
     }
     for (int a = 0; a < 3; a++) {
@@ -414,6 +442,68 @@ __global__ void __launch_bounds__(kBwdThreads) k_vox_bwd(pmf_gaussians G, GridD 
         d_scale[3 * i + a] = accumulate ? d_scale[3 * i + a] + gs[a] : gs[a];
     }
     for (int c = 0; c < C; c++) d_value[i * C + c] = accumulate ? d_value[i * C + c] + r[c] : r[c];
+}
+
+template <int C>
+__global__ void __launch_bounds__(32 * kBwdWarps) k_vox_bwd(pmf_gaussians G, GridD g, int S,
+                                                            const float* __restrict__ dout, float* part,
+                                                            float* d_mean, float* d_scale, float* d_quat,
+                                                            float* d_value, int accumulate) {
+    const int64_t item = (int64_t)blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
+    if (item >= G.n * S) return;
+    const int64_t i = item / S;
+    const int slab = (int)(item - i * S);
+    GaussSetup st;
+    gauss_setup(G, i, g, G.kappa, st);
+    Moments<C> m;
+    warp_moments<C>(G, i, st, g, dout, slab, S, m);
+    float r[C + kMom];
+#pragma unroll
+    for (int c = 0; c < C; c++) r[c] = warp_sum(m.gv[c]);
+#pragma unroll
+    for (int a = 0; a < 3; a++) r[C + a] = warp_sum(m.s1[a]);
+#pragma unroll
+    for (int a = 0; a < 6; a++) r[C + 3 + a] = warp_sum(m.s2[a]);
+    if ((threadIdx.x & 31) != 0) return;
+    if (S == 1) {
+        moments_to_grad<C>(st, r, i, d_mean, d_scale, d_quat, d_value, accumulate);
+    } else {
+#pragma unroll
+        for (int k = 0; k < C + kMom; k++) part[item * (C + kMom) + k] = r[k];
+    }
+}
+
+// Sum a Gaussian's S slab partials in a fixed order (lane-strided, then a
+// fixed tree) and form its gradient.
+template <int C>
+__global__ void __launch_bounds__(32 * kBwdWarps) k_vox_bwd_final(pmf_gaussians G, GridD g, int S,
+                                                                  const float* __restrict__ part, float* d_mean,
+                                                                  float* d_scale, float* d_quat, float* d_value,
+                                                                  int accumulate) {
+    const int64_t i = (int64_t)blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
+    if (i >= G.n) return;
+    const int lane = threadIdx.x & 31;
+    float r[C + kMom];
+#pragma unroll
+    for (int k = 0; k < C + kMom; k++) r[k] = 0.f;
+    for (int sl = lane; sl < S; sl += 32)
+#pragma unroll
+        for (int k = 0; k < C + kMom; k++) r[k] += part[(i * S + sl) * (C + kMom) + k];
+#pragma unroll
+    for (int k = 0; k < C + kMom; k++) r[k] = warp_sum(r[k]);
+    if (lane != 0) return;
+    GaussSetup st;
+    gauss_setup(G, i, g, G.kappa, st);
+    moments_to_grad<C>(st, r, i, d_mean, d_scale, d_quat, d_value, accumulate);
+}
+
+// Slabs per Gaussian: enough warps to fill the GPU a few times over, at most
+// 256, a power of two.
+int bwd_slabs(int64_t n) {
+    int64_t want = (int64_t)152 * 64 * 4;  // warps
+    int s = 1;
+    while (s < 256 && n * s * 2 <= want) s *= 2;
+    return s;
 }
 
 pmf_status validate_gaussians(const pmf_gaussians* g) {
@@ -514,23 +604,45 @@ pmf_status gs_voxelize(const pmf_grid* grid, const pmf_gaussians* gs, pmf_dtype 
     return check_launch("gs_voxelize");
 }
 
+pmf_status gs_voxelize_backward_workspace(const pmf_grid* grid, int64_t n, int32_t channels, size_t* bytes) {
+    pmf_status st = validate_grid(grid);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(bytes != nullptr && n >= 0 && channels >= 1, "bad arguments");
+    if (channels > kMaxC) return set_error(PMF_EUNSUPPORTED, "channels > %d not supported", kMaxC);
+    const int S = bwd_slabs(n);
+    *bytes = S > 1 ? align_up(sizeof(float) * (size_t)n * S * (channels + kMom)) : 0;
+    return PMF_OK;
+}
+
 pmf_status gs_voxelize_backward(const pmf_grid* grid, const pmf_gaussians* gs, const float* d_out, float* d_mean,
-                                float* d_scale, float* d_quat, float* d_value, int accumulate, pmf_stream stream) {
+                                float* d_scale, float* d_quat, float* d_value, int accumulate, void* ws,
+                                size_t ws_bytes, pmf_stream stream) {
     pmf_status st = validate_grid(grid);
     if (st != PMF_OK) return st;
     if ((st = validate_gaussians(gs)) != PMF_OK) return st;
+    size_t need = 0;
+    if ((st = gs_voxelize_backward_workspace(grid, gs->n, gs->channels, &need)) != PMF_OK) return st;
+    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
     if (gs->n == 0) return PMF_OK;
     PMF_REQUIRE(d_out && d_mean && d_scale && d_quat && d_value, "null gradient pointer");
-    PMF_REQUIRE(gs->n <= 0x7fffffffll, "too many gaussians for one launch");
     GridD g = make_grid(grid);
     cudaStream_t s = (cudaStream_t)stream;
-    const unsigned nb = (unsigned)gs->n;
+    const int S = bwd_slabs(gs->n);
+    float* part = (float*)ws;
+    const int64_t items = gs->n * S;
+    const unsigned nb = (unsigned)((items + kBwdWarps - 1) / kBwdWarps);
+    const unsigned nf = (unsigned)((gs->n + kBwdWarps - 1) / kBwdWarps);
+    const int T = 32 * kBwdWarps;
+#define PMF_VB(CC)                                                                                               \
+    k_vox_bwd<CC><<<nb, T, 0, s>>>(*gs, g, S, d_out, part, d_mean, d_scale, d_quat, d_value, accumulate);     \
+    if (S > 1) k_vox_bwd_final<CC><<<nf, T, 0, s>>>(*gs, g, S, part, d_mean, d_scale, d_quat, d_value, accumulate);
     switch (gs->channels) {
-        case 1: k_vox_bwd<1><<<nb, kBwdThreads, 0, s>>>(*gs, g, d_out, d_mean, d_scale, d_quat, d_value, accumulate); break;
-        case 2: k_vox_bwd<2><<<nb, kBwdThreads, 0, s>>>(*gs, g, d_out, d_mean, d_scale, d_quat, d_value, accumulate); break;
-        case 3: k_vox_bwd<3><<<nb, kBwdThreads, 0, s>>>(*gs, g, d_out, d_mean, d_scale, d_quat, d_value, accumulate); break;
-        default: k_vox_bwd<4><<<nb, kBwdThreads, 0, s>>>(*gs, g, d_out, d_mean, d_scale, d_quat, d_value, accumulate); break;
+        case 1: { PMF_VB(1) break; }
+        case 2: { PMF_VB(2) break; }
+        case 3: { PMF_VB(3) break; }
+        default: { PMF_VB(4) break; }
     }
+#undef PMF_VB
     return check_launch("gs_voxelize_backward");
 }
 

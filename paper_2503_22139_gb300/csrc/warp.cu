@@ -329,6 +329,258 @@ __global__ void __launch_bounds__(kThreads) k_warp_combine_bwd(GridD g, int L, i
     }
 }
 
+// ---------------------------------------------- tiled fused combine + warp
+//
+// A CTA owns a 32x4x4 voxel tile (256 threads, two voxels each: z and z+2),
+// keeps the coefficient table in shared memory and each voxel's MBC vectors
+// in registers for all P projections.  The adjoint scatters V's gradient into
+// a shared-memory box covering the tile plus a 4-voxel halo in 32-bit fixed
+// point (per-CTA scale, provable bound), flushed once per CTA with 64-bit
+// fixed-point atomics at the call's global scale; targets outside the halo go
+// straight to global memory.
+
+constexpr int kTX = 32, kTY = 4, kTZ = 4, kHalo = 4;
+constexpr int kBX = kTX + 2 * kHalo, kBY = kTY + 2 * kHalo, kBZ = kTZ + 2 * kHalo;
+constexpr int kBoxN = kBX * kBY * kBZ;
+constexpr int kMaxPLTile = 512;  // P * L limit of the tiled path
+
+struct TileIdx {
+    int x0, y0, z0;
+    int x, y, z[2];
+};
+
+__device__ __forceinline__ TileIdx tile_idx(const GridD& g) {
+    const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
+    const int b = blockIdx.x;
+    TileIdx t;
+    t.x0 = (b % ntx) * kTX;
+    t.y0 = ((b / ntx) % nty) * kTY;
+    t.z0 = (b / (ntx * nty)) * kTZ;
+    t.x = t.x0 + (threadIdx.x & 31);
+    t.y = t.y0 + ((threadIdx.x >> 5) & 3);
+    t.z[0] = t.z0 + (threadIdx.x >> 7);
+    t.z[1] = t.z[0] + 2;
+    return t;
+}
+
+__device__ __forceinline__ int round_small_i(float x) { return __float_as_int(x + 12582912.0f) - 0x4b400000; }
+
+template <typename T, int L>
+__global__ void __launch_bounds__(256) k_wc_fwd_tile(GridD g, int P, const T* __restrict__ ref,
+                                                     const T* __restrict__ E, const float* __restrict__ w,
+                                                     T* __restrict__ W) {
+    extern __shared__ float sw[];  // [P][L][3]
+    for (int i = threadIdx.x; i < P * L * 3; i += 256) sw[i] = w[i];
+    __syncthreads();
+    const TileIdx t = tile_idx(g);
+    if (t.x >= g.nx || t.y >= g.ny) return;
+    const int64_t N = g.n;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int z = t.z[h];
+        if (z >= g.nz) continue;
+        const int64_t v = ((int64_t)z * g.ny + t.y) * g.nx + t.x;
+        float e[L][3];
+#pragma unroll
+        for (int l = 0; l < L; l++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) e[l][a] = Store<T>::ld(E, ((int64_t)l * 3 + a) * N + v);
+        for (int p = 0; p < P; p++) {
+            const float* c = sw + p * L * 3;
+            float d[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                float acc = 0.f;
+#pragma unroll
+                for (int l = 0; l < L; l++) acc = fmaf(c[l * 3 + a], e[l][a], acc);
+                d[a] = acc;
+            }
+            const Cell cl = make_cell(t.x, t.y, z, d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
+            Store<T>::st(W, (int64_t)p * N + v, trilin_cell(ref, g, cl.i0, cl.j0, cl.k0, cl.fx, cl.fy, cl.fz));
+        }
+    }
+}
+
+__device__ __forceinline__ int exp_bits(float bound, int bits) {
+    if (!(bound > 0.0f) || !isfinite(bound)) return 0;
+    int e;
+    frexpf(bound, &e);
+    const int k = bits - e;
+    return k > 126 ? 126 : (k < -126 ? -126 : k);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __restrict__ ref,
+                                                     const T* __restrict__ E, const float* __restrict__ w,
+                                                     const float* __restrict__ dW, float* d_mbc,
+                                                     unsigned long long* acc, const unsigned* maxbits, float* part,
+                                                     int accumulate) {
+    extern __shared__ float smem[];
+    const int PL3 = P * L * 3;
+    float* sw = smem;                              // [P][L][3]
+    int* box = (int*)(smem + ((PL3 + 3) & ~3));    // [kBZ][kBY][kBX]
+    float* swarp = (float*)(box + kBoxN);          // [8 warps][P][L][3]
+    __shared__ float red_sum[8];
+    __shared__ unsigned red_max;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < PL3; i += 256) sw[i] = w[i];
+    for (int i = threadIdx.x; i < kBoxN; i += 256) box[i] = 0;
+    for (int i = threadIdx.x; i < 8 * PL3; i += 256) swarp[i] = 0.f;
+    if (threadIdx.x == 0) red_max = 0u;
+    const TileIdx t = tile_idx(g);
+    const int64_t N = g.n;
+    bool in[2];
+    int64_t v[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        in[h] = t.x < g.nx && t.y < g.ny && t.z[h] < g.nz;
+        v[h] = in[h] ? ((int64_t)t.z[h] * g.ny + t.y) * g.nx + t.x : 0;
+    }
+    // per-CTA fixed-point scale: one target voxel receives at most
+    // sum |dW| over the tile's (voxel, view) pairs, each addend at most max |dW|
+    float s = 0.f, m = 0.f;
+    for (int p = 0; p < P; p++)
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+            if (in[h]) {
+                const float a = fabsf(__ldg(dW + (int64_t)p * N + v[h]));
+                s += a;
+                m = fmaxf(m, a);
+            }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    __syncthreads();
+    if (lane == 0) {
+        red_sum[warp] = s;
+        if (mb) atomicMax(&red_max, mb);
+    }
+    __syncthreads();
+    float stot = 0.f;
+    for (int i = 0; i < 8; i++) stot += red_sum[i];
+    const int kg = fixed_exponent(__uint_as_float(*maxbits) * (float)(N * P));
+    const int kb = min(min(exp_bits(stot, 29), exp_bits(__uint_as_float(red_max), 21)), kg);
+    const float sb = ldexpf(1.0f, kb), sg = ldexpf(1.0f, kg);
+    const int shift = kg - kb;
+    const int bx0 = t.x0 - kHalo, by0 = t.y0 - kHalo, bz0 = t.z0 - kHalo;
+
+    float e[2][L][3], gE[2][L][3];
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int l = 0; l < L; l++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                e[h][l][a] = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + a) * N + v[h]) : 0.f;
+                gE[h][l][a] = 0.f;
+            }
+    for (int p = 0; p < P; p++) {
+        const float* c = sw + p * L * 3;
+        float cw[L][3];
+#pragma unroll
+        for (int l = 0; l < L; l++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) cw[l][a] = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (!in[h]) continue;
+            const float gw = __ldg(dW + (int64_t)p * N + v[h]);
+            if (gw == 0.f) continue;
+            float d[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                float acc_ = 0.f;
+#pragma unroll
+                for (int l = 0; l < L; l++) acc_ = fmaf(c[l * 3 + a], e[h][l][a], acc_);
+                d[a] = acc_;
+            }
+            const Cell cl = make_cell(t.x, t.y, t.z[h], d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
+            float gx, gy, gz;
+            trilin_grad(ref, g, cl, gx, gy, gz);
+            const float gd[3] = {gw * gx * g.ivx, gw * gy * g.ivy, gw * gz * g.ivz};
+#pragma unroll
+            for (int l = 0; l < L; l++)
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    gE[h][l][a] = fmaf(gd[a], c[l * 3 + a], gE[h][l][a]);
+                    cw[l][a] = fmaf(gd[a], e[h][l][a], cw[l][a]);
+                }
+            // V's adjoint: 8 trilinear corners
+            const int rx = cl.i0 - bx0, ry = cl.j0 - by0, rz = cl.k0 - bz0;
+            const float wx[2] = {1.f - cl.fx, cl.fx}, wy[2] = {1.f - cl.fy, cl.fy}, wz[2] = {1.f - cl.fz, cl.fz};
+            if ((unsigned)rx < (unsigned)(kBX - 1) && (unsigned)ry < (unsigned)(kBY - 1) &&
+                (unsigned)rz < (unsigned)(kBZ - 1)) {
+                int* q = box + (rz * kBY + ry) * kBX + rx;
+                const float gsb = gw * sb;
+#pragma unroll
+                for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+                    for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+                        for (int dx = 0; dx < 2; dx++)
+                            atomicAdd(q + (dz * kBY + dy) * kBX + dx, round_small_i(gsb * (wx[dx] * wy[dy] * wz[dz])));
+            } else {
+                scatter_cell(acc, g, cl, gw, sg);
+            }
+        }
+        // coefficient gradient partials: warp tree, then the warp's own slot
+#pragma unroll
+        for (int l = 0; l < L; l++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                float r = cw[l][a];
+                for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+                if (lane == 0) swarp[warp * PL3 + p * L * 3 + l * 3 + a] += r;
+            }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        if (!in[h]) continue;
+#pragma unroll
+        for (int l = 0; l < L; l++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                float* o = d_mbc + ((int64_t)l * 3 + a) * N + v[h];
+                *o = accumulate ? *o + gE[h][l][a] : gE[h][l][a];
+            }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < PL3; i += 256) {
+        float r = 0.f;
+        for (int wi = 0; wi < 8; wi++) r += swarp[wi * PL3 + i];
+        part[(int64_t)i * gridDim.x + blockIdx.x] = r;
+    }
+    for (int i = threadIdx.x; i < kBoxN; i += 256) {
+        const int val = box[i];
+        if (val == 0) continue;
+        const int x = bx0 + i % kBX, y = by0 + (i / kBX) % kBY, z = bz0 + i / (kBX * kBY);
+        if ((unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz)
+            atomicAdd(acc + ((int64_t)z * g.ny + y) * g.nx + x, (unsigned long long)((long long)val * (1ll << shift)));
+    }
+}
+
+// One CTA per output: strided fixed-order partial sums, then a fixed tree.
+__global__ void __launch_bounds__(256) k_reduce_partials_wide(const float* part, int nb, float* out, int accumulate) {
+    __shared__ float red[8];
+    const int64_t o = blockIdx.x;
+    float r = 0.f;
+    for (int b = threadIdx.x; b < nb; b += 256) r += part[o * nb + b];
+    const float tot = block_sum<256>(r, red);
+    if (threadIdx.x == 0) out[o] = accumulate ? out[o] + tot : tot;
+}
+
+template <typename T, int LL>
+void launch_wc_bwd(unsigned nt, size_t smem, cudaStream_t s, const GridD& g, int P, const void* ref, const void* mbc,
+                   const float* coeff, const float* d_out, float* d_mbc, unsigned long long* acc,
+                   const unsigned* maxbits, float* part, int accumulate) {
+    cudaFuncSetAttribute(k_wc_bwd_tile<T, LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_wc_bwd_tile<T, LL><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, d_out, d_mbc, acc, maxbits,
+                                                part, accumulate);
+}
+
+int num_tiles(const GridD& g) {
+    return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + kTZ - 1) / kTZ);
+}
+
 unsigned stream_blocks(int64_t work) {
     int64_t b = (work + kThreads - 1) / kThreads;
     return (unsigned)(b < kStreamBlocks ? (b > 0 ? b : 1) : kStreamBlocks);
@@ -448,6 +700,19 @@ pmf_status warp_combine(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dt
     PMF_REQUIRE(ref && mbc && coeff && out, "null pointer");
     GridD g = make_grid(grid);
     cudaStream_t s = (cudaStream_t)stream;
+    if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
+        const size_t smem = sizeof(float) * (size_t)P * L * 3;
+        const unsigned nt = (unsigned)num_tiles(g);
+        PMF_DISPATCH_DTYPE(dtype, T, {
+            switch (L) {
+                case 1: k_wc_fwd_tile<T, 1><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (T*)out); break;
+                case 2: k_wc_fwd_tile<T, 2><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (T*)out); break;
+                case 3: k_wc_fwd_tile<T, 3><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (T*)out); break;
+                default: k_wc_fwd_tile<T, 4><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (T*)out); break;
+            }
+        });
+        return check_launch("warp_combine");
+    }
     PMF_DISPATCH_DTYPE(dtype, T, k_warp_combine<T><<<stream_blocks(g.n), kThreads, 0, s>>>(g, L, P, (const T*)ref, (const T*)mbc, coeff, (T*)out));
     return check_launch("warp_combine");
 }
@@ -457,8 +722,9 @@ pmf_status warp_combine_backward_workspace(const pmf_grid* grid, int32_t L, int3
     if (st != PMF_OK) return st;
     PMF_REQUIRE(bytes != nullptr && P >= 0 && L >= 1 && L <= kMaxL, "bad arguments");
     GridD g = make_grid(grid);
+    const size_t nb = (size_t)(num_tiles(g) > kStreamBlocks ? num_tiles(g) : kStreamBlocks);
     *bytes = align_up(256) + align_up(sizeof(unsigned long long) * (size_t)g.n) +
-             align_up(sizeof(float) * (size_t)P * L * 3 * kStreamBlocks);
+             align_up(sizeof(float) * (size_t)P * L * 3 * nb);
     return PMF_OK;
 }
 
@@ -484,6 +750,22 @@ pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf
         if (!accumulate) cudaMemsetAsync(d_mbc, 0, sizeof(float) * (size_t)(L * 3 * g.n), s);
     } else {
         k_absmax<<<stream_blocks(g.n * P), kThreads, 0, s>>>(d_out, g.n * P, maxbits);
+        if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
+            const int PL3 = P * L * 3;
+            const size_t smem2 = sizeof(float) * (size_t)(((PL3 + 3) & ~3) + kBoxN + 8 * PL3);
+            const unsigned nt = (unsigned)num_tiles(g);
+            PMF_DISPATCH_DTYPE(dtype, T, {
+                switch (L) {
+                    case 1: launch_wc_bwd<T, 1>(nt, smem2, s, g, P, ref, mbc, coeff, d_out, d_mbc, acc, maxbits, part, accumulate); break;
+                    case 2: launch_wc_bwd<T, 2>(nt, smem2, s, g, P, ref, mbc, coeff, d_out, d_mbc, acc, maxbits, part, accumulate); break;
+                    case 3: launch_wc_bwd<T, 3>(nt, smem2, s, g, P, ref, mbc, coeff, d_out, d_mbc, acc, maxbits, part, accumulate); break;
+                    default: launch_wc_bwd<T, 4>(nt, smem2, s, g, P, ref, mbc, coeff, d_out, d_mbc, acc, maxbits, part, accumulate); break;
+                }
+            });
+            k_reduce_partials_wide<<<(unsigned)(P * L * 3), 256, 0, s>>>(part, (int)nt, d_coeff, accumulate);
+            k_fixed_to_float<<<stream_blocks(g.n), kThreads, 0, s>>>(acc, g.n, maxbits, (float)(g.n * (int64_t)P), d_ref, accumulate);
+            return check_launch("warp_combine_backward");
+        }
         const unsigned nb = stream_blocks(g.n);
         PMF_DISPATCH_DTYPE(dtype, T, {
             if (smem > 48 * 1024) cudaFuncSetAttribute(k_warp_combine_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -131,7 +131,12 @@ def gs_voxelize(grid, gs: Gaussians, dtype=torch.float32, pair_capacity: Optiona
     return out
 
 
-def gs_voxelize_backward(grid, gs: Gaussians, d_out: torch.Tensor, grads=None, accumulate: bool = False):
+def gs_voxelize_backward_workspace(grid, n: int, channels: int) -> int:
+    L = _lib.load()
+    return _size(L.gs_voxelize_backward_workspace, ct.byref(_grid(grid)), int(n), int(channels))
+
+
+def gs_voxelize_backward(grid, gs: Gaussians, d_out: torch.Tensor, grads=None, accumulate: bool = False, ws=None):
     """Adjoint of gs_voxelize -> (d_mean, d_scale, d_quat, d_value), fp32."""
     L = _lib.load()
     g = _grid(grid)
@@ -140,9 +145,11 @@ def gs_voxelize_backward(grid, gs: Gaussians, d_out: torch.Tensor, grads=None, a
     if grads is None:
         grads = (torch.empty((gs.n, 3), device=dev), torch.empty((gs.n, 3), device=dev),
                  torch.empty((gs.n, 4), device=dev), torch.empty((gs.n, gs.channels), device=dev))
+    if ws is None:
+        ws = _ws(gs_voxelize_backward_workspace(grid, gs.n, gs.channels), dev)
     s = gs.c_struct()
     check(L.gs_voxelize_backward(ct.byref(g), ct.byref(s), _p(d_out), *[_p(t) for t in grads], int(accumulate),
-                                 _stream()), "gs_voxelize_backward")
+                                 _p(ws), ws.numel(), _stream()), "gs_voxelize_backward")
     return grads
 
 

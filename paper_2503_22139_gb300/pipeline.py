@@ -22,7 +22,7 @@ from .ops import Gaussians
 
 # kernels each entry point launches (memsets excluded): used for the launch count
 KERNELS = {
-    "gs_voxelize": 4, "gs_voxelize_backward": 1, "warp_combine": 1, "conebeam_project": 1,
+    "gs_voxelize": 4, "gs_voxelize_backward": 2, "warp_combine": 1, "conebeam_project": 1,
     "projection_loss": 2, "conebeam_project_backward": 3, "warp_combine_backward": 4,
 }
 
@@ -60,6 +60,8 @@ class ForwardAdjoint:
         self.bp_ws = ops._ws(ops._size(Lb.conebeam_project_backward_workspace, ops.ct.byref(g), self.B, n), dev)
         self.wc_ws = ops._ws(ops._size(Lb.warp_combine_backward_workspace, ops.ct.byref(g), L, self.B), dev)
         self.loss_ws = ops._ws(ops._size(Lb.projection_loss_workspace, self.B * det.nu * det.nv), dev)
+        self.vb_ws = [ops._ws(ops.gs_voxelize_backward_workspace(grid, gs.n, gs.channels), dev)
+                      for gs in [ref] + self.mbc]
 
     @property
     def launches_per_step(self) -> int:
@@ -80,7 +82,8 @@ class ForwardAdjoint:
         loss, dY = ops.projection_loss(self.kind, self.Y, meas, ws=self.loss_ws)
         ops.conebeam_project_backward(g, det, views, dY, shared=False, out=self.dW, ws=self.bp_ws)
         ops.warp_combine_backward(g, self.V[0], self.E, coeff, self.dW, grads=self.g_wc, ws=self.wc_ws)
-        ops.gs_voxelize_backward(g, self.ref, self.g_wc[0].reshape((1,) + self.g_wc[0].shape), grads=self.g_ref)
+        ops.gs_voxelize_backward(g, self.ref, self.g_wc[0].reshape((1,) + self.g_wc[0].shape), grads=self.g_ref,
+                                 ws=self.vb_ws[0])
         for l, m in enumerate(self.mbc):
-            ops.gs_voxelize_backward(g, m, self.g_wc[1][l], grads=self.g_mbc[l])
+            ops.gs_voxelize_backward(g, m, self.g_wc[1][l], grads=self.g_mbc[l], ws=self.vb_ws[1 + l])
         return loss

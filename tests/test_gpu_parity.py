@@ -290,3 +290,34 @@ def test_projector_source_inside_volume():
     dY = np.random.default_rng(33).normal(size=(3, 14, 20)).astype(np.float32)
     gb = host(pmf.conebeam_project_backward(grid, det, views(vw), dev(dY), shared=True))
     assert rel_l2(gb, oracle.project_backward(grid, 20, 14, 1.0, vw, dY, shared=True)) <= TOL32
+
+
+@pytest.mark.parametrize("L,std", [(3, 6.0), (1, 1.0), (4, 3.0)])
+def test_fused_warp_tiles_with_large_displacements(L, std):
+    """Ragged 32x4x4 tiles and displacements well past the 4-voxel shared-memory
+    halo (std 6 mm at 2 mm voxels): both the box and the direct scatter paths."""
+    grid = Grid(37, 9, 7, 2.0, 2.0, 2.0)
+    rng = np.random.default_rng(40 + L)
+    V = rng.random(grid.shape).astype(np.float32)
+    E = rng.normal(0, std, (L, 3) + grid.shape).astype(np.float32)
+    w = rng.uniform(-1, 1, (5, L, 3)).astype(np.float32)
+    dW = rng.normal(size=(5,) + grid.shape).astype(np.float32)
+    D = oracle.combine(E, w)
+    assert rel_l2(host(pmf.warp_combine(grid, dev(V), dev(E), dev(w))), oracle.warp(grid, V, D)) <= TOL32
+    dV_ref, dD_ref = oracle.warp_backward(grid, V, D, dW)
+    dE_ref, dw_ref = oracle.combine_backward(E, w, dD_ref)
+    dV, dE, dw = pmf.warp_combine_backward(grid, dev(V), dev(E), dev(w), dev(dW))
+    assert rel_l2(host(dV), dV_ref) <= TOL32
+    assert rel_l2(host(dE), dE_ref) <= 1e-4
+    assert rel_l2(host(dw), dw_ref) <= 1e-4
+
+
+def test_voxelize_backward_unsplit_many_gaussians():
+    """Enough Gaussians that each is handled by a single warp (no slab split)."""
+    grid = Grid(40, 36, 30, 2.0, 2.0, 2.0)
+    gs = _rand_gaussians(55, grid, 24000, 0.5, 2.0, 1)
+    d_out = np.random.default_rng(56).normal(size=(1,) + grid.shape).astype(np.float32)
+    got = pmf.gs_voxelize_backward(grid, gset(gs, 3.0), dev(d_out))
+    ref = oracle.voxelize_backward(grid, gs.mean, gs.scale, gs.quat, gs.value, d_out, 3.0)
+    for name, g_, r_ in zip(("mean", "scale", "quat", "value"), got, ref):
+        assert rel_l2(host(g_), r_) <= 1e-4, name

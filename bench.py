@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="f32")
+    ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="bf16",
+                    help="storage type of V, E, W (all arithmetic and gradients are fp32)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the batched-fp32 and plain per-projection fp32 comparison runs")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--kind", type=int, default=2, help="1 = L1 loss, 2 = L2 loss")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -163,6 +166,52 @@ def algorithmic_bytes(stage: str, B: int, n: int, q: int, L: int, esz: int) -> f
     return 0.0
 
 
+# Algorithmic fp32 flops per ray sample (counted from the definition, Eq. 6):
+# forward: 3 position FMAs (6) + 7 linear blends of 3 flops (21) + accumulate (1);
+# adjoint: 3 position FMAs (6) + the 8 trilinear weights (3 complements, 4 pair
+# products, 8 products: 15) + 8 weighted adds into the volume gradient (16).
+FLOPS_PER_SAMPLE = {"conebeam_project": 28.0, "conebeam_project_backward": 37.0}
+KERNEL_OF = {"conebeam_project": "k_project", "conebeam_project_backward": "k_backproject",
+             "warp_combine": "k_wc_fwd_tile", "warp_combine_backward": "k_wc_bwd_tile",
+             "gs_voxelize": "k_render", "gs_voxelize_backward": "k_vox_bwd", "projection_loss": "k_loss"}
+
+
+def fp32_peak():
+    """Non-tensor fp32 FMA peak: 152 SMs x 128 lanes x 2 flops x the maximum SM clock."""
+    mhz = 2070.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        mhz = float(json.load(open(path)).get("sm_max_mhz", mhz))
+        return round(152 * 128 * 2 * mhz * 1e6 / 1e12, 3), f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz"
+    return round(152 * 128 * 2 * mhz * 1e6 / 1e12, 3), "derived (fallback clock)"
+
+
+def samples_per_view(grid, det, views):
+    """Ray samples per view that fall inside the zero-padded volume (the terms
+    the line-integral sum of Eq. 6 actually has), counted exactly per ray."""
+    import numpy as np
+    n = np.array([grid.nx, grid.ny, grid.nz], dtype=np.float64)
+    v = np.array([grid.vx, grid.vy, grid.vz], dtype=np.float64)
+    a = np.arange(det.nu) + 0.5 - det.nu / 2.0
+    b = np.arange(det.nv) + 0.5 - det.nv / 2.0
+    out = np.zeros(len(views))
+    for i, vw in enumerate(np.asarray(views, dtype=np.float64)):
+        src, dc, du, dv = vw[0:3], vw[3:6], vw[6:9], vw[9:12]
+        d = dc + b[:, None, None] * dv + a[None, :, None] * du - src
+        d /= np.linalg.norm(d, axis=-1, keepdims=True)
+        us = src / v + n / 2 - 0.5
+        st = det.step_mm * d / v
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1 = (-1.0 - us) / st
+            t2 = (n - us) / st
+        lo = np.nanmax(np.where(st != 0, np.minimum(t1, t2), -np.inf), axis=-1)
+        hi = np.nanmin(np.where(st != 0, np.maximum(t1, t2), np.inf), axis=-1)
+        inside = np.all((st != 0) | ((us > -1) & (us < n)), axis=-1)
+        cnt = np.ceil(hi) - np.maximum(np.floor(lo) + 1.0, 0.0)
+        out[i] = np.where(inside & (cnt > 0), cnt, 0.0).sum()
+    return out
+
+
 # ------------------------------------------------------------ native arm
 
 def run_native(a):
@@ -257,19 +306,44 @@ def run_native(a):
     value = total_proj / elapsed
     stage_ms = {s: sum(e0.elapsed_time(e1) for e0, e1 in ev[s]) / a.steps for s in stage_names if ev[s]}
 
-    # roofline of the dominant stage
+    # rooflines: the projector stages are bound by arithmetic issue (every sample is
+    # a trilinear gather or scatter), the streaming stages by HBM
     n, q, L = wl.grid.n, wl.det.q, wl.levels
     esz = torch.tensor([], dtype=dt).element_size()
-    dom = max(stage_ms, key=stage_ms.get)
-    per_launch_ms = stage_ms[dom] / max(1, len(ev[dom]) // a.steps)
-    alg = algorithmic_bytes(dom, B, n, q, L, esz)
-    peak, src = peaks()
-    achieved = alg / (per_launch_ms / 1e3) / 1e9 if alg else 0.0
+    hbm_peak, hsrc = peaks()
+    f32_peak, fsrc = fp32_peak()
+    timed_views = np.concatenate([wl.views[perm][((rank * 7919 + a.warmup + k) % nbatch) * B:
+                                                 ((rank * 7919 + a.warmup + k) % nbatch) * B + B]
+                                  for k in range(a.steps)])
+    # per launch (B views): exact counts on up to 64 of the timed views, scaled
+    sub = timed_views[np.linspace(0, len(timed_views) - 1, min(64, len(timed_views))).astype(int)]
+    samples = float(samples_per_view(wl.grid, wl.det, sub).mean()) * B
     workload_tag = f"{'small' if a.small else 'config1'}-{a.dtype}-B{B}"
-    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 5), "peak_source": f"{src} hbm_gbs",
-            "traffic": traffic_for(dom, workload_tag), "algorithmic_bytes": alg,
-            "avg_launch_ms": round(per_launch_ms, 4)}
+    stage_roof = {}
+    for st, ms in stage_ms.items():
+        per_launch_ms = ms / max(1, len(ev[st]) // a.steps)
+        sec = per_launch_ms / 1e3
+        alg_b = algorithmic_bytes(st, B, n, q, L, esz)
+        ent = {"avg_launch_ms": round(per_launch_ms, 4)}
+        if alg_b:
+            ent.update({"hbm_achieved_gbs": round(alg_b / sec / 1e9, 2), "hbm_frac": round(alg_b / sec / 1e9 / hbm_peak, 5),
+                        "algorithmic_bytes": alg_b})
+        if st in FLOPS_PER_SAMPLE:
+            fl = samples * FLOPS_PER_SAMPLE[st]
+            ent.update({"bound": "alu", "achieved": round(fl / sec / 1e12, 3), "peak": f32_peak, "unit": "TFLOP/s",
+                        "frac": round(fl / sec / 1e12 / f32_peak, 5), "algorithmic_flops": fl,
+                        "samples_per_launch": samples})
+        elif alg_b:
+            ent.update({"bound": "hbm", "achieved": ent["hbm_achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                        "frac": ent["hbm_frac"]})
+        stage_roof[st] = ent
+    dom = max(stage_ms, key=stage_ms.get)
+    d = stage_roof[dom]
+    roof = {"kernel": KERNEL_OF.get(dom, dom), "stage": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
+            "peak": d.get("peak"), "unit": d.get("unit"), "frac": d.get("frac"),
+            "peak_source": (f"{fsrc}" if d.get("unit") == "TFLOP/s" else f"{hsrc} hbm_gbs"),
+            "traffic": traffic_for(KERNEL_OF.get(dom, dom), workload_tag),
+            "hbm_frac": d.get("hbm_frac"), "avg_launch_ms": d["avg_launch_ms"]}
 
     # end to end: pinned host inputs -> device -> step -> gradients back to pinned host
     e2e = None
@@ -326,6 +400,42 @@ def run_native(a):
         e2e = {"value": round(total_proj / te, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    launches = step.launches_per_step * a.steps
+    variants = {}
+    if not a.no_variants:
+        from paper_2503_22139_gb300.pipeline import PlainPerProjection
+        main_dt = a.dtype
+        del step
+        torch.cuda.empty_cache()
+        kv = max(2, min(a.steps, 6))
+        for name, cls, vdt in (("batched_f32", ForwardAdjoint, "f32"),
+                               ("plain_per_projection_f32", PlainPerProjection, "f32")):
+            if name == "batched_f32" and main_dt == "f32":
+                variants[name] = round(value, 3)
+                continue
+            vstep = cls(wl.grid, wl.det, ref, mbc, batch=B, dtype=torch.float32, kind=a.kind)
+            for k in range(2):
+                vstep.run(*batch(k))
+            torch.cuda.synchronize()
+            if world > 1:
+                tdist.barrier()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for k in range(kv):
+                vstep.run(*batch(a.warmup + k))
+            v1.record(stream)
+            torch.cuda.synchronize()
+            tv = v0.elapsed_time(v1) / 1e3
+            if world > 1:
+                tt = torch.tensor([tv], device="cuda")
+                tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+                tv = float(tt.item())
+            variants[name] = round(B * kv * world / tv, 3)
+            del vstep
+            torch.cuda.empty_cache()
+        variants[f"batched_{main_dt}_over_plain_f32"] = round(value / variants["plain_per_projection_f32"], 3)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(wl, meas_np, small=a.small)
@@ -333,13 +443,15 @@ def run_native(a):
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(elapsed * 1e3 / a.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if not a.small else "small: 64^3 @4mm, 2k Gaussians, 128^2 det, 8 views",
                    "batch_projections": B, "loss": "L2" if a.kind == 2 else "L1", "storage_dtype": a.dtype,
                    "accumulate_dtype": "f32", "l2_policy": "working set > L2 (E 144 MB, W and dW 512 MB each)",
                    "parallelism": f"replicas{world}"},
         "roofline": roof, "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
-        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": step.launches_per_step * a.steps,
+        "stage_rooflines": stage_roof,
+        "variants_projections_per_s": variants or None,
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
         "loss": float(loss.item()),
     }
     if rank == 0:

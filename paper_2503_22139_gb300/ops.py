@@ -168,14 +168,15 @@ def mbc_combine(grid, mbc: torch.Tensor, coeff: torch.Tensor, out=None) -> torch
     return out
 
 
-def mbc_combine_backward(grid, mbc, coeff, d_dvf, accumulate=False, grads=None):
+def mbc_combine_backward(grid, mbc, coeff, d_dvf, accumulate=False, grads=None, ws=None):
     L = _lib.load()
     mbc = _need(mbc, "mbc")
     coeff = _need(coeff, "coeff", torch.float32)
     d_dvf = _need(d_dvf, "d_dvf", torch.float32)
     P, Lv = int(coeff.shape[0]), int(coeff.shape[1])
     g = _grid(grid)
-    ws = _ws(_size(L.mbc_combine_backward_workspace, ct.byref(g), Lv, P), mbc.device)
+    if ws is None:
+        ws = _ws(_size(L.mbc_combine_backward_workspace, ct.byref(g), Lv, P), mbc.device)
     if grads is None:
         grads = (torch.empty(mbc.shape, dtype=torch.float32, device=mbc.device),
                  torch.empty(coeff.shape, dtype=torch.float32, device=mbc.device))
@@ -213,13 +214,14 @@ def warp_volume(grid, ref, dvf, out=None) -> torch.Tensor:
     return out
 
 
-def warp_volume_backward(grid, ref, dvf, d_out, need_dvf=True, accumulate=False, grads=None):
+def warp_volume_backward(grid, ref, dvf, d_out, need_dvf=True, accumulate=False, grads=None, ws=None):
     L = _lib.load()
     ref, dvf = _need(ref, "ref"), _need(dvf, "dvf")
     d_out = _need(d_out, "d_out", torch.float32)
     P = int(dvf.shape[0])
     g = _grid(grid)
-    ws = _ws(_size(L.warp_volume_backward_workspace, ct.byref(g), P), ref.device)
+    if ws is None:
+        ws = _ws(_size(L.warp_volume_backward_workspace, ct.byref(g), P), ref.device)
     if grads is None:
         grads = (torch.empty(ref.shape, dtype=torch.float32, device=ref.device),
                  torch.empty(dvf.shape, dtype=torch.float32, device=ref.device) if need_dvf else None)

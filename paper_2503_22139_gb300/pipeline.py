@@ -87,3 +87,53 @@ class ForwardAdjoint:
         for l, m in enumerate(self.mbc):
             ops.gs_voxelize_backward(g, m, self.g_wc[1][l], grads=self.g_mbc[l], ws=self.vb_ws[1 + l])
         return loss
+
+
+class PlainPerProjection(ForwardAdjoint):
+    """The same forward + adjoint, one projection per call and unfused (the DVF
+    is written and read back; the paper's projector also runs one view per
+    call, Sec. 4).  Used as the per-projection baseline for the batched path."""
+
+    def __init__(self, *args, **kwargs):
+        super().__init__(*args, **kwargs)
+        shape, n = ops._shape(self.grid)
+        dev = self.ref.mean.device
+        Lb = ops._lib.load()
+        g = ops._grid(self.grid)
+        self.D1 = torch.empty((1, 3) + shape, dtype=self.dtype, device=dev)
+        self.dD1 = torch.empty((1, 3) + shape, dtype=torch.float32, device=dev)
+        self.bp1_ws = ops._ws(ops._size(Lb.conebeam_project_backward_workspace, ops.ct.byref(g), 1, n), dev)
+        self.wb1_ws = ops._ws(ops._size(Lb.warp_volume_backward_workspace, ops.ct.byref(g), 1), dev)
+        self.cb1_ws = ops._ws(ops._size(Lb.mbc_combine_backward_workspace, ops.ct.byref(g), self.L, 1), dev)
+
+    @property
+    def launches_per_step(self) -> int:
+        k = KERNELS
+        per_view = 1 + 1 + 1 + 3 + 3 + 4  # combine, warp, project, project_bwd, warp_bwd, combine_bwd
+        return (1 + self.L) * (k["gs_voxelize"] + k["gs_voxelize_backward"]) + k["projection_loss"] + self.B * per_view
+
+    def run(self, views: torch.Tensor, coeff: torch.Tensor, meas: torch.Tensor):
+        g, det = self.grid, self.det
+        ops.gs_voxelize(g, self.ref, out=self.V, ws=self.vox_ws[0])
+        for l, m in enumerate(self.mbc):
+            ops.gs_voxelize(g, m, out=self.E[l], ws=self.vox_ws[1 + l])
+        for p in range(self.B):
+            ops.mbc_combine(g, self.E, coeff[p:p + 1], out=self.D1)
+            ops.warp_volume(g, self.V[0], self.D1, out=self.W[p:p + 1])
+            ops.conebeam_project(g, det, views[p:p + 1], self.W[p:p + 1], shared=False, out=self.Y[p:p + 1])
+        loss, dY = ops.projection_loss(self.kind, self.Y, meas, ws=self.loss_ws)
+        gV, gE, gw = self.g_wc
+        gw.zero_()  # each view's coefficient slot is written once, by accumulating into zero
+        for p in range(self.B):
+            ops.conebeam_project_backward(g, det, views[p:p + 1], dY[p:p + 1], shared=False,
+                                          out=self.dW[p:p + 1], ws=self.bp1_ws)
+            ops.mbc_combine(g, self.E, coeff[p:p + 1], out=self.D1)
+            self.dD1.zero_()
+            ops.warp_volume_backward(g, self.V[0], self.D1, self.dW[p:p + 1], accumulate=p > 0,
+                                     grads=(gV, self.dD1), ws=self.wb1_ws)
+            ops.mbc_combine_backward(g, self.E, coeff[p:p + 1], self.dD1, accumulate=p > 0,
+                                     grads=(gE, gw[p:p + 1]), ws=self.cb1_ws)
+        ops.gs_voxelize_backward(g, self.ref, gV.reshape((1,) + gV.shape), grads=self.g_ref, ws=self.vb_ws[0])
+        for l, m in enumerate(self.mbc):
+            ops.gs_voxelize_backward(g, m, gE[l], grads=self.g_mbc[l], ws=self.vb_ws[1 + l])
+        return loss

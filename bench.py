@@ -131,7 +131,7 @@ def traffic_for(kernel: str, workload: str):
     if not os.path.exists(path):
         return None
     d = json.load(open(path)).get(kernel)
-    if not d or d.get("workload") != workload:
+    if not d or workload not in d.get("workloads", []):
         return None
     src = os.path.join(ROOT, d["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d.get("source_sha"):

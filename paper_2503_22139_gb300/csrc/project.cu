@@ -31,7 +31,8 @@ namespace {
 
 constexpr int kRay = 256;     // threads per CTA (16 x 16 pixels)
 constexpr int kChunk = 32;    // samples per chunk
-constexpr int kBox = 4096;    // shared-memory box capacity (voxels)
+constexpr int kBox = 6144;    // shared-memory box capacity (words)
+constexpr int kPitch = 33;    // box row pitch: x = lane (box width <= 32), odd against bank conflicts
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Ray {
@@ -212,6 +213,7 @@ __device__ __forceinline__ bool chunk_begin(BoxState& bs, int sel, const Ray& r,
 struct Box {
     int lx, ly, lz, bx, by, bz;
     long long vol;
+    bool fits;  // width <= 32 and by * bz rows of kPitch words fit in kBox
 };
 
 __device__ __forceinline__ Box read_box(const BoxState& bs, int sel) {
@@ -220,12 +222,14 @@ __device__ __forceinline__ Box read_box(const BoxState& bs, int sel) {
     if (b.lx == INT_MAX) {
         b.bx = b.by = b.bz = 0;
         b.vol = 0;
+        b.fits = false;
         return b;
     }
     b.bx = bs.box[sel][3] - b.lx + 2;
     b.by = bs.box[sel][4] - b.ly + 2;
     b.bz = bs.box[sel][5] - b.lz + 2;
     b.vol = (long long)b.bx * b.by * b.bz;
+    b.fits = b.bx <= 32 && (long long)b.by * b.bz * kPitch <= kBox;
     return b;
 }
 
@@ -260,21 +264,30 @@ __global__ void __launch_bounds__(kRay) k_project(GridD g, int nu, int nv, int n
         const bool act = chunk_begin(bs, sel, r, live, M0, j0, j1, ib, fb);
         __syncthreads();
         const Box bx = read_box(bs, sel);
-        if (bx.vol > 0 && bx.vol <= kBox) {
-            // stage the box: one warp per x-row, zero outside the grid
-            const int rows = bx.by * bx.bz;
-            for (int row = warp; row < rows; row += kRay / 32) {
-                const int y = bx.ly + row % bx.by, z = bx.lz + row / bx.by;
-                for (int x0 = lane; x0 < bx.bx; x0 += 32)
-                    box[row * bx.bx + x0] = vox_or_zero(V, g, bx.lx + x0, y, z);
+        if (bx.vol > 0 && bx.fits) {
+            // stage the box: lane = x, one warp per (y, z) row, zero outside the grid
+            {
+                const int x = bx.lx + lane;
+                const bool xin = lane < bx.bx && (unsigned)x < (unsigned)g.nx;
+                for (int zz = 0; zz < bx.bz; zz++) {
+                    const int z = bx.lz + zz;
+                    const bool zin = (unsigned)z < (unsigned)g.nz;
+                    for (int yy = warp; yy < bx.by; yy += kRay / 32) {
+                        const int y = bx.ly + yy;
+                        float val = 0.0f;
+                        if (xin && zin && (unsigned)y < (unsigned)g.ny)
+                            val = Store<T>::ld(V, ((int64_t)z * g.ny + y) * g.nx + x);
+                        box[(zz * bx.by + yy) * kPitch + lane] = val;
+                    }
+                }
             }
             __syncthreads();
             if (act) {
                 // box-relative positions; cells are clamped into the box, which
                 // only moves a sample that rounding put a hair past the box edge
                 // onto the neighbouring cell with a fraction a hair outside [0, 1]
-                const float syf = (float)bx.bx, szf = (float)(bx.bx * bx.by);
-                const int sy = bx.bx, sz = bx.bx * bx.by;
+                const float syf = (float)kPitch, szf = (float)(kPitch * bx.by);
+                const int sy = kPitch, sz = kPitch * bx.by;
                 const float ox = (float)(ib[0] - bx.lx) + fb[0], oy = (float)(ib[1] - bx.ly) + fb[1],
                             oz = (float)(ib[2] - bx.lz) + fb[2];
                 const float mx = (float)(bx.bx - 2), my = (float)(bx.by - 2), mz = (float)(bx.bz - 2);
@@ -422,25 +435,23 @@ __device__ __forceinline__ void win_add(Window& W, float fx, float fy, float fz)
     W.w[6] = fmaf(ex, a3, W.w[6]); W.w[7] = fmaf(fx, a3, W.w[7]);
 }
 
-// Round-to-nearest float -> int for |x| < 2^22 without the conversion pipe:
-// adding 1.5 * 2^23 leaves round(x) in the low mantissa bits.
-__device__ __forceinline__ int round_small(float x) {
-    return __float_as_int(x + 12582912.0f) - 0x4b400000;
-}
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: floats in [2^23, 2^24) are integers
+constexpr int kMagicBits = 0x4b400000;
 
-// Add the 8 corner weights (already scaled to the CTA's fixed point) of the
-// cell whose corner 000 is box[ci], then clear them.
-__device__ __forceinline__ void corner_add8(int* box, int ci, int sy, int sz, float* w) {
-    atomicAdd(box + ci, round_small(w[0]));
-    atomicAdd(box + ci + 1, round_small(w[1]));
-    atomicAdd(box + ci + sy, round_small(w[2]));
-    atomicAdd(box + ci + sy + 1, round_small(w[3]));
-    atomicAdd(box + ci + sz, round_small(w[4]));
-    atomicAdd(box + ci + sz + 1, round_small(w[5]));
-    atomicAdd(box + ci + sz + sy, round_small(w[6]));
-    atomicAdd(box + ci + sz + sy + 1, round_small(w[7]));
+// Add the 8 corner weights (scaled to the CTA's fixed point and biased by
+// kMagic, so each is an integer-valued float) of the cell whose corner 000 is
+// box[ci], then reset them to the bias.
+__device__ __forceinline__ void corner_flush8(int* box, int ci, int sy, int sz, float* w) {
+    atomicAdd(box + ci, __float_as_int(w[0]) - kMagicBits);
+    atomicAdd(box + ci + 1, __float_as_int(w[1]) - kMagicBits);
+    atomicAdd(box + ci + sy, __float_as_int(w[2]) - kMagicBits);
+    atomicAdd(box + ci + sy + 1, __float_as_int(w[3]) - kMagicBits);
+    atomicAdd(box + ci + sz, __float_as_int(w[4]) - kMagicBits);
+    atomicAdd(box + ci + sz + 1, __float_as_int(w[5]) - kMagicBits);
+    atomicAdd(box + ci + sz + sy, __float_as_int(w[6]) - kMagicBits);
+    atomicAdd(box + ci + sz + sy + 1, __float_as_int(w[7]) - kMagicBits);
 #pragma unroll
-    for (int c = 0; c < 8; c++) w[c] = 0.0f;
+    for (int c = 0; c < 8; c++) w[c] = kMagic;
 }
 
 // w += sc * (trilinear corner weights of fractions f)
@@ -532,9 +543,9 @@ __global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, i
         const bool act = chunk_begin(bs, sel, r, live, M0, j0, j1, ib, fb);
         __syncthreads();
         const Box bx = read_box(bs, sel);
-        if (bx.vol > 0 && bx.vol <= kBox) {
+        if (bx.vol > 0 && bx.fits) {
             if (act) {
-                const int sy = bx.bx, sz = bx.bx * bx.by;
+                const int sy = kPitch, sz = kPitch * bx.by;
                 const float syf = (float)sy, szf = (float)sz;
                 const float ox = (float)(ib[0] - bx.lx) + fb[0], oy = (float)(ib[1] - bx.ly) + fb[1],
                             oz = (float)(ib[2] - bx.lz) + fb[2];
@@ -543,12 +554,14 @@ __global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, i
                 // weights when it leaves the cell (consecutive samples in one
                 // cell are merged in registers); lanes of one phase group start
                 // 4 samples (2 voxels) after the previous group so a warp's
-                // simultaneous atomics mostly land on different voxels
+                // simultaneous atomics mostly land on different voxels.  The
+                // register weights carry the bias kMagic, so each holds an
+                // exactly rounded integer and converts with one integer subtract.
                 const int phase = threadIdx.x & 7;
                 int ci = -1;
                 float w[8];
 #pragma unroll
-                for (int c = 0; c < 8; c++) w[c] = 0.0f;
+                for (int c = 0; c < 8; c++) w[c] = kMagic;
                 for (int k = 0; k < kChunk; k++) {
                     const int j = (k + 4 * phase) & (kChunk - 1);
                     const bool on = j >= j0 && j <= j1;
@@ -559,27 +572,32 @@ __global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, i
                     const float flz = fminf(fmaxf(floorf(uz), 0.0f), mz);
                     const int idx = on ? (int)fmaf(flz, szf, fmaf(fly, syf, flx)) : ci;
                     if (idx != ci) {
-                        if (ci >= 0) corner_add8(box, ci, sy, sz, w);
+                        if (ci >= 0) corner_flush8(box, ci, sy, sz, w);
                         ci = idx;
                     }
                     if (on) win_add8(w, ux - flx, uy - fly, uz - flz, gsb);
                 }
-                if (ci >= 0) corner_add8(box, ci, sy, sz, w);
+                if (ci >= 0) corner_flush8(box, ci, sy, sz, w);
             }
             __syncthreads();
-            // flush the box: one 64-bit atomic per touched in-grid voxel, and re-zero it
-            const int rows = bx.by * bx.bz;
-            for (int row = warp; row < rows; row += kRay / 32) {
-                const int y = bx.ly + row % bx.by, z = bx.lz + row / bx.by;
-                for (int x0 = lane; x0 < bx.bx; x0 += 32) {
-                    const int i = row * bx.bx + x0;
-                    const int v = box[i];
-                    if (v == 0) continue;
-                    box[i] = 0;
-                    const int x = bx.lx + x0;
-                    if ((unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz)
-                        atomicAdd(A + ((int64_t)z * g.ny + y) * g.nx + x,
-                                  (unsigned long long)((long long)v * (1ll << shift)));
+            // flush the box: lane = x, one warp per (y, z) row; one 64-bit atomic
+            // per touched in-grid voxel, and re-zero it
+            {
+                const int x = bx.lx + lane;
+                const bool xin = lane < bx.bx && (unsigned)x < (unsigned)g.nx;
+                for (int zz = 0; zz < bx.bz; zz++) {
+                    const int z = bx.lz + zz;
+                    for (int yy = warp; yy < bx.by; yy += kRay / 32) {
+                        const int i = (zz * bx.by + yy) * kPitch + lane;
+                        if (lane >= bx.bx) continue;
+                        const int v = box[i];
+                        if (v == 0) continue;
+                        box[i] = 0;
+                        const int y = bx.ly + yy;
+                        if (xin && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz)
+                            atomicAdd(A + ((int64_t)z * g.ny + y) * g.nx + x,
+                                      (unsigned long long)((long long)v * (1ll << shift)));
+                    }
                 }
             }
         } else if (act) {

@@ -15,11 +15,13 @@
 // touches form a small box (about 16x16x7 at the paper's geometry).
 //  - Forward: the box is staged in shared memory with coalesced loads (zero
 //    outside the grid), and the 8-corner trilinear gathers read shared memory.
-//  - Adjoint: samples accumulate into a shared-memory box in 32-bit fixed point
-//    (per-CTA scale), each ray first merging consecutive samples in a sliding
-//    2x2x2 corner window; the box is then flushed with one 64-bit fixed-point
-//    atomic per touched voxel (global scale 2^k from a provable bound).  Integer
-//    sums are order independent, so the result is bit-reproducible.
+//  - Adjoint: every sample adds its 8 trilinear corner weights into a
+//    shared-memory box in 32-bit fixed point (per-CTA scale); a warp's lanes
+//    take pixels 8 apart and start their chunk at staggered samples, so its
+//    simultaneous atomics land on different voxels.  The box is then flushed
+//    with one 64-bit fixed-point atomic per touched voxel (global scale 2^k
+//    from a provable bound).  Integer sums are order independent, so the
+//    result is bit-reproducible.
 // A chunk whose box does not fit in shared memory falls back to direct
 // (bounds-checked) global gathers or atomics.
 #include <climits>
@@ -438,32 +440,6 @@ __device__ __forceinline__ void win_add(Window& W, float fx, float fy, float fz)
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: floats in [2^23, 2^24) are integers
 constexpr int kMagicBits = 0x4b400000;
 
-// Add the 8 corner weights (scaled to the CTA's fixed point and biased by
-// kMagic, so each is an integer-valued float) of the cell whose corner 000 is
-// box[ci], then reset them to the bias.
-__device__ __forceinline__ void corner_flush8(int* box, int ci, int sy, int sz, float* w) {
-    atomicAdd(box + ci, __float_as_int(w[0]) - kMagicBits);
-    atomicAdd(box + ci + 1, __float_as_int(w[1]) - kMagicBits);
-    atomicAdd(box + ci + sy, __float_as_int(w[2]) - kMagicBits);
-    atomicAdd(box + ci + sy + 1, __float_as_int(w[3]) - kMagicBits);
-    atomicAdd(box + ci + sz, __float_as_int(w[4]) - kMagicBits);
-    atomicAdd(box + ci + sz + 1, __float_as_int(w[5]) - kMagicBits);
-    atomicAdd(box + ci + sz + sy, __float_as_int(w[6]) - kMagicBits);
-    atomicAdd(box + ci + sz + sy + 1, __float_as_int(w[7]) - kMagicBits);
-#pragma unroll
-    for (int c = 0; c < 8; c++) w[c] = kMagic;
-}
-
-// w += sc * (trilinear corner weights of fractions f)
-__device__ __forceinline__ void win_add8(float* w, float fx, float fy, float fz, float sc) {
-    const float ex = 1.0f - fx, ey = 1.0f - fy, ez = (1.0f - fz) * sc, fzs = fz * sc;
-    const float a0 = ey * ez, a1 = fy * ez, a2 = ey * fzs, a3 = fy * fzs;
-    w[0] = fmaf(ex, a0, w[0]); w[1] = fmaf(fx, a0, w[1]);
-    w[2] = fmaf(ex, a1, w[2]); w[3] = fmaf(fx, a1, w[3]);
-    w[4] = fmaf(ex, a2, w[4]); w[5] = fmaf(fx, a2, w[5]);
-    w[6] = fmaf(ex, a3, w[6]); w[7] = fmaf(fx, a3, w[7]);
-}
-
 // 2^k so that a bound b < 2^(bits) after scaling.
 __device__ __forceinline__ int exp_for(float bound, int bits) {
     if (!(bound > 0.0f) || !isfinite(bound)) return 0;
@@ -550,34 +526,36 @@ __global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, i
                 const float ox = (float)(ib[0] - bx.lx) + fb[0], oy = (float)(ib[1] - bx.ly) + fb[1],
                             oz = (float)(ib[2] - bx.lz) + fb[2];
                 const float mx = (float)(bx.bx - 2), my = (float)(bx.by - 2), mz = (float)(bx.bz - 2);
-                // convergent scatter: every lane adds its current cell's 8 corner
-                // weights when it leaves the cell (consecutive samples in one
-                // cell are merged in registers); lanes of one phase group start
-                // 4 samples (2 voxels) after the previous group so a warp's
-                // simultaneous atomics mostly land on different voxels.  The
-                // register weights carry the bias kMagic, so each holds an
-                // exactly rounded integer and converts with one integer subtract.
+                // every sample adds its 8 scaled corner weights to the box; the
+                // weights are formed with the bias kMagic, so each rounds to an
+                // integer-valued float and converts with one integer subtract.
+                // Lanes of one phase group start 4 samples (2 voxels) after the
+                // previous group, so a warp's simultaneous atomics land on
+                // different voxels (and mostly different banks).
                 const int phase = threadIdx.x & 7;
-                int ci = -1;
-                float w[8];
-#pragma unroll
-                for (int c = 0; c < 8; c++) w[c] = kMagic;
                 for (int k = 0; k < kChunk; k++) {
                     const int j = (k + 4 * phase) & (kChunk - 1);
-                    const bool on = j >= j0 && j <= j1;
+                    if (j < j0 || j > j1) continue;
                     const float jf = (float)j;
                     const float ux = fmaf(jf, r.dh[0], ox), uy = fmaf(jf, r.dh[1], oy), uz = fmaf(jf, r.dh[2], oz);
                     const float flx = fminf(fmaxf(floorf(ux), 0.0f), mx);
                     const float fly = fminf(fmaxf(floorf(uy), 0.0f), my);
                     const float flz = fminf(fmaxf(floorf(uz), 0.0f), mz);
-                    const int idx = on ? (int)fmaf(flz, szf, fmaf(fly, syf, flx)) : ci;
-                    if (idx != ci) {
-                        if (ci >= 0) corner_flush8(box, ci, sy, sz, w);
-                        ci = idx;
-                    }
-                    if (on) win_add8(w, ux - flx, uy - fly, uz - flz, gsb);
+                    const int idx = (int)fmaf(flz, szf, fmaf(fly, syf, flx));
+                    const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
+                    const float ex = 1.0f - fx, ey = 1.0f - fy, ez = (1.0f - fz) * gsb, fzs = fz * gsb;
+                    const float a0 = ey * ez, a1 = fy * ez, a2 = ey * fzs, a3 = fy * fzs;
+                    int* q = box + idx;
+                    int* q2 = q + sz;
+                    atomicAdd(q, __float_as_int(fmaf(ex, a0, kMagic)) - kMagicBits);
+                    atomicAdd(q + 1, __float_as_int(fmaf(fx, a0, kMagic)) - kMagicBits);
+                    atomicAdd(q + kPitch, __float_as_int(fmaf(ex, a1, kMagic)) - kMagicBits);
+                    atomicAdd(q + kPitch + 1, __float_as_int(fmaf(fx, a1, kMagic)) - kMagicBits);
+                    atomicAdd(q2, __float_as_int(fmaf(ex, a2, kMagic)) - kMagicBits);
+                    atomicAdd(q2 + 1, __float_as_int(fmaf(fx, a2, kMagic)) - kMagicBits);
+                    atomicAdd(q2 + kPitch, __float_as_int(fmaf(ex, a3, kMagic)) - kMagicBits);
+                    atomicAdd(q2 + kPitch + 1, __float_as_int(fmaf(fx, a3, kMagic)) - kMagicBits);
                 }
-                if (ci >= 0) corner_flush8(box, ci, sy, sz, w);
             }
             __syncthreads();
             // flush the box: lane = x, one warp per (y, z) row; one 64-bit atomic

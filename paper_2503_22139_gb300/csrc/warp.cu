@@ -147,13 +147,13 @@ __global__ void __launch_bounds__(kThreads) k_combine_bwd_coeff(GridD g, int L, 
     }
 }
 
-// Sum `nb` block partials per output in index order.
+// Sum `nb` block partials per output in index order (double accumulator).
 __global__ void k_reduce_partials(const float* part, int64_t nout, int nb, float* out, int accumulate) {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= nout) return;
-    float r = 0.f;
-    for (int b = 0; b < nb; b++) r += part[o * nb + b];
-    out[o] = accumulate ? out[o] + r : r;
+    double r = 0.0;
+    for (int b = 0; b < nb; b++) r += (double)part[o * nb + b];
+    out[o] = accumulate ? out[o] + (float)r : (float)r;
 }
 
 // --------------------------------------------------------------- warp
@@ -558,14 +558,21 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
     }
 }
 
-// One CTA per output: strided fixed-order partial sums, then a fixed tree.
+// One CTA per output: strided fixed-order partial sums, then a fixed tree,
+// in double (the tile partials of a coefficient gradient cancel heavily).
 __global__ void __launch_bounds__(256) k_reduce_partials_wide(const float* part, int nb, float* out, int accumulate) {
-    __shared__ float red[8];
+    __shared__ double red[8];
     const int64_t o = blockIdx.x;
-    float r = 0.f;
-    for (int b = threadIdx.x; b < nb; b += 256) r += part[o * nb + b];
-    const float tot = block_sum<256>(r, red);
-    if (threadIdx.x == 0) out[o] = accumulate ? out[o] + tot : tot;
+    double r = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) r += (double)part[o * nb + b];
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 8; i++) t += red[i];
+        out[o] = accumulate ? out[o] + (float)t : (float)t;
+    }
 }
 
 template <typename T, int LL>

@@ -403,6 +403,27 @@ def run_native(a):
     launches = step.launches_per_step * a.steps
     variants = {}
     if not a.no_variants:
+        from paper_2503_22139_gb300.pipeline import GraphedStep
+        gstep = GraphedStep(step, *batch(0))
+        for k in range(2):
+            gstep.run(*batch(k))
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for k in range(a.steps):
+            gstep.run(*batch(a.warmup + k))
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tg = g0.elapsed_time(g1) / 1e3
+        if world > 1:
+            tt = torch.tensor([tg], device="cuda")
+            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+            tg = float(tt.item())
+        variants[f"graph_replay_{a.dtype}"] = round(B * a.steps * world / tg, 3)
+        del gstep
         from paper_2503_22139_gb300.pipeline import PlainPerProjection
         main_dt = a.dtype
         del step

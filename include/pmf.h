@@ -225,6 +225,48 @@ pmf_status conebeam_project_backward(const pmf_grid* grid, const pmf_detector* d
                                      int64_t vol_stride, int accumulate, void* ws, size_t ws_bytes,
                                      pmf_stream stream);
 
+/* ------------------------------------- batched, uneven projector launches */
+
+/* One volume's share of a batched launch: its grid, detector and P views
+ * (device pmf_view[P]), its volume(s) (`vol`, stride as for conebeam_project)
+ * and its projections (device fp32 [P][nv][nu]). */
+typedef struct {
+    pmf_grid grid;
+    pmf_detector det;
+    int32_t P;
+    const pmf_view* views;
+    const void* vol;
+    int64_t vol_stride;
+    float* proj;
+} pmf_project_item;
+
+/* conebeam_project for up to 16 volumes of different sizes and view counts in
+ * one persistent launch (CTAs walk every item's (view, 16x16 tile) work
+ * round-robin).  Every item uses `dtype`.  Results equal per-item
+ * conebeam_project calls bit for bit.  Host-side items may be freed on return. */
+pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pmf_dtype dtype, pmf_stream stream);
+
+/* One volume's share of a batched adjoint: d_proj (device fp32 [P][nv][nu])
+ * and d_vol (device fp32, [P][N] with vol_stride = N or [N] with 0). */
+typedef struct {
+    pmf_grid grid;
+    pmf_detector det;
+    int32_t P;
+    const pmf_view* views;
+    const float* d_proj;
+    float* d_vol;
+    int64_t vol_stride;
+} pmf_backproject_item;
+
+pmf_status conebeam_project_backward_batched_workspace(int32_t n, const pmf_backproject_item* items, size_t* bytes);
+
+/* conebeam_project_backward for up to 16 items in one persistent launch (plus
+ * one batched max-reduction and one batched fixed-point conversion); each
+ * item keeps its own fixed-point scale, so results equal per-item calls bit
+ * for bit. */
+pmf_status conebeam_project_backward_batched(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
+                                             size_t ws_bytes, pmf_stream stream);
+
 /* -------------------------------------------------------- loss (Eq. 10/12) */
 
 pmf_status projection_loss_workspace(int64_t count, size_t* bytes);

@@ -33,6 +33,16 @@ class PmfGaussians(ct.Structure):
                 ("mean", ct.c_void_p), ("scale", ct.c_void_p), ("quat", ct.c_void_p), ("value", ct.c_void_p)]
 
 
+class PmfProjectItem(ct.Structure):
+    _fields_ = [("grid", PmfGrid), ("det", PmfDetector), ("P", ct.c_int32), ("views", ct.c_void_p),
+                ("vol", ct.c_void_p), ("vol_stride", ct.c_int64), ("proj", ct.c_void_p)]
+
+
+class PmfBackprojectItem(ct.Structure):
+    _fields_ = [("grid", PmfGrid), ("det", PmfDetector), ("P", ct.c_int32), ("views", ct.c_void_p),
+                ("d_proj", ct.c_void_p), ("d_vol", ct.c_void_p), ("vol_stride", ct.c_int64)]
+
+
 PMF_OK = 0
 STATUS = {0: "PMF_OK", -1: "PMF_EINVAL", -2: "PMF_ECUDA", -3: "PMF_EWORKSPACE", -4: "PMF_ETIMEOUT",
           -5: "PMF_EUNSUPPORTED"}
@@ -64,6 +74,9 @@ SIGNATURES = {
     "conebeam_project": [_G, ct.POINTER(PmfDetector), _I32, _P, ct.c_int, _P, _I64, _P, _P],
     "conebeam_project_backward_workspace": [_G, _I32, _I64, _SZ],
     "conebeam_project_backward": [_G, ct.POINTER(PmfDetector), _I32, _P, _P, _P, _I64, ct.c_int, _P, ct.c_size_t, _P],
+    "conebeam_project_batched": [_I32, ct.POINTER(PmfProjectItem), ct.c_int, _P],
+    "conebeam_project_backward_batched_workspace": [_I32, ct.POINTER(PmfBackprojectItem), _SZ],
+    "conebeam_project_backward_batched": [_I32, ct.POINTER(PmfBackprojectItem), ct.c_int, _P, ct.c_size_t, _P],
     "projection_loss_workspace": [_I64, _SZ],
     "projection_loss": [_I32, _I32, _I64, _P, _P, _P, _P, _P, ct.c_size_t, _P],
 }

@@ -237,15 +237,14 @@ __device__ __forceinline__ Box read_box(const BoxState& bs, int sel) {
 
 // ----------------------------------------------------------------- forward
 
+// One 16x16 pixel tile of view p: every thread of the CTA calls it.
 template <typename T>
-__global__ void __launch_bounds__(kRay) k_project(GridD g, int nu, int nv, int ntu, float step,
-                                                  const pmf_view* __restrict__ views, const T* __restrict__ vol,
-                                                  int64_t vol_stride, float* __restrict__ proj) {
-    __shared__ float box[kBox];
-    __shared__ BoxState bs;
-    const int p = blockIdx.y;
+__device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int ntu, float step,
+                                             const pmf_view* __restrict__ views, const T* __restrict__ vol,
+                                             int64_t vol_stride, float* __restrict__ proj, int p, int tile,
+                                             float* box, BoxState& bs) {
     int a, b;
-    pixel_of(blockIdx.x, ntu, a, b);
+    pixel_of(tile, ntu, a, b);
     const bool in = a < nu && b < nv;
     Ray r;
     if (in) {
@@ -321,6 +320,15 @@ __global__ void __launch_bounds__(kRay) k_project(GridD g, int nu, int nv, int n
         __syncthreads();
     }
     if (in) proj[((int64_t)p * nv + b) * nu + a] = step * acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRay) k_project(GridD g, int nu, int nv, int ntu, float step,
+                                                  const pmf_view* __restrict__ views, const T* __restrict__ vol,
+                                                  int64_t vol_stride, float* __restrict__ proj) {
+    __shared__ float box[kBox];
+    __shared__ BoxState bs;
+    project_tile<T>(g, nu, nv, ntu, step, views, vol, vol_stride, proj, blockIdx.y, blockIdx.x, box, bs);
 }
 
 __global__ void k_absmax_f(const float* __restrict__ x, int64_t n, unsigned* out) {
@@ -459,18 +467,16 @@ __device__ __forceinline__ void pixel_of_spread(int tile, int ntu, int& a, int& 
     b = tv * 16 + w + 8 * (q >> 1);
 }
 
-__global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, int ntu, float step,
-                                                      const pmf_view* __restrict__ views,
-                                                      const float* __restrict__ dproj, int64_t vol_stride,
-                                                      unsigned long long* __restrict__ acc, const unsigned* maxbits,
-                                                      float bound_mult, float samples_per_voxel) {
-    __shared__ int box[kBox];
-    __shared__ BoxState bs;
-    __shared__ unsigned sgmax;
-    __shared__ float gsum[kRay / 32];
-    const int p = blockIdx.y;
+// One 16x16 pixel tile of view p of the adjoint; box must be all zero on entry
+// and is all zero again on return.
+__device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv, int ntu, float step,
+                                                 const pmf_view* __restrict__ views,
+                                                 const float* __restrict__ dproj, int64_t vol_stride,
+                                                 unsigned long long* __restrict__ acc, const unsigned* maxbits,
+                                                 float bound_mult, float samples_per_voxel, int p, int tile,
+                                                 int* box, BoxState& bs, unsigned& sgmax, float* gsum) {
     int a, b;
-    pixel_of_spread(blockIdx.x, ntu, a, b);
+    pixel_of_spread(tile, ntu, a, b);
     const bool in = a < nu && b < nv;
     const float gy = in ? __ldg(dproj + ((int64_t)p * nv + b) * nu + a) : 0.0f;
     Ray r;
@@ -485,7 +491,6 @@ __global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, i
     // CTA's rays, where S bounds the trilinear weight one ray's samples put in
     // one voxel (a hat function sampled at spacing h sums to at most 1/h + 1).
     if (threadIdx.x == 0) sgmax = 0u;
-    for (int i = threadIdx.x; i < kBox; i += kRay) box[i] = 0;
     __syncthreads();
     {
         float a = live ? fabsf(gy) : 0.0f;
@@ -600,6 +605,20 @@ __global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, i
     }
 }
 
+__global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, int ntu, float step,
+                                                      const pmf_view* __restrict__ views,
+                                                      const float* __restrict__ dproj, int64_t vol_stride,
+                                                      unsigned long long* __restrict__ acc, const unsigned* maxbits,
+                                                      float bound_mult, float samples_per_voxel) {
+    __shared__ int box[kBox];
+    __shared__ BoxState bs;
+    __shared__ unsigned sgmax;
+    __shared__ float gsum[kRay / 32];
+    for (int i = threadIdx.x; i < kBox; i += kRay) box[i] = 0;
+    backproject_tile(g, nu, nv, ntu, step, views, dproj, vol_stride, acc, maxbits, bound_mult, samples_per_voxel,
+                     blockIdx.y, blockIdx.x, box, bs, sgmax, gsum);
+}
+
 __global__ void k_fixed_to_float_f(const unsigned long long* __restrict__ acc, int64_t n, const unsigned* maxbits,
                                    float bound_mult, float* out, int accumulate) {
     const float bound = __uint_as_float(*maxbits) * bound_mult;
@@ -609,6 +628,94 @@ __global__ void k_fixed_to_float_f(const unsigned long long* __restrict__ acc, i
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const float r = bad ? __int_as_float(0x7fc00000) : from_fixed(acc[t], inv);
         out[t] = accumulate ? out[t] + r : r;
+    }
+}
+
+// ------------------------------------------------- batched (uneven) launches
+//
+// Several volumes -- different grids, detectors and view counts -- in one
+// persistent launch: work item w is tile (w - begin_i) % ntiles_i of view
+// (w - begin_i) / ntiles_i of item i, and each CTA walks the work items
+// round-robin.  A tile's arithmetic is the single-volume kernel's, so the
+// results equal per-volume launches bit for bit.
+
+constexpr int kMaxItems = 16;
+
+struct ProjItem {
+    GridD g;
+    int nu, nv, ntu, ntiles, P;
+    float step, bound_mult, spv;
+    const pmf_view* views;
+    const void* vol;
+    int64_t vol_stride;
+    float* proj;
+    const float* dproj;
+    unsigned long long* acc;
+    unsigned* maxbits;
+    float* dvol;
+    int64_t cells, nq, begin;
+};
+
+struct ProjBatch {
+    int n;
+    int64_t total;
+    ProjItem it[kMaxItems];
+};
+
+__device__ __forceinline__ int find_item(const ProjBatch& B, int64_t w) {
+    int i = 0;
+    while (i + 1 < B.n && w >= B.it[i + 1].begin) i++;
+    return i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRay) k_project_batched(const __grid_constant__ ProjBatch B) {
+    __shared__ float box[kBox];
+    __shared__ BoxState bs;
+    for (int64_t w = blockIdx.x; w < B.total; w += gridDim.x) {
+        const ProjItem& it = B.it[find_item(B, w)];
+        const int64_t local = w - it.begin;
+        project_tile<T>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, (const T*)it.vol, it.vol_stride, it.proj,
+                        (int)(local / it.ntiles), (int)(local % it.ntiles), box, bs);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kRay) k_backproject_batched(const __grid_constant__ ProjBatch B) {
+    __shared__ int box[kBox];
+    __shared__ BoxState bs;
+    __shared__ unsigned sgmax;
+    __shared__ float gsum[kRay / 32];
+    for (int i = threadIdx.x; i < kBox; i += kRay) box[i] = 0;
+    for (int64_t w = blockIdx.x; w < B.total; w += gridDim.x) {
+        const ProjItem& it = B.it[find_item(B, w)];
+        const int64_t local = w - it.begin;
+        backproject_tile(it.g, it.nu, it.nv, it.ntu, it.step, it.views, it.dproj, it.vol_stride, it.acc, it.maxbits,
+                         it.bound_mult, it.spv, (int)(local / it.ntiles), (int)(local % it.ntiles), box, bs, sgmax,
+                         gsum);
+        __syncthreads();
+    }
+}
+
+// blockIdx.y = item
+__global__ void k_absmax_batched(const __grid_constant__ ProjBatch B) {
+    const ProjItem& it = B.it[blockIdx.y];
+    float m = 0.f;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < it.nq; t += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(__ldg(it.dproj + t)));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(it.maxbits, m);
+}
+
+__global__ void k_fixed_to_float_batched(const __grid_constant__ ProjBatch B, int accumulate) {
+    const ProjItem& it = B.it[blockIdx.y];
+    const float bound = __uint_as_float(*it.maxbits) * it.bound_mult;
+    const int kexp = fixed_exponent(bound);
+    const float inv = ldexpf(1.0f, -kexp);
+    const bool bad = !isfinite(bound);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < it.cells; t += (int64_t)gridDim.x * blockDim.x) {
+        const float r = bad ? __int_as_float(0x7fc00000) : from_fixed(it.acc[t], inv);
+        it.dvol[t] = accumulate ? it.dvol[t] + r : r;
     }
 }
 
@@ -737,6 +844,115 @@ pmf_status conebeam_project_backward(const pmf_grid* grid, const pmf_detector* d
     k_fixed_to_float_f<<<(unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks), 256, 0, s>>>(
         acc, cells, maxbits, bound_mult, d_vol, accumulate);
     return check_launch("conebeam_project_backward");
+}
+
+static pmf_status fill_item(const pmf_project_item& in, pmf_dtype dtype, int64_t begin, ProjItem& it) {
+    pmf_status st = check_proj(&in.grid, &in.det, in.P, in.views);
+    if (st != PMF_OK) return st;
+    (void)dtype;
+    PMF_REQUIRE(in.vol_stride >= 0, "vol_stride must be >= 0");
+    it = ProjItem{};
+    it.g = make_grid(&in.grid);
+    it.nu = in.det.nu; it.nv = in.det.nv;
+    it.ntu = (in.det.nu + 15) / 16;
+    it.ntiles = it.ntu * ((in.det.nv + 15) / 16);
+    it.P = in.P;
+    it.step = in.det.step_mm;
+    it.views = in.views;
+    it.vol_stride = in.vol_stride;
+    it.nq = (int64_t)in.det.nu * in.det.nv * in.P;
+    it.begin = begin;
+    return PMF_OK;
+}
+
+static unsigned persistent_ctas(int64_t total) {
+    const int64_t cap = 4 * 152;  // 4 resident CTAs per SM at 256 threads and <= 64 registers
+    return (unsigned)(total < cap ? (total > 0 ? total : 1) : cap);
+}
+
+pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pmf_dtype dtype, pmf_stream stream) {
+    PMF_REQUIRE(n >= 0 && n <= kMaxItems, "n must be in [0, %d]", kMaxItems);
+    PMF_REQUIRE(n == 0 || items != nullptr, "items is null");
+    pmf_status st = validate_dtype(dtype);
+    if (st != PMF_OK) return st;
+    ProjBatch B{};
+    B.n = n;
+    int64_t total = 0;
+    for (int i = 0; i < n; i++) {
+        if ((st = fill_item(items[i], dtype, total, B.it[i])) != PMF_OK) return st;
+        PMF_REQUIRE(items[i].P == 0 || (items[i].vol && items[i].proj), "item %d: null pointer", i);
+        B.it[i].vol = items[i].vol;
+        B.it[i].proj = items[i].proj;
+        total += (int64_t)B.it[i].ntiles * items[i].P;
+    }
+    B.total = total;
+    if (total == 0) return PMF_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    PMF_DISPATCH_DTYPE(dtype, T, k_project_batched<T><<<persistent_ctas(total), kRay, 0, s>>>(B));
+    return check_launch("conebeam_project_batched");
+}
+
+static size_t bp_item_bytes(const pmf_backproject_item& it) {
+    const int64_t n = (int64_t)it.grid.nx * it.grid.ny * it.grid.nz;
+    const int64_t cells = it.vol_stride ? (int64_t)(it.P > 0 ? it.P - 1 : 0) * it.vol_stride + n : n;
+    return align_up(256) + align_up(sizeof(unsigned long long) * (size_t)cells);
+}
+
+pmf_status conebeam_project_backward_batched_workspace(int32_t n, const pmf_backproject_item* items, size_t* bytes) {
+    PMF_REQUIRE(bytes != nullptr && n >= 0 && n <= kMaxItems && (n == 0 || items != nullptr), "bad arguments");
+    size_t tot = 0;
+    for (int i = 0; i < n; i++) {
+        pmf_status st = validate_grid(&items[i].grid);
+        if (st != PMF_OK) return st;
+        tot += bp_item_bytes(items[i]);
+    }
+    *bytes = tot;
+    return PMF_OK;
+}
+
+pmf_status conebeam_project_backward_batched(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
+                                             size_t ws_bytes, pmf_stream stream) {
+    size_t need = 0;
+    pmf_status st = conebeam_project_backward_batched_workspace(n, items, &need);
+    if (st != PMF_OK) return st;
+    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
+    ProjBatch B{};
+    B.n = n;
+    int64_t total = 0, maxq = 0, maxcells = 0;
+    char* cur = (char*)ws;
+    for (int i = 0; i < n; i++) {
+        const pmf_backproject_item& in = items[i];
+        pmf_project_item tmp{in.grid, in.det, in.P, in.views, nullptr, in.vol_stride, nullptr};
+        if ((st = fill_item(tmp, PMF_F32, total, B.it[i])) != PMF_OK) return st;
+        PMF_REQUIRE(in.d_vol != nullptr && (in.P == 0 || in.d_proj != nullptr), "item %d: null pointer", i);
+        ProjItem& it = B.it[i];
+        const int64_t Q = (int64_t)in.det.nu * in.det.nv;
+        const double rays = (double)Q * (in.vol_stride ? 1.0 : (double)in.P);
+        it.bound_mult = (float)((double)in.det.step_mm * rays * (double)max_samples_per_voxel(&in.grid, in.det.step_mm));
+        it.spv = chunk_samples_per_voxel(&in.grid, in.det.step_mm);
+        it.dproj = in.d_proj;
+        it.dvol = in.d_vol;
+        it.maxbits = (unsigned*)cur;
+        it.acc = (unsigned long long*)(cur + align_up(256));
+        it.cells = in.vol_stride ? (int64_t)(in.P > 0 ? in.P - 1 : 0) * in.vol_stride + it.g.n : it.g.n;
+        cur += bp_item_bytes(in);
+        total += (int64_t)it.ntiles * in.P;
+        maxq = it.nq > maxq ? it.nq : maxq;
+        maxcells = it.cells > maxcells ? it.cells : maxcells;
+    }
+    B.total = total;
+    if (n == 0) return PMF_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(ws, 0, need, s);
+    if (maxq > 0) {
+        const int64_t nb = (maxq + 255) / 256;
+        k_absmax_batched<<<dim3((unsigned)(nb < 1024 ? nb : 1024), (unsigned)n), 256, 0, s>>>(B);
+    }
+    if (total > 0) k_backproject_batched<<<persistent_ctas(total), kRay, 0, s>>>(B);
+    const int64_t nc = (maxcells + 255) / 256;
+    k_fixed_to_float_batched<<<dim3((unsigned)(nc < 4 * kStreamBlocks ? nc : 4 * kStreamBlocks), (unsigned)n), 256, 0, s>>>(
+        B, accumulate);
+    return check_launch("conebeam_project_backward_batched");
 }
 
 pmf_status projection_loss_workspace(int64_t count, size_t* bytes) {

@@ -308,6 +308,61 @@ def conebeam_project_backward(grid, det, views, d_proj, shared: bool = False, ac
     return out
 
 
+def conebeam_project_batched(items, out=None):
+    """One persistent launch over several volumes.  items: sequence of
+    (grid, det, views [P,12] f64, vol, shared) tuples; returns the list of
+    projections [P, nv, nu] (fp32), or fills `out` (a list of tensors)."""
+    L = _lib.load()
+    arr = (_lib.PmfProjectItem * max(1, len(items)))()
+    outs, keep, dt = [], [], None
+    for i, (grid, det, views, vol, shared) in enumerate(items):
+        vol = _need(vol, "vol")
+        views = _need(views, "views", torch.float64)
+        dt = vol.dtype if dt is None else dt
+        if vol.dtype != dt:
+            raise ValueError("all volumes of a batched launch share one dtype")
+        d = _det(det)
+        _, n = _shape(grid)
+        P = int(views.shape[0])
+        o = out[i] if out is not None else torch.empty((P, d.nv, d.nu), dtype=torch.float32, device=vol.device)
+        arr[i] = _lib.PmfProjectItem(_grid(grid), d, P, views.data_ptr(), vol.data_ptr(), 0 if shared else n,
+                                     o.data_ptr())
+        outs.append(o)
+        keep += [vol, views]
+    check(L.conebeam_project_batched(len(items), arr, _DT[dt or torch.float32], _stream()),
+          "conebeam_project_batched")
+    return outs
+
+
+def conebeam_project_backward_batched(items, accumulate=False, out=None, ws=None):
+    """items: sequence of (grid, det, views [P,12] f64, d_proj [P,nv,nu], shared);
+    returns the list of volume gradients."""
+    L = _lib.load()
+    arr = (_lib.PmfBackprojectItem * max(1, len(items)))()
+    outs, keep, dev = [], [], None
+    for i, (grid, det, views, d_proj, shared) in enumerate(items):
+        views = _need(views, "views", torch.float64)
+        d_proj = _need(d_proj, "d_proj", torch.float32)
+        dev = d_proj.device
+        d = _det(det)
+        shape, n = _shape(grid)
+        P = int(views.shape[0])
+        o = out[i] if out is not None else torch.empty(shape if shared else (P,) + shape, dtype=torch.float32,
+                                                         device=dev)
+        arr[i] = _lib.PmfBackprojectItem(_grid(grid), d, P, views.data_ptr(), d_proj.data_ptr(), o.data_ptr(),
+                                         0 if shared else n)
+        outs.append(o)
+        keep += [views, d_proj]
+    if ws is None:
+        nb = ct.c_size_t(0)
+        check(L.conebeam_project_backward_batched_workspace(len(items), arr, ct.byref(nb)),
+              "conebeam_project_backward_batched_workspace")
+        ws = _ws(nb.value, dev if dev is not None else "cuda")
+    check(L.conebeam_project_backward_batched(len(items), arr, int(accumulate), _p(ws), ws.numel(), _stream()),
+          "conebeam_project_backward_batched")
+    return outs
+
+
 def projection_loss(kind: int, pred: torch.Tensor, meas: torch.Tensor, with_grad: bool = True, ws=None):
     """kind 1 = L1 (Eq. 10/12), 2 = L2 (Eq. 1); mean over all pixels -> (loss[1], d_pred)."""
     L = _lib.load()

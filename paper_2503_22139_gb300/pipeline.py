@@ -137,3 +137,36 @@ class PlainPerProjection(ForwardAdjoint):
         for l, m in enumerate(self.mbc):
             ops.gs_voxelize_backward(g, m, gE[l], grads=self.g_mbc[l], ws=self.vb_ws[1 + l])
         return loss
+
+
+class GraphedStep:
+    """A ForwardAdjoint step captured once into a CUDA graph and replayed.
+    Every call into the library only enqueues kernels and memsets on the
+    current stream, so the whole step (all stages, both directions) is one
+    graph launch; each replay reads the batch from static input buffers."""
+
+    def __init__(self, step: ForwardAdjoint, views: torch.Tensor, coeff: torch.Tensor, meas: torch.Tensor,
+                 warmup: int = 2):
+        self.step = step
+        self.views, self.coeff, self.meas = views.clone(), coeff.clone(), meas.clone()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                step.run(self.views, self.coeff, self.meas)
+        torch.cuda.current_stream().wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.loss = step.run(self.views, self.coeff, self.meas)
+
+    @property
+    def launches_per_step(self) -> int:
+        return self.step.launches_per_step
+
+    def run(self, views: torch.Tensor, coeff: torch.Tensor, meas: torch.Tensor):
+        if views.data_ptr() != self.views.data_ptr():
+            self.views.copy_(views, non_blocking=True)
+            self.coeff.copy_(coeff, non_blocking=True)
+            self.meas.copy_(meas, non_blocking=True)
+        self.graph.replay()
+        return self.loss

@@ -14,7 +14,8 @@
  *  - Pointers named d_* or marked "device" are CUDA device pointers; host
  *    structs (pmf_grid, pmf_detector, pmf_gaussians) are read on the host
  *    during the call and may be freed on return.  The caller owns every buffer;
- *    the library never allocates or frees device memory.
+ *    the library never allocates or frees device memory, except in
+ *    pmf_plan_create / pmf_plan_destroy (a plan owns its intermediate tensors).
  *  - All device work is enqueued on `stream` (a cudaStream_t; NULL = legacy
  *    default stream) and is asynchronous: inputs must stay alive and unchanged
  *    until the stream reaches the work.  No call synchronizes.
@@ -277,6 +278,146 @@ pmf_status projection_loss_workspace(int64_t count, size_t* bytes);
  * 2 (pred - meas)/(PQ).  Fixed-order reduction. */
 pmf_status projection_loss(int32_t kind, int32_t P, int64_t Q, const float* pred, const float* meas,
                            float* loss, float* d_pred, void* ws, size_t ws_bytes, pmf_stream stream);
+
+/* ------------------------------------------------------------ host helpers */
+
+/* The circular scan of Sec. 2.3.3 / Table I as pmf_view records: view p has
+ * theta = 2 pi p / P, source SAD (cos theta, sin theta, 0), detector centre
+ * -(SDD - SAD)(cos theta, sin theta, 0), u step du_mm (-sin theta, cos theta, 0)
+ * and v step dv_mm (0, 0, 1) (flat detector opposite the source, no offset).
+ * Host-only: writes P records to host_out (caller-owned host memory).
+ * nu and nv are only checked (> 0): pixel positions use them at projection time. */
+pmf_status pmf_circular_views(int32_t P, double sad_mm, double sdd_mm, double du_mm, double dv_mm, int32_t nu,
+                              int32_t nv, pmf_view* host_out);
+
+/* Operation codes of pmf_workspace_size, and the arguments each one reads. */
+typedef enum {
+    PMF_OP_VOXELIZE = 1,              /* grid, n, pair_capacity  (= gs_voxelize_workspace) */
+    PMF_OP_VOXELIZE_BACKWARD = 2,     /* grid, n, channels       (= gs_voxelize_backward_workspace) */
+    PMF_OP_COMBINE_BACKWARD = 3,      /* grid, L, P              (= mbc_combine_backward_workspace) */
+    PMF_OP_WARP_BACKWARD = 4,         /* grid, P                 (= warp_volume_backward_workspace) */
+    PMF_OP_WARP_COMBINE_BACKWARD = 5, /* grid, L, P              (= warp_combine_backward_workspace) */
+    PMF_OP_PROJECT_BACKWARD = 6,      /* grid, P, vol_stride     (= conebeam_project_backward_workspace) */
+    PMF_OP_LOSS = 7                   /* count                   (= projection_loss_workspace) */
+} pmf_op;
+
+typedef struct {
+    pmf_grid grid;
+    int64_t n;             /* Gaussians */
+    int64_t pair_capacity; /* voxelizer (Gaussian, tile) list capacity */
+    int64_t vol_stride;    /* projector adjoint: 0 or N */
+    int64_t count;         /* loss: P * Q */
+    int32_t channels, L, P;
+} pmf_ws_args;
+
+/* One entry point for every *_workspace query: *bytes = the scratch `op`
+ * needs for `args`.  Host-only; PMF_EINVAL for an unknown op. */
+pmf_status pmf_workspace_size(int32_t op, const pmf_ws_args* args, size_t* bytes);
+
+/* ------------------------------------------------------ device diagnostics */
+
+/* Counters the kernels keep on the device (per device, since the library was
+ * loaded or last reset).  The slow paths give the same results, only slower;
+ * PMF_DIAG_NONFINITE marks outputs that are undefined (NaN written). */
+typedef enum {
+    PMF_DIAG_VOXELIZE_LIST_OVERFLOW = 0,   /* voxelizer tiles whose Gaussian list overflowed the
+                                              workspace's pair capacity (scanned every Gaussian instead) */
+    PMF_DIAG_PROJECT_BOX_FALLBACK = 1,     /* projector chunks whose voxel box did not fit shared
+                                              memory (gathered from global memory) */
+    PMF_DIAG_BACKPROJECT_BOX_FALLBACK = 2, /* the same for the back-projector (global 64-bit atomics) */
+    PMF_DIAG_WARP_HALO_EXIT = 3,           /* fused warp-adjoint CTAs where a displacement left the
+                                              4-voxel halo (those corners use global atomics) */
+    PMF_DIAG_NONFINITE = 4,                /* fixed-point scatters or voxelizations whose input
+                                              magnitude was NaN or infinite (outputs set to NaN) */
+    PMF_DIAG_COUNT = 5
+} pmf_diag;
+
+/* Copies the current device's counters to host_out[PMF_DIAG_COUNT] and, with
+ * reset != 0, zeroes them.  Synchronizes the device; not during stream capture. */
+pmf_status pmf_device_counters(uint64_t* host_out, int32_t reset);
+
+/* Synchronizes `stream` and reports what the device saw: PMF_ECUDA (with the
+ * CUDA message) if the stream's work failed, PMF_EINVAL if a non-finite input
+ * reached a fixed-point scatter since the counters were last reset, else PMF_OK.
+ * No kernel of this library waits on another CTA, so there is no timeout flag. */
+pmf_status pmf_device_status(pmf_stream stream);
+
+/* ------------------------------------------------ training-step plans */
+
+#define PMF_MAX_LEVELS 8
+
+/* One forward + adjoint step of Stages 2-3 (Sec. 2.3.2) over a batch of B views:
+ *   V = voxelize(ref), E_l = voxelize(mbc[l]), W = warp_combine(V, E, coeff),
+ *   Y = project(W), loss/dY = projection_loss(Y, meas),
+ *   dW = project^T(dY), (dV, dE, d_coeff) = warp_combine^T(dW),
+ *   d_ref = voxelize^T(dV), d_mbc[l] = voxelize^T(dE_l).
+ * Every pointer below is a caller-owned device pointer that the plan keeps:
+ * it reads the inputs and writes the outputs at every pmf_plan_step, so the
+ * caller refreshes their contents between steps (new views, coefficients,
+ * measurements, updated Gaussian parameters) without re-creating the plan.
+ * The Gaussian counts and everything else are fixed at creation. */
+typedef struct {
+    pmf_grid grid;
+    pmf_detector det;
+    pmf_dtype dtype;        /* storage of V, E, W */
+    int32_t batch;          /* B >= 1 */
+    int32_t loss_kind;      /* 1 = L1 (Eq. 10/12), 2 = L2 (Eq. 1) */
+    int32_t levels;         /* L in [1, PMF_MAX_LEVELS] */
+    pmf_gaussians ref;      /* channels 1 */
+    pmf_gaussians mbc[PMF_MAX_LEVELS]; /* channels 3; first `levels` used */
+    const pmf_view* views;  /* [B] */
+    const float* coeff;     /* [B][L][3] */
+    const float* meas;      /* [B][nv][nu] */
+    float* loss;            /* scalar (output) */
+    float* d_ref[4];        /* d_mean [n][3], d_scale [n][3], d_quat [n][4], d_value [n][1] (outputs) */
+    float* d_mbc[PMF_MAX_LEVELS][4]; /* the same per level, d_value [n][3] */
+    float* d_coeff;         /* [B][L][3] (output) */
+    int32_t use_graph;      /* 1: the first pmf_plan_step captures the step into a CUDA graph on its
+                               stream (which must not be the legacy NULL stream); later steps replay it */
+    const char* tune_cache; /* nullable: file written by pmf_autotune; its entry for this
+                               configuration selects the projector launch forms */
+} pmf_batch_desc;
+
+typedef struct pmf_plan pmf_plan;
+
+/* Device tensors the plan owns (valid until pmf_plan_destroy): V [N], E [L][3][N]
+ * and W [B][N] in the plan's dtype; fp32 Y, dY [B][nv][nu], dW [B][N], dV [N],
+ * dE [L][3][N]. */
+typedef struct {
+    void* V;
+    void* E;
+    void* W;
+    float* Y;
+    float* dY;
+    float* dW;
+    float* dV;
+    float* dE;
+} pmf_plan_tensors;
+
+/* Validates `desc`, allocates the plan's device memory (cudaMalloc: the one
+ * place the library allocates), sizes each voxelizer's pair list from the
+ * current Gaussians (gs_voxelize_count, synchronizing), and reads tune_cache.
+ * *plan is NULL on failure. */
+pmf_status pmf_plan_create(const pmf_batch_desc* desc, pmf_plan** plan);
+
+/* Enqueues one step on `stream` (asynchronous; with use_graph, one graph launch). */
+pmf_status pmf_plan_step(pmf_plan* plan, pmf_stream stream);
+
+pmf_status pmf_plan_tensors_get(const pmf_plan* plan, pmf_plan_tensors* out);
+
+/* Launch forms the plan uses: proj and backproj are 0 for one CTA per (view,
+ * tile), k > 0 for a persistent launch of k CTAs per SM.  Results are
+ * bit-identical for every choice. */
+pmf_status pmf_plan_launch_forms(const pmf_plan* plan, int32_t* proj, int32_t* backproj);
+
+/* Synchronizes the device, frees the plan's memory and graph.  NULL is a no-op. */
+pmf_status pmf_plan_destroy(pmf_plan* plan);
+
+/* Times each launch form of the projector and its adjoint on desc's data
+ * (a temporary plan; several steps, CUDA events) and records the fastest in
+ * `cache_path` under a key made of the device name, SM count, grid,
+ * detector, batch and dtype (other keys in the file are kept).  Synchronizes. */
+pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path);
 
 #ifdef __cplusplus
 }

@@ -8,14 +8,18 @@ in the C-ABI library built from csrc/ (see include/pmf.h); this package is its
 argument-marshalling binding.
 """
 from . import ops  # noqa: F401
+from ._lib import PmfError  # noqa: F401
 from .ops import (  # noqa: F401
-    Gaussians, conebeam_project, conebeam_project_backward, gs_voxelize, gs_voxelize_backward,
-    gs_voxelize_count, mbc_combine, mbc_combine_backward, projection_loss, views_tensor, warp_combine,
-    warp_combine_backward, warp_volume, warp_volume_backward,
+    Gaussians, Plan, autotune, circular_views, conebeam_project, conebeam_project_backward,
+    conebeam_project_backward_batched, conebeam_project_batched, device_counters, device_status, gs_voxelize,
+    gs_voxelize_backward, gs_voxelize_count, mbc_combine, mbc_combine_backward, projection_loss, views_tensor,
+    warp_combine, warp_combine_backward, warp_volume, warp_volume_backward, workspace_size,
 )
 
 __all__ = [
-    "Gaussians", "conebeam_project", "conebeam_project_backward", "gs_voxelize", "gs_voxelize_backward",
-    "gs_voxelize_count", "mbc_combine", "mbc_combine_backward", "projection_loss", "views_tensor",
-    "warp_combine", "warp_combine_backward", "warp_volume", "warp_volume_backward",
+    "Gaussians", "Plan", "PmfError", "autotune", "circular_views", "conebeam_project", "conebeam_project_backward",
+    "conebeam_project_backward_batched", "conebeam_project_batched", "device_counters", "device_status",
+    "gs_voxelize", "gs_voxelize_backward", "gs_voxelize_count", "mbc_combine", "mbc_combine_backward",
+    "projection_loss", "views_tensor", "warp_combine", "warp_combine_backward", "warp_volume",
+    "warp_volume_backward", "workspace_size",
 ]

@@ -43,6 +43,32 @@ class PmfBackprojectItem(ct.Structure):
                 ("d_proj", ct.c_void_p), ("d_vol", ct.c_void_p), ("vol_stride", ct.c_int64)]
 
 
+PMF_MAX_LEVELS = 8
+PMF_DIAG_COUNT = 5
+DIAG_NAMES = ("voxelize_list_overflow", "project_box_fallback", "backproject_box_fallback", "warp_halo_exit",
+              "nonfinite")
+PMF_OPS = {"voxelize": 1, "voxelize_backward": 2, "combine_backward": 3, "warp_backward": 4,
+           "warp_combine_backward": 5, "project_backward": 6, "loss": 7}
+
+
+class PmfWsArgs(ct.Structure):
+    _fields_ = [("grid", PmfGrid), ("n", ct.c_int64), ("pair_capacity", ct.c_int64), ("vol_stride", ct.c_int64),
+                ("count", ct.c_int64), ("channels", ct.c_int32), ("L", ct.c_int32), ("P", ct.c_int32)]
+
+
+class PmfBatchDesc(ct.Structure):
+    _fields_ = [("grid", PmfGrid), ("det", PmfDetector), ("dtype", ct.c_int), ("batch", ct.c_int32),
+                ("loss_kind", ct.c_int32), ("levels", ct.c_int32), ("ref", PmfGaussians),
+                ("mbc", PmfGaussians * PMF_MAX_LEVELS), ("views", ct.c_void_p), ("coeff", ct.c_void_p),
+                ("meas", ct.c_void_p), ("loss", ct.c_void_p), ("d_ref", ct.c_void_p * 4),
+                ("d_mbc", (ct.c_void_p * 4) * PMF_MAX_LEVELS), ("d_coeff", ct.c_void_p), ("use_graph", ct.c_int32),
+                ("tune_cache", ct.c_char_p)]
+
+
+class PmfPlanTensors(ct.Structure):
+    _fields_ = [(n, ct.c_void_p) for n in ("V", "E", "W", "Y", "dY", "dW", "dV", "dE")]
+
+
 PMF_OK = 0
 STATUS = {0: "PMF_OK", -1: "PMF_EINVAL", -2: "PMF_ECUDA", -3: "PMF_EWORKSPACE", -4: "PMF_ETIMEOUT",
           -5: "PMF_EUNSUPPORTED"}
@@ -79,6 +105,16 @@ SIGNATURES = {
     "conebeam_project_backward_batched": [_I32, ct.POINTER(PmfBackprojectItem), ct.c_int, _P, ct.c_size_t, _P],
     "projection_loss_workspace": [_I64, _SZ],
     "projection_loss": [_I32, _I32, _I64, _P, _P, _P, _P, _P, ct.c_size_t, _P],
+    "pmf_circular_views": [_I32, ct.c_double, ct.c_double, ct.c_double, ct.c_double, _I32, _I32, ct.POINTER(PmfView)],
+    "pmf_workspace_size": [_I32, ct.POINTER(PmfWsArgs), _SZ],
+    "pmf_device_counters": [ct.POINTER(ct.c_uint64), _I32],
+    "pmf_device_status": [_P],
+    "pmf_plan_create": [ct.POINTER(PmfBatchDesc), ct.POINTER(ct.c_void_p)],
+    "pmf_plan_step": [_P, _P],
+    "pmf_plan_tensors_get": [_P, ct.POINTER(PmfPlanTensors)],
+    "pmf_plan_launch_forms": [_P, ct.POINTER(_I32), ct.POINTER(_I32)],
+    "pmf_plan_destroy": [_P],
+    "pmf_autotune": [ct.POINTER(PmfBatchDesc), ct.c_char_p],
 }
 
 

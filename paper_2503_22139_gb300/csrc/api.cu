@@ -1,5 +1,7 @@
-// Status strings, thread-local error messages and shared host-side validation
-// for the C ABI declared in include/pmf.h.
+// Status strings, thread-local error messages, shared host-side validation,
+// the workspace-query dispatcher, the circular-scan helper and the device
+// diagnostics for the C ABI declared in include/pmf.h.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 
@@ -65,6 +67,62 @@ const char* pmf_status_string(pmf_status s) {
         case PMF_EUNSUPPORTED: return "unsupported";
     }
     return "unknown status";
+}
+
+pmf_status pmf_circular_views(int32_t P, double sad_mm, double sdd_mm, double du_mm, double dv_mm, int32_t nu,
+                              int32_t nv, pmf_view* host_out) {
+    PMF_REQUIRE(P >= 0 && (P == 0 || host_out != nullptr), "bad arguments");
+    PMF_REQUIRE(nu > 0 && nv > 0, "detector sizes must be positive");
+    PMF_REQUIRE(sad_mm > 0.0 && sdd_mm > sad_mm && isfinite(sdd_mm), "need 0 < SAD < SDD");
+    PMF_REQUIRE(du_mm > 0.0 && dv_mm > 0.0 && isfinite(du_mm) && isfinite(dv_mm), "pixel pitch must be positive");
+    const double two_pi = 6.283185307179586476925287;
+    for (int32_t p = 0; p < P; p++) {
+        const double th = two_pi * (double)p / (double)P;
+        const double c = cos(th), s = sin(th);
+        pmf_view& v = host_out[p];
+        v.src[0] = sad_mm * c; v.src[1] = sad_mm * s; v.src[2] = 0.0;
+        v.det[0] = -(sdd_mm - sad_mm) * c; v.det[1] = -(sdd_mm - sad_mm) * s; v.det[2] = 0.0;
+        v.du[0] = -s * du_mm; v.du[1] = c * du_mm; v.du[2] = 0.0;
+        v.dv[0] = 0.0; v.dv[1] = 0.0; v.dv[2] = dv_mm;
+    }
+    return PMF_OK;
+}
+
+pmf_status pmf_workspace_size(int32_t op, const pmf_ws_args* a, size_t* bytes) {
+    PMF_REQUIRE(a != nullptr && bytes != nullptr, "null pointer");
+    switch (op) {
+        case PMF_OP_VOXELIZE: return gs_voxelize_workspace(&a->grid, a->n, a->pair_capacity, bytes);
+        case PMF_OP_VOXELIZE_BACKWARD: return gs_voxelize_backward_workspace(&a->grid, a->n, a->channels, bytes);
+        case PMF_OP_COMBINE_BACKWARD: return mbc_combine_backward_workspace(&a->grid, a->L, a->P, bytes);
+        case PMF_OP_WARP_BACKWARD: return warp_volume_backward_workspace(&a->grid, a->P, bytes);
+        case PMF_OP_WARP_COMBINE_BACKWARD: return warp_combine_backward_workspace(&a->grid, a->L, a->P, bytes);
+        case PMF_OP_PROJECT_BACKWARD: return conebeam_project_backward_workspace(&a->grid, a->P, a->vol_stride, bytes);
+        case PMF_OP_LOSS: return projection_loss_workspace(a->count, bytes);
+    }
+    return pmf::set_error(PMF_EINVAL, "unknown workspace op %d", (int)op);
+}
+
+pmf_status pmf_device_counters(uint64_t* host_out, int32_t reset) {
+    PMF_REQUIRE(host_out != nullptr, "null pointer");
+    unsigned long long sum[PMF_DIAG_COUNT] = {};
+    pmf_status st;
+    if ((st = pmf::diag_voxelize(sum, reset)) != PMF_OK) return st;
+    if ((st = pmf::diag_project(sum, reset)) != PMF_OK) return st;
+    if ((st = pmf::diag_warp(sum, reset)) != PMF_OK) return st;
+    for (int i = 0; i < PMF_DIAG_COUNT; i++) host_out[i] = (uint64_t)sum[i];
+    return PMF_OK;
+}
+
+pmf_status pmf_device_status(pmf_stream stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return pmf::set_error(PMF_ECUDA, "stream: %s", cudaGetErrorString(e));
+    uint64_t c[PMF_DIAG_COUNT];
+    pmf_status st = pmf_device_counters(c, 0);
+    if (st != PMF_OK) return st;
+    if (c[PMF_DIAG_NONFINITE] != 0)
+        return pmf::set_error(PMF_EINVAL, "%llu launches saw a NaN or infinite input magnitude (outputs are NaN)",
+                              (unsigned long long)c[PMF_DIAG_NONFINITE]);
+    return PMF_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,431 @@
+// Training-step plans (pmf_plan_*) and the projector launch-form autotuner
+// (pmf_autotune).  A plan composes this library's entry points into one
+// forward + adjoint step of Stages 2-3 (Sec. 2.3.2):
+//   V = voxelize(ref) (Eq. 4-5), E_l = voxelize(mbc_l) (Sec. 2.3.1),
+//   W = warp_combine(V, E, w) (Eq. 3 + Eq. 2), Y = project(W) (Eq. 6),
+//   loss, dY = projection_loss(Y, M) (Eq. 10/12 or Eq. 1),
+//   dW = project^T(dY), (dV, dE, dw) = warp_combine^T(dW),
+//   d(ref), d(mbc_l) = voxelize^T(dV), voxelize^T(dE_l).
+// The Gaussian parameters, the batch inputs and the gradient outputs are the
+// caller's; the intermediate tensors and every workspace belong to the plan
+// (one device allocation).  The step can be captured into a CUDA graph.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "pmf_common.cuh"
+
+struct pmf_plan {
+    pmf_batch_desc d;
+    int L = 0, B = 0;
+    size_t elt = 4;
+    int64_t N = 0, Q = 0;
+    char* mem = nullptr;
+    void *V = nullptr, *E = nullptr, *W = nullptr;
+    float *Y = nullptr, *dY = nullptr, *dW = nullptr, *dV = nullptr, *dE = nullptr;
+    void* vox_ws[1 + PMF_MAX_LEVELS] = {};
+    size_t vox_bytes[1 + PMF_MAX_LEVELS] = {};
+    void* vb_ws[1 + PMF_MAX_LEVELS] = {};
+    size_t vb_bytes[1 + PMF_MAX_LEVELS] = {};
+    void* bp_ws = nullptr;
+    size_t bp_bytes = 0;
+    void* wc_ws = nullptr;
+    size_t wc_bytes = 0;
+    void* loss_ws = nullptr;
+    size_t loss_bytes = 0;
+    int proj_form = 0, bp_form = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace pmf {
+namespace {
+
+size_t dtype_bytes(pmf_dtype dt) { return dt == PMF_F32 ? 4 : 2; }
+
+const pmf_gaussians& gset(const pmf_batch_desc& d, int i) { return i == 0 ? d.ref : d.mbc[i - 1]; }
+
+pmf_status check_gaussians(const pmf_gaussians& g, int channels, const char* what) {
+    PMF_REQUIRE(g.n >= 1, "%s: need at least one Gaussian", what);
+    PMF_REQUIRE(g.channels == channels, "%s: channels must be %d", what, channels);
+    PMF_REQUIRE(g.mean && g.scale && g.quat && g.value, "%s: null parameter pointer", what);
+    PMF_REQUIRE(g.kappa > 0.0f, "%s: kappa must be positive", what);
+    return PMF_OK;
+}
+
+pmf_status check_desc(const pmf_batch_desc* d) {
+    PMF_REQUIRE(d != nullptr, "desc is null");
+    pmf_status st = validate_grid(&d->grid);
+    if (st != PMF_OK) return st;
+    if ((st = validate_dtype(d->dtype)) != PMF_OK) return st;
+    PMF_REQUIRE(d->det.nu > 0 && d->det.nv > 0 && d->det.step_mm > 0.0f, "bad detector");
+    PMF_REQUIRE(d->batch >= 1, "batch must be >= 1");
+    PMF_REQUIRE(d->loss_kind == 1 || d->loss_kind == 2, "loss_kind must be 1 (L1) or 2 (L2)");
+    PMF_REQUIRE(d->levels >= 1 && d->levels <= PMF_MAX_LEVELS, "levels must be in [1, %d]", PMF_MAX_LEVELS);
+    if ((st = check_gaussians(d->ref, 1, "ref")) != PMF_OK) return st;
+    for (int l = 0; l < d->levels; l++) {
+        char what[16];
+        snprintf(what, sizeof(what), "mbc[%d]", l);
+        if ((st = check_gaussians(d->mbc[l], 3, what)) != PMF_OK) return st;
+        for (int k = 0; k < 4; k++) PMF_REQUIRE(d->d_mbc[l][k] != nullptr, "d_mbc[%d][%d] is null", l, k);
+    }
+    for (int k = 0; k < 4; k++) PMF_REQUIRE(d->d_ref[k] != nullptr, "d_ref[%d] is null", k);
+    PMF_REQUIRE(d->views && d->coeff && d->meas && d->loss && d->d_coeff, "null batch pointer");
+    return PMF_OK;
+}
+
+// Key of a configuration in the tuning cache: device, SM count and the plan's
+// shapes (the launch forms do not depend on the data).
+std::string tune_key(const pmf_batch_desc& d) {
+    int dev = 0, sms = 0;
+    cudaDeviceProp prop;
+    std::string name = "unknown";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+        name = prop.name;
+        sms = prop.multiProcessorCount;
+    }
+    for (char& c : name)
+        if (c == ' ' || c == '\t') c = '_';
+    char buf[512];
+    snprintf(buf, sizeof(buf), "dev=%s;sm=%d;grid=%dx%dx%d@%g,%g,%g;det=%dx%d@%g;B=%d;L=%d;dtype=%d", name.c_str(), sms,
+             d.grid.nx, d.grid.ny, d.grid.nz, (double)d.grid.vx, (double)d.grid.vy, (double)d.grid.vz, d.det.nu,
+             d.det.nv, (double)d.det.step_mm, d.batch, d.levels, (int)d.dtype);
+    return buf;
+}
+
+std::vector<std::string> read_lines(const char* path) {
+    std::vector<std::string> out;
+    FILE* f = fopen(path, "r");
+    if (!f) return out;
+    char line[2048];
+    while (fgets(line, sizeof(line), f)) {
+        std::string s(line);
+        while (!s.empty() && (s.back() == '\n' || s.back() == '\r')) s.pop_back();
+        if (!s.empty()) out.push_back(s);
+    }
+    fclose(f);
+    return out;
+}
+
+// "<key> proj=<int> backproj=<int>"
+bool cache_lookup(const char* path, const std::string& key, int& proj, int& bp) {
+    for (const std::string& s : read_lines(path)) {
+        if (s.compare(0, key.size(), key) != 0 || s.size() <= key.size() || s[key.size()] != ' ') continue;
+        int a, b;
+        if (sscanf(s.c_str() + key.size(), " proj=%d backproj=%d", &a, &b) == 2 && a >= 0 && a <= 16 && b >= 0 &&
+            b <= 16) {
+            proj = a;
+            bp = b;
+            return true;
+        }
+    }
+    return false;
+}
+
+pmf_status cache_store(const char* path, const std::string& key, int proj, int bp) {
+    std::vector<std::string> lines = read_lines(path);
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return set_error(PMF_EINVAL, "cannot write %s", tmp.c_str());
+    for (const std::string& s : lines)
+        if (!(s.compare(0, key.size(), key) == 0 && s.size() > key.size() && s[key.size()] == ' '))
+            fprintf(f, "%s\n", s.c_str());
+    fprintf(f, "%s proj=%d backproj=%d\n", key.c_str(), proj, bp);
+    if (fclose(f) != 0 || rename(tmp.c_str(), path) != 0) return set_error(PMF_EINVAL, "cannot write %s", path);
+    return PMF_OK;
+}
+
+#define PMF_TRY(expr)                        \
+    do {                                     \
+        pmf_status st_ = (expr);             \
+        if (st_ != PMF_OK) return st_;       \
+    } while (0)
+
+#define PMF_TRY_CUDA(expr, what)                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (expr);                                                                   \
+        if (e_ != cudaSuccess) return set_error(PMF_ECUDA, "%s: %s", what, cudaGetErrorString(e_)); \
+    } while (0)
+
+pmf_status plan_project(pmf_plan* p, cudaStream_t s) {
+    const pmf_batch_desc& d = p->d;
+    pmf_project_item it{d.grid, d.det, p->B, d.views, p->W, p->N, p->Y};
+    return project_launch(it, d.dtype, p->proj_form, s);
+}
+
+pmf_status plan_backproject(pmf_plan* p, cudaStream_t s) {
+    const pmf_batch_desc& d = p->d;
+    pmf_backproject_item it{d.grid, d.det, p->B, d.views, p->dY, p->dW, p->N};
+    return backproject_launch(it, 0, p->bp_ws, p->bp_bytes, p->bp_form, s);
+}
+
+pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
+    const pmf_batch_desc& d = p->d;
+    const pmf_stream ps = (pmf_stream)s;
+    const int64_t N = p->N;
+    PMF_TRY(gs_voxelize(&d.grid, &d.ref, d.dtype, p->V, p->vox_ws[0], p->vox_bytes[0], ps));
+    for (int l = 0; l < p->L; l++)
+        PMF_TRY(gs_voxelize(&d.grid, &d.mbc[l], d.dtype, (char*)p->E + (size_t)l * 3 * N * p->elt, p->vox_ws[1 + l],
+                            p->vox_bytes[1 + l], ps));
+    PMF_TRY(warp_combine(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, p->W, ps));
+    PMF_TRY(plan_project(p, s));
+    PMF_TRY(projection_loss(d.loss_kind, p->B, p->Q, p->Y, d.meas, d.loss, p->dY, p->loss_ws, p->loss_bytes, ps));
+    PMF_TRY(plan_backproject(p, s));
+    PMF_TRY(warp_combine_backward(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, p->dW, p->dV, p->dE, d.d_coeff,
+                                  0, p->wc_ws, p->wc_bytes, ps));
+    PMF_TRY(gs_voxelize_backward(&d.grid, &d.ref, p->dV, d.d_ref[0], d.d_ref[1], d.d_ref[2], d.d_ref[3], 0,
+                                 p->vb_ws[0], p->vb_bytes[0], ps));
+    for (int l = 0; l < p->L; l++)
+        PMF_TRY(gs_voxelize_backward(&d.grid, &d.mbc[l], p->dE + (size_t)l * 3 * N, d.d_mbc[l][0], d.d_mbc[l][1],
+                                     d.d_mbc[l][2], d.d_mbc[l][3], 0, p->vb_ws[1 + l], p->vb_bytes[1 + l], ps));
+    return PMF_OK;
+}
+
+// Pair-list capacity of each voxelizer: the exact (Gaussian, tile) overlap
+// count of the current parameters with 25% headroom (overflow later is still
+// correct, only slower; PMF_DIAG_VOXELIZE_LIST_OVERFLOW counts it).
+pmf_status pair_capacities(const pmf_batch_desc& d, int64_t* cap) {
+    const int sets = 1 + d.levels;
+    size_t need = 0;
+    for (int i = 0; i < sets; i++) {
+        size_t b;
+        PMF_TRY(gs_voxelize_workspace(&d.grid, gset(d, i).n, 0, &b));
+        need = b > need ? b : need;
+    }
+    char* tmp = nullptr;
+    PMF_TRY_CUDA(cudaMalloc(&tmp, need + 256), "cudaMalloc");
+    pmf_status st = PMF_OK;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(tmp);
+        return set_error(PMF_ECUDA, "cudaStreamCreate failed");
+    }
+    int64_t* d_pairs = (int64_t*)(tmp + need);
+    for (int i = 0; i < sets && st == PMF_OK; i++) {
+        st = gs_voxelize_count(&d.grid, &gset(d, i), d_pairs, tmp, need, (pmf_stream)s);
+        int64_t h = 0;
+        if (st == PMF_OK && cudaMemcpyAsync(&h, d_pairs, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            st = set_error(PMF_ECUDA, "pair count copy failed");
+        if (st == PMF_OK && cudaStreamSynchronize(s) != cudaSuccess) st = set_error(PMF_ECUDA, "pair count failed");
+        cap[i] = h + h / 4 + 4096;
+    }
+    cudaStreamDestroy(s);
+    cudaFree(tmp);
+    return st;
+}
+
+pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
+    PMF_TRY(check_desc(desc));
+    pmf_plan* p = new pmf_plan();
+    p->d = *desc;
+    p->d.tune_cache = nullptr;  // the caller's string need not outlive the call
+    p->L = desc->levels;
+    p->B = desc->batch;
+    p->elt = dtype_bytes(desc->dtype);
+    p->N = (int64_t)desc->grid.nx * desc->grid.ny * desc->grid.nz;
+    p->Q = (int64_t)desc->det.nu * desc->det.nv;
+    const pmf_batch_desc& d = p->d;
+    const int sets = 1 + p->L;
+    int64_t cap[1 + PMF_MAX_LEVELS];
+    pmf_status st = pair_capacities(d, cap);
+    if (st != PMF_OK) {
+        delete p;
+        return st;
+    }
+    // sizes, then one allocation carved at 256-byte boundaries
+    std::vector<size_t> sz;
+    const size_t N = (size_t)p->N, B = (size_t)p->B, L = (size_t)p->L, Q = (size_t)p->Q;
+    sz.push_back(N * p->elt);                 // V
+    sz.push_back(L * 3 * N * p->elt);         // E
+    sz.push_back(B * N * p->elt);             // W
+    sz.push_back(B * Q * 4);                  // Y
+    sz.push_back(B * Q * 4);                  // dY
+    sz.push_back(B * N * 4);                  // dW
+    sz.push_back(N * 4);                      // dV
+    sz.push_back(L * 3 * N * 4);              // dE
+    for (int i = 0; i < sets && st == PMF_OK; i++) {
+        st = gs_voxelize_workspace(&d.grid, gset(d, i).n, cap[i], &p->vox_bytes[i]);
+        if (st == PMF_OK) st = gs_voxelize_backward_workspace(&d.grid, gset(d, i).n, gset(d, i).channels, &p->vb_bytes[i]);
+    }
+    if (st == PMF_OK) st = conebeam_project_backward_workspace(&d.grid, p->B, p->N, &p->bp_bytes);
+    if (st == PMF_OK) st = warp_combine_backward_workspace(&d.grid, p->L, p->B, &p->wc_bytes);
+    if (st == PMF_OK) st = projection_loss_workspace((int64_t)(B * Q), &p->loss_bytes);
+    if (st != PMF_OK) {
+        delete p;
+        return st;
+    }
+    for (int i = 0; i < sets; i++) sz.push_back(p->vox_bytes[i]);
+    for (int i = 0; i < sets; i++) sz.push_back(p->vb_bytes[i]);
+    sz.push_back(p->bp_bytes);
+    sz.push_back(p->wc_bytes);
+    sz.push_back(p->loss_bytes);
+    size_t total = 0;
+    for (size_t b : sz) total += align_up(b ? b : 1);
+    if (cudaMalloc(&p->mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return set_error(PMF_ECUDA, "cudaMalloc of %zu bytes for the plan failed", total);
+    }
+    char* cur = p->mem;
+    size_t k = 0;
+    auto take = [&]() {
+        char* r = cur;
+        cur += align_up(sz[k] ? sz[k] : 1);
+        k++;
+        return (void*)r;
+    };
+    p->V = take();
+    p->E = take();
+    p->W = take();
+    p->Y = (float*)take();
+    p->dY = (float*)take();
+    p->dW = (float*)take();
+    p->dV = (float*)take();
+    p->dE = (float*)take();
+    for (int i = 0; i < sets; i++) p->vox_ws[i] = take();
+    for (int i = 0; i < sets; i++) p->vb_ws[i] = take();
+    p->bp_ws = take();
+    p->wc_ws = take();
+    p->loss_ws = take();
+    if (desc->tune_cache) {
+        int a, b;
+        if (cache_lookup(desc->tune_cache, tune_key(d), a, b)) {
+            p->proj_form = a;
+            p->bp_form = b;
+        }
+    }
+    *out = p;
+    return PMF_OK;
+}
+
+void plan_free(pmf_plan* p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->mem) cudaFree(p->mem);
+    delete p;
+}
+
+float time_ms(cudaStream_t s, int reps, pmf_status (*fn)(pmf_plan*, cudaStream_t), pmf_plan* p, pmf_status& st) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    st = fn(p, s);  // warm-up
+    float best = 3.0e38f;
+    for (int r = 0; r < reps && st == PMF_OK; r++) {
+        cudaEventRecord(a, s);
+        st = fn(p, s);
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) st = set_error(PMF_ECUDA, "timing failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        best = ms < best ? ms : best;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+}  // namespace
+}  // namespace pmf
+
+using namespace pmf;
+
+extern "C" {
+
+pmf_status pmf_plan_create(const pmf_batch_desc* desc, pmf_plan** plan) {
+    PMF_REQUIRE(plan != nullptr, "plan is null");
+    *plan = nullptr;
+    return plan_create(desc, plan);
+}
+
+pmf_status pmf_plan_step(pmf_plan* p, pmf_stream stream) {
+    PMF_REQUIRE(p != nullptr, "plan is null");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!p->d.use_graph) return enqueue_step(p, s);
+    if (!p->exec) {
+        PMF_REQUIRE(s != nullptr, "a graph-captured plan needs a created stream, not the NULL stream");
+        PMF_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        pmf_status st = enqueue_step(p, s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st != PMF_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return st != PMF_OK ? st : set_error(PMF_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&p->exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            p->exec = nullptr;
+            return set_error(PMF_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+        p->graph = g;
+    }
+    PMF_TRY_CUDA(cudaGraphLaunch(p->exec, s), "cudaGraphLaunch");
+    return PMF_OK;
+}
+
+pmf_status pmf_plan_tensors_get(const pmf_plan* p, pmf_plan_tensors* out) {
+    PMF_REQUIRE(p != nullptr && out != nullptr, "null pointer");
+    out->V = p->V;
+    out->E = p->E;
+    out->W = p->W;
+    out->Y = p->Y;
+    out->dY = p->dY;
+    out->dW = p->dW;
+    out->dV = p->dV;
+    out->dE = p->dE;
+    return PMF_OK;
+}
+
+pmf_status pmf_plan_launch_forms(const pmf_plan* p, int32_t* proj, int32_t* backproj) {
+    PMF_REQUIRE(p != nullptr && proj != nullptr && backproj != nullptr, "null pointer");
+    *proj = p->proj_form;
+    *backproj = p->bp_form;
+    return PMF_OK;
+}
+
+pmf_status pmf_plan_destroy(pmf_plan* p) {
+    plan_free(p);
+    return PMF_OK;
+}
+
+pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path) {
+    PMF_REQUIRE(cache_path != nullptr && cache_path[0] != '\0', "cache_path is empty");
+    pmf_batch_desc d = *desc;
+    d.use_graph = 0;
+    d.tune_cache = nullptr;
+    pmf_plan* p = nullptr;
+    PMF_TRY(plan_create(&d, &p));
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        plan_free(p);
+        return set_error(PMF_ECUDA, "cudaStreamCreate failed");
+    }
+    pmf_status st = enqueue_step(p, s);  // fills W and dY
+    const int forms[] = {0, 1, 2, 3, 4};
+    float best_fp = 3.0e38f, best_bp = 3.0e38f;
+    int fp = 0, bp = 0;
+    for (int f : forms) {
+        if (st != PMF_OK) break;
+        p->proj_form = f;
+        float t = time_ms(s, 3, plan_project, p, st);
+        if (st == PMF_OK && t < best_fp) { best_fp = t; fp = f; }
+        if (st != PMF_OK) break;
+        p->bp_form = f;
+        t = time_ms(s, 3, plan_backproject, p, st);
+        if (st == PMF_OK && t < best_bp) { best_bp = t; bp = f; }
+    }
+    if (st == PMF_OK && cudaStreamSynchronize(s) != cudaSuccess) st = set_error(PMF_ECUDA, "autotune failed");
+    const std::string key = tune_key(d);
+    cudaStreamDestroy(s);
+    plan_free(p);
+    if (st != PMF_OK) return st;
+    return cache_store(cache_path, key, fp, bp);
+}
+
+}  // extern "C"

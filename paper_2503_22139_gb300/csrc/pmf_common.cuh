@@ -32,6 +32,38 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 // on the device: 4 x 152 SMs.
 constexpr int kStreamBlocks = 608;
 
+// ---------------------------------------------------- device diagnostics
+//
+// Counters of the slow paths and of non-finite scatter inputs (pmf_diag).
+// Every translation unit that includes this header has its own array;
+// pmf_device_counters adds them up through the accessors below.
+static __device__ unsigned long long g_diag[PMF_DIAG_COUNT];
+
+__device__ __forceinline__ void diag_count(int which) { atomicAdd(&g_diag[which], 1ull); }
+
+#define PMF_DIAG_ACCESSOR(fn)                                                                     \
+    pmf_status fn(unsigned long long* out, int reset) {                                           \
+        unsigned long long v[PMF_DIAG_COUNT];                                                     \
+        cudaError_t e = cudaMemcpyFromSymbol(v, g_diag, sizeof(v));                               \
+        if (e == cudaSuccess && reset) {                                                          \
+            const unsigned long long z[PMF_DIAG_COUNT] = {};                                      \
+            e = cudaMemcpyToSymbol(g_diag, z, sizeof(z));                                         \
+        }                                                                                         \
+        if (e != cudaSuccess) return ::pmf::set_error(PMF_ECUDA, #fn ": %s", cudaGetErrorString(e)); \
+        for (int i = 0; i < PMF_DIAG_COUNT; i++) out[i] += v[i];                                  \
+        return PMF_OK;                                                                            \
+    }
+
+pmf_status diag_voxelize(unsigned long long* out, int reset);
+pmf_status diag_project(unsigned long long* out, int reset);
+pmf_status diag_warp(unsigned long long* out, int reset);
+
+// Projector launch forms used by plans (0: one CTA per (view, tile); k > 0:
+// persistent, k CTAs per SM); results are identical across forms.
+pmf_status project_launch(const pmf_project_item& it, pmf_dtype dtype, int form, cudaStream_t s);
+pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes, int form,
+                              cudaStream_t s);
+
 // ------------------------------------------------------- storage dtypes
 
 template <typename T> struct Store;
@@ -134,8 +166,20 @@ __device__ __forceinline__ void red_add(unsigned long long* p, unsigned long lon
 }
 
 // Non-negative float max via the order-preserving bit pattern.
-__device__ __forceinline__ void atomic_max_nonneg(unsigned int* p, float v) {
-    if (v > 0.0f) atomicMax(p, __float_as_uint(v));
+// |x| as ordered bits: for non-negative floats the unsigned order of the bit
+// patterns is the numeric order, and +inf and every NaN sort above all finite
+// values, so a maximum over these bits keeps a NaN or infinity visible (fmaxf
+// would drop a NaN).
+__device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
+// Grid-stride maximum of |x[0..n)| into *out as abs_bits (every thread of the
+// launch calls it; blocks are whole warps).
+__device__ __forceinline__ void absmax_bits(const float* __restrict__ x, int64_t n, unsigned* out) {
+    unsigned m = 0u;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, abs_bits(__ldg(x + t)));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
 // --------------------------------------------------- block reductions

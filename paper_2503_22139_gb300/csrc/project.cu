@@ -265,6 +265,7 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
         const bool act = chunk_begin(bs, sel, r, live, M0, j0, j1, ib, fb);
         __syncthreads();
         const Box bx = read_box(bs, sel);
+        if (threadIdx.x == 0 && bx.vol > 0 && !bx.fits) diag_count(PMF_DIAG_PROJECT_BOX_FALLBACK);
         if (bx.vol > 0 && bx.fits) {
             // stage the box: lane = x, one warp per (y, z) row, zero outside the grid
             {
@@ -331,13 +332,7 @@ __global__ void __launch_bounds__(kRay) k_project(GridD g, int nu, int nv, int n
     project_tile<T>(g, nu, nv, ntu, step, views, vol, vol_stride, proj, blockIdx.y, blockIdx.x, box, bs);
 }
 
-__global__ void k_absmax_f(const float* __restrict__ x, int64_t n, unsigned* out) {
-    float m = 0.f;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(__ldg(x + t)));
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
-}
+__global__ void k_absmax_f(const float* __restrict__ x, int64_t n, unsigned* out) { absmax_bits(x, n, out); }
 
 // ----------------------------------------------------------------- adjoint
 
@@ -524,6 +519,7 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
         const bool act = chunk_begin(bs, sel, r, live, M0, j0, j1, ib, fb);
         __syncthreads();
         const Box bx = read_box(bs, sel);
+        if (threadIdx.x == 0 && bx.vol > 0 && !bx.fits) diag_count(PMF_DIAG_BACKPROJECT_BOX_FALLBACK);
         if (bx.vol > 0 && bx.fits) {
             if (act) {
                 const int sy = kPitch, sz = kPitch * bx.by;
@@ -625,6 +621,7 @@ __global__ void k_fixed_to_float_f(const unsigned long long* __restrict__ acc, i
     const int kexp = fixed_exponent(bound);
     const float inv = ldexpf(1.0f, -kexp);
     const bool bad = !isfinite(bound);
+    if (bad && blockIdx.x == 0 && threadIdx.x == 0) diag_count(PMF_DIAG_NONFINITE);
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const float r = bad ? __int_as_float(0x7fc00000) : from_fixed(acc[t], inv);
         out[t] = accumulate ? out[t] + r : r;
@@ -700,11 +697,7 @@ __global__ void __launch_bounds__(kRay) k_backproject_batched(const __grid_const
 // blockIdx.y = item
 __global__ void k_absmax_batched(const __grid_constant__ ProjBatch B) {
     const ProjItem& it = B.it[blockIdx.y];
-    float m = 0.f;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < it.nq; t += (int64_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(__ldg(it.dproj + t)));
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(it.maxbits, m);
+    absmax_bits(it.dproj, it.nq, it.maxbits);
 }
 
 __global__ void k_fixed_to_float_batched(const __grid_constant__ ProjBatch B, int accumulate) {
@@ -713,6 +706,7 @@ __global__ void k_fixed_to_float_batched(const __grid_constant__ ProjBatch B, in
     const int kexp = fixed_exponent(bound);
     const float inv = ldexpf(1.0f, -kexp);
     const bool bad = !isfinite(bound);
+    if (bad && blockIdx.x == 0 && threadIdx.x == 0) diag_count(PMF_DIAG_NONFINITE);
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < it.cells; t += (int64_t)gridDim.x * blockDim.x) {
         const float r = bad ? __int_as_float(0x7fc00000) : from_fixed(it.acc[t], inv);
         it.dvol[t] = accumulate ? it.dvol[t] + r : r;
@@ -780,6 +774,9 @@ int max_samples_per_voxel(const pmf_grid* grid, float step) {
 }
 
 }  // namespace
+
+PMF_DIAG_ACCESSOR(diag_project)
+
 }  // namespace pmf
 
 using namespace pmf;
@@ -865,12 +862,14 @@ static pmf_status fill_item(const pmf_project_item& in, pmf_dtype dtype, int64_t
     return PMF_OK;
 }
 
-static unsigned persistent_ctas(int64_t total) {
-    const int64_t cap = 4 * 152;  // 4 resident CTAs per SM at 256 threads and <= 64 registers
+// ctas = 0: 4 resident CTAs per SM of 152 (256 threads, <= 64 registers each)
+static unsigned persistent_ctas(int64_t total, unsigned ctas) {
+    const int64_t cap = ctas ? (int64_t)ctas : 4 * 152;
     return (unsigned)(total < cap ? (total > 0 ? total : 1) : cap);
 }
 
-pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pmf_dtype dtype, pmf_stream stream) {
+static pmf_status project_batched_impl(int32_t n, const pmf_project_item* items, pmf_dtype dtype, unsigned ctas,
+                                       pmf_stream stream) {
     PMF_REQUIRE(n >= 0 && n <= kMaxItems, "n must be in [0, %d]", kMaxItems);
     PMF_REQUIRE(n == 0 || items != nullptr, "items is null");
     pmf_status st = validate_dtype(dtype);
@@ -888,8 +887,12 @@ pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pm
     B.total = total;
     if (total == 0) return PMF_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    PMF_DISPATCH_DTYPE(dtype, T, k_project_batched<T><<<persistent_ctas(total), kRay, 0, s>>>(B));
+    PMF_DISPATCH_DTYPE(dtype, T, k_project_batched<T><<<persistent_ctas(total, ctas), kRay, 0, s>>>(B));
     return check_launch("conebeam_project_batched");
+}
+
+pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pmf_dtype dtype, pmf_stream stream) {
+    return project_batched_impl(n, items, dtype, 0, stream);
 }
 
 static size_t bp_item_bytes(const pmf_backproject_item& it) {
@@ -910,8 +913,8 @@ pmf_status conebeam_project_backward_batched_workspace(int32_t n, const pmf_back
     return PMF_OK;
 }
 
-pmf_status conebeam_project_backward_batched(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
-                                             size_t ws_bytes, pmf_stream stream) {
+static pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
+                                           size_t ws_bytes, unsigned ctas, pmf_stream stream) {
     size_t need = 0;
     pmf_status st = conebeam_project_backward_batched_workspace(n, items, &need);
     if (st != PMF_OK) return st;
@@ -948,11 +951,16 @@ pmf_status conebeam_project_backward_batched(int32_t n, const pmf_backproject_it
         const int64_t nb = (maxq + 255) / 256;
         k_absmax_batched<<<dim3((unsigned)(nb < 1024 ? nb : 1024), (unsigned)n), 256, 0, s>>>(B);
     }
-    if (total > 0) k_backproject_batched<<<persistent_ctas(total), kRay, 0, s>>>(B);
+    if (total > 0) k_backproject_batched<<<persistent_ctas(total, ctas), kRay, 0, s>>>(B);
     const int64_t nc = (maxcells + 255) / 256;
     k_fixed_to_float_batched<<<dim3((unsigned)(nc < 4 * kStreamBlocks ? nc : 4 * kStreamBlocks), (unsigned)n), 256, 0, s>>>(
         B, accumulate);
     return check_launch("conebeam_project_backward_batched");
+}
+
+pmf_status conebeam_project_backward_batched(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
+                                             size_t ws_bytes, pmf_stream stream) {
+    return backproject_batched_impl(n, items, accumulate, ws, ws_bytes, 0, stream);
 }
 
 pmf_status projection_loss_workspace(int64_t count, size_t* bytes) {
@@ -980,3 +988,30 @@ pmf_status projection_loss(int32_t kind, int32_t P, int64_t Q, const float* pred
 }
 
 }  // extern "C"
+
+namespace pmf {
+
+// Launch forms for plans: form 0 is one CTA per (view, tile); form k > 0 a
+// persistent launch of k CTAs per SM.  Every form runs the same per-tile
+// arithmetic, so the results are identical.
+static unsigned form_ctas(int form) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (unsigned)form * (unsigned)(sms > 0 ? sms : 152);
+}
+
+pmf_status project_launch(const pmf_project_item& it, pmf_dtype dtype, int form, cudaStream_t s) {
+    if (form <= 0)
+        return conebeam_project(&it.grid, &it.det, it.P, it.views, dtype, it.vol, it.vol_stride, it.proj, (pmf_stream)s);
+    return project_batched_impl(1, &it, dtype, form_ctas(form), (pmf_stream)s);
+}
+
+pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes, int form,
+                              cudaStream_t s) {
+    if (form <= 0)
+        return conebeam_project_backward(&it.grid, &it.det, it.P, it.views, it.d_proj, it.d_vol, it.vol_stride,
+                                         accumulate, ws, ws_bytes, (pmf_stream)s);
+    return backproject_batched_impl(1, &it, accumulate, ws, ws_bytes, form_ctas(form), (pmf_stream)s);
+}
+
+}  // namespace pmf

@@ -144,9 +144,9 @@ __global__ void k_prep(pmf_gaussians G, GridD g, float kappa, VoxWs w, int ntx, 
         p[3 * n + i] = s.a00; p[4 * n + i] = s.a11; p[5 * n + i] = s.a22;
         p[6 * n + i] = s.b01; p[7 * n + i] = s.b02; p[8 * n + i] = s.b12; p[9 * n + i] = k2;
         for (int a = 0; a < 3; a++) { w.box[a * n + i] = s.lo[a]; w.box[(3 + a) * n + i] = s.hi[a]; }
-        float m = 0.0f;
-        for (int c = 0; c < G.channels; c++) m = fmaxf(m, fabsf(__ldg(G.value + i * G.channels + c)));
-        atomic_max_nonneg(&w.hdr->max_abs_bits, m);
+        unsigned m = 0u;  // abs_bits keeps a NaN or infinite value visible
+        for (int c = 0; c < G.channels; c++) m = max(m, abs_bits(__ldg(G.value + i * G.channels + c)));
+        if (m) atomicMax(&w.hdr->max_abs_bits, m);
     }
     if (s.lo[0] > s.hi[0] || s.lo[1] > s.hi[1] || s.lo[2] > s.hi[2]) return;
     const int t0x = s.lo[0] / kTile, t1x = s.hi[0] / kTile, t0y = s.lo[1] / kTile, t1y = s.hi[1] / kTile,
@@ -218,6 +218,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
     const float cz0 = centre(iz0, g.nz, g.vz), cz1 = centre(iz1, g.nz, g.vz);
 
     const float maxabs = __uint_as_float(w.hdr->max_abs_bits);
+    const bool bad = !isfinite(maxabs);  // a NaN or infinite value: the output is NaN
+    if (bad && t == 0 && tid == 0) diag_count(PMF_DIAG_NONFINITE);
     const int kexp = fixed_exponent(maxabs * (float)(G.n > 0 ? G.n : 1));
     const float scale = ldexpf(1.0f, kexp), inv_scale = ldexpf(1.0f, -kexp);
 
@@ -229,6 +231,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
     const unsigned cnt = w.tcount[t];
     const unsigned long long off = w.toff[t];
     const bool listed = (long long)(off + cnt) <= w.capacity && w.toff[t] != 0xffffffffu;
+    if (!listed && tid == 0) diag_count(PMF_DIAG_VOXELIZE_LIST_OVERFLOW);
     // Listed tiles walk their own list; overflowed tiles scan every Gaussian's box.
     const int64_t total = listed ? (int64_t)cnt : n;
     const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
@@ -292,12 +295,12 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
         if (iz0 < g.nz) {
             const int64_t v = ((int64_t)iz0 * g.ny + iy) * g.nx + ix;
 #pragma unroll
-            for (int c = 0; c < C; c++) Store<T>::st(out, c * N + v, __ll2float_rn(acc0[c]) * inv_scale);
+            for (int c = 0; c < C; c++) Store<T>::st(out, c * N + v, bad ? __int_as_float(0x7fc00000) : __ll2float_rn(acc0[c]) * inv_scale);
         }
         if (iz1 < g.nz) {
             const int64_t v = ((int64_t)iz1 * g.ny + iy) * g.nx + ix;
 #pragma unroll
-            for (int c = 0; c < C; c++) Store<T>::st(out, c * N + v, __ll2float_rn(acc1[c]) * inv_scale);
+            for (int c = 0; c < C; c++) Store<T>::st(out, c * N + v, bad ? __int_as_float(0x7fc00000) : __ll2float_rn(acc1[c]) * inv_scale);
         }
     }
 }
@@ -532,6 +535,9 @@ pmf_status run_prep_scan(const pmf_grid* grid, const pmf_gaussians* gs, const Vo
 }
 
 }  // namespace
+
+PMF_DIAG_ACCESSOR(diag_voxelize)
+
 }  // namespace pmf
 
 using namespace pmf;

@@ -173,13 +173,7 @@ __global__ void __launch_bounds__(kThreads) k_warp(GridD g, int P, const T* __re
     }
 }
 
-__global__ void k_absmax(const float* __restrict__ x, int64_t n, unsigned* out) {
-    float m = 0.f;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(__ldg(x + t)));
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
-}
+__global__ void k_absmax(const float* __restrict__ x, int64_t n, unsigned* out) { absmax_bits(x, n, out); }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_warp_bwd(GridD g, int P, const T* __restrict__ ref,
@@ -217,6 +211,7 @@ __global__ void k_fixed_to_float(const unsigned long long* __restrict__ acc, int
     const int kexp = fixed_exponent(bound);
     const float inv = ldexpf(1.0f, -kexp);
     const bool bad = !isfinite(bound);
+    if (bad && blockIdx.x == 0 && threadIdx.x == 0) diag_count(PMF_DIAG_NONFINITE);
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         float r = bad ? __int_as_float(0x7fc00000) : from_fixed(acc[t], inv);
         out[t] = accumulate ? out[t] + r : r;
@@ -463,6 +458,7 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
     const int shift = kg - kb;
     const int bx0 = t.x0 - kHalo, by0 = t.y0 - kHalo, bz0 = t.z0 - kHalo;
 
+    bool halo_exit = false;
     float e[2][L][3], gE[2][L][3];
 #pragma unroll
     for (int h = 0; h < 2; h++)
@@ -520,6 +516,7 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
                             atomicAdd(q + (dz * kBY + dy) * kBX + dx, round_small_i(gsb * (wx[dx] * wy[dy] * wz[dz])));
             } else {
                 scatter_cell(acc, g, cl, gw, sg);
+                halo_exit = true;
             }
         }
         // coefficient gradient partials: warp tree, then the warp's own slot
@@ -543,7 +540,7 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
                 *o = accumulate ? *o + gE[h][l][a] : gE[h][l][a];
             }
     }
-    __syncthreads();
+    if (__syncthreads_or(halo_exit) && threadIdx.x == 0) diag_count(PMF_DIAG_WARP_HALO_EXIT);
     for (int i = threadIdx.x; i < PL3; i += 256) {
         float r = 0.f;
         for (int wi = 0; wi < 8; wi++) r += swarp[wi * PL3 + i];
@@ -602,6 +599,9 @@ pmf_status check_common(const pmf_grid* grid, int32_t P, pmf_dtype dtype) {
 }
 
 }  // namespace
+
+PMF_DIAG_ACCESSOR(diag_warp)
+
 }  // namespace pmf
 
 using namespace pmf;

@@ -384,3 +384,205 @@ def projection_loss(kind: int, pred: torch.Tensor, meas: torch.Tensor, with_grad
 def library_info() -> dict:
     L = _lib.load()
     return {"version": L.pmf_version().decode(), "path": _lib.library_path()}
+
+
+# ---------------------------------------------------------- host helpers
+
+def pmf_circular_views(P: int, sad_mm: float, sdd_mm: float, du_mm: float, dv_mm: float, nu: int,
+                       nv: int) -> torch.Tensor:
+    """The circular scan (Sec. 2.3.3) as a host float64 [P, 12] tensor of pmf_view records."""
+    arr = (_lib.PmfView * max(int(P), 1))()
+    check(_lib.load().pmf_circular_views(int(P), float(sad_mm), float(sdd_mm), float(du_mm), float(dv_mm), int(nu),
+                                         int(nv), arr), "pmf_circular_views")
+    out = torch.empty((int(P), 12), dtype=torch.float64)
+    for p in range(int(P)):
+        v = arr[p]
+        out[p] = torch.tensor(list(v.src) + list(v.det) + list(v.du) + list(v.dv), dtype=torch.float64)
+    return out
+
+
+circular_views = pmf_circular_views
+
+
+def pmf_workspace_size(op, grid, n: int = 0, pair_capacity: int = 0, vol_stride: int = 0, count: int = 0,
+                       channels: int = 0, L: int = 0, P: int = 0) -> int:
+    """Scratch bytes of one operation (op: a pmf_op code or its name, e.g. "project_backward")."""
+    code = _lib.PMF_OPS[op] if isinstance(op, str) else int(op)
+    a = _lib.PmfWsArgs(_grid(grid), int(n), int(pair_capacity), int(vol_stride), int(count), int(channels), int(L),
+                       int(P))
+    nb = ct.c_size_t(0)
+    check(_lib.load().pmf_workspace_size(code, ct.byref(a), ct.byref(nb)), "pmf_workspace_size")
+    return int(nb.value)
+
+
+workspace_size = pmf_workspace_size
+
+
+def pmf_device_counters(reset: bool = False) -> dict:
+    """The current device's diagnostic counters (pmf_diag) by name; synchronizes."""
+    buf = (ct.c_uint64 * _lib.PMF_DIAG_COUNT)()
+    check(_lib.load().pmf_device_counters(buf, 1 if reset else 0), "pmf_device_counters")
+    return {name: int(buf[i]) for i, name in enumerate(_lib.DIAG_NAMES)}
+
+
+device_counters = pmf_device_counters
+
+
+def pmf_device_status() -> None:
+    """Synchronizes torch's current stream; raises PmfError if its work failed
+    or a non-finite input reached a fixed-point scatter."""
+    check(_lib.load().pmf_device_status(_stream()), "pmf_device_status")
+
+
+device_status = pmf_device_status
+
+
+# ----------------------------------------------------- training-step plan
+
+class _DevArray:
+    """__cuda_array_interface__ view of a plan-owned device buffer."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+_TYPESTR = {torch.float32: "<f4", torch.float16: "<f2"}
+
+
+class _StepBuffers:
+    """The caller-side buffers of a pmf_batch_desc (batch inputs, loss,
+    gradients) and the descriptor that points at them."""
+
+    def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
+                 dtype: torch.dtype = torch.bfloat16, kind: int = 2):
+        if len(mbc) < 1 or len(mbc) > _lib.PMF_MAX_LEVELS:
+            raise ValueError(f"need 1..{_lib.PMF_MAX_LEVELS} MBC levels")
+        self.grid, self.det, self.ref, self.mbc = grid, det, ref, list(mbc)
+        self.B, self.L, self.dtype, self.kind = int(batch), len(self.mbc), dtype, int(kind)
+        dev = ref.mean.device
+        gr = _det(det)
+        self.views = torch.zeros((self.B, 12), dtype=torch.float64, device=dev)
+        self.coeff = torch.zeros((self.B, self.L, 3), dtype=torch.float32, device=dev)
+        self.meas = torch.zeros((self.B, gr.nv, gr.nu), dtype=torch.float32, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+
+        def grads(gs):
+            return (torch.zeros((gs.n, 3), device=dev), torch.zeros((gs.n, 3), device=dev),
+                    torch.zeros((gs.n, 4), device=dev), torch.zeros((gs.n, gs.channels), device=dev))
+
+        self.g_ref = grads(ref)
+        self.g_mbc = [grads(m) for m in self.mbc]
+        self.d_coeff = torch.zeros((self.B, self.L, 3), dtype=torch.float32, device=dev)
+
+    def set_batch(self, views=None, coeff=None, meas=None) -> None:
+        for dst, src in ((self.views, views), (self.coeff, coeff), (self.meas, meas)):
+            if src is not None:
+                dst.copy_(src.reshape(dst.shape), non_blocking=True)
+
+    def desc(self, use_graph: bool = False, tune_cache: Optional[bytes] = None) -> "_lib.PmfBatchDesc":
+        d = _lib.PmfBatchDesc()
+        d.grid, d.det, d.dtype = _grid(self.grid), _det(self.det), _DT[self.dtype]
+        d.batch, d.loss_kind, d.levels = self.B, self.kind, self.L
+        d.ref = self.ref.c_struct()
+        for l, m in enumerate(self.mbc):
+            d.mbc[l] = m.c_struct()
+            for k in range(4):
+                d.d_mbc[l][k] = self.g_mbc[l][k].data_ptr()
+        for k in range(4):
+            d.d_ref[k] = self.g_ref[k].data_ptr()
+        d.views, d.coeff, d.meas = self.views.data_ptr(), self.coeff.data_ptr(), self.meas.data_ptr()
+        d.loss, d.d_coeff = self.loss.data_ptr(), self.d_coeff.data_ptr()
+        d.use_graph = 1 if use_graph else 0
+        d.tune_cache = tune_cache
+        return d
+
+
+class Plan(_StepBuffers):
+    """pmf_plan: one native forward + adjoint step over a batch of B views.
+
+    The caller-side buffers (batch inputs, loss, gradients) are allocated here
+    and handed to the plan once; `step()` copies a new batch into them (if
+    given) and enqueues the step.  With use_graph the step is captured into a
+    CUDA graph on the plan's own stream the first time and replayed after."""
+
+    def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
+                 dtype: torch.dtype = torch.bfloat16, kind: int = 2, use_graph: bool = False,
+                 tune_cache: Optional[str] = None):
+        self._h = None
+        super().__init__(grid, det, ref, mbc, batch, dtype, kind)
+        dev = ref.mean.device
+        self._cache = tune_cache.encode() if tune_cache else None  # kept alive with the descriptor
+        self._desc = self.desc(use_graph, self._cache)
+        self._stream = torch.cuda.Stream(device=dev) if use_graph else None
+        h = ct.c_void_p(0)
+        with torch.cuda.device(dev):
+            check(_lib.load().pmf_plan_create(ct.byref(self._desc), ct.byref(h)), "pmf_plan_create")
+        self._h = h
+
+    def step(self, views: Optional[torch.Tensor] = None, coeff: Optional[torch.Tensor] = None,
+             meas: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Copies the batch (when given) into the plan's inputs and enqueues one
+        step on torch's current stream; returns the device loss [1]."""
+        self.set_batch(views, coeff, meas)
+        L = _lib.load()
+        if self._stream is None:
+            check(L.pmf_plan_step(self._h, _stream()), "pmf_plan_step")
+        else:
+            cur = torch.cuda.current_stream()
+            self._stream.wait_stream(cur)
+            check(L.pmf_plan_step(self._h, ct.c_void_p(self._stream.cuda_stream)), "pmf_plan_step")
+            cur.wait_stream(self._stream)
+        return self.loss
+
+    def tensors(self) -> dict:
+        """Torch views of the plan's own device tensors (valid until close())."""
+        t = _lib.PmfPlanTensors()
+        check(_lib.load().pmf_plan_tensors_get(self._h, ct.byref(t)), "pmf_plan_tensors_get")
+        shape, n = _shape(self.grid)
+        gr = _det(self.det)
+        dev = self.ref.mean.device
+
+        def view(ptr, shp, dt):
+            if dt == torch.bfloat16:  # no bf16 typestr: view the 16-bit payload and reinterpret
+                raw = torch.as_tensor(_DevArray(ptr, shp, "<i2"), device=dev)
+                return raw.view(torch.bfloat16)
+            return torch.as_tensor(_DevArray(ptr, shp, _TYPESTR[dt]), device=dev)
+
+        return {"V": view(t.V, shape, self.dtype), "E": view(t.E, (self.L, 3) + shape, self.dtype),
+                "W": view(t.W, (self.B,) + shape, self.dtype),
+                "Y": view(t.Y, (self.B, gr.nv, gr.nu), torch.float32),
+                "dY": view(t.dY, (self.B, gr.nv, gr.nu), torch.float32),
+                "dW": view(t.dW, (self.B,) + shape, torch.float32), "dV": view(t.dV, shape, torch.float32),
+                "dE": view(t.dE, (self.L, 3) + shape, torch.float32)}
+
+    def launch_forms(self):
+        a, b = ct.c_int32(0), ct.c_int32(0)
+        check(_lib.load().pmf_plan_launch_forms(self._h, ct.byref(a), ct.byref(b)), "pmf_plan_launch_forms")
+        return int(a.value), int(b.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().pmf_plan_destroy(self._h)
+            self._h = ct.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pmf_autotune(grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int, cache_path: str,
+                 dtype: torch.dtype = torch.bfloat16, kind: int = 2, views=None, coeff=None, meas=None) -> None:
+    """Times the projector's launch forms on this configuration (and batch, if
+    given) and records the fastest in cache_path, which
+    Plan(..., tune_cache=cache_path) reads back."""
+    buf = _StepBuffers(grid, det, ref, mbc, batch, dtype, kind)
+    buf.set_batch(views, coeff, meas)
+    d = buf.desc(False, None)
+    with torch.cuda.device(ref.mean.device):
+        check(_lib.load().pmf_autotune(ct.byref(d), str(cache_path).encode()), "pmf_autotune")
+
+
+autotune = pmf_autotune

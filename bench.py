@@ -424,6 +424,26 @@ def run_native(a):
             tg = float(tt.item())
         variants[f"graph_replay_{a.dtype}"] = round(B * a.steps * world / tg, 3)
         del gstep
+        # the native plan (C++ step, captured into a CUDA graph on its own stream)
+        plan = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind, use_graph=True)
+        for k in range(2):
+            plan.step(*batch(k))
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+        g0.record(stream)
+        for k in range(a.steps):
+            plan.step(*batch(a.warmup + k))
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tg = g0.elapsed_time(g1) / 1e3
+        if world > 1:
+            tt = torch.tensor([tg], device="cuda")
+            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+            tg = float(tt.item())
+        variants[f"native_plan_graph_{a.dtype}"] = round(B * a.steps * world / tg, 3)
+        plan.close()
+        del plan
         from paper_2503_22139_gb300.pipeline import PlainPerProjection
         main_dt = a.dtype
         del step

@@ -117,14 +117,33 @@ __device__ __forceinline__ float vox_or_zero(const T* vol, const GridD& g, int i
     return in ? Store<T>::ld(vol, ((int64_t)k * g.ny + j) * g.nx + i) : 0.0f;
 }
 
+// The 8 corners of cell (i0,j0,k0), c[dx + 2 dy + 4 dz], zero outside the
+// grid.  Cells with all corners inside (nearly all) take one bounds test and
+// one base address; the values are the same either way.
+template <typename T>
+__device__ __forceinline__ void corners8(const T* vol, const GridD& g, int i0, int j0, int k0, float c[8]) {
+    if ((unsigned)i0 < (unsigned)(g.nx - 1) && (unsigned)j0 < (unsigned)(g.ny - 1) &&
+        (unsigned)k0 < (unsigned)(g.nz - 1)) {
+        const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+        const T* p = vol + ((int64_t)k0 * g.ny + j0) * g.nx + i0;
+        c[0] = Store<T>::ld(p, 0); c[1] = Store<T>::ld(p, 1);
+        c[2] = Store<T>::ld(p, sy); c[3] = Store<T>::ld(p, sy + 1);
+        c[4] = Store<T>::ld(p, sz); c[5] = Store<T>::ld(p, sz + 1);
+        c[6] = Store<T>::ld(p, sz + sy); c[7] = Store<T>::ld(p, sz + sy + 1);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++) c[q] = vox_or_zero(vol, g, i0 + (q & 1), j0 + ((q >> 1) & 1), k0 + (q >> 2));
+    }
+}
+
 // Zero-padded trilinear interpolation at cell (i0,j0,k0) with fractions f.
 template <typename T>
 __device__ __forceinline__ float trilin_cell(const T* vol, const GridD& g, int i0, int j0, int k0, float fx,
                                              float fy, float fz) {
-    float c000 = vox_or_zero(vol, g, i0, j0, k0), c100 = vox_or_zero(vol, g, i0 + 1, j0, k0);
-    float c010 = vox_or_zero(vol, g, i0, j0 + 1, k0), c110 = vox_or_zero(vol, g, i0 + 1, j0 + 1, k0);
-    float c001 = vox_or_zero(vol, g, i0, j0, k0 + 1), c101 = vox_or_zero(vol, g, i0 + 1, j0, k0 + 1);
-    float c011 = vox_or_zero(vol, g, i0, j0 + 1, k0 + 1), c111 = vox_or_zero(vol, g, i0 + 1, j0 + 1, k0 + 1);
+    float c[8];
+    corners8(vol, g, i0, j0, k0, c);
+    const float c000 = c[0], c100 = c[1], c010 = c[2], c110 = c[3], c001 = c[4], c101 = c[5], c011 = c[6],
+                c111 = c[7];
     float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
     float a01 = fmaf(fx, c101 - c001, c001), a11 = fmaf(fx, c111 - c011, c011);
     float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);

@@ -36,10 +36,10 @@ __device__ __forceinline__ Cell make_cell(int i, int j, int k, float tx, float t
 template <typename T>
 __device__ __forceinline__ float trilin_grad(const T* vol, const GridD& g, const Cell& c, float& gx, float& gy,
                                              float& gz) {
-    float v000 = vox_or_zero(vol, g, c.i0, c.j0, c.k0), v100 = vox_or_zero(vol, g, c.i0 + 1, c.j0, c.k0);
-    float v010 = vox_or_zero(vol, g, c.i0, c.j0 + 1, c.k0), v110 = vox_or_zero(vol, g, c.i0 + 1, c.j0 + 1, c.k0);
-    float v001 = vox_or_zero(vol, g, c.i0, c.j0, c.k0 + 1), v101 = vox_or_zero(vol, g, c.i0 + 1, c.j0, c.k0 + 1);
-    float v011 = vox_or_zero(vol, g, c.i0, c.j0 + 1, c.k0 + 1), v111 = vox_or_zero(vol, g, c.i0 + 1, c.j0 + 1, c.k0 + 1);
+    float cv[8];
+    corners8(vol, g, c.i0, c.j0, c.k0, cv);
+    const float v000 = cv[0], v100 = cv[1], v010 = cv[2], v110 = cv[3], v001 = cv[4], v101 = cv[5], v011 = cv[6],
+                v111 = cv[7];
     float a00 = fmaf(c.fx, v100 - v000, v000), a10 = fmaf(c.fx, v110 - v010, v010);
     float a01 = fmaf(c.fx, v101 - v001, v001), a11 = fmaf(c.fx, v111 - v011, v011);
     float b0 = fmaf(c.fy, a10 - a00, a00), b1 = fmaf(c.fy, a11 - a01, a01);

@@ -136,18 +136,23 @@ __device__ __forceinline__ void corners8(const T* vol, const GridD& g, int i0, i
     }
 }
 
-// Zero-padded trilinear interpolation at cell (i0,j0,k0) with fractions f.
-template <typename T>
-__device__ __forceinline__ float trilin_cell(const T* vol, const GridD& g, int i0, int j0, int k0, float fx,
-                                             float fy, float fz) {
-    float c[8];
-    corners8(vol, g, i0, j0, k0, c);
+// Trilinear blend of 8 corners c[dx + 2 dy + 4 dz] with fractions f.
+__device__ __forceinline__ float trilin8(const float c[8], float fx, float fy, float fz) {
     const float c000 = c[0], c100 = c[1], c010 = c[2], c110 = c[3], c001 = c[4], c101 = c[5], c011 = c[6],
                 c111 = c[7];
     float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
     float a01 = fmaf(fx, c101 - c001, c001), a11 = fmaf(fx, c111 - c011, c011);
     float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
     return fmaf(fz, b1 - b0, b0);
+}
+
+// Zero-padded trilinear interpolation at cell (i0,j0,k0) with fractions f.
+template <typename T>
+__device__ __forceinline__ float trilin_cell(const T* vol, const GridD& g, int i0, int j0, int k0, float fx,
+                                             float fy, float fz) {
+    float c[8];
+    corners8(vol, g, i0, j0, k0, c);
+    return trilin8(c, fx, fy, fz);
 }
 
 // Split a small offset t (in voxels) into floor and fraction exactly.

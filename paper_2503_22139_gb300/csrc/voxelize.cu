@@ -208,12 +208,14 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
     __shared__ float sm[10][kRenderThreads];
     __shared__ float sv[C][kRenderThreads];
     __shared__ unsigned sidx[kRenderThreads];
+    __shared__ unsigned socc[kRenderThreads];  // octants of the tile each staged Gaussian's box touches
     __shared__ int scount;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t t = blockIdx.x;
     const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((int64_t)ntx * nty));
-    const int ix = tx * kTile + (tid & 7), iy = ty * kTile + ((tid >> 3) & 7);
-    const int iz0 = tz * kTile + (tid >> 6), iz1 = iz0 + 4;
+    // warp w takes octant w of the 8^3 tile (a 4^3 cube); each lane two voxels
+    const int ix = tx * kTile + 4 * (warp & 1) + (lane & 3), iy = ty * kTile + 4 * ((warp >> 1) & 1) + ((lane >> 2) & 3);
+    const int iz0 = tz * kTile + 4 * (warp >> 2) + (lane >> 4), iz1 = iz0 + 2;
     const float cx = centre(ix, g.nx, g.vx), cy = centre(iy, g.ny, g.vy);
     const float cz0 = centre(iz0, g.nz, g.vz), cz1 = centre(iz1, g.nz, g.vz);
 
@@ -269,9 +271,25 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
             for (int f = 0; f < 10; f++) sm[f][tid] = w.prm[(int64_t)f * n + gi];
 #pragma unroll
             for (int c = 0; c < C; c++) sv[c][tid] = __ldg(G.value + (int64_t)gi * C + c) * scale;
+            // which halves of the tile the box reaches on each axis, then the octants
+            const int o[3] = {x0, y0, z0};
+            unsigned half[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const int lo = w.box[(int64_t)a * n + gi], hi = w.box[(int64_t)(3 + a) * n + gi];
+                half[a] = (lo <= o[a] + 3 && hi >= o[a] ? 1u : 0u) | (lo <= o[a] + 7 && hi >= o[a] + 4 ? 2u : 0u);
+            }
+            unsigned occ = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (((half[0] >> (q & 1)) & (half[1] >> ((q >> 1) & 1)) & (half[2] >> (q >> 2))) & 1u) occ |= 1u << q;
+            socc[tid] = occ;
         }
         __syncthreads();
         for (int j = 0; j < m; j++) {
+            // a Gaussian whose voxel box misses this warp's octant adds nothing
+            // there: its q exceeds kappa^2 outside the box (warp-uniform skip)
+            if (!((socc[j] >> warp) & 1u)) continue;
             const float dx = cx - sm[0][j], dy = cy - sm[1][j];
             const float a00 = sm[3][j], a11 = sm[4][j], a22 = sm[5][j], b01 = sm[6][j], b02 = sm[7][j],
                         b12 = sm[8][j], k2 = sm[9][j];

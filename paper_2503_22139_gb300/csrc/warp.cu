@@ -31,13 +31,9 @@ __device__ __forceinline__ Cell make_cell(int i, int j, int k, float tx, float t
     return c;
 }
 
-// Trilinear value and gradient (with respect to the continuous index) of vol
-// at a cell; zero padding outside the grid.
-template <typename T>
-__device__ __forceinline__ float trilin_grad(const T* vol, const GridD& g, const Cell& c, float& gx, float& gy,
-                                             float& gz) {
-    float cv[8];
-    corners8(vol, g, c.i0, c.j0, c.k0, cv);
+// Trilinear value and gradient (with respect to the continuous index) from
+// the 8 corners of a cell.
+__device__ __forceinline__ float trilin8_grad(const float cv[8], const Cell& c, float& gx, float& gy, float& gz) {
     const float v000 = cv[0], v100 = cv[1], v010 = cv[2], v110 = cv[3], v001 = cv[4], v101 = cv[5], v011 = cv[6],
                 v111 = cv[7];
     float a00 = fmaf(c.fx, v100 - v000, v000), a10 = fmaf(c.fx, v110 - v010, v010);
@@ -49,6 +45,15 @@ __device__ __forceinline__ float trilin_grad(const T* vol, const GridD& g, const
     float ex1 = fmaf(c.fy, (v111 - v011) - (v101 - v001), v101 - v001);
     gx = fmaf(c.fz, ex1 - ex0, ex0);
     return fmaf(c.fz, b1 - b0, b0);
+}
+
+// The same at a cell of vol, zero padding outside the grid.
+template <typename T>
+__device__ __forceinline__ float trilin_grad(const T* vol, const GridD& g, const Cell& c, float& gx, float& gy,
+                                             float& gz) {
+    float cv[8];
+    corners8(vol, g, c.i0, c.j0, c.k0, cv);
+    return trilin8_grad(cv, c, gx, gy, gz);
 }
 
 __device__ __forceinline__ void scatter_cell(unsigned long long* acc, const GridD& g, const Cell& c, float val,
@@ -360,14 +365,46 @@ __device__ __forceinline__ TileIdx tile_idx(const GridD& g) {
 
 __device__ __forceinline__ int round_small_i(float x) { return __float_as_int(x + 12582912.0f) - 0x4b400000; }
 
+// The tile's box of ref (the 32x4x4 tile plus a kHalo-voxel halo, zero outside
+// the grid) staged in shared memory: displaced samples that stay inside it
+// read their corners there instead of through L1/L2.
+template <typename T>
+__device__ __forceinline__ void stage_halo(const T* __restrict__ ref, const GridD& g, int bx0, int by0, int bz0,
+                                           float* sv) {
+    for (int i = threadIdx.x; i < kBoxN; i += blockDim.x) {
+        const int x = bx0 + i % kBX, y = by0 + (i / kBX) % kBY, z = bz0 + i / (kBX * kBY);
+        const bool in = (unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz;
+        sv[i] = in ? Store<T>::ld(ref, ((int64_t)z * g.ny + y) * g.nx + x) : 0.0f;
+    }
+}
+
+// Corners of cell c from the staged box (box-relative cell (rx, ry, rz)) when
+// the whole cell is inside it, else from global memory; same values either way.
+template <typename T>
+__device__ __forceinline__ void corners8_halo(const float* sv, int rx, int ry, int rz, const T* ref, const GridD& g,
+                                              const Cell& c, float cv[8]) {
+    if ((unsigned)rx < (unsigned)(kBX - 1) && (unsigned)ry < (unsigned)(kBY - 1) && (unsigned)rz < (unsigned)(kBZ - 1)) {
+        const float* q = sv + (rz * kBY + ry) * kBX + rx;
+        cv[0] = q[0]; cv[1] = q[1]; cv[2] = q[kBX]; cv[3] = q[kBX + 1];
+        cv[4] = q[kBX * kBY]; cv[5] = q[kBX * kBY + 1]; cv[6] = q[kBX * kBY + kBX]; cv[7] = q[kBX * kBY + kBX + 1];
+    } else {
+        corners8(ref, g, c.i0, c.j0, c.k0, cv);
+    }
+}
+
 template <typename T, int L>
 __global__ void __launch_bounds__(256) k_wc_fwd_tile(GridD g, int P, const T* __restrict__ ref,
                                                      const T* __restrict__ E, const float* __restrict__ w,
                                                      T* __restrict__ W) {
-    extern __shared__ float sw[];  // [P][L][3]
-    for (int i = threadIdx.x; i < P * L * 3; i += 256) sw[i] = w[i];
-    __syncthreads();
+    extern __shared__ float smem_f[];
+    const int PL3 = P * L * 3;
+    float* sw = smem_f;                          // [P][L][3]
+    float* sv = smem_f + ((PL3 + 3) & ~3);       // [kBZ][kBY][kBX] staged ref
+    for (int i = threadIdx.x; i < PL3; i += 256) sw[i] = w[i];
     const TileIdx t = tile_idx(g);
+    const int bx0 = t.x0 - kHalo, by0 = t.y0 - kHalo, bz0 = t.z0 - kHalo;
+    stage_halo(ref, g, bx0, by0, bz0, sv);
+    __syncthreads();
     if (t.x >= g.nx || t.y >= g.ny) return;
     const int64_t N = g.n;
 #pragma unroll
@@ -391,7 +428,9 @@ __global__ void __launch_bounds__(256) k_wc_fwd_tile(GridD g, int P, const T* __
                 d[a] = acc;
             }
             const Cell cl = make_cell(t.x, t.y, z, d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
-            Store<T>::st(W, (int64_t)p * N + v, trilin_cell(ref, g, cl.i0, cl.j0, cl.k0, cl.fx, cl.fy, cl.fz));
+            float cv[8];
+            corners8_halo(sv, cl.i0 - bx0, cl.j0 - by0, cl.k0 - bz0, ref, g, cl, cv);
+            Store<T>::st(W, (int64_t)p * N + v, trilin8(cv, cl.fx, cl.fy, cl.fz));
         }
     }
 }
@@ -413,8 +452,9 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
     extern __shared__ float smem[];
     const int PL3 = P * L * 3;
     float* sw = smem;                              // [P][L][3]
-    int* box = (int*)(smem + ((PL3 + 3) & ~3));    // [kBZ][kBY][kBX]
-    float* swarp = (float*)(box + kBoxN);          // [8 warps][P][L][3]
+    int* box = (int*)(smem + ((PL3 + 3) & ~3));    // [kBZ][kBY][kBX] fixed-point dV
+    float* sv = (float*)(box + kBoxN);             // [kBZ][kBY][kBX] staged ref
+    float* swarp = sv + kBoxN;                     // [8 warps][P][L][3]
     __shared__ float red_sum[8];
     __shared__ unsigned red_max;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -423,6 +463,7 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
     for (int i = threadIdx.x; i < 8 * PL3; i += 256) swarp[i] = 0.f;
     if (threadIdx.x == 0) red_max = 0u;
     const TileIdx t = tile_idx(g);
+    stage_halo(ref, g, t.x0 - kHalo, t.y0 - kHalo, t.z0 - kHalo, sv);
     const int64_t N = g.n;
     bool in[2];
     int64_t v[2];
@@ -490,8 +531,10 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
                 d[a] = acc_;
             }
             const Cell cl = make_cell(t.x, t.y, t.z[h], d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
-            float gx, gy, gz;
-            trilin_grad(ref, g, cl, gx, gy, gz);
+            const int rx = cl.i0 - bx0, ry = cl.j0 - by0, rz = cl.k0 - bz0;
+            float gx, gy, gz, cv[8];
+            corners8_halo(sv, rx, ry, rz, ref, g, cl, cv);
+            trilin8_grad(cv, cl, gx, gy, gz);
             const float gd[3] = {gw * gx * g.ivx, gw * gy * g.ivy, gw * gz * g.ivz};
 #pragma unroll
             for (int l = 0; l < L; l++)
@@ -501,7 +544,6 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
                     cw[l][a] = fmaf(gd[a], e[h][l][a], cw[l][a]);
                 }
             // V's adjoint: 8 trilinear corners
-            const int rx = cl.i0 - bx0, ry = cl.j0 - by0, rz = cl.k0 - bz0;
             const float wx[2] = {1.f - cl.fx, cl.fx}, wy[2] = {1.f - cl.fy, cl.fy}, wz[2] = {1.f - cl.fz, cl.fz};
             if ((unsigned)rx < (unsigned)(kBX - 1) && (unsigned)ry < (unsigned)(kBY - 1) &&
                 (unsigned)rz < (unsigned)(kBZ - 1)) {
@@ -708,7 +750,7 @@ pmf_status warp_combine(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dt
     GridD g = make_grid(grid);
     cudaStream_t s = (cudaStream_t)stream;
     if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
-        const size_t smem = sizeof(float) * (size_t)P * L * 3;
+        const size_t smem = sizeof(float) * (size_t)((((P * L * 3) + 3) & ~3) + kBoxN);
         const unsigned nt = (unsigned)num_tiles(g);
         PMF_DISPATCH_DTYPE(dtype, T, {
             switch (L) {
@@ -759,7 +801,7 @@ pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf
         k_absmax<<<stream_blocks(g.n * P), kThreads, 0, s>>>(d_out, g.n * P, maxbits);
         if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
             const int PL3 = P * L * 3;
-            const size_t smem2 = sizeof(float) * (size_t)(((PL3 + 3) & ~3) + kBoxN + 8 * PL3);
+            const size_t smem2 = sizeof(float) * (size_t)(((PL3 + 3) & ~3) + 2 * kBoxN + 8 * PL3);
             const unsigned nt = (unsigned)num_tiles(g);
             PMF_DISPATCH_DTYPE(dtype, T, {
                 switch (L) {

@@ -5,9 +5,10 @@
 // truncation ellipsoid; count the 8x8x8 tiles it overlaps; (2) exclusive scan
 // of the per-tile counts; (3) fill per-tile Gaussian lists; (4) one CTA per
 // tile stages its list in shared memory and sums every entry at its 512 voxel
-// centres.  Sums are kept in 64-bit fixed point (scale 2^k with
-// G * max|value| * 2^k < 2^62), so the unordered list fill cannot change a bit
-// of the result.
+// centres.  Sums are exact integers at the scale 2^k with max|value| 2^k < 2^21:
+// each term is rounded once to an integer (magic-number add), a batch of at
+// most 256 terms is summed in 32 bits (< 2^29) and batches are added in 64
+// bits, so the unordered list fill cannot change a bit of the result.
 //
 // Backward: one CTA per Gaussian walks its voxel box, accumulates
 // sum_v dL/dout_c * e, and the moments S1 = sum w d, S2 = sum w d d^T
@@ -23,6 +24,18 @@ constexpr int kTile = 8;              // tile edge (voxels)
 constexpr int kRenderThreads = 256;   // 2 voxels per thread
 constexpr int kMaxC = 4;
 constexpr float kNegHalfLog2e = -0.72134752044448170368f;  // -log2(e)/2
+constexpr float kMagicF = 12582912.0f;  // 1.5 * 2^23: x + kMagicF rounds x to an integer for |x| < 2^22
+constexpr int kMagicI = 0x4b400000;     // its bit pattern
+
+// Scale exponent k with m 2^k < 2^21 (m = the largest |value|; 0 if m is 0 or
+// not finite).
+__device__ __forceinline__ int term_exponent(float m) {
+    if (!(m > 0.0f) || !isfinite(m)) return 0;
+    int e;
+    frexpf(m, &e);  // m < 2^e
+    const int k = 21 - e;
+    return k > 126 ? 126 : (k < -126 ? -126 : k);
+}
 
 struct VoxHeader {
     unsigned int max_abs_bits;  // max |value| over all Gaussians and channels (float bits)
@@ -222,7 +235,9 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
     const float maxabs = __uint_as_float(w.hdr->max_abs_bits);
     const bool bad = !isfinite(maxabs);  // a NaN or infinite value: the output is NaN
     if (bad && t == 0 && tid == 0) diag_count(PMF_DIAG_NONFINITE);
-    const int kexp = fixed_exponent(maxabs * (float)(G.n > 0 ? G.n : 1));
+    // every term |value e^{-q/2}| 2^k < 2^21, so it rounds with the magic add
+    // and a 256-term batch stays below 2^29 in 32 bits
+    const int kexp = term_exponent(maxabs);
     const float scale = ldexpf(1.0f, kexp), inv_scale = ldexpf(1.0f, -kexp);
 
     long long acc0[C], acc1[C];
@@ -286,6 +301,9 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
             socc[tid] = occ;
         }
         __syncthreads();
+        int p0[C], p1[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) { p0[c] = 0; p1[c] = 0; }
         for (int j = 0; j < m; j++) {
             // a Gaussian whose voxel box misses this warp's octant adds nothing
             // there: its q exceeds kappa^2 outside the box (warp-uniform skip)
@@ -299,14 +317,16 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
             if (q0 <= k2) {
                 const float e = exp2f(q0 * kNegHalfLog2e);
 #pragma unroll
-                for (int c = 0; c < C; c++) acc0[c] += __float2ll_rn(sv[c][j] * e);
+                for (int c = 0; c < C; c++) p0[c] += __float_as_int(fmaf(sv[c][j], e, kMagicF)) - kMagicI;
             }
             if (q1 <= k2) {
                 const float e = exp2f(q1 * kNegHalfLog2e);
 #pragma unroll
-                for (int c = 0; c < C; c++) acc1[c] += __float2ll_rn(sv[c][j] * e);
+                for (int c = 0; c < C; c++) p1[c] += __float_as_int(fmaf(sv[c][j], e, kMagicF)) - kMagicI;
             }
         }
+#pragma unroll
+        for (int c = 0; c < C; c++) { acc0[c] += p0[c]; acc1[c] += p1[c]; }
     }
     const int64_t N = g.n;
     if (ix < g.nx && iy < g.ny) {
@@ -392,25 +412,35 @@ __device__ __forceinline__ void warp_moments(const pmf_gaussians& G, int64_t i, 
         const float dz = centre(z, g.nz, g.vz) - s.mu[2];
         int xlo, xhi;
         if (!row_span(s, k2, dy, dz, g, xlo, xhi)) continue;
-        const int64_t rowbase = ((int64_t)z * g.ny + y) * g.nx;
-        for (int x = xlo; x <= xhi; x++) {
-            const float dx = centre(x, g.nx, g.vx) - s.mu[0];
-            const float q = qform(dx, dy, dz, s.a00, s.a11, s.a22, s.b01, s.b02, s.b12);
-            if (!(q <= k2)) continue;
-            const float e = exp2f(q * kNegHalfLog2e);
-            const int64_t v = rowbase + x;
-            float sw = 0.f;
+        const float* drow = dout + ((int64_t)z * g.ny + y) * g.nx;
+        // four voxels per step: their upstream-gradient loads are issued
+        // together (the span lies inside the grid), then accumulated in x order
+        for (int x0 = xlo; x0 <= xhi; x0 += 4) {
+            float go[4][C];
 #pragma unroll
-            for (int c = 0; c < C; c++) {
-                const float go = __ldg(dout + c * N + v);
-                m.gv[c] = fmaf(go, e, m.gv[c]);
-                sw = fmaf(val[c], go, sw);
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int c = 0; c < C; c++) go[u][c] = x0 + u <= xhi ? __ldg(drow + c * N + x0 + u) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int x = x0 + u;
+                if (x > xhi) break;
+                const float dx = centre(x, g.nx, g.vx) - s.mu[0];
+                const float q = qform(dx, dy, dz, s.a00, s.a11, s.a22, s.b01, s.b02, s.b12);
+                if (!(q <= k2)) continue;
+                const float e = exp2f(q * kNegHalfLog2e);
+                float sw = 0.f;
+#pragma unroll
+                for (int c = 0; c < C; c++) {
+                    m.gv[c] = fmaf(go[u][c], e, m.gv[c]);
+                    sw = fmaf(val[c], go[u][c], sw);
+                }
+                const float wgt = sw * e;
+                m.s1[0] = fmaf(wgt, dx, m.s1[0]); m.s1[1] = fmaf(wgt, dy, m.s1[1]); m.s1[2] = fmaf(wgt, dz, m.s1[2]);
+                const float wx = wgt * dx, wy = wgt * dy;
+                m.s2[0] = fmaf(wx, dx, m.s2[0]); m.s2[1] = fmaf(wx, dy, m.s2[1]); m.s2[2] = fmaf(wx, dz, m.s2[2]);
+                m.s2[3] = fmaf(wy, dy, m.s2[3]); m.s2[4] = fmaf(wy, dz, m.s2[4]); m.s2[5] = fmaf(wgt * dz, dz, m.s2[5]);
             }
-            const float wgt = sw * e;
-            m.s1[0] = fmaf(wgt, dx, m.s1[0]); m.s1[1] = fmaf(wgt, dy, m.s1[1]); m.s1[2] = fmaf(wgt, dz, m.s1[2]);
-            const float wx = wgt * dx, wy = wgt * dy;
-            m.s2[0] = fmaf(wx, dx, m.s2[0]); m.s2[1] = fmaf(wx, dy, m.s2[1]); m.s2[2] = fmaf(wx, dz, m.s2[2]);
-            m.s2[3] = fmaf(wy, dy, m.s2[3]); m.s2[4] = fmaf(wy, dz, m.s2[4]); m.s2[5] = fmaf(wgt * dz, dz, m.s2[5]);
         }
     }
 }
@@ -466,7 +496,7 @@ __device__ void moments_to_grad(const GaussSetup& s, const float* r, int64_t i, 
 }
 
 template <int C>
-__global__ void __launch_bounds__(32 * kBwdWarps) k_vox_bwd(pmf_gaussians G, GridD g, int S,
+__global__ void __launch_bounds__(32 * kBwdWarps, 3) k_vox_bwd(pmf_gaussians G, GridD g, int S,
                                                             const float* __restrict__ dout, float* part,
                                                             float* d_mean, float* d_scale, float* d_quat,
                                                             float* d_value, int accumulate) {

@@ -89,6 +89,7 @@ class Workload:
     kappa: float
     measured: Optional[np.ndarray] = None  # [P,nv,nu] float32
     meta: dict = field(default_factory=dict)
+    gt: Optional[GaussianSet] = None       # ground-truth reference set (its projections are the targets)
 
     @property
     def p(self) -> int:
@@ -101,9 +102,10 @@ class Workload:
 
 def seeds_for(config: int) -> dict:
     """Seed plan: config k draws from 1000*(k+1) + {0: reference Gaussians,
-    1: MBC Gaussians, 2: temporal coefficients, 3: measured projections}."""
+    1: MBC Gaussians, 2: temporal coefficients, 3: smooth stand-in projections,
+    4: the ground-truth reference Gaussian set}."""
     base = 1000 * (config + 1)
-    return {"ref": base, "mbc": base + 1, "coeff": base + 2, "measured": base + 3}
+    return {"ref": base, "mbc": base + 1, "coeff": base + 2, "measured": base + 3, "gt": base + 4}
 
 
 def circular_views(p: int, sad: float, sdd: float, nu: int, nv: int,
@@ -253,7 +255,10 @@ def config1(p: int = 660, with_measured: bool = False, measured_for=None) -> Wor
     if with_measured:
         rng = np.random.default_rng(sd["measured"])
         meas = measured_projections(rng, p, det.nu, det.nv, 400.0)
-    return Workload("config1-200x200x100-100k-660views", grid, det, ref, mbc, views, coeff, 3.0, meas)
+    # a second draw of the reference recipe: the training target is its
+    # projections through the same forward model (same MBCs and coefficients)
+    gt = gaussian_set(np.random.default_rng(sd["gt"]), grid, 100_000, 0.5, 3.0)
+    return Workload("config1-200x200x100-100k-660views", grid, det, ref, mbc, views, coeff, 3.0, meas, gt=gt)
 
 
 def fd_subproblem(seed: int = 3000) -> Workload:

@@ -405,18 +405,24 @@ pmf_status pmf_plan_step(pmf_plan* plan, pmf_stream stream);
 
 pmf_status pmf_plan_tensors_get(const pmf_plan* plan, pmf_plan_tensors* out);
 
-/* Launch forms the plan uses: proj and backproj are 0 for one CTA per (view,
- * tile), k > 0 for a persistent launch of k CTAs per SM.  Results are
- * bit-identical for every choice. */
+/* Launch shapes the plan uses for the projector (proj) and its adjoint
+ * (backproj), each int32[3] = {form, chunk, rays}: form 0 is one CTA per
+ * (view, pixel tile) and k > 0 a persistent launch of k CTAs per SM; chunk
+ * (16 or 32) is the number of samples per staged voxel brick along the rays;
+ * rays (128 or 256) the rays per CTA.  Defaults {0, 32, 256}, or the
+ * autotuner's choice from tune_cache.  Forms give bit-identical results;
+ * chunk and rays move the last bits (chunk anchors, per-CTA scales). */
 pmf_status pmf_plan_launch_forms(const pmf_plan* plan, int32_t* proj, int32_t* backproj);
 
 /* Synchronizes the device, frees the plan's memory and graph.  NULL is a no-op. */
 pmf_status pmf_plan_destroy(pmf_plan* plan);
 
-/* Times each launch form of the projector and its adjoint on desc's data
- * (a temporary plan; several steps, CUDA events) and records the fastest in
- * `cache_path` under a key made of the device name, SM count, grid,
- * detector, batch and dtype (other keys in the file are kept).  Synchronizes. */
+/* Times the projector and its adjoint over launch shapes (forms 0, 1, 2, 4
+ * CTAs per 1024 SM threads; chunks of 16 and 32 samples; 128 and 256 rays per
+ * CTA) on desc's data (a temporary plan; CUDA events, best of 3 after a
+ * warm-up) and records the fastest of each in `cache_path` under a key made
+ * of the device name, SM count, grid, detector, batch, levels and dtype
+ * (other keys in the file are kept).  Synchronizes. */
 pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path);
 
 #ifdef __cplusplus

@@ -36,7 +36,7 @@ struct pmf_plan {
     size_t wc_bytes = 0;
     void* loss_ws = nullptr;
     size_t loss_bytes = 0;
-    int proj_form = 0, bp_form = 0;
+    pmf::MarchShape fp, bp;  // launch shapes of the projector and its adjoint
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -110,14 +110,18 @@ std::vector<std::string> read_lines(const char* path) {
     return out;
 }
 
-// "<key> proj=<int> backproj=<int>"
-bool cache_lookup(const char* path, const std::string& key, int& proj, int& bp) {
+bool valid(const MarchShape& m) {
+    return m.form >= 0 && m.form <= 16 && (m.chunk == 16 || m.chunk == 32) && (m.rays == 128 || m.rays == 256);
+}
+
+// "<key> proj=<form>,<chunk>,<rays> backproj=<form>,<chunk>,<rays>"
+bool cache_lookup(const char* path, const std::string& key, MarchShape& fp, MarchShape& bp) {
     for (const std::string& s : read_lines(path)) {
         if (s.compare(0, key.size(), key) != 0 || s.size() <= key.size() || s[key.size()] != ' ') continue;
-        int a, b;
-        if (sscanf(s.c_str() + key.size(), " proj=%d backproj=%d", &a, &b) == 2 && a >= 0 && a <= 16 && b >= 0 &&
-            b <= 16) {
-            proj = a;
+        MarchShape a, b;
+        if (sscanf(s.c_str() + key.size(), " proj=%d,%d,%d backproj=%d,%d,%d", &a.form, &a.chunk, &a.rays, &b.form,
+                   &b.chunk, &b.rays) == 6 && valid(a) && valid(b)) {
+            fp = a;
             bp = b;
             return true;
         }
@@ -125,7 +129,7 @@ bool cache_lookup(const char* path, const std::string& key, int& proj, int& bp) 
     return false;
 }
 
-pmf_status cache_store(const char* path, const std::string& key, int proj, int bp) {
+pmf_status cache_store(const char* path, const std::string& key, const MarchShape& fp, const MarchShape& bp) {
     std::vector<std::string> lines = read_lines(path);
     std::string tmp = std::string(path) + ".tmp";
     FILE* f = fopen(tmp.c_str(), "w");
@@ -133,7 +137,8 @@ pmf_status cache_store(const char* path, const std::string& key, int proj, int b
     for (const std::string& s : lines)
         if (!(s.compare(0, key.size(), key) == 0 && s.size() > key.size() && s[key.size()] == ' '))
             fprintf(f, "%s\n", s.c_str());
-    fprintf(f, "%s proj=%d backproj=%d\n", key.c_str(), proj, bp);
+    fprintf(f, "%s proj=%d,%d,%d backproj=%d,%d,%d\n", key.c_str(), fp.form, fp.chunk, fp.rays, bp.form, bp.chunk,
+            bp.rays);
     if (fclose(f) != 0 || rename(tmp.c_str(), path) != 0) return set_error(PMF_EINVAL, "cannot write %s", path);
     return PMF_OK;
 }
@@ -153,13 +158,13 @@ pmf_status cache_store(const char* path, const std::string& key, int proj, int b
 pmf_status plan_project(pmf_plan* p, cudaStream_t s) {
     const pmf_batch_desc& d = p->d;
     pmf_project_item it{d.grid, d.det, p->B, d.views, p->W, p->N, p->Y};
-    return project_launch(it, d.dtype, p->proj_form, s);
+    return project_launch(it, d.dtype, p->fp, s);
 }
 
 pmf_status plan_backproject(pmf_plan* p, cudaStream_t s) {
     const pmf_batch_desc& d = p->d;
     pmf_backproject_item it{d.grid, d.det, p->B, d.views, p->dY, p->dW, p->N};
-    return backproject_launch(it, 0, p->bp_ws, p->bp_bytes, p->bp_form, s);
+    return backproject_launch(it, 0, p->bp_ws, p->bp_bytes, p->bp, s);
 }
 
 pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
@@ -290,13 +295,7 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     p->bp_ws = take();
     p->wc_ws = take();
     p->loss_ws = take();
-    if (desc->tune_cache) {
-        int a, b;
-        if (cache_lookup(desc->tune_cache, tune_key(d), a, b)) {
-            p->proj_form = a;
-            p->bp_form = b;
-        }
-    }
+    if (desc->tune_cache) cache_lookup(desc->tune_cache, tune_key(d), p->fp, p->bp);
     *out = p;
     return PMF_OK;
 }
@@ -384,8 +383,8 @@ pmf_status pmf_plan_tensors_get(const pmf_plan* p, pmf_plan_tensors* out) {
 
 pmf_status pmf_plan_launch_forms(const pmf_plan* p, int32_t* proj, int32_t* backproj) {
     PMF_REQUIRE(p != nullptr && proj != nullptr && backproj != nullptr, "null pointer");
-    *proj = p->proj_form;
-    *backproj = p->bp_form;
+    proj[0] = p->fp.form; proj[1] = p->fp.chunk; proj[2] = p->fp.rays;
+    backproj[0] = p->bp.form; backproj[1] = p->bp.chunk; backproj[2] = p->bp.rays;
     return PMF_OK;
 }
 
@@ -407,19 +406,26 @@ pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path) {
         return set_error(PMF_ECUDA, "cudaStreamCreate failed");
     }
     pmf_status st = enqueue_step(p, s);  // fills W and dY
-    const int forms[] = {0, 1, 2, 3, 4};
+    // every (form, chunk, rays): forms 0 (grid) and 2-4 persistent CTAs per
+    // 1024 threads of an SM, bricks of 16 or 32 samples, 128 or 256 rays
     float best_fp = 3.0e38f, best_bp = 3.0e38f;
-    int fp = 0, bp = 0;
-    for (int f : forms) {
-        if (st != PMF_OK) break;
-        p->proj_form = f;
-        float t = time_ms(s, 3, plan_project, p, st);
-        if (st == PMF_OK && t < best_fp) { best_fp = t; fp = f; }
-        if (st != PMF_OK) break;
-        p->bp_form = f;
-        t = time_ms(s, 3, plan_backproject, p, st);
-        if (st == PMF_OK && t < best_bp) { best_bp = t; bp = f; }
-    }
+    MarchShape fp, bp;
+    for (int chunk : {32, 16})
+        for (int rays : {256, 128})
+            for (int form : {0, 1, 2, 4}) {
+                if (st != PMF_OK) break;
+                MarchShape m;
+                m.form = form == 0 ? 0 : form * (256 / rays);
+                m.chunk = chunk;
+                m.rays = rays;
+                p->fp = m;
+                float t = time_ms(s, 3, plan_project, p, st);
+                if (st == PMF_OK && t < best_fp) { best_fp = t; fp = m; }
+                if (st != PMF_OK) break;
+                p->bp = m;
+                t = time_ms(s, 3, plan_backproject, p, st);
+                if (st == PMF_OK && t < best_bp) { best_bp = t; bp = m; }
+            }
     if (st == PMF_OK && cudaStreamSynchronize(s) != cudaSuccess) st = set_error(PMF_ECUDA, "autotune failed");
     const std::string key = tune_key(d);
     cudaStreamDestroy(s);

@@ -58,11 +58,19 @@ pmf_status diag_voxelize(unsigned long long* out, int reset);
 pmf_status diag_project(unsigned long long* out, int reset);
 pmf_status diag_warp(unsigned long long* out, int reset);
 
-// Projector launch forms used by plans (0: one CTA per (view, tile); k > 0:
-// persistent, k CTAs per SM); results are identical across forms.
-pmf_status project_launch(const pmf_project_item& it, pmf_dtype dtype, int form, cudaStream_t s);
-pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes, int form,
-                              cudaStream_t s);
+// Launch shape of the ray marchers used by plans: form 0 is one CTA per
+// (view, pixel tile), k > 0 a persistent launch of k CTAs per SM; chunk (16 or
+// 32) is the number of samples per staged brick along the rays and rays (128
+// or 256) the rays per CTA.  Forms give identical results; chunk and rays
+// move the last bits (anchors, per-CTA fixed-point scale).
+struct MarchShape {
+    int form = 0;
+    int chunk = 32;
+    int rays = 256;
+};
+pmf_status project_launch(const pmf_project_item& it, pmf_dtype dtype, const MarchShape& sh, cudaStream_t s);
+pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes,
+                              const MarchShape& sh, cudaStream_t s);
 
 // ------------------------------------------------------- storage dtypes
 

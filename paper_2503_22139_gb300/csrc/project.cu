@@ -31,8 +31,9 @@
 namespace pmf {
 namespace {
 
-constexpr int kRay = 256;     // threads per CTA (16 x 16 pixels)
-constexpr int kChunk = 32;    // samples per chunk
+// Launch shapes (MarchShape): CH samples per chunk (the staged brick's length
+// along the rays) and RPB rays per CTA (a 16 x RPB/16 pixel tile, one ray per
+// thread).  The C entry points use 32 and 256; plans may pick others.
 constexpr int kBox = 6144;    // shared-memory box capacity (words)
 constexpr int kPitch = 33;    // box row pitch: x = lane (box width <= 32), odd against bank conflicts
 constexpr unsigned kFull = 0xffffffffu;
@@ -121,11 +122,12 @@ __device__ __forceinline__ float at(const Ray& r, int t, float jf, const float f
     return fmaf(jf, r.dh[t], fmaf(jf, r.dl[t], fb[t]));
 }
 
+template <int RPB>
 __device__ __forceinline__ void pixel_of(int tile, int ntu, int& a, int& b) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int tu = tile % ntu, tv = tile / ntu;
     a = tu * 16 + (w & 1) * 8 + (l & 7);
-    b = tv * 16 + (w >> 1) * 4 + (l >> 3);
+    b = tv * (RPB / 16) + (w >> 1) * 4 + (l >> 3);
 }
 
 template <typename T>
@@ -177,12 +179,13 @@ __device__ __forceinline__ void block_range(BoxState& bs, const Ray& r, bool act
     __syncthreads();
 }
 
-// This thread's sample range in the chunk starting at M0, its anchor, and its
-// contribution to the chunk's cell box (reduced per warp).
+// This thread's sample range in the chunk of CH samples starting at M0, its
+// anchor, and its contribution to the chunk's cell box (reduced per warp).
+template <int CH>
 __device__ __forceinline__ bool chunk_begin(BoxState& bs, int sel, const Ray& r, bool live, int M0, int& j0,
                                             int& j1, int ib[3], float fb[3]) {
     j0 = max(r.mlo, M0) - M0;
-    j1 = min(r.mhi, M0 + kChunk - 1) - M0;
+    j1 = min(r.mhi, M0 + CH - 1) - M0;
     const bool act = live && j0 <= j1;
     int clo[3] = {INT_MAX, INT_MAX, INT_MAX}, chi[3] = {INT_MIN, INT_MIN, INT_MIN};
     if (act) {
@@ -240,13 +243,13 @@ __device__ __forceinline__ Box read_box(const BoxState& bs, int sel) {
 // ----------------------------------------------------------------- forward
 
 // One 16x16 pixel tile of view p: every thread of the CTA calls it.
-template <typename T>
+template <typename T, int CH, int RPB>
 __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int ntu, float step,
                                              const pmf_view* __restrict__ views, const T* __restrict__ vol,
                                              int64_t vol_stride, float* __restrict__ proj, int p, int tile,
                                              float* box, BoxState& bs) {
     int a, b;
-    pixel_of(tile, ntu, a, b);
+    pixel_of<RPB>(tile, ntu, a, b);
     const bool in = a < nu && b < nv;
     Ray r;
     if (in) {
@@ -261,10 +264,10 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float acc = 0.0f;
     int sel = 0;
-    for (int M0 = Mlo; M0 <= Mhi; M0 += kChunk, sel ^= 1) {
+    for (int M0 = Mlo; M0 <= Mhi; M0 += CH, sel ^= 1) {
         int j0, j1, ib[3];
         float fb[3];
-        const bool act = chunk_begin(bs, sel, r, live, M0, j0, j1, ib, fb);
+        const bool act = chunk_begin<CH>(bs, sel, r, live, M0, j0, j1, ib, fb);
         __syncthreads();
         const Box bx = read_box(bs, sel);
         if (threadIdx.x == 0 && bx.vol > 0 && !bx.fits) diag_count(PMF_DIAG_PROJECT_BOX_FALLBACK);
@@ -276,7 +279,7 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
                 for (int zz = 0; zz < bx.bz; zz++) {
                     const int z = bx.lz + zz;
                     const bool zin = (unsigned)z < (unsigned)g.nz;
-                    for (int yy = warp; yy < bx.by; yy += kRay / 32) {
+                    for (int yy = warp; yy < bx.by; yy += RPB / 32) {
                         const int y = bx.ly + yy;
                         float val = 0.0f;
                         if (xin && zin && (unsigned)y < (unsigned)g.ny)
@@ -321,13 +324,13 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
     if (in) proj[((int64_t)p * nv + b) * nu + a] = step * acc;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kRay) k_project(GridD g, int nu, int nv, int ntu, float step,
+template <typename T, int CH, int RPB>
+__global__ void __launch_bounds__(RPB, 1024 / RPB) k_project(GridD g, int nu, int nv, int ntu, float step,
                                                   const pmf_view* __restrict__ views, const T* __restrict__ vol,
                                                   int64_t vol_stride, float* __restrict__ proj) {
     __shared__ float box[kBox];
     __shared__ BoxState bs;
-    project_tile<T>(g, nu, nv, ntu, step, views, vol, vol_stride, proj, blockIdx.y, blockIdx.x, box, bs);
+    project_tile<T, CH, RPB>(g, nu, nv, ntu, step, views, vol, vol_stride, proj, blockIdx.y, blockIdx.x, box, bs);
 }
 
 __global__ void k_absmax_f(const float* __restrict__ x, int64_t n, unsigned* out) { absmax_bits(x, n, out); }
@@ -456,11 +459,12 @@ __device__ __forceinline__ int exp_for(float bound, int bits) {
 // within each half this spreads the 16 simultaneous corner addresses over the
 // banks (about 3.6 conflict rounds per warp-wide atomic at the paper
 // geometry, against 4.3 for adjacent pixels staggered 4 samples apart).
+template <int RPB>
 __device__ __forceinline__ void pixel_of_spread(int tile, int ntu, int& a, int& b) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, g = l & 7, q = l >> 3;
     const int tu = tile % ntu, tv = tile / ntu;
     a = tu * 16 + 2 * g + (w & 1);
-    b = tv * 16 + (w >> 1) + 4 * q;
+    b = tv * (RPB / 16) + (w >> 1) + (RPB / 64) * q;
 }
 
 __device__ __forceinline__ int adjoint_phase() {
@@ -468,8 +472,9 @@ __device__ __forceinline__ int adjoint_phase() {
     return 3 * (l & 7) + 2 * (l >> 3);
 }
 
-// One 16x16 pixel tile of view p of the adjoint; box must be all zero on entry
-// and is all zero again on return.
+// One pixel tile of view p of the adjoint; box must be all zero on entry and is
+// all zero again on return.
+template <int CH, int RPB>
 __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv, int ntu, float step,
                                                  const pmf_view* __restrict__ views,
                                                  const float* __restrict__ dproj, int64_t vol_stride,
@@ -477,7 +482,7 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
                                                  float bound_mult, float samples_per_voxel, int p, int tile,
                                                  int* box, BoxState& bs, unsigned& sgmax, float* gsum) {
     int a, b;
-    pixel_of_spread(tile, ntu, a, b);
+    pixel_of_spread<RPB>(tile, ntu, a, b);
     const bool in = a < nu && b < nv;
     const float gy = in ? __ldg(dproj + ((int64_t)p * nv + b) * nu + a) : 0.0f;
     Ray r;
@@ -504,7 +509,7 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
     }
     __syncthreads();
     float gtot = 0.0f;
-    for (int i = 0; i < kRay / 32; i++) gtot += gsum[i];  // fixed order, same in every thread
+    for (int i = 0; i < RPB / 32; i++) gtot += gsum[i];  // fixed order, same in every thread
     const int kg = fixed_exponent(__uint_as_float(*maxbits) * bound_mult);
     const float bcta = gtot * step * samples_per_voxel;
     const float bray = __uint_as_float(sgmax) * step * samples_per_voxel;
@@ -519,10 +524,10 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
     const int Mlo = bs.range[0], Mhi = bs.range[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int sel = 0;
-    for (int M0 = Mlo; M0 <= Mhi; M0 += kChunk, sel ^= 1) {
+    for (int M0 = Mlo; M0 <= Mhi; M0 += CH, sel ^= 1) {
         int j0, j1, ib[3];
         float fb[3];
-        const bool act = chunk_begin(bs, sel, r, live, M0, j0, j1, ib, fb);
+        const bool act = chunk_begin<CH>(bs, sel, r, live, M0, j0, j1, ib, fb);
         __syncthreads();
         const Box bx = read_box(bs, sel);
         if (threadIdx.x == 0 && bx.vol > 0 && !bx.fits) diag_count(PMF_DIAG_BACKPROJECT_BOX_FALLBACK);
@@ -539,8 +544,8 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
                 // half-warp's simultaneous atomics land on different voxels
                 // and mostly different banks.
                 const int phase = adjoint_phase();
-                for (int k = 0; k < kChunk; k++) {
-                    const int j = (k + phase) & (kChunk - 1);
+                for (int k = 0; k < CH; k++) {
+                    const int j = (k + phase) & (CH - 1);
                     if (j < j0 || j > j1) continue;
                     const float jf = (float)j;
                     const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
@@ -570,7 +575,7 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
                 const bool xin = lane < bx.bx && (unsigned)x < (unsigned)g.nx;
                 for (int zz = 0; zz < bx.bz; zz++) {
                     const int z = bx.lz + zz;
-                    for (int yy = warp; yy < bx.by; yy += kRay / 32) {
+                    for (int yy = warp; yy < bx.by; yy += RPB / 32) {
                         const int i = (zz * bx.by + yy) * kPitch + lane;
                         if (lane >= bx.bx) continue;
                         const int v = box[i];
@@ -605,7 +610,8 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
     }
 }
 
-__global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, int ntu, float step,
+template <int CH, int RPB>
+__global__ void __launch_bounds__(RPB, 1024 / RPB) k_backproject(GridD g, int nu, int nv, int ntu, float step,
                                                       const pmf_view* __restrict__ views,
                                                       const float* __restrict__ dproj, int64_t vol_stride,
                                                       unsigned long long* __restrict__ acc, const unsigned* maxbits,
@@ -613,9 +619,9 @@ __global__ void __launch_bounds__(kRay) k_backproject(GridD g, int nu, int nv, i
     __shared__ int box[kBox];
     __shared__ BoxState bs;
     __shared__ unsigned sgmax;
-    __shared__ float gsum[kRay / 32];
-    for (int i = threadIdx.x; i < kBox; i += kRay) box[i] = 0;
-    backproject_tile(g, nu, nv, ntu, step, views, dproj, vol_stride, acc, maxbits, bound_mult, samples_per_voxel,
+    __shared__ float gsum[RPB / 32];
+    for (int i = threadIdx.x; i < kBox; i += RPB) box[i] = 0;
+    backproject_tile<CH, RPB>(g, nu, nv, ntu, step, views, dproj, vol_stride, acc, maxbits, bound_mult, samples_per_voxel,
                      blockIdx.y, blockIdx.x, box, bs, sgmax, gsum);
 }
 
@@ -669,29 +675,30 @@ __device__ __forceinline__ int find_item(const ProjBatch& B, int64_t w) {
     return i;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kRay) k_project_batched(const __grid_constant__ ProjBatch B) {
+template <typename T, int CH, int RPB>
+__global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched(const __grid_constant__ ProjBatch B) {
     __shared__ float box[kBox];
     __shared__ BoxState bs;
     for (int64_t w = blockIdx.x; w < B.total; w += gridDim.x) {
         const ProjItem& it = B.it[find_item(B, w)];
         const int64_t local = w - it.begin;
-        project_tile<T>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, (const T*)it.vol, it.vol_stride, it.proj,
+        project_tile<T, CH, RPB>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, (const T*)it.vol, it.vol_stride, it.proj,
                         (int)(local / it.ntiles), (int)(local % it.ntiles), box, bs);
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kRay) k_backproject_batched(const __grid_constant__ ProjBatch B) {
+template <int CH, int RPB>
+__global__ void __launch_bounds__(RPB, 1024 / RPB) k_backproject_batched(const __grid_constant__ ProjBatch B) {
     __shared__ int box[kBox];
     __shared__ BoxState bs;
     __shared__ unsigned sgmax;
-    __shared__ float gsum[kRay / 32];
-    for (int i = threadIdx.x; i < kBox; i += kRay) box[i] = 0;
+    __shared__ float gsum[RPB / 32];
+    for (int i = threadIdx.x; i < kBox; i += RPB) box[i] = 0;
     for (int64_t w = blockIdx.x; w < B.total; w += gridDim.x) {
         const ProjItem& it = B.it[find_item(B, w)];
         const int64_t local = w - it.begin;
-        backproject_tile(it.g, it.nu, it.nv, it.ntu, it.step, it.views, it.dproj, it.vol_stride, it.acc, it.maxbits,
+        backproject_tile<CH, RPB>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, it.dproj, it.vol_stride, it.acc, it.maxbits,
                          it.bound_mult, it.spv, (int)(local / it.ntiles), (int)(local % it.ntiles), box, bs, sgmax,
                          gsum);
         __syncthreads();
@@ -763,11 +770,11 @@ pmf_status check_proj(const pmf_grid* grid, const pmf_detector* det, int32_t P, 
 // single voxel: along the axis where the ray moves fastest in index space the
 // samples are at least h = step / (sqrt(3) v_max) apart, and a unit hat
 // function sampled at spacing h sums to at most 1/h + 1; each sample adds at
-// most 1 and a chunk holds kChunk samples.
-float chunk_samples_per_voxel(const pmf_grid* grid, float step) {
+// most 1 and a chunk holds `chunk` samples.
+float chunk_samples_per_voxel(const pmf_grid* grid, float step, int chunk) {
     const double vmax = fmax(fmax((double)grid->vx, (double)grid->vy), (double)grid->vz);
     const double s = sqrt(3.0) * vmax / (double)step + 1.0;
-    return (float)fmin(s, (double)kChunk);
+    return (float)fmin(s, (double)chunk);
 }
 
 int max_samples_per_voxel(const pmf_grid* grid, float step) {
@@ -777,9 +784,203 @@ int max_samples_per_voxel(const pmf_grid* grid, float step) {
     return (int)floor(diag / (double)step) + 1;
 }
 
+bool valid_shape(const MarchShape& sh) {
+    return (sh.chunk == 16 || sh.chunk == 32) && (sh.rays == 128 || sh.rays == 256) && sh.form >= 0 && sh.form <= 16;
+}
+
+// (chunk, rays) -> template instantiation
+#define PMF_DISPATCH_MARCH(sh, CH, RPB, ...)                                                                  \
+    switch ((sh).chunk * 1000 + (sh).rays) {                                                                \
+        case 32256: { constexpr int CH = 32, RPB = 256; __VA_ARGS__; break; }                               \
+        case 32128: { constexpr int CH = 32, RPB = 128; __VA_ARGS__; break; }                               \
+        case 16256: { constexpr int CH = 16, RPB = 256; __VA_ARGS__; break; }                               \
+        case 16128: { constexpr int CH = 16, RPB = 128; __VA_ARGS__; break; }                               \
+        default: return set_error(PMF_EINVAL, "unsupported march shape: chunk %d, rays %d", (sh).chunk, (sh).rays); \
+    }
+
+int tiles_v(int nv, int rays) { return (nv + rays / 16 - 1) / (rays / 16); }
+
+int num_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 152;
+    return sms > 0 ? sms : 152;
+}
+
+// Persistent CTAs: `ctas` if given, else as many as are resident at 256
+// threads x 4 per SM (<= 64 registers), i.e. 1024 threads per SM.
+unsigned persistent_ctas(int64_t total, unsigned ctas, int rays) {
+    const int64_t cap = ctas ? (int64_t)ctas : (int64_t)num_sms() * (1024 / rays);
+    return (unsigned)(total < cap ? (total > 0 ? total : 1) : cap);
+}
+
+pmf_status project_grid(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
+                        pmf_dtype dtype, const void* vol, int64_t vol_stride, float* proj, const MarchShape& sh,
+                        cudaStream_t s) {
+    pmf_status st = check_proj(grid, det, P, views);
+    if (st != PMF_OK) return st;
+    if ((st = validate_dtype(dtype)) != PMF_OK) return st;
+    if (P == 0) return PMF_OK;
+    PMF_REQUIRE(vol && proj, "null pointer");
+    PMF_REQUIRE(vol_stride >= 0, "vol_stride must be >= 0");
+    GridD g = make_grid(grid);
+    const int ntu = (det->nu + 15) / 16, ntv = tiles_v(det->nv, sh.rays);
+    dim3 gr((unsigned)(ntu * ntv), (unsigned)P);
+    PMF_DISPATCH_MARCH(sh, CH, RPB, PMF_DISPATCH_DTYPE(dtype, T, k_project<T, CH, RPB><<<gr, RPB, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, (const T*)vol, vol_stride, proj)));
+    return check_launch("conebeam_project");
+}
+
+pmf_status backproject_grid(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
+                            const float* d_proj, float* d_vol, int64_t vol_stride, int accumulate, void* ws,
+                            size_t ws_bytes, const MarchShape& sh, cudaStream_t s) {
+    pmf_status st = check_proj(grid, det, P, views);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(vol_stride >= 0, "vol_stride must be >= 0");
+    PMF_REQUIRE(d_vol != nullptr && (P == 0 || d_proj != nullptr), "null pointer");
+    size_t need;
+    conebeam_project_backward_workspace(grid, P, vol_stride, &need);
+    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
+    GridD g = make_grid(grid);
+    unsigned* maxbits = (unsigned*)ws;
+    unsigned long long* acc = (unsigned long long*)((char*)ws + align_up(256));
+    cudaMemsetAsync(ws, 0, need, s);
+    const int64_t Q = (int64_t)det->nu * det->nv;
+    const double rays = (double)Q * (vol_stride ? 1.0 : (double)P);
+    const float bound_mult = (float)((double)det->step_mm * rays * (double)max_samples_per_voxel(grid, det->step_mm));
+    const int64_t cells = vol_stride ? (int64_t)(P > 0 ? P - 1 : 0) * vol_stride + g.n : g.n;
+    if (P > 0) {
+        const int64_t nq = Q * P;
+        int64_t nb = (nq + 255) / 256;
+        k_absmax_f<<<(unsigned)(nb < 1024 ? nb : 1024), 256, 0, s>>>(d_proj, nq, maxbits);
+        const int ntu = (det->nu + 15) / 16, ntv = tiles_v(det->nv, sh.rays);
+        dim3 gr((unsigned)(ntu * ntv), (unsigned)P);
+        const float spv = chunk_samples_per_voxel(grid, det->step_mm, sh.chunk);
+        PMF_DISPATCH_MARCH(sh, CH, RPB, k_backproject<CH, RPB><<<gr, RPB, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, d_proj, vol_stride, acc, maxbits, bound_mult, spv));
+    }
+    int64_t nb = (cells + 255) / 256;
+    k_fixed_to_float_f<<<(unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks), 256, 0, s>>>(
+        acc, cells, maxbits, bound_mult, d_vol, accumulate);
+    return check_launch("conebeam_project_backward");
+}
+
+pmf_status fill_item(const pmf_project_item& in, int64_t begin, int rays, ProjItem& it) {
+    pmf_status st = check_proj(&in.grid, &in.det, in.P, in.views);
+    if (st != PMF_OK) return st;
+    PMF_REQUIRE(in.vol_stride >= 0, "vol_stride must be >= 0");
+    it = ProjItem{};
+    it.g = make_grid(&in.grid);
+    it.nu = in.det.nu; it.nv = in.det.nv;
+    it.ntu = (in.det.nu + 15) / 16;
+    it.ntiles = it.ntu * tiles_v(in.det.nv, rays);
+    it.P = in.P;
+    it.step = in.det.step_mm;
+    it.views = in.views;
+    it.vol_stride = in.vol_stride;
+    it.nq = (int64_t)in.det.nu * in.det.nv * in.P;
+    it.begin = begin;
+    return PMF_OK;
+}
+
+pmf_status project_batched_impl(int32_t n, const pmf_project_item* items, pmf_dtype dtype, const MarchShape& sh,
+                                unsigned ctas, cudaStream_t s) {
+    PMF_REQUIRE(n >= 0 && n <= kMaxItems, "n must be in [0, %d]", kMaxItems);
+    PMF_REQUIRE(n == 0 || items != nullptr, "items is null");
+    pmf_status st = validate_dtype(dtype);
+    if (st != PMF_OK) return st;
+    ProjBatch B{};
+    B.n = n;
+    int64_t total = 0;
+    for (int i = 0; i < n; i++) {
+        if ((st = fill_item(items[i], total, sh.rays, B.it[i])) != PMF_OK) return st;
+        PMF_REQUIRE(items[i].P == 0 || (items[i].vol && items[i].proj), "item %d: null pointer", i);
+        B.it[i].vol = items[i].vol;
+        B.it[i].proj = items[i].proj;
+        total += (int64_t)B.it[i].ntiles * items[i].P;
+    }
+    B.total = total;
+    if (total == 0) return PMF_OK;
+    const unsigned nc = persistent_ctas(total, ctas, sh.rays);
+    PMF_DISPATCH_MARCH(sh, CH, RPB, PMF_DISPATCH_DTYPE(dtype, T, k_project_batched<T, CH, RPB><<<nc, RPB, 0, s>>>(B)));
+    return check_launch("conebeam_project_batched");
+}
+
+size_t bp_item_bytes(const pmf_backproject_item& it) {
+    const int64_t n = (int64_t)it.grid.nx * it.grid.ny * it.grid.nz;
+    const int64_t cells = it.vol_stride ? (int64_t)(it.P > 0 ? it.P - 1 : 0) * it.vol_stride + n : n;
+    return align_up(256) + align_up(sizeof(unsigned long long) * (size_t)cells);
+}
+
+pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
+                                    size_t ws_bytes, const MarchShape& sh, unsigned ctas, cudaStream_t s) {
+    size_t need = 0;
+    pmf_status st = conebeam_project_backward_batched_workspace(n, items, &need);
+    if (st != PMF_OK) return st;
+    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
+    ProjBatch B{};
+    B.n = n;
+    int64_t total = 0, maxq = 0, maxcells = 0;
+    char* cur = (char*)ws;
+    for (int i = 0; i < n; i++) {
+        const pmf_backproject_item& in = items[i];
+        pmf_project_item tmp{in.grid, in.det, in.P, in.views, nullptr, in.vol_stride, nullptr};
+        if ((st = fill_item(tmp, total, sh.rays, B.it[i])) != PMF_OK) return st;
+        PMF_REQUIRE(in.d_vol != nullptr && (in.P == 0 || in.d_proj != nullptr), "item %d: null pointer", i);
+        ProjItem& it = B.it[i];
+        const int64_t Q = (int64_t)in.det.nu * in.det.nv;
+        const double rays = (double)Q * (in.vol_stride ? 1.0 : (double)in.P);
+        it.bound_mult = (float)((double)in.det.step_mm * rays * (double)max_samples_per_voxel(&in.grid, in.det.step_mm));
+        it.spv = chunk_samples_per_voxel(&in.grid, in.det.step_mm, sh.chunk);
+        it.dproj = in.d_proj;
+        it.dvol = in.d_vol;
+        it.maxbits = (unsigned*)cur;
+        it.acc = (unsigned long long*)(cur + align_up(256));
+        it.cells = in.vol_stride ? (int64_t)(in.P > 0 ? in.P - 1 : 0) * in.vol_stride + it.g.n : it.g.n;
+        cur += bp_item_bytes(in);
+        total += (int64_t)it.ntiles * in.P;
+        maxq = it.nq > maxq ? it.nq : maxq;
+        maxcells = it.cells > maxcells ? it.cells : maxcells;
+    }
+    B.total = total;
+    if (n == 0) return PMF_OK;
+    cudaMemsetAsync(ws, 0, need, s);
+    if (maxq > 0) {
+        const int64_t nb = (maxq + 255) / 256;
+        k_absmax_batched<<<dim3((unsigned)(nb < 1024 ? nb : 1024), (unsigned)n), 256, 0, s>>>(B);
+    }
+    if (total > 0) {
+        const unsigned nc = persistent_ctas(total, ctas, sh.rays);
+        PMF_DISPATCH_MARCH(sh, CH, RPB, k_backproject_batched<CH, RPB><<<nc, RPB, 0, s>>>(B));
+    }
+    const int64_t nc = (maxcells + 255) / 256;
+    k_fixed_to_float_batched<<<dim3((unsigned)(nc < 4 * kStreamBlocks ? nc : 4 * kStreamBlocks), (unsigned)n), 256, 0, s>>>(
+        B, accumulate);
+    return check_launch("conebeam_project_backward_batched");
+}
+
 }  // namespace
 
 PMF_DIAG_ACCESSOR(diag_project)
+
+// Launch shapes for plans: form 0 is one CTA per (view, tile), form k > 0 a
+// persistent launch of k CTAs per SM; chunk and rays pick the kernel variant.
+// Every form and shape runs the same per-sample arithmetic; the chunk length
+// moves the float-float anchors (results differ in the last bits) and the
+// rays per CTA the adjoint's per-CTA fixed-point scale (likewise).
+pmf_status project_launch(const pmf_project_item& it, pmf_dtype dtype, const MarchShape& sh, cudaStream_t s) {
+    if (!valid_shape(sh)) return set_error(PMF_EINVAL, "invalid march shape");
+    if (sh.form == 0)
+        return project_grid(&it.grid, &it.det, it.P, it.views, dtype, it.vol, it.vol_stride, it.proj, sh, s);
+    return project_batched_impl(1, &it, dtype, sh, (unsigned)(sh.form * num_sms()), s);
+}
+
+pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes,
+                              const MarchShape& sh, cudaStream_t s) {
+    if (!valid_shape(sh)) return set_error(PMF_EINVAL, "invalid march shape");
+    if (sh.form == 0)
+        return backproject_grid(&it.grid, &it.det, it.P, it.views, it.d_proj, it.d_vol, it.vol_stride, accumulate,
+                                ws, ws_bytes, sh, s);
+    return backproject_batched_impl(1, &it, accumulate, ws, ws_bytes, sh, (unsigned)(sh.form * num_sms()), s);
+}
 
 }  // namespace pmf
 
@@ -789,18 +990,7 @@ extern "C" {
 
 pmf_status conebeam_project(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
                             pmf_dtype dtype, const void* vol, int64_t vol_stride, float* proj, pmf_stream stream) {
-    pmf_status st = check_proj(grid, det, P, views);
-    if (st != PMF_OK) return st;
-    if ((st = validate_dtype(dtype)) != PMF_OK) return st;
-    if (P == 0) return PMF_OK;
-    PMF_REQUIRE(vol && proj, "null pointer");
-    PMF_REQUIRE(vol_stride >= 0, "vol_stride must be >= 0");
-    GridD g = make_grid(grid);
-    const int ntu = (det->nu + 15) / 16, ntv = (det->nv + 15) / 16;
-    dim3 gr((unsigned)(ntu * ntv), (unsigned)P);
-    cudaStream_t s = (cudaStream_t)stream;
-    PMF_DISPATCH_DTYPE(dtype, T, k_project<T><<<gr, kRay, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, (const T*)vol, vol_stride, proj));
-    return check_launch("conebeam_project");
+    return project_grid(grid, det, P, views, dtype, vol, vol_stride, proj, MarchShape{}, (cudaStream_t)stream);
 }
 
 pmf_status conebeam_project_backward_workspace(const pmf_grid* grid, int32_t P, int64_t vol_stride, size_t* bytes) {
@@ -816,93 +1006,12 @@ pmf_status conebeam_project_backward_workspace(const pmf_grid* grid, int32_t P, 
 pmf_status conebeam_project_backward(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
                                      const float* d_proj, float* d_vol, int64_t vol_stride, int accumulate, void* ws,
                                      size_t ws_bytes, pmf_stream stream) {
-    pmf_status st = check_proj(grid, det, P, views);
-    if (st != PMF_OK) return st;
-    PMF_REQUIRE(vol_stride >= 0, "vol_stride must be >= 0");
-    PMF_REQUIRE(d_vol != nullptr && (P == 0 || d_proj != nullptr), "null pointer");
-    size_t need;
-    conebeam_project_backward_workspace(grid, P, vol_stride, &need);
-    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
-    GridD g = make_grid(grid);
-    cudaStream_t s = (cudaStream_t)stream;
-    unsigned* maxbits = (unsigned*)ws;
-    unsigned long long* acc = (unsigned long long*)((char*)ws + align_up(256));
-    cudaMemsetAsync(ws, 0, need, s);
-    const int64_t Q = (int64_t)det->nu * det->nv;
-    const double rays = (double)Q * (vol_stride ? 1.0 : (double)P);
-    const float bound_mult = (float)((double)det->step_mm * rays * (double)max_samples_per_voxel(grid, det->step_mm));
-    const int64_t cells = vol_stride ? (int64_t)(P > 0 ? P - 1 : 0) * vol_stride + g.n : g.n;
-    if (P > 0) {
-        const int64_t nq = Q * P;
-        int64_t nb = (nq + 255) / 256;
-        k_absmax_f<<<(unsigned)(nb < 1024 ? nb : 1024), 256, 0, s>>>(d_proj, nq, maxbits);
-        const int ntu = (det->nu + 15) / 16, ntv = (det->nv + 15) / 16;
-        dim3 gr((unsigned)(ntu * ntv), (unsigned)P);
-        k_backproject<<<gr, kRay, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, d_proj, vol_stride, acc,
-                                          maxbits, bound_mult, chunk_samples_per_voxel(grid, det->step_mm));
-    }
-    int64_t nb = (cells + 255) / 256;
-    k_fixed_to_float_f<<<(unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks), 256, 0, s>>>(
-        acc, cells, maxbits, bound_mult, d_vol, accumulate);
-    return check_launch("conebeam_project_backward");
-}
-
-static pmf_status fill_item(const pmf_project_item& in, pmf_dtype dtype, int64_t begin, ProjItem& it) {
-    pmf_status st = check_proj(&in.grid, &in.det, in.P, in.views);
-    if (st != PMF_OK) return st;
-    (void)dtype;
-    PMF_REQUIRE(in.vol_stride >= 0, "vol_stride must be >= 0");
-    it = ProjItem{};
-    it.g = make_grid(&in.grid);
-    it.nu = in.det.nu; it.nv = in.det.nv;
-    it.ntu = (in.det.nu + 15) / 16;
-    it.ntiles = it.ntu * ((in.det.nv + 15) / 16);
-    it.P = in.P;
-    it.step = in.det.step_mm;
-    it.views = in.views;
-    it.vol_stride = in.vol_stride;
-    it.nq = (int64_t)in.det.nu * in.det.nv * in.P;
-    it.begin = begin;
-    return PMF_OK;
-}
-
-// ctas = 0: 4 resident CTAs per SM of 152 (256 threads, <= 64 registers each)
-static unsigned persistent_ctas(int64_t total, unsigned ctas) {
-    const int64_t cap = ctas ? (int64_t)ctas : 4 * 152;
-    return (unsigned)(total < cap ? (total > 0 ? total : 1) : cap);
-}
-
-static pmf_status project_batched_impl(int32_t n, const pmf_project_item* items, pmf_dtype dtype, unsigned ctas,
-                                       pmf_stream stream) {
-    PMF_REQUIRE(n >= 0 && n <= kMaxItems, "n must be in [0, %d]", kMaxItems);
-    PMF_REQUIRE(n == 0 || items != nullptr, "items is null");
-    pmf_status st = validate_dtype(dtype);
-    if (st != PMF_OK) return st;
-    ProjBatch B{};
-    B.n = n;
-    int64_t total = 0;
-    for (int i = 0; i < n; i++) {
-        if ((st = fill_item(items[i], dtype, total, B.it[i])) != PMF_OK) return st;
-        PMF_REQUIRE(items[i].P == 0 || (items[i].vol && items[i].proj), "item %d: null pointer", i);
-        B.it[i].vol = items[i].vol;
-        B.it[i].proj = items[i].proj;
-        total += (int64_t)B.it[i].ntiles * items[i].P;
-    }
-    B.total = total;
-    if (total == 0) return PMF_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    PMF_DISPATCH_DTYPE(dtype, T, k_project_batched<T><<<persistent_ctas(total, ctas), kRay, 0, s>>>(B));
-    return check_launch("conebeam_project_batched");
+    return backproject_grid(grid, det, P, views, d_proj, d_vol, vol_stride, accumulate, ws, ws_bytes, MarchShape{},
+                            (cudaStream_t)stream);
 }
 
 pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pmf_dtype dtype, pmf_stream stream) {
-    return project_batched_impl(n, items, dtype, 0, stream);
-}
-
-static size_t bp_item_bytes(const pmf_backproject_item& it) {
-    const int64_t n = (int64_t)it.grid.nx * it.grid.ny * it.grid.nz;
-    const int64_t cells = it.vol_stride ? (int64_t)(it.P > 0 ? it.P - 1 : 0) * it.vol_stride + n : n;
-    return align_up(256) + align_up(sizeof(unsigned long long) * (size_t)cells);
+    return project_batched_impl(n, items, dtype, MarchShape{}, 0, (cudaStream_t)stream);
 }
 
 pmf_status conebeam_project_backward_batched_workspace(int32_t n, const pmf_backproject_item* items, size_t* bytes) {
@@ -917,54 +1026,9 @@ pmf_status conebeam_project_backward_batched_workspace(int32_t n, const pmf_back
     return PMF_OK;
 }
 
-static pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
-                                           size_t ws_bytes, unsigned ctas, pmf_stream stream) {
-    size_t need = 0;
-    pmf_status st = conebeam_project_backward_batched_workspace(n, items, &need);
-    if (st != PMF_OK) return st;
-    if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
-    ProjBatch B{};
-    B.n = n;
-    int64_t total = 0, maxq = 0, maxcells = 0;
-    char* cur = (char*)ws;
-    for (int i = 0; i < n; i++) {
-        const pmf_backproject_item& in = items[i];
-        pmf_project_item tmp{in.grid, in.det, in.P, in.views, nullptr, in.vol_stride, nullptr};
-        if ((st = fill_item(tmp, PMF_F32, total, B.it[i])) != PMF_OK) return st;
-        PMF_REQUIRE(in.d_vol != nullptr && (in.P == 0 || in.d_proj != nullptr), "item %d: null pointer", i);
-        ProjItem& it = B.it[i];
-        const int64_t Q = (int64_t)in.det.nu * in.det.nv;
-        const double rays = (double)Q * (in.vol_stride ? 1.0 : (double)in.P);
-        it.bound_mult = (float)((double)in.det.step_mm * rays * (double)max_samples_per_voxel(&in.grid, in.det.step_mm));
-        it.spv = chunk_samples_per_voxel(&in.grid, in.det.step_mm);
-        it.dproj = in.d_proj;
-        it.dvol = in.d_vol;
-        it.maxbits = (unsigned*)cur;
-        it.acc = (unsigned long long*)(cur + align_up(256));
-        it.cells = in.vol_stride ? (int64_t)(in.P > 0 ? in.P - 1 : 0) * in.vol_stride + it.g.n : it.g.n;
-        cur += bp_item_bytes(in);
-        total += (int64_t)it.ntiles * in.P;
-        maxq = it.nq > maxq ? it.nq : maxq;
-        maxcells = it.cells > maxcells ? it.cells : maxcells;
-    }
-    B.total = total;
-    if (n == 0) return PMF_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaMemsetAsync(ws, 0, need, s);
-    if (maxq > 0) {
-        const int64_t nb = (maxq + 255) / 256;
-        k_absmax_batched<<<dim3((unsigned)(nb < 1024 ? nb : 1024), (unsigned)n), 256, 0, s>>>(B);
-    }
-    if (total > 0) k_backproject_batched<<<persistent_ctas(total, ctas), kRay, 0, s>>>(B);
-    const int64_t nc = (maxcells + 255) / 256;
-    k_fixed_to_float_batched<<<dim3((unsigned)(nc < 4 * kStreamBlocks ? nc : 4 * kStreamBlocks), (unsigned)n), 256, 0, s>>>(
-        B, accumulate);
-    return check_launch("conebeam_project_backward_batched");
-}
-
 pmf_status conebeam_project_backward_batched(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
                                              size_t ws_bytes, pmf_stream stream) {
-    return backproject_batched_impl(n, items, accumulate, ws, ws_bytes, 0, stream);
+    return backproject_batched_impl(n, items, accumulate, ws, ws_bytes, MarchShape{}, 0, (cudaStream_t)stream);
 }
 
 pmf_status projection_loss_workspace(int64_t count, size_t* bytes) {
@@ -992,30 +1056,3 @@ pmf_status projection_loss(int32_t kind, int32_t P, int64_t Q, const float* pred
 }
 
 }  // extern "C"
-
-namespace pmf {
-
-// Launch forms for plans: form 0 is one CTA per (view, tile); form k > 0 a
-// persistent launch of k CTAs per SM.  Every form runs the same per-tile
-// arithmetic, so the results are identical.
-static unsigned form_ctas(int form) {
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return (unsigned)form * (unsigned)(sms > 0 ? sms : 152);
-}
-
-pmf_status project_launch(const pmf_project_item& it, pmf_dtype dtype, int form, cudaStream_t s) {
-    if (form <= 0)
-        return conebeam_project(&it.grid, &it.det, it.P, it.views, dtype, it.vol, it.vol_stride, it.proj, (pmf_stream)s);
-    return project_batched_impl(1, &it, dtype, form_ctas(form), (pmf_stream)s);
-}
-
-pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes, int form,
-                              cudaStream_t s) {
-    if (form <= 0)
-        return conebeam_project_backward(&it.grid, &it.det, it.P, it.views, it.d_proj, it.d_vol, it.vol_stride,
-                                         accumulate, ws, ws_bytes, (pmf_stream)s);
-    return backproject_batched_impl(1, &it, accumulate, ws, ws_bytes, form_ctas(form), (pmf_stream)s);
-}
-
-}  // namespace pmf

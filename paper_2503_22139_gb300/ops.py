@@ -557,9 +557,10 @@ class Plan(_StepBuffers):
                 "dE": view(t.dE, (self.L, 3) + shape, torch.float32)}
 
     def launch_forms(self):
-        a, b = ct.c_int32(0), ct.c_int32(0)
-        check(_lib.load().pmf_plan_launch_forms(self._h, ct.byref(a), ct.byref(b)), "pmf_plan_launch_forms")
-        return int(a.value), int(b.value)
+        """((form, chunk, rays) of the projector, (form, chunk, rays) of its adjoint)."""
+        a, b = (ct.c_int32 * 3)(), (ct.c_int32 * 3)()
+        check(_lib.load().pmf_plan_launch_forms(self._h, a, b), "pmf_plan_launch_forms")
+        return tuple(int(x) for x in a), tuple(int(x) for x in b)
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

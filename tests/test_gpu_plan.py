@@ -88,36 +88,54 @@ def test_graph_plan_replays_the_eager_step(wl):
     graph.close()
 
 
-def test_autotune_cache_selects_launch_forms_with_identical_results(wl, tmp_path):
+def _shape(txt):
+    return tuple(int(x) for x in txt.split("=")[1].split(","))
+
+
+def test_autotune_cache_selects_launch_shapes(wl, tmp_path):
+    """The autotuner records one shape per direction; a plan reads it back.
+    Launch forms (grid or persistent) give bit-identical results; brick length
+    and rays per CTA move only the last bits (chunk anchors, per-CTA fixed-point
+    scales), so every forced shape stays within 1e-6 of the default plan's
+    volumes and projections and within 1e-4 of its gradients (a tenth of the
+    gradient bar: the quaternion gradient sums terms of both signs); the
+    default itself is pinned to the oracle by the parity tests."""
     ref, mbc = _sets(wl)
     b = _batch(wl)
     cache = tmp_path / "tune.txt"
-    pmf.autotune(wl.grid, wl.det, ref, mbc, wl.p, str(cache), dtype=torch.bfloat16, views=b[0], coeff=b[1],
+    pmf.autotune(wl.grid, wl.det, ref, mbc, wl.p, str(cache), dtype=torch.float32, views=b[0], coeff=b[1],
                  meas=b[2])
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and " proj=" in lines[0] and " backproj=" in lines[0]
-    key = lines[0].split(" ")[0]
-    tuned = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.bfloat16, tune_cache=str(cache))
-    fp, bp = (int(x.split("=")[1]) for x in lines[0].split(" ")[1:3])
-    assert tuned.launch_forms() == (fp, bp)
-    # force persistent forms that differ from the default per-(view, tile) grid
-    cache.write_text(f"other-key proj=1 backproj=1\n{key} proj=2 backproj=3\n")
-    forced = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.bfloat16, tune_cache=str(cache))
-    assert forced.launch_forms() == (2, 3)
-    default = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.bfloat16)
-    assert default.launch_forms() == (0, 0)
-    for p in (forced, default, tuned):
-        p.step(*b)
+    key, fp_txt, bp_txt = lines[0].split(" ")
+    tuned = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.float32, tune_cache=str(cache))
+    assert tuned.launch_forms() == (_shape(fp_txt), _shape(bp_txt))
+    default = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.float32)
+    assert default.launch_forms() == ((0, 32, 256), (0, 32, 256))
+    default.step(*b)
     torch.cuda.synchronize()
     base = _plan_outputs(default)
-    _assert_same(base, _plan_outputs(forced))
-    _assert_same(base, _plan_outputs(tuned))
+    for fp, bp in [((2, 32, 256), (3, 32, 256)), ((0, 16, 256), (0, 16, 128)), ((4, 32, 128), (1, 16, 256))]:
+        cache.write_text(f"other-key proj=1,32,256 backproj=1,32,256\n{key} proj={','.join(map(str, fp))} "
+                         f"backproj={','.join(map(str, bp))}\n")
+        forced = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.float32, tune_cache=str(cache))
+        assert forced.launch_forms() == (fp, bp)
+        forced.step(*b)
+        torch.cuda.synchronize()
+        got = _plan_outputs(forced)
+        if fp[1:] == (32, 256) and bp[1:] == (32, 256):
+            _assert_same(base, got)  # forms alone: bit-identical
+        else:
+            for k in base:
+                d = (got[k].double() - base[k].double()).norm() / max(base[k].double().norm(), 1e-30)
+                assert d <= (1e-6 if k in ("V", "E", "W", "Y", "loss") else 1e-4), (k, fp, bp, float(d))
+        forced.close()
     # a second autotune of the same key replaces its line and keeps the others
-    pmf.autotune(wl.grid, wl.det, ref, mbc, wl.p, str(cache), dtype=torch.bfloat16, views=b[0], coeff=b[1],
+    pmf.autotune(wl.grid, wl.det, ref, mbc, wl.p, str(cache), dtype=torch.float32, views=b[0], coeff=b[1],
                  meas=b[2])
     lines = cache.read_text().splitlines()
     assert len(lines) == 2 and lines[0].startswith("other-key ") and lines[1].startswith(key + " ")
-    for p in (forced, default, tuned):
+    for p in (default, tuned):
         p.close()
 
 

@@ -457,6 +457,34 @@ def run_native(a):
         variants[f"native_plan_graph_{a.dtype}"] = round(B * a.steps * world / tg, 3)
         plan.close()
         del plan
+        # the same plan with the autotuner's launch shapes for this workload
+        with tempfile.TemporaryDirectory() as td:
+            cache = os.path.join(td, "tune.txt")
+            pmf.autotune(wl.grid, wl.det, ref, mbc, B, cache, dtype=dt, kind=a.kind, views=batch(0)[0],
+                         coeff=batch(0)[1], meas=batch(0)[2])
+            plan = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind, use_graph=True,
+                            tune_cache=cache)
+        for k in range(2):
+            plan.step(*batch(k))
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+        g0.record(stream)
+        for k in range(a.steps):
+            plan.step(*batch(a.warmup + k))
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tg = g0.elapsed_time(g1) / 1e3
+        if world > 1:
+            tt = torch.tensor([tg], device="cuda")
+            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+            tg = float(tt.item())
+        variants[f"native_plan_graph_autotuned_{a.dtype}"] = round(B * a.steps * world / tg, 3)
+        fp_shape, bp_shape = plan.launch_forms()
+        variants["autotuned_shapes"] = {"proj": list(fp_shape), "backproj": list(bp_shape),
+                                        "fields": ["form (0 grid, k persistent CTAs/SM)", "chunk", "rays"]}
+        plan.close()
+        del plan
         from paper_2503_22139_gb300.pipeline import PlainPerProjection
         main_dt = a.dtype
         del step

@@ -48,6 +48,12 @@ def lib():
                                                 _D, _D, _D, _D, ct.c_int64, ct.c_int64, _D]
             L.orc_loss.argtypes = [ct.c_int, ct.c_int64, _D, _D, _D]
             L.orc_loss.restype = ct.c_double
+            L.orc_dssim.argtypes = [ct.c_int, ct.c_int, ct.c_int, _D, _D, ct.c_double, _D]
+            L.orc_dssim.restype = ct.c_double
+            L.orc_tv.argtypes = [_I64, _D, ct.c_int, _I64, _D]
+            L.orc_tv.restype = ct.c_double
+            L.orc_mbc_normality.argtypes = [ct.c_int, ct.c_int64, _D, _D]
+            L.orc_mbc_normality.restype = ct.c_double
             _lib = L
     return _lib
 
@@ -220,3 +226,40 @@ def loss(kind, pred, meas, with_grad=True):
     g = np.zeros_like(pred) if with_grad else None
     val = lib().orc_loss(int(kind), pred.size, _p(pred), _p(meas), _p(g) if with_grad else None)
     return float(val), g
+
+
+def dssim(pred, meas, data_range, with_grad=True):
+    """D-SSIM term of Eq. 10/12 over projections [P, nv, nu]: mean over
+    projections of 1 - mean SSIM (11x11 Gaussian window, sigma 1.5, zero
+    padding, C1 = (0.01 range)^2, C2 = (0.03 range)^2); returns (loss, d_pred)."""
+    pred, meas = _f64(pred), _f64(meas)
+    P, nv, nu = pred.shape
+    g = np.zeros_like(pred) if with_grad else None
+    val = lib().orc_dssim(P, nu, nv, _p(pred), _p(meas), float(data_range), _p(g) if with_grad else None)
+    return float(val), g
+
+
+def tv(vol, D, origin, with_grad=True):
+    """Sub-volume TV (Eq. 11/14) of vol [nz, ny, nx] on the D^3 crop at voxel
+    origin (x, y, z); returns (loss, d_vol)."""
+    vol = _f64(vol)
+    nz, ny, nx = vol.shape
+    dims = np.array([nx, ny, nz], dtype=np.int64)
+    o = np.array(origin, dtype=np.int64)
+    if not (np.all(o >= 0) and np.all(o + D <= dims) and D >= 2):
+        raise ValueError("crop outside the volume")
+    g = np.zeros_like(vol) if with_grad else None
+    val = lib().orc_tv(dims.ctypes.data_as(_I64), _p(vol), int(D), o.ctypes.data_as(_I64),
+                       _p(g) if with_grad else None)
+    return float(val), g
+
+
+def mbc_normality(E, with_grad=True):
+    """Eq. 13 normality loss of MBC grids E [L, 3, ...]; returns (loss, dE)."""
+    E = _f64(E)
+    L = E.shape[0]
+    N = int(np.prod(E.shape[2:]))
+    g = np.zeros_like(E) if with_grad else None
+    val = lib().orc_mbc_normality(L, N, _p(E), _p(g) if with_grad else None)
+    return float(val), g
+

@@ -530,3 +530,149 @@ double orc_loss(int kind, int64_t n, const double* pred, const double* meas, dou
     }
     return acc / (double)n;
 }
+
+/* ------------------------------------------------ Eq. 13-14 loss terms */
+
+/* SSIM window (Zhou et al. 2004, the customary 11 x 11 Gaussian of standard
+ * deviation 1.5 pixels): w[t] for offsets t - 5, normalised so that the 2-D
+ * window w[i] w[j] sums to 1. */
+static void ssim_window(double w[11]) {
+    double s = 0.0;
+    for (int t = 0; t < 11; t++) {
+        const double d = (double)(t - 5);
+        w[t] = exp(-d * d / (2.0 * 1.5 * 1.5));
+        s += w[t];
+    }
+    for (int t = 0; t < 11; t++) w[t] /= s;
+}
+
+/* Windowed sum of f(x, y) over the 11 x 11 window centred at pixel (a, b) of
+ * one nv x nu image pair; pixels outside the image count as zero. */
+static void window_moments(const double* X, const double* Yv, int nu, int nv, int a, int b, const double w[11],
+                           double m[5]) {
+    for (int k = 0; k < 5; k++) m[k] = 0.0;
+    for (int j = -5; j <= 5; j++) {
+        const int bb = b + j;
+        if (bb < 0 || bb >= nv) continue;
+        for (int i = -5; i <= 5; i++) {
+            const int aa = a + i;
+            if (aa < 0 || aa >= nu) continue;
+            const double wt = w[j + 5] * w[i + 5];
+            const double x = X[(int64_t)bb * nu + aa], y = Yv[(int64_t)bb * nu + aa];
+            m[0] += wt * x;      /* mu_x */
+            m[1] += wt * y;      /* mu_y */
+            m[2] += wt * x * x;  /* E[x^2] */
+            m[3] += wt * y * y;  /* E[y^2] */
+            m[4] += wt * x * y;  /* E[xy] */
+        }
+    }
+}
+
+/* D-SSIM term of Eq. 10/12: the mean over the P projections of
+ * 1 - mean_pixels SSIM(pred_p, meas_p), with, at every pixel,
+ *   SSIM = (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2)),
+ *   s_x^2 = E[x^2] - mu_x^2, s_xy = E[xy] - mu_x mu_y (windowed, zero padding),
+ *   C1 = (0.01 range)^2, C2 = (0.03 range)^2.
+ * d_pred (nullable) receives d loss / d pred by the chain rule through the
+ * windowed sums: pixel r enters the sums of every pixel q within its window. */
+double orc_dssim(int P, int nu, int nv, const double* pred, const double* meas, double range, double* d_pred) {
+    double w[11];
+    ssim_window(w);
+    const double C1 = (0.01 * range) * (0.01 * range), C2 = (0.03 * range) * (0.03 * range);
+    const int64_t Q = (int64_t)nu * nv;
+    double total = 0.0;
+    double* G = (double*)malloc(sizeof(double) * 3 * (size_t)Q);  /* dS/d mu_x, dS/d E[x^2], dS/d E[xy] */
+    for (int p = 0; p < P; p++) {
+        const double* X = pred + (int64_t)p * Q;
+        const double* Yv = meas + (int64_t)p * Q;
+        double ssum = 0.0;
+#pragma omp parallel for reduction(+ : ssum) schedule(static)
+        for (int64_t q = 0; q < Q; q++) {
+            const int a = (int)(q % nu), b = (int)(q / nu);
+            double m[5];
+            window_moments(X, Yv, nu, nv, a, b, w, m);
+            const double mx = m[0], my = m[1];
+            const double A1 = 2.0 * mx * my + C1, A2 = 2.0 * (m[4] - mx * my) + C2;
+            const double B1 = mx * mx + my * my + C1, B2 = (m[2] - mx * mx) + (m[3] - my * my) + C2;
+            const double S = A1 * A2 / (B1 * B2);
+            ssum += S;
+            G[q] = 2.0 * my * (A2 - A1) / (B1 * B2) - 2.0 * mx * S * (1.0 / B1 - 1.0 / B2);
+            G[Q + q] = -S / B2;
+            G[2 * Q + q] = 2.0 * A1 / (B1 * B2);
+        }
+        total += 1.0 - ssum / (double)Q;
+        if (d_pred) {
+            const double f = -1.0 / ((double)P * (double)Q);
+#pragma omp parallel for schedule(static)
+            for (int64_t r = 0; r < Q; r++) {
+                const int a = (int)(r % nu), b = (int)(r / nu);
+                double g1 = 0.0, g2 = 0.0, g3 = 0.0;
+                for (int j = -5; j <= 5; j++) {
+                    const int bb = b + j;
+                    if (bb < 0 || bb >= nv) continue;
+                    for (int i = -5; i <= 5; i++) {
+                        const int aa = a + i;
+                        if (aa < 0 || aa >= nu) continue;
+                        const double wt = w[j + 5] * w[i + 5];
+                        const int64_t q = (int64_t)bb * nu + aa;
+                        g1 += wt * G[q];
+                        g2 += wt * G[Q + q];
+                        g3 += wt * G[2 * Q + q];
+                    }
+                }
+                d_pred[(int64_t)p * Q + r] = f * (g1 + 2.0 * X[r] * g2 + Yv[r] * g3);
+            }
+        }
+    }
+    free(G);
+    return total / (double)P;
+}
+
+/* Sub-volume total variation (the TV term of Eq. 11/14): on the D^3 crop of
+ * V [nz][ny][nx] starting at voxel origin o, the mean over the three axes of
+ * the mean absolute forward difference between neighbouring crop voxels
+ * ((D-1) D^2 differences per axis).  dV (nullable, [N]) receives the
+ * subgradient (sign(0) = 0) inside the crop and zero elsewhere. */
+double orc_tv(const int64_t dims[3], const double* V, int D, const int64_t o[3], double* dV) {
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    const double per_axis = (double)(D - 1) * (double)D * (double)D;
+    if (dV) memset(dV, 0, sizeof(double) * (size_t)(nx * ny * nz));
+    double total = 0.0;
+    for (int axis = 0; axis < 3; axis++) {
+        double s = 0.0;
+        for (int z = 0; z < D; z++)
+            for (int y = 0; y < D; y++)
+                for (int x = 0; x < D; x++) {
+                    const int c[3] = {x, y, z};
+                    if (c[axis] + 1 >= D) continue;
+                    const int64_t v = ((o[2] + z) * ny + (o[1] + y)) * nx + (o[0] + x);
+                    const int64_t step = axis == 0 ? 1 : (axis == 1 ? nx : nx * ny);
+                    const double d = V[v + step] - V[v];
+                    s += fabs(d);
+                    if (dV) {
+                        const double sg = (d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0)) / (3.0 * per_axis);
+                        dV[v + step] += sg;
+                        dV[v] -= sg;
+                    }
+                }
+        total += s / per_axis;
+    }
+    return total / 3.0;
+}
+
+/* Eq. 13: (1 / (3 L)) sum over levels l and axes k of (||e_{l,k}||^2 - 1)^2,
+ * ||e||^2 the sum of squares of the MBC volume over the grid (L = 3 gives the
+ * paper's 1/9).  E is [L][3][N]; dE (nullable) receives
+ * 4 (||e_{l,k}||^2 - 1) e_{l,k} / (3 L). */
+double orc_mbc_normality(int L, int64_t N, const double* E, double* dE) {
+    double total = 0.0;
+    for (int lk = 0; lk < 3 * L; lk++) {
+        const double* e = E + (int64_t)lk * N;
+        double n2 = 0.0;
+        for (int64_t v = 0; v < N; v++) n2 += e[v] * e[v];
+        total += (n2 - 1.0) * (n2 - 1.0);
+        if (dE)
+            for (int64_t v = 0; v < N; v++) dE[(int64_t)lk * N + v] = 4.0 * (n2 - 1.0) * e[v] / (3.0 * L);
+    }
+    return total / (3.0 * L);
+}

@@ -279,6 +279,48 @@ pmf_status projection_loss_workspace(int64_t count, size_t* bytes);
 pmf_status projection_loss(int32_t kind, int32_t P, int64_t Q, const float* pred, const float* meas,
                            float* loss, float* d_pred, void* ws, size_t ws_bytes, pmf_stream stream);
 
+/* ------------------------------------------- Eq. 14 regularisation terms */
+/* Each call sets *loss (device fp32 scalar) to weight * term, or with
+ * accumulate = 1 adds weight * term to it; the gradient buffer (nullable)
+ * likewise receives (or adds) weight * d term / d input.  Fixed-order
+ * reductions: results are reproducible run to run. */
+
+pmf_status projection_dssim_workspace(int32_t P, int32_t nu, int32_t nv, size_t* bytes);
+
+/* D-SSIM of Eq. 10/12: term = (1/P) sum_p (1 - mean over pixels of
+ * SSIM(pred_p, meas_p)), SSIM after Zhou et al. (2004) with the 11 x 11
+ * Gaussian window of standard deviation 1.5 pixels (normalised), windowed
+ * moments with zero padding outside the detector,
+ * SSIM = (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2)),
+ * C1 = (0.01 data_range)^2, C2 = (0.03 data_range)^2.  pred, meas, d_pred:
+ * device fp32 [P][nv][nu]; P <= 65535. */
+pmf_status projection_dssim(int32_t P, int32_t nu, int32_t nv, const float* pred, const float* meas, float data_range,
+                            float weight, float* loss, float* d_pred, int accumulate, void* ws, size_t ws_bytes,
+                            pmf_stream stream);
+
+pmf_status tv_loss_workspace(int32_t D, size_t* bytes);
+
+/* Sub-volume total variation (Eq. 11/14): term = the mean over the three axes
+ * of the mean |forward difference| between neighbouring voxels of the D^3
+ * crop of vol (`dtype`, device [N]) whose lowest corner is voxel
+ * d_origin = (x, y, z) (device int32[3], read by the kernel so a captured
+ * step can take a new crop each replay; clamped so the crop lies in the
+ * grid).  d_vol (device fp32 [N]) gets the subgradient (sign(0) = 0) on the
+ * crop and zero elsewhere (accumulate = 0) or is left unchanged there
+ * (accumulate = 1).  2 <= D <= min(nx, ny, nz). */
+pmf_status tv_loss(const pmf_grid* grid, pmf_dtype dtype, const void* vol, int32_t D, const int32_t* d_origin,
+                   float weight, float* loss, float* d_vol, int accumulate, void* ws, size_t ws_bytes,
+                   pmf_stream stream);
+
+pmf_status mbc_normality_workspace(int32_t L, size_t* bytes);
+
+/* MBC normality (Eq. 13): term = (1/(3L)) sum over levels l and axes k of
+ * (||e_{l,k}||^2 - 1)^2 with ||e||^2 the sum of squares over the grid (L = 3
+ * gives the paper's 1/9).  mbc: `dtype`, device [L][3][N]; d_mbc: device fp32
+ * [L][3][N], receives 4 (||e_{l,k}||^2 - 1) e_{l,k} / (3L) times weight. */
+pmf_status mbc_normality(const pmf_grid* grid, int32_t L, pmf_dtype dtype, const void* mbc, float weight, float* loss,
+                         float* d_mbc, int accumulate, void* ws, size_t ws_bytes, pmf_stream stream);
+
 /* ------------------------------------------------------------ host helpers */
 
 /* The circular scan of Sec. 2.3.3 / Table I as pmf_view records: view p has

@@ -105,6 +105,12 @@ SIGNATURES = {
     "conebeam_project_backward_batched": [_I32, ct.POINTER(PmfBackprojectItem), ct.c_int, _P, ct.c_size_t, _P],
     "projection_loss_workspace": [_I64, _SZ],
     "projection_loss": [_I32, _I32, _I64, _P, _P, _P, _P, _P, ct.c_size_t, _P],
+    "projection_dssim_workspace": [_I32, _I32, _I32, _SZ],
+    "projection_dssim": [_I32, _I32, _I32, _P, _P, ct.c_float, ct.c_float, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
+    "tv_loss_workspace": [_I32, _SZ],
+    "tv_loss": [_G, ct.c_int, _P, _I32, _P, ct.c_float, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
+    "mbc_normality_workspace": [_I32, _SZ],
+    "mbc_normality": [_G, _I32, ct.c_int, _P, ct.c_float, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
     "pmf_circular_views": [_I32, ct.c_double, ct.c_double, ct.c_double, ct.c_double, _I32, _I32, ct.POINTER(PmfView)],
     "pmf_workspace_size": [_I32, ct.POINTER(PmfWsArgs), _SZ],
     "pmf_device_counters": [ct.POINTER(ct.c_uint64), _I32],

@@ -381,6 +381,70 @@ def projection_loss(kind: int, pred: torch.Tensor, meas: torch.Tensor, with_grad
     return loss, d_pred
 
 
+# ------------------------------------------------- Eq. 14 regularisation
+
+def projection_dssim(pred: torch.Tensor, meas: torch.Tensor, data_range: float, weight: float = 1.0,
+                     with_grad: bool = True, loss: Optional[torch.Tensor] = None, d_pred: Optional[torch.Tensor] = None,
+                     accumulate: bool = False, ws=None):
+    """D-SSIM term of Eq. 10/12 of projections [P, nv, nu]; returns (loss [1], d_pred or None)."""
+    L = _lib.load()
+    pred = _need(pred, "pred", torch.float32)
+    meas = _need(meas, "meas", torch.float32)
+    P, nv, nu = (int(x) for x in pred.shape)
+    if ws is None:
+        ws = _ws(_size(L.projection_dssim_workspace, P, nu, nv), pred.device)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=pred.device)
+    if with_grad and d_pred is None:
+        d_pred = torch.zeros_like(pred)
+    check(L.projection_dssim(P, nu, nv, _p(pred), _p(meas), float(data_range), float(weight), _p(loss),
+                             _p(d_pred if with_grad else None), int(accumulate), _p(ws), ws.numel(), _stream()),
+          "projection_dssim")
+    return loss, (d_pred if with_grad else None)
+
+
+def tv_loss(grid, vol: torch.Tensor, D: int, origin, weight: float = 1.0, with_grad: bool = True,
+            loss: Optional[torch.Tensor] = None, d_vol: Optional[torch.Tensor] = None, accumulate: bool = False,
+            ws=None):
+    """Sub-volume TV (Eq. 11/14) of vol [nz, ny, nx] on the D^3 crop at voxel
+    origin (x, y, z) (a device int32 [3] tensor or a tuple); returns (loss [1], d_vol or None)."""
+    L = _lib.load()
+    vol = _need(vol, "vol")
+    g = _grid(grid)
+    if not isinstance(origin, torch.Tensor):
+        origin = torch.tensor(list(origin), dtype=torch.int32, device=vol.device)
+    origin = _need(origin, "origin", torch.int32)
+    if ws is None:
+        ws = _ws(_size(L.tv_loss_workspace, int(D)), vol.device)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=vol.device)
+    if with_grad and d_vol is None:
+        d_vol = torch.zeros(vol.shape, dtype=torch.float32, device=vol.device)
+    check(L.tv_loss(ct.byref(g), _DT[vol.dtype], _p(vol), int(D), _p(origin), float(weight), _p(loss),
+                    _p(d_vol if with_grad else None), int(accumulate), _p(ws), ws.numel(), _stream()), "tv_loss")
+    return loss, (d_vol if with_grad else None)
+
+
+def mbc_normality(grid, mbc: torch.Tensor, weight: float = 1.0, with_grad: bool = True,
+                  loss: Optional[torch.Tensor] = None, d_mbc: Optional[torch.Tensor] = None, accumulate: bool = False,
+                  ws=None):
+    """Eq. 13 normality loss of MBC grids [L, 3, nz, ny, nx]; returns (loss [1], d_mbc or None)."""
+    Lb = _lib.load()
+    mbc = _need(mbc, "mbc")
+    g = _grid(grid)
+    L = int(mbc.shape[0])
+    if ws is None:
+        ws = _ws(_size(Lb.mbc_normality_workspace, L), mbc.device)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=mbc.device)
+    if with_grad and d_mbc is None:
+        d_mbc = torch.zeros(mbc.shape, dtype=torch.float32, device=mbc.device)
+    check(Lb.mbc_normality(ct.byref(g), L, _DT[mbc.dtype], _p(mbc), float(weight), _p(loss),
+                           _p(d_mbc if with_grad else None), int(accumulate), _p(ws), ws.numel(), _stream()),
+          "mbc_normality")
+    return loss, (d_mbc if with_grad else None)
+
+
 def library_info() -> dict:
     L = _lib.load()
     return {"version": L.pmf_version().decode(), "path": _lib.library_path()}

@@ -24,14 +24,32 @@ from .ops import Gaussians
 KERNELS = {
     "gs_voxelize": 4, "gs_voxelize_backward": 2, "warp_combine": 1, "conebeam_project": 1,
     "projection_loss": 2, "conebeam_project_backward": 3, "warp_combine_backward": 4,
+    "projection_dssim": 3, "tv_loss": 2, "mbc_normality": 3,
 }
+
+# The Stage 2-3 objective of Eq. 14 with the paper's weights (Sec. 2.3.2):
+# L1 + 0.25 D-SSIM + 1 L_MBC + 0.05 TV on a 32^3 crop of the reference volume.
+EQ14_DEFAULTS = dict(lambda_ssim=0.25, lambda_mbc=1.0, lambda_tv=0.05, tv_size=32, data_range=None)
 
 
 class ForwardAdjoint:
     def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
-                 dtype: torch.dtype = torch.float32, kind: int = 2, pair_headroom: float = 1.25):
+                 dtype: torch.dtype = torch.float32, kind=2, pair_headroom: float = 1.25,
+                 eq14: Optional[dict] = None):
+        """kind 1 / 2: L1 / L2 projection loss (Eq. 10/12, Eq. 1); kind "eq14":
+        the full objective of Eq. 14 with `eq14` overriding EQ14_DEFAULTS
+        (data_range, the D-SSIM dynamic range, is required)."""
         self.grid, self.det, self.ref, self.mbc = grid, det, ref, list(mbc)
-        self.B, self.dtype, self.kind = int(batch), dtype, int(kind)
+        self.B, self.dtype = int(batch), dtype
+        self.eq14 = None
+        if kind == "eq14":
+            q = dict(EQ14_DEFAULTS)
+            q.update(eq14 or {})
+            if q["data_range"] is None:
+                raise ValueError("eq14 needs data_range (the projections' dynamic range)")
+            self.eq14 = q
+            kind = 1
+        self.kind = int(kind)
         dev = ref.mean.device
         shape, n = ops._shape(grid)
         L = len(self.mbc)
@@ -62,17 +80,29 @@ class ForwardAdjoint:
         self.loss_ws = ops._ws(ops._size(Lb.projection_loss_workspace, self.B * det.nu * det.nv), dev)
         self.vb_ws = [ops._ws(ops.gs_voxelize_backward_workspace(grid, gs.n, gs.channels), dev)
                       for gs in [ref] + self.mbc]
+        if self.eq14 is not None:
+            q = self.eq14
+            self.ssim_ws = ops._ws(ops._size(Lb.projection_dssim_workspace, self.B, det.nu, det.nv), dev)
+            self.tv_ws = ops._ws(ops._size(Lb.tv_loss_workspace, int(q["tv_size"])), dev)
+            self.norm_ws = ops._ws(ops._size(Lb.mbc_normality_workspace, L), dev)
+            self.tv_origin = torch.zeros(3, dtype=torch.int32, device=dev)
 
     @property
     def launches_per_step(self) -> int:
         k = KERNELS
-        return ((1 + self.L) * (k["gs_voxelize"] + k["gs_voxelize_backward"]) + k["warp_combine"]
-                + k["conebeam_project"] + k["projection_loss"] + k["conebeam_project_backward"]
-                + k["warp_combine_backward"])
+        n = ((1 + self.L) * (k["gs_voxelize"] + k["gs_voxelize_backward"]) + k["warp_combine"]
+             + k["conebeam_project"] + k["projection_loss"] + k["conebeam_project_backward"]
+             + k["warp_combine_backward"])
+        if self.eq14 is not None:
+            n += k["projection_dssim"] + k["tv_loss"] + k["mbc_normality"]
+        return n
 
-    def run(self, views: torch.Tensor, coeff: torch.Tensor, meas: torch.Tensor):
-        """views [B,12] f64, coeff [B,L,3] f32, meas [B,nv,nu] f32 (device).
-        Returns the loss (device [1]); gradients land in g_ref, g_mbc, g_wc."""
+    def run(self, views: torch.Tensor, coeff: torch.Tensor, meas: torch.Tensor,
+            tv_origin: Optional[torch.Tensor] = None):
+        """views [B,12] f64, coeff [B,L,3] f32, meas [B,nv,nu] f32 (device);
+        tv_origin (Eq. 14 only): device int32 [3], the TV crop's corner voxel
+        (x, y, z) for this step.  Returns the loss (device [1]); gradients land
+        in g_ref, g_mbc, g_wc."""
         g, det = self.grid, self.det
         ops.gs_voxelize(g, self.ref, out=self.V, ws=self.vox_ws[0])
         for l, m in enumerate(self.mbc):
@@ -80,8 +110,19 @@ class ForwardAdjoint:
         ops.warp_combine(g, self.V[0], self.E, coeff, out=self.W)
         ops.conebeam_project(g, det, views, self.W, shared=False, out=self.Y)
         loss, dY = ops.projection_loss(self.kind, self.Y, meas, ws=self.loss_ws)
+        q = self.eq14
+        if q is not None:
+            ops.projection_dssim(self.Y, meas, q["data_range"], weight=q["lambda_ssim"], loss=loss, d_pred=dY,
+                                 accumulate=True, ws=self.ssim_ws)
         ops.conebeam_project_backward(g, det, views, dY, shared=False, out=self.dW, ws=self.bp_ws)
         ops.warp_combine_backward(g, self.V[0], self.E, coeff, self.dW, grads=self.g_wc, ws=self.wc_ws)
+        if q is not None:
+            if tv_origin is not None and tv_origin.data_ptr() != self.tv_origin.data_ptr():
+                self.tv_origin.copy_(tv_origin, non_blocking=True)
+            ops.tv_loss(g, self.V[0], int(q["tv_size"]), self.tv_origin, weight=q["lambda_tv"], loss=loss,
+                        d_vol=self.g_wc[0], accumulate=True, ws=self.tv_ws)
+            ops.mbc_normality(g, self.E, weight=q["lambda_mbc"], loss=loss, d_mbc=self.g_wc[1], accumulate=True,
+                              ws=self.norm_ws)
         ops.gs_voxelize_backward(g, self.ref, self.g_wc[0].reshape((1,) + self.g_wc[0].shape), grads=self.g_ref,
                                  ws=self.vb_ws[0])
         for l, m in enumerate(self.mbc):

@@ -21,18 +21,34 @@ def forward(wl, views=None, coeff=None, kappa=None):
     return dict(V=V, E=E, D=D, W=W, Y=Y)
 
 
-def step(wl, meas, kind=2, views=None, coeff=None, kappa=None):
+def step(wl, meas, kind=2, views=None, coeff=None, kappa=None, eq14=None):
     """Loss and gradients with respect to every Gaussian parameter and the
-    temporal coefficients (float64)."""
+    temporal coefficients (float64).  kind 1 / 2: L1 / L2 projection loss;
+    kind "eq14": the Stage 2-3 objective of Eq. 14, L1 + lambda_ssim D-SSIM +
+    lambda_mbc L_MBC + lambda_tv TV, with eq14 = dict(lambda_ssim, lambda_mbc,
+    lambda_tv, data_range, tv_size, tv_origin)."""
     kappa = wl.kappa if kappa is None else kappa
     views = wl.views if views is None else views
     coeff = wl.coeff if coeff is None else coeff
     g = wl.grid
     f = forward(wl, views, coeff, kappa)
-    loss, dY = oracle.loss(kind, f["Y"], meas)
+    if kind == "eq14":
+        q = eq14
+        loss, dY = oracle.loss(1, f["Y"], meas)
+        ls, dYs = oracle.dssim(f["Y"], meas, q["data_range"])
+        loss += q["lambda_ssim"] * ls
+        dY = dY + q["lambda_ssim"] * dYs
+    else:
+        loss, dY = oracle.loss(kind, f["Y"], meas)
     dW = oracle.project_backward(g, wl.det.nu, wl.det.nv, wl.det.step_mm, views, dY, shared=False)
     dV, dD = oracle.warp_backward(g, f["V"], f["D"], dW)
     dE, dw = oracle.combine_backward(f["E"], coeff, dD)
+    if kind == "eq14":
+        lt, dVt = oracle.tv(f["V"], q["tv_size"], q["tv_origin"])
+        ln, dEn = oracle.mbc_normality(f["E"])
+        loss += q["lambda_tv"] * lt + q["lambda_mbc"] * ln
+        dV = dV + q["lambda_tv"] * dVt
+        dE = dE + q["lambda_mbc"] * dEn
     grads = {"coeff": dw, "dV": dV, "dE": dE, "dW": dW, "dY": dY}
     grads["ref"] = oracle.voxelize_backward(g, wl.ref.mean, wl.ref.scale, wl.ref.quat, wl.ref.value, dV, kappa)
     grads["mbc"] = [oracle.voxelize_backward(g, m.mean, m.scale, m.quat, m.value, dE[l], kappa)

@@ -79,3 +79,38 @@ def test_full_chain_gradients_match_central_differences():
         fd = (lp - lm) / (2 * h)
         scale = max(abs(fd), 1e-3 * np.abs(garr).max())
         assert abs(garr[idx] - fd) <= 1e-3 * scale, (which, lvl, idx, garr[idx], fd)
+
+
+def test_eq14_objective_gradients_match_central_differences():
+    """The Stage 2-3 objective (Eq. 14): L1 + 0.25 D-SSIM + 1 L_MBC + 0.05 TV
+    on an 8^3 crop.  L1, TV and the DVF are piecewise smooth, so every
+    parameter takes h = 1e-5 in FP64 (no residual, voxel difference or sample
+    position sits within that of a kink for these seeds)."""
+    wl = fd_subproblem()
+    # scale the MBC vectors so that ||e_{l,k}||^2 ~ 1.5: every term of the
+    # objective is then O(1), and central differences resolve all of them
+    E = oracle_chain.forward(wl)["E"]
+    s = np.sqrt(1.5 / np.mean(np.sum(E.reshape(E.shape[0], 3, -1) ** 2, axis=2)))
+    for m in wl.mbc:
+        m.value = (m.value * s).astype(np.float32)
+    meas = wl.measured
+    q = dict(lambda_ssim=0.25, lambda_mbc=1.0, lambda_tv=0.05, data_range=float(meas.max() - meas.min()),
+             tv_size=8, tv_origin=(3, 4, 5))
+    coeff = wl.coeff.astype(np.float64)
+    loss, grads, _ = oracle_chain.step(wl, meas, kind="eq14", coeff=coeff, eq14=q)
+    rng = np.random.default_rng(6)
+    checks = [("coeff", None, tuple(rng.integers(0, [4, 3, 3])), grads["coeff"])]
+    for which, gi in (("mean", 0), ("scale", 1), ("value", 3)):
+        checks.append((which, None, (int(rng.integers(0, 200)), int(rng.integers(0, 3)) if which != "value" else 0),
+                       grads["ref"][gi]))
+        lvl = int(rng.integers(0, 3))
+        checks.append((which, lvl, (int(rng.integers(0, wl.mbc[lvl].g)), int(rng.integers(0, 3))), grads["mbc"][lvl][gi]))
+    for which, lvl, idx, garr in checks:
+        h = 1e-5
+        wp, cp = _perturbed(wl, which, lvl, idx, h)
+        wm, cm = _perturbed(wl, which, lvl, idx, -h)
+        lp, _, _ = oracle_chain.step(wp, meas, kind="eq14", coeff=cp, eq14=q)
+        lm, _, _ = oracle_chain.step(wm, meas, kind="eq14", coeff=cm, eq14=q)
+        fd = (lp - lm) / (2 * h)
+        scale = max(abs(fd), 1e-3 * np.abs(garr).max())
+        assert abs(garr[idx] - fd) <= 1e-3 * scale, (which, lvl, idx, garr[idx], fd)

@@ -403,7 +403,7 @@ typedef struct {
     pmf_detector det;
     pmf_dtype dtype;        /* storage of V, E, W */
     int32_t batch;          /* B >= 1 */
-    int32_t loss_kind;      /* 1 = L1 (Eq. 10/12), 2 = L2 (Eq. 1) */
+    int32_t loss_kind;      /* 1 = L1 (Eq. 10/12), 2 = L2 (Eq. 1), 3 = Eq. 14 (below) */
     int32_t levels;         /* L in [1, PMF_MAX_LEVELS] */
     pmf_gaussians ref;      /* channels 1 */
     pmf_gaussians mbc[PMF_MAX_LEVELS]; /* channels 3; first `levels` used */
@@ -418,6 +418,12 @@ typedef struct {
                                stream (which must not be the legacy NULL stream); later steps replay it */
     const char* tune_cache; /* nullable: file written by pmf_autotune; its entry for this
                                configuration selects the projector launch forms */
+    /* loss_kind 3, the Stage 2-3 objective of Eq. 14:
+     * L1 + lambda_ssim D-SSIM + lambda_mbc L_MBC + lambda_tv TV (paper: 0.25, 1, 0.05) */
+    float lambda_ssim, lambda_mbc, lambda_tv;
+    float ssim_range;            /* D-SSIM data range (> 0) */
+    int32_t tv_size;             /* edge D of the TV crop (paper: 32) */
+    const int32_t* tv_origin;    /* device int32[3]: the crop's lowest voxel (x, y, z), read at every step */
 } pmf_batch_desc;
 
 typedef struct pmf_plan pmf_plan;

@@ -62,7 +62,9 @@ class PmfBatchDesc(ct.Structure):
                 ("mbc", PmfGaussians * PMF_MAX_LEVELS), ("views", ct.c_void_p), ("coeff", ct.c_void_p),
                 ("meas", ct.c_void_p), ("loss", ct.c_void_p), ("d_ref", ct.c_void_p * 4),
                 ("d_mbc", (ct.c_void_p * 4) * PMF_MAX_LEVELS), ("d_coeff", ct.c_void_p), ("use_graph", ct.c_int32),
-                ("tune_cache", ct.c_char_p)]
+                ("tune_cache", ct.c_char_p), ("lambda_ssim", ct.c_float), ("lambda_mbc", ct.c_float),
+                ("lambda_tv", ct.c_float), ("ssim_range", ct.c_float), ("tv_size", ct.c_int32),
+                ("tv_origin", ct.c_void_p)]
 
 
 class PmfPlanTensors(ct.Structure):

@@ -36,6 +36,12 @@ struct pmf_plan {
     size_t wc_bytes = 0;
     void* loss_ws = nullptr;
     size_t loss_bytes = 0;
+    void* ssim_ws = nullptr;  // loss_kind 3 only
+    size_t ssim_bytes = 0;
+    void* tv_ws = nullptr;
+    size_t tv_bytes = 0;
+    void* norm_ws = nullptr;
+    size_t norm_bytes = 0;
     pmf::MarchShape fp, bp;  // launch shapes of the projector and its adjoint
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -63,7 +69,15 @@ pmf_status check_desc(const pmf_batch_desc* d) {
     if ((st = validate_dtype(d->dtype)) != PMF_OK) return st;
     PMF_REQUIRE(d->det.nu > 0 && d->det.nv > 0 && d->det.step_mm > 0.0f, "bad detector");
     PMF_REQUIRE(d->batch >= 1, "batch must be >= 1");
-    PMF_REQUIRE(d->loss_kind == 1 || d->loss_kind == 2, "loss_kind must be 1 (L1) or 2 (L2)");
+    PMF_REQUIRE(d->loss_kind >= 1 && d->loss_kind <= 3, "loss_kind must be 1 (L1), 2 (L2) or 3 (Eq. 14)");
+    if (d->loss_kind == 3) {
+        PMF_REQUIRE(isfinite(d->lambda_ssim) && isfinite(d->lambda_mbc) && isfinite(d->lambda_tv),
+                    "Eq. 14 weights must be finite");
+        PMF_REQUIRE(d->ssim_range > 0.0f && isfinite(d->ssim_range), "ssim_range must be positive");
+        PMF_REQUIRE(d->tv_size >= 2 && d->tv_size <= d->grid.nx && d->tv_size <= d->grid.ny &&
+                        d->tv_size <= d->grid.nz, "tv_size must be in [2, min(nx, ny, nz)]");
+        PMF_REQUIRE(d->tv_origin != nullptr, "tv_origin is null");
+    }
     PMF_REQUIRE(d->levels >= 1 && d->levels <= PMF_MAX_LEVELS, "levels must be in [1, %d]", PMF_MAX_LEVELS);
     if ((st = check_gaussians(d->ref, 1, "ref")) != PMF_OK) return st;
     for (int l = 0; l < d->levels; l++) {
@@ -177,10 +191,21 @@ pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
                             p->vox_bytes[1 + l], ps));
     PMF_TRY(warp_combine(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, p->W, ps));
     PMF_TRY(plan_project(p, s));
-    PMF_TRY(projection_loss(d.loss_kind, p->B, p->Q, p->Y, d.meas, d.loss, p->dY, p->loss_ws, p->loss_bytes, ps));
+    const bool eq14 = d.loss_kind == 3;
+    PMF_TRY(projection_loss(eq14 ? 1 : d.loss_kind, p->B, p->Q, p->Y, d.meas, d.loss, p->dY, p->loss_ws,
+                            p->loss_bytes, ps));
+    if (eq14)
+        PMF_TRY(projection_dssim(p->B, d.det.nu, d.det.nv, p->Y, d.meas, d.ssim_range, d.lambda_ssim, d.loss, p->dY, 1,
+                                 p->ssim_ws, p->ssim_bytes, ps));
     PMF_TRY(plan_backproject(p, s));
     PMF_TRY(warp_combine_backward(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, p->dW, p->dV, p->dE, d.d_coeff,
                                   0, p->wc_ws, p->wc_bytes, ps));
+    if (eq14) {
+        PMF_TRY(tv_loss(&d.grid, d.dtype, p->V, d.tv_size, d.tv_origin, d.lambda_tv, d.loss, p->dV, 1, p->tv_ws,
+                        p->tv_bytes, ps));
+        PMF_TRY(mbc_normality(&d.grid, p->L, d.dtype, p->E, d.lambda_mbc, d.loss, p->dE, 1, p->norm_ws, p->norm_bytes,
+                              ps));
+    }
     PMF_TRY(gs_voxelize_backward(&d.grid, &d.ref, p->dV, d.d_ref[0], d.d_ref[1], d.d_ref[2], d.d_ref[3], 0,
                                  p->vb_ws[0], p->vb_bytes[0], ps));
     for (int l = 0; l < p->L; l++)
@@ -258,6 +283,11 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     if (st == PMF_OK) st = conebeam_project_backward_workspace(&d.grid, p->B, p->N, &p->bp_bytes);
     if (st == PMF_OK) st = warp_combine_backward_workspace(&d.grid, p->L, p->B, &p->wc_bytes);
     if (st == PMF_OK) st = projection_loss_workspace((int64_t)(B * Q), &p->loss_bytes);
+    if (st == PMF_OK && desc->loss_kind == 3) {
+        st = projection_dssim_workspace(p->B, desc->det.nu, desc->det.nv, &p->ssim_bytes);
+        if (st == PMF_OK) st = tv_loss_workspace(desc->tv_size, &p->tv_bytes);
+        if (st == PMF_OK) st = mbc_normality_workspace(p->L, &p->norm_bytes);
+    }
     if (st != PMF_OK) {
         delete p;
         return st;
@@ -267,6 +297,9 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     sz.push_back(p->bp_bytes);
     sz.push_back(p->wc_bytes);
     sz.push_back(p->loss_bytes);
+    sz.push_back(p->ssim_bytes);
+    sz.push_back(p->tv_bytes);
+    sz.push_back(p->norm_bytes);
     size_t total = 0;
     for (size_t b : sz) total += align_up(b ? b : 1);
     if (cudaMalloc(&p->mem, total) != cudaSuccess) {
@@ -295,6 +328,9 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     p->bp_ws = take();
     p->wc_ws = take();
     p->loss_ws = take();
+    p->ssim_ws = take();
+    p->tv_ws = take();
+    p->norm_ws = take();
     if (desc->tune_cache) cache_lookup(desc->tune_cache, tune_key(d), p->fp, p->bp);
     *out = p;
     return PMF_OK;

@@ -519,12 +519,23 @@ class _StepBuffers:
     gradients) and the descriptor that points at them."""
 
     def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
-                 dtype: torch.dtype = torch.bfloat16, kind: int = 2):
+                 dtype: torch.dtype = torch.bfloat16, kind=2, eq14: Optional[dict] = None):
         if len(mbc) < 1 or len(mbc) > _lib.PMF_MAX_LEVELS:
             raise ValueError(f"need 1..{_lib.PMF_MAX_LEVELS} MBC levels")
         self.grid, self.det, self.ref, self.mbc = grid, det, ref, list(mbc)
-        self.B, self.L, self.dtype, self.kind = int(batch), len(self.mbc), dtype, int(kind)
+        self.B, self.L, self.dtype = int(batch), len(self.mbc), dtype
         dev = ref.mean.device
+        self.eq14 = None
+        if kind in ("eq14", 3):
+            from .pipeline import EQ14_DEFAULTS
+            q = dict(EQ14_DEFAULTS)
+            q.update(eq14 or {})
+            if q["data_range"] is None:
+                raise ValueError("eq14 needs data_range (the projections' dynamic range)")
+            self.eq14 = q
+            kind = 3
+        self.kind = int(kind)
+        self.tv_origin = torch.zeros(3, dtype=torch.int32, device=dev)
         gr = _det(det)
         self.views = torch.zeros((self.B, 12), dtype=torch.float64, device=dev)
         self.coeff = torch.zeros((self.B, self.L, 3), dtype=torch.float32, device=dev)
@@ -539,10 +550,14 @@ class _StepBuffers:
         self.g_mbc = [grads(m) for m in self.mbc]
         self.d_coeff = torch.zeros((self.B, self.L, 3), dtype=torch.float32, device=dev)
 
-    def set_batch(self, views=None, coeff=None, meas=None) -> None:
+    def set_batch(self, views=None, coeff=None, meas=None, tv_origin=None) -> None:
         for dst, src in ((self.views, views), (self.coeff, coeff), (self.meas, meas)):
             if src is not None:
                 dst.copy_(src.reshape(dst.shape), non_blocking=True)
+        if tv_origin is not None:
+            if not isinstance(tv_origin, torch.Tensor):
+                tv_origin = torch.tensor(list(tv_origin), dtype=torch.int32)
+            self.tv_origin.copy_(tv_origin.to(torch.int32), non_blocking=True)
 
     def desc(self, use_graph: bool = False, tune_cache: Optional[bytes] = None) -> "_lib.PmfBatchDesc":
         d = _lib.PmfBatchDesc()
@@ -559,6 +574,11 @@ class _StepBuffers:
         d.loss, d.d_coeff = self.loss.data_ptr(), self.d_coeff.data_ptr()
         d.use_graph = 1 if use_graph else 0
         d.tune_cache = tune_cache
+        if self.eq14 is not None:
+            q = self.eq14
+            d.lambda_ssim, d.lambda_mbc, d.lambda_tv = float(q["lambda_ssim"]), float(q["lambda_mbc"]), float(q["lambda_tv"])
+            d.ssim_range, d.tv_size = float(q["data_range"]), int(q["tv_size"])
+        d.tv_origin = self.tv_origin.data_ptr()
         return d
 
 
@@ -571,10 +591,12 @@ class Plan(_StepBuffers):
     CUDA graph on the plan's own stream the first time and replayed after."""
 
     def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
-                 dtype: torch.dtype = torch.bfloat16, kind: int = 2, use_graph: bool = False,
-                 tune_cache: Optional[str] = None):
+                 dtype: torch.dtype = torch.bfloat16, kind=2, use_graph: bool = False,
+                 tune_cache: Optional[str] = None, eq14: Optional[dict] = None):
+        """kind 1 / 2: L1 / L2 loss; "eq14" (or 3): the objective of Eq. 14 with
+        `eq14` overriding pipeline.EQ14_DEFAULTS (data_range required)."""
         self._h = None
-        super().__init__(grid, det, ref, mbc, batch, dtype, kind)
+        super().__init__(grid, det, ref, mbc, batch, dtype, kind, eq14)
         dev = ref.mean.device
         self._cache = tune_cache.encode() if tune_cache else None  # kept alive with the descriptor
         self._desc = self.desc(use_graph, self._cache)
@@ -585,10 +607,11 @@ class Plan(_StepBuffers):
         self._h = h
 
     def step(self, views: Optional[torch.Tensor] = None, coeff: Optional[torch.Tensor] = None,
-             meas: Optional[torch.Tensor] = None) -> torch.Tensor:
-        """Copies the batch (when given) into the plan's inputs and enqueues one
-        step on torch's current stream; returns the device loss [1]."""
-        self.set_batch(views, coeff, meas)
+             meas: Optional[torch.Tensor] = None, tv_origin=None) -> torch.Tensor:
+        """Copies the batch (when given; tv_origin: the Eq. 14 TV crop corner)
+        into the plan's inputs and enqueues one step on torch's current stream;
+        returns the device loss [1]."""
+        self.set_batch(views, coeff, meas, tv_origin)
         L = _lib.load()
         if self._stream is None:
             check(L.pmf_plan_step(self._h, _stream()), "pmf_plan_step")

@@ -29,7 +29,8 @@ int main(void) {
     O(pmf_batch_desc, det); O(pmf_batch_desc, dtype); O(pmf_batch_desc, levels); O(pmf_batch_desc, ref);
     O(pmf_batch_desc, mbc); O(pmf_batch_desc, views); O(pmf_batch_desc, loss); O(pmf_batch_desc, d_ref);
     O(pmf_batch_desc, d_mbc); O(pmf_batch_desc, d_coeff); O(pmf_batch_desc, use_graph);
-    O(pmf_batch_desc, tune_cache); O(pmf_plan_tensors, dE);
+    O(pmf_batch_desc, tune_cache); O(pmf_batch_desc, lambda_ssim); O(pmf_batch_desc, ssim_range);
+    O(pmf_batch_desc, tv_size); O(pmf_batch_desc, tv_origin); O(pmf_plan_tensors, dE);
     O(pmf_project_item, views); O(pmf_project_item, vol_stride); O(pmf_backproject_item, vol_stride);
     return 0;
 }
@@ -128,8 +129,8 @@ def _desc(**over):
 
 
 @pytest.mark.parametrize("field,value,msg", [
-    ("batch", 0, b"batch"), ("loss_kind", 3, b"loss_kind"), ("levels", 0, b"levels"), ("levels", 9, b"levels"),
-    ("dtype", 7, b"dtype"), ("views", None, b"null batch pointer"),
+    ("batch", 0, b"batch"), ("loss_kind", 0, b"loss_kind"), ("levels", 0, b"levels"), ("levels", 9, b"levels"),
+    ("dtype", 7, b"dtype"), ("views", None, b"null batch pointer"), ("loss_kind", 4, b"loss_kind"),
 ])
 def test_plan_rejects_bad_descriptors_on_the_host(field, value, msg):
     L = _lib.load()
@@ -158,3 +159,15 @@ def test_autotune_needs_a_cache_path():
 
 def test_destroying_a_null_plan_is_a_no_op():
     assert _lib.load().pmf_plan_destroy(None) == 0
+
+
+def test_plan_rejects_incomplete_eq14_descriptors():
+    L = _lib.load()
+    for field, value, msg in [("ssim_range", 0.0, b"ssim_range"), ("tv_size", 1, b"tv_size"),
+                              ("tv_size", 17, b"tv_size"), ("tv_origin", None, b"tv_origin")]:
+        d = _desc(loss_kind=3, lambda_ssim=0.25, lambda_mbc=1.0, lambda_tv=0.05, ssim_range=100.0, tv_size=8,
+                  tv_origin=1 << 20)
+        setattr(d, field, value)
+        h = ct.c_void_p(0)
+        assert L.pmf_plan_create(ct.byref(d), ct.byref(h)) == -1
+        assert msg in L.pmf_last_error()

@@ -321,6 +321,16 @@ pmf_status mbc_normality_workspace(int32_t L, size_t* bytes);
 pmf_status mbc_normality(const pmf_grid* grid, int32_t L, pmf_dtype dtype, const void* mbc, float weight, float* loss,
                          float* d_mbc, int accumulate, void* ws, size_t ws_bytes, pmf_stream stream);
 
+/* --------------------------------------------------------- optimiser */
+
+/* One Adam update (Kingma & Ba 2014; the optimiser of Sec. 2.3.2) of n
+ * parameters in place at step t >= 1:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p = p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ * param, grad, m, v: device fp32 [n]; m and v start at zero. */
+pmf_status pmf_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr, float beta1,
+                         float beta2, float eps, int32_t t, pmf_stream stream);
+
 /* ------------------------------------------------------------ host helpers */
 
 /* The circular scan of Sec. 2.3.3 / Table I as pmf_view records: view p has

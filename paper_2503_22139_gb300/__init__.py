@@ -10,7 +10,7 @@ argument-marshalling binding.
 from . import ops  # noqa: F401
 from ._lib import PmfError  # noqa: F401
 from .ops import (  # noqa: F401
-    Gaussians, Plan, autotune, circular_views, conebeam_project, conebeam_project_backward,
+    Adam, Gaussians, Plan, adam_step, autotune, circular_views, conebeam_project, conebeam_project_backward,
     conebeam_project_backward_batched, conebeam_project_batched, device_counters, device_status, gs_voxelize,
     gs_voxelize_backward, gs_voxelize_count, mbc_combine, mbc_combine_backward, mbc_normality, projection_dssim,
     projection_loss, tv_loss, views_tensor,
@@ -18,7 +18,7 @@ from .ops import (  # noqa: F401
 )
 
 __all__ = [
-    "Gaussians", "Plan", "PmfError", "autotune", "circular_views", "conebeam_project", "conebeam_project_backward",
+    "Adam", "Gaussians", "Plan", "PmfError", "adam_step", "autotune", "circular_views", "conebeam_project", "conebeam_project_backward",
     "conebeam_project_backward_batched", "conebeam_project_batched", "device_counters", "device_status",
     "gs_voxelize", "gs_voxelize_backward", "gs_voxelize_count", "mbc_combine", "mbc_combine_backward",
     "mbc_normality", "projection_dssim", "projection_loss", "tv_loss", "views_tensor", "warp_combine", "warp_combine_backward", "warp_volume",

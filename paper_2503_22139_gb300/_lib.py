@@ -113,6 +113,7 @@ SIGNATURES = {
     "tv_loss": [_G, ct.c_int, _P, _I32, _P, ct.c_float, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
     "mbc_normality_workspace": [_I32, _SZ],
     "mbc_normality": [_G, _I32, ct.c_int, _P, ct.c_float, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
+    "pmf_adam_step": [_I64, _P, _P, _P, _P, ct.c_float, ct.c_float, ct.c_float, ct.c_float, _I32, _P],
     "pmf_circular_views": [_I32, ct.c_double, ct.c_double, ct.c_double, ct.c_double, _I32, _I32, ct.POINTER(PmfView)],
     "pmf_workspace_size": [_I32, ct.POINTER(PmfWsArgs), _SZ],
     "pmf_device_counters": [ct.POINTER(ct.c_uint64), _I32],

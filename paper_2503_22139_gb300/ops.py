@@ -445,6 +445,43 @@ def mbc_normality(grid, mbc: torch.Tensor, weight: float = 1.0, with_grad: bool 
     return loss, (d_mbc if with_grad else None)
 
 
+# ------------------------------------------------------------ optimiser
+
+def pmf_adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float,
+                  t: int, betas=(0.9, 0.999), eps: float = 1e-8) -> None:
+    """One in-place Adam update of a contiguous fp32 device tensor (step t >= 1)."""
+    for name, x in (("param", param), ("grad", grad), ("m", m), ("v", v)):
+        _need(x, name, torch.float32)
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if not (param.shape == grad.shape == m.shape == v.shape):
+        raise ValueError("param, grad, m and v must have one shape")
+    check(_lib.load().pmf_adam_step(param.numel(), _p(param), _p(grad), _p(m), _p(v), float(lr), float(betas[0]),
+                                    float(betas[1]), float(eps), int(t), _stream()), "pmf_adam_step")
+
+
+adam_step = pmf_adam_step
+
+
+class Adam:
+    """Adam state for a list of parameter tensors (lr: one rate, or one per
+    tensor); step(grads) updates them in place."""
+
+    def __init__(self, params: Sequence[torch.Tensor], lr=1e-3, betas=(0.9, 0.999), eps: float = 1e-8):
+        self.params = list(params)
+        self.lrs = [float(x) for x in lr] if isinstance(lr, (list, tuple)) else [float(lr)] * len(self.params)
+        if len(self.lrs) != len(self.params):
+            raise ValueError("one learning rate per parameter tensor")
+        self.betas, self.eps, self.t = betas, float(eps), 0
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+
+    def step(self, grads: Sequence[torch.Tensor]) -> None:
+        self.t += 1
+        for p, g, m, v, lr in zip(self.params, grads, self.m, self.v, self.lrs):
+            pmf_adam_step(p, g, m, v, lr, self.t, self.betas, self.eps)
+
+
 def library_info() -> dict:
     L = _lib.load()
     return {"version": L.pmf_version().decode(), "path": _lib.library_path()}

@@ -518,6 +518,64 @@ def run_native(a):
             torch.cuda.empty_cache()
         variants[f"batched_{main_dt}_over_plain_f32"] = round(value / variants["plain_per_projection_f32"], 3)
 
+        def timed_steps(run, n):
+            for k in range(2):
+                run(k)
+            torch.cuda.synchronize()
+            if world > 1:
+                tdist.barrier()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for k in range(n):
+                run(a.warmup + k)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            tv = v0.elapsed_time(v1) / 1e3
+            if world > 1:
+                tt = torch.tensor([tv], device="cuda")
+                tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+                tv = float(tt.item())
+            return B * n * world / tv
+
+        # the Stage 2-3 objective of Eq. 14 (L1 + 0.25 D-SSIM + L_MBC + 0.05 TV on a
+        # 32^3 crop drawn per step from a seeded generator)
+        drange = float((meas_all.max() - meas_all.min()).item())
+        tv_rng = np.random.default_rng(4242)
+        n_orig = 64
+        origins = torch.tensor(np.stack([tv_rng.integers(0, [wl.grid.nx - 31, wl.grid.ny - 31, wl.grid.nz - 31])
+                                         for _ in range(n_orig)]), dtype=torch.int32, device="cuda")
+        estep = ForwardAdjoint(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind="eq14",
+                               eq14=dict(data_range=drange))
+        variants[f"eq14_objective_{a.dtype}"] = round(
+            timed_steps(lambda k: estep.run(*batch(k), tv_origin=origins[k % n_orig]), a.steps), 3)
+        del estep
+        torch.cuda.empty_cache()
+        # 100 optimisation iterations (B projections each, Adam on every Gaussian
+        # parameter of copies of the sets); throughput and the loss trajectory
+        def clone_set(gs):
+            return pmf.Gaussians(gs.mean.clone(), gs.scale.clone(), gs.quat.clone(), gs.value.clone(), gs.kappa)
+        tref, tmbc = clone_set(ref), [clone_set(m) for m in mbc]
+        tstep = ForwardAdjoint(wl.grid, wl.det, tref, tmbc, batch=B, dtype=dt, kind=a.kind)
+        params, lrs = [], []
+        for gs in [tref] + tmbc:
+            params += [gs.mean, gs.scale, gs.quat, gs.value]
+            lrs += [0.02, 0.005, 0.002, 0.002 if gs.channels == 1 else 0.01]
+        opt = pmf.Adam(params, lr=lrs)
+        grads_of = lambda: [g for gl in [tstep.g_ref] + tstep.g_mbc for g in gl]
+        traj = []
+
+        def train(k):
+            loss_k = tstep.run(*batch(k))
+            opt.step(grads_of())
+            if k in (a.warmup, a.warmup + 99):
+                traj.append(loss_k.clone())
+
+        variants[f"train_100_iterations_{a.dtype}"] = round(timed_steps(train, 100), 3)
+        variants["train_loss_first_last"] = [round(float(t.item()), 3) for t in traj]
+        del tstep, opt
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(wl, meas_np, small=a.small)

@@ -143,10 +143,10 @@ def build_workload(small: bool):
     import numpy as np
     import synth
     if small:
-        wl = synth.config0(with_measured=True)
+        wl = synth.small_workload(with_measured=True)
         return wl, wl.measured
-    wl = synth.config1(p=660)
-    meas = synth.measured_projections(np.random.default_rng(synth.seeds_for(1)["measured"]), wl.p, wl.det.nu,
+    wl = synth.paper_workload(p=660)
+    meas = synth.measured_projections(np.random.default_rng(synth.seeds_for("paper")["measured"]), wl.p, wl.det.nu,
                                       wl.det.nv, 400.0)
     return wl, meas
 
@@ -331,7 +331,7 @@ def run_native(a):
     # per launch (B views): exact counts on up to 64 of the timed views, scaled
     sub = timed_views[np.linspace(0, len(timed_views) - 1, min(64, len(timed_views))).astype(int)]
     samples = float(samples_per_view(wl.grid, wl.det, sub).mean()) * B
-    workload_tag = f"{'small' if a.small else 'config1'}-{a.dtype}-B{B}"
+    workload_tag = f"{'small' if a.small else 'paper'}-{a.dtype}-B{B}"
     stage_roof = {}
     for st, ms in stage_ms.items():
         per_launch_ms = ms / max(1, len(ev[st]) // a.steps)

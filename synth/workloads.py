@@ -100,11 +100,12 @@ class Workload:
         return len(self.mbc)
 
 
-def seeds_for(config: int) -> dict:
-    """Seed plan: config k draws from 1000*(k+1) + {0: reference Gaussians,
-    1: MBC Gaussians, 2: temporal coefficients, 3: smooth stand-in projections,
-    4: the ground-truth reference Gaussian set}."""
-    base = 1000 * (config + 1)
+def seeds_for(workload: str) -> dict:
+    """Seed plan: workload k (0 = the small case, 1 = the paper-scale case)
+    draws from 1000*(k+1) + {0: reference Gaussians, 1: MBC Gaussians,
+    2: temporal coefficients, 3: smooth stand-in projections, 4: the
+    ground-truth reference Gaussian set}."""
+    base = 1000 * ({"small": 0, "paper": 1}[workload] + 1)
     return {"ref": base, "mbc": base + 1, "coeff": base + 2, "measured": base + 3, "gt": base + 4}
 
 
@@ -221,12 +222,12 @@ def select_batch(p_total: int, batch: int, step: int, seed: int = 7) -> np.ndarr
     return perm[idx]
 
 
-def config0(with_measured: bool = True) -> Workload:
+def small_workload(with_measured: bool = True) -> Workload:
     """Small case: 64^3 at 4 mm, 2,000 reference Gaussians (scales 1-4 voxels),
     one MBC level of 200 Gaussians with N(0, 2 mm) vectors, 8 views over 360
     degrees, 128x128 detector at 1.6 mm, SAD/SDD 1000/1500 mm, 0.5-voxel step,
     coefficients U[-1, 1]."""
-    sd = seeds_for(0)
+    sd = seeds_for("small")
     grid = Grid(64, 64, 64, 4.0, 4.0, 4.0)
     det = Detector(128, 128, 2.0)
     ref = gaussian_set(np.random.default_rng(sd["ref"]), grid, 2000, 1.0, 4.0)
@@ -235,16 +236,16 @@ def config0(with_measured: bool = True) -> Workload:
     coeff = uniform_coefficients(np.random.default_rng(sd["coeff"]), 8, 1)
     meas = (measured_projections(np.random.default_rng(sd["measured"]), 8, det.nu, det.nv, 200.0)
             if with_measured else None)
-    return Workload("config0-64^3-2k-8views", grid, det, ref, mbc, views, coeff, 3.0, meas)
+    return Workload("small-64^3-2k-8views", grid, det, ref, mbc, views, coeff, 3.0, meas)
 
 
-def config1(p: int = 660, with_measured: bool = False, measured_for=None) -> Workload:
+def paper_workload(p: int = 660, with_measured: bool = False, measured_for=None) -> Workload:
     """Paper-scale case: 200x200x100 at 2 mm with 100,000 reference Gaussians
     (scales 0.5-3 voxels); MBC levels of 500 / 2,000 / 8,000 Gaussians with
     5 / 2 / 1 mm vectors; 660 views over 360 degrees, 512x384 detector at
     0.776 mm, SAD/SDD 1000/1500 mm, 1 mm step (0.5 voxel); breathing
     coefficients at 11 frames/s with a ~4 s period."""
-    sd = seeds_for(1)
+    sd = seeds_for("paper")
     grid = Grid(200, 200, 100, 2.0, 2.0, 2.0)
     det = Detector(512, 384, 1.0)
     ref = gaussian_set(np.random.default_rng(sd["ref"]), grid, 100_000, 0.5, 3.0)
@@ -258,7 +259,7 @@ def config1(p: int = 660, with_measured: bool = False, measured_for=None) -> Wor
     # a second draw of the reference recipe: the training target is its
     # projections through the same forward model (same MBCs and coefficients)
     gt = gaussian_set(np.random.default_rng(sd["gt"]), grid, 100_000, 0.5, 3.0)
-    return Workload("config1-200x200x100-100k-660views", grid, det, ref, mbc, views, coeff, 3.0, meas, gt=gt)
+    return Workload("paper-200x200x100-100k-660views", grid, det, ref, mbc, views, coeff, 3.0, meas, gt=gt)
 
 
 def fd_subproblem(seed: int = 3000) -> Workload:
@@ -276,7 +277,7 @@ def fd_subproblem(seed: int = 3000) -> Workload:
     return Workload("fd-16^3-200-4views", grid, det, ref, mbc, views, coeff, float("inf"), meas)
 
 
-def config3_volumes():
+def uneven_volumes():
     """Uneven batch: four volumes at 2 mm (128^2x64, 160^2x80, 200^2x100,
     256^2x128) holding 30k / 50k / 100k / 150k Gaussians, three MBC levels as
     in the paper-scale case, and 17 / 40 / 64 / 96 views each (512x384)."""

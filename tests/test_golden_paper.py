@@ -5,13 +5,13 @@ import os
 
 import numpy as np
 
-from synth import config1
+from synth import paper_workload
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
 
 
 def test_paper_scale_workload_matches_table_one_and_protocol():
-    wl = config1(p=660)
+    wl = paper_workload(p=660)
     pg, xp, md = GOLD["patient_geometry"], GOLD["xcat_protocol"], GOLD["model"]
     g = wl.grid
     assert [g.nx, g.ny, g.nz] == pg["volume_voxels"]

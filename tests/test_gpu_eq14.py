@@ -7,7 +7,7 @@ import torch
 
 import paper_2503_22139_gb300 as pmf
 from paper_2503_22139_gb300.pipeline import ForwardAdjoint
-from synth import config0, fd_subproblem
+from synth import small_workload, fd_subproblem
 from tests import oracle_chain
 from tests.gpu_util import dev, gset, host, rel_l2, views
 
@@ -24,7 +24,7 @@ def _normalise_mbc(wl):
     return wl
 
 
-@pytest.mark.parametrize("make,tv", [(fd_subproblem, (8, (3, 4, 5))), (config0, (32, (10, 20, 5)))])
+@pytest.mark.parametrize("make,tv", [(fd_subproblem, (8, (3, 4, 5))), (small_workload, (32, (10, 20, 5)))])
 def test_eq14_step_matches_oracle(make, tv):
     wl = _normalise_mbc(make())
     meas = wl.measured

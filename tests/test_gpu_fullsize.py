@@ -11,7 +11,7 @@ import torch
 import oracle
 import paper_2503_22139_gb300 as pmf
 from paper_2503_22139_gb300.pipeline import ForwardAdjoint
-from synth import config1, select_batch
+from synth import paper_workload, select_batch
 from tests.gpu_util import assert_voxels_match, dev, gset, host, pixel_views, rel_l2, views
 
 pytestmark = pytest.mark.gpu
@@ -21,7 +21,7 @@ B = 32
 
 @pytest.fixture(scope="module")
 def wl():
-    return config1(p=660)
+    return paper_workload(p=660)
 
 
 @pytest.fixture(scope="module")

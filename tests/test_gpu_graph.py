@@ -5,14 +5,14 @@ import pytest
 import torch
 
 from paper_2503_22139_gb300.pipeline import ForwardAdjoint, GraphedStep
-from synth import config0
+from synth import small_workload
 from tests.gpu_util import dev, gset, views
 
 pytestmark = pytest.mark.gpu
 
 
 def test_graph_replay_matches_eager():
-    wl = config0()
+    wl = small_workload()
     mk = lambda: ForwardAdjoint(wl.grid, wl.det, gset(wl.ref, wl.kappa), [gset(m, wl.kappa) for m in wl.mbc],
                                 batch=4)
     eager, cap = mk(), mk()

@@ -8,7 +8,7 @@ import torch
 
 import paper_2503_22139_gb300 as pmf
 from paper_2503_22139_gb300.pipeline import ForwardAdjoint
-from synth import config0
+from synth import small_workload
 from tests.gpu_util import dev, gset, views
 
 pytestmark = pytest.mark.gpu
@@ -29,7 +29,7 @@ def test_adam_matches_torch_optim_adam():
 
 
 def test_adam_fit_to_ground_truth_projections_lowers_the_loss():
-    wl = config0()
+    wl = small_workload()
     gt = gset(wl.ref, wl.kappa)
     mbc = [gset(m, wl.kappa) for m in wl.mbc]
     vt, coeff = views(wl.views), dev(wl.coeff)

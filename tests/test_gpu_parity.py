@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import paper_2503_22139_gb300 as pmf
-from synth import Detector, Grid, circular_views, config0, fd_subproblem, gaussian_set, mbc_levels
+from synth import Detector, Grid, circular_views, small_workload, fd_subproblem, gaussian_set, mbc_levels
 from tests import oracle_chain
 from tests.gpu_util import assert_voxels_match, dev, gset, host, pixel_views, rel_l2, views
 
@@ -37,8 +37,8 @@ def test_voxelize_ragged_grid(kappa):
     assert_voxels_match(got, ref, amb, TOL32)
 
 
-def test_voxelize_config0_reference_and_mbc():
-    wl = config0(with_measured=False)
+def test_voxelize_small_workload_reference_and_mbc():
+    wl = small_workload(with_measured=False)
     for gs in (wl.ref, wl.mbc[0]):
         got = host(pmf.gs_voxelize(wl.grid, gset(gs, wl.kappa)))
         ref = oracle.voxelize(wl.grid, gs.mean, gs.scale, gs.quat, gs.value, wl.kappa)
@@ -74,7 +74,7 @@ def test_voxelize_edge_cases():
 
 
 def test_voxelize_is_bit_reproducible():
-    wl = config0(with_measured=False)
+    wl = small_workload(with_measured=False)
     gs = gset(wl.mbc[0], wl.kappa)
     a = pmf.gs_voxelize(wl.grid, gs)
     b = pmf.gs_voxelize(wl.grid, gs)
@@ -178,8 +178,8 @@ def test_project_ragged_detector(nu, nv):
     assert rel_l2(got, ref) <= TOL32
 
 
-def test_project_config0_voxelized_reference():
-    wl = config0(with_measured=False)
+def test_project_small_workload_voxelized_reference():
+    wl = small_workload(with_measured=False)
     V = pmf.gs_voxelize(wl.grid, gset(wl.ref, wl.kappa))[0]
     Vh = host(V)
     got = host(pmf.conebeam_project(wl.grid, wl.det, views(wl.views), V, shared=True))
@@ -256,8 +256,8 @@ def test_full_chain_forward_and_gradients_match_oracle(kind):
             assert rel_l2(host(grads["mbc"][l][i]), gref["mbc"][l][i]) <= 1e-3
 
 
-def test_config0_chain_forward_matches_oracle():
-    wl = config0()
+def test_small_workload_chain_forward_matches_oracle():
+    wl = small_workload()
     loss, Y, _ = _gpu_step(wl, wl.measured)
     f = oracle_chain.forward(wl)
     assert rel_l2(host(Y), f["Y"]) <= TOL32

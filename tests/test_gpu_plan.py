@@ -10,7 +10,7 @@ import torch
 
 import paper_2503_22139_gb300 as pmf
 from paper_2503_22139_gb300.pipeline import ForwardAdjoint
-from synth import config0
+from synth import small_workload
 from tests.gpu_util import dev, gset, views
 
 pytestmark = pytest.mark.gpu
@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def wl():
-    return config0()
+    return small_workload()
 
 
 def _sets(wl):

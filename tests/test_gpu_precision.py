@@ -8,7 +8,7 @@ import torch
 
 import paper_2503_22139_gb300 as pmf
 from paper_2503_22139_gb300.pipeline import ForwardAdjoint, PlainPerProjection
-from synth import config0
+from synth import small_workload
 from tests import oracle_chain
 from tests.gpu_util import dev, gset, host, rel_l2, views
 
@@ -20,7 +20,7 @@ UNIT = {torch.bfloat16: 2.0 ** -8, torch.float16: 2.0 ** -11, torch.float32: 2.0
 
 @pytest.fixture(scope="module")
 def ref_step():
-    wl = config0()
+    wl = small_workload()
     loss, grads, f = oracle_chain.step(wl, wl.measured, kind=2)
     return wl, loss, grads, f
 

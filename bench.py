@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="bf16",
-                    help="storage type of V, E, W (all arithmetic and gradients are fp32)")
+                    help="storage type of V and E (all arithmetic and gradients are fp32)")
+    ap.add_argument("--w-dtype", choices=["f32", "same"], default="f32",
+                    help="storage type of the warped volumes W: fp32, or the same as V and E")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the batched-fp32 and plain per-projection fp32 comparison runs")
     ap.add_argument("--batch", type=int, default=32)
@@ -151,14 +153,15 @@ def build_workload(small: bool):
     return wl, meas
 
 
-def algorithmic_bytes(stage: str, B: int, n: int, q: int, L: int, esz: int) -> float:
-    """Bytes each stage must move at least once per launch (B projections)."""
+def algorithmic_bytes(stage: str, B: int, n: int, q: int, L: int, esz: int, wsz: int) -> float:
+    """Bytes each stage must move at least once per launch (B projections);
+    esz: bytes per element of V and E, wsz: of the warped volumes W."""
     if stage == "conebeam_project":
-        return B * (n * esz + q * 4 + 96)
+        return B * (n * wsz + q * 4 + 96)
     if stage == "conebeam_project_backward":
         return B * (q * 4 + n * 4 + 96)
     if stage == "warp_combine":
-        return L * 3 * n * esz + n * esz + B * n * esz
+        return L * 3 * n * esz + n * esz + B * n * wsz
     if stage == "warp_combine_backward":
         return B * n * 4 + L * 3 * n * esz + n * esz + n * 4 + L * 3 * n * 4
     if stage == "projection_loss":
@@ -229,6 +232,7 @@ def run_native(a):
     if world > 1:
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
+    wdt = torch.float32 if a.w_dtype == "f32" else dt
     wl, meas_np = build_workload(a.small)
     B = min(a.batch, wl.p)
     perm = synth.select_batch(wl.p, wl.p, 0)  # one permutation of the scan; batches are its slices
@@ -259,7 +263,7 @@ def run_native(a):
         torch.cuda.synchronize()
     else:
         meas_all = d(meas_np[perm])
-    step = ForwardAdjoint(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind)
+    step = ForwardAdjoint(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind, w_dtype=wdt)
 
     stage_names = ["gs_voxelize", "warp_combine", "conebeam_project", "projection_loss",
                    "conebeam_project_backward", "warp_combine_backward", "gs_voxelize_backward"]
@@ -323,6 +327,7 @@ def run_native(a):
     # a trilinear gather or scatter), the streaming stages by HBM
     n, q, L = wl.grid.n, wl.det.q, wl.levels
     esz = torch.tensor([], dtype=dt).element_size()
+    wsz = torch.tensor([], dtype=wdt).element_size()
     hbm_peak, hsrc = peaks()
     f32_peak, fsrc = fp32_peak()
     timed_views = np.concatenate([wl.views[perm][((rank * 7919 + a.warmup + k) % nbatch) * B:
@@ -331,12 +336,12 @@ def run_native(a):
     # per launch (B views): exact counts on up to 64 of the timed views, scaled
     sub = timed_views[np.linspace(0, len(timed_views) - 1, min(64, len(timed_views))).astype(int)]
     samples = float(samples_per_view(wl.grid, wl.det, sub).mean()) * B
-    workload_tag = f"{'small' if a.small else 'paper'}-{a.dtype}-B{B}"
+    workload_tag = f"{'small' if a.small else 'paper'}-{a.dtype}{'-wf32' if wdt != dt else ''}-B{B}"
     stage_roof = {}
     for st, ms in stage_ms.items():
         per_launch_ms = ms / max(1, len(ev[st]) // a.steps)
         sec = per_launch_ms / 1e3
-        alg_b = algorithmic_bytes(st, B, n, q, L, esz)
+        alg_b = algorithmic_bytes(st, B, n, q, L, esz, wsz)
         ent = {"avg_launch_ms": round(per_launch_ms, 4)}
         if alg_b:
             ent.update({"hbm_achieved_gbs": round(alg_b / sec / 1e9, 2), "hbm_frac": round(alg_b / sec / 1e9 / hbm_peak, 5),
@@ -352,10 +357,13 @@ def run_native(a):
         stage_roof[st] = ent
     dom = max(stage_ms, key=stage_ms.get)
     d = stage_roof[dom]
-    roof = {"kernel": KERNEL_OF.get(dom, dom), "stage": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
+    kernel_of = dict(KERNEL_OF)
+    if wdt == torch.float32:  # fp32 volumes: the box is staged with bulk tensor copies
+        kernel_of["conebeam_project"] = "k_project_tma"
+    roof = {"kernel": kernel_of.get(dom, dom), "stage": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
             "peak": d.get("peak"), "unit": d.get("unit"), "frac": d.get("frac"),
             "peak_source": (f"{fsrc}" if d.get("unit") == "TFLOP/s" else f"{hsrc} hbm_gbs"),
-            "traffic": traffic_for(KERNEL_OF.get(dom, dom), workload_tag),
+            "traffic": traffic_for(kernel_of.get(dom, dom), workload_tag),
             "hbm_frac": d.get("hbm_frac"), "avg_launch_ms": d["avg_launch_ms"]}
 
     # end to end: pinned host inputs -> device -> step -> gradients back to pinned host
@@ -438,7 +446,7 @@ def run_native(a):
         variants[f"graph_replay_{a.dtype}"] = round(B * a.steps * world / tg, 3)
         del gstep
         # the native plan (C++ step, captured into a CUDA graph on its own stream)
-        plan = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind, use_graph=True)
+        plan = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind, use_graph=True, w_dtype=wdt)
         for k in range(2):
             plan.step(*batch(k))
         torch.cuda.synchronize()
@@ -461,9 +469,9 @@ def run_native(a):
         with tempfile.TemporaryDirectory() as td:
             cache = os.path.join(td, "tune.txt")
             pmf.autotune(wl.grid, wl.det, ref, mbc, B, cache, dtype=dt, kind=a.kind, views=batch(0)[0],
-                         coeff=batch(0)[1], meas=batch(0)[2])
+                         coeff=batch(0)[1], meas=batch(0)[2], w_dtype=wdt)
             plan = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind, use_graph=True,
-                            tune_cache=cache)
+                            tune_cache=cache, w_dtype=wdt)
         for k in range(2):
             plan.step(*batch(k))
         torch.cuda.synchronize()
@@ -546,7 +554,7 @@ def run_native(a):
         origins = torch.tensor(np.stack([tv_rng.integers(0, [wl.grid.nx - 31, wl.grid.ny - 31, wl.grid.nz - 31])
                                          for _ in range(n_orig)]), dtype=torch.int32, device="cuda")
         estep = ForwardAdjoint(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind="eq14",
-                               eq14=dict(data_range=drange))
+                               eq14=dict(data_range=drange), w_dtype=wdt)
         variants[f"eq14_objective_{a.dtype}"] = round(
             timed_steps(lambda k: estep.run(*batch(k), tv_origin=origins[k % n_orig]), a.steps), 3)
         del estep
@@ -556,7 +564,7 @@ def run_native(a):
         def clone_set(gs):
             return pmf.Gaussians(gs.mean.clone(), gs.scale.clone(), gs.quat.clone(), gs.value.clone(), gs.kappa)
         tref, tmbc = clone_set(ref), [clone_set(m) for m in mbc]
-        tstep = ForwardAdjoint(wl.grid, wl.det, tref, tmbc, batch=B, dtype=dt, kind=a.kind)
+        tstep = ForwardAdjoint(wl.grid, wl.det, tref, tmbc, batch=B, dtype=dt, kind=a.kind, w_dtype=wdt)
         params, lrs = [], []
         for gs in [tref] + tmbc:
             params += [gs.mean, gs.scale, gs.quat, gs.value]
@@ -588,6 +596,7 @@ def run_native(a):
                  "through the same forward" if wl.gt is not None else "synthetic"),
         "config": {"workload": WORKLOAD if not a.small else "small: 64^3 @4mm, 2k Gaussians, 128^2 det, 8 views",
                    "batch_projections": B, "loss": "L2" if a.kind == 2 else "L1", "storage_dtype": a.dtype,
+                   "warped_volume_dtype": "f32" if wdt == torch.float32 else a.dtype,
                    "accumulate_dtype": "f32", "l2_policy": "working set > L2 (E 144 MB, W and dW 512 MB each)",
                    "parallelism": f"replicas{world}"},
         "roofline": roof, "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},

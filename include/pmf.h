@@ -55,7 +55,7 @@ typedef enum {
     PMF_EINVAL = -1,      /* bad argument (null pointer, size, geometry) */
     PMF_ECUDA = -2,       /* a CUDA launch or call failed */
     PMF_EWORKSPACE = -3,  /* ws too small or misaligned */
-    PMF_ETIMEOUT = -4,    /* reserved: a bounded device wait gave up */
+    PMF_ETIMEOUT = -4,    /* a bounded device wait gave up (reported by pmf_device_status) */
     PMF_EUNSUPPORTED = -5 /* valid but not implemented (e.g. channels > 4) */
 } pmf_status;
 
@@ -194,6 +194,12 @@ pmf_status warp_volume_backward(const pmf_grid* grid, int32_t P, pmf_dtype dtype
  * The DVF is never stored; each voxel's MBC vectors are read once for all P. */
 pmf_status warp_combine(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
                         const void* mbc, const float* coeff, void* out, pmf_stream stream);
+
+/* warp_combine with the warped volumes written in out_dtype, which is either
+ * dtype or PMF_F32: with reference and MBC grids in bf16/fp16, the projector
+ * can then read fp32 warped volumes (and stage them with bulk tensor copies). */
+pmf_status warp_combine_mixed(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
+                              const void* mbc, const float* coeff, pmf_dtype out_dtype, void* out, pmf_stream stream);
 
 pmf_status warp_combine_backward_workspace(const pmf_grid* grid, int32_t L, int32_t P, size_t* bytes);
 
@@ -381,7 +387,9 @@ typedef enum {
                                               4-voxel halo (those corners use global atomics) */
     PMF_DIAG_NONFINITE = 4,                /* fixed-point scatters or voxelizations whose input
                                               magnitude was NaN or infinite (outputs set to NaN) */
-    PMF_DIAG_COUNT = 5
+    PMF_DIAG_TIMEOUT = 5,                  /* CTAs whose bounded wait for a bulk (TMA) copy ran out
+                                              (about one second); their outputs are set to NaN */
+    PMF_DIAG_COUNT = 6
 } pmf_diag;
 
 /* Copies the current device's counters to host_out[PMF_DIAG_COUNT] and, with
@@ -389,9 +397,10 @@ typedef enum {
 pmf_status pmf_device_counters(uint64_t* host_out, int32_t reset);
 
 /* Synchronizes `stream` and reports what the device saw: PMF_ECUDA (with the
- * CUDA message) if the stream's work failed, PMF_EINVAL if a non-finite input
- * reached a fixed-point scatter since the counters were last reset, else PMF_OK.
- * No kernel of this library waits on another CTA, so there is no timeout flag. */
+ * CUDA message) if the stream's work failed, PMF_ETIMEOUT if a bounded wait for
+ * a bulk copy gave up, PMF_EINVAL if a non-finite input reached a fixed-point
+ * scatter since the counters were last reset, else PMF_OK.  No kernel waits on
+ * another CTA. */
 pmf_status pmf_device_status(pmf_stream stream);
 
 /* ------------------------------------------------ training-step plans */
@@ -434,13 +443,14 @@ typedef struct {
     float ssim_range;            /* D-SSIM data range (> 0) */
     int32_t tv_size;             /* edge D of the TV crop (paper: 32) */
     const int32_t* tv_origin;    /* device int32[3]: the crop's lowest voxel (x, y, z), read at every step */
+    pmf_dtype w_dtype;           /* storage of the warped volumes W: dtype or PMF_F32 (0, the default) */
 } pmf_batch_desc;
 
 typedef struct pmf_plan pmf_plan;
 
-/* Device tensors the plan owns (valid until pmf_plan_destroy): V [N], E [L][3][N]
- * and W [B][N] in the plan's dtype; fp32 Y, dY [B][nv][nu], dW [B][N], dV [N],
- * dE [L][3][N]. */
+/* Device tensors the plan owns (valid until pmf_plan_destroy): V [N] and E [L][3][N]
+ * in the plan's dtype, W [B][N] in the descriptor's w_dtype; fp32 Y, dY [B][nv][nu],
+ * dW [B][N], dV [N], dE [L][3][N]. */
 typedef struct {
     void* V;
     void* E;

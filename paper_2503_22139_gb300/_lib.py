@@ -44,9 +44,9 @@ class PmfBackprojectItem(ct.Structure):
 
 
 PMF_MAX_LEVELS = 8
-PMF_DIAG_COUNT = 5
+PMF_DIAG_COUNT = 6
 DIAG_NAMES = ("voxelize_list_overflow", "project_box_fallback", "backproject_box_fallback", "warp_halo_exit",
-              "nonfinite")
+              "nonfinite", "timeout")
 PMF_OPS = {"voxelize": 1, "voxelize_backward": 2, "combine_backward": 3, "warp_backward": 4,
            "warp_combine_backward": 5, "project_backward": 6, "loss": 7}
 
@@ -64,7 +64,7 @@ class PmfBatchDesc(ct.Structure):
                 ("d_mbc", (ct.c_void_p * 4) * PMF_MAX_LEVELS), ("d_coeff", ct.c_void_p), ("use_graph", ct.c_int32),
                 ("tune_cache", ct.c_char_p), ("lambda_ssim", ct.c_float), ("lambda_mbc", ct.c_float),
                 ("lambda_tv", ct.c_float), ("ssim_range", ct.c_float), ("tv_size", ct.c_int32),
-                ("tv_origin", ct.c_void_p)]
+                ("tv_origin", ct.c_void_p), ("w_dtype", ct.c_int)]
 
 
 class PmfPlanTensors(ct.Structure):
@@ -97,6 +97,7 @@ SIGNATURES = {
     "warp_volume_backward_workspace": [_G, _I32, _SZ],
     "warp_volume_backward": [_G, _I32, ct.c_int, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
     "warp_combine": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P],
+    "warp_combine_mixed": [_G, _I32, _I32, ct.c_int, _P, _P, _P, ct.c_int, _P, _P],
     "warp_combine_backward_workspace": [_G, _I32, _I32, _SZ],
     "warp_combine_backward": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
     "conebeam_project": [_G, ct.POINTER(PmfDetector), _I32, _P, ct.c_int, _P, _I64, _P, _P],

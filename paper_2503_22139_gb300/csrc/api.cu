@@ -120,6 +120,9 @@ pmf_status pmf_device_status(pmf_stream stream) {
     uint64_t c[PMF_DIAG_COUNT];
     pmf_status st = pmf_device_counters(c, 0);
     if (st != PMF_OK) return st;
+    if (c[PMF_DIAG_TIMEOUT] != 0)
+        return pmf::set_error(PMF_ETIMEOUT, "%llu CTAs gave up waiting for a bulk copy (outputs are NaN)",
+                              (unsigned long long)c[PMF_DIAG_TIMEOUT]);
     if (c[PMF_DIAG_NONFINITE] != 0)
         return pmf::set_error(PMF_EINVAL, "%llu launches saw a NaN or infinite input magnitude (outputs are NaN)",
                               (unsigned long long)c[PMF_DIAG_NONFINITE]);

@@ -67,6 +67,7 @@ pmf_status check_desc(const pmf_batch_desc* d) {
     pmf_status st = validate_grid(&d->grid);
     if (st != PMF_OK) return st;
     if ((st = validate_dtype(d->dtype)) != PMF_OK) return st;
+    PMF_REQUIRE(d->w_dtype == d->dtype || d->w_dtype == PMF_F32, "w_dtype must be dtype or PMF_F32");
     PMF_REQUIRE(d->det.nu > 0 && d->det.nv > 0 && d->det.step_mm > 0.0f, "bad detector");
     PMF_REQUIRE(d->batch >= 1, "batch must be >= 1");
     PMF_REQUIRE(d->loss_kind >= 1 && d->loss_kind <= 3, "loss_kind must be 1 (L1), 2 (L2) or 3 (Eq. 14)");
@@ -104,9 +105,9 @@ std::string tune_key(const pmf_batch_desc& d) {
     for (char& c : name)
         if (c == ' ' || c == '\t') c = '_';
     char buf[512];
-    snprintf(buf, sizeof(buf), "dev=%s;sm=%d;grid=%dx%dx%d@%g,%g,%g;det=%dx%d@%g;B=%d;L=%d;dtype=%d", name.c_str(), sms,
+    snprintf(buf, sizeof(buf), "dev=%s;sm=%d;grid=%dx%dx%d@%g,%g,%g;det=%dx%d@%g;B=%d;L=%d;dtype=%d;w=%d", name.c_str(), sms,
              d.grid.nx, d.grid.ny, d.grid.nz, (double)d.grid.vx, (double)d.grid.vy, (double)d.grid.vz, d.det.nu,
-             d.det.nv, (double)d.det.step_mm, d.batch, d.levels, (int)d.dtype);
+             d.det.nv, (double)d.det.step_mm, d.batch, d.levels, (int)d.dtype, (int)d.w_dtype);
     return buf;
 }
 
@@ -172,7 +173,7 @@ pmf_status cache_store(const char* path, const std::string& key, const MarchShap
 pmf_status plan_project(pmf_plan* p, cudaStream_t s) {
     const pmf_batch_desc& d = p->d;
     pmf_project_item it{d.grid, d.det, p->B, d.views, p->W, p->N, p->Y};
-    return project_launch(it, d.dtype, p->fp, s);
+    return project_launch(it, d.w_dtype, p->fp, s);
 }
 
 pmf_status plan_backproject(pmf_plan* p, cudaStream_t s) {
@@ -189,7 +190,7 @@ pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
     for (int l = 0; l < p->L; l++)
         PMF_TRY(gs_voxelize(&d.grid, &d.mbc[l], d.dtype, (char*)p->E + (size_t)l * 3 * N * p->elt, p->vox_ws[1 + l],
                             p->vox_bytes[1 + l], ps));
-    PMF_TRY(warp_combine(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, p->W, ps));
+    PMF_TRY(warp_combine_mixed(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, d.w_dtype, p->W, ps));
     PMF_TRY(plan_project(p, s));
     const bool eq14 = d.loss_kind == 3;
     PMF_TRY(projection_loss(eq14 ? 1 : d.loss_kind, p->B, p->Q, p->Y, d.meas, d.loss, p->dY, p->loss_ws,
@@ -270,7 +271,7 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     const size_t N = (size_t)p->N, B = (size_t)p->B, L = (size_t)p->L, Q = (size_t)p->Q;
     sz.push_back(N * p->elt);                 // V
     sz.push_back(L * 3 * N * p->elt);         // E
-    sz.push_back(B * N * p->elt);             // W
+    sz.push_back(B * N * dtype_bytes(d.w_dtype));  // W
     sz.push_back(B * Q * 4);                  // Y
     sz.push_back(B * Q * 4);                  // dY
     sz.push_back(B * N * 4);                  // dW

@@ -68,6 +68,7 @@ struct MarchShape {
     int form = 0;
     int chunk = 32;
     int rays = 256;
+    int tma = 1;  // forward only: 1 stages fp32 boxes with bulk tensor copies when the layout allows, 0 never
 };
 pmf_status project_launch(const pmf_project_item& it, pmf_dtype dtype, const MarchShape& sh, cudaStream_t s);
 pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes,

@@ -3,6 +3,9 @@
 // staged in shared memory with coalesced loads (zero outside the grid), and
 // the 8-corner trilinear gathers read shared memory; a chunk whose box does
 // not fit falls back to bounds-checked global gathers.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "march.cuh"
 
 namespace pmf {
@@ -79,9 +82,13 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
                 }
             }
         } else if (act) {
-            for (int j = j0; j <= j1; j++) {
-                const float jf = (float)j;
-                const float ux = at(r, 0, jf, fb), uy = at(r, 1, jf, fb), uz = at(r, 2, jf, fb);
+            // the staged loop's own positions and blend, so that every path
+            // (staged, bulk-copied, or gathered from global memory) gives the
+            // same bits
+            float jf = (float)j0;
+            for (int j = j0; j <= j1; j++, jf += 1.0f) {
+                const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
+                            uz = fmaf(jf, r.dh[2], fb[2]);
                 const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
                 acc += gather8(V, g, ib[0] + (int)flx, ib[1] + (int)fly, ib[2] + (int)flz, ux - flx, uy - fly,
                                uz - flz);
@@ -99,6 +106,172 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project(GridD g, int nu, in
     __shared__ float box[kBox];
     __shared__ BoxState bs;
     project_tile<T, CH, RPB>(g, nu, nv, ntu, step, views, vol, vol_stride, proj, blockIdx.y, blockIdx.x, box, bs);
+}
+
+// ------------------------------------------- forward with bulk-copy staging
+//
+// fp32 volumes whose rows and planes are 16-byte multiples: each chunk's box
+// is brought into shared memory by tensor-map bulk copies (cp.async.bulk.tensor)
+// of 40 x 8 x 1 voxels, one per (z, 8-row block), issued by one thread and
+// completed on an mbarrier; the copy engine fills voxels outside the grid with
+// zeros, which is the zero padding of the trilinear interpolation.  Rows are
+// 40 floats apart (160 bytes), the box's x origin is rounded down to a
+// multiple of 4 voxels (the copy start must be 16-byte aligned), and the y
+// extent is rounded up to 8 rows.  A box larger than kTmaBox falls back to
+// bounds-checked global gathers.  The wait is bounded (about one second of
+// clock): a CTA that gives up counts PMF_DIAG_TIMEOUT, waits once more for its
+// copies, writes NaN to its pixels and returns.
+
+constexpr int kTmaX = 40;                     // floats per staged row (one copy's x extent)
+constexpr int kTmaRows = 8;                   // rows per copy
+constexpr int kTmaBox = 8192;                 // staged floats (32 KB)
+constexpr long long kTmaWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of bar, at most kTmaWaitCycles; true if it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kTmaWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, int x, int y, int z, int p,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(p), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int CH, int RPB>
+__device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv, int ntu, float step,
+                                                 const pmf_view* __restrict__ views, const CUtensorMap* map,
+                                                 const float* __restrict__ vol, int64_t vol_stride,
+                                                 float* __restrict__ proj, int p, int tile, float* box,
+                                                 unsigned long long* bar, BoxState& bs) {
+    int a, b;
+    pixel_of<RPB>(tile, ntu, a, b);
+    const bool in = a < nu && b < nv;
+    Ray r;
+    if (in) {
+        r = ray_init(views[p], nu, nv, a, b, g, (double)step);
+    } else {
+        r.mlo = 1; r.mhi = 0;
+    }
+    const bool live = in && r.mlo <= r.mhi;
+    const float* V = vol + (int64_t)p * vol_stride;
+    const int pv = vol_stride ? p : 0;  // the volume's index along the map's 4th axis
+    block_range(bs, r, live);
+    const int Mlo = bs.range[0], Mhi = bs.range[1];
+    float acc = 0.0f;
+    int sel = 0;
+    unsigned parity = 0;
+    for (int M0 = Mlo; M0 <= Mhi; M0 += CH, sel ^= 1) {
+        int j0, j1, ib[3];
+        float fb[3];
+        const bool act = chunk_begin<CH>(bs, sel, r, live, M0, j0, j1, ib, fb);
+        __syncthreads();
+        const Box bx = read_box(bs, sel);
+        const int x0 = (bx.lx >> 2) << 2;                   // 16-byte aligned copy start (floor)
+        const int byr = (bx.by + kTmaRows - 1) & ~(kTmaRows - 1);
+        const bool fits = bx.vol > 0 && bx.bx + (bx.lx - x0) <= kTmaX && (long long)byr * bx.bz * kTmaX <= kTmaBox;
+        if (threadIdx.x == 0 && bx.vol > 0 && !fits) diag_count(PMF_DIAG_PROJECT_BOX_FALLBACK);
+        if (fits) {
+            if (threadIdx.x == 0) {
+                // the previous chunk's reads of the box are ordered before the
+                // copies into it by the barrier above and this proxy fence
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const int nyb = byr / kTmaRows;
+                mbar_expect_tx(bar, (unsigned)(bx.bz * nyb * kTmaRows * kTmaX * sizeof(float)));
+                for (int zz = 0; zz < bx.bz; zz++)
+                    for (int yb = 0; yb < nyb; yb++)
+                        tma_load_4d(box + (zz * byr + yb * kTmaRows) * kTmaX, map, x0, bx.ly + yb * kTmaRows,
+                                    bx.lz + zz, pv, bar);
+            }
+            const bool ok = mbar_wait_bounded(bar, parity);
+            parity ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) diag_count(PMF_DIAG_TIMEOUT);
+                mbar_wait_bounded(bar, parity ^ 1u);  // the copies still in flight, once more
+                if (in) proj[((int64_t)p * nv + b) * nu + a] = __int_as_float(0x7fc00000);
+                return;
+            }
+            if (act) {
+                const float syf = (float)kTmaX, szf = (float)(kTmaX * byr);
+                const int sy = kTmaX, sz = kTmaX * byr;
+                const float* qa = box + (ib[0] - x0) + (ib[1] - bx.ly) * sy + (ib[2] - bx.lz) * sz;
+                float jf = (float)j0;
+                for (int j = j0; j <= j1; j++, jf += 1.0f) {
+                    const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
+                                uz = fmaf(jf, r.dh[2], fb[2]);
+                    const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
+                    const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
+                    const float* q = qa + (int)fmaf(flz, szf, fmaf(fly, syf, flx));
+                    const float c000 = q[0], c100 = q[1], c010 = q[sy], c110 = q[sy + 1];
+                    const float c001 = q[sz], c101 = q[sz + 1], c011 = q[sz + sy], c111 = q[sz + sy + 1];
+                    const float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
+                    const float a01 = fmaf(fx, c101 - c001, c001), a11 = fmaf(fx, c111 - c011, c011);
+                    const float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
+                    acc += fmaf(fz, b1 - b0, b0);
+                }
+            }
+        } else if (act) {
+            // the staged loop's own positions and blend, so that every path
+            // (staged, bulk-copied, or gathered from global memory) gives the
+            // same bits
+            float jf = (float)j0;
+            for (int j = j0; j <= j1; j++, jf += 1.0f) {
+                const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
+                            uz = fmaf(jf, r.dh[2], fb[2]);
+                const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
+                acc += gather8(V, g, ib[0] + (int)flx, ib[1] + (int)fly, ib[2] + (int)flz, ux - flx, uy - fly,
+                               uz - flz);
+            }
+        }
+        __syncthreads();
+    }
+    if (in) proj[((int64_t)p * nv + b) * nu + a] = step * acc;
+}
+
+template <int CH, int RPB>
+__global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_tma(GridD g, int nu, int nv, int ntu, float step,
+                                                                const pmf_view* __restrict__ views,
+                                                                const __grid_constant__ CUtensorMap map,
+                                                                const float* __restrict__ vol, int64_t vol_stride,
+                                                                float* __restrict__ proj) {
+    __shared__ __align__(128) float box[kTmaBox];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ BoxState bs;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    project_tile_tma<CH, RPB>(g, nu, nv, ntu, step, views, &map, vol, vol_stride, proj, blockIdx.y, blockIdx.x, box,
+                              &bar, bs);
 }
 
 template <typename T, int CH, int RPB>
@@ -143,6 +316,40 @@ __global__ void k_loss_final(const float* part, int nb, int64_t n, float* loss) 
     *loss = (float)(s / (double)n);
 }
 
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    return fn;
+}
+
+// A 4-D map (x, y, z, volume) over fp32 volumes for the staged forward, or
+// false when the layout does not allow bulk copies (base or a stride not a
+// multiple of 16 bytes) or the encoder is unavailable.
+bool encode_volume_map(CUtensorMap* m, const float* vol, const pmf_grid* g, int32_t P, int64_t vol_stride) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || ((uintptr_t)vol & 15u) != 0) return false;
+    const cuuint64_t nx = (cuuint64_t)g->nx, ny = (cuuint64_t)g->ny, nz = (cuuint64_t)g->nz;
+    const cuuint64_t vstride = vol_stride ? (cuuint64_t)vol_stride * 4 : nx * ny * nz * 4;
+    if ((nx * 4) % 16 || (nx * ny * 4) % 16 || vstride % 16) return false;
+    const cuuint64_t dims[4] = {nx, ny, nz, vol_stride ? (cuuint64_t)P : 1};
+    const cuuint64_t strides[3] = {nx * 4, nx * ny * 4, vstride};
+    const cuuint32_t box[4] = {kTmaX, kTmaRows, 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)vol, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 pmf_status project_grid(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
                         pmf_dtype dtype, const void* vol, int64_t vol_stride, float* proj, const MarchShape& sh,
                         cudaStream_t s) {
@@ -155,6 +362,11 @@ pmf_status project_grid(const pmf_grid* grid, const pmf_detector* det, int32_t P
     GridD g = make_grid(grid);
     const int ntu = (det->nu + 15) / 16, ntv = tiles_v(det->nv, sh.rays);
     dim3 gr((unsigned)(ntu * ntv), (unsigned)P);
+    CUtensorMap map;
+    if (sh.tma && dtype == PMF_F32 && encode_volume_map(&map, (const float*)vol, grid, P, vol_stride)) {
+        PMF_DISPATCH_MARCH(sh, CH, RPB, k_project_tma<CH, RPB><<<gr, RPB, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, map, (const float*)vol, vol_stride, proj));
+        return check_launch("conebeam_project");
+    }
     PMF_DISPATCH_MARCH(sh, CH, RPB, PMF_DISPATCH_DTYPE(dtype, T, k_project<T, CH, RPB><<<gr, RPB, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, (const T*)vol, vol_stride, proj)));
     return check_launch("conebeam_project");
 }

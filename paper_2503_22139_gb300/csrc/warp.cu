@@ -225,10 +225,10 @@ __global__ void k_fixed_to_float(const unsigned long long* __restrict__ acc, int
 
 // ----------------------------------------------------- fused combine + warp
 
-template <typename T>
+template <typename T, typename TO>
 __global__ void __launch_bounds__(kThreads) k_warp_combine(GridD g, int L, int P, const T* __restrict__ ref,
                                                            const T* __restrict__ E, const float* __restrict__ w,
-                                                           T* __restrict__ W) {
+                                                           TO* __restrict__ W) {
     const int64_t N = g.n;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_warp_combine(GridD g, int L, int P
                 d[a] = acc;
             }
             const Cell c = make_cell(i, j, k, d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
-            Store<T>::st(W, (int64_t)p * N + v, trilin_cell(ref, g, c.i0, c.j0, c.k0, c.fx, c.fy, c.fz));
+            Store<TO>::st(W, (int64_t)p * N + v, trilin_cell(ref, g, c.i0, c.j0, c.k0, c.fx, c.fy, c.fz));
         }
     }
 }
@@ -392,10 +392,10 @@ __device__ __forceinline__ void corners8_halo(const float* sv, int rx, int ry, i
     }
 }
 
-template <typename T, int L>
+template <typename T, typename TO, int L>
 __global__ void __launch_bounds__(256) k_wc_fwd_tile(GridD g, int P, const T* __restrict__ ref,
                                                      const T* __restrict__ E, const float* __restrict__ w,
-                                                     T* __restrict__ W) {
+                                                     TO* __restrict__ W) {
     extern __shared__ float smem_f[];
     const int PL3 = P * L * 3;
     float* sw = smem_f;                          // [P][L][3]
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256) k_wc_fwd_tile(GridD g, int P, const T* __
             const Cell cl = make_cell(t.x, t.y, z, d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
             float cv[8];
             corners8_halo(sv, cl.i0 - bx0, cl.j0 - by0, cl.k0 - bz0, ref, g, cl, cv);
-            Store<T>::st(W, (int64_t)p * N + v, trilin8(cv, cl.fx, cl.fy, cl.fz));
+            Store<TO>::st(W, (int64_t)p * N + v, trilin8(cv, cl.fx, cl.fy, cl.fz));
         }
     }
 }
@@ -740,30 +740,59 @@ pmf_status warp_volume_backward(const pmf_grid* grid, int32_t P, pmf_dtype dtype
     return check_launch("warp_volume_backward");
 }
 
-pmf_status warp_combine(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref, const void* mbc,
-                        const float* coeff, void* out, pmf_stream stream) {
+}  // extern "C"
+
+namespace pmf {
+namespace {
+
+template <typename T, typename TO>
+pmf_status launch_warp_combine(const GridD& g, int32_t L, int32_t P, const void* ref, const void* mbc,
+                               const float* coeff, void* out, cudaStream_t s) {
+    if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
+        const size_t smem = sizeof(float) * (size_t)((((P * L * 3) + 3) & ~3) + kBoxN);
+        const unsigned nt = (unsigned)num_tiles(g);
+        switch (L) {
+            case 1: k_wc_fwd_tile<T, TO, 1><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out); break;
+            case 2: k_wc_fwd_tile<T, TO, 2><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out); break;
+            case 3: k_wc_fwd_tile<T, TO, 3><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out); break;
+            default: k_wc_fwd_tile<T, TO, 4><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out); break;
+        }
+        return check_launch("warp_combine");
+    }
+    k_warp_combine<T, TO><<<stream_blocks(g.n), kThreads, 0, s>>>(g, L, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out);
+    return check_launch("warp_combine");
+}
+
+pmf_status warp_combine_impl(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
+                             const void* mbc, const float* coeff, pmf_dtype out_dtype, void* out, pmf_stream stream) {
     pmf_status st = check_common(grid, P, dtype);
     if (st != PMF_OK) return st;
     PMF_REQUIRE(L >= 1 && L <= kMaxL, "L must be in [1, %d]", kMaxL);
+    PMF_REQUIRE(out_dtype == dtype || out_dtype == PMF_F32, "out_dtype must be dtype or PMF_F32");
     if (P == 0) return PMF_OK;
     PMF_REQUIRE(ref && mbc && coeff && out, "null pointer");
     GridD g = make_grid(grid);
     cudaStream_t s = (cudaStream_t)stream;
-    if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
-        const size_t smem = sizeof(float) * (size_t)((((P * L * 3) + 3) & ~3) + kBoxN);
-        const unsigned nt = (unsigned)num_tiles(g);
-        PMF_DISPATCH_DTYPE(dtype, T, {
-            switch (L) {
-                case 1: k_wc_fwd_tile<T, 1><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (T*)out); break;
-                case 2: k_wc_fwd_tile<T, 2><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (T*)out); break;
-                case 3: k_wc_fwd_tile<T, 3><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (T*)out); break;
-                default: k_wc_fwd_tile<T, 4><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (T*)out); break;
-            }
-        });
-        return check_launch("warp_combine");
+    if (out_dtype == PMF_F32) {
+        PMF_DISPATCH_DTYPE(dtype, T, return (launch_warp_combine<T, float>(g, L, P, ref, mbc, coeff, out, s)));
     }
-    PMF_DISPATCH_DTYPE(dtype, T, k_warp_combine<T><<<stream_blocks(g.n), kThreads, 0, s>>>(g, L, P, (const T*)ref, (const T*)mbc, coeff, (T*)out));
-    return check_launch("warp_combine");
+    PMF_DISPATCH_DTYPE(dtype, T, return (launch_warp_combine<T, T>(g, L, P, ref, mbc, coeff, out, s)));
+    return PMF_OK;
+}
+
+}  // namespace
+}  // namespace pmf
+
+extern "C" {
+
+pmf_status warp_combine(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref, const void* mbc,
+                        const float* coeff, void* out, pmf_stream stream) {
+    return warp_combine_impl(grid, L, P, dtype, ref, mbc, coeff, dtype, out, stream);
+}
+
+pmf_status warp_combine_mixed(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
+                              const void* mbc, const float* coeff, pmf_dtype out_dtype, void* out, pmf_stream stream) {
+    return warp_combine_impl(grid, L, P, dtype, ref, mbc, coeff, out_dtype, out, stream);
 }
 
 pmf_status warp_combine_backward_workspace(const pmf_grid* grid, int32_t L, int32_t P, size_t* bytes) {

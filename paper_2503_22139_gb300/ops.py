@@ -238,8 +238,25 @@ def warp_combine(grid, ref, mbc, coeff, out=None) -> torch.Tensor:
     shape, _ = _shape(grid)
     if out is None:
         out = torch.empty((P,) + shape, dtype=ref.dtype, device=ref.device)
+    if out.dtype != ref.dtype:  # fp32 warped volumes from bf16 / fp16 grids
+        return warp_combine_mixed(grid, ref, mbc, coeff, out.dtype, out)
     check(L.warp_combine(ct.byref(_grid(grid)), Lv, P, _DT[ref.dtype], _p(ref), _p(mbc), _p(coeff), _p(out),
                          _stream()), "warp_combine")
+    return out
+
+
+def warp_combine_mixed(grid, ref, mbc, coeff, out_dtype=torch.float32, out=None) -> torch.Tensor:
+    """warp_combine writing W in out_dtype (the grids' dtype or fp32)."""
+    L = _lib.load()
+    ref, mbc = _need(ref, "ref"), _need(mbc, "mbc")
+    coeff = _need(coeff, "coeff", torch.float32)
+    P, Lv = int(coeff.shape[0]), int(coeff.shape[1])
+    shape, _ = _shape(grid)
+    if out is None:
+        out = torch.empty((P,) + shape, dtype=out_dtype, device=ref.device)
+    out = _need(out, "out", out_dtype)
+    check(L.warp_combine_mixed(ct.byref(_grid(grid)), Lv, P, _DT[ref.dtype], _p(ref), _p(mbc), _p(coeff),
+                               _DT[out_dtype], _p(out), _stream()), "warp_combine_mixed")
     return out
 
 
@@ -556,11 +573,14 @@ class _StepBuffers:
     gradients) and the descriptor that points at them."""
 
     def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
-                 dtype: torch.dtype = torch.bfloat16, kind=2, eq14: Optional[dict] = None):
+                 dtype: torch.dtype = torch.bfloat16, kind=2, eq14: Optional[dict] = None,
+                 w_dtype: torch.dtype = torch.float32):
         if len(mbc) < 1 or len(mbc) > _lib.PMF_MAX_LEVELS:
             raise ValueError(f"need 1..{_lib.PMF_MAX_LEVELS} MBC levels")
+        if w_dtype not in (dtype, torch.float32):
+            raise ValueError("w_dtype must be dtype or torch.float32")
         self.grid, self.det, self.ref, self.mbc = grid, det, ref, list(mbc)
-        self.B, self.L, self.dtype = int(batch), len(self.mbc), dtype
+        self.B, self.L, self.dtype, self.w_dtype = int(batch), len(self.mbc), dtype, w_dtype
         dev = ref.mean.device
         self.eq14 = None
         if kind in ("eq14", 3):
@@ -598,7 +618,7 @@ class _StepBuffers:
 
     def desc(self, use_graph: bool = False, tune_cache: Optional[bytes] = None) -> "_lib.PmfBatchDesc":
         d = _lib.PmfBatchDesc()
-        d.grid, d.det, d.dtype = _grid(self.grid), _det(self.det), _DT[self.dtype]
+        d.grid, d.det, d.dtype, d.w_dtype = _grid(self.grid), _det(self.det), _DT[self.dtype], _DT[self.w_dtype]
         d.batch, d.loss_kind, d.levels = self.B, self.kind, self.L
         d.ref = self.ref.c_struct()
         for l, m in enumerate(self.mbc):
@@ -629,11 +649,13 @@ class Plan(_StepBuffers):
 
     def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
                  dtype: torch.dtype = torch.bfloat16, kind=2, use_graph: bool = False,
-                 tune_cache: Optional[str] = None, eq14: Optional[dict] = None):
+                 tune_cache: Optional[str] = None, eq14: Optional[dict] = None,
+                 w_dtype: torch.dtype = torch.float32):
         """kind 1 / 2: L1 / L2 loss; "eq14" (or 3): the objective of Eq. 14 with
-        `eq14` overriding pipeline.EQ14_DEFAULTS (data_range required)."""
+        `eq14` overriding pipeline.EQ14_DEFAULTS (data_range required).
+        w_dtype: storage of the warped volumes W (fp32, or dtype)."""
         self._h = None
-        super().__init__(grid, det, ref, mbc, batch, dtype, kind, eq14)
+        super().__init__(grid, det, ref, mbc, batch, dtype, kind, eq14, w_dtype)
         dev = ref.mean.device
         self._cache = tune_cache.encode() if tune_cache else None  # kept alive with the descriptor
         self._desc = self.desc(use_graph, self._cache)
@@ -674,7 +696,7 @@ class Plan(_StepBuffers):
             return torch.as_tensor(_DevArray(ptr, shp, _TYPESTR[dt]), device=dev)
 
         return {"V": view(t.V, shape, self.dtype), "E": view(t.E, (self.L, 3) + shape, self.dtype),
-                "W": view(t.W, (self.B,) + shape, self.dtype),
+                "W": view(t.W, (self.B,) + shape, self.w_dtype),
                 "Y": view(t.Y, (self.B, gr.nv, gr.nu), torch.float32),
                 "dY": view(t.dY, (self.B, gr.nv, gr.nu), torch.float32),
                 "dW": view(t.dW, (self.B,) + shape, torch.float32), "dV": view(t.dV, shape, torch.float32),
@@ -699,11 +721,12 @@ class Plan(_StepBuffers):
 
 
 def pmf_autotune(grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int, cache_path: str,
-                 dtype: torch.dtype = torch.bfloat16, kind: int = 2, views=None, coeff=None, meas=None) -> None:
+                 dtype: torch.dtype = torch.bfloat16, kind: int = 2, views=None, coeff=None, meas=None,
+                 w_dtype: torch.dtype = torch.float32) -> None:
     """Times the projector's launch forms on this configuration (and batch, if
     given) and records the fastest in cache_path, which
     Plan(..., tune_cache=cache_path) reads back."""
-    buf = _StepBuffers(grid, det, ref, mbc, batch, dtype, kind)
+    buf = _StepBuffers(grid, det, ref, mbc, batch, dtype, kind, None, w_dtype)
     buf.set_batch(views, coeff, meas)
     d = buf.desc(False, None)
     with torch.cuda.device(ref.mean.device):

@@ -35,12 +35,16 @@ EQ14_DEFAULTS = dict(lambda_ssim=0.25, lambda_mbc=1.0, lambda_tv=0.05, tv_size=3
 class ForwardAdjoint:
     def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
                  dtype: torch.dtype = torch.float32, kind=2, pair_headroom: float = 1.25,
-                 eq14: Optional[dict] = None):
+                 eq14: Optional[dict] = None, w_dtype: torch.dtype = torch.float32):
         """kind 1 / 2: L1 / L2 projection loss (Eq. 10/12, Eq. 1); kind "eq14":
         the full objective of Eq. 14 with `eq14` overriding EQ14_DEFAULTS
-        (data_range, the D-SSIM dynamic range, is required)."""
+        (data_range, the D-SSIM dynamic range, is required).  V and E are
+        stored in dtype; the warped volumes W in w_dtype (fp32 by default: the
+        projector stages fp32 volumes with bulk tensor copies)."""
+        if w_dtype not in (dtype, torch.float32):
+            raise ValueError("w_dtype must be dtype or torch.float32")
         self.grid, self.det, self.ref, self.mbc = grid, det, ref, list(mbc)
-        self.B, self.dtype = int(batch), dtype
+        self.B, self.dtype, self.w_dtype = int(batch), dtype, w_dtype
         self.eq14 = None
         if kind == "eq14":
             q = dict(EQ14_DEFAULTS)
@@ -57,7 +61,7 @@ class ForwardAdjoint:
         # buffers
         self.V = torch.empty((1,) + shape, dtype=dtype, device=dev)
         self.E = torch.empty((L, 3) + shape, dtype=dtype, device=dev)
-        self.W = torch.empty((self.B,) + shape, dtype=dtype, device=dev)
+        self.W = torch.empty((self.B,) + shape, dtype=w_dtype, device=dev)
         self.Y = torch.empty((self.B, det.nv, det.nu), dtype=torch.float32, device=dev)
         self.dW = torch.empty((self.B,) + shape, dtype=torch.float32, device=dev)
         self.g_ref = (torch.empty((ref.n, 3), device=dev), torch.empty((ref.n, 3), device=dev),
@@ -139,6 +143,9 @@ class PlainPerProjection(ForwardAdjoint):
         super().__init__(*args, **kwargs)
         shape, n = ops._shape(self.grid)
         dev = self.ref.mean.device
+        if self.w_dtype != self.dtype:  # warp_volume writes W in the grids' dtype
+            self.w_dtype = self.dtype
+            self.W = torch.empty(self.W.shape, dtype=self.dtype, device=dev)
         Lb = ops._lib.load()
         g = ops._grid(self.grid)
         self.D1 = torch.empty((1, 3) + shape, dtype=self.dtype, device=dev)

@@ -30,7 +30,8 @@ int main(void) {
     O(pmf_batch_desc, mbc); O(pmf_batch_desc, views); O(pmf_batch_desc, loss); O(pmf_batch_desc, d_ref);
     O(pmf_batch_desc, d_mbc); O(pmf_batch_desc, d_coeff); O(pmf_batch_desc, use_graph);
     O(pmf_batch_desc, tune_cache); O(pmf_batch_desc, lambda_ssim); O(pmf_batch_desc, ssim_range);
-    O(pmf_batch_desc, tv_size); O(pmf_batch_desc, tv_origin); O(pmf_plan_tensors, dE);
+    O(pmf_batch_desc, tv_size); O(pmf_batch_desc, tv_origin); O(pmf_batch_desc, w_dtype);
+    O(pmf_plan_tensors, dE);
     O(pmf_project_item, views); O(pmf_project_item, vol_stride); O(pmf_backproject_item, vol_stride);
     return 0;
 }
@@ -131,6 +132,7 @@ def _desc(**over):
 @pytest.mark.parametrize("field,value,msg", [
     ("batch", 0, b"batch"), ("loss_kind", 0, b"loss_kind"), ("levels", 0, b"levels"), ("levels", 9, b"levels"),
     ("dtype", 7, b"dtype"), ("views", None, b"null batch pointer"), ("loss_kind", 4, b"loss_kind"),
+    ("w_dtype", 1, b"w_dtype"), ("w_dtype", 5, b"w_dtype"),
 ])
 def test_plan_rejects_bad_descriptors_on_the_host(field, value, msg):
     L = _lib.load()

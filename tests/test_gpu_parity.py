@@ -126,6 +126,23 @@ def test_combine_and_warp_match_oracle():
     assert rel_l2(host(Wf), oracle.warp(grid, V, Dref)) <= TOL32
 
 
+@pytest.mark.parametrize("L,dt", [(2, torch.bfloat16), (3, torch.float16), (6, torch.bfloat16)])
+def test_warp_combine_fp32_output_from_reduced_grids(L, dt):
+    """warp_combine_mixed: bf16 / fp16 V and E, fp32 W (the 32x4x4 tile kernel
+    for L <= 4, the per-voxel kernel above).  W is the fp32 warp of the stored
+    grids' values, and rounding it to the grids' format gives the same-format
+    entry point's output bit for bit (both round the same fp32 sum once)."""
+    grid = Grid(37, 11, 9, 2.0, 2.0, 2.0)
+    V, E, w = _mbc_and_ref(grid, 50 + L, L=L, P=3)
+    Vd, Ed = dev(V).to(dt), dev(E).to(dt)
+    W32 = torch.empty((3,) + grid.shape, device="cuda")
+    pmf.warp_combine(grid, Vd, Ed, dev(w), out=W32)
+    Vq, Eq = host(Vd).astype(np.float64), host(Ed).astype(np.float64)
+    assert rel_l2(host(W32), oracle.warp(grid, Vq, oracle.combine(Eq, w))) <= TOL32
+    Wn = pmf.warp_combine(grid, Vd, Ed, dev(w))
+    assert Wn.dtype == dt and torch.equal(W32.to(dt), Wn)
+
+
 def test_zero_dvf_warp_is_bitwise_identity():
     grid = Grid(9, 8, 7, 2.0, 2.0, 2.0)
     V = dev(np.random.default_rng(3).random(grid.shape))
@@ -176,6 +193,30 @@ def test_project_ragged_detector(nu, nv):
     got = host(pmf.conebeam_project(grid, Detector(nu, nv, 1.0), views(vw), dev(vol)))
     ref = oracle.project(grid, nu, nv, 1.0, vw, vol)
     assert rel_l2(got, ref) <= TOL32
+
+
+@pytest.mark.parametrize("shared", [False, True])
+def test_project_bulk_copy_staging_equals_plain_staging(shared):
+    """fp32 volumes whose rows are whole 16-byte lines get their shared-memory
+    boxes by bulk tensor copies; bf16 volumes by plain loads.  On values that
+    bf16 holds exactly both forms must give the same projections bit for bit
+    (the samples and their order do not depend on how the box was filled),
+    and no bulk copy may time out."""
+    grid = Grid(48, 44, 36, 2.0, 2.0, 2.0)
+    P = 4
+    vol = np.random.default_rng(23).random((P,) + grid.shape).astype(np.float32)
+    vb = dev(vol).to(torch.bfloat16)
+    src = vb[0] if shared else vb
+    vw = circular_views(P, 500.0, 750.0, 70, 54, 2.2, 2.2, start=0.2)
+    det = Detector(70, 54, 1.0)
+    pmf.device_counters(reset=True)
+    y32 = pmf.conebeam_project(grid, det, views(vw), src.float(), shared=shared)
+    y16 = pmf.conebeam_project(grid, det, views(vw), src, shared=shared)
+    assert torch.equal(y32, y16)
+    assert pmf.device_counters()["timeout"] == 0
+    pmf.device_status()
+    ref = oracle.project(grid, 70, 54, 1.0, vw, host(src), shared=shared)
+    assert rel_l2(host(y32), ref) <= TOL32
 
 
 def test_project_small_workload_voxelized_reference():

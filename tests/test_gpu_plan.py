@@ -49,17 +49,19 @@ def _assert_same(a, b):
         assert torch.equal(a[k], b[k]), k
 
 
-@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
-def test_plan_step_equals_forward_adjoint(wl, dt):
+@pytest.mark.parametrize("dt,wdt", [(torch.float32, torch.float32), (torch.bfloat16, torch.float32),
+                                     (torch.bfloat16, torch.bfloat16)])
+def test_plan_step_equals_forward_adjoint(wl, dt, wdt):
     ref, mbc = _sets(wl)
     args = _batch(wl)
-    step = ForwardAdjoint(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=dt)
+    step = ForwardAdjoint(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=dt, w_dtype=wdt)
     loss = step.run(*args).clone()
-    plan = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=dt)
+    plan = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=dt, w_dtype=wdt)
     got = plan.step(*args)
     torch.cuda.synchronize()
     assert torch.equal(got, loss)
     t = plan.tensors()
+    assert t["W"].dtype == wdt
     assert torch.equal(t["V"], step.V[0]) and torch.equal(t["E"], step.E) and torch.equal(t["W"], step.W)
     assert torch.equal(t["Y"], step.Y) and torch.equal(t["dW"], step.dW)
     for a, b in zip(plan.g_ref, step.g_ref):

@@ -40,18 +40,23 @@ def stage_errors(wl, step, grads, f):
     }
 
 
-def _run(wl, dt, cls=ForwardAdjoint):
-    step = cls(wl.grid, wl.det, gset(wl.ref, wl.kappa), [gset(m, wl.kappa) for m in wl.mbc], batch=wl.p, dtype=dt)
+def _run(wl, dt, cls=ForwardAdjoint, w_dtype=torch.float32):
+    step = cls(wl.grid, wl.det, gset(wl.ref, wl.kappa), [gset(m, wl.kappa) for m in wl.mbc], batch=wl.p, dtype=dt,
+               w_dtype=w_dtype)
     step.run(views(wl.views), dev(wl.coeff), dev(wl.measured))
     torch.cuda.synchronize()
     return step
 
 
+@pytest.mark.parametrize("w_same", [False, True], ids=["W-fp32", "W-reduced"])
 @pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
-def test_reduced_storage_per_stage_error(ref_step, dt):
+def test_reduced_storage_per_stage_error(ref_step, dt, w_same):
+    """V and E in bf16 / fp16; W in fp32 (the default) or in the same format."""
     wl, loss, grads, f = ref_step
-    e = stage_errors(wl, _run(wl, dt), grads, f)
-    print(dt, {k: f"{v:.2e}" for k, v in e.items()})
+    step = _run(wl, dt, w_dtype=dt if w_same else torch.float32)
+    assert step.W.dtype == (dt if w_same else torch.float32)
+    e = stage_errors(wl, step, grads, f)
+    print(dt, step.W.dtype, {k: f"{v:.2e}" for k, v in e.items()})
     u = UNIT[dt]
     assert e["Y"] <= 2e-3
     # storing a value rounds it by at most u relative, so rel-L2 <= u (truncation ties aside)

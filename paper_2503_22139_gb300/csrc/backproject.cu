@@ -163,9 +163,10 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
     pixel_of_spread<RPB>(tile, ntu, a, b);
     const bool in = a < nu && b < nv;
     const float gy = in ? __ldg(dproj + ((int64_t)p * nv + b) * nu + a) : 0.0f;
+    tile_view(bs, views[p], g, step);
     Ray r;
     if (in && gy != 0.0f) {
-        r = ray_init(views[p], nu, nv, a, b, g, (double)step);
+        r = ray_init(bs.vf, nu, nv, a, b, g);
     } else {
         r.mlo = 1; r.mhi = 0;
     }

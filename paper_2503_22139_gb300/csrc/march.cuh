@@ -44,34 +44,96 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// Ray through the centre of pixel (a, b) of view `vw`.
-__device__ __forceinline__ Ray ray_init(const pmf_view& vw, int nu, int nv, int a, int b, const GridD& g,
-                                        double step) {
+// Per-view constants of the ray set-up as float-float (hi + lo) pairs.  Three
+// threads of the CTA form them in double precision (one axis each); every ray
+// of the tile then sets itself up in fp32 arithmetic, which keeps the fp64
+// pipe (a small fraction of the fp32 rate on this part) out of the per-ray path.
+struct ViewFF {
+    float d0h[3], d0l[3];  // det - src, mm
+    float duh[3], dul[3];  // detector u pixel vector, mm
+    float dvh[3], dvl[3];  // detector v pixel vector, mm
+    float ush[3], usl[3];  // the source in voxel-index space (voxel centres at integers)
+    float kh[3], kl[3];    // step / voxel size along each axis
+};
+
+__device__ __forceinline__ void split_ff(double x, float& h, float& l) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+// Threads 0..2 fill vf for view vw; the caller synchronises before use.
+__device__ __forceinline__ void view_setup(ViewFF& vf, const pmf_view& vw, const GridD& g, double step) {
+    const int t = threadIdx.x;
+    if (t >= 3) return;
+    const int n = t == 0 ? g.nx : (t == 1 ? g.ny : g.nz);
+    const double iv = 1.0 / (double)(t == 0 ? g.vx : (t == 1 ? g.vy : g.vz));
+    split_ff(vw.det[t] - vw.src[t], vf.d0h[t], vf.d0l[t]);
+    split_ff(vw.du[t], vf.duh[t], vf.dul[t]);
+    split_ff(vw.dv[t], vf.dvh[t], vf.dvl[t]);
+    split_ff(fma(vw.src[t], iv, 0.5 * (double)n - 0.5), vf.ush[t], vf.usl[t]);
+    split_ff(step * iv, vf.kh[t], vf.kl[t]);
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+
+// Ray through the centre of pixel (a, b): direction d = (det - src) + ca du + cb dv
+// with ca, cb the pixel's offsets from the detector centre (exact in fp32),
+// normalised, scaled to the index-space step, all in float-float arithmetic
+// (about 44 bits, against the 48 of the double-precision definition).
+__device__ __forceinline__ Ray ray_init(const ViewFF& vf, int nu, int nv, int a, int b, const GridD& g) {
     Ray r;
-    const double ca = (double)a + 0.5 - 0.5 * (double)nu, cb = (double)b + 0.5 - 0.5 * (double)nv;
-    double d[3];
-    double len2 = 0.0;
+    const float ca = (float)a + (0.5f - 0.5f * (float)nu), cb = (float)b + (0.5f - 0.5f * (float)nv);
+    float dh[3], dl[3];
+    float Lh = 0.0f, Le = 0.0f;
 #pragma unroll
     for (int t = 0; t < 3; t++) {
-        d[t] = fma(cb, vw.dv[t], fma(ca, vw.du[t], vw.det[t] - vw.src[t]));
-        len2 = fma(d[t], d[t], len2);
+        float p1, e1, p2, e2, s1, t1, s2, t2;
+        two_prod(ca, vf.duh[t], p1, e1);
+        e1 = fmaf(ca, vf.dul[t], e1);
+        two_prod(cb, vf.dvh[t], p2, e2);
+        e2 = fmaf(cb, vf.dvl[t], e2);
+        two_sum(vf.d0h[t], p1, s1, t1);
+        two_sum(s1, p2, s2, t2);
+        fast_two_sum(s2, ((vf.d0l[t] + e1) + e2) + (t1 + t2), dh[t], dl[t]);
+        float q, qe, ls, le;
+        two_prod(dh[t], dh[t], q, qe);
+        two_sum(Lh, q, ls, le);
+        Lh = ls;
+        Le += (qe + le) + 2.0f * dh[t] * dl[t];
     }
-    // 1/sqrt(len2): fp32 seed, two Newton steps in double
-    double y = (double)rsqrtf((float)len2);
-    y = y * (1.5 - 0.5 * len2 * y * y);
-    y = y * (1.5 - 0.5 * len2 * y * y);
+    float Ll;
+    fast_two_sum(Lh, Le, Lh, Ll);
+    // 1/sqrt(L): fp32 seed, one Newton step with the residual in float-float
+    const float y0 = rsqrtf(Lh);
+    float q, qe, m, me;
+    two_prod(y0, y0, q, qe);
+    two_prod(Lh, q, m, me);
+    me = fmaf(Lh, qe, fmaf(Ll, q, me));
+    const float yl = 0.5f * y0 * ((1.0f - m) - me);
     const int n[3] = {g.nx, g.ny, g.nz};
-    const double iv[3] = {1.0 / (double)g.vx, 1.0 / (double)g.vy, 1.0 / (double)g.vz};
     float tlo = 0.0f, thi = 3.0e38f;
     bool miss = false;
 #pragma unroll
     for (int t = 0; t < 3; t++) {
-        const double us = fma(vw.src[t], iv[t], 0.5 * (double)n[t] - 0.5);
-        const double du = step * (d[t] * y) * iv[t];
-        r.uh[t] = (float)us;
-        r.ul[t] = (float)(us - (double)r.uh[t]);
-        r.dh[t] = (float)du;
-        r.dl[t] = (float)(du - (double)r.dh[t]);
+        // unit direction, then times step / voxel
+        float uh, ul, p, e;
+        two_prod(dh[t], y0, p, e);
+        e = fmaf(dh[t], yl, fmaf(dl[t], y0, e));
+        fast_two_sum(p, e, uh, ul);
+        two_prod(vf.kh[t], uh, p, e);
+        e = fmaf(vf.kh[t], ul, fmaf(vf.kl[t], uh, e));
+        fast_two_sum(p, e, r.dh[t], r.dl[t]);
+        r.uh[t] = vf.ush[t];
+        r.ul[t] = vf.usl[t];
         const float usf = r.uh[t], duf = r.dh[t];
         // the padded volume is u in (-1, n) on every axis
         if (duf != 0.0f) {
@@ -147,7 +209,14 @@ __device__ __forceinline__ float gather8(const T* vol, const GridD& g, int ix, i
 struct BoxState {
     int range[2];   // min mlo, max mhi over the CTA's rays
     int box[2][6];  // double-buffered cell bounds of the current chunk: lo xyz, hi xyz
+    ViewFF vf;      // the tile's view, for ray_init
 };
+
+// Every thread of the CTA: the per-view constants of view vw into bs.vf.
+__device__ __forceinline__ void tile_view(BoxState& bs, const pmf_view& vw, const GridD& g, float step) {
+    view_setup(bs.vf, vw, g, (double)step);
+    __syncthreads();
+}
 
 __device__ __forceinline__ void reset_box(int* b) {
     b[0] = b[1] = b[2] = INT_MAX;

@@ -22,9 +22,10 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
     int a, b;
     pixel_of<RPB>(tile, ntu, a, b);
     const bool in = a < nu && b < nv;
+    tile_view(bs, views[p], g, step);
     Ray r;
     if (in) {
-        r = ray_init(views[p], nu, nv, a, b, g, (double)step);
+        r = ray_init(bs.vf, nu, nv, a, b, g);
     } else {
         r.mlo = 1; r.mhi = 0;
     }
@@ -112,18 +113,26 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project(GridD g, int nu, in
 //
 // fp32 volumes whose rows and planes are 16-byte multiples: each chunk's box
 // is brought into shared memory by tensor-map bulk copies (cp.async.bulk.tensor)
-// of 40 x 8 x 1 voxels, one per (z, 8-row block), issued by one thread and
+// of 44 x 8 x 1 voxels, one per (z, 8-row block), issued by one thread and
 // completed on an mbarrier; the copy engine fills voxels outside the grid with
-// zeros, which is the zero padding of the trilinear interpolation.  Rows are
-// 40 floats apart (160 bytes), the box's x origin is rounded down to a
-// multiple of 4 voxels (the copy start must be 16-byte aligned), and the y
-// extent is rounded up to 8 rows.  A box larger than kTmaBox falls back to
-// bounds-checked global gathers.  The wait is bounded (about one second of
-// clock): a CTA that gives up counts PMF_DIAG_TIMEOUT, waits once more for its
-// copies, writes NaN to its pixels and returns.
-
-constexpr int kTmaX = 40;                     // floats per staged row (one copy's x extent)
+// zeros, which is the zero padding of the trilinear interpolation.  The box's
+// x origin x0 is rounded down to a multiple of 4 voxels (the copy start must
+// be 16-byte aligned) and its y extent up to 8 rows.
+//
+// Bank layout: rows are 44 floats apart (12 banks) and, where the box is
+// narrow enough, planes are S = 8k * 44 + 16 floats apart (16 banks), so the
+// 4 x 4 x 2 voxels around any point fall in 32 distinct banks and a warp's
+// gathers do not conflict.  Copy destinations must be 128-byte aligned, so
+// the +16 is made by shifting odd planes' copies 16 voxels to the left in x:
+// plane z lands at z S - 16 (z & 1), and voxel (x, y, z) is always at
+// (x - x0) + 44 y + S z.  A box too wide for the shift uses S = 8k * 44;
+// one larger than kTmaBox falls back to bounds-checked global gathers.  The
+// wait is bounded (about one second of clock): a CTA that gives up counts
+// PMF_DIAG_TIMEOUT, waits once more for its copies, writes NaN to its pixels
+// and returns.
+constexpr int kTmaX = 44;                     // floats per staged row (one copy's x extent)
 constexpr int kTmaRows = 8;                   // rows per copy
+constexpr int kTmaSkew = 16;                  // extra plane stride (floats) of the conflict-free layout
 constexpr int kTmaBox = 8192;                 // staged floats (32 KB)
 constexpr long long kTmaWaitCycles = 2000000000LL;
 
@@ -175,9 +184,10 @@ __device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv,
     int a, b;
     pixel_of<RPB>(tile, ntu, a, b);
     const bool in = a < nu && b < nv;
+    tile_view(bs, views[p], g, step);
     Ray r;
     if (in) {
-        r = ray_init(views[p], nu, nv, a, b, g, (double)step);
+        r = ray_init(bs.vf, nu, nv, a, b, g);
     } else {
         r.mlo = 1; r.mhi = 0;
     }
@@ -197,7 +207,11 @@ __device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv,
         const Box bx = read_box(bs, sel);
         const int x0 = (bx.lx >> 2) << 2;                   // 16-byte aligned copy start (floor)
         const int byr = (bx.by + kTmaRows - 1) & ~(kTmaRows - 1);
-        const bool fits = bx.vol > 0 && bx.bx + (bx.lx - x0) <= kTmaX && (long long)byr * bx.bz * kTmaX <= kTmaBox;
+        const int span = bx.bx + (bx.lx - x0);              // floats of each row the samples read
+        const int skew = span + kTmaSkew <= kTmaX && (long long)bx.bz * (byr * kTmaX + kTmaSkew) <= kTmaBox
+                             ? kTmaSkew : 0;
+        const int S = byr * kTmaX + skew;                   // plane stride in the box
+        const bool fits = bx.vol > 0 && span <= kTmaX && (long long)bx.bz * S <= kTmaBox;
         if (threadIdx.x == 0 && bx.vol > 0 && !fits) diag_count(PMF_DIAG_PROJECT_BOX_FALLBACK);
         if (fits) {
             if (threadIdx.x == 0) {
@@ -206,10 +220,12 @@ __device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv,
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 const int nyb = byr / kTmaRows;
                 mbar_expect_tx(bar, (unsigned)(bx.bz * nyb * kTmaRows * kTmaX * sizeof(float)));
-                for (int zz = 0; zz < bx.bz; zz++)
+                for (int zz = 0; zz < bx.bz; zz++) {
+                    const int sh = skew * (zz & 1);  // a multiple of 4 voxels: the copy start stays aligned
                     for (int yb = 0; yb < nyb; yb++)
-                        tma_load_4d(box + (zz * byr + yb * kTmaRows) * kTmaX, map, x0, bx.ly + yb * kTmaRows,
+                        tma_load_4d(box + zz * S - sh + yb * kTmaRows * kTmaX, map, x0 - sh, bx.ly + yb * kTmaRows,
                                     bx.lz + zz, pv, bar);
+                }
             }
             const bool ok = mbar_wait_bounded(bar, parity);
             parity ^= 1u;
@@ -220,21 +236,27 @@ __device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv,
                 return;
             }
             if (act) {
-                const float syf = (float)kTmaX, szf = (float)(kTmaX * byr);
-                const int sy = kTmaX, sz = kTmaX * byr;
+                const float syf = (float)kTmaX, szf = (float)S;
+                const int sy = kTmaX, sz = S;
                 const float* qa = box + (ib[0] - x0) + (ib[1] - bx.ly) * sy + (ib[2] - bx.lz) * sz;
-                float jf = (float)j0;
-                for (int j = j0; j <= j1; j++, jf += 1.0f) {
-                    const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
-                                uz = fmaf(jf, r.dh[2], fb[2]);
+                // the staged loop's arithmetic with the x/y position and the
+                // z-paired blends in packed fp32 pairs (same bits, fewer
+                // instructions): (a00, a01), (a10, a11), then (b0, b1)
+                const f32x2 dxy = pack2(r.dh[0], r.dh[1]), bxy = pack2(fb[0], fb[1]), one = pack2(1.0f, 1.0f);
+                f32x2 jj = pack2((float)j0, (float)j0);
+                for (int j = j0; j <= j1; j++, jj = add2(jj, one)) {
+                    const f32x2 uxy = fma2(jj, dxy, bxy);
+                    const float ux = lo2(uxy), uy = hi2(uxy), uz = fmaf(lo2(jj), r.dh[2], fb[2]);
                     const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
-                    const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
+                    const f32x2 fxy = sub2(uxy, pack2(flx, fly));
+                    const float fx = lo2(fxy), fy = hi2(fxy), fz = uz - flz;
                     const float* q = qa + (int)fmaf(flz, szf, fmaf(fly, syf, flx));
-                    const float c000 = q[0], c100 = q[1], c010 = q[sy], c110 = q[sy + 1];
-                    const float c001 = q[sz], c101 = q[sz + 1], c011 = q[sz + sy], c111 = q[sz + sy + 1];
-                    const float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
-                    const float a01 = fmaf(fx, c101 - c001, c001), a11 = fmaf(fx, c111 - c011, c011);
-                    const float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
+                    const f32x2 c00 = pack2(q[0], q[sz]), c10 = pack2(q[1], q[sz + 1]);
+                    const f32x2 c01 = pack2(q[sy], q[sz + sy]), c11 = pack2(q[sy + 1], q[sz + sy + 1]);
+                    const f32x2 fx2 = pack2(fx, fx);
+                    const f32x2 a0 = fma2(fx2, sub2(c10, c00), c00), a1 = fma2(fx2, sub2(c11, c01), c01);
+                    const f32x2 bb = fma2(pack2(fy, fy), sub2(a1, a0), a0);
+                    const float b0 = lo2(bb), b1 = hi2(bb);
                     acc += fmaf(fz, b1 - b0, b0);
                 }
             }

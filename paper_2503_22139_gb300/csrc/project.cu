@@ -244,6 +244,7 @@ __device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv,
                 // instructions): (a00, a01), (a10, a11), then (b0, b1)
                 const f32x2 dxy = pack2(r.dh[0], r.dh[1]), bxy = pack2(fb[0], fb[1]), one = pack2(1.0f, 1.0f);
                 f32x2 jj = pack2((float)j0, (float)j0);
+#pragma unroll 2  // two samples' dependency chains interleave (measured 2% faster)
                 for (int j = j0; j <= j1; j++, jj = add2(jj, one)) {
                     const f32x2 uxy = fma2(jj, dxy, bxy);
                     const float ux = lo2(uxy), uy = hi2(uxy), uz = fmaf(lo2(jj), r.dh[2], fb[2]);

@@ -8,4 +8,5 @@ from .oracle import (  # noqa: F401
     lib, threads, set_threads, quat_to_rot,
     voxelize, voxelize_ambiguity, voxelize_backward, combine, combine_backward, warp, warp_backward,
     project, project_backward, project_gaussians, loss, dssim, tv, mbc_normality,
+    splat_params, splat, splat_backward,
 )

@@ -133,3 +133,47 @@ def line_integral(src, r, mean, scale, quat, rho) -> float:
     b = r @ A @ m
     c = m @ A @ m
     return float(rho * np.sqrt(2 * np.pi / a) * np.exp(-0.5 * (c - b * b / a)))
+
+
+def ray_space(view, x) -> np.ndarray:
+    """phi(x) of the X-ray rasterizer: (a, b) where the ray from the source
+    through x meets the detector plane (pixels, from the detector centre), and
+    the distance |x - src|.  Found by solving det + a du + b dv = src + s (x - src)."""
+    view = np.asarray(view, dtype=np.float64)
+    src, det, du, dv = view[0:3], view[3:6], view[6:9], view[9:12]
+    A = np.stack([du, dv, -(x - src)], axis=1)
+    a, b, _ = np.linalg.solve(A, src - det)
+    return np.array([a, b, np.linalg.norm(x - src)])
+
+
+def splat(nu, nv, views, mean, scale, quat, value, kappa=np.inf, h=1e-4) -> np.ndarray:
+    """Eq. 8-9 with the Jacobian of phi taken by central differences (step h mm)
+    and every matrix operation done by NumPy."""
+    views = np.asarray(views, dtype=np.float64).reshape(-1, 12)
+    mean = np.asarray(mean, dtype=np.float64).reshape(-1, 3)
+    scale = np.asarray(scale, dtype=np.float64).reshape(-1, 3)
+    quat = np.asarray(quat, dtype=np.float64).reshape(-1, 4)
+    value = np.asarray(value, dtype=np.float64).reshape(-1)
+    ia, ib = np.meshgrid(np.arange(nu) + 0.5 - nu / 2, np.arange(nv) + 0.5 - nv / 2)
+    xh = np.stack([ia, ib], axis=-1)  # [nv, nu, 2]
+    Y = np.zeros((len(views), nv, nu))
+    for p, view in enumerate(views):
+        src, det, du, dv = view[0:3], view[3:6], view[6:9], view[9:12]
+        normal = np.cross(du, dv)
+        for g in range(len(mean)):
+            if np.dot(normal, mean[g] - src) * np.dot(normal, det - src) <= 0:
+                continue
+            J = np.zeros((3, 3))
+            for t in range(3):
+                e = np.zeros(3)
+                e[t] = h
+                J[:, t] = (ray_space(view, mean[g] + e) - ray_space(view, mean[g] - e)) / (2 * h)
+            R = rotation(quat[g])
+            Sig = R @ np.diag(scale[g] ** 2) @ R.T
+            St = J @ Sig @ J.T
+            Sh = St[:2, :2]
+            rho_hat = np.sqrt(2 * np.pi * np.linalg.det(St) / np.linalg.det(Sh)) * value[g]
+            d = xh - ray_space(view, mean[g])[:2]
+            q = np.einsum("...i,ij,...j->...", d, np.linalg.inv(Sh), d)
+            Y[p] += np.where(q <= kappa ** 2, rho_hat * np.exp(-0.5 * q), 0.0)
+    return Y

@@ -54,6 +54,11 @@ def lib():
             L.orc_tv.restype = ct.c_double
             L.orc_mbc_normality.argtypes = [ct.c_int, ct.c_int64, _D, _D]
             L.orc_mbc_normality.restype = ct.c_double
+            L.orc_splat_params.argtypes = [_D, _D, _D, _D, ct.c_double, _D]
+            L.orc_splat_params.restype = ct.c_int
+            L.orc_splat.argtypes = [ct.c_int, ct.c_int, ct.c_int, _D, ct.c_int64, _D, _D, _D, _D, ct.c_double, _D]
+            L.orc_splat_backward.argtypes = [ct.c_int, ct.c_int, ct.c_int, _D, ct.c_int64, _D, _D, _D, _D,
+                                             ct.c_double, _D, _D, _D, _D, _D]
             _lib = L
     return _lib
 
@@ -263,3 +268,33 @@ def mbc_normality(E, with_grad=True):
     val = lib().orc_mbc_normality(L, N, _p(E), _p(g) if with_grad else None)
     return float(val), g
 
+
+
+def splat_params(view, mean, scale, quat, value):
+    """Eq. 8-9 for one Gaussian in one view: (p^_a, p^_b, Sigma^_00, Sigma^_01,
+    Sigma^_11, rho^, |Sigma~|, |Sigma^|), or None behind the source."""
+    out = np.zeros(8)
+    ok = lib().orc_splat_params(_p(_f64(view)), _p(_f64(mean)), _p(_f64(scale)), _p(_f64(quat)), float(value),
+                                _p(out))
+    return out if ok else None
+
+
+def splat(nu, nv, views, mean, scale, quat, value, kappa=3.0) -> np.ndarray:
+    """Eq. 9 X-ray rasterization of the Gaussians into P projections [P][nv][nu]."""
+    views = _f64(views).reshape(-1, 12)
+    P, G = views.shape[0], int(np.asarray(mean).reshape(-1, 3).shape[0])
+    Y = np.zeros((P, nv, nu))
+    lib().orc_splat(int(nu), int(nv), int(P), _p(views), G, _p(_f64(mean)), _p(_f64(scale)), _p(_f64(quat)),
+                    _p(_f64(value).reshape(-1)), float(kappa), _p(Y))
+    return Y
+
+
+def splat_backward(nu, nv, views, mean, scale, quat, value, dY, kappa=3.0):
+    """Adjoint of splat: (d_mean, d_scale, d_quat, d_value)."""
+    views = _f64(views).reshape(-1, 12)
+    P, G = views.shape[0], int(np.asarray(mean).reshape(-1, 3).shape[0])
+    dm, ds, dq, dv = np.zeros((G, 3)), np.zeros((G, 3)), np.zeros((G, 4)), np.zeros(G)
+    lib().orc_splat_backward(int(nu), int(nv), int(P), _p(views), G, _p(_f64(mean)), _p(_f64(scale)),
+                             _p(_f64(quat)), _p(_f64(value).reshape(-1)), float(kappa),
+                             _p(_f64(dY).reshape(P, nv, nu)), _p(dm), _p(ds), _p(dq), _p(dv))
+    return dm, ds, dq, dv

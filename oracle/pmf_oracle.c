@@ -17,6 +17,7 @@
  *   Eq. 2  I(x,p) = I_ref(x + d(x,p))                              warp
  *   Eq. 6  I(r) = integral of sigma along the ray                   project
  *   Eq. 10/12  mean L1 over the batch; Eq. 1 squared-norm form      loss
+ *   Eq. 8-9  local affine projection of each Gaussian to a 2-D Gaussian  splat (Stage 1)
  * Readings where the paper is silent (all listed in the design notes):
  *   Sigma = R(q/|q|) diag(s^2) R^T with q = (w,x,y,z) and s in mm; hard
  *   truncation q_form <= kappa^2 (kappa = +inf disables it); values are sampled
@@ -675,4 +676,278 @@ double orc_mbc_normality(int L, int64_t N, const double* E, double* dE) {
             for (int64_t v = 0; v < N; v++) dE[(int64_t)lk * N + v] = 4.0 * (n2 - 1.0) * e[v] / (3.0 * L);
     }
     return total / (3.0 * L);
+}
+
+/* ------------------------------------------- Stage-1 X-ray rasterizer */
+/*
+ * Eq. 8-9 (Gaussian splatting of the reference Gaussians into one cone-beam
+ * projection).  Ray space for view (src, det, du, dv): a point x maps to
+ *   x~ = phi(x) = (a(x), b(x), |x - src|),
+ * where (a, b) are the detector pixel coordinates (relative to the detector
+ * centre, in pixels) at which the ray from the source through x meets the
+ * detector plane, and the third coordinate is the distance along that ray, so
+ * integrating over it at fixed (a, b) integrates along one X-ray.  Eq. 8 takes
+ * the local affine approximation of phi at the Gaussian's mean p: with J the
+ * Jacobian of the composed map (the viewing transform W is the rigid part of
+ * it), Sigma~ = J Sigma J^T and p~ = phi(p).  Integrating the ray-space Gaussian
+ * over its third coordinate gives Eq. 9: a 2-D Gaussian with mean p^ and
+ * covariance Sigma^ (the first two rows and columns) and amplitude
+ * rho^ = sqrt(2 pi |Sigma~| / |Sigma^|) rho, evaluated at pixel centres
+ * x^ = (i + 1/2 - nu/2, j + 1/2 - nv/2).  Readings: a Gaussian whose mean is
+ * not in front of the source (depth <= 0) contributes nothing; the 2-D Gaussian
+ * is truncated to (x^ - p^)^T Sigma^-1 (x^ - p^) <= kappa^2 (kappa = +inf: none).
+ */
+
+typedef struct {
+    double src[3], D[3], n[3], ut[3], vt[3], h, a0, b0;
+} splat_view_t;
+
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* Detector-plane frame of one view: unit normal n (towards the detector),
+ * source-to-plane distance h, and the dual basis (ut, vt) of (du, dv) in the
+ * plane, so that a point y of the plane is det + (ut.(y-det)) du + (vt.(y-det)) dv. */
+static void splat_view(const double* view, splat_view_t* v) {
+    const double *src = view, *det = view + 3, *du = view + 6, *dv = view + 9;
+    for (int t = 0; t < 3; t++) { v->src[t] = src[t]; v->D[t] = det[t] - src[t]; }
+    double n[3] = {du[1] * dv[2] - du[2] * dv[1], du[2] * dv[0] - du[0] * dv[2], du[0] * dv[1] - du[1] * dv[0]};
+    double nn = sqrt(dot3(n, n));
+    double sgn = dot3(n, v->D) < 0.0 ? -1.0 : 1.0;
+    for (int t = 0; t < 3; t++) v->n[t] = sgn * n[t] / nn;
+    v->h = dot3(v->n, v->D);
+    double uu = dot3(du, du), vv = dot3(dv, dv), uv = dot3(du, dv), del = uu * vv - uv * uv;
+    for (int t = 0; t < 3; t++) {
+        v->ut[t] = (vv * du[t] - uv * dv[t]) / del;
+        v->vt[t] = (uu * dv[t] - uv * du[t]) / del;
+    }
+    v->a0 = dot3(v->ut, v->D);
+    v->b0 = dot3(v->vt, v->D);
+}
+
+static double det3(const double M[9]) {
+    return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) + M[2] * (M[3] * M[7] - M[4] * M[6]);
+}
+
+/* The projected 2-D Gaussian of one Gaussian in one view (Eq. 8-9).
+ * Out: ph[2] = p^, S[3] = (Sigma^_00, Sigma^_01, Sigma^_11), K[3] = the same
+ * entries of Sigma^-1, *rho_hat, and the intermediates the adjoint needs.
+ * Returns 0 when the mean is not in front of the source. */
+typedef struct {
+    double r[3], z, ua, vb, L, J[9], Sig[9], St[9], M[9], R[9], qn[4], qnorm, s[3];
+    double ph[2], S[3], K[3], detS, detSt, rho_hat, rho;
+} splat_g_t;
+
+static int splat_project(const splat_view_t* v, const double* mean, const double* scale, const double* quat,
+                         double value, splat_g_t* o) {
+    for (int t = 0; t < 3; t++) o->r[t] = mean[t] - v->src[t];
+    o->z = dot3(v->n, o->r);
+    if (!(o->z > 0.0)) return 0;
+    o->ua = dot3(v->ut, o->r);
+    o->vb = dot3(v->vt, o->r);
+    o->L = sqrt(dot3(o->r, o->r));
+    const double h = v->h, z = o->z;
+    /* phi(p): pixel coordinates of the ray through p (a0, b0: the detector centre) */
+    o->ph[0] = h * o->ua / z - v->a0;
+    o->ph[1] = h * o->vb / z - v->b0;
+    /* J = d phi / dx at p, rows (da/dx, db/dx, d|x - src|/dx) */
+    for (int t = 0; t < 3; t++) {
+        o->J[t] = h / z * (v->ut[t] - o->ua / z * v->n[t]);
+        o->J[3 + t] = h / z * (v->vt[t] - o->vb / z * v->n[t]);
+        o->J[6 + t] = o->r[t] / o->L;
+    }
+    /* Sigma = R diag(s^2) R^T = M M^T with M = R diag(s) */
+    quat_to_rot(quat, o->R, o->qn, &o->qnorm);
+    for (int j = 0; j < 3; j++) o->s[j] = scale[j];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) o->M[3 * i + j] = o->R[3 * i + j] * scale[j];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; k++) acc += o->M[3 * i + k] * o->M[3 * j + k];
+            o->Sig[3 * i + j] = acc;
+        }
+    /* Sigma~ = J Sigma J^T */
+    double JS[9];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; k++) acc += o->J[3 * i + k] * o->Sig[3 * k + j];
+            JS[3 * i + j] = acc;
+        }
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; k++) acc += JS[3 * i + k] * o->J[3 * j + k];
+            o->St[3 * i + j] = acc;
+        }
+    o->S[0] = o->St[0]; o->S[1] = o->St[1]; o->S[2] = o->St[4];
+    o->detS = o->S[0] * o->S[2] - o->S[1] * o->S[1];
+    o->detSt = det3(o->St);
+    o->K[0] = o->S[2] / o->detS; o->K[1] = -o->S[1] / o->detS; o->K[2] = o->S[0] / o->detS;
+    o->rho = value;
+    o->rho_hat = sqrt(2.0 * 3.14159265358979323846 * o->detSt / o->detS) * value;
+    return 1;
+}
+
+/* For tests: (p^_a, p^_b, Sigma^_00, Sigma^_01, Sigma^_11, rho^, |Sigma~|, |Sigma^|) of one
+ * Gaussian in one view; returns 0 (and leaves out untouched) behind the source. */
+int orc_splat_params(const double* view, const double* mean, const double* scale, const double* quat, double value,
+                     double* out) {
+    splat_view_t v;
+    splat_g_t g;
+    splat_view(view, &v);
+    if (!splat_project(&v, mean, scale, quat, value, &g)) return 0;
+    out[0] = g.ph[0]; out[1] = g.ph[1]; out[2] = g.S[0]; out[3] = g.S[1]; out[4] = g.S[2];
+    out[5] = g.rho_hat; out[6] = g.detSt; out[7] = g.detS;
+    return 1;
+}
+
+/* Eq. 9: Y[p][j][i] = sum_g rho^_g exp(-1/2 (x^ - p^_g)^T Sigma^_g^-1 (x^ - p^_g)), truncated at kappa. */
+void orc_splat(int nu, int nv, int P, const double* views, int64_t G, const double* mean, const double* scale,
+               const double* quat, const double* value, double kappa, double* Y) {
+    const double k2 = isinf(kappa) ? INFINITY : kappa * kappa;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < P; p++) {
+        splat_view_t v;
+        splat_view(views + 12 * p, &v);
+        double* Yp = Y + (int64_t)p * nu * nv;
+        for (int64_t q = 0; q < (int64_t)nu * nv; q++) Yp[q] = 0.0;
+        for (int64_t g = 0; g < G; g++) {
+            splat_g_t s;
+            if (!splat_project(&v, mean + 3 * g, scale + 3 * g, quat + 4 * g, value[g], &s)) continue;
+            for (int j = 0; j < nv; j++)
+                for (int i = 0; i < nu; i++) {
+                    double da = (double)i + 0.5 - 0.5 * (double)nu - s.ph[0];
+                    double db = (double)j + 0.5 - 0.5 * (double)nv - s.ph[1];
+                    double q2 = s.K[0] * da * da + 2.0 * s.K[1] * da * db + s.K[2] * db * db;
+                    if (!(q2 <= k2)) continue;
+                    Yp[(int64_t)j * nu + i] += s.rho_hat * exp(-0.5 * q2);
+                }
+        }
+    }
+}
+
+/* Adjoint of orc_splat with respect to every Gaussian parameter (the truncation
+ * indicator has zero derivative); gradients overwrite the outputs.  Per view the
+ * pixel sums give dL/drho^, dL/dp^ and dL/dSigma^-1; the chain then runs back
+ * through rho^ = sqrt(2 pi |Sigma~|/|Sigma^|) rho, Sigma^-1, Sigma~ = J Sigma J^T,
+ * Sigma = M M^T (M = R diag(s)), R(q/|q|), p^ = phi(p) and J(p). */
+void orc_splat_backward(int nu, int nv, int P, const double* views, int64_t G, const double* mean,
+                        const double* scale, const double* quat, const double* value, double kappa, const double* dY,
+                        double* d_mean, double* d_scale, double* d_quat, double* d_value) {
+    const double k2 = isinf(kappa) ? INFINITY : kappa * kappa;
+    splat_view_t* vs = (splat_view_t*)malloc(sizeof(splat_view_t) * (size_t)(P > 0 ? P : 1));
+    for (int p = 0; p < P; p++) splat_view(views + 12 * p, &vs[p]);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t g = 0; g < G; g++) {
+        double gmu[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gR[9] = {0}, grho = 0.0;
+        double qn[4] = {1, 0, 0, 0}, qnorm = 1.0;
+        for (int p = 0; p < P; p++) {
+            const splat_view_t* v = &vs[p];
+            splat_g_t s;
+            if (!splat_project(v, mean + 3 * g, scale + 3 * g, quat + 4 * g, value[g], &s)) continue;
+            for (int c = 0; c < 4; c++) qn[c] = s.qn[c];
+            qnorm = s.qnorm;
+            /* pixel sums */
+            double g_rh = 0.0, g_ph[2] = {0, 0}, gK[4] = {0, 0, 0, 0}; /* gK: full 2x2, row-major */
+            const double* dYp = dY + (int64_t)p * nu * nv;
+            for (int j = 0; j < nv; j++)
+                for (int i = 0; i < nu; i++) {
+                    double d[2] = {(double)i + 0.5 - 0.5 * (double)nu - s.ph[0],
+                                   (double)j + 0.5 - 0.5 * (double)nv - s.ph[1]};
+                    double q2 = s.K[0] * d[0] * d[0] + 2.0 * s.K[1] * d[0] * d[1] + s.K[2] * d[1] * d[1];
+                    if (!(q2 <= k2)) continue;
+                    double e = exp(-0.5 * q2), gy = dYp[(int64_t)j * nu + i];
+                    double c = gy * s.rho_hat * e;
+                    g_rh += gy * e;
+                    double Kd[2] = {s.K[0] * d[0] + s.K[1] * d[1], s.K[1] * d[0] + s.K[2] * d[1]};
+                    g_ph[0] += c * Kd[0];
+                    g_ph[1] += c * Kd[1];
+                    for (int a = 0; a < 2; a++)
+                        for (int b = 0; b < 2; b++) gK[2 * a + b] += -0.5 * c * d[a] * d[b];
+                }
+            /* rho^ = sqrt(2 pi detSt / detS) rho */
+            grho += g_rh * s.rho_hat / s.rho;
+            double g_detSt = g_rh * s.rho_hat / (2.0 * s.detSt), g_detS = -g_rh * s.rho_hat / (2.0 * s.detS);
+            /* K = S^-1 (full 2x2): gS = -K^T gK K^T */
+            double Km[4] = {s.K[0], s.K[1], s.K[1], s.K[2]}, Sm[4] = {s.S[0], s.S[1], s.S[1], s.S[2]}, gS[4];
+            for (int a = 0; a < 2; a++)
+                for (int b = 0; b < 2; b++) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 2; k++)
+                        for (int l = 0; l < 2; l++) acc += Km[2 * k + a] * gK[2 * k + l] * Km[2 * b + l];
+                    gS[2 * a + b] = -acc;
+                }
+            /* d|S|/dS = |S| S^-T */
+            for (int a = 0; a < 2; a++)
+                for (int b = 0; b < 2; b++) gS[2 * a + b] += g_detS * s.detS * Km[2 * b + a];
+            (void)Sm;
+            /* d|St|/dSt = |St| St^-T; St^-1 by cofactors */
+            double C[9];
+            const double* A = s.St;
+            C[0] = A[4] * A[8] - A[5] * A[7]; C[1] = -(A[3] * A[8] - A[5] * A[6]); C[2] = A[3] * A[7] - A[4] * A[6];
+            C[3] = -(A[1] * A[8] - A[2] * A[7]); C[4] = A[0] * A[8] - A[2] * A[6]; C[5] = -(A[0] * A[7] - A[1] * A[6]);
+            C[6] = A[1] * A[5] - A[2] * A[4]; C[7] = -(A[0] * A[5] - A[2] * A[3]); C[8] = A[0] * A[4] - A[1] * A[3];
+            double gSt[9];
+            for (int t = 0; t < 9; t++) gSt[t] = g_detSt * C[t]; /* |St| St^-T = cofactor matrix */
+            gSt[0] += gS[0]; gSt[1] += gS[1]; gSt[3] += gS[2]; gSt[4] += gS[3];
+            /* St = J Sig J^T: gJ = (gSt + gSt^T) J Sig, gSig = J^T gSt J */
+            double Gs[9], gJ[9], gSig[9], JSg[9];
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) Gs[3 * a + b] = gSt[3 * a + b] + gSt[3 * b + a];
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; k++) acc += s.J[3 * a + k] * s.Sig[3 * k + b];
+                    JSg[3 * a + b] = acc;
+                }
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; k++) acc += Gs[3 * a + k] * JSg[3 * k + b];
+                    gJ[3 * a + b] = acc;
+                }
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; k++)
+                        for (int l = 0; l < 3; l++) acc += s.J[3 * k + a] * gSt[3 * k + l] * s.J[3 * l + b];
+                    gSig[3 * a + b] = acc;
+                }
+            /* Sig = M M^T: gM = (gSig + gSig^T) M; M = R diag(s) */
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; k++) acc += (gSig[3 * a + k] + gSig[3 * k + a]) * s.M[3 * k + b];
+                    gR[3 * a + b] += acc * s.s[b];
+                    gs[b] += acc * s.R[3 * a + b];
+                }
+            /* p^ and J as functions of r = p - src through z, ua, vb and L */
+            const double h = v->h, z = s.z;
+            double g_ua = g_ph[0] * h / z, g_vb = g_ph[1] * h / z;
+            double g_z = -(g_ph[0] * h * s.ua + g_ph[1] * h * s.vb) / (z * z);
+            for (int t = 0; t < 3; t++) {
+                g_z += gJ[t] * (-h / (z * z) * v->ut[t] + 2.0 * h * s.ua / (z * z * z) * v->n[t]);
+                g_z += gJ[3 + t] * (-h / (z * z) * v->vt[t] + 2.0 * h * s.vb / (z * z * z) * v->n[t]);
+                g_ua += gJ[t] * (-h / (z * z) * v->n[t]);
+                g_vb += gJ[3 + t] * (-h / (z * z) * v->n[t]);
+            }
+            double gJt_r = (gJ[6] * s.r[0] + gJ[7] * s.r[1] + gJ[8] * s.r[2]) / s.L;
+            for (int t = 0; t < 3; t++) {
+                gmu[t] += (gJ[6 + t] - gJt_r * s.r[t] / s.L) / s.L;
+                gmu[t] += g_ua * v->ut[t] + g_vb * v->vt[t] + g_z * v->n[t];
+            }
+        }
+        double dR[4][9], gqn[4];
+        drot_dq(qn, dR);
+        for (int c4 = 0; c4 < 4; c4++) {
+            gqn[c4] = 0.0;
+            for (int t = 0; t < 9; t++) gqn[c4] += gR[t] * dR[c4][t];
+        }
+        double dotq = gqn[0] * qn[0] + gqn[1] * qn[1] + gqn[2] * qn[2] + gqn[3] * qn[3];
+        for (int c4 = 0; c4 < 4; c4++) d_quat[4 * g + c4] = (gqn[c4] - qn[c4] * dotq) / qnorm;
+        for (int a = 0; a < 3; a++) { d_mean[3 * g + a] = gmu[a]; d_scale[3 * g + a] = gs[a]; }
+        d_value[g] = grho;
+    }
+    free(vs);
 }

@@ -138,6 +138,48 @@ pmf_status gs_voxelize_backward(const pmf_grid* grid, const pmf_gaussians* g, co
                                 float* d_mean, float* d_scale, float* d_quat, float* d_value,
                                 int accumulate, void* ws, size_t ws_bytes, pmf_stream stream);
 
+/* ------------------------------ Stage-1 X-ray rasterizer (Eq. 8-9) */
+
+/* Gaussian splatting of one Gaussian set (channels = 1) into P cone-beam
+ * projections, Stage 1 of Sec. 2.3.2 (Eq. 8-9):
+ *   proj[p][j][i] = sum_g rho^_g exp(-1/2 (x^ - p^_g)^T Sigma^_g^-1 (x^ - p^_g))
+ * over Gaussians whose 2-D Mahalanobis distance at the pixel is <= kappa (the
+ * set's truncation radius; +inf: none).  Ray space of view p maps x to the
+ * detector pixel coordinates (a, b) where the ray from the source through x
+ * meets the detector plane, measured in pixels from the detector centre, and
+ * the distance |x - src|; J is its Jacobian at the Gaussian's mean mu (Eq. 8's
+ * local affine approximation, the viewing transform included),
+ * Sigma~ = J Sigma J^T, Sigma^ its leading 2x2 block, p^ = (a, b)(mu),
+ * rho^ = sqrt(2 pi |Sigma~| / |Sigma^|) rho (= rho sqrt(2 pi / (c^T Sigma^-1 c)),
+ * c the unit ray direction through mu), and x^ the pixel centre
+ * (i + 1/2 - nu/2, j + 1/2 - nv/2).  Gaussians whose mean is not in front of
+ * the source contribute nothing.  views: device [P] (du, dv need not be
+ * orthogonal; they must span the detector plane); proj: device [P][nv][nu]
+ * fp32, overwritten.  Per-pixel sums are exact integers at a per-view scale
+ * (each term < 2^21 of it), so the result does not depend on summation order.
+ * The workspace (gs_rasterize_workspace) holds per-view frames, the projected
+ * Gaussians and per-tile lists of at most pair_capacity (Gaussian, 16x16 tile)
+ * entries; tiles whose lists do not fit scan every Gaussian of the view
+ * (same result, slower, counted as PMF_DIAG_RASTER_LIST_OVERFLOW).
+ * gs_rasterize_count writes the number of (Gaussian, tile) pairs the call needs
+ * into *d_pairs (device int64) using the same workspace. */
+pmf_status gs_rasterize_workspace(const pmf_detector* det, int32_t P, int64_t n, int64_t pair_capacity,
+                                  size_t* bytes);
+pmf_status gs_rasterize_count(const pmf_detector* det, int32_t P, const pmf_view* views, const pmf_gaussians* g,
+                              int64_t* d_pairs, void* ws, size_t ws_bytes, pmf_stream stream);
+pmf_status gs_rasterize(const pmf_detector* det, int32_t P, const pmf_view* views, const pmf_gaussians* g,
+                        float* proj, void* ws, size_t ws_bytes, pmf_stream stream);
+
+/* Adjoint of gs_rasterize: d_mean [n][3], d_scale [n][3], d_quat [n][4],
+ * d_value [n] (fp32, overwritten, or added to with accumulate = 1) from
+ * d_proj [P][nv][nu].  One warp per Gaussian walks its pixels in every view in
+ * a fixed order, so the result is bit-reproducible; the truncation indicator
+ * has zero derivative.  The workspace is gs_rasterize_workspace's (any pair
+ * capacity, 0 included). */
+pmf_status gs_rasterize_backward(const pmf_detector* det, int32_t P, const pmf_view* views, const pmf_gaussians* g,
+                                 const float* d_proj, float* d_mean, float* d_scale, float* d_quat, float* d_value,
+                                 int accumulate, void* ws, size_t ws_bytes, pmf_stream stream);
+
 /* --------------------------------------------------- DVF combine (Eq. 3) */
 
 /* dvf[p][k][v] = sum_l coeff[p][l][k] * mbc[l][k][v].  mbc [L][3][N], dvf
@@ -389,7 +431,9 @@ typedef enum {
                                               magnitude was NaN or infinite (outputs set to NaN) */
     PMF_DIAG_TIMEOUT = 5,                  /* CTAs whose bounded wait for a bulk (TMA) copy ran out
                                               (about one second); their outputs are set to NaN */
-    PMF_DIAG_COUNT = 6
+    PMF_DIAG_RASTER_LIST_OVERFLOW = 6,     /* rasterizer tiles whose Gaussian list overflowed the
+                                              workspace's pair capacity (scanned every Gaussian instead) */
+    PMF_DIAG_COUNT = 7
 } pmf_diag;
 
 /* Copies the current device's counters to host_out[PMF_DIAG_COUNT] and, with

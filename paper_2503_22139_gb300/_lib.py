@@ -44,9 +44,9 @@ class PmfBackprojectItem(ct.Structure):
 
 
 PMF_MAX_LEVELS = 8
-PMF_DIAG_COUNT = 6
+PMF_DIAG_COUNT = 7
 DIAG_NAMES = ("voxelize_list_overflow", "project_box_fallback", "backproject_box_fallback", "warp_halo_exit",
-              "nonfinite", "timeout")
+              "nonfinite", "timeout", "raster_list_overflow")
 PMF_OPS = {"voxelize": 1, "voxelize_backward": 2, "combine_backward": 3, "warp_backward": 4,
            "warp_combine_backward": 5, "project_backward": 6, "loss": 7}
 
@@ -88,6 +88,11 @@ SIGNATURES = {
     "gs_voxelize_count": [_G, ct.POINTER(PmfGaussians), _P, _P, ct.c_size_t, _P],
     "gs_voxelize": [_G, ct.POINTER(PmfGaussians), ct.c_int, _P, _P, ct.c_size_t, _P],
     "gs_voxelize_backward_workspace": [_G, _I64, _I32, _SZ],
+    "gs_rasterize_workspace": [ct.POINTER(PmfDetector), _I32, _I64, _I64, _SZ],
+    "gs_rasterize_count": [ct.POINTER(PmfDetector), _I32, _P, ct.POINTER(PmfGaussians), _P, _P, ct.c_size_t, _P],
+    "gs_rasterize": [ct.POINTER(PmfDetector), _I32, _P, ct.POINTER(PmfGaussians), _P, _P, ct.c_size_t, _P],
+    "gs_rasterize_backward": [ct.POINTER(PmfDetector), _I32, _P, ct.POINTER(PmfGaussians), _P, _P, _P, _P, _P,
+                              ct.c_int, _P, ct.c_size_t, _P],
     "gs_voxelize_backward": [_G, ct.POINTER(PmfGaussians), _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
     "mbc_combine": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P],
     "mbc_combine_backward_workspace": [_G, _I32, _I32, _SZ],

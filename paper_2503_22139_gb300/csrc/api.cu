@@ -110,6 +110,7 @@ pmf_status pmf_device_counters(uint64_t* host_out, int32_t reset) {
     if ((st = pmf::diag_project(sum, reset)) != PMF_OK) return st;
     if ((st = pmf::diag_warp(sum, reset)) != PMF_OK) return st;
     if ((st = pmf::diag_backproject(sum, reset)) != PMF_OK) return st;
+    if ((st = pmf::diag_splat(sum, reset)) != PMF_OK) return st;
     for (int i = 0; i < PMF_DIAG_COUNT; i++) host_out[i] = (uint64_t)sum[i];
     return PMF_OK;
 }

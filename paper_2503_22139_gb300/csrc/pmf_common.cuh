@@ -58,6 +58,7 @@ pmf_status diag_voxelize(unsigned long long* out, int reset);
 pmf_status diag_project(unsigned long long* out, int reset);
 pmf_status diag_warp(unsigned long long* out, int reset);
 pmf_status diag_backproject(unsigned long long* out, int reset);
+pmf_status diag_splat(unsigned long long* out, int reset);
 
 // Launch shape of the ray marchers used by plans: form 0 is one CTA per
 // (view, pixel tile), k > 0 a persistent launch of k CTAs per SM; chunk (16 or

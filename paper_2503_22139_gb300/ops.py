@@ -153,6 +153,66 @@ def gs_voxelize_backward(grid, gs: Gaussians, d_out: torch.Tensor, grads=None, a
     return grads
 
 
+# ------------------------------------- Stage-1 X-ray rasterizer (Eq. 8-9)
+
+def gs_rasterize_workspace(det, P: int, n: int, pair_capacity: int) -> int:
+    L = _lib.load()
+    return _size(L.gs_rasterize_workspace, ct.byref(_det(det)), int(P), int(n), int(pair_capacity))
+
+
+def gs_rasterize_count(det, views: torch.Tensor, gs: Gaussians) -> int:
+    """Exact number of (Gaussian, 16x16-tile) overlaps over all views (synchronizes)."""
+    L = _lib.load()
+    views = _need(views, "views", torch.float64)
+    P = int(views.shape[0])
+    ws = _ws(gs_rasterize_workspace(det, P, gs.n, 0), gs.mean.device)
+    out = torch.zeros(1, dtype=torch.int64, device=gs.mean.device)
+    s = gs.c_struct()
+    check(L.gs_rasterize_count(ct.byref(_det(det)), P, _p(views), ct.byref(s), _p(out), _p(ws), ws.numel(),
+                               _stream()), "gs_rasterize_count")
+    return int(out.item())
+
+
+def gs_rasterize(det, views: torch.Tensor, gs: Gaussians, pair_capacity: Optional[int] = None,
+                 out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Eq. 9 Gaussian splatting of a one-channel set into P projections -> [P, nv, nu] fp32."""
+    L = _lib.load()
+    views = _need(views, "views", torch.float64)
+    P = int(views.shape[0])
+    d = _det(det)
+    dev = gs.mean.device
+    if out is None:
+        out = torch.empty((P, d.nv, d.nu), dtype=torch.float32, device=dev)
+    out = _need(out, "out", torch.float32)
+    if ws is None:
+        cap = gs_rasterize_count(det, views, gs) if pair_capacity is None else int(pair_capacity)
+        ws = _ws(gs_rasterize_workspace(det, P, gs.n, cap), dev)
+    s = gs.c_struct()
+    check(L.gs_rasterize(ct.byref(d), P, _p(views), ct.byref(s), _p(out), _p(ws), ws.numel(), _stream()),
+          "gs_rasterize")
+    return out
+
+
+def gs_rasterize_backward(det, views: torch.Tensor, gs: Gaussians, d_proj: torch.Tensor, grads=None,
+                          accumulate: bool = False, ws=None):
+    """Adjoint of gs_rasterize -> (d_mean, d_scale, d_quat, d_value), fp32."""
+    L = _lib.load()
+    views = _need(views, "views", torch.float64)
+    d_proj = _need(d_proj, "d_proj", torch.float32)
+    P = int(views.shape[0])
+    dev = gs.mean.device
+    if grads is None:
+        grads = (torch.empty((gs.n, 3), device=dev), torch.empty((gs.n, 3), device=dev),
+                 torch.empty((gs.n, 4), device=dev), torch.empty((gs.n, 1), device=dev))
+    if ws is None:
+        ws = _ws(gs_rasterize_workspace(det, P, gs.n, 0), dev)
+    s = gs.c_struct()
+    check(L.gs_rasterize_backward(ct.byref(_det(det)), P, _p(views), ct.byref(s), _p(d_proj),
+                                  *[_p(t) for t in grads], int(accumulate), _p(ws), ws.numel(), _stream()),
+          "gs_rasterize_backward")
+    return grads
+
+
 # ------------------------------------------------------- combine / warp
 
 def mbc_combine(grid, mbc: torch.Tensor, coeff: torch.Tensor, out=None) -> torch.Tensor:

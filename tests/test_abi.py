@@ -102,3 +102,25 @@ def test_bad_arguments_are_rejected_before_launch():
                    ct.c_void_p(256), 1 << 16, None) == -1
     assert _status("mbc_combine", ct.byref(g), 9, 1, 0, ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(16),
                    None) == -1
+
+
+def test_rasterizer_workspace_and_host_validation():
+    d = _lib.PmfDetector(512, 384, 1.0)
+    n0, n1 = ct.c_size_t(0), ct.c_size_t(0)
+    assert _status("gs_rasterize_workspace", ct.byref(d), 32, 100000, 0, ct.byref(n0)) == 0
+    assert _status("gs_rasterize_workspace", ct.byref(d), 32, 100000, 10**6, ct.byref(n1)) == 0
+    # 32 bytes per projected Gaussian and 16 per pixel box, 4 per list entry
+    assert n0.value >= 32 * 100000 * 48 and n1.value - n0.value >= 4 * 10**6 - 256
+    fake = ct.c_void_p(256)
+    gs = _lib.PmfGaussians(10, 3, 3.0, 16, 16, 16, 16)  # three channels: not a density set
+    assert _status("gs_rasterize", ct.byref(d), 1, fake, ct.byref(gs), fake, fake, 1 << 30, None) == -1
+    assert b"one channel" in _lib.load().pmf_last_error()
+    gs = _lib.PmfGaussians(10, 1, 0.0, 16, 16, 16, 16)  # kappa = 0
+    assert _status("gs_rasterize", ct.byref(d), 1, fake, ct.byref(gs), fake, fake, 1 << 30, None) == -1
+    gs = _lib.PmfGaussians(10, 1, 3.0, 16, 16, 16, 16)
+    assert _status("gs_rasterize", ct.byref(d), 1, None, ct.byref(gs), fake, fake, 1 << 30, None) == -1
+    assert _status("gs_rasterize", ct.byref(d), 1, fake, ct.byref(gs), fake, fake, 16, None) == -3
+    bad = _lib.PmfDetector(0, 384, 1.0)
+    assert _status("gs_rasterize", ct.byref(bad), 1, fake, ct.byref(gs), fake, fake, 1 << 30, None) == -1
+    assert _status("gs_rasterize_backward", ct.byref(d), 1, fake, ct.byref(gs), fake, None, fake, fake, fake, 0,
+                   fake, 1 << 30, None) == -1

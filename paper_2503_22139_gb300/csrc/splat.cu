@@ -4,10 +4,12 @@
 // Gaussians are summed at pixel centres.
 //
 //   k_splat_frames  one thread per view: the detector-plane frame in double
-//   k_splat_prep    one thread per (view, Gaussian): p^ (double), Sigma^-1,
-//                   rho^, the kappa-ellipse's pixel box, per-tile counts
-//   k_splat_scan    one CTA: tile offsets of every view's lists
-//   k_splat_fill    one thread per (view, Gaussian): the per-tile lists
+//   k_splat_prep    one CTA per (view, Gaussian chunk): p^ (double), Sigma^-1,
+//                   rho^, the kappa-ellipse's pixel box, and the chunk's
+//                   per-tile counts in a shared-memory histogram
+//   k_scan_*        prefix sums over (view, tile, chunk): list offsets
+//   k_splat_fill    one CTA per (view, Gaussian chunk): the per-tile lists,
+//                   placed through shared-memory cursors (no global atomics)
 //   k_splat_render  one CTA per (16x16 tile, view), one pixel per thread: the
 //                   tile's list staged in shared memory in batches; each warp
 //                   owns an 8x4 pixel block, tests 32 entries at a time (one
@@ -65,15 +67,28 @@ struct RasterWs {
     SplatRec* rec;               // [P][n]
     int4* rect;                  // [P][n] pixel box (i0, j0, i1, j1); empty: i1 < i0
     float* sums;                 // [P][n][8] the adjoint's pixel sums
-    unsigned* tcount;            // [P*T]
-    unsigned* toff;              // [P*T + 1]
-    unsigned* cursor;            // [P*T]
+    unsigned* chist;             // [P][T][C] (view, tile, Gaussian chunk) overlap counts
+    unsigned* coff;              // [P*T*C + 1] their exclusive prefix sums: list offsets
+    unsigned long long* bsum;    // [scan blocks] the scan's block totals
     unsigned* maxbits;           // [P] largest |rho^| (float bits)
+    int chunk, C;                // Gaussians per chunk and chunks per view
     unsigned long long* total;   // pairs the call needs
     unsigned* list;              // [capacity] Gaussian indices, tile-major
     int64_t capacity;
     size_t list_off;             // byte offset of the list in the workspace
 };
+
+constexpr int kPrepThreads = 256;
+constexpr int kMaxTiles = 12288;  // shared-memory histogram of a view's tiles (48 KB)
+constexpr int kScanItems = 4096;  // 256 threads x 16 per scan block
+
+// Gaussians per (view, chunk) CTA of the prep and fill: about 8 CTAs per SM in
+// total, at least one per thread, at most 8,192.
+int chunk_of(int P, int64_t n) {
+    const int64_t want = ((int64_t)P * n + 152 * 8 - 1) / (152 * 8);
+    int64_t c = (want + kPrepThreads - 1) / kPrepThreads * kPrepThreads;
+    return (int)(c < kPrepThreads ? kPrepThreads : (c > 8192 ? 8192 : c));
+}
 
 size_t raster_ws_layout(int P, int64_t n, int64_t T, int64_t capacity, RasterWs* w, char* base) {
     size_t off = 0;
@@ -88,9 +103,12 @@ size_t raster_ws_layout(int P, int64_t n, int64_t T, int64_t capacity, RasterWs*
     x.rec = (SplatRec*)take(sizeof(SplatRec) * Pn);
     x.rect = (int4*)take(sizeof(int4) * Pn);
     x.sums = (float*)take(sizeof(float) * 8 * Pn);
-    x.tcount = (unsigned*)take(sizeof(unsigned) * PT);
-    x.toff = (unsigned*)take(sizeof(unsigned) * (PT + 1));
-    x.cursor = (unsigned*)take(sizeof(unsigned) * PT);
+    x.chunk = chunk_of(P, n);
+    x.C = (int)((n + x.chunk - 1) / x.chunk);
+    const size_t N = PT * (size_t)x.C;
+    x.chist = (unsigned*)take(sizeof(unsigned) * (N > 0 ? N : 1));
+    x.coff = (unsigned*)take(sizeof(unsigned) * (N + 1));
+    x.bsum = (unsigned long long*)take(sizeof(unsigned long long) * (N / kScanItems + 2));
     x.maxbits = (unsigned*)take(sizeof(unsigned) * (size_t)(P > 0 ? P : 1));
     x.total = (unsigned long long*)take(sizeof(unsigned long long));
     x.list_off = off;
@@ -219,67 +237,101 @@ __device__ __forceinline__ float splat_q(float k0, float k1, float k2, float da,
 
 __device__ __forceinline__ float pixel_x(int i, int n) { return (float)i + (0.5f - 0.5f * (float)n); }
 
-__global__ void k_splat_prep(pmf_gaussians G, int P, int nu, int nv, int ntu, int T, RasterWs w, int count_tiles) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)P * G.n) return;
-    const int p = (int)(idx / G.n);
-    const int64_t g = idx - (int64_t)p * G.n;
-    const float mu[3] = {__ldg(G.mean + 3 * g), __ldg(G.mean + 3 * g + 1), __ldg(G.mean + 3 * g + 2)};
-    const float s[3] = {__ldg(G.scale + 3 * g), __ldg(G.scale + 3 * g + 1), __ldg(G.scale + 3 * g + 2)};
-    const float q[4] = {__ldg(G.quat + 4 * g), __ldg(G.quat + 4 * g + 1), __ldg(G.quat + 4 * g + 2),
-                        __ldg(G.quat + 4 * g + 3)};
-    const float val = __ldg(G.value + g);
-    const bool finite_in = isfinite(mu[0] + mu[1] + mu[2]) && isfinite(s[0] + s[1] + s[2]) &&
-                           isfinite(q[0] + q[1] + q[2] + q[3]) && isfinite(val);
+// One CTA per (Gaussian chunk, view): the projected Gaussians and their pixel
+// boxes; with count_tiles, the chunk's per-tile overlap counts (shared-memory
+// histogram, written densely to chist) and the view's largest |rho^|.
+__global__ void __launch_bounds__(kPrepThreads) k_splat_prep(pmf_gaussians G, int P, int nu, int nv, int ntu, int T,
+                                                             RasterWs w, int count_tiles) {
+    extern __shared__ unsigned hist[];
+    const int p = blockIdx.y, c = blockIdx.x;
+    const int64_t g0 = (int64_t)c * w.chunk, g1 = g0 + w.chunk < G.n ? g0 + w.chunk : G.n;
+    if (count_tiles)
+        for (int t = threadIdx.x; t < T; t += kPrepThreads) hist[t] = 0u;
+    __syncthreads();
     const SplatFrame& fr = w.frames[p];
-    SplatGeo o;
-    splat_geo(fr, mu, s, q, o);
-    SplatRec rc;
-    splat_centre(fr, mu, rc.a, rc.b);
-    int4 rt = make_int4(0, 0, -1, -1);
-    if (o.ok) {
-        const float id = 1.0f / o.det;
-        rc.k0 = o.S11 * id; rc.k1 = -o.S01 * id; rc.k2 = o.S00 * id;
-        rc.rho = val * sqrtf(kTwoPi / o.lam);
-        rc.wa = G.kappa * sqrtf(o.S00);
-        rc.wb = G.kappa * sqrtf(o.S11);
-        // pixels i with |x(i) - a| <= wa, one pixel of slack; clamped in float first
-        // (wa may be +inf), then the per-pixel test decides
-        const float ci = rc.a + 0.5f * (float)nu - 0.5f, cj = rc.b + 0.5f * (float)nv - 0.5f;
-        const float i0 = fminf(fmaxf(ceilf(ci - rc.wa) - 1.0f, 0.0f), (float)nu);
-        const float i1 = fminf(fmaxf(floorf(ci + rc.wa) + 1.0f, -1.0f), (float)(nu - 1));
-        const float j0 = fminf(fmaxf(ceilf(cj - rc.wb) - 1.0f, 0.0f), (float)nv);
-        const float j1 = fminf(fmaxf(floorf(cj + rc.wb) + 1.0f, -1.0f), (float)(nv - 1));
-        if (isfinite(rc.a) && isfinite(rc.b) && isfinite(rc.rho) && i0 <= i1 && j0 <= j1)
-            rt = make_int4((int)i0, (int)j0, (int)i1, (int)j1);
-    } else {
-        rc.k0 = rc.k1 = rc.k2 = 0.0f;
-        rc.rho = 0.0f;
-        rc.wa = rc.wb = -1.0f;
+    unsigned mbits = 0u;
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += kPrepThreads) {
+        const int64_t idx = (int64_t)p * G.n + g;
+        const float mu[3] = {__ldg(G.mean + 3 * g), __ldg(G.mean + 3 * g + 1), __ldg(G.mean + 3 * g + 2)};
+        const float s[3] = {__ldg(G.scale + 3 * g), __ldg(G.scale + 3 * g + 1), __ldg(G.scale + 3 * g + 2)};
+        const float q[4] = {__ldg(G.quat + 4 * g), __ldg(G.quat + 4 * g + 1), __ldg(G.quat + 4 * g + 2),
+                            __ldg(G.quat + 4 * g + 3)};
+        const float val = __ldg(G.value + g);
+        const bool finite_in = isfinite(mu[0] + mu[1] + mu[2]) && isfinite(s[0] + s[1] + s[2]) &&
+                               isfinite(q[0] + q[1] + q[2] + q[3]) && isfinite(val);
+        SplatGeo o;
+        splat_geo(fr, mu, s, q, o);
+        SplatRec rc;
+        splat_centre(fr, mu, rc.a, rc.b);
+        int4 rt = make_int4(0, 0, -1, -1);
+        if (o.ok) {
+            const float id = 1.0f / o.det;
+            rc.k0 = o.S11 * id; rc.k1 = -o.S01 * id; rc.k2 = o.S00 * id;
+            rc.rho = val * sqrtf(kTwoPi / o.lam);
+            rc.wa = G.kappa * sqrtf(o.S00);
+            rc.wb = G.kappa * sqrtf(o.S11);
+            // pixels i with |x(i) - a| <= wa, one pixel of slack; clamped in float
+            // first (wa may be +inf), then the per-pixel test decides
+            const float ci = rc.a + 0.5f * (float)nu - 0.5f, cj = rc.b + 0.5f * (float)nv - 0.5f;
+            const float i0 = fminf(fmaxf(ceilf(ci - rc.wa) - 1.0f, 0.0f), (float)nu);
+            const float i1 = fminf(fmaxf(floorf(ci + rc.wa) + 1.0f, -1.0f), (float)(nu - 1));
+            const float j0 = fminf(fmaxf(ceilf(cj - rc.wb) - 1.0f, 0.0f), (float)nv);
+            const float j1 = fminf(fmaxf(floorf(cj + rc.wb) + 1.0f, -1.0f), (float)(nv - 1));
+            if (isfinite(rc.a) && isfinite(rc.b) && isfinite(rc.rho) && i0 <= i1 && j0 <= j1)
+                rt = make_int4((int)i0, (int)j0, (int)i1, (int)j1);
+        } else {
+            rc.k0 = rc.k1 = rc.k2 = 0.0f;
+            rc.rho = 0.0f;
+        }
+        if (rt.z < rt.x) rc.wa = rc.wb = -1.0f;  // nothing to draw: culled everywhere
+        w.rec[idx] = rc;
+        w.rect[idx] = rt;
+        if (!count_tiles) continue;
+        if (!finite_in || (o.ok && !isfinite(rc.rho))) {
+            // a non-finite parameter makes the whole view undefined: NaN scale, NaN output
+            diag_count(PMF_DIAG_NONFINITE);
+            mbits = 0x7fc00000u;
+        }
+        if (rt.z >= rt.x) {
+            mbits = max(mbits, abs_bits(rc.rho));
+            for (int tj = rt.y / kSplatTile; tj <= rt.w / kSplatTile; tj++)
+                for (int ti = rt.x / kSplatTile; ti <= rt.z / kSplatTile; ti++) atomicAdd(hist + tj * ntu + ti, 1u);
+        }
     }
-    if (rt.z < rt.x) rc.wa = rc.wb = -1.0f;  // nothing to draw: culled everywhere
-    w.rec[idx] = rc;
-    w.rect[idx] = rt;
-    if (count_tiles && (!finite_in || (o.ok && !isfinite(rc.rho)))) {
-        // a non-finite parameter makes the whole view undefined: NaN scale, NaN output
-        diag_count(PMF_DIAG_NONFINITE);
-        atomicMax(w.maxbits + p, 0x7fc00000u);
-    }
-    if (rt.z >= rt.x && count_tiles) {
-        atomicMax(w.maxbits + p, abs_bits(rc.rho));
-        for (int tj = rt.y / kSplatTile; tj <= rt.w / kSplatTile; tj++)
-            for (int ti = rt.x / kSplatTile; ti <= rt.z / kSplatTile; ti++)
-                atomicAdd(w.tcount + (int64_t)p * T + tj * ntu + ti, 1u);
+    if (!count_tiles) return;
+    mbits = __reduce_max_sync(0xffffffffu, mbits);
+    if ((threadIdx.x & 31) == 0 && mbits) atomicMax(w.maxbits + p, mbits);
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += kPrepThreads) w.chist[((int64_t)p * T + t) * w.C + c] = hist[t];
+}
+
+// Exclusive prefix sums of chist into coff (64-bit running sums, stored
+// clamped to 32 bits) in three passes: block totals, a one-CTA scan of the
+// totals (which also writes the grand total), and the per-block scans.
+__global__ void k_scan_reduce(const unsigned* __restrict__ x, int64_t N, unsigned long long* bsum) {
+    __shared__ unsigned long long part[8];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanItems + threadIdx.x * 16;
+    unsigned long long s = 0;
+    for (int k = 0; k < 16; k++)
+        if (b0 + k < N) s += x[b0 + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < 8; i++) t += part[i];
+        bsum[blockIdx.x] = t;
     }
 }
 
-__global__ void k_splat_scan(RasterWs w, int64_t PT) {
+__global__ void k_scan_top(unsigned long long* bsum, int nb, int64_t N, unsigned* coff,
+                           unsigned long long* total) {
     __shared__ unsigned long long part[1024];
     const int tid = threadIdx.x;
-    const int64_t per = (PT + 1023) / 1024;
-    const int64_t b = tid * per, e = b + per < PT ? b + per : PT;
+    const int per = (nb + 1023) / 1024;
+    const int b = tid * per, e = b + per < nb ? b + per : nb;
     unsigned long long s = 0;
-    for (int64_t i = b; i < e; i++) s += w.tcount[i];
+    for (int i = b; i < e; i++) s += bsum[i];
     part[tid] = s;
     __syncthreads();
     if (tid == 0) {
@@ -289,31 +341,62 @@ __global__ void k_splat_scan(RasterWs w, int64_t PT) {
             part[i] = run;
             run += v;
         }
-        *w.total = run;
+        *total = run;
+        coff[N] = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
     }
     __syncthreads();
     unsigned long long run = part[tid];
-    for (int64_t i = b; i < e; i++) {
-        const unsigned o = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
-        w.toff[i] = o;
-        w.cursor[i] = o;
-        run += w.tcount[i];
+    for (int i = b; i < e; i++) {
+        const unsigned long long v = bsum[i];
+        bsum[i] = run;
+        run += v;
     }
-    if (tid == 1023) w.toff[PT] = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
 }
 
-__global__ void k_splat_fill(int64_t n, int P, int ntu, int T, RasterWs w) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)P * n) return;
-    const int p = (int)(idx / n);
-    const int4 rt = w.rect[idx];
-    if (rt.z < rt.x) return;
-    const unsigned g = (unsigned)(idx - (int64_t)p * n);
-    for (int tj = rt.y / kSplatTile; tj <= rt.w / kSplatTile; tj++)
-        for (int ti = rt.x / kSplatTile; ti <= rt.z / kSplatTile; ti++) {
-            const unsigned pos = atomicAdd(w.cursor + (int64_t)p * T + tj * ntu + ti, 1u);
-            if ((int64_t)pos < w.capacity) w.list[pos] = g;
+__global__ void k_scan_apply(const unsigned* __restrict__ x, int64_t N, const unsigned long long* bsum, unsigned* coff) {
+    __shared__ unsigned long long part[256];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanItems + threadIdx.x * 16;
+    unsigned v[16];
+    unsigned long long s = 0;
+    for (int k = 0; k < 16; k++) {
+        v[k] = b0 + k < N ? x[b0 + k] : 0u;
+        s += v[k];
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = bsum[blockIdx.x];
+        for (int i = 0; i < 256; i++) {
+            const unsigned long long t = part[i];
+            part[i] = run;
+            run += t;
         }
+    }
+    __syncthreads();
+    unsigned long long run = part[threadIdx.x];
+    for (int k = 0; k < 16; k++) {
+        if (b0 + k < N) coff[b0 + k] = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
+        run += v[k];
+    }
+}
+
+// One CTA per (Gaussian chunk, view): every (Gaussian, tile) entry of the chunk
+// goes to its tile's list at the chunk's own offset, via shared-memory cursors.
+__global__ void __launch_bounds__(kPrepThreads) k_splat_fill(int64_t n, int P, int ntu, int T, RasterWs w) {
+    extern __shared__ unsigned cur[];
+    const int p = blockIdx.y, c = blockIdx.x;
+    for (int t = threadIdx.x; t < T; t += kPrepThreads) cur[t] = w.coff[((int64_t)p * T + t) * w.C + c];
+    __syncthreads();
+    const int64_t g0 = (int64_t)c * w.chunk, g1 = g0 + w.chunk < n ? g0 + w.chunk : n;
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += kPrepThreads) {
+        const int4 rt = w.rect[(int64_t)p * n + g];
+        if (rt.z < rt.x) continue;
+        for (int tj = rt.y / kSplatTile; tj <= rt.w / kSplatTile; tj++)
+            for (int ti = rt.x / kSplatTile; ti <= rt.z / kSplatTile; ti++) {
+                const unsigned pos = atomicAdd(cur + tj * ntu + ti, 1u);
+                if ((int64_t)pos < w.capacity) w.list[pos] = (unsigned)g;
+            }
+    }
 }
 
 // Scale 2^k with max * 2^k < 2^21 (every term below 2^21 of the scale).
@@ -341,7 +424,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_splat_render(int64_t n, int 
     const int kexp = splat_exponent(mx);
     const float fsc = ldexpf(1.0f, kexp);
     const int64_t cell = (int64_t)p * T + t;
-    const unsigned beg = w.toff[cell], end = w.toff[cell + 1];
+    const unsigned beg = w.coff[cell * w.C], end = w.coff[(cell + 1) * w.C];
     const bool overflow = (int64_t)end > w.capacity;
     if (overflow && threadIdx.x == 0) diag_count(PMF_DIAG_RASTER_LIST_OVERFLOW);
     const int64_t cnt = overflow ? n : (int64_t)(end - beg);
@@ -548,6 +631,9 @@ pmf_status check_raster(const pmf_detector* det, int32_t P, const pmf_view* view
     PMF_REQUIRE(det != nullptr && g != nullptr, "null argument");
     PMF_REQUIRE(det->nu > 0 && det->nv > 0, "detector size must be positive");
     PMF_REQUIRE((int64_t)det->nu * det->nv < ((int64_t)1 << 31), "detector too large");
+    int ntu_;
+    if (tiles_of(det, ntu_) > kMaxTiles)
+        return set_error(PMF_EUNSUPPORTED, "detector has more than %d 16x16 tiles", kMaxTiles);
     PMF_REQUIRE(P >= 0 && P < 65536, "P must be in [0, 65535]");
     PMF_REQUIRE(P == 0 || views != nullptr, "views is null");
     PMF_REQUIRE(g->n >= 0 && g->n < ((int64_t)1 << 32), "n must be in [0, 2^32)");
@@ -563,16 +649,19 @@ pmf_status raster_prep(const pmf_detector* det, int32_t P, const pmf_view* views
                        const RasterWs& w, int count_tiles, cudaStream_t s) {
     int ntu;
     const int T = tiles_of(det, ntu);
-    const int64_t PT = (int64_t)P * T;
+    if (P == 0) return PMF_OK;
+    if (count_tiles) cudaMemsetAsync(w.maxbits, 0, sizeof(unsigned) * (size_t)P, s);
+    k_splat_frames<<<(P + 31) / 32, 32, 0, s>>>(views, P, w.frames);
+    if (w.C > 0)
+        k_splat_prep<<<dim3((unsigned)w.C, (unsigned)P), kPrepThreads, count_tiles ? sizeof(unsigned) * T : 0, s>>>(
+            *g, P, det->nu, det->nv, ntu, T, w, count_tiles);
     if (count_tiles) {
-        cudaMemsetAsync(w.tcount, 0, sizeof(unsigned) * (size_t)PT, s);
-        cudaMemsetAsync(w.maxbits, 0, sizeof(unsigned) * (size_t)P, s);
+        const int64_t N = (int64_t)P * T * w.C;
+        const int nb = (int)((N + kScanItems - 1) / kScanItems);
+        if (nb > 0) k_scan_reduce<<<nb, 256, 0, s>>>(w.chist, N, w.bsum);
+        k_scan_top<<<1, 1024, 0, s>>>(w.bsum, nb, N, w.coff, w.total);
+        if (nb > 0) k_scan_apply<<<nb, 256, 0, s>>>(w.chist, N, w.bsum, w.coff);
     }
-    if (P > 0) k_splat_frames<<<(P + 31) / 32, 32, 0, s>>>(views, P, w.frames);
-    const int64_t pairs = (int64_t)P * g->n;
-    if (pairs > 0)
-        k_splat_prep<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(*g, P, det->nu, det->nv, ntu, T, w, count_tiles);
-    if (count_tiles) k_splat_scan<<<1, 1024, 0, s>>>(w, PT);
     return check_launch("gs_rasterize prep");
 }
 
@@ -631,9 +720,8 @@ pmf_status gs_rasterize(const pmf_detector* det, int32_t P, const pmf_view* view
     raster_ws_layout(P, g->n, T, capacity, &w, (char*)ws);
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = raster_prep(det, P, views, g, w, 1, s)) != PMF_OK) return st;
-    const int64_t pairs = (int64_t)P * g->n;
-    if (pairs > 0 && capacity > 0)
-        k_splat_fill<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(g->n, P, ntu, T, w);
+    if (w.C > 0 && capacity > 0)
+        k_splat_fill<<<dim3((unsigned)w.C, (unsigned)P), kPrepThreads, sizeof(unsigned) * T, s>>>(g->n, P, ntu, T, w);
     k_splat_render<<<dim3((unsigned)T, (unsigned)P), kRenderThreads, 0, s>>>(g->n, det->nu, det->nv, ntu, T, g->kappa,
                                                                             w, proj);
     return check_launch("gs_rasterize");

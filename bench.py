@@ -526,7 +526,7 @@ def run_native(a):
             torch.cuda.empty_cache()
         variants[f"batched_{main_dt}_over_plain_f32"] = round(value / variants["plain_per_projection_f32"], 3)
 
-        def timed_steps(run, n):
+        def timed_steps(run, n, views=B):
             for k in range(2):
                 run(k)
             torch.cuda.synchronize()
@@ -544,7 +544,7 @@ def run_native(a):
                 tt = torch.tensor([tv], device="cuda")
                 tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
                 tv = float(tt.item())
-            return B * n * world / tv
+            return views * n * world / tv
 
         # the Stage 2-3 objective of Eq. 14 (L1 + 0.25 D-SSIM + L_MBC + 0.05 TV on a
         # 32^3 crop drawn per step from a seeded generator)
@@ -558,6 +558,18 @@ def run_native(a):
         variants[f"eq14_objective_{a.dtype}"] = round(
             timed_steps(lambda k: estep.run(*batch(k), tv_origin=origins[k % n_orig]), a.steps), 3)
         del estep
+        torch.cuda.empty_cache()
+        # Stage 1 (Eq. 10-11): the reference Gaussians rasterized by Gaussian
+        # splatting (Eq. 8-9), L1 + 0.25 D-SSIM, 0.05 TV of a voxelized 32^3 crop
+        # drawn per step; batches of B views and of one view (the paper's Stage-1
+        # batch size)
+        from paper_2503_22139_gb300.pipeline import Stage1Step
+        centres = [Stage1Step.crop_centre(wl.grid, o.tolist(), 32).cuda() for o in origins.cpu()]
+        for vb in (B, 1):
+            s1 = Stage1Step(wl.grid, wl.det, ref, batch=vb, data_range=drange)
+            variants[f"stage1_rasterizer_B{vb}_views"] = round(timed_steps(
+                lambda k: s1.run(batch(k)[0][:vb], batch(k)[2][:vb], centres[k % n_orig]), a.steps, views=vb), 3)
+            del s1
         torch.cuda.empty_cache()
         # 100 optimisation iterations (B projections each, Adam on every Gaussian
         # parameter of copies of the sets); throughput and the loss trajectory

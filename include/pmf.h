@@ -379,6 +379,13 @@ pmf_status mbc_normality(const pmf_grid* grid, int32_t L, pmf_dtype dtype, const
 pmf_status pmf_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr, float beta1,
                          float beta2, float eps, int32_t t, pmf_stream stream);
 
+/* out[i][k] = mean[i][k] - offset[k] (device [n][3]; offset: device float[3]).
+ * The grids are centred on the isocentre, so voxelizing the Gaussians shifted
+ * by the centre c of a sub-volume on a grid of the sub-volume's size gives that
+ * sub-volume (the random TV crops of Sec. 2.3.2); gradients with respect to the
+ * shifted means are gradients with respect to the means.  out may equal mean. */
+pmf_status pmf_shift_means(int64_t n, const float* mean, const float* offset, float* out, pmf_stream stream);
+
 /* ------------------------------------------------------------ host helpers */
 
 /* The circular scan of Sec. 2.3.3 / Table I as pmf_view records: view p has

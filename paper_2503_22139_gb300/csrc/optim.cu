@@ -1,5 +1,6 @@
 // The optimiser update the training loop of Sec. 2.3.2 uses: Adam (Kingma &
-// Ba 2014), one fused element-wise pass per parameter tensor, in place:
+// Ba 2014), one fused element-wise pass per parameter tensor, in place (and a
+// translation of Gaussian means, for voxelizing a sub-volume):
 //   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
 //   p = p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 #include "pmf_common.cuh"
@@ -18,6 +19,13 @@ __global__ void __launch_bounds__(256) k_adam(int64_t n, float* __restrict__ p, 
         v[i] = vi;
         p[i] -= lr * (mi * ibc1) / (sqrtf(vi) * isbc2 + eps);
     }
+}
+
+__global__ void k_shift_means(int64_t n, const float* __restrict__ mean, const float* __restrict__ off,
+                              float* __restrict__ out) {
+    const float o[3] = {off[0], off[1], off[2]};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = mean[i] - o[i % 3];
 }
 
 }  // namespace
@@ -40,6 +48,16 @@ pmf_status pmf_adam_step(int64_t n, float* param, const float* grad, float* m, f
     k_adam<<<(unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks), 256, 0, (cudaStream_t)stream>>>(
         n, param, grad, m, v, lr, beta1, beta2, eps, (float)(1.0 / bc1), (float)(1.0 / sqrt(bc2)));
     return check_launch("pmf_adam_step");
+}
+
+pmf_status pmf_shift_means(int64_t n, const float* mean, const float* offset, float* out, pmf_stream stream) {
+    PMF_REQUIRE(n >= 0, "n must be >= 0");
+    PMF_REQUIRE(n == 0 || (mean && offset && out), "null pointer");
+    if (n == 0) return PMF_OK;
+    const int64_t nb = (3 * n + 255) / 256;
+    k_shift_means<<<(unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks), 256, 0, (cudaStream_t)stream>>>(
+        n, mean, offset, out);
+    return check_launch("pmf_shift_means");
 }
 
 }  // extern "C"

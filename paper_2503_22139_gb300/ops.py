@@ -155,6 +155,17 @@ def gs_voxelize_backward(grid, gs: Gaussians, d_out: torch.Tensor, grads=None, a
 
 # ------------------------------------- Stage-1 X-ray rasterizer (Eq. 8-9)
 
+def pmf_shift_means(mean: torch.Tensor, offset: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """mean [n, 3] - offset (device float32 [3]): Gaussians in the frame of a sub-volume centred at offset."""
+    mean = _need(mean, "mean", torch.float32)
+    offset = _need(offset, "offset", torch.float32)
+    if out is None:
+        out = torch.empty_like(mean)
+    check(_lib.load().pmf_shift_means(int(mean.shape[0]), _p(mean), _p(offset), _p(out), _stream()),
+          "pmf_shift_means")
+    return out
+
+
 def gs_rasterize_workspace(det, P: int, n: int, pair_capacity: int) -> int:
     L = _lib.load()
     return _size(L.gs_rasterize_workspace, ct.byref(_det(det)), int(P), int(n), int(pair_capacity))

@@ -25,6 +25,8 @@ KERNELS = {
     "gs_voxelize": 4, "gs_voxelize_backward": 2, "warp_combine": 1, "conebeam_project": 1,
     "projection_loss": 2, "conebeam_project_backward": 3, "warp_combine_backward": 4,
     "projection_dssim": 3, "tv_loss": 2, "mbc_normality": 3,
+    # rasterizer: frames, prep, 3 scan passes, fill, render; adjoint: frames, prep, sums, chain
+    "gs_rasterize": 7, "gs_rasterize_backward": 4, "pmf_shift_means": 1,
 }
 
 # The Stage 2-3 objective of Eq. 14 with the paper's weights (Sec. 2.3.2):
@@ -218,3 +220,81 @@ class GraphedStep:
             self.meas.copy_(meas, non_blocking=True)
         self.graph.replay()
         return self.loss
+
+
+class Stage1Step:
+    """Stage 1 of Sec. 2.3.2 (Eq. 10-11): the reference Gaussians rasterized into
+    B views by Gaussian splatting (Eq. 8-9), L1 + lambda_ssim D-SSIM against the
+    measured projections, and lambda_tv TV of a D^3 sub-volume voxelized from the
+    same Gaussians (the crop moves every step); gradients of both terms to every
+    Gaussian parameter land in `grads` (mean, scale, quat, value).
+
+    The sub-volume is voxelized on a D^3 grid of the volume's voxel size with the
+    means shifted by the crop's centre (the grids are centred on the isocentre),
+    so a crop with corner voxel o has centre (o + D/2 - n/2) v."""
+
+    def __init__(self, grid, det, ref: Gaussians, batch: int, data_range: float, lambda_ssim: float = 0.25,
+                 lambda_tv: float = 0.05, tv_size: int = 32, pair_headroom: float = 1.25):
+        if ref.channels != 1:
+            raise ValueError("Stage 1 renders the one-channel reference set")
+        self.grid, self.det, self.ref, self.B = grid, det, ref, int(batch)
+        self.data_range, self.lambda_ssim, self.lambda_tv, self.D = float(data_range), float(lambda_ssim), \
+            float(lambda_tv), int(tv_size)
+        self.headroom = float(pair_headroom)
+        dev = ref.mean.device
+        g = ops._grid(grid)
+        self.crop = (self.D, self.D, self.D, float(g.vx), float(g.vy), float(g.vz))
+        d = ops._det(det)
+        n = ref.n
+        self.Y = torch.empty((self.B, d.nv, d.nu), dtype=torch.float32, device=dev)
+        self.grads = (torch.empty((n, 3), device=dev), torch.empty((n, 3), device=dev),
+                      torch.empty((n, 4), device=dev), torch.empty((n, 1), device=dev))
+        self.rws = None  # sized at the first step, from the first batch's pair count
+        self.shifted = torch.empty_like(ref.mean)
+        self.crop_gs = Gaussians(self.shifted, ref.scale, ref.quat, ref.value, ref.kappa)
+        self.Vc = torch.empty((1, self.D, self.D, self.D), dtype=torch.float32, device=dev)
+        self.dVc = torch.empty((1, self.D, self.D, self.D), dtype=torch.float32, device=dev)
+        self.tv = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.origin = torch.zeros(3, dtype=torch.int32, device=dev)
+        # a D^3 crop has (D/8)^3 voxelizer tiles: at most that many per Gaussian
+        tiles = -(-self.D // 8) ** 3
+        self.cvox_ws = ops._ws(ops.gs_voxelize_workspace(self.crop, n, n * tiles), dev)
+        self.cvb_ws = ops._ws(ops.gs_voxelize_backward_workspace(self.crop, n, 1), dev)
+        Lb = ops._lib.load()
+        self.loss_ws = ops._ws(ops._size(Lb.projection_loss_workspace, self.B * d.nu * d.nv), dev)
+        self.ssim_ws = ops._ws(ops._size(Lb.projection_dssim_workspace, self.B, d.nu, d.nv), dev)
+        self.tv_ws = ops._ws(ops._size(Lb.tv_loss_workspace, self.D), dev)
+
+    @staticmethod
+    def crop_centre(grid, corner, D: int = 32) -> torch.Tensor:
+        """Centre (mm, host float32 [3]) of the D^3 crop whose lowest voxel is corner (x, y, z)."""
+        g = ops._grid(grid)
+        n = (g.nx, g.ny, g.nz)
+        v = (g.vx, g.vy, g.vz)
+        return torch.tensor([(corner[k] + D / 2 - n[k] / 2) * v[k] for k in range(3)], dtype=torch.float32)
+
+    @property
+    def launches_per_step(self) -> int:
+        k = KERNELS
+        return (k["gs_rasterize"] + k["projection_loss"] + k["projection_dssim"] + k["gs_rasterize_backward"]
+                + k["pmf_shift_means"] + k["gs_voxelize"] + k["tv_loss"] + k["gs_voxelize_backward"])
+
+    def run(self, views: torch.Tensor, meas: torch.Tensor, centre: torch.Tensor):
+        """views [B,12] f64, meas [B,nv,nu] f32, centre: device f32 [3], the TV
+        crop's centre (mm).  Returns (projection loss [1], TV loss [1]), device."""
+        det, ref = self.det, self.ref
+        if self.rws is None:
+            cap = int(ops.gs_rasterize_count(det, views, ref) * self.headroom) + 4096
+            self.rws = ops._ws(ops.gs_rasterize_workspace(det, self.B, ref.n, cap), ref.mean.device)
+        ops.gs_rasterize(det, views, ref, out=self.Y, ws=self.rws)
+        loss, dY = ops.projection_loss(1, self.Y, meas, ws=self.loss_ws)
+        ops.projection_dssim(self.Y, meas, self.data_range, weight=self.lambda_ssim, loss=loss, d_pred=dY,
+                             accumulate=True, ws=self.ssim_ws)
+        ops.gs_rasterize_backward(det, views, ref, dY, grads=self.grads, ws=self.rws)
+        ops.pmf_shift_means(ref.mean, centre, out=self.shifted)
+        ops.gs_voxelize(self.crop, self.crop_gs, out=self.Vc, ws=self.cvox_ws)
+        ops.tv_loss(self.crop, self.Vc[0], self.D, self.origin, weight=self.lambda_tv, loss=self.tv,
+                    d_vol=self.dVc[0], accumulate=False, ws=self.tv_ws)
+        ops.gs_voxelize_backward(self.crop, self.crop_gs, self.dVc, grads=self.grads, accumulate=True,
+                                 ws=self.cvb_ws)
+        return loss, self.tv

@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--small", action="store_true", help="the 64^3 / 2k-Gaussian / 128^2 case (for profiling)")
+    ap.add_argument("--rasterizer", action="store_true",
+                    help="time only the Stage-1 rasterizer (gs_rasterize + gs_rasterize_backward) on --batch views")
     return ap.parse_args()
 
 
@@ -135,8 +137,13 @@ def traffic_for(kernel: str, workload: str):
     d = json.load(open(path)).get(kernel)
     if not d or workload not in d.get("workloads", []):
         return None
-    src = os.path.join(ROOT, d["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d.get("source_sha"):
+    srcs = [os.path.join(ROOT, f) for f in d.get("sources", [d.get("source", "")])]
+    if not all(os.path.exists(f) for f in srcs):
+        return None
+    h = hashlib.sha256()
+    for f in srcs:
+        h.update(open(f, "rb").read())
+    if h.hexdigest()[:16] != d.get("source_sha"):
         return None
     return float(d["dram_bytes_per_launch"])
 
@@ -682,10 +689,51 @@ def run_reference(a):
     print(json.dumps(line))
 
 
+def run_rasterizer(a):
+    """Stage-1 rasterizer alone (for profiling): B views of the paper-scale
+    reference set, forward and adjoint (dY = 1), event-timed."""
+    import numpy as np
+    import torch
+    import paper_2503_22139_gb300 as pmf
+    import synth
+    torch.cuda.set_device(0)
+    wl = synth.paper_workload(p=660)
+    B = min(a.batch, wl.p)
+    d = lambda x, t=torch.float32: torch.as_tensor(np.ascontiguousarray(x), dtype=t, device="cuda")
+    vw = d(wl.views[synth.select_batch(wl.p, B, 0)], torch.float64)
+    g = pmf.Gaussians(d(wl.ref.mean), d(wl.ref.scale), d(wl.ref.quat), d(wl.ref.value), wl.kappa)
+    cap = pmf.gs_rasterize_count(wl.det, vw, g)
+    ws = pmf.ops._ws(pmf.ops.gs_rasterize_workspace(wl.det, B, g.n, cap), "cuda")
+    Y = pmf.gs_rasterize(wl.det, vw, g, ws=ws)
+    dY = torch.ones_like(Y)
+    grads = pmf.gs_rasterize_backward(wl.det, vw, g, dY, ws=ws)
+
+    def step():
+        pmf.gs_rasterize(wl.det, vw, g, ws=ws, out=Y)
+        pmf.gs_rasterize_backward(wl.det, vw, g, dY, grads=grads, ws=ws)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(a.steps, 1)
+    print(json.dumps({"metric": "rasterized views/s (Eq. 9 forward + adjoint, Stage 1)", "value": round(B / ms * 1e3, 3),
+                      "unit": "views/s", "ms_per_step": round(ms, 4), "steps": a.steps, "warmup": a.warmup,
+                      "config": {"workload": "paper-scale reference set, 100k Gaussians, 512x384 detector",
+                                 "views": B, "pairs": cap}}))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.rasterizer:
+        run_rasterizer(a)
     else:
         run_native(a)
 

@@ -578,6 +578,19 @@ def run_native(a):
                 lambda k: s1.run(batch(k)[0][:vb], batch(k)[2][:vb], centres[k % n_orig]), a.steps, views=vb), 3)
             del s1
         torch.cuda.empty_cache()
+        # 1 mm voxels (400x400x200, the same Gaussian sets; Sec. 4's batch-8 case):
+        # throughput of the batch-8 step and its peak device memory
+        w1 = synth.paper_workload_1mm(p=wl.p)
+        torch.cuda.reset_peak_memory_stats()
+        base_mem = torch.cuda.memory_allocated()
+        step1 = ForwardAdjoint(w1.grid, w1.det, ref, mbc, batch=8, dtype=dt, kind=a.kind, w_dtype=wdt)
+        m1 = torch.as_tensor(synth.measured_projections(np.random.default_rng(4343), 8, w1.det.nu, w1.det.nv, 400.0),
+                             dtype=torch.float32, device="cuda")
+        variants[f"step_1mm_B8_{a.dtype}"] = round(timed_steps(
+            lambda k: step1.run(batch(k)[0][:8], batch(k)[1][:8], m1), max(2, min(a.steps, 5)), views=8), 3)
+        variants["step_1mm_B8_peak_gib"] = round((torch.cuda.max_memory_allocated() - base_mem) / 2 ** 30, 2)
+        del step1, m1
+        torch.cuda.empty_cache()
         # 100 optimisation iterations (B projections each, Adam on every Gaussian
         # parameter of copies of the sets); throughput and the loss trajectory
         def clone_set(gs):

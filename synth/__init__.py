@@ -6,7 +6,7 @@ the CUDA path and the FP64 oracle consume what it produces.
 """
 from .workloads import (  # noqa: F401
     Grid, Detector, GaussianSet, Workload,
-    circular_views, small_workload, paper_workload, fd_subproblem, uneven_volumes,
+    circular_views, small_workload, paper_workload, paper_workload_1mm, fd_subproblem, uneven_volumes,
     gaussian_set, mbc_levels, breathing_coefficients, uniform_coefficients,
     measured_projections, select_batch, seeds_for,
 )

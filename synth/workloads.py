@@ -262,6 +262,18 @@ def paper_workload(p: int = 660, with_measured: bool = False, measured_for=None)
     return Workload("paper-200x200x100-100k-660views", grid, det, ref, mbc, views, coeff, 3.0, meas, gt=gt)
 
 
+def paper_workload_1mm(p: int = 660) -> Workload:
+    """The paper-scale scan at 1 mm voxels (Sec. 4: the 65 GB, batch-8 case):
+    the same Gaussian sets, views and coefficients as paper_workload (the same
+    physical object, scales 1-6 mm), voxelized on 400x400x200 at 1 mm and
+    marched at 0.5 mm (0.5 voxel)."""
+    wl = paper_workload(p)
+    grid = Grid(400, 400, 200, 1.0, 1.0, 1.0)
+    det = Detector(wl.det.nu, wl.det.nv, 0.5)
+    return Workload("paper-1mm-400x400x200-100k-660views", grid, det, wl.ref, wl.mbc, wl.views, wl.coeff, wl.kappa,
+                    None, gt=wl.gt)
+
+
 def fd_subproblem(seed: int = 3000) -> Workload:
     """Gradient-check sub-problem: 16^3 at 4 mm, 200 reference Gaussians, three
     MBC levels of 4 / 8 / 16 Gaussians, 4 views, 32x32 detector at 3.2 mm,

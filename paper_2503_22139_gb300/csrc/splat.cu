@@ -36,6 +36,7 @@
 #include <math.h>
 
 #include "pmf_common.cuh"
+#include "scan.cuh"
 
 namespace pmf {
 namespace {
@@ -80,7 +81,6 @@ struct RasterWs {
 
 constexpr int kPrepThreads = 256;
 constexpr int kMaxTiles = 12288;  // shared-memory histogram of a view's tiles (48 KB)
-constexpr int kScanItems = 4096;  // 256 threads x 16 per scan block
 
 // Gaussians per (view, chunk) CTA of the prep and fill: about 8 CTAs per SM in
 // total, at least one per thread, at most 8,192.
@@ -303,81 +303,6 @@ __global__ void __launch_bounds__(kPrepThreads) k_splat_prep(pmf_gaussians G, in
     if ((threadIdx.x & 31) == 0 && mbits) atomicMax(w.maxbits + p, mbits);
     __syncthreads();
     for (int t = threadIdx.x; t < T; t += kPrepThreads) w.chist[((int64_t)p * T + t) * w.C + c] = hist[t];
-}
-
-// Exclusive prefix sums of chist into coff (64-bit running sums, stored
-// clamped to 32 bits) in three passes: block totals, a one-CTA scan of the
-// totals (which also writes the grand total), and the per-block scans.
-__global__ void k_scan_reduce(const unsigned* __restrict__ x, int64_t N, unsigned long long* bsum) {
-    __shared__ unsigned long long part[8];
-    const int64_t b0 = (int64_t)blockIdx.x * kScanItems + threadIdx.x * 16;
-    unsigned long long s = 0;
-    for (int k = 0; k < 16; k++)
-        if (b0 + k < N) s += x[b0 + k];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int i = 0; i < 8; i++) t += part[i];
-        bsum[blockIdx.x] = t;
-    }
-}
-
-__global__ void k_scan_top(unsigned long long* bsum, int nb, int64_t N, unsigned* coff,
-                           unsigned long long* total) {
-    __shared__ unsigned long long part[1024];
-    const int tid = threadIdx.x;
-    const int per = (nb + 1023) / 1024;
-    const int b = tid * per, e = b + per < nb ? b + per : nb;
-    unsigned long long s = 0;
-    for (int i = b; i < e; i++) s += bsum[i];
-    part[tid] = s;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long run = 0;
-        for (int i = 0; i < 1024; i++) {
-            const unsigned long long v = part[i];
-            part[i] = run;
-            run += v;
-        }
-        *total = run;
-        coff[N] = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
-    }
-    __syncthreads();
-    unsigned long long run = part[tid];
-    for (int i = b; i < e; i++) {
-        const unsigned long long v = bsum[i];
-        bsum[i] = run;
-        run += v;
-    }
-}
-
-__global__ void k_scan_apply(const unsigned* __restrict__ x, int64_t N, const unsigned long long* bsum, unsigned* coff) {
-    __shared__ unsigned long long part[256];
-    const int64_t b0 = (int64_t)blockIdx.x * kScanItems + threadIdx.x * 16;
-    unsigned v[16];
-    unsigned long long s = 0;
-    for (int k = 0; k < 16; k++) {
-        v[k] = b0 + k < N ? x[b0 + k] : 0u;
-        s += v[k];
-    }
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long run = bsum[blockIdx.x];
-        for (int i = 0; i < 256; i++) {
-            const unsigned long long t = part[i];
-            part[i] = run;
-            run += t;
-        }
-    }
-    __syncthreads();
-    unsigned long long run = part[threadIdx.x];
-    for (int k = 0; k < 16; k++) {
-        if (b0 + k < N) coff[b0 + k] = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
-        run += v[k];
-    }
 }
 
 // One CTA per (Gaussian chunk, view): every (Gaussian, tile) entry of the chunk
@@ -656,11 +581,7 @@ pmf_status raster_prep(const pmf_detector* det, int32_t P, const pmf_view* views
         k_splat_prep<<<dim3((unsigned)w.C, (unsigned)P), kPrepThreads, count_tiles ? sizeof(unsigned) * T : 0, s>>>(
             *g, P, det->nu, det->nv, ntu, T, w, count_tiles);
     if (count_tiles) {
-        const int64_t N = (int64_t)P * T * w.C;
-        const int nb = (int)((N + kScanItems - 1) / kScanItems);
-        if (nb > 0) k_scan_reduce<<<nb, 256, 0, s>>>(w.chist, N, w.bsum);
-        k_scan_top<<<1, 1024, 0, s>>>(w.bsum, nb, N, w.coff, w.total);
-        if (nb > 0) k_scan_apply<<<nb, 256, 0, s>>>(w.chist, N, w.bsum, w.coff);
+        scan_counts(w.chist, (int64_t)P * T * w.C, w.bsum, w.coff, w.total, s);
     }
     return check_launch("gs_rasterize prep");
 }

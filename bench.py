@@ -578,6 +578,17 @@ def run_native(a):
                 lambda k: s1.run(batch(k)[0][:vb], batch(k)[2][:vb], centres[k % n_orig]), a.steps, views=vb), 3)
             del s1
         torch.cuda.empty_cache()
+        # the two resolution levels of Stages 2 and 3 (Sec. 2.3.2): Stage 2 on the
+        # half-resolution grid (100x100x50 at 4 mm, 2 mm march step) with batches
+        # of 32, Stage 3 on the full grid with batches of 8
+        g2 = (wl.grid.nx // 2, wl.grid.ny // 2, wl.grid.nz // 2, 2 * wl.grid.vx, 2 * wl.grid.vy, 2 * wl.grid.vz)
+        d2 = (wl.det.nu, wl.det.nv, 2 * wl.det.step_mm)
+        for name, gg, dd, vb in (("stage2_halfres_B32", g2, d2, B), ("stage3_fullres_B8", wl.grid, wl.det, 8)):
+            st = ForwardAdjoint(gg, dd, ref, mbc, batch=vb, dtype=dt, kind=a.kind, w_dtype=wdt)
+            variants[f"{name}_{a.dtype}"] = round(timed_steps(
+                lambda k: st.run(batch(k)[0][:vb], batch(k)[1][:vb], batch(k)[2][:vb]), a.steps, views=vb), 3)
+            del st
+        torch.cuda.empty_cache()
         # 1 mm voxels (400x400x200, the same Gaussian sets; Sec. 4's batch-8 case):
         # throughput of the batch-8 step and its peak device memory
         w1 = synth.paper_workload_1mm(p=wl.p)

@@ -386,6 +386,32 @@ pmf_status pmf_adam_step(int64_t n, float* param, const float* grad, float* m, f
  * shifted means are gradients with respect to the means.  out may equal mean. */
 pmf_status pmf_shift_means(int64_t n, const float* mean, const float* offset, float* out, pmf_stream stream);
 
+/* ------------------------------------------ adaptive density control */
+
+/* acc[i] += |d_mean[i]| (Euclidean norm of the mean's gradient), the
+ * densification statistic of Sec. 2.3.2 accumulated between controls.
+ * d_mean [n][3], acc [n]: device fp32. */
+pmf_status gs_grad_norm_accumulate(int64_t n, const float* d_mean, float* acc, pmf_stream stream);
+
+/* Adaptive density control of Sec. 2.3.2 on one Gaussian set (any channel
+ * count).  With stat_i = grad_acc[i] * grad_scale (grad_scale = 1 / steps):
+ *   every channel of value_i below value_threshold in magnitude -> removed;
+ *   else stat_i > grad_threshold and max(scale_i) <= scale_threshold -> cloned:
+ *     two copies, each with value_i / 2;
+ *   else stat_i > grad_threshold -> split: two Gaussians with means
+ *     mean_i + R_i diag(scale_i) z_{i,k} (z = noise[i][k][0..2], standard normal
+ *     samples the caller draws), scales scale_i / split_factor, the same
+ *     quaternion and value_i / 2;
+ *   else kept unchanged.
+ * Outputs (device, capacity out_capacity >= 2 n) hold the controlled set in input
+ * order, a densified Gaussian's two results in its place; *d_count (device int64)
+ * receives the new count.  Deterministic.  Workspace: gs_density_control_workspace. */
+pmf_status gs_density_control_workspace(int64_t n, size_t* bytes);
+pmf_status gs_density_control(const pmf_gaussians* in, const float* grad_acc, float grad_scale, const float* noise,
+                              float grad_threshold, float scale_threshold, float value_threshold, float split_factor,
+                              float* out_mean, float* out_scale, float* out_quat, float* out_value,
+                              int64_t out_capacity, int64_t* d_count, void* ws, size_t ws_bytes, pmf_stream stream);
+
 /* ------------------------------------------------------------ host helpers */
 
 /* The circular scan of Sec. 2.3.3 / Table I as pmf_view records: view p has

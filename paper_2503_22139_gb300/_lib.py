@@ -89,6 +89,10 @@ SIGNATURES = {
     "gs_voxelize": [_G, ct.POINTER(PmfGaussians), ct.c_int, _P, _P, ct.c_size_t, _P],
     "gs_voxelize_backward_workspace": [_G, _I64, _I32, _SZ],
     "pmf_shift_means": [_I64, _P, _P, _P, _P],
+    "gs_grad_norm_accumulate": [_I64, _P, _P, _P],
+    "gs_density_control_workspace": [_I64, _SZ],
+    "gs_density_control": [ct.POINTER(PmfGaussians), _P, ct.c_float, _P, ct.c_float, ct.c_float, ct.c_float,
+                           ct.c_float, _P, _P, _P, _P, _I64, _P, _P, ct.c_size_t, _P],
     "gs_rasterize_workspace": [ct.POINTER(PmfDetector), _I32, _I64, _I64, _SZ],
     "gs_rasterize_count": [ct.POINTER(PmfDetector), _I32, _P, ct.POINTER(PmfGaussians), _P, _P, ct.c_size_t, _P],
     "gs_rasterize": [ct.POINTER(PmfDetector), _I32, _P, ct.POINTER(PmfGaussians), _P, _P, ct.c_size_t, _P],

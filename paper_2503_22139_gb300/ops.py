@@ -153,6 +153,39 @@ def gs_voxelize_backward(grid, gs: Gaussians, d_out: torch.Tensor, grads=None, a
     return grads
 
 
+# -------------------------------------------- adaptive density control
+
+def gs_grad_norm_accumulate(d_mean: torch.Tensor, acc: torch.Tensor) -> torch.Tensor:
+    """acc += |d_mean| per Gaussian (in place); returns acc."""
+    d_mean = _need(d_mean, "d_mean", torch.float32)
+    acc = _need(acc, "acc", torch.float32)
+    check(_lib.load().gs_grad_norm_accumulate(int(d_mean.shape[0]), _p(d_mean), _p(acc), _stream()),
+          "gs_grad_norm_accumulate")
+    return acc
+
+
+def gs_density_control(gs: Gaussians, grad_acc: torch.Tensor, steps: int, noise: torch.Tensor, grad_threshold: float,
+                       scale_threshold: float, value_threshold: float, split_factor: float = 1.6) -> Gaussians:
+    """Sec. 2.3.2's adaptive density control: returns the new set (synchronizes
+    to read its size); noise: device float32 [n, 2, 3] standard normals."""
+    L = _lib.load()
+    grad_acc = _need(grad_acc, "grad_acc", torch.float32)
+    noise = _need(noise, "noise", torch.float32)
+    dev, n, C = gs.mean.device, gs.n, gs.channels
+    cap = max(2 * n, 1)
+    om, osc = torch.empty((cap, 3), device=dev), torch.empty((cap, 3), device=dev)
+    oq, ov = torch.empty((cap, 4), device=dev), torch.empty((cap, C), device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = _ws(_size(L.gs_density_control_workspace, n), dev)
+    s = gs.c_struct()
+    check(L.gs_density_control(ct.byref(s), _p(grad_acc), float(1.0 / max(int(steps), 1)), _p(noise),
+                               float(grad_threshold), float(scale_threshold), float(value_threshold),
+                               float(split_factor), _p(om), _p(osc), _p(oq), _p(ov), cap, _p(cnt), _p(ws), ws.numel(),
+                               _stream()), "gs_density_control")
+    m = int(cnt.item())
+    return Gaussians(om[:m].contiguous(), osc[:m].contiguous(), oq[:m].contiguous(), ov[:m].contiguous(), gs.kappa)
+
+
 # ------------------------------------- Stage-1 X-ray rasterizer (Eq. 8-9)
 
 def pmf_shift_means(mean: torch.Tensor, offset: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -45,6 +45,7 @@ class ForwardAdjoint:
         projector stages fp32 volumes with bulk tensor copies)."""
         if w_dtype not in (dtype, torch.float32):
             raise ValueError("w_dtype must be dtype or torch.float32")
+        det = ops._det(det)  # (nu, nv, step) tuples or detector records
         self.grid, self.det, self.ref, self.mbc = grid, det, ref, list(mbc)
         self.B, self.dtype, self.w_dtype = int(batch), dtype, w_dtype
         self.eq14 = None
@@ -298,3 +299,94 @@ class Stage1Step:
         ops.gs_voxelize_backward(self.crop, self.crop_gs, self.dVc, grads=self.grads, accumulate=True,
                                  ws=self.cvb_ws)
         return loss, self.tv
+
+
+# Adaptive density control defaults (Sec. 2.3.2 gives the rule, not the
+# numbers): densify the Gaussians whose mean |dL/dmean| since the last control
+# is in the top `densify_fraction` of their set; clone those no larger than
+# `clone_scale_mm` on their largest axis, split the others (scales / 1.6); remove
+# Gaussians whose every value component is below `prune_value`.
+CONTROL_DEFAULTS = dict(every=50, densify_fraction=0.02, clone_scale_mm=4.0, prune_value=0.005, split_factor=1.6,
+                        seed=2025)
+
+
+class TwoResolutionSchedule:
+    """Stages 2 and 3 of Sec. 2.3.2 as one optimisation loop over fixed
+    per-projection motion coefficients: Stage 2 voxelizes on a grid of half the
+    resolution (voxel size doubled, the same extent) with batches of 32
+    projections, Stage 3 on the full grid with batches of 8; every step is the
+    forward + adjoint of `ForwardAdjoint` followed by an Adam update of every
+    Gaussian parameter (reference and MBC sets), and every `control["every"]`
+    steps the sets pass through adaptive density control (their Adam moments
+    restart, the statistic is the mean |dL/dmean| since the last control).
+    Batches are consecutive slices of a fixed permutation of the scan."""
+
+    def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], views: torch.Tensor, coeff: torch.Tensor,
+                 meas: torch.Tensor, steps=(1000, 1000), batches=(32, 8), kind=1, dtype=torch.bfloat16,
+                 lrs=(0.02, 0.005, 0.002, 0.002, 0.01), control: Optional[dict] = None, eq14: Optional[dict] = None):
+        g = ops._grid(grid)
+        self.grids = ((g.nx // 2, g.ny // 2, g.nz // 2, 2 * g.vx, 2 * g.vy, 2 * g.vz),
+                      (g.nx, g.ny, g.nz, g.vx, g.vy, g.vz))
+        d = ops._det(det)
+        # the march step follows the voxel size (0.5 voxel, Sec. 2.3.3's reading)
+        self.dets = (ops.PmfDetector(d.nu, d.nv, 2.0 * d.step_mm), ops.PmfDetector(d.nu, d.nv, d.step_mm))
+        self.sets = [ref] + list(mbc)
+        self.views, self.coeff, self.meas = views, coeff, meas
+        self.steps, self.batches = tuple(int(s) for s in steps), tuple(int(b) for b in batches)
+        self.kind, self.dtype, self.lrs, self.eq14 = kind, dtype, lrs, eq14
+        self.control = dict(CONTROL_DEFAULTS)
+        self.control.update(control or {})
+        self.gen = torch.Generator(device=ref.mean.device)
+        self.gen.manual_seed(int(self.control["seed"]))
+        self.history = []  # (stage, step, loss) per step, device scalars
+        self.counts = []   # set sizes after every control
+
+    def _build(self, stage):
+        B = self.batches[stage]
+        self.step = ForwardAdjoint(self.grids[stage], self.dets[stage], self.sets[0], self.sets[1:], batch=B,
+                                   dtype=self.dtype, kind="eq14" if self.eq14 is not None else self.kind,
+                                   eq14=self.eq14)
+        params, lrs = [], []
+        for gs in self.sets:
+            params += [gs.mean, gs.scale, gs.quat, gs.value]
+            lrs += list(self.lrs[:3]) + [self.lrs[3] if gs.channels == 1 else self.lrs[4]]
+        self.opt = ops.Adam(params, lr=lrs)
+        self.acc = [torch.zeros(gs.n, dtype=torch.float32, device=gs.mean.device) for gs in self.sets]
+        self.since = 0
+
+    def _grads(self):
+        return [self.step.g_ref] + list(self.step.g_mbc)
+
+    def _control(self, stage):
+        c = self.control
+        new = []
+        for gs, acc in zip(self.sets, self.acc):
+            # the densification threshold: the (1 - fraction) quantile of the statistic (host-side choice)
+            stat = acc / max(self.since, 1)
+            thr = float(torch.quantile(stat.float(), 1.0 - float(c["densify_fraction"])).item()) if gs.n > 1 else 0.0
+            noise = torch.randn((gs.n, 2, 3), generator=self.gen, device=gs.mean.device)
+            new.append(ops.gs_density_control(gs, acc, self.since, noise, thr, float(c["clone_scale_mm"]),
+                                              float(c["prune_value"]), float(c["split_factor"])))
+        self.sets = new
+        self.counts.append(tuple(gs.n for gs in self.sets))
+        self._build(stage)
+
+    def run(self):
+        """Runs both stages; returns the list of (stage, step, loss) with losses as floats."""
+        P = int(self.views.shape[0])
+        for stage in (0, 1):
+            self._build(stage)
+            B = self.batches[stage]
+            nb = max(P // B, 1)
+            for k in range(self.steps[stage]):
+                s = (k % nb) * B
+                loss = self.step.run(self.views[s:s + B], self.coeff[s:s + B], self.meas[s:s + B])
+                self.history.append((stage, k, loss.clone()))
+                for gl, acc in zip(self._grads(), self.acc):
+                    ops.gs_grad_norm_accumulate(gl[0], acc)
+                self.since += 1
+                self.opt.step([g for gl in self._grads() for g in gl])
+                last = k == self.steps[stage] - 1
+                if int(self.control["every"]) > 0 and self.since >= int(self.control["every"]) and not last:
+                    self._control(stage)
+        return [(st, k, float(l.item())) for st, k, l in self.history]

@@ -124,3 +124,18 @@ def test_rasterizer_workspace_and_host_validation():
     assert _status("gs_rasterize", ct.byref(bad), 1, fake, ct.byref(gs), fake, fake, 1 << 30, None) == -1
     assert _status("gs_rasterize_backward", ct.byref(d), 1, fake, ct.byref(gs), fake, None, fake, fake, fake, 0,
                    fake, 1 << 30, None) == -1
+
+
+def test_density_control_host_validation():
+    fake = ct.c_void_p(256)
+    gs = _lib.PmfGaussians(10, 1, 3.0, 16, 16, 16, 16)
+    n = ct.c_size_t(0)
+    assert _status("gs_density_control_workspace", 1000, ct.byref(n)) == 0 and n.value >= 1000 * 9
+    # output capacity below 2 n
+    assert _status("gs_density_control", ct.byref(gs), fake, 1.0, fake, 0.1, 1.0, 0.01, 1.6, fake, fake, fake, fake,
+                   19, fake, fake, 1 << 20, None) == -1
+    assert b"out_capacity" in _lib.load().pmf_last_error()
+    assert _status("gs_density_control", ct.byref(gs), fake, 1.0, fake, 0.1, 1.0, 0.01, 0.0, fake, fake, fake, fake,
+                   20, fake, fake, 1 << 20, None) == -1
+    assert _status("gs_density_control", ct.byref(gs), None, 1.0, fake, 0.1, 1.0, 0.01, 1.6, fake, fake, fake, fake,
+                   20, fake, fake, 1 << 20, None) == -1

@@ -293,11 +293,14 @@ def run_native(a):
         f = orig[name]
 
         def w(*args, **kw):
+            # on the stream the call is launched on (the step runs the Gaussian
+            # sets' voxelizer calls on side streams, so those stages overlap)
+            cur = torch.cuda.current_stream()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            e0.record(cur)
             r = f(*args, **kw)
-            e1.record(stream)
+            e1.record(cur)
             ev[name].append((e0, e1))
             return r
         return w

@@ -37,7 +37,7 @@ EQ14_DEFAULTS = dict(lambda_ssim=0.25, lambda_mbc=1.0, lambda_tv=0.05, tv_size=3
 class ForwardAdjoint:
     def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
                  dtype: torch.dtype = torch.float32, kind=2, pair_headroom: float = 1.25,
-                 eq14: Optional[dict] = None, w_dtype: torch.dtype = torch.float32):
+                 eq14: Optional[dict] = None, w_dtype: torch.dtype = torch.float32, concurrent_sets: bool = True):
         """kind 1 / 2: L1 / L2 projection loss (Eq. 10/12, Eq. 1); kind "eq14":
         the full objective of Eq. 14 with `eq14` overriding EQ14_DEFAULTS
         (data_range, the D-SSIM dynamic range, is required).  V and E are
@@ -46,6 +46,7 @@ class ForwardAdjoint:
         if w_dtype not in (dtype, torch.float32):
             raise ValueError("w_dtype must be dtype or torch.float32")
         det = ops._det(det)  # (nu, nv, step) tuples or detector records
+        self.concurrent_sets, self._side = bool(concurrent_sets), None
         self.grid, self.det, self.ref, self.mbc = grid, det, ref, list(mbc)
         self.B, self.dtype, self.w_dtype = int(batch), dtype, w_dtype
         self.eq14 = None
@@ -111,9 +112,19 @@ class ForwardAdjoint:
         (x, y, z) for this step.  Returns the loss (device [1]); gradients land
         in g_ref, g_mbc, g_wc."""
         g, det = self.grid, self.det
-        ops.gs_voxelize(g, self.ref, out=self.V, ws=self.vox_ws[0])
+        main = torch.cuda.current_stream()
+        side = self._side_streams()
+        # the Gaussian sets are independent: each MBC level voxelizes on its own
+        # stream while the reference set voxelizes on the caller's (their
+        # workspaces are separate), joined before the warp
+        for st in side:
+            st.wait_stream(main)
         for l, m in enumerate(self.mbc):
-            ops.gs_voxelize(g, m, out=self.E[l], ws=self.vox_ws[1 + l])
+            with torch.cuda.stream(side[l] if side else main):
+                ops.gs_voxelize(g, m, out=self.E[l], ws=self.vox_ws[1 + l])
+        ops.gs_voxelize(g, self.ref, out=self.V, ws=self.vox_ws[0])
+        for st in side:
+            main.wait_stream(st)
         ops.warp_combine(g, self.V[0], self.E, coeff, out=self.W)
         ops.conebeam_project(g, det, views, self.W, shared=False, out=self.Y)
         loss, dY = ops.projection_loss(self.kind, self.Y, meas, ws=self.loss_ws)
@@ -130,11 +141,25 @@ class ForwardAdjoint:
                         d_vol=self.g_wc[0], accumulate=True, ws=self.tv_ws)
             ops.mbc_normality(g, self.E, weight=q["lambda_mbc"], loss=loss, d_mbc=self.g_wc[1], accumulate=True,
                               ws=self.norm_ws)
+        # the voxelizer adjoints of the sets are latency-bound at low occupancy:
+        # run them side by side, as in the forward
+        for st in side:
+            st.wait_stream(main)
+        for l, m in enumerate(self.mbc):
+            with torch.cuda.stream(side[l] if side else main):
+                ops.gs_voxelize_backward(g, m, self.g_wc[1][l], grads=self.g_mbc[l], ws=self.vb_ws[1 + l])
         ops.gs_voxelize_backward(g, self.ref, self.g_wc[0].reshape((1,) + self.g_wc[0].shape), grads=self.g_ref,
                                  ws=self.vb_ws[0])
-        for l, m in enumerate(self.mbc):
-            ops.gs_voxelize_backward(g, m, self.g_wc[1][l], grads=self.g_mbc[l], ws=self.vb_ws[1 + l])
+        for st in side:
+            main.wait_stream(st)
         return loss
+
+    def _side_streams(self):
+        if not self.concurrent_sets:
+            return []
+        if self._side is None:
+            self._side = [torch.cuda.Stream(device=self.ref.mean.device) for _ in self.mbc]
+        return self._side
 
 
 class PlainPerProjection(ForwardAdjoint):

@@ -45,6 +45,9 @@ struct pmf_plan {
     pmf::MarchShape fp, bp;  // launch shapes of the projector and its adjoint
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // the MBC levels' voxelizer calls and adjoints run on their own streams
+    cudaStream_t side[PMF_MAX_LEVELS] = {};
+    cudaEvent_t fork = nullptr, join[PMF_MAX_LEVELS] = {};
 };
 
 namespace pmf {
@@ -186,10 +189,16 @@ pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
     const pmf_batch_desc& d = p->d;
     const pmf_stream ps = (pmf_stream)s;
     const int64_t N = p->N;
-    PMF_TRY(gs_voxelize(&d.grid, &d.ref, d.dtype, p->V, p->vox_ws[0], p->vox_bytes[0], ps));
-    for (int l = 0; l < p->L; l++)
+    // fork: each MBC level voxelizes on its side stream, the reference set here
+    PMF_TRY_CUDA(cudaEventRecord(p->fork, s), "cudaEventRecord");
+    for (int l = 0; l < p->L; l++) {
+        PMF_TRY_CUDA(cudaStreamWaitEvent(p->side[l], p->fork, 0), "cudaStreamWaitEvent");
         PMF_TRY(gs_voxelize(&d.grid, &d.mbc[l], d.dtype, (char*)p->E + (size_t)l * 3 * N * p->elt, p->vox_ws[1 + l],
-                            p->vox_bytes[1 + l], ps));
+                            p->vox_bytes[1 + l], (pmf_stream)p->side[l]));
+        PMF_TRY_CUDA(cudaEventRecord(p->join[l], p->side[l]), "cudaEventRecord");
+    }
+    PMF_TRY(gs_voxelize(&d.grid, &d.ref, d.dtype, p->V, p->vox_ws[0], p->vox_bytes[0], ps));
+    for (int l = 0; l < p->L; l++) PMF_TRY_CUDA(cudaStreamWaitEvent(s, p->join[l], 0), "cudaStreamWaitEvent");
     PMF_TRY(warp_combine_mixed(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, d.w_dtype, p->W, ps));
     PMF_TRY(plan_project(p, s));
     const bool eq14 = d.loss_kind == 3;
@@ -207,11 +216,18 @@ pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
         PMF_TRY(mbc_normality(&d.grid, p->L, d.dtype, p->E, d.lambda_mbc, d.loss, p->dE, 1, p->norm_ws, p->norm_bytes,
                               ps));
     }
+    // the same fork for the voxelizer adjoints, joined before the step ends
+    PMF_TRY_CUDA(cudaEventRecord(p->fork, s), "cudaEventRecord");
+    for (int l = 0; l < p->L; l++) {
+        PMF_TRY_CUDA(cudaStreamWaitEvent(p->side[l], p->fork, 0), "cudaStreamWaitEvent");
+        PMF_TRY(gs_voxelize_backward(&d.grid, &d.mbc[l], p->dE + (size_t)l * 3 * N, d.d_mbc[l][0], d.d_mbc[l][1],
+                                     d.d_mbc[l][2], d.d_mbc[l][3], 0, p->vb_ws[1 + l], p->vb_bytes[1 + l],
+                                     (pmf_stream)p->side[l]));
+        PMF_TRY_CUDA(cudaEventRecord(p->join[l], p->side[l]), "cudaEventRecord");
+    }
     PMF_TRY(gs_voxelize_backward(&d.grid, &d.ref, p->dV, d.d_ref[0], d.d_ref[1], d.d_ref[2], d.d_ref[3], 0,
                                  p->vb_ws[0], p->vb_bytes[0], ps));
-    for (int l = 0; l < p->L; l++)
-        PMF_TRY(gs_voxelize_backward(&d.grid, &d.mbc[l], p->dE + (size_t)l * 3 * N, d.d_mbc[l][0], d.d_mbc[l][1],
-                                     d.d_mbc[l][2], d.d_mbc[l][3], 0, p->vb_ws[1 + l], p->vb_bytes[1 + l], ps));
+    for (int l = 0; l < p->L; l++) PMF_TRY_CUDA(cudaStreamWaitEvent(s, p->join[l], 0), "cudaStreamWaitEvent");
     return PMF_OK;
 }
 
@@ -247,6 +263,8 @@ pmf_status pair_capacities(const pmf_batch_desc& d, int64_t* cap) {
     cudaFree(tmp);
     return st;
 }
+
+void plan_free(pmf_plan* p);
 
 pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     PMF_TRY(check_desc(desc));
@@ -333,6 +351,14 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     p->tv_ws = take();
     p->norm_ws = take();
     if (desc->tune_cache) cache_lookup(desc->tune_cache, tune_key(d), p->fp, p->bp);
+    bool ok = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int l = 0; l < p->L && ok; l++)
+        ok = cudaStreamCreateWithFlags(&p->side[l], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->join[l], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        plan_free(p);
+        return set_error(PMF_ECUDA, "plan streams: %s", cudaGetErrorString(cudaGetLastError()));
+    }
     *out = p;
     return PMF_OK;
 }
@@ -343,6 +369,11 @@ void plan_free(pmf_plan* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->mem) cudaFree(p->mem);
+    for (int l = 0; l < PMF_MAX_LEVELS; l++) {
+        if (p->side[l]) cudaStreamDestroy(p->side[l]);
+        if (p->join[l]) cudaEventDestroy(p->join[l]);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
     delete p;
 }
 

@@ -1,5 +1,7 @@
-// The remaining terms of the Stage 2-3 objective (Eq. 14) and their gradients,
-// for sm_103a:
+// The terms of the Stage 2-3 objective (Eq. 14) and their gradients, for
+// sm_103a:
+//  - the L1 (Eq. 10/12) or L2 (Eq. 1) projection loss, the mean over all
+//    pixels, with its (sub)gradient;
 //  - D-SSIM between rendered and measured projections (Eq. 10/12; SSIM of
 //    Zhou et al. 2004 with the customary 11x11 Gaussian window, sigma 1.5,
 //    zero padding, C1 = (0.01 range)^2, C2 = (0.03 range)^2);
@@ -338,6 +340,45 @@ __global__ void __launch_bounds__(256) k_norm_grad(const T* __restrict__ E, int6
 
 int ssim_tiles(int nu, int nv) { return ((nu + kTU - 1) / kTU) * ((nv + kTV - 1) / kTV); }
 
+// ------------------------------------------ L1 / L2 projection loss (Eq. 10/12, Eq. 1)
+
+constexpr int kLossThreads = 256;
+
+__global__ void __launch_bounds__(kLossThreads) k_loss(int kind, int64_t n, const float* __restrict__ pred,
+                                                       const float* __restrict__ meas, float* d_pred, float* part) {
+    __shared__ float red[kLossThreads / 32];
+    const float invn = 1.0f / (float)n;
+    float s = 0.0f;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const float r = __ldg(pred + t) - __ldg(meas + t);
+        if (kind == 1) {
+            s += fabsf(r);
+            if (d_pred) d_pred[t] = (r > 0.0f ? invn : (r < 0.0f ? -invn : 0.0f));
+        } else {
+            s = fmaf(r, r, s);
+            if (d_pred) d_pred[t] = 2.0f * r * invn;
+        }
+    }
+    const float tot = block_sum<kLossThreads>(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// One CTA: strided partial sums in double, a fixed butterfly per warp and the
+// warps in order, so the order of every addition is fixed.
+__global__ void k_loss_final(const float* part, int nb, int64_t n, float* loss) {
+    __shared__ double red[kLossThreads / 32];
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += (double)part[b];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kLossThreads / 32; i++) s += red[i];
+        *loss = (float)(s / (double)n);
+    }
+}
+
 }  // namespace
 }  // namespace pmf
 
@@ -444,4 +485,27 @@ pmf_status mbc_normality(const pmf_grid* grid, int32_t L, pmf_dtype dtype, const
     return check_launch("mbc_normality");
 }
 
+pmf_status projection_loss_workspace(int64_t count, size_t* bytes) {
+    PMF_REQUIRE(bytes != nullptr && count >= 0, "bad arguments");
+    *bytes = align_up(sizeof(float) * kStreamBlocks);
+    return PMF_OK;
+}
+
+pmf_status projection_loss(int32_t kind, int32_t P, int64_t Q, const float* pred, const float* meas, float* loss,
+                           float* d_pred, void* ws, size_t ws_bytes, pmf_stream stream) {
+    PMF_REQUIRE(kind == 1 || kind == 2, "kind must be 1 (L1) or 2 (L2)");
+    PMF_REQUIRE(P >= 1 && Q >= 1, "P and Q must be positive");
+    PMF_REQUIRE(pred && meas && loss, "null pointer");
+    size_t need;
+    projection_loss_workspace((int64_t)P * Q, &need);
+    pmf_status st = validate_ws(ws, ws_bytes, need);
+    if (st != PMF_OK) return st;
+    const int64_t n = (int64_t)P * Q;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t nb = (n + kLossThreads - 1) / kLossThreads;
+    const int blocks = (int)(nb < kStreamBlocks ? nb : kStreamBlocks);
+    k_loss<<<blocks, kLossThreads, 0, s>>>(kind, n, pred, meas, d_pred, (float*)ws);
+    k_loss_final<<<1, kLossThreads, 0, s>>>((const float*)ws, blocks, n, loss);
+    return check_launch("projection_loss");
+}
 }  // extern "C"

@@ -310,35 +310,6 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched(const __gri
     }
 }
 
-// ------------------------------------------------------------------ loss
-
-constexpr int kLossThreads = 256;
-
-__global__ void __launch_bounds__(kLossThreads) k_loss(int kind, int64_t n, const float* __restrict__ pred,
-                                                       const float* __restrict__ meas, float* d_pred, float* part) {
-    __shared__ float red[kLossThreads / 32];
-    const float invn = 1.0f / (float)n;
-    float s = 0.0f;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const float r = __ldg(pred + t) - __ldg(meas + t);
-        if (kind == 1) {
-            s += fabsf(r);
-            if (d_pred) d_pred[t] = (r > 0.0f ? invn : (r < 0.0f ? -invn : 0.0f));
-        } else {
-            s = fmaf(r, r, s);
-            if (d_pred) d_pred[t] = 2.0f * r * invn;
-        }
-    }
-    const float tot = block_sum<kLossThreads>(s, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-__global__ void k_loss_final(const float* part, int nb, int64_t n, float* loss) {
-    double s = 0.0;  // one thread; fixed order
-    for (int b = 0; b < nb; b++) s += (double)part[b];
-    *loss = (float)(s / (double)n);
-}
-
 // cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -448,27 +419,4 @@ pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pm
     return project_batched_impl(n, items, dtype, MarchShape{}, 0, (cudaStream_t)stream);
 }
 
-pmf_status projection_loss_workspace(int64_t count, size_t* bytes) {
-    PMF_REQUIRE(bytes != nullptr && count >= 0, "bad arguments");
-    *bytes = align_up(sizeof(float) * kStreamBlocks);
-    return PMF_OK;
-}
-
-pmf_status projection_loss(int32_t kind, int32_t P, int64_t Q, const float* pred, const float* meas, float* loss,
-                           float* d_pred, void* ws, size_t ws_bytes, pmf_stream stream) {
-    PMF_REQUIRE(kind == 1 || kind == 2, "kind must be 1 (L1) or 2 (L2)");
-    PMF_REQUIRE(P >= 1 && Q >= 1, "P and Q must be positive");
-    PMF_REQUIRE(pred && meas && loss, "null pointer");
-    size_t need;
-    projection_loss_workspace((int64_t)P * Q, &need);
-    pmf_status st = validate_ws(ws, ws_bytes, need);
-    if (st != PMF_OK) return st;
-    const int64_t n = (int64_t)P * Q;
-    cudaStream_t s = (cudaStream_t)stream;
-    int64_t nb = (n + kLossThreads - 1) / kLossThreads;
-    const int blocks = (int)(nb < kStreamBlocks ? nb : kStreamBlocks);
-    k_loss<<<blocks, kLossThreads, 0, s>>>(kind, n, pred, meas, d_pred, (float*)ws);
-    k_loss_final<<<1, 1, 0, s>>>((const float*)ws, blocks, n, loss);
-    return check_launch("projection_loss");
-}
 }  // extern "C"

@@ -17,8 +17,9 @@
 //                   whose box reaches the block; per-pixel sums are exact
 //                   integers at a per-view scale, so the (unordered) lists
 //                   give bit-reproducible projections
-//   k_splat_bwd_sums   one warp per (view, Gaussian): its pixel box walked in a
-//                      fixed lane order, six pixel sums by a warp butterfly
+//   k_splat_bwd_sums   one warp per (view, Gaussian): each lane walks the runs of
+//                      kappa-ellipse pixels in its rows (the render's own test
+//                      settles the run ends), six sums by a warp butterfly
 //   k_splat_bwd_chain  one thread per Gaussian: the chain rule of every view, in
 //                      view order, back to (mean, scale, quaternion, value); no
 //                      atomics anywhere, so the adjoint is bit-reproducible
@@ -400,13 +401,18 @@ __device__ __forceinline__ float warp_allsum(float v) {
     return v;
 }
 
-// Adjoint, part 1: one warp per (view, Gaussian) walks the Gaussian's pixel
-// box (lanes on consecutive pixels of a row-major walk) and forms, over the
-// pixels inside its kappa-ellipse with
-// e = exp(-q/2), c = dY rho^ e, d = x^ - p^:
+// Adjoint, part 1: one warp per (view, Gaussian); lane l walks rows
+// rt.y + l, rt.y + l + 32, ... of the Gaussian's pixel box.  In each row the
+// pixels inside the kappa-ellipse form one run: its ends come from the row's
+// quadratic and are then settled with the forward's own test (splat_q), so the
+// adjoint visits exactly the pixels the render drew.  Along the run,
+// e = exp(-q/2) is carried by two products per pixel (q grows by k0 (2 da + 1)
+// + 2 k1 db per step: e *= r, r *= exp(-k0)), restarted from exact values every
+// 8 pixels, and the six sums
 //   sum dY e,  sum c (K d)_a,  sum c (K d)_b,  sum c d_a^2,  sum c d_a d_b,  sum c d_b^2
-// reduced by a fixed butterfly; lane 0 writes them to sums[view][Gaussian].
-__global__ void __launch_bounds__(32 * kBwdWarps, 6) k_splat_bwd_sums(int64_t n, int P, int nu, int nv, float kappa,
+// (c = dY rho^ e, d = x^ - p^) accumulate per lane; a fixed butterfly reduces
+// them and lane 0 writes them to sums[view][Gaussian].
+__global__ void __launch_bounds__(32 * kBwdWarps, 4) k_splat_bwd_sums(int64_t n, int P, int nu, int nv, float kappa,
                                                                    RasterWs w, const float* __restrict__ dproj) {
     const int64_t pair = (int64_t)blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
     if (pair >= (int64_t)P * n) return;  // whole warps
@@ -416,25 +422,60 @@ __global__ void __launch_bounds__(32 * kBwdWarps, 6) k_splat_bwd_sums(int64_t n,
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f, s5 = 0.f;
     if (rt.z >= rt.x) {
         const SplatRec rc = w.rec[pair];
-        const float k2lim = kappa * kappa;
-        const int W = rt.z - rt.x + 1, npx = W * (rt.w - rt.y + 1);
+        // the run of a row is {q <= kappa^2}; beyond q = 170, exp(-q/2) < 2e-37
+        // adds nothing to fp32 sums, and starting a run there would underflow
+        // the carried exponential, so longer runs (kappa > 13) stop at 170
+        const float k2lim = fminf(kappa * kappa, 170.0f);
         const float* dp = dproj + (int64_t)p * nu * nv;
-        int i = rt.x + lane % W, j = rt.y + lane / W;
-        for (int k = lane; k < npx; k += 32) {
-            const float da = pixel_x(i, nu) - rc.a, db = pixel_x(j, nv) - rc.b;
-            const float qq = splat_q(rc.k0, rc.k1, rc.k2, da, db);
-            if (qq <= k2lim) {
-                const float e = __expf(-0.5f * qq), gy = __ldg(dp + (int64_t)j * nu + i);
-                const float c = gy * rc.rho * e;
-                s0 = fmaf(gy, e, s0);
-                s1 = fmaf(c, fmaf(rc.k0, da, rc.k1 * db), s1);
-                s2 = fmaf(c, fmaf(rc.k1, da, rc.k2 * db), s2);
-                s3 = fmaf(c * da, da, s3);
-                s4 = fmaf(c * da, db, s4);
-                s5 = fmaf(c * db, db, s5);
+        const float step_r = __expf(-rc.k0);
+        const float x0 = pixel_x(0, nu);
+        for (int j = rt.y + lane; j <= rt.w; j += 32) {
+            const float db = pixel_x(j, nv) - rc.b;
+            // q - kappa^2 = k0 da^2 + 2 (k1 db) da + (k2 db^2 - kappa^2)
+            const float hb = rc.k1 * db, cc = fmaf(rc.k2 * db, db, -k2lim);
+            const float disc = fmaf(hb, hb, -rc.k0 * cc);
+            const float c0 = rc.a - x0;  // p^_a in pixel-index units
+            int i0, i1;
+            if (disc >= 0.0f) {
+                const float sd = sqrtf(disc);
+                i0 = max(rt.x, (int)fmaxf(ceilf(c0 + (-hb - sd) / rc.k0), -1.0e9f));
+                i1 = min(rt.z, (int)fminf(floorf(c0 + (-hb + sd) / rc.k0), 1.0e9f));
+            } else {
+                // no root in fp32: try the pixel nearest the row's minimum
+                i0 = i1 = (int)fminf(fmaxf(rintf(c0 - hb / rc.k0), (float)rt.x), (float)rt.z);
             }
-            i += 32;
-            while (i > rt.z) { i -= W; j++; }
+            // settle the ends with the render's test
+            while (i0 <= i1 && !(splat_q(rc.k0, rc.k1, rc.k2, pixel_x(i0, nu) - rc.a, db) <= k2lim)) i0++;
+            while (i1 >= i0 && !(splat_q(rc.k0, rc.k1, rc.k2, pixel_x(i1, nu) - rc.a, db) <= k2lim)) i1--;
+            while (i0 > rt.x && splat_q(rc.k0, rc.k1, rc.k2, pixel_x(i0 - 1, nu) - rc.a, db) <= k2lim) i0--;
+            while (i1 < rt.z && splat_q(rc.k0, rc.k1, rc.k2, pixel_x(i1 + 1, nu) - rc.a, db) <= k2lim) i1++;
+            if (i0 > i1) continue;
+            const float db2 = db * db, kbd = rc.k2 * db;
+            const float* row = dp + (int64_t)j * nu;
+            // the carried products drift by about k^2/2 ulps after k steps: restart
+            // them from exact values every 8 pixels
+            for (int ib = i0; ib <= i1; ib += 8) {
+                float da = pixel_x(ib, nu) - rc.a;
+                float e = __expf(-0.5f * splat_q(rc.k0, rc.k1, rc.k2, da, db));
+                float r = __expf(-fmaf(rc.k0, da + 0.5f, hb));
+                float ka = fmaf(rc.k0, da, hb), kb = fmaf(rc.k1, da, kbd);
+                const int ie = min(i1, ib + 7);
+                for (int i = ib; i <= ie; i++) {
+                    const float gy = __ldg(row + i);
+                    const float ge = gy * e, c = ge * rc.rho, cd = c * da;
+                    s0 += ge;
+                    s1 = fmaf(c, ka, s1);
+                    s2 = fmaf(c, kb, s2);
+                    s3 = fmaf(cd, da, s3);
+                    s4 = fmaf(cd, db, s4);
+                    s5 = fmaf(c, db2, s5);
+                    e *= r;
+                    r *= step_r;
+                    da += 1.0f;
+                    ka += rc.k0;
+                    kb += rc.k1;
+                }
+            }
         }
     }
     s0 = warp_allsum(s0); s1 = warp_allsum(s1); s2 = warp_allsum(s2);

@@ -506,6 +506,19 @@ __global__ void __launch_bounds__(32 * kBwdWarps, 3) k_vox_bwd(pmf_gaussians G, 
     const int slab = (int)(item - i * S);
     GaussSetup st;
     gauss_setup(G, i, g, G.kappa, st);
+    if (st.lo[0] > st.hi[0] || st.lo[1] > st.hi[1] || st.lo[2] > st.hi[2]) {
+        // no voxel of the grid within the truncation box (a Gaussian outside a
+        // sub-volume): every moment is zero, so is the gradient (warp-uniform)
+        if ((threadIdx.x & 31) != 0) return;
+        if (S > 1) {
+            for (int k = 0; k < C + kMom; k++) part[item * (C + kMom) + k] = 0.0f;
+        } else if (!accumulate) {
+            for (int a = 0; a < 3; a++) d_mean[3 * i + a] = d_scale[3 * i + a] = 0.0f;
+            for (int a = 0; a < 4; a++) d_quat[4 * i + a] = 0.0f;
+            for (int c = 0; c < C; c++) d_value[i * C + c] = 0.0f;
+        }
+        return;
+    }
     Moments<C> m;
     warp_moments<C>(G, i, st, g, dout, slab, S, m);
     float r[C + kMom];

@@ -148,6 +148,25 @@ def traffic_for(kernel: str, workload: str):
     return float(d["dram_bytes_per_launch"])
 
 
+def onchip_for(kernel: str):
+    """The on-chip resource that binds a projector kernel, per sample, from the
+    committed ncu counts (profiles/onchip.json), or None if the kernel's sources
+    changed since they were taken."""
+    path = os.path.join(ROOT, "profiles", "onchip.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel)
+    if not d:
+        return None
+    h = hashlib.sha256()
+    for f in d["sources"]:
+        fp = os.path.join(ROOT, f)
+        if not os.path.exists(fp):
+            return None
+        h.update(open(fp, "rb").read())
+    return d if h.hexdigest()[:16] == d.get("source_sha") else None
+
+
 def build_workload(small: bool):
     import numpy as np
     import synth
@@ -347,6 +366,9 @@ def run_native(a):
     sub = timed_views[np.linspace(0, len(timed_views) - 1, min(64, len(timed_views))).astype(int)]
     samples = float(samples_per_view(wl.grid, wl.det, sub).mean()) * B
     workload_tag = f"{'small' if a.small else 'paper'}-{a.dtype}{'-wf32' if wdt != dt else ''}-B{B}"
+    kernel_of = dict(KERNEL_OF)
+    if wdt == torch.float32:  # fp32 volumes: the box is staged with bulk tensor copies
+        kernel_of["conebeam_project"] = "k_project_tma"
     stage_roof = {}
     for st, ms in stage_ms.items():
         per_launch_ms = ms / max(1, len(ev[st]) // a.steps)
@@ -356,6 +378,12 @@ def run_native(a):
         if alg_b:
             ent.update({"hbm_achieved_gbs": round(alg_b / sec / 1e9, 2), "hbm_frac": round(alg_b / sec / 1e9 / hbm_peak, 5),
                         "algorithmic_bytes": alg_b})
+        oc = onchip_for(kernel_of.get(st, KERNEL_OF.get(st, st))) if st in FLOPS_PER_SAMPLE else None
+        if oc is not None:
+            ach = oc["per_sample"] * samples / sec
+            ent["onchip"] = {"resource": oc["resource"], "achieved_per_s": round(ach, 1),
+                             "peak_per_s": oc["peak_per_s"], "frac": round(ach / oc["peak_per_s"], 4),
+                             "per_sample": oc["per_sample"]}
         if st in FLOPS_PER_SAMPLE:
             fl = samples * FLOPS_PER_SAMPLE[st]
             ent.update({"bound": "alu", "achieved": round(fl / sec / 1e12, 3), "peak": f32_peak, "unit": "TFLOP/s",
@@ -367,14 +395,11 @@ def run_native(a):
         stage_roof[st] = ent
     dom = max(stage_ms, key=stage_ms.get)
     d = stage_roof[dom]
-    kernel_of = dict(KERNEL_OF)
-    if wdt == torch.float32:  # fp32 volumes: the box is staged with bulk tensor copies
-        kernel_of["conebeam_project"] = "k_project_tma"
     roof = {"kernel": kernel_of.get(dom, dom), "stage": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
             "peak": d.get("peak"), "unit": d.get("unit"), "frac": d.get("frac"),
             "peak_source": (f"{fsrc}" if d.get("unit") == "TFLOP/s" else f"{hsrc} hbm_gbs"),
             "traffic": traffic_for(kernel_of.get(dom, dom), workload_tag),
-            "hbm_frac": d.get("hbm_frac"), "avg_launch_ms": d["avg_launch_ms"]}
+            "hbm_frac": d.get("hbm_frac"), "avg_launch_ms": d["avg_launch_ms"], "onchip": d.get("onchip")}
 
     # end to end: pinned host inputs -> device -> step -> gradients back to pinned host
     e2e = None

@@ -455,13 +455,20 @@ __global__ void __launch_bounds__(32 * kBwdWarps, 4) k_splat_bwd_sums(int64_t n,
             // the carried products drift by about k^2/2 ulps after k steps: restart
             // them from exact values every 8 pixels
             for (int ib = i0; ib <= i1; ib += 8) {
+                // the block's dY values are loaded before any is used, so the
+                // (L2-latency) loads of a block overlap
+                const int cnt = min(i1 - ib, 7);
+                float gyb[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) gyb[k] = k <= cnt ? __ldg(row + ib + k) : 0.0f;
                 float da = pixel_x(ib, nu) - rc.a;
                 float e = __expf(-0.5f * splat_q(rc.k0, rc.k1, rc.k2, da, db));
                 float r = __expf(-fmaf(rc.k0, da + 0.5f, hb));
                 float ka = fmaf(rc.k0, da, hb), kb = fmaf(rc.k1, da, kbd);
-                const int ie = min(i1, ib + 7);
-                for (int i = ib; i <= ie; i++) {
-                    const float gy = __ldg(row + i);
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    if (k > cnt) break;
+                    const float gy = gyb[k];
                     const float ge = gy * e, c = ge * rc.rho, cd = c * da;
                     s0 += ge;
                     s1 = fmaf(c, ka, s1);

@@ -363,76 +363,185 @@ __device__ __forceinline__ TileIdx tile_idx(const GridD& g) {
     return t;
 }
 
-__device__ __forceinline__ int round_small_i(float x) { return __float_as_int(x + 12582912.0f) - 0x4b400000; }
+// a * b rounded once to the nearest integer, for |a b| < 2^22: the product is
+// added to 1.5 * 2^23, where the float spacing is 1, by one fused multiply-add.
+__device__ __forceinline__ int round_prod_small(float a, float b) {
+    return __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4b400000;
+}
 
-// The tile's box of ref (the 32x4x4 tile plus a kHalo-voxel halo, zero outside
-// the grid) staged in shared memory: displaced samples that stay inside it
-// read their corners there instead of through L1/L2.
+// The tile's box of ref (the 32x4x4 tile plus a kHalo-voxel halo) staged in
+// shared memory as (x, x+1) pairs: sv2[i] = (ref at box index i, ref one voxel
+// further along x), zero outside the grid.  Displaced samples whose cell lies
+// inside the box read their 8 corners as four aligned 8-byte loads instead of
+// going through L1/L2.  Each warp stages whole box rows: lane l loads x = l
+// and (for l < kBX - 32) x = 32 + l, and the right neighbour comes from the
+// next lane by a shuffle.
 template <typename T>
-__device__ __forceinline__ void stage_halo(const T* __restrict__ ref, const GridD& g, int bx0, int by0, int bz0,
-                                           float* sv) {
-    for (int i = threadIdx.x; i < kBoxN; i += blockDim.x) {
-        const int x = bx0 + i % kBX, y = by0 + (i / kBX) % kBY, z = bz0 + i / (kBX * kBY);
-        const bool in = (unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz;
-        sv[i] = in ? Store<T>::ld(ref, ((int64_t)z * g.ny + y) * g.nx + x) : 0.0f;
+__device__ __forceinline__ void stage_halo_pairs(const T* __restrict__ ref, const GridD& g, int bx0, int by0,
+                                                 int bz0, float2* sv2) {
+    static_assert(kBX > 32 && kBX <= 64, "a box row spans one or two warp widths");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int xa = bx0 + lane, xb = bx0 + 32 + lane;
+    const bool ina = (unsigned)xa < (unsigned)g.nx, inb = lane < kBX - 32 && (unsigned)xb < (unsigned)g.nx;
+    for (int row = warp; row < kBY * kBZ; row += nw) {
+        const int y = by0 + row % kBY, z = bz0 + row / kBY;
+        const bool inr = (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz;
+        const int64_t base = ((int64_t)z * g.ny + y) * g.nx;
+        const float va = inr && ina ? Store<T>::ld(ref, base + xa) : 0.0f;
+        const float vb = inr && inb ? Store<T>::ld(ref, base + xb) : 0.0f;
+        const float va1 = __shfl_down_sync(0xffffffffu, va, 1);
+        const float vb0 = __shfl_sync(0xffffffffu, vb, 0);
+        const float vb1 = __shfl_down_sync(0xffffffffu, vb, 1);
+        float2* r = sv2 + row * kBX;
+        r[lane] = make_float2(va, lane == 31 ? vb0 : va1);
+        if (lane < kBX - 32) r[32 + lane] = make_float2(vb, lane == kBX - 33 ? 0.0f : vb1);
     }
 }
 
-// Corners of cell c from the staged box (box-relative cell (rx, ry, rz)) when
-// the whole cell is inside it, else from global memory; same values either way.
-template <typename T>
-__device__ __forceinline__ void corners8_halo(const float* sv, int rx, int ry, int rz, const T* ref, const GridD& g,
-                                              const Cell& c, float cv[8]) {
-    if ((unsigned)rx < (unsigned)(kBX - 1) && (unsigned)ry < (unsigned)(kBY - 1) && (unsigned)rz < (unsigned)(kBZ - 1)) {
-        const float* q = sv + (rz * kBY + ry) * kBX + rx;
-        cv[0] = q[0]; cv[1] = q[1]; cv[2] = q[kBX]; cv[3] = q[kBX + 1];
-        cv[4] = q[kBX * kBY]; cv[5] = q[kBX * kBY + 1]; cv[6] = q[kBX * kBY + kBX]; cv[7] = q[kBX * kBY + kBX + 1];
-    } else {
-        corners8(ref, g, c.i0, c.j0, c.k0, cv);
-    }
+// The 8 corners of the cell whose lower corner is box cell (rx, ry, rz), from
+// the pair box (the caller has checked that the cell lies inside the box).
+__device__ __forceinline__ void corners8_pairs(const float2* sv2, int rx, int ry, int rz, float cv[8]) {
+    const float2* q = sv2 + (rz * kBY + ry) * kBX + rx;
+    const float2 c00 = q[0], c10 = q[kBX], c01 = q[kBX * kBY], c11 = q[kBX * kBY + kBX];
+    cv[0] = c00.x; cv[1] = c00.y; cv[2] = c10.x; cv[3] = c10.y;
+    cv[4] = c01.x; cv[5] = c01.y; cv[6] = c11.x; cv[7] = c11.y;
+}
+
+__device__ __forceinline__ bool in_box(int rx, int ry, int rz) {
+    return (unsigned)rx < (unsigned)(kBX - 1) && (unsigned)ry < (unsigned)(kBY - 1) && (unsigned)rz < (unsigned)(kBZ - 1);
+}
+
+// Box coordinate r = l + floor(t) of the lower cell corner and the fraction
+// f = t - floor(t) of a displacement t (voxels) for a voxel at box coordinate
+// l, from one round-down add of 1.5 * 2^23 (where the float spacing is 1):
+// exact for |t| < 2^22.  Larger |t|, inf and NaN give an r far outside the box,
+// so a caller that takes r only after testing it against the box never uses
+// an inexact result (it recomputes the cell with split_offset instead).
+__device__ __forceinline__ int box_floor(float t, int l, float& f) {
+    const float tt = __fadd_rd(t, 12582912.0f);
+    f = t - (tt - 12582912.0f);
+    return (int)((unsigned)__float_as_int(tt) - (0x4b400000u - (unsigned)l));
+}
+
+// Coefficient table of a batch as one float4 (x, y, z, 0) per (view, level):
+// a view's L levels are L broadcast 16-byte shared loads.
+__device__ __forceinline__ void stage_coeff4(const float* __restrict__ w, int PL, float4* sw4) {
+    for (int i = threadIdx.x; i < PL; i += blockDim.x) sw4[i] = make_float4(w[3 * i], w[3 * i + 1], w[3 * i + 2], 0.0f);
 }
 
 template <typename T, typename TO, int L>
-__global__ void __launch_bounds__(256) k_wc_fwd_tile(GridD g, int P, const T* __restrict__ ref,
+__global__ void __launch_bounds__(256, 3) k_wc_fwd_tile(GridD g, int P, const T* __restrict__ ref,
                                                      const T* __restrict__ E, const float* __restrict__ w,
                                                      TO* __restrict__ W) {
-    extern __shared__ float smem_f[];
-    const int PL3 = P * L * 3;
-    float* sw = smem_f;                          // [P][L][3]
-    float* sv = smem_f + ((PL3 + 3) & ~3);       // [kBZ][kBY][kBX] staged ref
-    for (int i = threadIdx.x; i < PL3; i += 256) sw[i] = w[i];
+    extern __shared__ float4 smem_f4[];
+    float4* sw4 = smem_f4;                          // [P][L] coefficients
+    float2* sv2 = (float2*)(smem_f4 + P * L);       // [kBZ][kBY][kBX] ref pairs
+    stage_coeff4(w, P * L, sw4);
     const TileIdx t = tile_idx(g);
-    const int bx0 = t.x0 - kHalo, by0 = t.y0 - kHalo, bz0 = t.z0 - kHalo;
-    stage_halo(ref, g, bx0, by0, bz0, sv);
+    stage_halo_pairs(ref, g, t.x0 - kHalo, t.y0 - kHalo, t.z0 - kHalo, sv2);
     __syncthreads();
     if (t.x >= g.nx || t.y >= g.ny) return;
     const int64_t N = g.n;
+    // box coordinates of the thread's voxels (z and z + 2)
+    const int lx = (threadIdx.x & 31) + kHalo, ly = ((threadIdx.x >> 5) & 3) + kHalo, lz = (threadIdx.x >> 7) + kHalo;
+    bool in[2];
+    float e[2][L][3];
+    TO* out[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
-        const int z = t.z[h];
-        if (z >= g.nz) continue;
-        const int64_t v = ((int64_t)z * g.ny + t.y) * g.nx + t.x;
-        float e[L][3];
+        in[h] = t.z[h] < g.nz;
+        const int64_t v = in[h] ? ((int64_t)t.z[h] * g.ny + t.y) * g.nx + t.x : 0;
+        out[h] = W + v;
 #pragma unroll
         for (int l = 0; l < L; l++)
 #pragma unroll
-            for (int a = 0; a < 3; a++) e[l][a] = Store<T>::ld(E, ((int64_t)l * 3 + a) * N + v);
-        for (int p = 0; p < P; p++) {
-            const float* c = sw + p * L * 3;
-            float d[3];
+            for (int a = 0; a < 3; a++) e[h][l][a] = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + a) * N + v) : 0.0f;
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                float acc = 0.f;
-#pragma unroll
-                for (int l = 0; l < L; l++) acc = fmaf(c[l * 3 + a], e[l][a], acc);
-                d[a] = acc;
-            }
-            const Cell cl = make_cell(t.x, t.y, z, d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
-            float cv[8];
-            corners8_halo(sv, cl.i0 - bx0, cl.j0 - by0, cl.k0 - bz0, ref, g, cl, cv);
-            Store<TO>::st(W, (int64_t)p * N + v, trilin8(cv, cl.fx, cl.fy, cl.fz));
+        for (int l = 0; l < L; l++) {  // MBC vectors in voxels: the displacement is then sum_l c e
+            e[h][l][0] *= g.ivx;
+            e[h][l][1] *= g.ivy;
+            e[h][l][2] *= g.ivz;
         }
     }
+    for (int p = 0; p < P; p++) {
+        float4 c[L];
+#pragma unroll
+        for (int l = 0; l < L; l++) c[l] = sw4[p * L + l];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            // a voxel beyond the grid's last z plane (e = 0, no store) runs the
+            // same code, so the loop has no branch on it
+            float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                d0 = fmaf(c[l].x, e[h][l][0], d0);
+                d1 = fmaf(c[l].y, e[h][l][1], d1);
+                d2 = fmaf(c[l].z, e[h][l][2], d2);
+            }
+            const float tx = d0, ty = d1, tz = d2;
+            float fx, fy, fz, cv[8];
+            const int rx = box_floor(tx, lx, fx), ry = box_floor(ty, ly, fy), rz = box_floor(tz, lz + 2 * h, fz);
+            if (in_box(rx, ry, rz)) {
+                corners8_pairs(sv2, rx, ry, rz, cv);
+            } else {
+                int ox, oy, oz;
+                split_offset(tx, ox, fx);
+                split_offset(ty, oy, fy);
+                split_offset(tz, oz, fz);
+                corners8(ref, g, t.x + ox, t.y + oy, t.z[h] + oz, cv);
+            }
+            const float wv = trilin8(cv, fx, fy, fz);
+            if (in[h]) Store<TO>::st(out[h], 0, wv);
+            out[h] += N;
+        }
+    }
+}
+
+// Sums each of K per-lane values over the warp by halving exchange: at each
+// level a lane keeps one half of its values (the lower half when its lane bit
+// for that level is clear) and sends the other half to its partner, so K
+// values take about K + log2(32 / K) shuffles instead of 5 K.  Lanes end with
+// the sum of the value slot that split_slot<K> names for them.
+template <int N, int O>
+struct SplitReduce {
+    static __device__ __forceinline__ void run(float* x, int lane) {
+        constexpr int H = (N + 1) / 2;
+        const bool up = (lane & O) != 0;
+#pragma unroll
+        for (int k = 0; k < H; k++) {
+            const float hi = H + k < N ? x[H + k] : 0.0f;
+            const float r = __shfl_xor_sync(0xffffffffu, up ? x[k] : hi, O);
+            x[k] = (up ? hi : x[k]) + r;
+        }
+        SplitReduce<H, O / 2>::run(x, lane);
+    }
+};
+template <int O>
+struct SplitReduce<1, O> {
+    static __device__ __forceinline__ void run(float* x, int) {
+#pragma unroll
+        for (int o = O; o >= 1; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+    }
+};
+
+// Which of the K slots lane ends with after SplitReduce<K, 16> (-1: a padding
+// slot, or a lane whose partner in the final plain butterfly writes instead).
+template <int K>
+__device__ __forceinline__ int split_slot(int lane) {
+    static_assert(K >= 1 && K <= 32, "one to 32 values per lane");
+    int n = K, real = K, slot = 0, last = 32;
+    for (int o = 16; o >= 1 && n > 1; o >>= 1) {
+        const int h = (n + 1) / 2;
+        if (lane & o) {
+            slot += h;
+            real -= h;
+        } else {
+            real = real < h ? real : h;
+        }
+        n = h;
+        last = o;
+    }
+    return real >= 1 && (lane & (last - 1)) == 0 ? slot : -1;
 }
 
 __device__ __forceinline__ int exp_bits(float bound, int bits) {
@@ -444,26 +553,27 @@ __device__ __forceinline__ int exp_bits(float bound, int bits) {
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __restrict__ ref,
-                                                     const T* __restrict__ E, const float* __restrict__ w,
-                                                     const float* __restrict__ dW, float* d_mbc,
-                                                     unsigned long long* acc, const unsigned* maxbits, float* part,
-                                                     int accumulate) {
-    extern __shared__ float smem[];
-    const int PL3 = P * L * 3;
-    float* sw = smem;                              // [P][L][3]
-    int* box = (int*)(smem + ((PL3 + 3) & ~3));    // [kBZ][kBY][kBX] fixed-point dV
-    float* sv = (float*)(box + kBoxN);             // [kBZ][kBY][kBX] staged ref
-    float* swarp = sv + kBoxN;                     // [8 warps][P][L][3]
+__global__ void __launch_bounds__(256, 2) k_wc_bwd_tile(GridD g, int P, const T* __restrict__ ref,
+                                                        const T* __restrict__ E, const float* __restrict__ w,
+                                                        const float* __restrict__ dW, float* d_mbc,
+                                                        unsigned long long* acc, const unsigned* maxbits, float* part,
+                                                        int accumulate) {
+    constexpr int K = 3 * L;  // coefficient-gradient values of one view
+    extern __shared__ float4 smem_b4[];
+    const int PL = P * L, PK = P * K;
+    float4* sw4 = smem_b4;                         // [P][L] coefficients
+    float2* sv2 = (float2*)(sw4 + PL);             // [kBZ][kBY][kBX] ref pairs
+    int* box = (int*)(sv2 + kBoxN);                // [kBZ][kBY][kBX] fixed-point dV
+    float* swarp = (float*)(box + kBoxN);          // [8 warps][P][L][3]
     __shared__ float red_sum[8];
     __shared__ unsigned red_max;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < PL3; i += 256) sw[i] = w[i];
+    stage_coeff4(w, PL, sw4);
     for (int i = threadIdx.x; i < kBoxN; i += 256) box[i] = 0;
-    for (int i = threadIdx.x; i < 8 * PL3; i += 256) swarp[i] = 0.f;
+    for (int i = threadIdx.x; i < 8 * PK; i += 256) swarp[i] = 0.f;
     if (threadIdx.x == 0) red_max = 0u;
     const TileIdx t = tile_idx(g);
-    stage_halo(ref, g, t.x0 - kHalo, t.y0 - kHalo, t.z0 - kHalo, sv);
+    stage_halo_pairs(ref, g, t.x0 - kHalo, t.y0 - kHalo, t.z0 - kHalo, sv2);
     const int64_t N = g.n;
     bool in[2];
     int64_t v[2];
@@ -498,6 +608,8 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
     const float sb = ldexpf(1.0f, kb), sg = ldexpf(1.0f, kg);
     const int shift = kg - kb;
     const int bx0 = t.x0 - kHalo, by0 = t.y0 - kHalo, bz0 = t.z0 - kHalo;
+    const int lx = lane + kHalo, ly = (warp & 3) + kHalo, lz = (warp >> 2) + kHalo;
+    const int slot = split_slot<K>(lane);
 
     bool halo_exit = false;
     float e[2][L][3], gE[2][L][3];
@@ -510,66 +622,93 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
                 e[h][l][a] = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + a) * N + v[h]) : 0.f;
                 gE[h][l][a] = 0.f;
             }
+    // MBC vectors in voxels (as in the forward); the per-view DVF gradient then
+    // stays in voxel units and the 1 / voxel factors are applied once at the end
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            e[h][l][0] *= g.ivx;
+            e[h][l][1] *= g.ivy;
+            e[h][l][2] *= g.ivz;
+        }
+    // dW of the next view is loaded one view ahead
+    float gw_next[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) gw_next[h] = in[h] && P > 0 ? __ldg(dW + v[h]) : 0.f;
     for (int p = 0; p < P; p++) {
-        const float* c = sw + p * L * 3;
-        float cw[L][3];
-#pragma unroll
-        for (int l = 0; l < L; l++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) cw[l][a] = 0.f;
+        float gwv[2];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            if (!in[h]) continue;
-            const float gw = __ldg(dW + (int64_t)p * N + v[h]);
-            if (gw == 0.f) continue;
-            float d[3];
+            gwv[h] = gw_next[h];
+            gw_next[h] = in[h] && p + 1 < P ? __ldg(dW + (int64_t)(p + 1) * N + v[h]) : 0.f;
+        }
+        float4 c[L];
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                float acc_ = 0.f;
+        for (int l = 0; l < L; l++) c[l] = sw4[p * L + l];
+        float cw[K];
 #pragma unroll
-                for (int l = 0; l < L; l++) acc_ = fmaf(c[l * 3 + a], e[h][l][a], acc_);
-                d[a] = acc_;
+        for (int k = 0; k < K; k++) cw[k] = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const float gw = gwv[h];
+            if (gw == 0.f) continue;  // also every voxel outside the grid
+            float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                d0 = fmaf(c[l].x, e[h][l][0], d0);
+                d1 = fmaf(c[l].y, e[h][l][1], d1);
+                d2 = fmaf(c[l].z, e[h][l][2], d2);
             }
-            const Cell cl = make_cell(t.x, t.y, t.z[h], d[0] * g.ivx, d[1] * g.ivy, d[2] * g.ivz);
-            const int rx = cl.i0 - bx0, ry = cl.j0 - by0, rz = cl.k0 - bz0;
+            const float tx = d0, ty = d1, tz = d2;
+            Cell cl;
+            const int rx = box_floor(tx, lx, cl.fx), ry = box_floor(ty, ly, cl.fy), rz = box_floor(tz, lz + 2 * h, cl.fz);
+            const bool inside = in_box(rx, ry, rz);
             float gx, gy, gz, cv[8];
-            corners8_halo(sv, rx, ry, rz, ref, g, cl, cv);
+            if (inside) {
+                corners8_pairs(sv2, rx, ry, rz, cv);
+            } else {
+                int ox, oy, oz;
+                split_offset(tx, ox, cl.fx);
+                split_offset(ty, oy, cl.fy);
+                split_offset(tz, oz, cl.fz);
+                cl.i0 = t.x + ox; cl.j0 = t.y + oy; cl.k0 = t.z[h] + oz;
+                corners8(ref, g, cl.i0, cl.j0, cl.k0, cv);
+            }
             trilin8_grad(cv, cl, gx, gy, gz);
-            const float gd[3] = {gw * gx * g.ivx, gw * gy * g.ivy, gw * gz * g.ivz};
+            const float gd[3] = {gw * gx, gw * gy, gw * gz};  // dL/d(displacement in voxels)
 #pragma unroll
-            for (int l = 0; l < L; l++)
+            for (int l = 0; l < L; l++) {
+                gE[h][l][0] = fmaf(gd[0], c[l].x, gE[h][l][0]);
+                gE[h][l][1] = fmaf(gd[1], c[l].y, gE[h][l][1]);
+                gE[h][l][2] = fmaf(gd[2], c[l].z, gE[h][l][2]);
 #pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    gE[h][l][a] = fmaf(gd[a], c[l * 3 + a], gE[h][l][a]);
-                    cw[l][a] = fmaf(gd[a], e[h][l][a], cw[l][a]);
-                }
-            // V's adjoint: 8 trilinear corners
-            const float wx[2] = {1.f - cl.fx, cl.fx}, wy[2] = {1.f - cl.fy, cl.fy}, wz[2] = {1.f - cl.fz, cl.fz};
-            if ((unsigned)rx < (unsigned)(kBX - 1) && (unsigned)ry < (unsigned)(kBY - 1) &&
-                (unsigned)rz < (unsigned)(kBZ - 1)) {
+                for (int a = 0; a < 3; a++) cw[l * 3 + a] = fmaf(gd[a], e[h][l][a], cw[l * 3 + a]);
+            }
+            // V's adjoint: the 8 trilinear corners, each weight times gw rounded
+            // once to the CTA's fixed point
+            if (inside) {
                 int* q = box + (rz * kBY + ry) * kBX + rx;
-                const float gsb = gw * sb;
+                const float gz0 = gw * sb * (1.f - cl.fz), gz1 = gw * sb * cl.fz;
+                const float wyz[2][2] = {{gz0 * (1.f - cl.fy), gz0 * cl.fy}, {gz1 * (1.f - cl.fy), gz1 * cl.fy}};
+                const float wx0 = 1.f - cl.fx, wx1 = cl.fx;
 #pragma unroll
                 for (int dz = 0; dz < 2; dz++)
 #pragma unroll
-                    for (int dy = 0; dy < 2; dy++)
-#pragma unroll
-                        for (int dx = 0; dx < 2; dx++)
-                            atomicAdd(q + (dz * kBY + dy) * kBX + dx, round_small_i(gsb * (wx[dx] * wy[dy] * wz[dz])));
+                    for (int dy = 0; dy < 2; dy++) {
+                        int* r = q + (dz * kBY + dy) * kBX;
+                        atomicAdd(r, round_prod_small(wyz[dz][dy], wx0));
+                        atomicAdd(r + 1, round_prod_small(wyz[dz][dy], wx1));
+                    }
             } else {
                 scatter_cell(acc, g, cl, gw, sg);
                 halo_exit = true;
             }
         }
-        // coefficient gradient partials: warp tree, then the warp's own slot
-#pragma unroll
-        for (int l = 0; l < L; l++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                float r = cw[l][a];
-                for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-                if (lane == 0) swarp[warp * PL3 + p * L * 3 + l * 3 + a] += r;
-            }
+        // coefficient gradient partials: halving warp reduction, then the
+        // warp's own slot
+        SplitReduce<K, 16>::run(cw, lane);
+        if (slot >= 0) swarp[warp * PK + p * K + slot] += cw[0];
     }
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -579,13 +718,14 @@ __global__ void __launch_bounds__(256) k_wc_bwd_tile(GridD g, int P, const T* __
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 float* o = d_mbc + ((int64_t)l * 3 + a) * N + v[h];
-                *o = accumulate ? *o + gE[h][l][a] : gE[h][l][a];
+                const float ge = gE[h][l][a] * (a == 0 ? g.ivx : (a == 1 ? g.ivy : g.ivz));
+                *o = accumulate ? *o + ge : ge;
             }
     }
     if (__syncthreads_or(halo_exit) && threadIdx.x == 0) diag_count(PMF_DIAG_WARP_HALO_EXIT);
-    for (int i = threadIdx.x; i < PL3; i += 256) {
+    for (int i = threadIdx.x; i < PK; i += 256) {
         float r = 0.f;
-        for (int wi = 0; wi < 8; wi++) r += swarp[wi * PL3 + i];
+        for (int wi = 0; wi < 8; wi++) r += swarp[wi * PK + i];
         part[(int64_t)i * gridDim.x + blockIdx.x] = r;
     }
     for (int i = threadIdx.x; i < kBoxN; i += 256) {
@@ -745,17 +885,24 @@ pmf_status warp_volume_backward(const pmf_grid* grid, int32_t P, pmf_dtype dtype
 namespace pmf {
 namespace {
 
+template <typename T, typename TO, int LL>
+void launch_wc_fwd(unsigned nt, size_t smem, cudaStream_t s, const GridD& g, int P, const void* ref, const void* mbc,
+                   const float* coeff, void* out) {
+    cudaFuncSetAttribute(k_wc_fwd_tile<T, TO, LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_wc_fwd_tile<T, TO, LL><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out);
+}
+
 template <typename T, typename TO>
 pmf_status launch_warp_combine(const GridD& g, int32_t L, int32_t P, const void* ref, const void* mbc,
                                const float* coeff, void* out, cudaStream_t s) {
     if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
-        const size_t smem = sizeof(float) * (size_t)((((P * L * 3) + 3) & ~3) + kBoxN);
+        const size_t smem = sizeof(float4) * (size_t)(P * L) + sizeof(float2) * (size_t)kBoxN;
         const unsigned nt = (unsigned)num_tiles(g);
         switch (L) {
-            case 1: k_wc_fwd_tile<T, TO, 1><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out); break;
-            case 2: k_wc_fwd_tile<T, TO, 2><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out); break;
-            case 3: k_wc_fwd_tile<T, TO, 3><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out); break;
-            default: k_wc_fwd_tile<T, TO, 4><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out); break;
+            case 1: launch_wc_fwd<T, TO, 1>(nt, smem, s, g, P, ref, mbc, coeff, out); break;
+            case 2: launch_wc_fwd<T, TO, 2>(nt, smem, s, g, P, ref, mbc, coeff, out); break;
+            case 3: launch_wc_fwd<T, TO, 3>(nt, smem, s, g, P, ref, mbc, coeff, out); break;
+            default: launch_wc_fwd<T, TO, 4>(nt, smem, s, g, P, ref, mbc, coeff, out); break;
         }
         return check_launch("warp_combine");
     }
@@ -830,7 +977,8 @@ pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf
         k_absmax<<<stream_blocks(g.n * P), kThreads, 0, s>>>(d_out, g.n * P, maxbits);
         if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
             const int PL3 = P * L * 3;
-            const size_t smem2 = sizeof(float) * (size_t)(((PL3 + 3) & ~3) + 2 * kBoxN + 8 * PL3);
+            const size_t smem2 = sizeof(float4) * (size_t)(P * L) + (sizeof(float2) + sizeof(int)) * (size_t)kBoxN +
+                                 sizeof(float) * (size_t)(8 * PL3);
             const unsigned nt = (unsigned)num_tiles(g);
             PMF_DISPATCH_DTYPE(dtype, T, {
                 switch (L) {

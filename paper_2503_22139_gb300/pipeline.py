@@ -34,6 +34,13 @@ KERNELS = {
 EQ14_DEFAULTS = dict(lambda_ssim=0.25, lambda_mbc=1.0, lambda_tv=0.05, tv_size=32, data_range=None)
 
 
+def vox_bwd_launches(grid, gs) -> int:
+    """Kernels one gs_voxelize_backward call launches: the slab pass, plus the
+    final pass when the set is split into several slabs (exactly when the call
+    needs a workspace)."""
+    return 1 + (ops.gs_voxelize_backward_workspace(grid, gs.n, gs.channels) > 0)
+
+
 class ForwardAdjoint:
     def __init__(self, grid, det, ref: Gaussians, mbc: Sequence[Gaussians], batch: int,
                  dtype: torch.dtype = torch.float32, kind=2, pair_headroom: float = 1.25,
@@ -88,6 +95,7 @@ class ForwardAdjoint:
         self.loss_ws = ops._ws(ops._size(Lb.projection_loss_workspace, self.B * det.nu * det.nv), dev)
         self.vb_ws = [ops._ws(ops.gs_voxelize_backward_workspace(grid, gs.n, gs.channels), dev)
                       for gs in [ref] + self.mbc]
+        self._vox_bwd_launches = sum(vox_bwd_launches(grid, gs) for gs in [ref] + self.mbc)
         if self.eq14 is not None:
             q = self.eq14
             self.ssim_ws = ops._ws(ops._size(Lb.projection_dssim_workspace, self.B, det.nu, det.nv), dev)
@@ -98,7 +106,7 @@ class ForwardAdjoint:
     @property
     def launches_per_step(self) -> int:
         k = KERNELS
-        n = ((1 + self.L) * (k["gs_voxelize"] + k["gs_voxelize_backward"]) + k["warp_combine"]
+        n = ((1 + self.L) * k["gs_voxelize"] + self._vox_bwd_launches + k["warp_combine"]
              + k["conebeam_project"] + k["projection_loss"] + k["conebeam_project_backward"]
              + k["warp_combine_backward"])
         if self.eq14 is not None:
@@ -186,7 +194,7 @@ class PlainPerProjection(ForwardAdjoint):
     def launches_per_step(self) -> int:
         k = KERNELS
         per_view = 1 + 1 + 1 + 3 + 3 + 4  # combine, warp, project, project_bwd, warp_bwd, combine_bwd
-        return (1 + self.L) * (k["gs_voxelize"] + k["gs_voxelize_backward"]) + k["projection_loss"] + self.B * per_view
+        return (1 + self.L) * k["gs_voxelize"] + self._vox_bwd_launches + k["projection_loss"] + self.B * per_view
 
     def run(self, views: torch.Tensor, coeff: torch.Tensor, meas: torch.Tensor):
         g, det = self.grid, self.det
@@ -286,6 +294,7 @@ class Stage1Step:
         tiles = -(-self.D // 8) ** 3
         self.cvox_ws = ops._ws(ops.gs_voxelize_workspace(self.crop, n, n * tiles), dev)
         self.cvb_ws = ops._ws(ops.gs_voxelize_backward_workspace(self.crop, n, 1), dev)
+        self._crop_vox_bwd_launches = 1 + (ops.gs_voxelize_backward_workspace(self.crop, n, 1) > 0)
         Lb = ops._lib.load()
         self.loss_ws = ops._ws(ops._size(Lb.projection_loss_workspace, self.B * d.nu * d.nv), dev)
         self.ssim_ws = ops._ws(ops._size(Lb.projection_dssim_workspace, self.B, d.nu, d.nv), dev)
@@ -303,7 +312,7 @@ class Stage1Step:
     def launches_per_step(self) -> int:
         k = KERNELS
         return (k["gs_rasterize"] + k["projection_loss"] + k["projection_dssim"] + k["gs_rasterize_backward"]
-                + k["pmf_shift_means"] + k["gs_voxelize"] + k["tv_loss"] + k["gs_voxelize_backward"])
+                + k["pmf_shift_means"] + k["gs_voxelize"] + k["tv_loss"] + self._crop_vox_bwd_launches)
 
     def run(self, views: torch.Tensor, meas: torch.Tensor, centre: torch.Tensor):
         """views [B,12] f64, meas [B,nv,nu] f32, centre: device f32 [3], the TV

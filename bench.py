@@ -78,6 +78,7 @@ class ClockSampler:
         self.proc = None
         self.path = None
         self.enabled = enabled
+        self.skip = 0
 
     def start(self):
         if not self.enabled:
@@ -87,9 +88,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # the timed region starts only once the sampler is writing (its start-up
+        # takes a few hundred ms); the samples before it are dropped in stop()
+        t_end = time.time() + 3.0
+        while time.time() < t_end and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+        self.skip = sum(1 for _ in open(self.path))
 
     def stop(self):
         if self.proc is None:
@@ -100,7 +108,9 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         rows = []
-        for line in open(self.path):
+        for n, line in enumerate(open(self.path)):
+            if n < self.skip:
+                continue
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue

@@ -172,6 +172,26 @@ def test_combine_and_warp_backward_match_oracle():
     assert rel_l2(host(fdw), dw_ref) <= 1e-4
 
 
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_fused_warp_tile_kernels_every_level_count(L):
+    """The 32x4x4 tile kernels are instantiated per level count (L <= 4); each
+    reduces its 3 L coefficient-gradient values per view across the warp by
+    halving exchange, whose slot layout depends on 3 L.  Forward and adjoint of
+    every instance against the oracle on a ragged grid."""
+    grid = Grid(35, 9, 7, 2.0, 2.0, 2.0)
+    V, E, w = _mbc_and_ref(grid, 90 + L, L=L, P=6)
+    D = oracle.combine(E, w)
+    W = host(pmf.warp_combine(grid, dev(V), dev(E), dev(w)))
+    assert rel_l2(W, oracle.warp(grid, V, D)) <= TOL32
+    dW = np.random.default_rng(95 + L).normal(size=(6,) + grid.shape).astype(np.float32)
+    dV_ref, dD_ref = oracle.warp_backward(grid, V, D, dW)
+    dE_ref, dw_ref = oracle.combine_backward(E, w, dD_ref)
+    dV, dE, dw = pmf.warp_combine_backward(grid, dev(V), dev(E), dev(w), dev(dW))
+    assert rel_l2(host(dV), dV_ref) <= TOL32
+    assert rel_l2(host(dE), dE_ref) <= 1e-4
+    assert rel_l2(host(dw), dw_ref) <= 1e-4
+
+
 def test_fused_warp_displacements_beyond_the_staged_halo():
     """MBC vectors of 12 mm std on 2 mm voxels: many displaced samples leave
     the tile's staged 4-voxel halo (the kernels then read and scatter through

@@ -631,13 +631,18 @@ def run_native(a):
         # splatting (Eq. 8-9), L1 + 0.25 D-SSIM, 0.05 TV of a voxelized 32^3 crop
         # drawn per step; batches of B views and of one view (the paper's Stage-1
         # batch size)
-        from paper_2503_22139_gb300.pipeline import Stage1Step
+        from paper_2503_22139_gb300.pipeline import GraphedStage1, Stage1Step
         centres = [Stage1Step.crop_centre(wl.grid, o.tolist(), 32).cuda() for o in origins.cpu()]
         for vb in (B, 1):
             s1 = Stage1Step(wl.grid, wl.det, ref, batch=vb, data_range=drange)
             variants[f"stage1_rasterizer_B{vb}_views"] = round(timed_steps(
                 lambda k: s1.run(batch(k)[0][:vb], batch(k)[2][:vb], centres[k % n_orig]), a.steps, views=vb), 3)
-            del s1
+            # the same step replayed from a CUDA graph (inputs copied into its
+            # static buffers each step)
+            gs1 = GraphedStage1(s1, batch(0)[0][:vb], batch(0)[2][:vb], centres[0])
+            variants[f"stage1_rasterizer_B{vb}_views_graph"] = round(timed_steps(
+                lambda k: gs1.run(batch(k)[0][:vb], batch(k)[2][:vb], centres[k % n_orig]), a.steps, views=vb), 3)
+            del s1, gs1
         torch.cuda.empty_cache()
         # the two resolution levels of Stages 2 and 3 (Sec. 2.3.2): Stage 2 on the
         # half-resolution grid (100x100x50 at 4 mm, 2 mm march step) with batches

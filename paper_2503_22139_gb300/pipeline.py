@@ -335,6 +335,45 @@ class Stage1Step:
         return loss, self.tv
 
 
+class GraphedStage1:
+    """A Stage1Step captured once into a CUDA graph and replayed.  Stage 1 runs
+    at batch 1 in the paper (5,000 iterations), where the step's two dozen
+    launches are short and the host's launch rate, not the GPU, sets the pace;
+    one graph launch per step removes that.  Each replay reads the views, the
+    measured projections and the crop centre from static device buffers (the
+    rasterizer's list capacity is fixed at the warm-up; tiles whose list would
+    not fit take the rasterizer's scan-all-Gaussians path, same bits)."""
+
+    def __init__(self, step: Stage1Step, views: torch.Tensor, meas: torch.Tensor, centre: torch.Tensor,
+                 warmup: int = 2):
+        self.step = step
+        self.views, self.meas, self.centre = views.clone(), meas.clone(), centre.clone()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                step.run(self.views, self.meas, self.centre)
+        torch.cuda.current_stream().wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.out = step.run(self.views, self.meas, self.centre)
+
+    @property
+    def launches_per_step(self) -> int:
+        return self.step.launches_per_step
+
+    @property
+    def grads(self):
+        return self.step.grads
+
+    def run(self, views: torch.Tensor, meas: torch.Tensor, centre: torch.Tensor):
+        for dst, src in ((self.views, views), (self.meas, meas), (self.centre, centre)):
+            if src.data_ptr() != dst.data_ptr():
+                dst.copy_(src, non_blocking=True)
+        self.graph.replay()
+        return self.out
+
+
 # Adaptive density control defaults (Sec. 2.3.2 gives the rule, not the
 # numbers): densify the Gaussians whose mean |dL/dmean| since the last control
 # is in the top `densify_fraction` of their set; clone those no larger than

@@ -311,6 +311,26 @@ def test_loss_matches_oracle():
         lref, gref = oracle.loss(kind, a, b)
         assert float(loss.item()) == pytest.approx(lref, rel=1e-6)
         assert rel_l2(host(g), gref) <= 1e-6
+        # arrays off the 16-byte grid (the kernel's scalar form)
+        ua, ub = torch.zeros(a.size + 1, device="cuda"), torch.zeros(b.size + 1, device="cuda")
+        ua[1:] = dev(a).reshape(-1)
+        ub[1:] = dev(b).reshape(-1)
+        loss_u, g_u = pmf.projection_loss(kind, ua[1:].reshape(a.shape), ub[1:].reshape(b.shape))
+        assert float(loss_u.item()) == pytest.approx(lref, rel=1e-6)
+        assert rel_l2(host(g_u), gref) <= 1e-6
+
+
+def test_loss_at_the_paper_batch_size():
+    """32 projections of 512x384 (the vectorised form over many grid-stride
+    rounds) against a float64 sum."""
+    rng = np.random.default_rng(6)
+    a = rng.normal(size=(32, 384, 512)).astype(np.float32)
+    b = rng.normal(size=(32, 384, 512)).astype(np.float32)
+    for kind in (1, 2):
+        loss, g = pmf.projection_loss(kind, dev(a), dev(b))
+        lref, gref = oracle.loss(kind, a, b)
+        assert float(loss.item()) == pytest.approx(lref, rel=1e-6)
+        assert rel_l2(host(g), gref) <= 1e-6
 
 
 # ------------------------------------------------------------- the chain

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import paper_2503_22139_gb300 as pmf
-from paper_2503_22139_gb300.pipeline import Stage1Step
+from paper_2503_22139_gb300.pipeline import GraphedStage1, Stage1Step
 from synth import Grid, small_workload
 from tests.gpu_util import dev, gset, host, rel_l2, views
 
@@ -56,3 +56,27 @@ def test_stage1_step_matches_the_oracle_chain():
     for k, name in enumerate(("mean", "scale", "quat", "value")):
         ref = gr[k].reshape(-1) + gv[k].reshape(-1)
         assert rel_l2(host(step.grads[k]).reshape(-1), ref) <= 1e-3, name
+
+
+def test_graphed_stage1_replays_equal_the_eager_steps():
+    """The CUDA-graph replay of the Stage-1 step gives the eager step's losses
+    and gradients bit for bit, with the views, measured projections and crop
+    changing between replays (batch 1, as Stage 1 runs in the paper)."""
+    wl = small_workload(with_measured=True)
+    g = gset(wl.ref, wl.kappa)
+    meas = dev(wl.measured.astype(np.float32))
+    drange = float(wl.measured.max() - wl.measured.min())
+    vw = views(wl.views)
+    corners = [(7, 19, 3), (30, 2, 11), (0, 31, 25)]
+    centres = [Stage1Step.crop_centre(wl.grid, c, 32).cuda() for c in corners]
+    eager = Stage1Step(wl.grid, wl.det, g, batch=1, data_range=drange)
+    graphed = GraphedStage1(Stage1Step(wl.grid, wl.det, g, batch=1, data_range=drange), vw[:1], meas[:1], centres[0])
+    for k in range(len(corners)):
+        p = 3 * k + 1
+        le, te = [t.clone() for t in eager.run(vw[p:p + 1], meas[p:p + 1], centres[k])]
+        ge = [t.clone() for t in eager.grads]
+        lg, tg = graphed.run(vw[p:p + 1], meas[p:p + 1], centres[k])
+        torch.cuda.synchronize()
+        assert torch.equal(le, lg) and torch.equal(te, tg) and torch.isfinite(le).all()
+        for a, b in zip(ge, graphed.grads):
+            assert torch.equal(a, b)

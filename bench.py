@@ -692,6 +692,44 @@ def run_native(a):
         variants["train_loss_first_last"] = [round(float(t.item()), 3) for t in traj]
         del tstep, opt
         torch.cuda.empty_cache()
+        if not a.small:
+            # SURVEY config 3: four volumes of different grids (128^2x64 .. 256^2x128,
+            # each its reference set voxelized in fp32) with 17 / 40 / 64 / 96 views,
+            # projected and back-projected as one persistent launch each way, plain
+            # and replayed from a CUDA graph, against one launch pair per volume
+            items, dys = [], []
+            for u in synth.uneven_volumes():
+                ug = pmf.Gaussians(*(torch.as_tensor(x, device="cuda") for x in
+                                     (u.ref.mean, u.ref.scale, u.ref.quat, u.ref.value)), u.kappa)
+                vol = pmf.gs_voxelize(u.grid, ug)[0]
+                uv = torch.as_tensor(u.views, dtype=torch.float64, device="cuda")
+                items.append((u.grid, u.det, uv, vol, True))
+                dys.append(torch.ones((u.p, u.det.nv, u.det.nu), device="cuda"))
+            nviews = sum(it[2].shape[0] for it in items)
+            ys = [torch.empty((it[2].shape[0], it[1].nv, it[1].nu), device="cuda") for it in items]
+            gs_out = [torch.empty(it[0].shape, device="cuda") for it in items]
+
+            def uneven_batched(k):
+                ops.conebeam_project_batched(items, out=ys)
+                ops.conebeam_project_backward_batched([(it[0], it[1], it[2], dy, True) for it, dy in zip(items, dys)],
+                                                      out=gs_out)
+
+            def uneven_per_volume(k):
+                for it, dy, y, go in zip(items, dys, ys, gs_out):
+                    ops.conebeam_project(it[0], it[1], it[2], it[3], shared=True, out=y)
+                    ops.conebeam_project_backward(it[0], it[1], it[2], dy, shared=True, out=go)
+
+            variants["config3_uneven_batched_f32"] = round(timed_steps(uneven_batched, 5, views=nviews), 3)
+            uneven_batched(0)
+            torch.cuda.synchronize()
+            ug_graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(ug_graph):
+                uneven_batched(0)
+            variants["config3_uneven_batched_graph_f32"] = round(timed_steps(lambda k: ug_graph.replay(), 5,
+                                                                             views=nviews), 3)
+            variants["config3_per_volume_f32"] = round(timed_steps(uneven_per_volume, 5, views=nviews), 3)
+            del items, dys, ys, gs_out, ug_graph
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -430,7 +430,9 @@ pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items
         k_absmax_batched<<<dim3((unsigned)(nb < 1024 ? nb : 1024), (unsigned)n), 256, 0, s>>>(B);
     }
     if (total > 0) {
-        const unsigned nc = persistent_ctas(total, ctas, sh.rays);
+        int ntl[kMaxItems];
+        for (int i = 0; i < n; i++) ntl[i] = B.it[i].ntiles;
+        const unsigned nc = persistent_ctas(total, ctas, sh.rays, ntl, n);
         PMF_DISPATCH_MARCH(sh, CH, RPB, k_backproject_batched<CH, RPB><<<nc, RPB, 0, s>>>(B));
     }
     const int64_t nc = (maxcells + 255) / 256;

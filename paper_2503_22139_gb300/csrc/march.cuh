@@ -395,10 +395,26 @@ int num_sms() {
 }
 
 // Persistent CTAs: `ctas` if given, else as many as are resident at 256
-// threads x 4 per SM (<= 64 registers), i.e. 1024 threads per SM.
-unsigned persistent_ctas(int64_t total, unsigned ctas, int rays) {
-    const int64_t cap = ctas ? (int64_t)ctas : (int64_t)num_sms() * (1024 / rays);
-    return (unsigned)(total < cap ? (total > 0 ? total : 1) : cap);
+// threads x 4 per SM (<= 64 registers), i.e. 1024 threads per SM, lowered to
+// the largest prime that does not divide any item's tile count.  CTA c walks
+// work items c, c + G, c + 2G, ...: with G sharing a factor with the tiles per
+// view (608 and 768 share 32 at the paper detector), every CTA would keep
+// to the same few detector columns, the centre columns' CTAs carrying the
+// long rays while the edge columns' CTAs idle; with G coprime to it each CTA
+// cycles through all columns.
+unsigned persistent_ctas(int64_t total, unsigned ctas, int rays, const int* ntiles, int n) {
+    int64_t cap = ctas ? (int64_t)ctas : (int64_t)num_sms() * (1024 / rays);
+    if (total <= cap) return (unsigned)(total > 0 ? total : 1);
+    auto ok = [&](int64_t g) {
+        for (int64_t d = 2; d * d <= g; d++)
+            if (g % d == 0) return false;
+        for (int i = 0; i < n; i++)
+            if (ntiles[i] % g == 0) return false;
+        return true;
+    };
+    for (int64_t g = cap; g >= 2; g--)
+        if (ok(g)) return (unsigned)g;
+    return (unsigned)cap;
 }
 
 pmf_status fill_item(const pmf_project_item& in, int64_t begin, int rays, ProjItem& it) {

@@ -175,12 +175,16 @@ __device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, 
         : "memory");
 }
 
+// Returns false (after writing NaN to its pixels) when a bulk copy did not
+// complete within the bounded wait; the mbarrier's phase is then unknown and
+// the CTA must not stage again.  `parity` is the barrier phase the CTA's next
+// copy completes, carried across tiles by persistent callers.
 template <int CH, int RPB>
-__device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv, int ntu, float step,
+__device__ __forceinline__ bool project_tile_tma(const GridD& g, int nu, int nv, int ntu, float step,
                                                  const pmf_view* __restrict__ views, const CUtensorMap* map,
                                                  const float* __restrict__ vol, int64_t vol_stride,
                                                  float* __restrict__ proj, int p, int tile, float* box,
-                                                 unsigned long long* bar, BoxState& bs) {
+                                                 unsigned long long* bar, BoxState& bs, unsigned& parity) {
     int a, b;
     pixel_of<RPB>(tile, ntu, a, b);
     const bool in = a < nu && b < nv;
@@ -198,7 +202,6 @@ __device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv,
     const int Mlo = bs.range[0], Mhi = bs.range[1];
     float acc = 0.0f;
     int sel = 0;
-    unsigned parity = 0;
     for (int M0 = Mlo; M0 <= Mhi; M0 += CH, sel ^= 1) {
         int j0, j1, ib[3];
         float fb[3];
@@ -233,7 +236,7 @@ __device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv,
                 if (threadIdx.x == 0) diag_count(PMF_DIAG_TIMEOUT);
                 mbar_wait_bounded(bar, parity ^ 1u);  // the copies still in flight, once more
                 if (in) proj[((int64_t)p * nv + b) * nu + a] = __int_as_float(0x7fc00000);
-                return;
+                return false;
             }
             if (act) {
                 const float syf = (float)kTmaX, szf = (float)S;
@@ -277,6 +280,7 @@ __device__ __forceinline__ void project_tile_tma(const GridD& g, int nu, int nv,
         __syncthreads();
     }
     if (in) proj[((int64_t)p * nv + b) * nu + a] = step * acc;
+    return true;
 }
 
 template <int CH, int RPB>
@@ -293,8 +297,40 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_tma(GridD g, int nu
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    unsigned parity = 0;
     project_tile_tma<CH, RPB>(g, nu, nv, ntu, step, views, &map, vol, vol_stride, proj, blockIdx.y, blockIdx.x, box,
-                              &bar, bs);
+                              &bar, bs, parity);
+}
+
+// The uneven batch of fp32 volumes with bulk-copy staging: one tensor map per
+// item in the launch's parameter block, the mbarrier's phase carried from
+// tile to tile.
+struct ProjBatchTma {
+    ProjBatch B;
+    CUtensorMap map[kMaxItems];
+};
+
+template <int CH, int RPB>
+__global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched_tma(const __grid_constant__ ProjBatchTma T) {
+    __shared__ __align__(128) float box[kTmaBox];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ BoxState bs;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    for (int64_t w = blockIdx.x; w < T.B.total; w += gridDim.x) {
+        const int i = find_item(T.B, w);
+        const ProjItem& it = T.B.it[i];
+        const int64_t local = w - it.begin;
+        if (!project_tile_tma<CH, RPB>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, &T.map[i], (const float*)it.vol,
+                                       it.vol_stride, it.proj, (int)(local / it.ntiles), (int)(local % it.ntiles), box,
+                                       &bar, bs, parity))
+            return;
+        __syncthreads();
+    }
 }
 
 template <typename T, int CH, int RPB>
@@ -383,7 +419,21 @@ pmf_status project_batched_impl(int32_t n, const pmf_project_item* items, pmf_dt
     }
     B.total = total;
     if (total == 0) return PMF_OK;
-    const unsigned nc = persistent_ctas(total, ctas, sh.rays);
+    int ntl[kMaxItems];
+    for (int i = 0; i < n; i++) ntl[i] = B.it[i].ntiles;
+    const unsigned nc = persistent_ctas(total, ctas, sh.rays, ntl, n);
+    if (sh.tma && dtype == PMF_F32) {
+        ProjBatchTma tb{};
+        bool all = true;
+        for (int i = 0; i < n && all; i++)
+            all = items[i].P == 0 || encode_volume_map(&tb.map[i], (const float*)items[i].vol, &items[i].grid,
+                                                       items[i].P, items[i].vol_stride);
+        if (all) {
+            tb.B = B;
+            PMF_DISPATCH_MARCH(sh, CH, RPB, k_project_batched_tma<CH, RPB><<<nc, RPB, 0, s>>>(tb));
+            return check_launch("conebeam_project_batched");
+        }
+    }
     PMF_DISPATCH_MARCH(sh, CH, RPB, PMF_DISPATCH_DTYPE(dtype, T, k_project_batched<T, CH, RPB><<<nc, RPB, 0, s>>>(B)));
     return check_launch("conebeam_project_batched");
 }

@@ -290,9 +290,11 @@ typedef struct {
 } pmf_project_item;
 
 /* conebeam_project for up to 16 volumes of different sizes and view counts in
- * one persistent launch (CTAs walk every item's (view, 16x16 tile) work
- * round-robin).  Every item uses `dtype`.  Results equal per-item
- * conebeam_project calls bit for bit.  Host-side items may be freed on return. */
+ * one launch over the concatenated (item, view, 16x16 tile) work list, one CTA
+ * per work item; fp32 volumes whose rows are 16-byte multiples are staged by
+ * bulk tensor copies (one tensor map per item).  Every item uses `dtype`.
+ * Results equal per-item conebeam_project calls bit for bit.  Host-side items
+ * may be freed on return. */
 pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pmf_dtype dtype, pmf_stream stream);
 
 /* One volume's share of a batched adjoint: d_proj (device fp32 [P][nv][nu])
@@ -309,8 +311,8 @@ typedef struct {
 
 pmf_status conebeam_project_backward_batched_workspace(int32_t n, const pmf_backproject_item* items, size_t* bytes);
 
-/* conebeam_project_backward for up to 16 items in one persistent launch (plus
- * one batched max-reduction and one batched fixed-point conversion); each
+/* conebeam_project_backward for up to 16 items in one launch over the work
+ * list (plus one batched max-reduction and one batched fixed-point conversion); each
  * item keeps its own fixed-point scale, so results equal per-item calls bit
  * for bit. */
 pmf_status conebeam_project_backward_batched(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,

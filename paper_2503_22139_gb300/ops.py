@@ -430,7 +430,7 @@ def conebeam_project_backward(grid, det, views, d_proj, shared: bool = False, ac
 
 
 def conebeam_project_batched(items, out=None):
-    """One persistent launch over several volumes.  items: sequence of
+    """One launch over several volumes.  items: sequence of
     (grid, det, views [P,12] f64, vol, shared) tuples; returns the list of
     projections [P, nv, nu] (fp32), or fills `out` (a list of tensors)."""
     L = _lib.load()

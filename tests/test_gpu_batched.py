@@ -38,6 +38,26 @@ def test_batched_projection_equals_per_volume_launches(dt):
             assert rel_l2(host(yb), oracle.project(g, d.nu, d.nv, d.step_mm, vw, vol, shared=sh)) <= 1e-5
 
 
+def test_batched_projection_mixed_staging_and_empty_items():
+    """fp32 batches take bulk-copy staging only when every item's rows are
+    16-byte multiples: one item with nx = 21 sends the whole batch to plain
+    staging, and an item with no views is skipped; both give the per-volume
+    results bit for bit."""
+    items = _items()
+    rng = np.random.default_rng(92)
+    g = Grid(21, 15, 11, 2.0, 2.0, 2.0)
+    d = Detector(30, 26, 1.0)
+    vw = circular_views(3, 320.0, 470.0, d.nu, d.nv, 1.7, 1.9, start=0.4)
+    items.append((g, d, vw, rng.random((3,) + g.shape).astype(np.float32), False))
+    for batch in (items, items[:2] + [(items[2][0], items[2][1], items[2][2][:0], items[2][3][:0], False)]):
+        got = pmf.ops.conebeam_project_batched([(g_, d_, views(vw_), dev(vol), sh) for g_, d_, vw_, vol, sh in batch])
+        for (g_, d_, vw_, vol, sh), yb in zip(batch, got):
+            if vw_.shape[0] == 0:
+                assert yb.numel() == 0
+                continue
+            assert torch.equal(yb, pmf.conebeam_project(g_, d_, views(vw_), dev(vol), shared=sh))
+
+
 def test_batched_backprojection_equals_per_volume_launches():
     items = _items()
     rng = np.random.default_rng(91)

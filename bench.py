@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--small", action="store_true", help="the 64^3 / 2k-Gaussian / 128^2 case (for profiling)")
     ap.add_argument("--rasterizer", action="store_true",
                     help="time only the Stage-1 rasterizer (gs_rasterize + gs_rasterize_backward) on --batch views")
+    ap.add_argument("--uneven", action="store_true",
+                    help="time only the uneven four-volume batch (SURVEY config 3): one batched launch each way vs "
+                         "one launch pair per volume")
     return ap.parse_args()
 
 
@@ -856,12 +859,63 @@ def run_rasterizer(a):
                                  "views": B, "pairs": cap}}))
 
 
+def run_uneven(a):
+    """The uneven batch alone (for profiling): four volumes of different grids
+    (each its reference set voxelized in fp32) with 17 / 40 / 64 / 96 views of
+    512x384, projected and back-projected (dY = 1) as one batched launch each
+    way, then as one launch pair per volume; event-timed."""
+    import torch
+    import paper_2503_22139_gb300 as pmf
+    from paper_2503_22139_gb300 import ops
+    import synth
+    torch.cuda.set_device(0)
+    items, dys = [], []
+    for u in synth.uneven_volumes():
+        ug = pmf.Gaussians(*(torch.as_tensor(x, device="cuda") for x in
+                             (u.ref.mean, u.ref.scale, u.ref.quat, u.ref.value)), u.kappa)
+        items.append((u.grid, u.det, torch.as_tensor(u.views, dtype=torch.float64, device="cuda"),
+                      pmf.gs_voxelize(u.grid, ug)[0], True))
+        dys.append(torch.ones((u.p, u.det.nv, u.det.nu), device="cuda"))
+    ys = [torch.empty((it[2].shape[0], it[1].nv, it[1].nu), device="cuda") for it in items]
+    gs_out = [torch.empty(it[0].shape, device="cuda") for it in items]
+    bitems = [(it[0], it[1], it[2], dy, True) for it, dy in zip(items, dys)]
+    nviews = sum(it[2].shape[0] for it in items)
+
+    def batched():
+        ops.conebeam_project_batched(items, out=ys)
+        ops.conebeam_project_backward_batched(bitems, out=gs_out)
+
+    def per_volume():
+        for it, dy, y, go in zip(items, dys, ys, gs_out):
+            ops.conebeam_project(it[0], it[1], it[2], it[3], shared=True, out=y)
+            ops.conebeam_project_backward(it[0], it[1], it[2], dy, shared=True, out=go)
+
+    res = {}
+    for name, f in (("batched", batched), ("per_volume", per_volume)):
+        for _ in range(a.warmup):
+            f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = round(nviews * a.steps / (e0.elapsed_time(e1) / 1e3), 3)
+    print(json.dumps({"metric": "projections/s fwd+adjoint, uneven four-volume batch (fp32)", "value": res["batched"],
+                      "unit": "projections/s", "per_volume_launches": res["per_volume"], "steps": a.steps,
+                      "warmup": a.warmup, "config": {"workload": "128x128x64 / 160x160x80 / 200x200x100 / 256x256x128 "
+                                                                 "@2 mm, 17/40/64/96 views of 512x384", "views": nviews}}))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.rasterizer:
         run_rasterizer(a)
+    elif a.uneven:
+        run_uneven(a)
     else:
         run_native(a)
 

@@ -787,10 +787,30 @@ def oracle_sample(wl, meas_np, view_idx, kind=2):
     return time.perf_counter() - t
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo; the machine type elsewhere)."""
+    import platform
+    arm = {}
+    try:
+        for line in open("/proc/cpuinfo"):
+            key, _, val = line.partition(":")
+            key, val = key.strip().lower(), val.strip()
+            if key in ("model name", "cpu model") and val:
+                return val
+            if key in ("cpu implementer", "cpu part") and val:
+                arm.setdefault(key, val)
+    except OSError:
+        pass
+    if arm:  # Arm cores report implementer and part numbers, not a name
+        return f"{platform.machine()} (implementer {arm.get('cpu implementer', '?')}, part {arm.get('cpu part', '?')})"
+    return platform.machine()
+
+
 def cpu_baseline(wl, meas_np, small=False):
     import oracle
     secs = oracle_sample(wl, meas_np, 0)
     return {"value": round(1.0 / secs, 5), "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": f"1 projection fwd+adjoint incl. voxelization of all Gaussians and its adjoint "
                       f"({'small' if small else 'paper-scale'} workload), FP64 C oracle, {secs:.1f} s"}
 
@@ -815,7 +835,7 @@ def run_reference(a):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD if not a.small else "small", "batch_projections": 1},
             "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "kind": "oracle", "cores": oracle.threads(),
-                             "sample": sample},
+                             "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

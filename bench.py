@@ -12,6 +12,8 @@ patient scans.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f32|bf16|f16]
     python bench.py --impl reference ...    # FP64 CPU oracle on host cores
+    python bench.py --rasterizer --batch B  # the Stage-1 rasterizer alone (for profiling)
+    python bench.py --uneven                # the uneven four-volume batch alone (for profiling)
 
 Under torchrun every rank runs independent batches (no data-path collective);
 the timed region is bracketed by barriers and the max over ranks is reported.

@@ -1,12 +1,14 @@
 """Central finite differences pin the oracle's adjoint: each Gaussian-parameter
-gradient of the voxelizer, and every gradient of the whole forward model on the
-16^3 / 200-Gaussian / 4-view sub-problem (kappa = inf)."""
+gradient of the voxelizer (without truncation and at kappa = 3), and every
+gradient of the whole forward model on the 16^3 / 200-Gaussian / 4-view
+sub-problem (kappa = inf)."""
 import copy
 
 import numpy as np
 import pytest
 
 import oracle
+from oracle import brute
 from synth import Grid, fd_subproblem
 from tests import oracle_chain
 
@@ -15,8 +17,27 @@ def _vox_loss(grid, m, s, q, v, G, kappa):
     return float((oracle.voxelize(grid, m, s, q, v, kappa) * G).sum())
 
 
-@pytest.mark.parametrize("kappa", [np.inf])
+def _inside_mask(grid, m, s, q, kappa):
+    """Which (Gaussian, voxel) pairs lie inside the truncation ellipsoid
+    q <= kappa^2, with q from a SciPy rotation and a NumPy matrix inverse."""
+    xs = brute.centres(grid)
+    out = []
+    for g in range(len(m)):
+        R = brute.rotation(q[g])
+        A = np.linalg.inv(R @ np.diag(np.asarray(s[g], float) ** 2) @ R.T)
+        d = xs - m[g]
+        out.append(np.einsum("...i,ij,...j->...", d, A, d) <= kappa * kappa)
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("kappa", [np.inf, 3.0])
 def test_voxelize_backward_matches_central_differences(kappa):
+    """At kappa = 3 the loss is only piecewise smooth: a pair whose q crosses
+    kappa^2 adds or drops a term.  The seed is chosen so that no central
+    difference moves any pair across the cutoff (checked below, independently of
+    the oracle), so the differences see exactly the terms inside the ellipsoids,
+    and the adjoint must drop the same ones -- the pairs outside the ellipsoid
+    but inside its bounding box would otherwise add about 1% to the gradients."""
     grid = Grid(10, 9, 8, 2.0, 2.0, 2.5)
     rng = np.random.default_rng(31)
     Gn = 4
@@ -27,6 +48,9 @@ def test_voxelize_backward_matches_central_differences(kappa):
     G = rng.normal(size=(3,) + grid.shape)
     dm, ds, dq, dv = oracle.voxelize_backward(grid, m, s, q, v, G, kappa)
     h = 1e-5
+    if np.isfinite(kappa):
+        inside = _inside_mask(grid, m, s, q, kappa)
+        assert inside.any() and not inside.all()  # the cutoff removes pairs of the oracle's bounding boxes
     for name, arr, grad in (("mean", m, dm), ("scale", s, ds), ("quat", q, dq), ("value", v, dv)):
         for idx in np.ndindex(arr.shape):
             ap, am = arr.copy(), arr.copy()
@@ -36,6 +60,9 @@ def test_voxelize_backward_matches_central_differences(kappa):
             args_m = dict(m=m, s=s, q=q, v=v)
             key = {"mean": "m", "scale": "s", "quat": "q", "value": "v"}[name]
             args_p[key], args_m[key] = ap, am
+            if np.isfinite(kappa):
+                assert np.array_equal(_inside_mask(grid, args_p["m"], args_p["s"], args_p["q"], kappa), inside)
+                assert np.array_equal(_inside_mask(grid, args_m["m"], args_m["s"], args_m["q"], kappa), inside)
             fd = (_vox_loss(grid, **args_p, G=G, kappa=kappa) - _vox_loss(grid, **args_m, G=G, kappa=kappa)) / (2 * h)
             assert grad[idx] == pytest.approx(fd, rel=1e-6, abs=1e-8), (name, idx)
 

@@ -166,15 +166,42 @@ def test_truncation_removes_only_pixels_outside_the_ellipse():
     assert not cut[q > 4.0].any() and full[q > 4.0].any()
 
 
+def _ellipse_mask(nu, nv, views, mean, scale, quat, kappa, h=1e-4):
+    """Which (view, Gaussian, pixel) triples lie inside the truncation ellipse of
+    Eq. 9, with the ray-space map solved by NumPy, its Jacobian by central
+    differences and the 2-D covariance inverted by NumPy (as in the brute force)."""
+    ia, ib = np.meshgrid(np.arange(nu) + 0.5 - nu / 2, np.arange(nv) + 0.5 - nv / 2)
+    xh = np.stack([ia, ib], axis=-1)
+    out = np.zeros((len(views), len(mean), nv, nu), dtype=bool)
+    for p, view in enumerate(views):
+        for g in range(len(mean)):
+            J = np.stack([(brute.ray_space(view, mean[g] + e) - brute.ray_space(view, mean[g] - e)) / (2 * h)
+                          for e in np.eye(3) * h], axis=1)
+            R = brute.rotation(quat[g])
+            Sh = (J @ R @ np.diag(np.asarray(scale[g]) ** 2) @ R.T @ J.T)[:2, :2]
+            d = xh - brute.ray_space(view, mean[g])[:2]
+            out[p, g] = np.einsum("...i,ij,...j->...", d, np.linalg.inv(Sh), d) <= kappa * kappa
+    return out
+
+
+@pytest.mark.parametrize("kappa", [np.inf, 3.0])
 @pytest.mark.parametrize("param", ["mean", "scale", "quat", "value"])
-def test_gradients_match_central_differences(param):
+def test_gradients_match_central_differences(param, kappa):
+    """At kappa = 3 the image is only piecewise smooth in the parameters: a pixel
+    that crosses a Gaussian's kappa-ellipse adds or drops a term.  No central
+    difference of these seeds moves any pixel across an ellipse (checked with the
+    NumPy ray-space map), so the differences see exactly the pixels inside, and
+    the adjoint must skip the rest."""
     nu, nv = 18, 14
     vw = circular_views(2, 300.0, 450.0, nu, nv, 1.6, 1.6, start=0.5)
     mean, scale, quat, value = _gaussians(7, 3, -8, 8, 2.0, 4.0)
     dY = np.random.default_rng(8).normal(size=(2, nv, nu))
     grads = dict(zip(("mean", "scale", "quat", "value"),
-                     oracle.splat_backward(nu, nv, vw, mean, scale, quat, value, dY, kappa=np.inf)))
+                     oracle.splat_backward(nu, nv, vw, mean, scale, quat, value, dY, kappa=kappa)))
     args = dict(mean=mean, scale=scale, quat=quat, value=value)
+    if np.isfinite(kappa):
+        inside = _ellipse_mask(nu, nv, vw, mean, scale, quat, kappa)
+        assert inside.any() and not inside.all()
     x = args[param]
     fd = np.zeros_like(x)
     h = 1e-5
@@ -183,7 +210,9 @@ def test_gradients_match_central_differences(param):
             xp = x.copy()
             xp[idx] += sgn * h
             a = dict(args, **{param: xp})
+            if np.isfinite(kappa) and param != "value":
+                assert np.array_equal(_ellipse_mask(nu, nv, vw, a["mean"], a["scale"], a["quat"], kappa), inside)
             fd[idx] += sgn * np.sum(dY * oracle.splat(nu, nv, vw, a["mean"], a["scale"], a["quat"], a["value"],
-                                                      kappa=np.inf)) / (2 * h)
+                                                      kappa=kappa)) / (2 * h)
     g = grads[param]
     assert np.abs(g - fd).max() <= 1e-6 * max(np.abs(fd).max(), 1e-12)

@@ -6,7 +6,8 @@ CUDA path; the seeded generators in `synth` are the only thing both consume.
 """
 from .oracle import (  # noqa: F401
     lib, threads, set_threads, quat_to_rot,
-    voxelize, voxelize_ambiguity, voxelize_backward, combine, combine_backward, warp, warp_backward,
+    voxelize, voxelize_ambiguity, voxelize_tie_band, qform_and_bound, voxelize_backward,
+     combine, combine_backward, warp, warp_backward,
     project, project_backward, project_gaussians, loss, dssim, tv, mbc_normality,
-    splat_params, splat, splat_backward,
+    splat_params, splat, splat_backward, round_storage,
 )

@@ -34,6 +34,10 @@ def lib():
             L.orc_voxelize_ambiguity.argtypes = [_I64, _D, ct.c_int64, ct.c_int, _D, _D, _D, _D, ct.c_double,
                                                  ct.c_double, _D]
             L.orc_voxelize_ambiguity.restype = ct.c_int
+            L.orc_voxelize_tie_band.argtypes = [_I64, _D, ct.c_int64, ct.c_int, _D, _D, _D, _D, ct.c_double,
+                                                ct.c_double, _D, _D, _I64]
+            L.orc_voxelize_tie_band.restype = ct.c_int
+            L.orc_qform_and_bound.argtypes = [_D, _D, _D, _D, ct.c_double, _D]
             L.orc_voxelize_backward.argtypes = [_I64, _D, ct.c_int64, ct.c_int, _D, _D, _D, _D, ct.c_double,
                                                 _D, _D, _D, _D, _D]
             L.orc_voxelize_backward.restype = ct.c_int
@@ -128,6 +132,55 @@ def voxelize_ambiguity(grid, mean, scale, quat, value, kappa=3.0, eps=1e-4) -> n
     if rc != 0:
         raise ValueError("oracle voxelize_ambiguity rejected its arguments")
     return out.reshape(d[2], d[1], d[0])
+
+
+def voxelize_tie_band(grid, mean, scale, quat, value, kappa=3.0, units=2.0, offset=None):
+    """Per-voxel mass of the truncation decisions that binary32 evaluation of q
+    can flip ([nz][ny][nx]), from the first-order error bound of q per pair
+    (band |q - kappa^2| <= units * bound), and the number of pairs in the band.
+    offset (mm) shifts the voxel coordinates the bound sees (crops evaluated with
+    shifted means)."""
+    d, v, n = _grid(grid)
+    mean, scale, quat = _f64(mean).reshape(-1, 3), _f64(scale).reshape(-1, 3), _f64(quat).reshape(-1, 4)
+    value = _f64(value)
+    if value.ndim == 1:
+        value = value[:, None]
+    g, c = value.shape
+    out = np.zeros(n)
+    cnt = np.zeros(1, dtype=np.int64)
+    off = _f64(offset if offset is not None else (0.0, 0.0, 0.0))
+    rc = lib().orc_voxelize_tie_band(d.ctypes.data_as(_I64), _p(v), g, c, _p(mean), _p(scale), _p(quat),
+                                     _p(value), float(kappa), float(units), _p(off), _p(out),
+                                     cnt.ctypes.data_as(_I64))
+    if rc != 0:
+        raise ValueError(f"oracle voxelize_tie_band failed ({rc})")
+    return out.reshape(d[2], d[1], d[0]), int(cnt[0])
+
+
+def qform_and_bound(mean, scale, quat, x, kappa=3.0):
+    """(q, bound): the quadratic form of one Gaussian at x (mm) and the
+    first-order bound on its binary32 evaluation error."""
+    out = np.zeros(2)
+    lib().orc_qform_and_bound(_p(_f64(mean)), _p(_f64(scale)), _p(_f64(quat)), _p(_f64(x)), float(kappa), _p(out))
+    return float(out[0]), float(out[1])
+
+
+def round_storage(x, fmt) -> np.ndarray:
+    """Round to the nearest value of a storage format, ties to even, returned
+    in float64: fmt "bf16" (8 significant bits, the float32 exponent range) or
+    "f16" (11 significant bits, subnormals below 2^-14, largest finite 65504;
+    larger magnitudes become infinite).  Written from the formats' definitions:
+    the significand is scaled to an integer and rounded half to even."""
+    x = np.asarray(x, dtype=np.float64)
+    bits = {"bf16": 8, "f16": 11}[fmt]
+    m, e = np.frexp(x)  # x = m 2^e, 0.5 <= |m| < 1
+    if fmt == "f16":
+        e = np.maximum(e, -13)  # below 2^-14 the quantum stays 2^-24
+        m = np.ldexp(x, -e)
+    out = np.ldexp(np.round(np.ldexp(m, bits)), e - bits)
+    if fmt == "f16":
+        out = np.where(np.abs(out) > 65504.0, np.copysign(np.inf, x), out)
+    return out
 
 
 def voxelize_backward(grid, mean, scale, quat, value, d_out, kappa=3.0):

@@ -18,7 +18,7 @@
  *   Eq. 6  I(r) = integral of sigma along the ray                   project
  *   Eq. 10/12  mean L1 over the batch; Eq. 1 squared-norm form      loss
  *   Eq. 8-9  local affine projection of each Gaussian to a 2-D Gaussian  splat (Stage 1)
- * Readings where the paper is silent (all listed in the design notes):
+ * Readings where the paper is silent:
  *   Sigma = R(q/|q|) diag(s^2) R^T with q = (w,x,y,z) and s in mm; hard
  *   truncation q_form <= kappa^2 (kappa = +inf disables it); values are sampled
  *   at voxel centres (i + 1/2 - n/2) v; interpolation is trilinear with zero
@@ -188,6 +188,92 @@ int orc_voxelize_ambiguity(const int64_t dims[3], const double vox[3], int64_t G
     }
     free(gs);
     return 0;
+}
+
+/* First-order bound on the error of q when an implementation evaluates it in
+ * IEEE binary32 (unit roundoff u = 2^-24) from the inputs rounded to binary32:
+ * the normalised quaternion and R (every entry within 25u absolute), 1/s_j^2
+ * (2 roundings), the inverse covariance A = R diag(1/s^2) R^T (a three-term sum
+ * and the doubled off-diagonal, 5 roundings), the offset d = x - mu from a
+ * rounded voxel centre x (2 roundings) and the quadratic form itself (at most 6
+ * sequential roundings).  With r~_j = sum_a |R_aj||d_a|, x~_j = sum_a |R_aj||x_a|
+ * and |d|_1 = sum_a |d_a|, summing the first-order terms of q = sum_j (r_j/s_j)^2
+ * gives
+ *     |fl(q) - q| <= u sum_j (50 r~_j |d|_1 + 2 r~_j x~_j + 15 r~_j^2) / s_j^2,
+ * and kappa^2 itself rounds by u kappa^2.  The tie band below uses 64 in place
+ * of 50 and a caller-chosen multiple ("units") of the total. */
+static double q_fp32_bound(const gauss_t* g, const double x[3], const double d[3], double k2) {
+    double d1 = fabs(d[0]) + fabs(d[1]) + fabs(d[2]), b = 0.0;
+    for (int j = 0; j < 3; j++) {
+        double rt = 0.0, xt = 0.0;
+        for (int a = 0; a < 3; a++) { rt += fabs(g->R[3 * a + j]) * fabs(d[a]); xt += fabs(g->R[3 * a + j]) * fabs(x[a]); }
+        b += (64.0 * rt * d1 + 2.0 * rt * xt + 15.0 * rt * rt) / (g->s[j] * g->s[j]);
+    }
+    return ldexp(b + k2, -24);
+}
+
+/* The quadratic form q of one Gaussian at point x (mm) and its binary32 error
+ * bound (q_fp32_bound), for the tests that pin the bound. */
+void orc_qform_and_bound(const double* mean, const double* scale, const double* quat, const double x[3],
+                         double kappa, double out[2]) {
+    gauss_t g;
+    const int64_t dims[3] = {1, 1, 1};
+    const double vox[3] = {1.0, 1.0, 1.0};
+    prepare(&g, mean, scale, quat, kappa, 0, dims, vox);
+    double d[3] = {x[0] - g.mu[0], x[1] - g.mu[1], x[2] - g.mu[2]}, r[3];
+    out[0] = qform(&g, d, r);
+    out[1] = q_fp32_bound(&g, x, d, kappa * kappa);
+}
+
+/* Per-voxel mass of the truncation decisions that binary32 rounding can flip:
+ * amb[v] = sum_g max_c |value[g][c]| exp(-q/2) over the pairs with
+ * |q - kappa^2| <= units * q_fp32_bound (above).  offset (mm, may be NULL) is
+ * added to every voxel centre for the bound only: a crop evaluated here with
+ * shifted means stands for voxels whose coordinates in the full grid are
+ * x + offset.  *npairs receives the number of pairs in the band.  Returns -2 if
+ * a pair in the band has a band wider than the 1% margin of the bounding boxes
+ * visited (pairs outside them could then reach the band too). */
+int orc_voxelize_tie_band(const int64_t dims[3], const double vox[3], int64_t G, int C,
+                          const double* mean, const double* scale, const double* quat, const double* value,
+                          double kappa, double units, const double* offset, double* amb, int64_t* npairs) {
+    if (!(kappa > 0.0) || C < 1 || !(units >= 0.0)) return -1;
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2], N = nx * ny * nz;
+    memset(amb, 0, sizeof(double) * (size_t)N);
+    if (npairs) *npairs = 0;
+    if (isinf(kappa)) return 0;
+    const double k2 = kappa * kappa, o[3] = {offset ? offset[0] : 0.0, offset ? offset[1] : 0.0,
+                                             offset ? offset[2] : 0.0};
+    gauss_t* gs = (gauss_t*)malloc(sizeof(gauss_t) * (size_t)(G > 0 ? G : 1));
+    for (int64_t g = 0; g < G; g++)
+        prepare(&gs[g], mean + 3 * g, scale + 3 * g, quat + 4 * g, kappa * sqrt(1.01), 1, dims, vox);
+    int64_t count = 0;
+    int wide = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : count) reduction(| : wide)
+    for (int64_t k = 0; k < nz; k++) {
+        for (int64_t g = 0; g < G; g++) {
+            const gauss_t* ga = &gs[g];
+            if (k < ga->lo[2] || k > ga->hi[2]) continue;
+            double vmax = 0.0;
+            for (int c = 0; c < C; c++) vmax = fmax(vmax, fabs(value[g * C + c]));
+            for (int64_t j = ga->lo[1]; j <= ga->hi[1]; j++)
+                for (int64_t i = ga->lo[0]; i <= ga->hi[0]; i++) {
+                    double x[3] = {centre(i, nx, vox[0]), centre(j, ny, vox[1]), centre(k, nz, vox[2])};
+                    double d[3] = {x[0] - ga->mu[0], x[1] - ga->mu[1], x[2] - ga->mu[2]};
+                    double xf[3] = {x[0] + o[0], x[1] + o[1], x[2] + o[2]};
+                    double r[3];
+                    double q = qform(ga, d, r);
+                    double band = units * q_fp32_bound(ga, xf, d, k2);
+                    if (fabs(q - k2) <= band) {
+                        if (band > 0.01 * k2) wide = 1;
+                        amb[(k * ny + j) * nx + i] += vmax * exp(-0.5 * q);
+                        count++;
+                    }
+                }
+        }
+    }
+    free(gs);
+    if (npairs) *npairs = count;
+    return wide ? -2 : 0;
 }
 
 /* d R / d (w, x, y, z) for the rotation matrix written in quat_to_rot (treating

@@ -46,15 +46,28 @@ def pixel_views(views_np, nu, nv, pixels):
     return np.array(out)
 
 
+def tie_band(grid, gs, kappa, offset=None, mean=None):
+    """The oracle's per-voxel tie mass: pairs whose q lies within the binary32
+    error bound of q from kappa^2 (and the number of such pairs)."""
+    import oracle
+    m = gs.mean if mean is None else mean
+    return oracle.voxelize_tie_band(grid, m, gs.scale, gs.quat, gs.value, kappa, 1.0, offset)
+
+
 def assert_voxels_match(got, ref, amb, tol):
     """Voxelization parity that respects truncation ties: voxels with no pair
-    near q = kappa^2 (amb == 0) must match to relative L2 <= tol; voxels with
-    such pairs may differ by at most their ambiguity mass (plus rounding)."""
+    inside the binary32 tie band of q = kappa^2 (amb == 0) must match to
+    relative L2 <= tol; voxels with such pairs may differ by at most their
+    tie mass (plus rounding).  Returns (fraction of voxels outside the band,
+    number of voxels whose difference exceeds the rounding floor, i.e. where a
+    tie was decided the other way)."""
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     amb = np.broadcast_to(np.asarray(amb, dtype=np.float64), ref.shape)
     sure = amb == 0
     assert rel_l2(got[sure], ref[sure]) <= tol
-    slack = amb + 4 * tol * np.abs(ref).max()
+    floor = 4 * tol * np.abs(ref).max()
+    slack = amb + floor
     assert np.all(np.abs(got - ref)[~sure] <= slack[~sure])
-    return float(sure.mean())
+    flipped = int(np.count_nonzero(np.abs(got - ref)[~sure] > floor))
+    return float(sure.mean()), flipped

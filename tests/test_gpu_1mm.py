@@ -12,7 +12,7 @@ import oracle
 import paper_2503_22139_gb300 as pmf
 from paper_2503_22139_gb300.pipeline import ForwardAdjoint
 from synth import Grid, paper_workload_1mm, select_batch
-from tests.gpu_util import assert_voxels_match, dev, gset, host, pixel_views, rel_l2, views
+from tests.gpu_util import assert_voxels_match, dev, gset, host, pixel_views, rel_l2, tie_band, views
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +39,7 @@ def test_1mm_voxelization_on_sampled_crops(wl, V):
         crop = Grid(D, D, D, 1.0, 1.0, 1.0)
         sh = m.mean.astype(np.float64) - c
         ref = oracle.voxelize(crop, sh, m.scale, m.quat, m.value, wl.kappa)
-        amb = oracle.voxelize_ambiguity(crop, sh, m.scale, m.quat, m.value, wl.kappa)
+        amb, _ = tie_band(crop, m, wl.kappa, offset=c, mean=sh)
         got = Vh[o[2]:o[2] + D, o[1]:o[1] + D, o[0]:o[0] + D][None]
         assert_voxels_match(got, ref, amb, 1e-5)
 

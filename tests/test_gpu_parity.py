@@ -9,7 +9,7 @@ import oracle
 import paper_2503_22139_gb300 as pmf
 from synth import Detector, Grid, circular_views, small_workload, fd_subproblem, gaussian_set, mbc_levels
 from tests import oracle_chain
-from tests.gpu_util import assert_voxels_match, dev, gset, host, pixel_views, rel_l2, views
+from tests.gpu_util import assert_voxels_match, dev, gset, host, pixel_views, rel_l2, tie_band, views
 
 pytestmark = pytest.mark.gpu
 
@@ -33,19 +33,29 @@ def test_voxelize_ragged_grid(kappa):
     gs = _rand_gaussians(1, grid, 60, 0.7, 3.0, 1)
     got = host(pmf.gs_voxelize(grid, gset(gs, kappa)))
     ref = oracle.voxelize(grid, gs.mean, gs.scale, gs.quat, gs.value, kappa)
-    amb = oracle.voxelize_ambiguity(grid, gs.mean, gs.scale, gs.quat, gs.value, kappa)
+    amb, _ = tie_band(grid, gs, kappa)
     assert_voxels_match(got, ref, amb, TOL32)
 
 
-def test_voxelize_small_workload_reference_and_mbc():
+@pytest.mark.parametrize("kappa", [3.0, 5.0])
+def test_voxelize_small_workload_reference_and_mbc(kappa):
+    """At the workloads' kappa = 3 the voxels outside the binary32 tie band hold
+    1e-5 and the rest their tie mass; the number of pairs in the band and of
+    voxels where a tie actually went the other way are printed.  At kappa = 5
+    a flipped tie moves a voxel by at most max|value| e^{-12.5}, so every voxel
+    of the volume, ties included, holds 1e-5."""
     wl = small_workload(with_measured=False)
     for gs in (wl.ref, wl.mbc[0]):
-        got = host(pmf.gs_voxelize(wl.grid, gset(gs, wl.kappa)))
-        ref = oracle.voxelize(wl.grid, gs.mean, gs.scale, gs.quat, gs.value, wl.kappa)
-        amb = oracle.voxelize_ambiguity(wl.grid, gs.mean, gs.scale, gs.quat, gs.value, wl.kappa)
+        got = host(pmf.gs_voxelize(wl.grid, gset(gs, kappa)))
+        ref = oracle.voxelize(wl.grid, gs.mean, gs.scale, gs.quat, gs.value, kappa)
+        amb, npairs = tie_band(wl.grid, gs, kappa)
         assert got.shape == (gs.channels,) + wl.grid.shape
-        assert rel_l2(got, ref) <= 1e-4  # all voxels, ties included
-        assert assert_voxels_match(got, ref, amb, TOL32) > 0.99
+        sure, flipped = assert_voxels_match(got, ref, amb, TOL32)
+        print(f"kappa {kappa} C={gs.channels}: all-voxel rel-L2 {rel_l2(got, ref):.2e}, {npairs} pairs in the tie "
+              f"band, {int((amb > 0).sum())} voxels touched, {flipped} decided the other way")
+        assert sure > (0.999 if kappa == 3.0 else 0.99)
+        if kappa == 5.0:
+            assert rel_l2(got, ref) <= TOL32  # all voxels, ties included
 
 
 def test_voxelize_list_overflow_falls_back_correctly():
@@ -268,6 +278,43 @@ def test_project_bulk_copy_staging_equals_plain_staging(shared):
     pmf.device_status()
     ref = oracle.project(grid, 70, 54, 1.0, vw, host(src), shared=shared)
     assert rel_l2(host(y32), ref) <= TOL32
+
+
+def test_bulk_copy_wait_timeout_is_reported_and_recovers():
+    """The failure path of the bulk-copy projector's bounded wait, without a
+    fault: the test hook arms each chunk's mbarrier but issues no copy, so every
+    CTA that stages a box gives up after its short limit with nothing in flight.
+    Its pixels are NaN (the others equal a clean launch), the timeout counter
+    rises and pmf_device_status reports PMF_ETIMEOUT; once the hook is off, the
+    next launch equals a clean one bit for bit and the status is OK again."""
+    grid = Grid(48, 44, 36, 2.0, 2.0, 2.0)
+    P = 3
+    vol = dev(np.random.default_rng(24).random(grid.shape).astype(np.float32))
+    vw = views(circular_views(P, 500.0, 750.0, 70, 54, 2.2, 2.2, start=0.3))
+    det = Detector(70, 54, 1.0)
+    pmf.device_counters(reset=True)
+    clean = pmf.conebeam_project(grid, det, vw, vol, shared=True)
+    pmf.device_status()
+    try:
+        pmf.ops.pmf_debug_stall_bulk_copies(True)
+        stalled = pmf.conebeam_project(grid, det, vw, vol, shared=True)
+        torch.cuda.synchronize()
+    finally:
+        pmf.ops.pmf_debug_stall_bulk_copies(False)
+    # a CTA that stages a box times out and writes NaN to all its pixels; one
+    # whose every chunk takes the global-gather fallback computes as usual
+    nan = torch.isnan(stalled)
+    assert bool(torch.equal(stalled[~nan], clean[~nan]))
+    hit = clean != 0
+    assert float(nan[hit].float().mean()) > 0.5
+    assert pmf.device_counters()["timeout"] > 0
+    with pytest.raises(pmf.PmfError, match="ETIMEOUT"):
+        pmf.device_status()
+    pmf.device_counters(reset=True)
+    again = pmf.conebeam_project(grid, det, vw, vol, shared=True)
+    assert torch.equal(again, clean)
+    assert pmf.device_counters()["timeout"] == 0
+    pmf.device_status()
 
 
 def test_project_small_workload_voxelized_reference():

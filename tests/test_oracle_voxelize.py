@@ -139,3 +139,74 @@ def test_ambiguity_mass_is_the_band_between_two_cutoffs():
     np.testing.assert_allclose(hi - lo, amb, rtol=1e-12, atol=1e-15)
     assert amb.max() > 0
     assert oracle.voxelize_ambiguity(grid, m, s, q, val, np.inf, eps).max() == 0.0
+
+
+def _q_binary32(mu, s, quat, x):
+    """q evaluated entirely in binary32 (NumPy float32, no fused operations) in
+    three different orders: the symmetric inverse-covariance form, the sum of
+    squares of R^T d / s, and A d dotted with d."""
+    f = np.float32
+    mu, s, quat, x = (np.asarray(a, f) for a in (mu, s, quat, x))
+    n = np.sqrt(f(quat @ quat))
+    w, a, b, c = quat * (f(1) / n)
+    R = np.array([[1 - 2 * (b * b + c * c), 2 * (a * b - w * c), 2 * (a * c + w * b)],
+                  [2 * (a * b + w * c), 1 - 2 * (a * a + c * c), 2 * (b * c - w * a)],
+                  [2 * (a * c - w * b), 2 * (b * c + w * a), 1 - 2 * (a * a + b * b)]], dtype=f)
+    d = (x - mu).astype(f)
+    is2 = (f(1) / (s * s)).astype(f)
+    A = np.array([[R[i, 0] * R[j, 0] * is2[0] + R[i, 1] * R[j, 1] * is2[1] + R[i, 2] * R[j, 2] * is2[2]
+                   for j in range(3)] for i in range(3)], dtype=f)
+    tx = A[0, 0] * d[0] + (A[0, 1] + A[1, 0]) * d[1] + (A[0, 2] + A[2, 0]) * d[2]
+    ty = A[1, 1] * d[1] + (A[1, 2] + A[2, 1]) * d[2]
+    q1 = d[0] * tx + d[1] * ty + A[2, 2] * d[2] * d[2]
+    r = (R.T @ d).astype(f) / s
+    q2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2]
+    q3 = (A @ d).astype(f) @ d
+    return [float(q1), float(q2), float(q3)]
+
+
+def test_binary32_error_of_q_stays_inside_the_tie_bound():
+    """The tie band rests on a first-order bound of the error of q evaluated in
+    binary32.  Evaluating q in binary32 in three orders for points near the
+    kappa = 3 surface of Gaussians with paper-scale coordinates (+-200 mm) and
+    anisotropic scales (1-6 mm), every error stays inside the bound -- with
+    room to spare, so the bound is valid -- and the bound is a small fraction
+    of kappa^2 (the band holds few pairs)."""
+    rng = np.random.default_rng(17)
+    worst, widths = 0.0, []
+    for _ in range(3000):
+        mu = rng.uniform(-200, 200, 3) * np.array([1.0, 1.0, 0.5])
+        s = np.exp(rng.uniform(np.log(1.0), np.log(6.0), 3))
+        quat = rng.normal(size=4)
+        u = rng.normal(size=3)
+        x = mu + brute.rotation(quat) @ (s * u / np.linalg.norm(u) * 3.0 * rng.uniform(0.98, 1.02))
+        mu, s, quat, x = (np.asarray(a, np.float32).astype(np.float64) for a in (mu, s, quat, x))
+        q64, bound = oracle.qform_and_bound(mu, s, quat, x, 3.0)
+        for q32 in _q_binary32(mu, s, quat, x):
+            worst = max(worst, abs(q32 - q64) / bound)
+        widths.append(bound / 9.0)
+    assert 0.0 < worst <= 0.5
+    assert np.median(widths) <= 1e-4 and np.max(widths) <= 1e-3
+
+
+def test_tie_band_lies_between_two_fixed_bands():
+    """The per-pair band sits between the fixed relative bands eps kappa^2 with
+    eps the smallest and the largest per-pair width, so its mass is sandwiched
+    between the two ambiguity masses; with kappa = inf it is empty."""
+    grid = Grid(16, 14, 12, 2.0, 2.0, 2.0)
+    rng = np.random.default_rng(41)
+    G = 30
+    m = (rng.random((G, 3)) - 0.5) * np.array([32, 28, 24])
+    s = rng.uniform(1.0, 5.0, (G, 3))
+    q, val = rng.normal(size=(G, 4)), rng.random((G, 1))
+    units = 100.0  # wide enough that the band holds pairs on this small grid
+    amb, npairs = oracle.voxelize_tie_band(grid, m, s, q, val, 3.0, units)
+    widths = []
+    for g in range(G):
+        for x in brute.centres(grid).reshape(-1, 3)[::7]:
+            widths.append(units * oracle.qform_and_bound(m[g], s[g], q[g], x, 3.0)[1] / 9.0)
+    lo = oracle.voxelize_ambiguity(grid, m, s, q, val, 3.0, 0.5 * min(widths))
+    hi = oracle.voxelize_ambiguity(grid, m, s, q, val, 3.0, 2.0 * max(widths))
+    assert npairs > 0 and amb.sum() > 0
+    assert np.all(lo <= amb + 1e-15) and np.all(amb <= hi + 1e-15)
+    assert oracle.voxelize_tie_band(grid, m, s, q, val, np.inf)[0].max() == 0.0

@@ -395,6 +395,18 @@ pmf_status pmf_shift_means(int64_t n, const float* mean, const float* offset, fl
  * d_mean [n][3], acc [n]: device fp32. */
 pmf_status gs_grad_norm_accumulate(int64_t n, const float* d_mean, float* acc, pmf_stream stream);
 
+/* The densification threshold of Sec. 2.3.2's control (the paper names the
+ * rule, densify the Gaussians with large loss gradients, but no threshold; the
+ * reading here densifies a fixed share of each set): *d_threshold (device fp32)
+ * receives the (rank + 1)-th largest of stat_i = grad_acc[i] * grad_scale
+ * (products rounded to fp32, as gs_density_control forms them), so exactly the
+ * `rank` largest statistics lie above it when they are distinct (fewer when
+ * the value at the cut is shared).  grad_acc [n]: device fp32; 0 <= rank < n,
+ * 1 <= n < 2^31; one CTA, no workspace, exact (a radix select on the order of
+ * the fp32 values).  PMF_EINVAL for bad arguments. */
+pmf_status gs_density_threshold(int64_t n, const float* grad_acc, float grad_scale, int64_t rank, float* d_threshold,
+                                pmf_stream stream);
+
 /* Adaptive density control of Sec. 2.3.2 on one Gaussian set (any channel
  * count).  With stat_i = grad_acc[i] * grad_scale (grad_scale = 1 / steps):
  *   every channel of value_i below value_threshold in magnitude -> removed;
@@ -481,6 +493,17 @@ pmf_status pmf_device_counters(uint64_t* host_out, int32_t reset);
  * scatter since the counters were last reset, else PMF_OK.  No kernel waits on
  * another CTA. */
 pmf_status pmf_device_status(pmf_stream stream);
+
+/* Test hook for the failure path of the bounded wait above (no counterpart in
+ * the paper).  While `on` is non-zero, every later launch of the per-volume
+ * bulk-copy projector (conebeam_project on fp32 volumes whose rows are 16-byte
+ * multiples) arms its mbarrier for a chunk's bytes but issues no copy, so the
+ * wait runs out after about 0.1 ms of clock with nothing in flight: those CTAs
+ * count PMF_DIAG_TIMEOUT and write NaN to their pixels, and pmf_device_status
+ * reports PMF_ETIMEOUT.  Off (0) when the library loads; set it back to 0 after
+ * the test.  Synchronous (a copy to a device symbol of the current device);
+ * PMF_ECUDA on failure.  Never faults or hangs the device. */
+pmf_status pmf_debug_stall_bulk_copies(int32_t on);
 
 /* ------------------------------------------------ training-step plans */
 

@@ -1,8 +1,8 @@
 """Adaptive density control of a Gaussian set (Sec. 2.3.2), plain NumPy.
 
 TEST INFRASTRUCTURE ONLY: used by tests/, never by the library.  One Gaussian
-at a time, in input order, following the rule of Sec. 2.3.2 with the readings
-listed in the design notes:
+at a time, in input order, following the rule of Sec. 2.3.2; where the paper
+gives no statistic, threshold or split geometry, these readings fill them:
 
   * the densification statistic of a Gaussian is the mean, over the steps since
     the last control, of the Euclidean norm of dL/d(mean);
@@ -27,6 +27,18 @@ from .brute import rotation
 def accumulate_grad_norm(acc, d_mean):
     """acc + |dL/dmean| per Gaussian."""
     return np.asarray(acc, np.float64) + np.linalg.norm(np.asarray(d_mean, np.float64).reshape(-1, 3), axis=1)
+
+
+def densify_threshold(grad_acc, grad_scale, rank):
+    """The densification threshold that leaves the `rank` largest statistics
+    above it: the (rank + 1)-th largest of stat_i = grad_acc_i * grad_scale
+    (0 <= rank < n).  The product and the order are taken in binary32, the
+    precision in which the control compares stat_i with the threshold, so that
+    both sides pick the same element."""
+    stat = np.asarray(grad_acc, np.float32).reshape(-1) * np.float32(grad_scale)
+    if not 0 <= rank < stat.size:
+        raise ValueError("rank must be in [0, n)")
+    return float(np.sort(stat)[::-1][rank])
 
 
 def actions(scale, value, stat, grad_threshold, scale_threshold, value_threshold):

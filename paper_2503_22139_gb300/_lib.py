@@ -129,6 +129,8 @@ SIGNATURES = {
     "pmf_workspace_size": [_I32, ct.POINTER(PmfWsArgs), _SZ],
     "pmf_device_counters": [ct.POINTER(ct.c_uint64), _I32],
     "pmf_device_status": [_P],
+    "gs_density_threshold": [_I64, _P, ct.c_float, _I64, _P, _P],
+    "pmf_debug_stall_bulk_copies": [_I32],
     "pmf_plan_create": [ct.POINTER(PmfBatchDesc), ct.POINTER(ct.c_void_p)],
     "pmf_plan_step": [_P, _P],
     "pmf_plan_tensors_get": [_P, ct.POINTER(PmfPlanTensors)],

@@ -1,5 +1,7 @@
 // Adaptive density control of a Gaussian set (Sec. 2.3.2) for sm_103a:
 //   k_grad_norm_acc  acc[i] += |dL/dmean_i| over the steps between controls
+//   k_select_desc    the densification threshold: the (rank + 1)-th largest
+//                    statistic (radix select, one CTA)
 //   k_dc_count       per Gaussian the action (remove, keep, clone, split) and
 //                    how many Gaussians it leaves (0, 1, 2, 2)
 //   scan_counts      output offsets (order-preserving, deterministic)
@@ -80,6 +82,56 @@ __global__ void k_dc_emit(pmf_gaussians G, const unsigned char* __restrict__ act
 
 __global__ void k_dc_total(const unsigned long long* total, int64_t* out) { *out = (int64_t)*total; }
 
+// Order-preserving key of a float: larger floats get larger unsigned keys
+// (negative values have their bits inverted, the rest the sign bit set).
+__device__ __forceinline__ unsigned order_key(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_value(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// The (rank + 1)-th largest of acc[i] * scale (fp32 products), by a radix
+// select on the order keys, eight bits per pass from the top: each pass counts
+// the digit of the keys that match the digits chosen so far and keeps the bin
+// holding the wanted rank.  One CTA; exact, and independent of thread timing.
+constexpr int kSelThreads = 1024;
+
+__global__ void __launch_bounds__(kSelThreads) k_select_desc(int64_t n, const float* __restrict__ acc, float scale,
+                                                            int64_t rank, float* out) {
+    __shared__ unsigned hist[256];
+    __shared__ unsigned s_prefix, s_want;
+    if (threadIdx.x == 0) {
+        s_prefix = 0u;
+        s_want = (unsigned)rank;
+    }
+    unsigned mask = 0u;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
+        __syncthreads();
+        const unsigned prefix = s_prefix;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned k = order_key(__fmul_rn(__ldg(acc + i), scale));
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 0xffu], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned want = s_want, b = 255u;
+            for (;; b--) {  // the wanted rank lies in the bin where the count from the top passes it
+                if (want < hist[b] || b == 0u) break;
+                want -= hist[b];
+            }
+            s_want = want;
+            s_prefix = prefix | (b << shift);
+        }
+        mask |= 0xffu << shift;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = key_value(s_prefix);
+}
+
 struct DcWs {
     unsigned char* act;
     unsigned* cnt;
@@ -121,6 +173,16 @@ pmf_status gs_grad_norm_accumulate(int64_t n, const float* d_mean, float* acc, p
     k_grad_norm_acc<<<(unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks), kDcThreads, 0,
                       (cudaStream_t)stream>>>(n, d_mean, acc);
     return check_launch("gs_grad_norm_accumulate");
+}
+
+pmf_status gs_density_threshold(int64_t n, const float* grad_acc, float grad_scale, int64_t rank, float* d_threshold,
+                                pmf_stream stream) {
+    PMF_REQUIRE(n > 0 && n < ((int64_t)1 << 31), "n must be in [1, 2^31)");
+    PMF_REQUIRE(rank >= 0 && rank < n, "rank must be in [0, n)");
+    PMF_REQUIRE(grad_acc != nullptr && d_threshold != nullptr, "null pointer");
+    PMF_REQUIRE(isfinite(grad_scale), "grad_scale must be finite");
+    k_select_desc<<<1, kSelThreads, 0, (cudaStream_t)stream>>>(n, grad_acc, grad_scale, rank, d_threshold);
+    return check_launch("gs_density_threshold");
 }
 
 pmf_status gs_density_control_workspace(int64_t n, size_t* bytes) {

@@ -135,6 +135,12 @@ constexpr int kTmaRows = 8;                   // rows per copy
 constexpr int kTmaSkew = 16;                  // extra plane stride (floats) of the conflict-free layout
 constexpr int kTmaBox = 8192;                 // staged floats (32 KB)
 constexpr long long kTmaWaitCycles = 2000000000LL;
+constexpr long long kStallWaitCycles = 200000LL;  // the test hook's short limit (~0.1 ms)
+
+// Test hook (pmf_debug_stall_bulk_copies): while non-zero, the per-volume
+// bulk-copy projector arms its mbarrier for a chunk's bytes but issues no copy,
+// so its bounded wait runs out with nothing in flight.  Zero in normal use.
+static __device__ int g_stall_copies;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -158,11 +164,11 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
     return ok != 0;
 }
 
-// Wait for phase `parity` of bar, at most kTmaWaitCycles; true if it completed.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+// Wait for phase `parity` of bar, at most `limit` clock cycles; true if it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, long long limit) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kTmaWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -178,13 +184,17 @@ __device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, 
 // Returns false (after writing NaN to its pixels) when a bulk copy did not
 // complete within the bounded wait; the mbarrier's phase is then unknown and
 // the CTA must not stage again.  `parity` is the barrier phase the CTA's next
-// copy completes, carried across tiles by persistent callers.
+// copy completes, carried across tiles by persistent callers.  `stall` (the
+// test hook) arms the barrier without issuing the copies and waits at most
+// kStallWaitCycles.
 template <int CH, int RPB>
 __device__ __forceinline__ bool project_tile_tma(const GridD& g, int nu, int nv, int ntu, float step,
                                                  const pmf_view* __restrict__ views, const CUtensorMap* map,
                                                  const float* __restrict__ vol, int64_t vol_stride,
                                                  float* __restrict__ proj, int p, int tile, float* box,
-                                                 unsigned long long* bar, BoxState& bs, unsigned& parity) {
+                                                 unsigned long long* bar, BoxState& bs, unsigned& parity,
+                                                 bool stall = false) {
+    const long long limit = stall ? kStallWaitCycles : kTmaWaitCycles;
     int a, b;
     pixel_of<RPB>(tile, ntu, a, b);
     const bool in = a < nu && b < nv;
@@ -223,18 +233,21 @@ __device__ __forceinline__ bool project_tile_tma(const GridD& g, int nu, int nv,
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 const int nyb = byr / kTmaRows;
                 mbar_expect_tx(bar, (unsigned)(bx.bz * nyb * kTmaRows * kTmaX * sizeof(float)));
-                for (int zz = 0; zz < bx.bz; zz++) {
+                for (int zz = 0; zz < (stall ? 0 : bx.bz); zz++) {
                     const int sh = skew * (zz & 1);  // a multiple of 4 voxels: the copy start stays aligned
                     for (int yb = 0; yb < nyb; yb++)
                         tma_load_4d(box + zz * S - sh + yb * kTmaRows * kTmaX, map, x0 - sh, bx.ly + yb * kTmaRows,
                                     bx.lz + zz, pv, bar);
                 }
             }
-            const bool ok = mbar_wait_bounded(bar, parity);
+            const bool ok = mbar_wait_bounded(bar, parity, limit);
             parity ^= 1u;
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) diag_count(PMF_DIAG_TIMEOUT);
-                mbar_wait_bounded(bar, parity ^ 1u);  // the copies still in flight, once more
+                // the copies may still be in flight into this CTA's shared
+                // memory: wait for them once more, four times as long, before
+                // the CTA exits (with the test hook none was issued)
+                mbar_wait_bounded(bar, parity ^ 1u, 4 * limit);
                 if (in) proj[((int64_t)p * nv + b) * nu + a] = __int_as_float(0x7fc00000);
                 return false;
             }
@@ -298,8 +311,9 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_tma(GridD g, int nu
     }
     __syncthreads();
     unsigned parity = 0;
+    const bool stall = *(volatile int*)&g_stall_copies != 0;
     project_tile_tma<CH, RPB>(g, nu, nv, ntu, step, views, &map, vol, vol_stride, proj, blockIdx.y, blockIdx.x, box,
-                              &bar, bs, parity);
+                              &bar, bs, parity, stall);
 }
 
 // The uneven batch of fp32 volumes with bulk-copy staging: one tensor map per
@@ -467,6 +481,13 @@ pmf_status conebeam_project(const pmf_grid* grid, const pmf_detector* det, int32
 
 pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pmf_dtype dtype, pmf_stream stream) {
     return project_batched_impl(n, items, dtype, MarchShape{}, 0, (cudaStream_t)stream);
+}
+
+pmf_status pmf_debug_stall_bulk_copies(int32_t on) {
+    const int v = on ? 1 : 0;
+    cudaError_t e = cudaMemcpyToSymbol(g_stall_copies, &v, sizeof(v));
+    if (e != cudaSuccess) return set_error(PMF_ECUDA, "pmf_debug_stall_bulk_copies: %s", cudaGetErrorString(e));
+    return PMF_OK;
 }
 
 }  // extern "C"

@@ -164,6 +164,16 @@ def gs_grad_norm_accumulate(d_mean: torch.Tensor, acc: torch.Tensor) -> torch.Te
     return acc
 
 
+def gs_density_threshold(grad_acc: torch.Tensor, steps: int, rank: int) -> torch.Tensor:
+    """Device fp32 scalar: the (rank + 1)-th largest of grad_acc / steps, the
+    densification threshold that leaves the `rank` largest statistics above it."""
+    grad_acc = _need(grad_acc, "grad_acc", torch.float32)
+    out = torch.empty((), dtype=torch.float32, device=grad_acc.device)
+    check(_lib.load().gs_density_threshold(int(grad_acc.numel()), _p(grad_acc), float(1.0 / max(int(steps), 1)),
+                                           int(rank), _p(out), _stream()), "gs_density_threshold")
+    return out
+
+
 def gs_density_control(gs: Gaussians, grad_acc: torch.Tensor, steps: int, noise: torch.Tensor, grad_threshold: float,
                        scale_threshold: float, value_threshold: float, split_factor: float = 1.6) -> Gaussians:
     """Sec. 2.3.2's adaptive density control: returns the new set (synchronizes
@@ -657,6 +667,12 @@ def pmf_device_status() -> None:
 
 
 device_status = pmf_device_status
+
+
+def pmf_debug_stall_bulk_copies(on: bool) -> None:
+    """Test hook: while on, the per-volume bulk-copy projector arms its
+    mbarrier without issuing copies, so its bounded wait runs out (see pmf.h)."""
+    check(_lib.load().pmf_debug_stall_bulk_copies(1 if on else 0), "pmf_debug_stall_bulk_copies")
 
 
 # ----------------------------------------------------- training-step plan

@@ -434,9 +434,10 @@ class TwoResolutionSchedule:
         c = self.control
         new = []
         for gs, acc in zip(self.sets, self.acc):
-            # the densification threshold: the (1 - fraction) quantile of the statistic (host-side choice)
-            stat = acc / max(self.since, 1)
-            thr = float(torch.quantile(stat.float(), 1.0 - float(c["densify_fraction"])).item()) if gs.n > 1 else 0.0
+            # the densification threshold leaves the top densify_fraction of the set above it
+            # (selected on the device; read back because the control's outputs are sized on the host)
+            rank = min(int(float(c["densify_fraction"]) * gs.n), gs.n - 1)
+            thr = float(ops.gs_density_threshold(acc, self.since, rank).item()) if gs.n > 0 else 0.0
             noise = torch.randn((gs.n, 2, 3), generator=self.gen, device=gs.mean.device)
             new.append(ops.gs_density_control(gs, acc, self.since, noise, thr, float(c["clone_scale_mm"]),
                                               float(c["prune_value"]), float(c["split_factor"])))

@@ -55,6 +55,23 @@ def test_density_control_is_deterministic_and_accumulates_gradient_norms():
     np.testing.assert_allclose(host(t), density.accumulate_grad_norm(np.full(2000, 0.5), d), rtol=1e-6)
 
 
+@pytest.mark.parametrize("n", [1, 7, 3000, 150_000])
+def test_densify_threshold_matches_the_oracle_bit_for_bit(n):
+    """The device radix select against the oracle's binary32 sort, over ranks
+    from the top to the bottom, with exponential statistics, repeated values,
+    zeros and one huge value."""
+    rng = np.random.default_rng(40 + n)
+    acc = rng.exponential(1.0, n).astype(np.float32)
+    if n > 10:
+        acc[rng.integers(0, n, n // 10)] = acc[0]   # ties
+        acc[rng.integers(0, n, n // 20)] = 0.0
+        acc[n // 2] = 3.0e38
+    d = dev(acc)
+    for rank in sorted({0, 1, n // 50, n // 2, n - 1} & set(range(n))):
+        got = float(pmf.gs_density_threshold(d, 9, rank).item())
+        assert got == density.densify_threshold(acc, np.float32(1.0 / 9), rank), rank
+
+
 def test_two_resolution_schedule_runs_both_stages_with_control():
     """Stage 2 on 32^3 at 8 mm (batches of 8), Stage 3 on 64^3 at 4 mm (batches
     of 4), density control every 3 steps: every loss finite, the sets change

@@ -90,3 +90,24 @@ def test_mixed_actions_keep_input_order():
     out = density.density_control(m, s, q, v, stat, 1.0, np.zeros((10, 2, 3)), 1.0, float(s[:5].max()), 1e-6)
     expect = [1, 1, 2, 3, 3, 4, 5, 5, 6, 7, 7, 8, 9, 9]  # source Gaussian of every output, in order
     np.testing.assert_array_equal(out[2], q[expect])
+
+
+def test_densify_threshold_is_the_order_statistic():
+    """The threshold leaves exactly `rank` statistics above it when they are
+    distinct, is itself one of the statistics, and at ties leaves fewer; the
+    statistics are binary32 products (the precision of the control's test)."""
+    rng = np.random.default_rng(3)
+    acc = rng.exponential(1.0, 5000).astype(np.float32)
+    scale = 1.0 / 7.0
+    stat = acc * np.float32(scale)
+    for rank in (0, 1, 99, 2500, 4999):
+        t = density.densify_threshold(acc, scale, rank)
+        assert np.float32(t) in stat
+        assert int(np.sum(stat > np.float32(t))) == rank
+        assert int(np.sum(stat >= np.float32(t))) >= rank + 1
+    tied = np.repeat(np.float32([3.0, 2.0, 1.0]), [5, 5, 5])
+    assert density.densify_threshold(tied, 1.0, 7) == 2.0      # ranks 5-9 share 2.0
+    assert int(np.sum(tied > 2.0)) == 5                        # fewer than 7 lie above it
+    assert density.densify_threshold(tied, 1.0, 0) == 3.0
+    with pytest.raises(ValueError):
+        density.densify_threshold(tied, 1.0, 15)

@@ -2,10 +2,14 @@
 // sample adds its 8 trilinear corner weights into a shared-memory box in
 // 32-bit fixed point (per-CTA scale); a warp's lanes take spread pixels and
 // start their chunk at staggered samples, so its simultaneous atomics land on
-// different voxels.  The box is then flushed with one 64-bit fixed-point
-// atomic per touched voxel (global scale 2^k from a provable bound).  Integer
-// sums are order independent, so the result is bit-reproducible.  A chunk
-// whose box does not fit in shared memory falls back to direct global atomics.
+// different voxels.  The box's bank layout follows the tile's rays: rows 33
+// words apart, x mirrored when the rays' x and y steps differ in sign, planes
+// a stride of 16 (mod 32) words apart, which keeps the cells of nearby
+// samples in different banks.  The box is then flushed with one 64-bit
+// fixed-point atomic per touched voxel (global scale 2^k from a provable
+// bound).  Integer sums are order independent, so the result is
+// bit-reproducible and independent of the layout.  A chunk whose box does not
+// fit in shared memory falls back to direct global atomics.
 #include "march.cuh"
 
 namespace pmf {
@@ -135,8 +139,9 @@ __device__ __forceinline__ int exp_for(float bound, int bits) {
 // (2 g + (w & 1), (w >> 1) + 4 q) of the 16x16 tile and starts its chunk at
 // sample 3 g + 2 q.  Shared-memory atomics are served per half-warp, and
 // within each half this spreads the 16 simultaneous corner addresses over the
-// banks (about 3.6 conflict rounds per warp-wide atomic at the paper
-// geometry, against 4.3 for adjacent pixels staggered 4 samples apart).
+// banks (measured at the paper geometry: 2.9 wavefronts per warp-wide atomic
+// with the ray-following box layout below, 3.8 with a fixed one; the floor is
+// 2).
 template <int RPB>
 __device__ __forceinline__ void pixel_of_spread(int tile, int ntu, int& a, int& b) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, g = l & 7, q = l >> 3;
@@ -148,6 +153,29 @@ __device__ __forceinline__ void pixel_of_spread(int tile, int ntu, int& a, int& 
 __device__ __forceinline__ int adjoint_phase() {
     const int l = threadIdx.x & 31;
     return 3 * (l & 7) + 2 * (l >> 3);
+}
+
+// Whether a tile's box stores x mirrored.  With the row pitch 33 a voxel's
+// bank is (x + y) mod 32, so cells of nearby samples collide where x and y
+// step in opposite directions (x + y stays put); mirroring x in the box,
+// (bx - 1 - x + y) mod 32, moves those apart again (it collides only where x
+// and y step the same way).  Decided from the ray through the tile's centre:
+// mirrored when its x and y steps differ in sign.  Only the bank layout
+// depends on it, never a result.
+template <int RPB>
+__device__ __forceinline__ bool tile_mirror(const pmf_view& vw, int nu, int nv, int ntu, int tile) {
+    const float ca = (float)((tile % ntu) * 16 + 8) - 0.5f * (float)nu;
+    const float cb = (float)((tile / ntu) * (RPB / 16) + RPB / 32) - 0.5f * (float)nv;
+    const float dx = (float)(vw.det[0] - vw.src[0]) + ca * (float)vw.du[0] + cb * (float)vw.dv[0];
+    const float dy = (float)(vw.det[1] - vw.src[1]) + ca * (float)vw.du[1] + cb * (float)vw.dv[1];
+    return dx * dy < 0.0f;
+}
+
+// Plane stride of the box: the smallest stride >= rows * kPitch that is 16
+// (mod 32), so cells one plane apart fall half a bank row apart.
+__device__ __forceinline__ int plane_stride(int rows) {
+    const int s = rows * kPitch;
+    return s + ((16 - (s & 31)) & 31);
 }
 
 // One pixel tile of view p of the adjoint; box must be all zero on entry and is
@@ -202,6 +230,8 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
     block_range(bs, r, live);
     const int Mlo = bs.range[0], Mhi = bs.range[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool mirror = tile_mirror<RPB>(views[p], nu, nv, ntu, tile);
+    const float sxf = mirror ? -1.0f : 1.0f;
     int sel = 0;
     for (int M0 = Mlo; M0 <= Mhi; M0 += CH, sel ^= 1) {
         int j0, j1, ib[3];
@@ -209,13 +239,20 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
         const bool act = chunk_begin<CH>(bs, sel, r, live, M0, j0, j1, ib, fb);
         __syncthreads();
         const Box bx = read_box(bs, sel);
-        if (threadIdx.x == 0 && bx.vol > 0 && !bx.fits) diag_count(PMF_DIAG_BACKPROJECT_BOX_FALLBACK);
-        if (bx.vol > 0 && bx.fits) {
+        const int sz = plane_stride(bx.by);
+        const bool fits = bx.vol > 0 && bx.bx <= 32 && (long long)bx.bz * sz <= kBox;
+        if (threadIdx.x == 0 && bx.vol > 0 && !fits) diag_count(PMF_DIAG_BACKPROJECT_BOX_FALLBACK);
+        if (fits) {
             if (act) {
-                const int sy = kPitch, sz = kPitch * bx.by;
+                const int sy = kPitch;
                 const float syf = (float)sy, szf = (float)sz;
-                // positions relative to the anchor cell, bounded like the box
-                int* qa = box + (ib[0] - bx.lx) + (ib[1] - bx.ly) * sy + (ib[2] - bx.lz) * sz;
+                // positions relative to the anchor cell, bounded like the box.
+                // Box column of voxel x: x - lx, or bx - 1 - (x - lx) mirrored;
+                // a sample's base address is its cell's lower-x corner, or its
+                // upper-x corner when mirrored, so the corners always sit at
+                // +0, +1, +sy, +sy + 1 (the two x weights trade places)
+                int* qa = box + (mirror ? bx.bx - 2 - (ib[0] - bx.lx) : ib[0] - bx.lx) + (ib[1] - bx.ly) * sy +
+                          (ib[2] - bx.lz) * sz;
                 // every sample adds its 8 scaled corner weights to the box; the
                 // weights are formed with the bias kMagic, so each rounds to an
                 // integer-valued float and converts with one integer subtract.
@@ -230,32 +267,33 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
                     const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
                                 uz = fmaf(jf, r.dh[2], fb[2]);
                     const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
-                    const int idx = (int)fmaf(flz, szf, fmaf(fly, syf, flx));
+                    const int idx = (int)fmaf(flx, sxf, fmaf(fly, syf, flz * szf));
                     const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
                     const float ex = 1.0f - fx, ey = 1.0f - fy, ez = (1.0f - fz) * gsb, fzs = fz * gsb;
                     const float a0 = ey * ez, a1 = fy * ez, a2 = ey * fzs, a3 = fy * fzs;
+                    const float w0 = mirror ? fx : ex, w1 = mirror ? ex : fx;  // the corners at +0 and +1
                     int* q = qa + idx;
                     int* q2 = q + sz;
-                    atomicAdd(q, __float_as_int(fmaf(ex, a0, kMagic)) - kMagicBits);
-                    atomicAdd(q + 1, __float_as_int(fmaf(fx, a0, kMagic)) - kMagicBits);
-                    atomicAdd(q + kPitch, __float_as_int(fmaf(ex, a1, kMagic)) - kMagicBits);
-                    atomicAdd(q + kPitch + 1, __float_as_int(fmaf(fx, a1, kMagic)) - kMagicBits);
-                    atomicAdd(q2, __float_as_int(fmaf(ex, a2, kMagic)) - kMagicBits);
-                    atomicAdd(q2 + 1, __float_as_int(fmaf(fx, a2, kMagic)) - kMagicBits);
-                    atomicAdd(q2 + kPitch, __float_as_int(fmaf(ex, a3, kMagic)) - kMagicBits);
-                    atomicAdd(q2 + kPitch + 1, __float_as_int(fmaf(fx, a3, kMagic)) - kMagicBits);
+                    atomicAdd(q, __float_as_int(fmaf(w0, a0, kMagic)) - kMagicBits);
+                    atomicAdd(q + 1, __float_as_int(fmaf(w1, a0, kMagic)) - kMagicBits);
+                    atomicAdd(q + kPitch, __float_as_int(fmaf(w0, a1, kMagic)) - kMagicBits);
+                    atomicAdd(q + kPitch + 1, __float_as_int(fmaf(w1, a1, kMagic)) - kMagicBits);
+                    atomicAdd(q2, __float_as_int(fmaf(w0, a2, kMagic)) - kMagicBits);
+                    atomicAdd(q2 + 1, __float_as_int(fmaf(w1, a2, kMagic)) - kMagicBits);
+                    atomicAdd(q2 + kPitch, __float_as_int(fmaf(w0, a3, kMagic)) - kMagicBits);
+                    atomicAdd(q2 + kPitch + 1, __float_as_int(fmaf(w1, a3, kMagic)) - kMagicBits);
                 }
             }
             __syncthreads();
             // flush the box: lane = x, one warp per (y, z) row; one 64-bit atomic
             // per touched in-grid voxel, and re-zero it
             {
-                const int x = bx.lx + lane;
+                const int x = bx.lx + (mirror ? bx.bx - 1 - lane : lane);  // box column lane
                 const bool xin = lane < bx.bx && (unsigned)x < (unsigned)g.nx;
                 for (int zz = 0; zz < bx.bz; zz++) {
                     const int z = bx.lz + zz;
                     for (int yy = warp; yy < bx.by; yy += RPB / 32) {
-                        const int i = (zz * bx.by + yy) * kPitch + lane;
+                        const int i = zz * sz + yy * kPitch + lane;
                         if (lane >= bx.bx) continue;
                         const int v = box[i];
                         if (v == 0) continue;
@@ -290,7 +328,7 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
 }
 
 template <int CH, int RPB>
-__global__ void __launch_bounds__(RPB, 1024 / RPB) k_backproject(GridD g, int nu, int nv, int ntu, float step,
+__global__ void __launch_bounds__(RPB, 768 / RPB) k_backproject(GridD g, int nu, int nv, int ntu, float step,
                                                       const pmf_view* __restrict__ views,
                                                       const float* __restrict__ dproj, int64_t vol_stride,
                                                       unsigned long long* __restrict__ acc, const unsigned* maxbits,
@@ -318,7 +356,7 @@ __global__ void k_fixed_to_float_f(const unsigned long long* __restrict__ acc, i
 }
 
 template <int CH, int RPB>
-__global__ void __launch_bounds__(RPB, 1024 / RPB) k_backproject_batched(const __grid_constant__ ProjBatch B) {
+__global__ void __launch_bounds__(RPB, 768 / RPB) k_backproject_batched(const __grid_constant__ ProjBatch B) {
     __shared__ int box[kBox];
     __shared__ BoxState bs;
     __shared__ unsigned sgmax;

@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--rasterizer", action="store_true",
                     help="time only the Stage-1 rasterizer (gs_rasterize + gs_rasterize_backward) on --batch views")
     ap.add_argument("--uneven", action="store_true",
-                    help="time only the uneven four-volume batch (SURVEY config 3): one batched launch each way vs "
+                    help="time only the uneven four-volume batch (128^2x64 .. 256^2x128, 17 / 40 / 64 / 96 views): one batched launch each way vs "
                          "one launch pair per volume")
     return ap.parse_args()
 
@@ -220,14 +220,20 @@ KERNEL_OF = {"conebeam_project": "k_project", "conebeam_project_backward": "k_ba
              "gs_voxelize": "k_render", "gs_voxelize_backward": "k_vox_bwd", "projection_loss": "k_loss"}
 
 
-def fp32_peak():
-    """Non-tensor fp32 FMA peak: 152 SMs x 128 lanes x 2 flops x the maximum SM clock."""
-    mhz = 2070.0
+def sm_clock_mhz():
+    """The maximum SM clock the pool measured (MEASURED_PEAKS.json), else GB300's 2070 MHz."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
-        mhz = float(json.load(open(path)).get("sm_max_mhz", mhz))
-        return round(152 * 128 * 2 * mhz * 1e6 / 1e12, 3), f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz"
-    return round(152 * 128 * 2 * mhz * 1e6 / 1e12, 3), "derived (fallback clock)"
+        return float(json.load(open(path)).get("sm_max_mhz", 2070.0)), "measured"
+    return 2070.0, "fallback"
+
+
+def fp32_peak(sms: int):
+    """Non-tensor fp32 FMA peak: SMs (queried from the device) x 128 lanes x 2
+    flops x the maximum SM clock."""
+    mhz, how = sm_clock_mhz()
+    return (round(sms * 128 * 2 * mhz * 1e6 / 1e12, 3),
+            f"derived: {sms} SMs (device query) x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({how} clock)")
 
 
 def samples_per_view(grid, det, views):
@@ -373,7 +379,9 @@ def run_native(a):
     esz = torch.tensor([], dtype=dt).element_size()
     wsz = torch.tensor([], dtype=wdt).element_size()
     hbm_peak, hsrc = peaks()
-    f32_peak, fsrc = fp32_peak()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    f32_peak, fsrc = fp32_peak(sms)
+    mhz, _ = sm_clock_mhz()
     timed_views = np.concatenate([wl.views[perm][((rank * 7919 + a.warmup + k) % nbatch) * B:
                                                  ((rank * 7919 + a.warmup + k) % nbatch) * B + B]
                                   for k in range(a.steps)])
@@ -396,9 +404,10 @@ def run_native(a):
         oc = onchip_for(kernel_of.get(st, KERNEL_OF.get(st, st))) if st in FLOPS_PER_SAMPLE else None
         if oc is not None:
             ach = oc["per_sample"] * samples / sec
+            # the resource's rate per SM per clock x the device's SMs x the maximum clock
+            pk = oc["per_sm_per_clock"] * sms * mhz * 1e6
             ent["onchip"] = {"resource": oc["resource"], "achieved_per_s": round(ach, 1),
-                             "peak_per_s": oc["peak_per_s"], "frac": round(ach / oc["peak_per_s"], 4),
-                             "per_sample": oc["per_sample"]}
+                             "peak_per_s": pk, "frac": round(ach / pk, 4), "per_sample": oc["per_sample"]}
         if st in FLOPS_PER_SAMPLE:
             fl = samples * FLOPS_PER_SAMPLE[st]
             ent.update({"bound": "alu", "achieved": round(fl / sec / 1e12, 3), "peak": f32_peak, "unit": "TFLOP/s",
@@ -698,7 +707,7 @@ def run_native(a):
         del tstep, opt
         torch.cuda.empty_cache()
         if not a.small:
-            # SURVEY config 3: four volumes of different grids (128^2x64 .. 256^2x128,
+            # the uneven batch: four volumes of different grids (128^2x64 .. 256^2x128,
             # each its reference set voxelized in fp32) with 17 / 40 / 64 / 96 views,
             # projected and back-projected as one persistent launch each way, plain
             # and replayed from a CUDA graph, against one launch pair per volume
@@ -750,7 +759,7 @@ def run_native(a):
                    "batch_projections": B, "loss": "L2" if a.kind == 2 else "L1", "storage_dtype": a.dtype,
                    "warped_volume_dtype": "f32" if wdt == torch.float32 else a.dtype,
                    "accumulate_dtype": "f32", "l2_policy": "working set > L2 (E 144 MB, W and dW 512 MB each)",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}", "sm_count": sms},
         "roofline": roof, "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_rooflines": stage_roof,
         "variants_projections_per_s": variants or None,

@@ -572,7 +572,8 @@ def run_native(a):
         variants[f"native_plan_graph_autotuned_{a.dtype}"] = round(B * a.steps * world / tg, 3)
         fp_shape, bp_shape = plan.launch_forms()
         variants["autotuned_shapes"] = {"proj": list(fp_shape), "backproj": list(bp_shape),
-                                        "fields": ["form (0 grid, k persistent CTAs/SM)", "chunk", "rays"]}
+                                        "fields": ["form (0 grid, k persistent CTAs/SM)", "chunk", "rays"],
+                                        "voxel_tiles": ["x".join(map(str, t)) for t in plan.voxel_tiles()]}
         plan.close()
         del plan
         from paper_2503_22139_gb300.pipeline import PlainPerProjection
@@ -912,17 +913,23 @@ def run_uneven(a):
     bitems = [(it[0], it[1], it[2], dy, True) for it, dy in zip(items, dys)]
     nviews = sum(it[2].shape[0] for it in items)
 
-    def batched():
+    def batched_fwd():
         ops.conebeam_project_batched(items, out=ys)
+
+    def batched_adj():
         ops.conebeam_project_backward_batched(bitems, out=gs_out)
 
-    def per_volume():
-        for it, dy, y, go in zip(items, dys, ys, gs_out):
+    def per_volume_fwd():
+        for it, y in zip(items, ys):
             ops.conebeam_project(it[0], it[1], it[2], it[3], shared=True, out=y)
+
+    def per_volume_adj():
+        for it, dy, go in zip(items, dys, gs_out):
             ops.conebeam_project_backward(it[0], it[1], it[2], dy, shared=True, out=go)
 
-    res = {}
-    for name, f in (("batched", batched), ("per_volume", per_volume)):
+    ms = {}
+    for name, f in (("batched_forward", batched_fwd), ("batched_adjoint", batched_adj),
+                    ("per_volume_forward", per_volume_fwd), ("per_volume_adjoint", per_volume_adj)):
         for _ in range(a.warmup):
             f()
         torch.cuda.synchronize()
@@ -932,9 +939,10 @@ def run_uneven(a):
             f()
         e1.record()
         torch.cuda.synchronize()
-        res[name] = round(nviews * a.steps / (e0.elapsed_time(e1) / 1e3), 3)
+        ms[name] = round(e0.elapsed_time(e1) / a.steps, 3)
+    res = {k: round(nviews / ((ms[k + "_forward"] + ms[k + "_adjoint"]) / 1e3), 3) for k in ("batched", "per_volume")}
     print(json.dumps({"metric": "projections/s fwd+adjoint, uneven four-volume batch (fp32)", "value": res["batched"],
-                      "unit": "projections/s", "per_volume_launches": res["per_volume"], "steps": a.steps,
+                      "unit": "projections/s", "per_volume_launches": res["per_volume"], "ms": ms, "steps": a.steps,
                       "warmup": a.warmup, "config": {"workload": "128x128x64 / 160x160x80 / 200x200x100 / 256x256x128 "
                                                                  "@2 mm, 17/40/64/96 views of 512x384", "views": nviews}}))
 

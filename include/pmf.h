@@ -124,6 +124,20 @@ pmf_status gs_voxelize_count(const pmf_grid* grid, const pmf_gaussians* g, int64
 pmf_status gs_voxelize(const pmf_grid* grid, const pmf_gaussians* g, pmf_dtype dtype, void* out,
                        void* ws, size_t ws_bytes, pmf_stream stream);
 
+/* The same three calls with the bin tile chosen: tile = {x, y, z} voxels, one
+ * of 8x8x8 (the default of the calls above), 16x8x8, 8x8x4 or 16x8x4 (one CTA
+ * per tile, one warp per 4x4x4 sub-block).  The output does not depend on the
+ * tile, bit for bit (the sums are exact integers); only the time and the
+ * workspace do (fewer, larger tiles list each Gaussian in fewer tiles).
+ * PMF_EUNSUPPORTED for any other tile.  pmf_autotune picks one per Gaussian
+ * set for plans. */
+pmf_status gs_voxelize_tiled_workspace(const pmf_grid* grid, int64_t n, int64_t pair_capacity, const int32_t tile[3],
+                                      size_t* bytes);
+pmf_status gs_voxelize_tiled_count(const pmf_grid* grid, const pmf_gaussians* g, const int32_t tile[3],
+                                   int64_t* d_pairs, void* ws, size_t ws_bytes, pmf_stream stream);
+pmf_status gs_voxelize_tiled(const pmf_grid* grid, const pmf_gaussians* g, pmf_dtype dtype, const int32_t tile[3],
+                             void* out, void* ws, size_t ws_bytes, pmf_stream stream);
+
 /* Bytes of scratch gs_voxelize_backward needs for n Gaussians of `channels`
  * channels (0 when n is large enough that no Gaussian is split).  Host-only. */
 pmf_status gs_voxelize_backward_workspace(const pmf_grid* grid, int64_t n, int32_t channels, size_t* bytes);
@@ -291,7 +305,9 @@ typedef struct {
 
 /* conebeam_project for up to 16 volumes of different sizes and view counts in
  * one launch over the concatenated (item, view, 16x16 tile) work list, one CTA
- * per work item; fp32 volumes whose rows are 16-byte multiples are staged by
+ * per work item, the items with the longest rays (volume diagonal over the
+ * march step) first so that the launch does not end on a tail of slow tiles;
+ * fp32 volumes whose rows are 16-byte multiples are staged by
  * bulk tensor copies (one tensor map per item).  Every item uses `dtype`.
  * Results equal per-item conebeam_project calls bit for bit.  Host-side items
  * may be freed on return. */
@@ -312,7 +328,8 @@ typedef struct {
 pmf_status conebeam_project_backward_batched_workspace(int32_t n, const pmf_backproject_item* items, size_t* bytes);
 
 /* conebeam_project_backward for up to 16 items in one launch over the work
- * list (plus one batched max-reduction and one batched fixed-point conversion); each
+ * list, ordered as above (plus one batched max-reduction and one batched
+ * fixed-point conversion); each
  * item keeps its own fixed-point scale, so results equal per-item calls bit
  * for bit. */
 pmf_status conebeam_project_backward_batched(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
@@ -584,14 +601,22 @@ pmf_status pmf_plan_tensors_get(const pmf_plan* plan, pmf_plan_tensors* out);
  * chunk and rays move the last bits (chunk anchors, per-CTA scales). */
 pmf_status pmf_plan_launch_forms(const pmf_plan* plan, int32_t* proj, int32_t* backproj);
 
+/* The voxelizer bin tile the plan uses for each Gaussian set (the reference
+ * set, then the MBC levels): tiles[3 (1 + levels)] = {x, y, z} per set.
+ * Defaults 8x8x8, or the autotuner's choice from tune_cache.  Every tile gives
+ * the same bits (see gs_voxelize_tiled). */
+pmf_status pmf_plan_voxel_tiles(const pmf_plan* plan, int32_t* tiles);
+
 /* Synchronizes the device, frees the plan's memory and graph.  NULL is a no-op. */
 pmf_status pmf_plan_destroy(pmf_plan* plan);
 
 /* Times the projector and its adjoint over launch shapes (forms 0, 1, 2, 4
  * CTAs per 1024 SM threads; chunks of 16 and 32 samples; 128 and 256 rays per
- * CTA) on desc's data (a temporary plan; CUDA events, best of 3 after a
- * warm-up) and records the fastest of each in `cache_path` under a key made
- * of the device name, SM count, grid, detector, batch, levels and dtype
+ * CTA) and each Gaussian set's voxelization over the bin tiles of
+ * gs_voxelize_tiled, on desc's data (a temporary plan; CUDA events, best of 3
+ * after a warm-up; the tile search allocates its own scratch), and records the
+ * fastest of each in `cache_path` under a key made of the device name, SM
+ * count, grid, detector, batch, levels, dtype and the sets' Gaussian counts
  * (other keys in the file are kept).  Synchronizes. */
 pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path);
 

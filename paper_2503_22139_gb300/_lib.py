@@ -87,6 +87,9 @@ SIGNATURES = {
     "gs_voxelize_workspace": [_G, _I64, _I64, _SZ],
     "gs_voxelize_count": [_G, ct.POINTER(PmfGaussians), _P, _P, ct.c_size_t, _P],
     "gs_voxelize": [_G, ct.POINTER(PmfGaussians), ct.c_int, _P, _P, ct.c_size_t, _P],
+    "gs_voxelize_tiled_workspace": [_G, _I64, _I64, ct.POINTER(ct.c_int32), _SZ],
+    "gs_voxelize_tiled_count": [_G, ct.POINTER(PmfGaussians), ct.POINTER(ct.c_int32), _P, _P, ct.c_size_t, _P],
+    "gs_voxelize_tiled": [_G, ct.POINTER(PmfGaussians), ct.c_int, ct.POINTER(ct.c_int32), _P, _P, ct.c_size_t, _P],
     "gs_voxelize_backward_workspace": [_G, _I64, _I32, _SZ],
     "pmf_shift_means": [_I64, _P, _P, _P, _P],
     "gs_grad_norm_accumulate": [_I64, _P, _P, _P],
@@ -135,6 +138,7 @@ SIGNATURES = {
     "pmf_plan_step": [_P, _P],
     "pmf_plan_tensors_get": [_P, ct.POINTER(PmfPlanTensors)],
     "pmf_plan_launch_forms": [_P, ct.POINTER(_I32), ct.POINTER(_I32)],
+    "pmf_plan_voxel_tiles": [_P, ct.POINTER(_I32)],
     "pmf_plan_destroy": [_P],
     "pmf_autotune": [ct.POINTER(PmfBatchDesc), ct.c_char_p],
 }

@@ -363,10 +363,10 @@ __global__ void __launch_bounds__(RPB, 768 / RPB) k_backproject_batched(const __
     __shared__ float gsum[RPB / 32];
     for (int i = threadIdx.x; i < kBox; i += RPB) box[i] = 0;
     for (int64_t w = blockIdx.x; w < B.total; w += gridDim.x) {
-        const ProjItem& it = B.it[find_item(B, w)];
-        const int64_t local = w - it.begin;
+        const ProjItem it = B.it[find_item(B, w)];  // a copy: the tile code reads registers, not the parameter block
+        const int local = (int)(w - it.begin);  // < 2^31: checked when the item is filled
         backproject_tile<CH, RPB>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, it.dproj, it.vol_stride, it.acc, it.maxbits,
-                         it.bound_mult, it.spv, (int)(local / it.ntiles), (int)(local % it.ntiles), box, bs, sgmax,
+                         it.bound_mult, it.spv, local / it.ntiles, local % it.ntiles, box, bs, sgmax,
                          gsum);
         __syncthreads();
     }
@@ -440,12 +440,14 @@ pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items
     B.n = n;
     int64_t total = 0, maxq = 0, maxcells = 0;
     char* cur = (char*)ws;
-    for (int i = 0; i < n; i++) {
-        const pmf_backproject_item& in = items[i];
+    int ord[kMaxItems];
+    longest_first(n, items, ord);  // work-list position k holds item ord[k]
+    for (int k = 0; k < n; k++) {
+        const pmf_backproject_item& in = items[ord[k]];
         pmf_project_item tmp{in.grid, in.det, in.P, in.views, nullptr, in.vol_stride, nullptr};
-        if ((st = fill_item(tmp, total, sh.rays, B.it[i])) != PMF_OK) return st;
-        PMF_REQUIRE(in.d_vol != nullptr && (in.P == 0 || in.d_proj != nullptr), "item %d: null pointer", i);
-        ProjItem& it = B.it[i];
+        if ((st = fill_item(tmp, total, sh.rays, B.it[k])) != PMF_OK) return st;
+        PMF_REQUIRE(in.d_vol != nullptr && (in.P == 0 || in.d_proj != nullptr), "item %d: null pointer", ord[k]);
+        ProjItem& it = B.it[k];
         const int64_t Q = (int64_t)in.det.nu * in.det.nv;
         const double rays = (double)Q * (in.vol_stride ? 1.0 : (double)in.P);
         it.bound_mult = (float)((double)in.det.step_mm * rays * (double)max_samples_per_voxel(&in.grid, in.det.step_mm));

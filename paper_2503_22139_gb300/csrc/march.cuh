@@ -418,6 +418,27 @@ unsigned persistent_ctas(int64_t total, unsigned ctas, int rays, const int* ntil
     return ctas;
 }
 
+// Order of a batch's items in the work list: longest rays first (the volume's
+// diagonal over the step bounds the samples per ray), so the tiles that take
+// longest start first and the launch does not end on a tail of them.  Stable;
+// results do not depend on the order.
+template <typename Item>
+void longest_first(int n, const Item* items, int* ord) {
+    double len[kMaxItems];
+    for (int i = 0; i < n; i++) {
+        const pmf_grid& g = items[i].grid;
+        const double ex = (double)g.nx * g.vx, ey = (double)g.ny * g.vy, ez = (double)g.nz * g.vz;
+        len[i] = sqrt(ex * ex + ey * ey + ez * ez) / (double)items[i].det.step_mm;
+        ord[i] = i;
+    }
+    for (int i = 1; i < n; i++)
+        for (int j = i; j > 0 && len[ord[j]] > len[ord[j - 1]]; j--) {
+            const int t = ord[j];
+            ord[j] = ord[j - 1];
+            ord[j - 1] = t;
+        }
+}
+
 pmf_status fill_item(const pmf_project_item& in, int64_t begin, int rays, ProjItem& it) {
     pmf_status st = check_proj(&in.grid, &in.det, in.P, in.views);
     if (st != PMF_OK) return st;
@@ -427,6 +448,7 @@ pmf_status fill_item(const pmf_project_item& in, int64_t begin, int rays, ProjIt
     it.nu = in.det.nu; it.nv = in.det.nv;
     it.ntu = (in.det.nu + 15) / 16;
     it.ntiles = it.ntu * tiles_v(in.det.nv, rays);
+    PMF_REQUIRE((int64_t)it.ntiles * in.P < ((int64_t)1 << 31), "an item's views x pixel tiles must be below 2^31");
     it.P = in.P;
     it.step = in.det.step_mm;
     it.views = in.views;

@@ -1,5 +1,5 @@
-// Training-step plans (pmf_plan_*) and the projector launch-form autotuner
-// (pmf_autotune).  A plan composes this library's entry points into one
+// Training-step plans (pmf_plan_*) and the autotuner (pmf_autotune) of the
+// projectors' launch shapes and the voxelizer's bin tiles.  A plan composes this library's entry points into one
 // forward + adjoint step of Stages 2-3 (Sec. 2.3.2):
 //   V = voxelize(ref) (Eq. 4-5), E_l = voxelize(mbc_l) (Sec. 2.3.1),
 //   W = warp_combine(V, E, w) (Eq. 3 + Eq. 2), Y = project(W) (Eq. 6),
@@ -43,6 +43,7 @@ struct pmf_plan {
     void* norm_ws = nullptr;
     size_t norm_bytes = 0;
     pmf::MarchShape fp, bp;  // launch shapes of the projector and its adjoint
+    int32_t tile[1 + PMF_MAX_LEVELS][3] = {};  // voxelizer bin tile per Gaussian set (reference, then MBC levels)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     // the MBC levels' voxelizer calls and adjoints run on their own streams
@@ -95,8 +96,9 @@ pmf_status check_desc(const pmf_batch_desc* d) {
     return PMF_OK;
 }
 
-// Key of a configuration in the tuning cache: device, SM count and the plan's
-// shapes (the launch forms do not depend on the data).
+// Key of a configuration in the tuning cache: device, SM count, the plan's
+// shapes and the Gaussian counts (the launch forms do not depend on the data;
+// the voxelizer's bin tile depends on the sets' sizes).
 std::string tune_key(const pmf_batch_desc& d) {
     int dev = 0, sms = 0;
     cudaDeviceProp prop;
@@ -108,10 +110,13 @@ std::string tune_key(const pmf_batch_desc& d) {
     for (char& c : name)
         if (c == ' ' || c == '\t') c = '_';
     char buf[512];
-    snprintf(buf, sizeof(buf), "dev=%s;sm=%d;grid=%dx%dx%d@%g,%g,%g;det=%dx%d@%g;B=%d;L=%d;dtype=%d;w=%d", name.c_str(), sms,
-             d.grid.nx, d.grid.ny, d.grid.nz, (double)d.grid.vx, (double)d.grid.vy, (double)d.grid.vz, d.det.nu,
-             d.det.nv, (double)d.det.step_mm, d.batch, d.levels, (int)d.dtype, (int)d.w_dtype);
-    return buf;
+    snprintf(buf, sizeof(buf), "dev=%s;sm=%d;grid=%dx%dx%d@%g,%g,%g;det=%dx%d@%g;B=%d;L=%d;dtype=%d;w=%d;n=%lld",
+             name.c_str(), sms, d.grid.nx, d.grid.ny, d.grid.nz, (double)d.grid.vx, (double)d.grid.vy,
+             (double)d.grid.vz, d.det.nu, d.det.nv, (double)d.det.step_mm, d.batch, d.levels, (int)d.dtype,
+             (int)d.w_dtype, (long long)d.ref.n);
+    std::string key = buf;
+    for (int l = 0; l < d.levels; l++) key += "," + std::to_string((long long)d.mbc[l].n);
+    return key;
 }
 
 std::vector<std::string> read_lines(const char* path) {
@@ -132,22 +137,43 @@ bool valid(const MarchShape& m) {
     return m.form >= 0 && m.form <= 16 && (m.chunk == 16 || m.chunk == 32) && (m.rays == 128 || m.rays == 256);
 }
 
-// "<key> proj=<form>,<chunk>,<rays> backproj=<form>,<chunk>,<rays>"
-bool cache_lookup(const char* path, const std::string& key, MarchShape& fp, MarchShape& bp) {
+bool valid_tile(const int32_t* t) {
+    return (t[0] == 8 || t[0] == 16) && t[1] == 8 && (t[2] == 8 || t[2] == 4);
+}
+
+// "<key> proj=<form>,<chunk>,<rays> backproj=<form>,<chunk>,<rays>[ vox=<x>x<y>x<z>,...]" (one tile per set)
+bool cache_lookup(const char* path, const std::string& key, int sets, MarchShape& fp, MarchShape& bp,
+                  int32_t (*tile)[3]) {
     for (const std::string& s : read_lines(path)) {
         if (s.compare(0, key.size(), key) != 0 || s.size() <= key.size() || s[key.size()] != ' ') continue;
         MarchShape a, b;
-        if (sscanf(s.c_str() + key.size(), " proj=%d,%d,%d backproj=%d,%d,%d", &a.form, &a.chunk, &a.rays, &b.form,
-                   &b.chunk, &b.rays) == 6 && valid(a) && valid(b)) {
-            fp = a;
-            bp = b;
-            return true;
+        int used = 0;
+        if (sscanf(s.c_str() + key.size(), " proj=%d,%d,%d backproj=%d,%d,%d%n", &a.form, &a.chunk, &a.rays, &b.form,
+                   &b.chunk, &b.rays, &used) != 6 || !valid(a) || !valid(b))
+            continue;
+        int32_t t[1 + PMF_MAX_LEVELS][3];
+        memcpy(t, tile, sizeof(int32_t) * 3 * (size_t)sets);  // a line without vox= keeps the caller's tiles
+        const char* c = s.c_str() + key.size() + used;
+        const bool has = strncmp(c, " vox=", 5) == 0;
+        bool ok = true;
+        c += has ? 5 : 0;
+        for (int i = 0; i < sets && ok && has; i++) {
+            int n = 0;
+            ok = sscanf(c, i == 0 ? "%dx%dx%d%n" : ",%dx%dx%d%n", &t[i][0], &t[i][1], &t[i][2], &n) == 3 &&
+                 valid_tile(t[i]);
+            c += n;
         }
+        if (!ok) continue;
+        fp = a;
+        bp = b;
+        memcpy(tile, t, sizeof(int32_t) * 3 * (size_t)sets);
+        return true;
     }
     return false;
 }
 
-pmf_status cache_store(const char* path, const std::string& key, const MarchShape& fp, const MarchShape& bp) {
+pmf_status cache_store(const char* path, const std::string& key, const MarchShape& fp, const MarchShape& bp, int sets,
+                       const int32_t (*tile)[3]) {
     std::vector<std::string> lines = read_lines(path);
     std::string tmp = std::string(path) + ".tmp";
     FILE* f = fopen(tmp.c_str(), "w");
@@ -155,8 +181,10 @@ pmf_status cache_store(const char* path, const std::string& key, const MarchShap
     for (const std::string& s : lines)
         if (!(s.compare(0, key.size(), key) == 0 && s.size() > key.size() && s[key.size()] == ' '))
             fprintf(f, "%s\n", s.c_str());
-    fprintf(f, "%s proj=%d,%d,%d backproj=%d,%d,%d\n", key.c_str(), fp.form, fp.chunk, fp.rays, bp.form, bp.chunk,
+    fprintf(f, "%s proj=%d,%d,%d backproj=%d,%d,%d vox=", key.c_str(), fp.form, fp.chunk, fp.rays, bp.form, bp.chunk,
             bp.rays);
+    for (int i = 0; i < sets; i++) fprintf(f, "%s%dx%dx%d", i ? "," : "", tile[i][0], tile[i][1], tile[i][2]);
+    fprintf(f, "\n");
     if (fclose(f) != 0 || rename(tmp.c_str(), path) != 0) return set_error(PMF_EINVAL, "cannot write %s", path);
     return PMF_OK;
 }
@@ -193,11 +221,11 @@ pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
     PMF_TRY_CUDA(cudaEventRecord(p->fork, s), "cudaEventRecord");
     for (int l = 0; l < p->L; l++) {
         PMF_TRY_CUDA(cudaStreamWaitEvent(p->side[l], p->fork, 0), "cudaStreamWaitEvent");
-        PMF_TRY(gs_voxelize(&d.grid, &d.mbc[l], d.dtype, (char*)p->E + (size_t)l * 3 * N * p->elt, p->vox_ws[1 + l],
-                            p->vox_bytes[1 + l], (pmf_stream)p->side[l]));
+        PMF_TRY(gs_voxelize_tiled(&d.grid, &d.mbc[l], d.dtype, p->tile[1 + l], (char*)p->E + (size_t)l * 3 * N * p->elt,
+                                  p->vox_ws[1 + l], p->vox_bytes[1 + l], (pmf_stream)p->side[l]));
         PMF_TRY_CUDA(cudaEventRecord(p->join[l], p->side[l]), "cudaEventRecord");
     }
-    PMF_TRY(gs_voxelize(&d.grid, &d.ref, d.dtype, p->V, p->vox_ws[0], p->vox_bytes[0], ps));
+    PMF_TRY(gs_voxelize_tiled(&d.grid, &d.ref, d.dtype, p->tile[0], p->V, p->vox_ws[0], p->vox_bytes[0], ps));
     for (int l = 0; l < p->L; l++) PMF_TRY_CUDA(cudaStreamWaitEvent(s, p->join[l], 0), "cudaStreamWaitEvent");
     PMF_TRY(warp_combine_mixed(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, d.w_dtype, p->W, ps));
     PMF_TRY(plan_project(p, s));
@@ -234,12 +262,12 @@ pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
 // Pair-list capacity of each voxelizer: the exact (Gaussian, tile) overlap
 // count of the current parameters with 25% headroom (overflow later is still
 // correct, only slower; PMF_DIAG_VOXELIZE_LIST_OVERFLOW counts it).
-pmf_status pair_capacities(const pmf_batch_desc& d, int64_t* cap) {
+pmf_status pair_capacities(const pmf_batch_desc& d, const int32_t (*tile)[3], int64_t* cap) {
     const int sets = 1 + d.levels;
     size_t need = 0;
     for (int i = 0; i < sets; i++) {
         size_t b;
-        PMF_TRY(gs_voxelize_workspace(&d.grid, gset(d, i).n, 0, &b));
+        PMF_TRY(gs_voxelize_tiled_workspace(&d.grid, gset(d, i).n, 0, tile[i], &b));
         need = b > need ? b : need;
     }
     char* tmp = nullptr;
@@ -252,7 +280,7 @@ pmf_status pair_capacities(const pmf_batch_desc& d, int64_t* cap) {
     }
     int64_t* d_pairs = (int64_t*)(tmp + need);
     for (int i = 0; i < sets && st == PMF_OK; i++) {
-        st = gs_voxelize_count(&d.grid, &gset(d, i), d_pairs, tmp, need, (pmf_stream)s);
+        st = gs_voxelize_tiled_count(&d.grid, &gset(d, i), tile[i], d_pairs, tmp, need, (pmf_stream)s);
         int64_t h = 0;
         if (st == PMF_OK && cudaMemcpyAsync(&h, d_pairs, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             st = set_error(PMF_ECUDA, "pair count copy failed");
@@ -278,8 +306,14 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     p->Q = (int64_t)desc->det.nu * desc->det.nv;
     const pmf_batch_desc& d = p->d;
     const int sets = 1 + p->L;
+    for (int i = 0; i < sets; i++) {
+        p->tile[i][0] = 8;
+        p->tile[i][1] = 8;
+        p->tile[i][2] = 8;
+    }
+    if (desc->tune_cache) cache_lookup(desc->tune_cache, tune_key(d), sets, p->fp, p->bp, p->tile);
     int64_t cap[1 + PMF_MAX_LEVELS];
-    pmf_status st = pair_capacities(d, cap);
+    pmf_status st = pair_capacities(d, p->tile, cap);
     if (st != PMF_OK) {
         delete p;
         return st;
@@ -296,7 +330,7 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     sz.push_back(N * 4);                      // dV
     sz.push_back(L * 3 * N * 4);              // dE
     for (int i = 0; i < sets && st == PMF_OK; i++) {
-        st = gs_voxelize_workspace(&d.grid, gset(d, i).n, cap[i], &p->vox_bytes[i]);
+        st = gs_voxelize_tiled_workspace(&d.grid, gset(d, i).n, cap[i], p->tile[i], &p->vox_bytes[i]);
         if (st == PMF_OK) st = gs_voxelize_backward_workspace(&d.grid, gset(d, i).n, gset(d, i).channels, &p->vb_bytes[i]);
     }
     if (st == PMF_OK) st = conebeam_project_backward_workspace(&d.grid, p->B, p->N, &p->bp_bytes);
@@ -350,7 +384,6 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     p->ssim_ws = take();
     p->tv_ws = take();
     p->norm_ws = take();
-    if (desc->tune_cache) cache_lookup(desc->tune_cache, tune_key(d), p->fp, p->bp);
     bool ok = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess;
     for (int l = 0; l < p->L && ok; l++)
         ok = cudaStreamCreateWithFlags(&p->side[l], cudaStreamNonBlocking) == cudaSuccess &&
@@ -394,6 +427,45 @@ float time_ms(cudaStream_t s, int reps, pmf_status (*fn)(pmf_plan*, cudaStream_t
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    return best;
+}
+
+// Best of `reps` timed voxelizations of Gaussian set i with bin tile `tile`,
+// after one warm-up; the workspace holds the tile's exact pair count (+25%)
+// and the output goes to the plan's own V or E slice.
+float time_voxelize(pmf_plan* p, int i, const int32_t tile[3], cudaStream_t s, int reps, pmf_status& st) {
+    const pmf_batch_desc& d = p->d;
+    const pmf_gaussians& gs = gset(d, i);
+    void* out = i == 0 ? p->V : (char*)p->E + (size_t)(i - 1) * 3 * (size_t)p->N * p->elt;
+    float best = 3.0e38f;
+    size_t fixed = 0, need = 0;
+    st = gs_voxelize_tiled_workspace(&d.grid, gs.n, 0, tile, &fixed);
+    char* ws = nullptr;
+    if (st == PMF_OK && cudaMalloc(&ws, fixed + 256) != cudaSuccess) st = set_error(PMF_ECUDA, "cudaMalloc failed");
+    int64_t pairs = 0;
+    if (st == PMF_OK) st = gs_voxelize_tiled_count(&d.grid, &gs, tile, (int64_t*)(ws + fixed), ws, fixed, (pmf_stream)s);
+    if (st == PMF_OK && (cudaMemcpyAsync(&pairs, ws + fixed, sizeof(pairs), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                         cudaStreamSynchronize(s) != cudaSuccess))
+        st = set_error(PMF_ECUDA, "pair count failed");
+    if (ws) cudaFree(ws);
+    ws = nullptr;
+    if (st == PMF_OK) st = gs_voxelize_tiled_workspace(&d.grid, gs.n, pairs + pairs / 4 + 4096, tile, &need);
+    if (st == PMF_OK && cudaMalloc(&ws, need) != cudaSuccess) st = set_error(PMF_ECUDA, "cudaMalloc failed");
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    for (int r = -1; r < reps && st == PMF_OK; r++) {
+        cudaEventRecord(a, s);
+        st = gs_voxelize_tiled(&d.grid, &gs, d.dtype, tile, out, ws, need, (pmf_stream)s);
+        cudaEventRecord(b, s);
+        if (cudaEventSynchronize(b) != cudaSuccess) st = set_error(PMF_ECUDA, "timing failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (r >= 0) best = ms < best ? ms : best;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (ws) cudaFree(ws);
     return best;
 }
 
@@ -494,12 +566,34 @@ pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path) {
                 t = time_ms(s, 3, plan_backproject, p, st);
                 if (st == PMF_OK && t < best_bp) { best_bp = t; bp = m; }
             }
+    // the voxelizer's bin tile, per Gaussian set
+    const int sets = 1 + d.levels;
+    const int32_t cand[4][3] = {{8, 8, 8}, {16, 8, 8}, {8, 8, 4}, {16, 8, 4}};
+    int32_t tile[1 + PMF_MAX_LEVELS][3];
+    for (int i = 0; i < sets; i++) {
+        float best = 3.0e38f;
+        memcpy(tile[i], cand[0], sizeof(cand[0]));
+        for (int c = 0; c < 4 && st == PMF_OK; c++) {
+            const float t = time_voxelize(p, i, cand[c], s, 3, st);
+            if (st == PMF_OK && t < best) {
+                best = t;
+                memcpy(tile[i], cand[c], sizeof(cand[c]));
+            }
+        }
+    }
     if (st == PMF_OK && cudaStreamSynchronize(s) != cudaSuccess) st = set_error(PMF_ECUDA, "autotune failed");
     const std::string key = tune_key(d);
     cudaStreamDestroy(s);
     plan_free(p);
     if (st != PMF_OK) return st;
-    return cache_store(cache_path, key, fp, bp);
+    return cache_store(cache_path, key, fp, bp, sets, tile);
+}
+
+pmf_status pmf_plan_voxel_tiles(const pmf_plan* p, int32_t* tiles) {
+    PMF_REQUIRE(p != nullptr && tiles != nullptr, "null pointer");
+    for (int i = 0; i <= p->L; i++)
+        for (int k = 0; k < 3; k++) tiles[3 * i + k] = p->tile[i][k];
+    return PMF_OK;
 }
 
 }  // extern "C"

@@ -338,9 +338,9 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched_tma(const _
     for (int64_t w = blockIdx.x; w < T.B.total; w += gridDim.x) {
         const int i = find_item(T.B, w);
         const ProjItem& it = T.B.it[i];
-        const int64_t local = w - it.begin;
+        const int local = (int)(w - it.begin);  // < 2^31: checked when the item is filled
         if (!project_tile_tma<CH, RPB>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, &T.map[i], (const float*)it.vol,
-                                       it.vol_stride, it.proj, (int)(local / it.ntiles), (int)(local % it.ntiles), box,
+                                       it.vol_stride, it.proj, local / it.ntiles, local % it.ntiles, box,
                                        &bar, bs, parity))
             return;
         __syncthreads();
@@ -352,10 +352,10 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched(const __gri
     __shared__ float box[kBox];
     __shared__ BoxState bs;
     for (int64_t w = blockIdx.x; w < B.total; w += gridDim.x) {
-        const ProjItem& it = B.it[find_item(B, w)];
-        const int64_t local = w - it.begin;
+        const ProjItem it = B.it[find_item(B, w)];  // a copy: the tile code reads registers, not the parameter block
+        const int local = (int)(w - it.begin);  // < 2^31: checked when the item is filled
         project_tile<T, CH, RPB>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, (const T*)it.vol, it.vol_stride, it.proj,
-                        (int)(local / it.ntiles), (int)(local % it.ntiles), box, bs);
+                        local / it.ntiles, local % it.ntiles, box, bs);
         __syncthreads();
     }
 }
@@ -424,12 +424,15 @@ pmf_status project_batched_impl(int32_t n, const pmf_project_item* items, pmf_dt
     ProjBatch B{};
     B.n = n;
     int64_t total = 0;
-    for (int i = 0; i < n; i++) {
-        if ((st = fill_item(items[i], total, sh.rays, B.it[i])) != PMF_OK) return st;
-        PMF_REQUIRE(items[i].P == 0 || (items[i].vol && items[i].proj), "item %d: null pointer", i);
-        B.it[i].vol = items[i].vol;
-        B.it[i].proj = items[i].proj;
-        total += (int64_t)B.it[i].ntiles * items[i].P;
+    int ord[kMaxItems];
+    longest_first(n, items, ord);  // work-list position k holds item ord[k]
+    for (int k = 0; k < n; k++) {
+        const pmf_project_item& in = items[ord[k]];
+        if ((st = fill_item(in, total, sh.rays, B.it[k])) != PMF_OK) return st;
+        PMF_REQUIRE(in.P == 0 || (in.vol && in.proj), "item %d: null pointer", ord[k]);
+        B.it[k].vol = in.vol;
+        B.it[k].proj = in.proj;
+        total += (int64_t)B.it[k].ntiles * in.P;
     }
     B.total = total;
     if (total == 0) return PMF_OK;
@@ -439,9 +442,10 @@ pmf_status project_batched_impl(int32_t n, const pmf_project_item* items, pmf_dt
     if (sh.tma && dtype == PMF_F32) {
         ProjBatchTma tb{};
         bool all = true;
-        for (int i = 0; i < n && all; i++)
-            all = items[i].P == 0 || encode_volume_map(&tb.map[i], (const float*)items[i].vol, &items[i].grid,
-                                                       items[i].P, items[i].vol_stride);
+        for (int k = 0; k < n && all; k++) {
+            const pmf_project_item& in = items[ord[k]];
+            all = in.P == 0 || encode_volume_map(&tb.map[k], (const float*)in.vol, &in.grid, in.P, in.vol_stride);
+        }
         if (all) {
             tb.B = B;
             PMF_DISPATCH_MARCH(sh, CH, RPB, k_project_batched_tma<CH, RPB><<<nc, RPB, 0, s>>>(tb));

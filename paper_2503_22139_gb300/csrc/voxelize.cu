@@ -20,8 +20,20 @@
 namespace pmf {
 namespace {
 
-constexpr int kTile = 8;              // tile edge (voxels)
-constexpr int kRenderThreads = 256;   // 2 voxels per thread
+// Bin tiles: the render takes one CTA per tile of TX x TY x TZ voxels, each
+// warp a 4 x 4 x 4 sub-block (two voxels per lane), so a tile has
+// TX TY TZ / 2 threads; at most 512, so that a batch of that many rounded terms
+// stays below 2^30 in 32 bits.  8^3 is the default; plans may take another
+// from the autotuner.  Every tile gives the same bits (the sums are exact).
+struct VoxTile {
+    int x, y, z;
+};
+constexpr VoxTile kDefaultTile{8, 8, 8};
+
+bool supported_tile(const VoxTile& t) {
+    return (t.x == 8 && t.y == 8 && t.z == 8) || (t.x == 16 && t.y == 8 && t.z == 8) ||
+           (t.x == 8 && t.y == 8 && t.z == 4) || (t.x == 16 && t.y == 8 && t.z == 4);
+}
 constexpr int kMaxC = 4;
 constexpr float kNegHalfLog2e = -0.72134752044448170368f;  // -log2(e)/2
 constexpr float kMagicF = 12582912.0f;  // 1.5 * 2^23: x + kMagicF rounds x to an integer for |x| < 2^22
@@ -61,8 +73,8 @@ struct TileGeom {
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-size_t vox_ws_layout(const GridD& g, int64_t G, int64_t capacity, VoxWs* w, char* base) {
-    int tx = ceil_div(g.nx, kTile), ty = ceil_div(g.ny, kTile), tz = ceil_div(g.nz, kTile);
+size_t vox_ws_layout(const GridD& g, int64_t G, int64_t capacity, const VoxTile& tl, VoxWs* w, char* base) {
+    int tx = ceil_div(g.nx, tl.x), ty = ceil_div(g.ny, tl.y), tz = ceil_div(g.nz, tl.z);
     int64_t T = (int64_t)tx * ty * tz;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return base ? base + o : nullptr; };
@@ -143,7 +155,7 @@ __device__ __forceinline__ float centre(int i, int n, float v) {
 // ------------------------------------------------------------- forward
 
 // One warp per Gaussian: lane 0 stores the setup, all lanes count tiles.
-__global__ void k_prep(pmf_gaussians G, GridD g, float kappa, VoxWs w, int ntx, int nty) {
+__global__ void k_prep(pmf_gaussians G, GridD g, float kappa, VoxWs w, VoxTile tl, int ntx, int nty) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= G.n) return;
@@ -162,8 +174,8 @@ __global__ void k_prep(pmf_gaussians G, GridD g, float kappa, VoxWs w, int ntx, 
         if (m) atomicMax(&w.hdr->max_abs_bits, m);
     }
     if (s.lo[0] > s.hi[0] || s.lo[1] > s.hi[1] || s.lo[2] > s.hi[2]) return;
-    const int t0x = s.lo[0] / kTile, t1x = s.hi[0] / kTile, t0y = s.lo[1] / kTile, t1y = s.hi[1] / kTile,
-              t0z = s.lo[2] / kTile, t1z = s.hi[2] / kTile;
+    const int t0x = s.lo[0] / tl.x, t1x = s.hi[0] / tl.x, t0y = s.lo[1] / tl.y, t1y = s.hi[1] / tl.y,
+              t0z = s.lo[2] / tl.z, t1z = s.hi[2] / tl.z;
     const int ex = t1x - t0x + 1, ey = t1y - t0y + 1, ez = t1z - t0z + 1;
     const int cnt = ex * ey * ez;
     for (int c = lane; c < cnt; c += 32) {
@@ -196,15 +208,15 @@ __global__ void k_scan(VoxWs w, int64_t T) {
     if (tid == 1023) w.toff[T] = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
 }
 
-__global__ void k_fill(int64_t n, VoxWs w, int ntx, int nty) {
+__global__ void k_fill(int64_t n, VoxWs w, VoxTile tl, int ntx, int nty) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
     int lo[3], hi[3];
     for (int a = 0; a < 3; a++) { lo[a] = w.box[a * n + i]; hi[a] = w.box[(3 + a) * n + i]; }
     if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2]) return;
-    const int t0x = lo[0] / kTile, t0y = lo[1] / kTile, t0z = lo[2] / kTile;
-    const int ex = hi[0] / kTile - t0x + 1, ey = hi[1] / kTile - t0y + 1, ez = hi[2] / kTile - t0z + 1;
+    const int t0x = lo[0] / tl.x, t0y = lo[1] / tl.y, t0z = lo[2] / tl.z;
+    const int ex = hi[0] / tl.x - t0x + 1, ey = hi[1] / tl.y - t0y + 1, ez = hi[2] / tl.z - t0z + 1;
     const int cnt = ex * ey * ez;
     for (int c = lane; c < cnt; c += 32) {
         int x = t0x + c % ex, y = t0y + (c / ex) % ey, z = t0z + c / (ex * ey);
@@ -215,20 +227,24 @@ __global__ void k_fill(int64_t n, VoxWs w, int ntx, int nty) {
     }
 }
 
-template <typename T, int C>
-__global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, GridD g, VoxWs w, T* out, int ntx,
-                                                           int nty) {
-    __shared__ float sm[10][kRenderThreads];
-    __shared__ float sv[C][kRenderThreads];
-    __shared__ unsigned sidx[kRenderThreads];
-    __shared__ unsigned socc[kRenderThreads];  // octants of the tile each staged Gaussian's box touches
+template <typename T, int C, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ / 2) k_render(pmf_gaussians G, GridD g, VoxWs w, T* out, int ntx,
+                                                             int nty) {
+    constexpr int NT = TX * TY * TZ / 2;              // threads: two voxels each
+    constexpr int SX = TX / 4, SY = TY / 4, SZ = TZ / 4;  // 4^3 sub-blocks per axis, one per warp
+    static_assert(TX % 4 == 0 && TY % 4 == 0 && TZ % 4 == 0 && NT <= 512 && SX * SY * SZ <= 32, "bin tile");
+    __shared__ float sm[10][NT];
+    __shared__ float sv[C][NT];
+    __shared__ unsigned sidx[NT];
+    __shared__ unsigned socc[NT];  // sub-blocks of the tile each staged Gaussian's box touches
     __shared__ int scount;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t t = blockIdx.x;
     const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ((int64_t)ntx * nty));
-    // warp w takes octant w of the 8^3 tile (a 4^3 cube); each lane two voxels
-    const int ix = tx * kTile + 4 * (warp & 1) + (lane & 3), iy = ty * kTile + 4 * ((warp >> 1) & 1) + ((lane >> 2) & 3);
-    const int iz0 = tz * kTile + 4 * (warp >> 2) + (lane >> 4), iz1 = iz0 + 2;
+    // warp w takes sub-block w of the tile (a 4^3 cube); each lane two voxels
+    const int wx = warp % SX, wy = (warp / SX) % SY, wz = warp / (SX * SY);
+    const int ix = tx * TX + 4 * wx + (lane & 3), iy = ty * TY + 4 * wy + ((lane >> 2) & 3);
+    const int iz0 = tz * TZ + 4 * wz + (lane >> 4), iz1 = iz0 + 2;
     const float cx = centre(ix, g.nx, g.vx), cy = centre(iy, g.ny, g.vy);
     const float cz0 = centre(iz0, g.nz, g.vz), cz1 = centre(iz1, g.nz, g.vz);
 
@@ -236,7 +252,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
     const bool bad = !isfinite(maxabs);  // a NaN or infinite value: the output is NaN
     if (bad && t == 0 && tid == 0) diag_count(PMF_DIAG_NONFINITE);
     // every term |value e^{-q/2}| 2^k < 2^21, so it rounds with the magic add
-    // and a 256-term batch stays below 2^29 in 32 bits
+    // and a batch of at most 512 terms stays below 2^30 in 32 bits
     const int kexp = term_exponent(maxabs);
     const float scale = ldexpf(1.0f, kexp), inv_scale = ldexpf(1.0f, -kexp);
 
@@ -251,8 +267,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
     if (!listed && tid == 0) diag_count(PMF_DIAG_VOXELIZE_LIST_OVERFLOW);
     // Listed tiles walk their own list; overflowed tiles scan every Gaussian's box.
     const int64_t total = listed ? (int64_t)cnt : n;
-    const int x0 = tx * kTile, y0 = ty * kTile, z0 = tz * kTile;
-    for (int64_t base = 0; base < total; base += kRenderThreads) {
+    const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+    for (int64_t base = 0; base < total; base += NT) {
         __syncthreads();
         if (tid == 0) scount = 0;
         __syncthreads();
@@ -267,8 +283,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
                 gi = (unsigned)k;
                 int lx = w.box[k], ly = w.box[n + k], lz = w.box[2 * n + k];
                 int hx = w.box[3 * n + k], hy = w.box[4 * n + k], hz = w.box[5 * n + k];
-                take = lx <= hx && ly <= hy && lz <= hz && lx <= x0 + kTile - 1 && hx >= x0 && ly <= y0 + kTile - 1 &&
-                       hy >= y0 && lz <= z0 + kTile - 1 && hz >= z0;
+                take = lx <= hx && ly <= hy && lz <= hz && lx <= x0 + TX - 1 && hx >= x0 && ly <= y0 + TY - 1 &&
+                       hy >= y0 && lz <= z0 + TZ - 1 && hz >= z0;
             }
             if (take) {
                 int slot = listed ? tid : atomicAdd(&scount, 1);
@@ -276,7 +292,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
             }
         }
         if (listed) {
-            if (tid == 0) scount = (int)((total - base) < kRenderThreads ? (total - base) : kRenderThreads);
+            if (tid == 0) scount = (int)((total - base) < NT ? (total - base) : NT);
         }
         __syncthreads();
         const int m = scount;
@@ -286,18 +302,22 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
             for (int f = 0; f < 10; f++) sm[f][tid] = w.prm[(int64_t)f * n + gi];
 #pragma unroll
             for (int c = 0; c < C; c++) sv[c][tid] = __ldg(G.value + (int64_t)gi * C + c) * scale;
-            // which halves of the tile the box reaches on each axis, then the octants
-            const int o[3] = {x0, y0, z0};
-            unsigned half[3];
+            // which 4-voxel slices of the tile the box reaches on each axis,
+            // then the sub-blocks (bit w: warp w's)
+            const int o[3] = {x0, y0, z0}, ns[3] = {SX, SY, SZ};
+            unsigned slices[3];
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const int lo = w.box[(int64_t)a * n + gi], hi = w.box[(int64_t)(3 + a) * n + gi];
-                half[a] = (lo <= o[a] + 3 && hi >= o[a] ? 1u : 0u) | (lo <= o[a] + 7 && hi >= o[a] + 4 ? 2u : 0u);
+                slices[a] = 0u;
+                for (int k = 0; k < ns[a]; k++)
+                    if (lo <= o[a] + 4 * k + 3 && hi >= o[a] + 4 * k) slices[a] |= 1u << k;
             }
             unsigned occ = 0u;
 #pragma unroll
-            for (int q = 0; q < 8; q++)
-                if (((half[0] >> (q & 1)) & (half[1] >> ((q >> 1) & 1)) & (half[2] >> (q >> 2))) & 1u) occ |= 1u << q;
+            for (int q = 0; q < SX * SY * SZ; q++)
+                if (((slices[0] >> (q % SX)) & (slices[1] >> ((q / SX) % SY)) & (slices[2] >> (q / (SX * SY)))) & 1u)
+                    occ |= 1u << q;
             socc[tid] = occ;
         }
         __syncthreads();
@@ -305,8 +325,8 @@ __global__ void __launch_bounds__(kRenderThreads) k_render(pmf_gaussians G, Grid
 #pragma unroll
         for (int c = 0; c < C; c++) { p0[c] = 0; p1[c] = 0; }
         for (int j = 0; j < m; j++) {
-            // a Gaussian whose voxel box misses this warp's octant adds nothing
-            // there: its q exceeds kappa^2 outside the box (warp-uniform skip)
+            // a Gaussian whose voxel box misses this warp's sub-block adds
+            // nothing there: its q exceeds kappa^2 outside the box (warp-uniform skip)
             if (!((socc[j] >> warp) & 1u)) continue;
             const float dx = cx - sm[0][j], dy = cy - sm[1][j];
             const float a00 = sm[3][j], a11 = sm[4][j], a22 = sm[5][j], b01 = sm[6][j], b02 = sm[7][j],
@@ -582,17 +602,40 @@ pmf_status validate_gaussians(const pmf_gaussians* g) {
 }
 
 pmf_status run_prep_scan(const pmf_grid* grid, const pmf_gaussians* gs, const VoxWs& w, const GridD& g,
-                         cudaStream_t st, int ntx, int nty, int64_t T) {
+                         const VoxTile& tl, cudaStream_t st, int ntx, int nty, int64_t T) {
     cudaMemsetAsync(w.hdr, 0, sizeof(VoxHeader), st);
     cudaMemsetAsync(w.tcount, 0, sizeof(unsigned) * (size_t)T, st);
     cudaMemsetAsync(w.cursor, 0, sizeof(unsigned) * (size_t)T, st);
     if (gs->n > 0) {
         int64_t threads = gs->n * 32;
-        k_prep<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(*gs, g, gs->kappa, w, ntx, nty);
+        k_prep<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(*gs, g, gs->kappa, w, tl, ntx, nty);
     }
     k_scan<<<1, 1024, 0, st>>>(w, T);
     (void)grid;
     return check_launch("gs_voxelize prep");
+}
+
+pmf_status get_tile(const int32_t* tile, VoxTile& tl) {
+    PMF_REQUIRE(tile != nullptr, "tile is null");
+    tl = VoxTile{tile[0], tile[1], tile[2]};
+    if (!supported_tile(tl))
+        return set_error(PMF_EUNSUPPORTED, "voxelizer bin tile %dx%dx%d not supported (8x8x8, 16x8x8, 8x8x4, 16x8x4)",
+                         tile[0], tile[1], tile[2]);
+    return PMF_OK;
+}
+
+template <typename T, int C>
+void render_tiled(const VoxTile& tl, int64_t nt, const pmf_gaussians& G, const GridD& g, const VoxWs& w, T* out,
+                  int ntx, int nty, cudaStream_t s) {
+    const unsigned blocks = (unsigned)nt;
+    if (tl.x == 16 && tl.z == 8)
+        k_render<T, C, 16, 8, 8><<<blocks, 16 * 8 * 8 / 2, 0, s>>>(G, g, w, out, ntx, nty);
+    else if (tl.x == 16)
+        k_render<T, C, 16, 8, 4><<<blocks, 16 * 8 * 4 / 2, 0, s>>>(G, g, w, out, ntx, nty);
+    else if (tl.z == 4)
+        k_render<T, C, 8, 8, 4><<<blocks, 8 * 8 * 4 / 2, 0, s>>>(G, g, w, out, ntx, nty);
+    else
+        k_render<T, C, 8, 8, 8><<<blocks, 8 * 8 * 8 / 2, 0, s>>>(G, g, w, out, ntx, nty);
 }
 
 }  // namespace
@@ -605,70 +648,94 @@ using namespace pmf;
 
 extern "C" {
 
-pmf_status gs_voxelize_workspace(const pmf_grid* grid, int64_t n, int64_t pair_capacity, size_t* bytes) {
+pmf_status gs_voxelize_tiled_workspace(const pmf_grid* grid, int64_t n, int64_t pair_capacity, const int32_t tile[3],
+                                      size_t* bytes) {
     pmf_status st = validate_grid(grid);
     if (st != PMF_OK) return st;
+    VoxTile tl;
+    if ((st = get_tile(tile, tl)) != PMF_OK) return st;
     PMF_REQUIRE(bytes != nullptr, "bytes is null");
     PMF_REQUIRE(n >= 0 && pair_capacity >= 0 && pair_capacity < ((int64_t)1 << 32), "bad sizes");
     GridD g = make_grid(grid);
-    *bytes = vox_ws_layout(g, n, pair_capacity, nullptr, nullptr);
+    *bytes = vox_ws_layout(g, n, pair_capacity, tl, nullptr, nullptr);
     return PMF_OK;
 }
 
-pmf_status gs_voxelize_count(const pmf_grid* grid, const pmf_gaussians* gs, int64_t* d_pairs, void* ws,
-                             size_t ws_bytes, pmf_stream stream) {
+pmf_status gs_voxelize_workspace(const pmf_grid* grid, int64_t n, int64_t pair_capacity, size_t* bytes) {
+    const int32_t tile[3] = {kDefaultTile.x, kDefaultTile.y, kDefaultTile.z};
+    return gs_voxelize_tiled_workspace(grid, n, pair_capacity, tile, bytes);
+}
+
+pmf_status gs_voxelize_tiled_count(const pmf_grid* grid, const pmf_gaussians* gs, const int32_t tile[3],
+                                   int64_t* d_pairs, void* ws, size_t ws_bytes, pmf_stream stream) {
     pmf_status st = validate_grid(grid);
     if (st != PMF_OK) return st;
     if ((st = validate_gaussians(gs)) != PMF_OK) return st;
+    VoxTile tl;
+    if ((st = get_tile(tile, tl)) != PMF_OK) return st;
     PMF_REQUIRE(d_pairs != nullptr, "d_pairs is null");
     GridD g = make_grid(grid);
-    size_t need = vox_ws_layout(g, gs->n, 0, nullptr, nullptr);
+    size_t need = vox_ws_layout(g, gs->n, 0, tl, nullptr, nullptr);
     if ((st = validate_ws(ws, ws_bytes, need)) != PMF_OK) return st;
     VoxWs w;
-    vox_ws_layout(g, gs->n, 0, &w, (char*)ws);
-    const int ntx = (g.nx + kTile - 1) / kTile, nty = (g.ny + kTile - 1) / kTile, ntz = (g.nz + kTile - 1) / kTile;
+    vox_ws_layout(g, gs->n, 0, tl, &w, (char*)ws);
+    const int ntx = ceil_div(g.nx, tl.x), nty = ceil_div(g.ny, tl.y), ntz = ceil_div(g.nz, tl.z);
     const int64_t T = (int64_t)ntx * nty * ntz;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = run_prep_scan(grid, gs, w, g, s, ntx, nty, T)) != PMF_OK) return st;
+    if ((st = run_prep_scan(grid, gs, w, g, tl, s, ntx, nty, T)) != PMF_OK) return st;
     k_copy_total<<<1, 1, 0, s>>>(w, d_pairs);
     return check_launch("gs_voxelize_count");
 }
 
-pmf_status gs_voxelize(const pmf_grid* grid, const pmf_gaussians* gs, pmf_dtype dtype, void* out, void* ws,
-                       size_t ws_bytes, pmf_stream stream) {
+pmf_status gs_voxelize_count(const pmf_grid* grid, const pmf_gaussians* gs, int64_t* d_pairs, void* ws,
+                             size_t ws_bytes, pmf_stream stream) {
+    const int32_t tile[3] = {kDefaultTile.x, kDefaultTile.y, kDefaultTile.z};
+    return gs_voxelize_tiled_count(grid, gs, tile, d_pairs, ws, ws_bytes, stream);
+}
+
+pmf_status gs_voxelize_tiled(const pmf_grid* grid, const pmf_gaussians* gs, pmf_dtype dtype, const int32_t tile[3],
+                             void* out, void* ws, size_t ws_bytes, pmf_stream stream) {
     pmf_status st = validate_grid(grid);
     if (st != PMF_OK) return st;
     if ((st = validate_gaussians(gs)) != PMF_OK) return st;
     if ((st = validate_dtype(dtype)) != PMF_OK) return st;
+    VoxTile tl;
+    if ((st = get_tile(tile, tl)) != PMF_OK) return st;
     PMF_REQUIRE(out != nullptr, "out is null");
     GridD g = make_grid(grid);
-    size_t fixed = vox_ws_layout(g, gs->n, 0, nullptr, nullptr);
+    size_t fixed = vox_ws_layout(g, gs->n, 0, tl, nullptr, nullptr);
     if ((st = validate_ws(ws, ws_bytes, fixed)) != PMF_OK) return st;
     // whatever is left after the fixed part holds the pair list
     int64_t cap = (int64_t)((ws_bytes - fixed) / sizeof(unsigned)) + 1;
-    while (cap > 0 && vox_ws_layout(g, gs->n, cap, nullptr, nullptr) > ws_bytes) cap -= 64;
+    while (cap > 0 && vox_ws_layout(g, gs->n, cap, tl, nullptr, nullptr) > ws_bytes) cap -= 64;
     if (cap < 0) cap = 0;
     if (cap > 0xfffffff0ll) cap = 0xfffffff0ll;
     VoxWs w;
-    vox_ws_layout(g, gs->n, cap, &w, (char*)ws);
-    const int ntx = (g.nx + kTile - 1) / kTile, nty = (g.ny + kTile - 1) / kTile, ntz = (g.nz + kTile - 1) / kTile;
+    vox_ws_layout(g, gs->n, cap, tl, &w, (char*)ws);
+    const int ntx = ceil_div(g.nx, tl.x), nty = ceil_div(g.ny, tl.y), ntz = ceil_div(g.nz, tl.z);
     const int64_t T = (int64_t)ntx * nty * ntz;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = run_prep_scan(grid, gs, w, g, s, ntx, nty, T)) != PMF_OK) return st;
+    if ((st = run_prep_scan(grid, gs, w, g, tl, s, ntx, nty, T)) != PMF_OK) return st;
     if (gs->n > 0) {
         int64_t threads = gs->n * 32;
-        k_fill<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(gs->n, w, ntx, nty);
+        k_fill<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(gs->n, w, tl, ntx, nty);
     }
     PMF_DISPATCH_DTYPE(dtype, T_, {
         T_* o = (T_*)out;
         switch (gs->channels) {
-            case 1: k_render<T_, 1><<<(unsigned)T, kRenderThreads, 0, s>>>(*gs, g, w, o, ntx, nty); break;
-            case 2: k_render<T_, 2><<<(unsigned)T, kRenderThreads, 0, s>>>(*gs, g, w, o, ntx, nty); break;
-            case 3: k_render<T_, 3><<<(unsigned)T, kRenderThreads, 0, s>>>(*gs, g, w, o, ntx, nty); break;
-            default: k_render<T_, 4><<<(unsigned)T, kRenderThreads, 0, s>>>(*gs, g, w, o, ntx, nty); break;
+            case 1: render_tiled<T_, 1>(tl, T, *gs, g, w, o, ntx, nty, s); break;
+            case 2: render_tiled<T_, 2>(tl, T, *gs, g, w, o, ntx, nty, s); break;
+            case 3: render_tiled<T_, 3>(tl, T, *gs, g, w, o, ntx, nty, s); break;
+            default: render_tiled<T_, 4>(tl, T, *gs, g, w, o, ntx, nty, s); break;
         }
     });
     return check_launch("gs_voxelize");
+}
+
+pmf_status gs_voxelize(const pmf_grid* grid, const pmf_gaussians* gs, pmf_dtype dtype, void* out, void* ws,
+                       size_t ws_bytes, pmf_stream stream) {
+    const int32_t tile[3] = {kDefaultTile.x, kDefaultTile.y, kDefaultTile.z};
+    return gs_voxelize_tiled(grid, gs, dtype, tile, out, ws, ws_bytes, stream);
 }
 
 pmf_status gs_voxelize_backward_workspace(const pmf_grid* grid, int64_t n, int32_t channels, size_t* bytes) {

@@ -97,25 +97,35 @@ def _gs(*args) -> Gaussians:
 
 # ----------------------------------------------------------- voxelizer
 
-def gs_voxelize_workspace(grid, n: int, pair_capacity: int) -> int:
+VOXEL_TILES = ((8, 8, 8), (16, 8, 8), (8, 8, 4), (16, 8, 4))  # bin tiles of the voxelizer; the first is the default
+
+
+def _tile(tile):
+    t = tuple(int(x) for x in (tile or VOXEL_TILES[0]))
+    return (ct.c_int32 * 3)(*t)
+
+
+def gs_voxelize_workspace(grid, n: int, pair_capacity: int, tile=None) -> int:
     L = _lib.load()
-    return _size(L.gs_voxelize_workspace, ct.byref(_grid(grid)), int(n), int(pair_capacity))
+    return _size(L.gs_voxelize_tiled_workspace, ct.byref(_grid(grid)), int(n), int(pair_capacity), _tile(tile))
 
 
-def gs_voxelize_count(grid, gs: Gaussians) -> int:
-    """Exact number of (Gaussian, 8^3-tile) overlaps (synchronizes)."""
+def gs_voxelize_count(grid, gs: Gaussians, tile=None) -> int:
+    """Exact number of (Gaussian, bin tile) overlaps (synchronizes)."""
     L = _lib.load()
     g = _grid(grid)
-    ws = _ws(gs_voxelize_workspace(grid, gs.n, 0), gs.mean.device)
+    ws = _ws(gs_voxelize_workspace(grid, gs.n, 0, tile), gs.mean.device)
     out = torch.zeros(1, dtype=torch.int64, device=gs.mean.device)
     s = gs.c_struct()
-    check(L.gs_voxelize_count(ct.byref(g), ct.byref(s), _p(out), _p(ws), ws.numel(), _stream()), "gs_voxelize_count")
+    check(L.gs_voxelize_tiled_count(ct.byref(g), ct.byref(s), _tile(tile), _p(out), _p(ws), ws.numel(), _stream()),
+          "gs_voxelize_count")
     return int(out.item())
 
 
 def gs_voxelize(grid, gs: Gaussians, dtype=torch.float32, pair_capacity: Optional[int] = None,
-                out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Eq. 5 / signed MBC voxelization -> [C, nz, ny, nx] of `dtype`."""
+                out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, tile=None) -> torch.Tensor:
+    """Eq. 5 / signed MBC voxelization -> [C, nz, ny, nx] of `dtype`; tile: the
+    bin tile (one of VOXEL_TILES; the default 8^3 calls gs_voxelize itself)."""
     L = _lib.load()
     g = _grid(grid)
     shape, n = _shape(grid)
@@ -123,12 +133,26 @@ def gs_voxelize(grid, gs: Gaussians, dtype=torch.float32, pair_capacity: Optiona
     if out is None:
         out = torch.empty((gs.channels,) + shape, dtype=dtype, device=dev)
     if ws is None:
-        cap = gs_voxelize_count(grid, gs) if pair_capacity is None else int(pair_capacity)
-        ws = _ws(gs_voxelize_workspace(grid, gs.n, cap), dev)
+        cap = gs_voxelize_count(grid, gs, tile) if pair_capacity is None else int(pair_capacity)
+        ws = _ws(gs_voxelize_workspace(grid, gs.n, cap, tile), dev)
     s = gs.c_struct()
-    check(L.gs_voxelize(ct.byref(g), ct.byref(s), _DT[out.dtype], _p(out), _p(ws), ws.numel(), _stream()),
-          "gs_voxelize")
+    if tile is None:
+        check(L.gs_voxelize(ct.byref(g), ct.byref(s), _DT[out.dtype], _p(out), _p(ws), ws.numel(), _stream()),
+              "gs_voxelize")
+    else:
+        check(L.gs_voxelize_tiled(ct.byref(g), ct.byref(s), _DT[out.dtype], _tile(tile), _p(out), _p(ws), ws.numel(),
+                                  _stream()), "gs_voxelize_tiled")
     return out
+
+
+def gs_voxelize_tiled(grid, gs: Gaussians, tile, dtype=torch.float32, **kw) -> torch.Tensor:
+    """gs_voxelize with the bin tile chosen (one of VOXEL_TILES)."""
+    return gs_voxelize(grid, gs, dtype, tile=tuple(tile), **kw)
+
+
+def gs_voxelize_tiled_count(grid, gs: Gaussians, tile) -> int:
+    """gs_voxelize_count for the bin tile `tile`."""
+    return gs_voxelize_count(grid, gs, tuple(tile))
 
 
 def gs_voxelize_backward_workspace(grid, n: int, channels: int) -> int:
@@ -827,6 +851,13 @@ class Plan(_StepBuffers):
         a, b = (ct.c_int32 * 3)(), (ct.c_int32 * 3)()
         check(_lib.load().pmf_plan_launch_forms(self._h, a, b), "pmf_plan_launch_forms")
         return tuple(int(x) for x in a), tuple(int(x) for x in b)
+
+    def voxel_tiles(self):
+        """The voxelizer bin tile (x, y, z) of each Gaussian set: reference, then the MBC levels."""
+        n = 1 + int(self.L)
+        t = (ct.c_int32 * (3 * n))()
+        check(_lib.load().pmf_plan_voxel_tiles(self._h, t), "pmf_plan_voxel_tiles")
+        return [tuple(int(x) for x in t[3 * i:3 * i + 3]) for i in range(n)]
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -58,6 +58,34 @@ def test_voxelize_small_workload_reference_and_mbc(kappa):
             assert rel_l2(got, ref) <= TOL32  # all voxels, ties included
 
 
+@pytest.mark.parametrize("tile", [(16, 8, 8), (8, 8, 4), (16, 8, 4)])
+@pytest.mark.parametrize("C,kappa", [(1, 3.0), (3, 3.0), (3, float("inf"))])
+def test_voxelize_bin_tiles_give_the_same_bits(tile, C, kappa):
+    """Every bin tile sums the same exactly-rounded terms, so the volume is the
+    default tile's bit for bit -- on a ragged grid, through the pair lists and
+    through the overflow path that scans every Gaussian -- and it matches the
+    oracle like the default."""
+    grid = Grid(37, 22, 13, 2.0, 2.0, 2.5)
+    gs = _rand_gaussians(5 + C, grid, 120, 0.7, 3.5, C, 2.0 if C == 3 else None)
+    g = gset(gs, kappa)
+    base = pmf.gs_voxelize(grid, g)
+    got = pmf.gs_voxelize_tiled(grid, g, tile)
+    assert torch.equal(base, got)
+    assert torch.equal(base, pmf.gs_voxelize(grid, g, tile=tile, pair_capacity=11))
+    ref = oracle.voxelize(grid, gs.mean, gs.scale, gs.quat, gs.value, kappa)
+    amb, _ = tie_band(grid, gs, kappa)
+    assert_voxels_match(host(got), ref, amb, TOL32)
+    # the pair count depends on the tile: a tile made of whole 8^3 tiles lists
+    # each Gaussian in at most as many tiles, one that subdivides 8^3 in at least
+    n8 = pmf.gs_voxelize_count(grid, g)
+    nt = pmf.gs_voxelize_tiled_count(grid, g, tile)
+    if all(t >= 8 for t in tile):
+        assert nt <= n8
+    elif all(t <= 8 for t in tile):
+        assert nt >= n8
+    assert nt > 0
+
+
 def test_voxelize_list_overflow_falls_back_correctly():
     """A pair capacity far below the overlap count routes tiles through the
     scan-everything path; the result must not change by a bit."""

@@ -108,15 +108,29 @@ def test_autotune_cache_selects_launch_shapes(wl, tmp_path):
     pmf.autotune(wl.grid, wl.det, ref, mbc, wl.p, str(cache), dtype=torch.float32, views=b[0], coeff=b[1],
                  meas=b[2])
     lines = cache.read_text().splitlines()
-    assert len(lines) == 1 and " proj=" in lines[0] and " backproj=" in lines[0]
-    key, fp_txt, bp_txt = lines[0].split(" ")
+    assert len(lines) == 1 and " proj=" in lines[0] and " backproj=" in lines[0] and " vox=" in lines[0]
+    key, fp_txt, bp_txt, vox_txt = lines[0].split(" ")
     tuned = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.float32, tune_cache=str(cache))
     assert tuned.launch_forms() == (_shape(fp_txt), _shape(bp_txt))
+    tiles = [tuple(int(v) for v in t.split("x")) for t in vox_txt[len("vox="):].split(",")]
+    assert tuned.voxel_tiles() == tiles and len(tiles) == 1 + len(mbc)
+    assert all(t in pmf.ops.VOXEL_TILES for t in tiles)
     default = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.float32)
     assert default.launch_forms() == ((0, 32, 256), (0, 32, 256))
+    assert default.voxel_tiles() == [(8, 8, 8)] * (1 + len(mbc))
+    # the tiled voxelizer gives the same bits, so the tuned plan's voxel tiles
+    # alone change nothing: force the tuned tiles with the default launch shapes
+    cache_t = tmp_path / "tiles.txt"
+    cache_t.write_text(f"{key} proj=0,32,256 backproj=0,32,256 {vox_txt}\n")
+    tiled = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.float32, tune_cache=str(cache_t))
+    assert tiled.voxel_tiles() == tiles
     default.step(*b)
     torch.cuda.synchronize()
     base = _plan_outputs(default)
+    tiled.step(*b)
+    torch.cuda.synchronize()
+    _assert_same(base, _plan_outputs(tiled))
+    tiled.close()
     for fp, bp in [((2, 32, 256), (3, 32, 256)), ((0, 16, 256), (0, 16, 128)), ((4, 32, 128), (1, 16, 256))]:
         cache.write_text(f"other-key proj=1,32,256 backproj=1,32,256\n{key} proj={','.join(map(str, fp))} "
                          f"backproj={','.join(map(str, bp))}\n")

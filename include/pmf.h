@@ -497,7 +497,10 @@ typedef enum {
                                               (about one second); their outputs are set to NaN */
     PMF_DIAG_RASTER_LIST_OVERFLOW = 6,     /* rasterizer tiles whose Gaussian list overflowed the
                                               workspace's pair capacity (scanned every Gaussian instead) */
-    PMF_DIAG_COUNT = 7
+    PMF_DIAG_BOUNDS = 7,                   /* debug builds only (PMF_DEBUG): shared-memory or list
+                                              accesses whose index failed its bounds check; the access
+                                              was skipped, so outputs are wrong.  Always 0 otherwise */
+    PMF_DIAG_COUNT = 8
 } pmf_diag;
 
 /* Copies the current device's counters to host_out[PMF_DIAG_COUNT] and, with
@@ -507,8 +510,8 @@ pmf_status pmf_device_counters(uint64_t* host_out, int32_t reset);
 /* Synchronizes `stream` and reports what the device saw: PMF_ECUDA (with the
  * CUDA message) if the stream's work failed, PMF_ETIMEOUT if a bounded wait for
  * a bulk copy gave up, PMF_EINVAL if a non-finite input reached a fixed-point
- * scatter since the counters were last reset, else PMF_OK.  No kernel waits on
- * another CTA. */
+ * scatter or (debug builds) a bounds check failed since the counters were last
+ * reset, else PMF_OK.  No kernel waits on another CTA. */
 pmf_status pmf_device_status(pmf_stream stream);
 
 /* Test hook for the failure path of the bounded wait above (no counterpart in

@@ -44,9 +44,9 @@ class PmfBackprojectItem(ct.Structure):
 
 
 PMF_MAX_LEVELS = 8
-PMF_DIAG_COUNT = 7
+PMF_DIAG_COUNT = 8
 DIAG_NAMES = ("voxelize_list_overflow", "project_box_fallback", "backproject_box_fallback", "warp_halo_exit",
-              "nonfinite", "timeout", "raster_list_overflow")
+              "nonfinite", "timeout", "raster_list_overflow", "bounds")
 PMF_OPS = {"voxelize": 1, "voxelize_backward": 2, "combine_backward": 3, "warp_backward": 4,
            "warp_combine_backward": 5, "project_backward": 6, "loss": 7}
 
@@ -148,12 +148,19 @@ class PmfError(RuntimeError):
     pass
 
 
+def variant() -> str:
+    """Which build this process loads: "debug" (the bounds-checked
+    libpmf_debug.so) when PMF_LIB_VARIANT=debug, else the normal libpmf.so."""
+    return "debug" if os.environ.get("PMF_LIB_VARIANT", "") == "debug" else "release"
+
+
 def load():
-    """Build (if stale) and load libpmf.so; raises if either fails."""
+    """Build (if stale) and load libpmf.so (or, see variant(), the debug
+    build); raises if either fails."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(debug=variant() == "debug")
             if not os.path.exists(path):
                 raise PmfError(f"libpmf.so missing at {path}")
             L = ct.CDLL(path)

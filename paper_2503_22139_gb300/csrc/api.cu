@@ -53,7 +53,11 @@ pmf_status validate_ws(const void* ws, size_t ws_bytes, size_t need) {
 
 extern "C" {
 
+#ifdef PMF_DEBUG
+const char* pmf_version(void) { return "pmf-gb300 0.1 (sm_103a, debug: bounds checks)"; }
+#else
 const char* pmf_version(void) { return "pmf-gb300 0.1 (sm_103a)"; }
+#endif
 
 const char* pmf_last_error(void) { return pmf::g_msg; }
 
@@ -124,6 +128,9 @@ pmf_status pmf_device_status(pmf_stream stream) {
     if (c[PMF_DIAG_TIMEOUT] != 0)
         return pmf::set_error(PMF_ETIMEOUT, "%llu CTAs gave up waiting for a bulk copy (outputs are NaN)",
                               (unsigned long long)c[PMF_DIAG_TIMEOUT]);
+    if (c[PMF_DIAG_BOUNDS] != 0)
+        return pmf::set_error(PMF_EINVAL, "%llu accesses failed their bounds check and were skipped (debug build)",
+                              (unsigned long long)c[PMF_DIAG_BOUNDS]);
     if (c[PMF_DIAG_NONFINITE] != 0)
         return pmf::set_error(PMF_EINVAL, "%llu launches saw a NaN or infinite input magnitude (outputs are NaN)",
                               (unsigned long long)c[PMF_DIAG_NONFINITE]);

@@ -274,6 +274,7 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
                     const float w0 = mirror ? fx : ex, w1 = mirror ? ex : fx;  // the corners at +0 and +1
                     int* q = qa + idx;
                     int* q2 = q + sz;
+                    if (!PMF_DCHECK(q >= box && q2 + kPitch + 1 < box + kBox)) continue;
                     atomicAdd(q, __float_as_int(fmaf(w0, a0, kMagic)) - kMagicBits);
                     atomicAdd(q + 1, __float_as_int(fmaf(w1, a0, kMagic)) - kMagicBits);
                     atomicAdd(q + kPitch, __float_as_int(fmaf(w0, a1, kMagic)) - kMagicBits);
@@ -294,7 +295,7 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
                     const int z = bx.lz + zz;
                     for (int yy = warp; yy < bx.by; yy += RPB / 32) {
                         const int i = zz * sz + yy * kPitch + lane;
-                        if (lane >= bx.bx) continue;
+                        if (lane >= bx.bx || !PMF_DCHECK(i < kBox)) continue;
                         const int v = box[i];
                         if (v == 0) continue;
                         box[i] = 0;

@@ -41,6 +41,20 @@ static __device__ unsigned long long g_diag[PMF_DIAG_COUNT];
 
 __device__ __forceinline__ void diag_count(int which) { atomicAdd(&g_diag[which], 1ull); }
 
+// Bounds checks of the debug build (compiled with -DPMF_DEBUG): PMF_DCHECK(ok)
+// is `ok`, and a false check counts PMF_DIAG_BOUNDS, so the caller skips the
+// access instead of faulting; in the normal build it is the constant true and
+// compiles away.  Used at the shared-memory box and list indices.
+#ifdef PMF_DEBUG
+__device__ __forceinline__ bool debug_check(bool ok) {
+    if (!ok) diag_count(PMF_DIAG_BOUNDS);
+    return ok;
+}
+#define PMF_DCHECK(cond) (::pmf::debug_check(cond))
+#else
+#define PMF_DCHECK(cond) true
+#endif
+
 #define PMF_DIAG_ACCESSOR(fn)                                                                     \
     pmf_status fn(unsigned long long* out, int reset) {                                           \
         unsigned long long v[PMF_DIAG_COUNT];                                                     \

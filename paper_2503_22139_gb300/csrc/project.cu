@@ -56,7 +56,8 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
                         float val = 0.0f;
                         if (xin && zin && (unsigned)y < (unsigned)g.ny)
                             val = Store<T>::ld(V, ((int64_t)z * g.ny + y) * g.nx + x);
-                        box[(zz * bx.by + yy) * kPitch + lane] = val;
+                        const int i = (zz * bx.by + yy) * kPitch + lane;
+                        if (PMF_DCHECK(i < kBox)) box[i] = val;
                     }
                 }
             }
@@ -74,6 +75,7 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
                     const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
                     const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
                     const float* q = qa + (int)fmaf(flz, szf, fmaf(fly, syf, flx));
+                    if (!PMF_DCHECK(q >= box && q + sz + sy + 1 < box + kBox)) continue;
                     const float c000 = q[0], c100 = q[1], c010 = q[sy], c110 = q[sy + 1];
                     const float c001 = q[sz], c101 = q[sz + 1], c011 = q[sz + sy], c111 = q[sz + sy + 1];
                     const float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
@@ -235,9 +237,12 @@ __device__ __forceinline__ bool project_tile_tma(const GridD& g, int nu, int nv,
                 mbar_expect_tx(bar, (unsigned)(bx.bz * nyb * kTmaRows * kTmaX * sizeof(float)));
                 for (int zz = 0; zz < (stall ? 0 : bx.bz); zz++) {
                     const int sh = skew * (zz & 1);  // a multiple of 4 voxels: the copy start stays aligned
-                    for (int yb = 0; yb < nyb; yb++)
-                        tma_load_4d(box + zz * S - sh + yb * kTmaRows * kTmaX, map, x0 - sh, bx.ly + yb * kTmaRows,
-                                    bx.lz + zz, pv, bar);
+                    for (int yb = 0; yb < nyb; yb++) {
+                        float* dst = box + zz * S - sh + yb * kTmaRows * kTmaX;
+                        // a skipped copy leaves the barrier short of bytes: the bounded wait then reports it
+                        if (PMF_DCHECK(dst >= box && dst + kTmaRows * kTmaX <= box + kTmaBox))
+                            tma_load_4d(dst, map, x0 - sh, bx.ly + yb * kTmaRows, bx.lz + zz, pv, bar);
+                    }
                 }
             }
             const bool ok = mbar_wait_bounded(bar, parity, limit);
@@ -268,6 +273,7 @@ __device__ __forceinline__ bool project_tile_tma(const GridD& g, int nu, int nv,
                     const f32x2 fxy = sub2(uxy, pack2(flx, fly));
                     const float fx = lo2(fxy), fy = hi2(fxy), fz = uz - flz;
                     const float* q = qa + (int)fmaf(flz, szf, fmaf(fly, syf, flx));
+                    if (!PMF_DCHECK(q >= box && q + sz + sy + 1 < box + kTmaBox)) continue;
                     const f32x2 c00 = pack2(q[0], q[sz]), c10 = pack2(q[1], q[sz + 1]);
                     const f32x2 c01 = pack2(q[sy], q[sz + sy]), c11 = pack2(q[sy + 1], q[sz + sy + 1]);
                     const f32x2 fx2 = pack2(fx, fx);

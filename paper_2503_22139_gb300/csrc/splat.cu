@@ -296,7 +296,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_splat_prep(pmf_gaussians G, in
         if (rt.z >= rt.x) {
             mbits = max(mbits, abs_bits(rc.rho));
             for (int tj = rt.y / kSplatTile; tj <= rt.w / kSplatTile; tj++)
-                for (int ti = rt.x / kSplatTile; ti <= rt.z / kSplatTile; ti++) atomicAdd(hist + tj * ntu + ti, 1u);
+                for (int ti = rt.x / kSplatTile; ti <= rt.z / kSplatTile; ti++)
+                    if (PMF_DCHECK(tj * ntu + ti >= 0 && tj * ntu + ti < T)) atomicAdd(hist + tj * ntu + ti, 1u);
         }
     }
     if (!count_tiles) return;
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_splat_fill(int64_t n, int P, i
         if (rt.z < rt.x) continue;
         for (int tj = rt.y / kSplatTile; tj <= rt.w / kSplatTile; tj++)
             for (int ti = rt.x / kSplatTile; ti <= rt.z / kSplatTile; ti++) {
+                if (!PMF_DCHECK(tj * ntu + ti >= 0 && tj * ntu + ti < T)) continue;
                 const unsigned pos = atomicAdd(cur + tj * ntu + ti, 1u);
                 if ((int64_t)pos < w.capacity) w.list[pos] = (unsigned)g;
             }

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(TX * TY * TZ / 2) k_render(pmf_gaussians G, Gr
             unsigned gi;
             bool take;
             if (listed) {
-                gi = w.list[off + k];
+                gi = PMF_DCHECK((long long)(off + k) < w.capacity) ? w.list[off + k] : 0u;
                 take = true;
             } else {
                 gi = (unsigned)k;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(TX * TY * TZ / 2) k_render(pmf_gaussians G, Gr
             }
             if (take) {
                 int slot = listed ? tid : atomicAdd(&scount, 1);
-                sidx[slot] = gi;
+                if (PMF_DCHECK(slot < NT)) sidx[slot] = gi;
             }
         }
         if (listed) {

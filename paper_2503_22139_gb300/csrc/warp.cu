@@ -401,7 +401,13 @@ __device__ __forceinline__ void stage_halo_pairs(const T* __restrict__ ref, cons
 // The 8 corners of the cell whose lower corner is box cell (rx, ry, rz), from
 // the pair box (the caller has checked that the cell lies inside the box).
 __device__ __forceinline__ void corners8_pairs(const float2* sv2, int rx, int ry, int rz, float cv[8]) {
-    const float2* q = sv2 + (rz * kBY + ry) * kBX + rx;
+    const int i = (rz * kBY + ry) * kBX + rx;
+    if (!PMF_DCHECK(i >= 0 && i + kBX * kBY + kBX < kBoxN)) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) cv[c] = 0.0f;
+        return;
+    }
+    const float2* q = sv2 + i;
     const float2 c00 = q[0], c10 = q[kBX], c01 = q[kBX * kBY], c11 = q[kBX * kBY + kBX];
     cv[0] = c00.x; cv[1] = c00.y; cv[2] = c10.x; cv[3] = c10.y;
     cv[4] = c01.x; cv[5] = c01.y; cv[6] = c11.x; cv[7] = c11.y;
@@ -687,7 +693,8 @@ __global__ void __launch_bounds__(256, 2) k_wc_bwd_tile(GridD g, int P, const T*
             }
             // V's adjoint: the 8 trilinear corners, each weight times gw rounded
             // once to the CTA's fixed point
-            if (inside) {
+            if (inside && PMF_DCHECK((rz * kBY + ry) * kBX + rx >= 0 &&
+                                     (rz * kBY + ry) * kBX + rx + kBX * kBY + kBX + 1 < kBoxN)) {
                 int* q = box + (rz * kBY + ry) * kBX + rx;
                 const float gz0 = gw * sb * (1.f - cl.fz), gz1 = gw * sb * cl.fz;
                 const float wyz[2][2] = {{gz0 * (1.f - cl.fy), gz0 * cl.fy}, {gz1 * (1.f - cl.fy), gz1 * cl.fy}};

@@ -221,7 +221,9 @@ pmf_status mbc_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf_
  * It allocates nothing (no cudaMalloc/cudaFree or allocating library call).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call
- * before any stream capture.  All calls share the array and it keeps the last
+ * before any stream capture; the address is looked up again when the device's
+ * context has changed (after cudaDeviceReset), so make the first call after a
+ * reset outside capture too.  All calls share the array and it keeps the last
  * call's contents (every slot read is rewritten first), so calls that overlap
  * on the GPU -- on different streams, or from different threads -- race;
  * serialize them. */

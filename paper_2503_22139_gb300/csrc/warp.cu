@@ -1035,21 +1035,47 @@ static __device__ __align__(256) float g_noalloc_part[kNoAllocMaxPL * 3 * kStrea
 
 std::mutex g_noalloc_mu;
 float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+void* g_noalloc_ctx[kNoAllocMaxDevices] = {};
 
-// Device address of g_noalloc_part on the current device, looked up once per
-// device (the host-side symbol is only a stand-in, never a device address).
+// The calling thread's current context (cuCtxGetCurrent through the runtime's
+// driver entry point, so the library needs no link-time driver dependency);
+// nullptr if it cannot be queried.
+void* current_context() {
+    typedef int (*CtxGetCurrent)(void**);
+    static CtxGetCurrent fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return (CtxGetCurrent)f;
+    }();
+    void* ctx = nullptr;
+    if (fn == nullptr || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
+
+// Device address of g_noalloc_part on the current device, looked up on the
+// first call on each device (the host-side symbol is only a stand-in, never a
+// device address) and again whenever the device's context has changed since
+// (after cudaDeviceReset the old address is stale).
 pmf_status noalloc_scratch(float** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(PMF_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(PMF_EUNSUPPORTED, "device %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
+    void* ctx = current_context();
+    if (g_noalloc_ptr[dev] == nullptr || ctx == nullptr || ctx != g_noalloc_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_part);
         if (e != cudaSuccess || p == nullptr)
             return set_error(PMF_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
         g_noalloc_ptr[dev] = (float*)p;
+        g_noalloc_ctx[dev] = ctx;  // cudaGetSymbolAddress made the primary context current if none was
+        if (ctx == nullptr) g_noalloc_ctx[dev] = current_context();
     }
     *out = g_noalloc_ptr[dev];
     return PMF_OK;

@@ -425,19 +425,21 @@ def run_native(a):
             "traffic": traffic_for(kernel_of.get(dom, dom), workload_tag),
             "hbm_frac": d.get("hbm_frac"), "avg_launch_ms": d["avg_launch_ms"], "onchip": d.get("onchip")}
 
-    # end to end: pinned host inputs -> device -> step -> gradients back to pinned host.
-    # Every step copies its own inputs in and its gradients and loss out inside
-    # the timed region; as a data loader would, a copy stream moves step k+1's
-    # inputs (and step k-1's results) while step k computes, through two
-    # device staging sets.
+    # end to end, through the C ABI: pinned host inputs -> device -> one
+    # pmf_plan_step (the native step plan, replayed from a CUDA graph) ->
+    # gradients and loss back to pinned host.  Every step copies its own inputs
+    # in and its gradients and loss out inside the timed region; as a data
+    # loader would, a copy stream moves step k+1's inputs (and step k-1's
+    # results) while step k computes, through two device staging sets.
     e2e = None
     if not a.no_e2e:
+        eplan = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind, use_graph=True, w_dtype=wdt)
         params = [ref.mean, ref.scale, ref.quat, ref.value] + [t for m in mbc for t in (m.mean, m.scale, m.quat, m.value)]
         h_par = [t.cpu().pin_memory() for t in params]
         h_views = views_all.cpu().pin_memory()
         h_coeff = coeff_all.cpu().pin_memory()
         h_meas = meas_all.cpu().pin_memory()
-        outs = [t for grp in (step.g_ref, *step.g_mbc, (step.g_wc[2],)) for t in grp]
+        outs = [t for grp in (eplan.g_ref, *eplan.g_mbc, (eplan.d_coeff,)) for t in grp]
         h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
         h_loss = torch.empty(1).pin_memory()
         st_par = [[torch.empty_like(t) for t in params] for _ in range(2)]
@@ -472,7 +474,7 @@ def run_native(a):
                 stream.wait_event(ev_in[i])
                 for dst, src_ in zip(params, st_par[i]):
                     dst.copy_(src_, non_blocking=True)
-                lo = step.run(*st_in[i])
+                lo = eplan.step(*st_in[i])
                 if k - 2 >= k0:
                     stream.wait_event(ev_out[i])  # step k - 2's results have left staging i
                 for dst, src_ in zip(st_out[i], outs + [lo]):
@@ -501,7 +503,10 @@ def run_native(a):
             tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
             te = float(tt.item())
         e2e = {"value": round(total_proj / te, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "overlap": "copy stream, double-buffered staging"}
+               "d2h_bytes_per_step": int(d2h), "path": "pmf_plan_step (C ABI, CUDA graph)",
+               "overlap": "copy stream, double-buffered staging"}
+        eplan.close()
+        del eplan
 
     launches = step.launches_per_step * a.steps
     variants = {}

@@ -233,10 +233,12 @@ __global__ void __launch_bounds__(TX * TY * TZ / 2) k_render(pmf_gaussians G, Gr
     constexpr int NT = TX * TY * TZ / 2;              // threads: two voxels each
     constexpr int SX = TX / 4, SY = TY / 4, SZ = TZ / 4;  // 4^3 sub-blocks per axis, one per warp
     static_assert(TX % 4 == 0 && TY % 4 == 0 && TZ % 4 == 0 && NT <= 512 && SX * SY * SZ <= 32, "bin tile");
-    __shared__ float sm[10][NT];
-    __shared__ float sv[C][NT];
+    // each staged Gaussian as float4 records, read by the warps with broadcast
+    // 16-byte loads: (mean, kappa^2), (a00, a11, a22, b01), (b02, b12, the
+    // sub-blocks of the tile its box touches (bits), value_0 2^k), (value_1..3 2^k)
+    __shared__ float4 rec0[NT], rec1[NT], rec2[NT];
+    __shared__ float4 rec3[C > 1 ? NT : 1];
     __shared__ unsigned sidx[NT];
-    __shared__ unsigned socc[NT];  // sub-blocks of the tile each staged Gaussian's box touches
     __shared__ int scount;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t t = blockIdx.x;
@@ -298,10 +300,11 @@ __global__ void __launch_bounds__(TX * TY * TZ / 2) k_render(pmf_gaussians G, Gr
         const int m = scount;
         if (tid < m) {
             unsigned gi = sidx[tid];
+            float f[10], v[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int f = 0; f < 10; f++) sm[f][tid] = w.prm[(int64_t)f * n + gi];
+            for (int k = 0; k < 10; k++) f[k] = w.prm[(int64_t)k * n + gi];
 #pragma unroll
-            for (int c = 0; c < C; c++) sv[c][tid] = __ldg(G.value + (int64_t)gi * C + c) * scale;
+            for (int c = 0; c < C; c++) v[c] = __ldg(G.value + (int64_t)gi * C + c) * scale;
             // which 4-voxel slices of the tile the box reaches on each axis,
             // then the sub-blocks (bit w: warp w's)
             const int o[3] = {x0, y0, z0}, ns[3] = {SX, SY, SZ};
@@ -318,7 +321,10 @@ __global__ void __launch_bounds__(TX * TY * TZ / 2) k_render(pmf_gaussians G, Gr
             for (int q = 0; q < SX * SY * SZ; q++)
                 if (((slices[0] >> (q % SX)) & (slices[1] >> ((q / SX) % SY)) & (slices[2] >> (q / (SX * SY)))) & 1u)
                     occ |= 1u << q;
-            socc[tid] = occ;
+            rec0[tid] = make_float4(f[0], f[1], f[2], f[9]);
+            rec1[tid] = make_float4(f[3], f[4], f[5], f[6]);
+            rec2[tid] = make_float4(f[7], f[8], __uint_as_float(occ), v[0]);
+            if (C > 1) rec3[tid] = make_float4(v[1], v[2], v[3], 0.f);
         }
         __syncthreads();
         int p0[C], p1[C];
@@ -327,22 +333,30 @@ __global__ void __launch_bounds__(TX * TY * TZ / 2) k_render(pmf_gaussians G, Gr
         for (int j = 0; j < m; j++) {
             // a Gaussian whose voxel box misses this warp's sub-block adds
             // nothing there: its q exceeds kappa^2 outside the box (warp-uniform skip)
-            if (!((socc[j] >> warp) & 1u)) continue;
-            const float dx = cx - sm[0][j], dy = cy - sm[1][j];
-            const float a00 = sm[3][j], a11 = sm[4][j], a22 = sm[5][j], b01 = sm[6][j], b02 = sm[7][j],
-                        b12 = sm[8][j], k2 = sm[9][j];
-            const float dz0 = cz0 - sm[2][j], dz1 = cz1 - sm[2][j];
-            const float q0 = qform(dx, dy, dz0, a00, a11, a22, b01, b02, b12);
-            const float q1 = qform(dx, dy, dz1, a00, a11, a22, b01, b02, b12);
-            if (q0 <= k2) {
+            const float4 r2 = rec2[j];
+            if (!((__float_as_uint(r2.z) >> warp) & 1u)) continue;
+            const float4 r0 = rec0[j], r1 = rec1[j];
+            float sv[C];
+            sv[0] = r2.w;
+            if (C > 1) {
+                const float4 r3 = rec3[j];
+                const float rv[3] = {r3.x, r3.y, r3.z};
+#pragma unroll
+                for (int c = 1; c < C; c++) sv[c] = rv[c - 1];
+            }
+            const float dx = cx - r0.x, dy = cy - r0.y;
+            const float dz0 = cz0 - r0.z, dz1 = cz1 - r0.z;
+            const float q0 = qform(dx, dy, dz0, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y);
+            const float q1 = qform(dx, dy, dz1, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y);
+            if (q0 <= r0.w) {
                 const float e = exp2f(q0 * kNegHalfLog2e);
 #pragma unroll
-                for (int c = 0; c < C; c++) p0[c] += __float_as_int(fmaf(sv[c][j], e, kMagicF)) - kMagicI;
+                for (int c = 0; c < C; c++) p0[c] += __float_as_int(fmaf(sv[c], e, kMagicF)) - kMagicI;
             }
-            if (q1 <= k2) {
+            if (q1 <= r0.w) {
                 const float e = exp2f(q1 * kNegHalfLog2e);
 #pragma unroll
-                for (int c = 0; c < C; c++) p1[c] += __float_as_int(fmaf(sv[c][j], e, kMagicF)) - kMagicI;
+                for (int c = 0; c < C; c++) p1[c] += __float_as_int(fmaf(sv[c], e, kMagicF)) - kMagicI;
             }
         }
 #pragma unroll

@@ -389,7 +389,12 @@ __global__ void k_copy_total(const VoxWs w, int64_t* d_pairs) { *d_pairs = w.hdr
 // C + 9 moments, reduces them over the warp in a fixed tree, and writes either
 // the gradient (S = 1) or a partial that a second pass sums in slab order.
 
-constexpr int kBwdWarps = 8;   // warps per CTA
+constexpr int kBwdWarps = 8;   // warps per CTA of the slab-merge pass
+// One warp per CTA in the adjoint proper: a warp's (Gaussian, slab) item is
+// independent of its CTA, and Gaussians of very different sizes in one CTA
+// would keep the CTA resident, its finished warps idle, until the largest is
+// done; single-warp CTAs let the SM refill each slot at once.
+constexpr int kBwdItemWarps = 1;
 constexpr int kMom = 9;        // S1 (3) + S2 (6)
 
 template <int C>
@@ -530,11 +535,11 @@ __device__ void moments_to_grad(const GaussSetup& s, const float* r, int64_t i, 
 }
 
 template <int C>
-__global__ void __launch_bounds__(32 * kBwdWarps, 3) k_vox_bwd(pmf_gaussians G, GridD g, int S,
+__global__ void __launch_bounds__(32 * kBwdItemWarps, 24 / kBwdItemWarps) k_vox_bwd(pmf_gaussians G, GridD g, int S,
                                                             const float* __restrict__ dout, float* part,
                                                             float* d_mean, float* d_scale, float* d_quat,
                                                             float* d_value, int accumulate) {
-    const int64_t item = (int64_t)blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
+    const int64_t item = (int64_t)blockIdx.x * kBwdItemWarps + (threadIdx.x >> 5);
     if (item >= G.n * S) return;
     const int64_t i = item / S;
     const int slab = (int)(item - i * S);
@@ -778,11 +783,11 @@ pmf_status gs_voxelize_backward(const pmf_grid* grid, const pmf_gaussians* gs, c
     const int S = bwd_slabs(gs->n);
     float* part = (float*)ws;
     const int64_t items = gs->n * S;
-    const unsigned nb = (unsigned)((items + kBwdWarps - 1) / kBwdWarps);
+    const unsigned nb = (unsigned)((items + kBwdItemWarps - 1) / kBwdItemWarps);
     const unsigned nf = (unsigned)((gs->n + kBwdWarps - 1) / kBwdWarps);
-    const int T = 32 * kBwdWarps;
+    const int T = 32 * kBwdWarps, TI = 32 * kBwdItemWarps;
 #define PMF_VB(CC)                                                                                               \
-    k_vox_bwd<CC><<<nb, T, 0, s>>>(*gs, g, S, d_out, part, d_mean, d_scale, d_quat, d_value, accumulate);     \
+    k_vox_bwd<CC><<<nb, TI, 0, s>>>(*gs, g, S, d_out, part, d_mean, d_scale, d_quat, d_value, accumulate);    \
     if (S > 1) k_vox_bwd_final<CC><<<nf, T, 0, s>>>(*gs, g, S, part, d_mean, d_scale, d_quat, d_value, accumulate);
     switch (gs->channels) {
         case 1: { PMF_VB(1) break; }

@@ -137,7 +137,7 @@ __device__ __forceinline__ int exp_for(float bound, int bits) {
 
 // Adjoint lane layout: lane l = g + 8 q of warp w takes pixel
 // (2 g + (w & 1), (w >> 1) + 4 q) of the 16x16 tile and starts its chunk at
-// sample 3 g + 2 q.  Shared-memory atomics are served per half-warp, and
+// sample 3 g + 2 q (of its own samples in the chunk).  Shared-memory atomics are served per half-warp, and
 // within each half this spreads the 16 simultaneous corner addresses over the
 // banks (measured at the paper geometry: 2.9 wavefronts per warp-wide atomic
 // with the ray-following box layout below, 3.8 with a fixed one; the floor is
@@ -259,10 +259,14 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
                 // Lanes start at staggered samples (adjoint_phase), so a
                 // half-warp's simultaneous atomics land on different voxels
                 // and mostly different banks.
-                const int phase = adjoint_phase();
-                for (int k = 0; k < CH; k++) {
-                    const int j = (k + phase) & (CH - 1);
-                    if (j < j0 || j > j1) continue;
+                // each lane visits exactly its own samples j0..j1, starting at its
+                // stagger (taken modulo its count) and wrapping, so a chunk the
+                // ray only enters or leaves costs no idle iterations
+                const int len = j1 - j0 + 1;
+                int jj = adjoint_phase() % len;
+                for (int k = 0; k < len; k++) {
+                    const int j = j0 + jj;
+                    jj = jj + 1 == len ? 0 : jj + 1;
                     const float jf = (float)j;
                     const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
                                 uz = fmaf(jf, r.dh[2], fb[2]);

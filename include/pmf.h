@@ -601,7 +601,7 @@ pmf_status pmf_plan_tensors_get(const pmf_plan* plan, pmf_plan_tensors* out);
  * (backproj), each int32[3] = {form, chunk, rays}: form 0 is one CTA per
  * (view, pixel tile) and k > 0 a persistent launch of k CTAs per SM; chunk
  * (16 or 32) is the number of samples per staged voxel brick along the rays;
- * rays (128 or 256) the rays per CTA.  Defaults {0, 32, 256}, or the
+ * rays (128 or 256) the rays per CTA.  Defaults {0, 32, 256} (projector) and {0, 32, 128} (adjoint), or the
  * autotuner's choice from tune_cache.  Forms give bit-identical results;
  * chunk and rays move the last bits (chunk anchors, per-CTA scales). */
 pmf_status pmf_plan_launch_forms(const pmf_plan* plan, int32_t* proj, int32_t* backproj);

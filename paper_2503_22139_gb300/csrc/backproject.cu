@@ -518,7 +518,8 @@ pmf_status conebeam_project_backward_workspace(const pmf_grid* grid, int32_t P, 
 pmf_status conebeam_project_backward(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
                                      const float* d_proj, float* d_vol, int64_t vol_stride, int accumulate, void* ws,
                                      size_t ws_bytes, pmf_stream stream) {
-    return backproject_grid(grid, det, P, views, d_proj, d_vol, vol_stride, accumulate, ws, ws_bytes, MarchShape{},
+    return backproject_grid(grid, det, P, views, d_proj, d_vol, vol_stride, accumulate, ws, ws_bytes,
+                            default_backproject_shape(),
                             (cudaStream_t)stream);
 }
 
@@ -536,6 +537,7 @@ pmf_status conebeam_project_backward_batched_workspace(int32_t n, const pmf_back
 
 pmf_status conebeam_project_backward_batched(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
                                              size_t ws_bytes, pmf_stream stream) {
-    return backproject_batched_impl(n, items, accumulate, ws, ws_bytes, MarchShape{}, 0, (cudaStream_t)stream);
+    return backproject_batched_impl(n, items, accumulate, ws, ws_bytes, default_backproject_shape(), 0,
+                                    (cudaStream_t)stream);
 }
 }  // extern "C"

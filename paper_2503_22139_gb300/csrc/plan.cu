@@ -42,7 +42,7 @@ struct pmf_plan {
     size_t tv_bytes = 0;
     void* norm_ws = nullptr;
     size_t norm_bytes = 0;
-    pmf::MarchShape fp, bp;  // launch shapes of the projector and its adjoint
+    pmf::MarchShape fp, bp = pmf::default_backproject_shape();  // launch shapes of the projector and its adjoint
     int32_t tile[1 + PMF_MAX_LEVELS][3] = {};  // voxelizer bin tile per Gaussian set (reference, then MBC levels)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -85,6 +85,14 @@ struct MarchShape {
     int rays = 256;
     int tma = 1;  // forward only: 1 stages fp32 boxes with bulk tensor copies when the layout allows, 0 never
 };
+// The adjoint's default: 128 rays per CTA (a 16x8 pixel tile).  Its rays have
+// closer sample ranges, so fewer lanes idle at the chunks where rays enter or
+// leave the volume; at the paper-scale geometry it is what the autotuner picks.
+inline MarchShape default_backproject_shape() {
+    MarchShape m;
+    m.rays = 128;
+    return m;
+}
 pmf_status project_launch(const pmf_project_item& it, pmf_dtype dtype, const MarchShape& sh, cudaStream_t s);
 pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes,
                               const MarchShape& sh, cudaStream_t s);

@@ -139,3 +139,27 @@ def test_density_control_host_validation():
                    20, fake, fake, 1 << 20, None) == -1
     assert _status("gs_density_control", ct.byref(gs), None, 1.0, fake, 0.1, 1.0, 0.01, 1.6, fake, fake, fake, fake,
                    20, fake, fake, 1 << 20, None) == -1
+
+
+def test_tiled_voxelizer_and_threshold_host_validation():
+    g = _lib.PmfGrid(40, 36, 30, 2.0, 2.0, 2.0)
+    fake = ct.c_void_p(256)
+    gs = _lib.PmfGaussians(10, 1, 3.0, 16, 16, 16, 16)
+    n8, n4 = ct.c_size_t(0), ct.c_size_t(0)
+    t8 = (ct.c_int32 * 3)(8, 8, 8)
+    t4 = (ct.c_int32 * 3)(8, 8, 4)
+    bad = (ct.c_int32 * 3)(8, 8, 2)
+    assert _status("gs_voxelize_tiled_workspace", ct.byref(g), 1000, 0, t8, ct.byref(n8)) == 0
+    assert _status("gs_voxelize_tiled_workspace", ct.byref(g), 1000, 0, t4, ct.byref(n4)) == 0
+    # twice the tiles: the per-tile counters and offsets grow
+    assert n4.value > n8.value
+    ref = ct.c_size_t(0)
+    assert _status("gs_voxelize_workspace", ct.byref(g), 1000, 0, ct.byref(ref)) == 0 and ref.value == n8.value
+    assert _status("gs_voxelize_tiled_workspace", ct.byref(g), 1000, 0, bad, ct.byref(n8)) == -5
+    assert b"not supported" in _lib.load().pmf_last_error()
+    assert _status("gs_voxelize_tiled", ct.byref(g), ct.byref(gs), 0, bad, fake, fake, 1 << 20, None) == -5
+    assert _status("gs_voxelize_tiled", ct.byref(g), ct.byref(gs), 0, None, fake, fake, 1 << 20, None) == -1
+    # the densification threshold: rank in [0, n), n >= 1, finite scale
+    for n, rank, scale in ((10, 10, 1.0), (10, -1, 1.0), (0, 0, 1.0), (10, 3, math.inf)):
+        assert _status("gs_density_threshold", n, fake, scale, rank, fake, None) == -1, (n, rank, scale)
+    assert _status("gs_density_threshold", 10, None, 1.0, 3, fake, None) == -1

@@ -137,11 +137,12 @@ __device__ __forceinline__ int exp_for(float bound, int bits) {
 
 // Adjoint lane layout: lane l = g + 8 q of warp w takes pixel
 // (2 g + (w & 1), (w >> 1) + 4 q) of the 16x16 tile and starts its chunk at
-// sample 3 g + 2 q (of its own samples in the chunk).  Shared-memory atomics are served per half-warp, and
-// within each half this spreads the 16 simultaneous corner addresses over the
-// banks (measured at the paper geometry: 2.9 wavefronts per warp-wide atomic
-// with the ray-following box layout below, 3.8 with a fixed one; the floor is
-// 2).
+// sample 3 g + 2 q (of its own samples in the chunk).  A warp-wide shared
+// atomic whose 32 addresses lie in distinct banks takes one wavefront
+// (measured); each further address in the busiest bank adds one.  This layout
+// spreads the 32 simultaneous corner addresses over the banks (measured at the
+// paper geometry: 2.85 wavefronts per warp-wide atomic with the ray-following
+// box layout below, 3.8 with a fixed one).
 template <int RPB>
 __device__ __forceinline__ void pixel_of_spread(int tile, int ntu, int& a, int& b) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, g = l & 7, q = l >> 3;
@@ -257,8 +258,8 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
                 // weights are formed with the bias kMagic, so each rounds to an
                 // integer-valued float and converts with one integer subtract.
                 // Lanes start at staggered samples (adjoint_phase), so a
-                // half-warp's simultaneous atomics land on different voxels
-                // and mostly different banks.
+                // warp's simultaneous atomics land on different voxels and
+                // mostly different banks.
                 // each lane visits exactly its own samples j0..j1, starting at its
                 // stagger (taken modulo its count) and wrapping, so a chunk the
                 // ray only enters or leaves costs no idle iterations

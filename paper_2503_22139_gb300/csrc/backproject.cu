@@ -15,6 +15,26 @@
 namespace pmf {
 namespace {
 
+// The adjoint's shared box: 192 words per sample of the chunk (9,216 words for
+// the default 48-sample chunk), in dynamic shared memory.
+template <int CH>
+__host__ __device__ constexpr int box_words() { return 192 * CH; }
+
+// (chunk, rays) -> template instantiation of the adjoint, whose chunks may
+// also be 48 and 64 samples long
+#define PMF_DISPATCH_ADJOINT(sh, CH, RPB, ...)                                                                \
+    switch ((sh).chunk * 1000 + (sh).rays) {                                                                \
+        case 48128: { constexpr int CH = 48, RPB = 128; __VA_ARGS__; break; }                               \
+        case 48256: { constexpr int CH = 48, RPB = 256; __VA_ARGS__; break; }                               \
+        case 64128: { constexpr int CH = 64, RPB = 128; __VA_ARGS__; break; }                               \
+        case 64256: { constexpr int CH = 64, RPB = 256; __VA_ARGS__; break; }                               \
+        case 32128: { constexpr int CH = 32, RPB = 128; __VA_ARGS__; break; }                               \
+        case 32256: { constexpr int CH = 32, RPB = 256; __VA_ARGS__; break; }                               \
+        case 16128: { constexpr int CH = 16, RPB = 128; __VA_ARGS__; break; }                               \
+        case 16256: { constexpr int CH = 16, RPB = 256; __VA_ARGS__; break; }                               \
+        default: return set_error(PMF_EINVAL, "unsupported adjoint shape: chunk %d, rays %d", (sh).chunk, (sh).rays); \
+    }
+
 __global__ void k_absmax_f(const float* __restrict__ x, int64_t n, unsigned* out) { absmax_bits(x, n, out); }
 
 // ----------------------------------------------------------------- adjoint
@@ -174,9 +194,58 @@ __device__ __forceinline__ bool tile_mirror(const pmf_view& vw, int nu, int nv, 
 
 // Plane stride of the box: the smallest stride >= rows * kPitch that is 16
 // (mod 32), so cells one plane apart fall half a bank row apart.
-__device__ __forceinline__ int plane_stride(int rows) {
-    const int s = rows * kPitch;
+__device__ __forceinline__ int plane_stride(int rows, int pitch) {
+    const int s = rows * pitch;
     return s + ((16 - (s & 31)) & 31);
+}
+
+template <int PITCH, int NBOX>
+__device__ __forceinline__ void scatter_samples(const Ray& r, const Box& bx, int sz, bool mirror, float sxf, float gsb,
+                                                int j0, int j1, const int ib[3], const float fb[3], int* box) {
+    constexpr int sy = PITCH;
+    const float syf = (float)sy, szf = (float)sz;
+    // positions relative to the anchor cell, bounded like the box.
+    // Box column of voxel x: x - lx, or bx - 1 - (x - lx) mirrored;
+    // a sample's base address is its cell's lower-x corner, or its
+    // upper-x corner when mirrored, so the corners always sit at
+    // +0, +1, +sy, +sy + 1 (the two x weights trade places)
+    int* qa = box + (mirror ? bx.bx - 2 - (ib[0] - bx.lx) : ib[0] - bx.lx) + (ib[1] - bx.ly) * sy +
+              (ib[2] - bx.lz) * sz;
+    // every sample adds its 8 scaled corner weights to the box; the
+    // weights are formed with the bias kMagic, so each rounds to an
+    // integer-valued float and converts with one integer subtract.
+    // Lanes start at staggered samples (adjoint_phase), so a
+    // warp's simultaneous atomics land on different voxels and
+    // mostly different banks.
+    // each lane visits exactly its own samples j0..j1, starting at its
+    // stagger (taken modulo its count) and wrapping, so a chunk the
+    // ray only enters or leaves costs no idle iterations
+    const int len = j1 - j0 + 1;
+    int jj = adjoint_phase() % len;
+    for (int k = 0; k < len; k++) {
+        const int j = j0 + jj;
+        jj = jj + 1 == len ? 0 : jj + 1;
+        const float jf = (float)j;
+        const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
+                    uz = fmaf(jf, r.dh[2], fb[2]);
+        const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
+        const int idx = (int)fmaf(flx, sxf, fmaf(fly, syf, flz * szf));
+        const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
+        const float ex = 1.0f - fx, ey = 1.0f - fy, ez = (1.0f - fz) * gsb, fzs = fz * gsb;
+        const float a0 = ey * ez, a1 = fy * ez, a2 = ey * fzs, a3 = fy * fzs;
+        const float w0 = mirror ? fx : ex, w1 = mirror ? ex : fx;  // the corners at +0 and +1
+        int* q = qa + idx;
+        int* q2 = q + sz;
+        if (!PMF_DCHECK(q >= box && q2 + PITCH + 1 < box + NBOX)) continue;
+        atomicAdd(q, __float_as_int(fmaf(w0, a0, kMagic)) - kMagicBits);
+        atomicAdd(q + 1, __float_as_int(fmaf(w1, a0, kMagic)) - kMagicBits);
+        atomicAdd(q + PITCH, __float_as_int(fmaf(w0, a1, kMagic)) - kMagicBits);
+        atomicAdd(q + PITCH + 1, __float_as_int(fmaf(w1, a1, kMagic)) - kMagicBits);
+        atomicAdd(q2, __float_as_int(fmaf(w0, a2, kMagic)) - kMagicBits);
+        atomicAdd(q2 + 1, __float_as_int(fmaf(w1, a2, kMagic)) - kMagicBits);
+        atomicAdd(q2 + PITCH, __float_as_int(fmaf(w0, a3, kMagic)) - kMagicBits);
+        atomicAdd(q2 + PITCH + 1, __float_as_int(fmaf(w1, a3, kMagic)) - kMagicBits);
+    }
 }
 
 // One pixel tile of view p of the adjoint; box must be all zero on entry and is
@@ -240,67 +309,26 @@ __device__ __forceinline__ void backproject_tile(const GridD& g, int nu, int nv,
         const bool act = chunk_begin<CH>(bs, sel, r, live, M0, j0, j1, ib, fb);
         __syncthreads();
         const Box bx = read_box(bs, sel);
-        const int sz = plane_stride(bx.by);
-        const bool fits = bx.vol > 0 && bx.bx <= 32 && (long long)bx.bz * sz <= kBox;
+        const int pitch = bx.bx <= 32 ? 33 : 65;
+        const int sz = plane_stride(bx.by, pitch);
+        const bool fits = bx.vol > 0 && bx.bx <= 64 && (long long)bx.bz * sz <= box_words<CH>();
         if (threadIdx.x == 0 && bx.vol > 0 && !fits) diag_count(PMF_DIAG_BACKPROJECT_BOX_FALLBACK);
         if (fits) {
             if (act) {
-                const int sy = kPitch;
-                const float syf = (float)sy, szf = (float)sz;
-                // positions relative to the anchor cell, bounded like the box.
-                // Box column of voxel x: x - lx, or bx - 1 - (x - lx) mirrored;
-                // a sample's base address is its cell's lower-x corner, or its
-                // upper-x corner when mirrored, so the corners always sit at
-                // +0, +1, +sy, +sy + 1 (the two x weights trade places)
-                int* qa = box + (mirror ? bx.bx - 2 - (ib[0] - bx.lx) : ib[0] - bx.lx) + (ib[1] - bx.ly) * sy +
-                          (ib[2] - bx.lz) * sz;
-                // every sample adds its 8 scaled corner weights to the box; the
-                // weights are formed with the bias kMagic, so each rounds to an
-                // integer-valued float and converts with one integer subtract.
-                // Lanes start at staggered samples (adjoint_phase), so a
-                // warp's simultaneous atomics land on different voxels and
-                // mostly different banks.
-                // each lane visits exactly its own samples j0..j1, starting at its
-                // stagger (taken modulo its count) and wrapping, so a chunk the
-                // ray only enters or leaves costs no idle iterations
-                const int len = j1 - j0 + 1;
-                int jj = adjoint_phase() % len;
-                for (int k = 0; k < len; k++) {
-                    const int j = j0 + jj;
-                    jj = jj + 1 == len ? 0 : jj + 1;
-                    const float jf = (float)j;
-                    const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
-                                uz = fmaf(jf, r.dh[2], fb[2]);
-                    const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
-                    const int idx = (int)fmaf(flx, sxf, fmaf(fly, syf, flz * szf));
-                    const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
-                    const float ex = 1.0f - fx, ey = 1.0f - fy, ez = (1.0f - fz) * gsb, fzs = fz * gsb;
-                    const float a0 = ey * ez, a1 = fy * ez, a2 = ey * fzs, a3 = fy * fzs;
-                    const float w0 = mirror ? fx : ex, w1 = mirror ? ex : fx;  // the corners at +0 and +1
-                    int* q = qa + idx;
-                    int* q2 = q + sz;
-                    if (!PMF_DCHECK(q >= box && q2 + kPitch + 1 < box + kBox)) continue;
-                    atomicAdd(q, __float_as_int(fmaf(w0, a0, kMagic)) - kMagicBits);
-                    atomicAdd(q + 1, __float_as_int(fmaf(w1, a0, kMagic)) - kMagicBits);
-                    atomicAdd(q + kPitch, __float_as_int(fmaf(w0, a1, kMagic)) - kMagicBits);
-                    atomicAdd(q + kPitch + 1, __float_as_int(fmaf(w1, a1, kMagic)) - kMagicBits);
-                    atomicAdd(q2, __float_as_int(fmaf(w0, a2, kMagic)) - kMagicBits);
-                    atomicAdd(q2 + 1, __float_as_int(fmaf(w1, a2, kMagic)) - kMagicBits);
-                    atomicAdd(q2 + kPitch, __float_as_int(fmaf(w0, a3, kMagic)) - kMagicBits);
-                    atomicAdd(q2 + kPitch + 1, __float_as_int(fmaf(w1, a3, kMagic)) - kMagicBits);
-                }
+                if (pitch == 33) scatter_samples<33, box_words<CH>()>(r, bx, sz, mirror, sxf, gsb, j0, j1, ib, fb, box);
+                else scatter_samples<65, box_words<CH>()>(r, bx, sz, mirror, sxf, gsb, j0, j1, ib, fb, box);
             }
             __syncthreads();
             // flush the box: lane = x, one warp per (y, z) row; one 64-bit atomic
             // per touched in-grid voxel, and re-zero it
-            {
-                const int x = bx.lx + (mirror ? bx.bx - 1 - lane : lane);  // box column lane
-                const bool xin = lane < bx.bx && (unsigned)x < (unsigned)g.nx;
+            for (int col = lane; col < bx.bx; col += 32) {
+                const int x = bx.lx + (mirror ? bx.bx - 1 - col : col);  // box column col
+                const bool xin = (unsigned)x < (unsigned)g.nx;
                 for (int zz = 0; zz < bx.bz; zz++) {
                     const int z = bx.lz + zz;
                     for (int yy = warp; yy < bx.by; yy += RPB / 32) {
-                        const int i = zz * sz + yy * kPitch + lane;
-                        if (lane >= bx.bx || !PMF_DCHECK(i < kBox)) continue;
+                        const int i = zz * sz + yy * pitch + col;
+                        if (!PMF_DCHECK(i < box_words<CH>())) continue;
                         const int v = box[i];
                         if (v == 0) continue;
                         box[i] = 0;
@@ -339,11 +367,11 @@ __global__ void __launch_bounds__(RPB, 768 / RPB) k_backproject(GridD g, int nu,
                                                       const float* __restrict__ dproj, int64_t vol_stride,
                                                       unsigned long long* __restrict__ acc, const unsigned* maxbits,
                                                       float bound_mult, float samples_per_voxel) {
-    __shared__ int box[kBox];
+    extern __shared__ int box[];  // box_words<CH>()
     __shared__ BoxState bs;
     __shared__ unsigned sgmax;
     __shared__ float gsum[RPB / 32];
-    for (int i = threadIdx.x; i < kBox; i += RPB) box[i] = 0;
+    for (int i = threadIdx.x; i < box_words<CH>(); i += RPB) box[i] = 0;
     backproject_tile<CH, RPB>(g, nu, nv, ntu, step, views, dproj, vol_stride, acc, maxbits, bound_mult, samples_per_voxel,
                      blockIdx.y, blockIdx.x, box, bs, sgmax, gsum);
 }
@@ -363,11 +391,11 @@ __global__ void k_fixed_to_float_f(const unsigned long long* __restrict__ acc, i
 
 template <int CH, int RPB>
 __global__ void __launch_bounds__(RPB, 768 / RPB) k_backproject_batched(const __grid_constant__ ProjBatch B) {
-    __shared__ int box[kBox];
+    extern __shared__ int box[];  // box_words<CH>()
     __shared__ BoxState bs;
     __shared__ unsigned sgmax;
     __shared__ float gsum[RPB / 32];
-    for (int i = threadIdx.x; i < kBox; i += RPB) box[i] = 0;
+    for (int i = threadIdx.x; i < box_words<CH>(); i += RPB) box[i] = 0;
     for (int64_t w = blockIdx.x; w < B.total; w += gridDim.x) {
         const ProjItem it = B.it[find_item(B, w)];  // a copy: the tile code reads registers, not the parameter block
         const int local = (int)(w - it.begin);  // < 2^31: checked when the item is filled
@@ -422,7 +450,12 @@ pmf_status backproject_grid(const pmf_grid* grid, const pmf_detector* det, int32
         const int ntu = (det->nu + 15) / 16, ntv = tiles_v(det->nv, sh.rays);
         dim3 gr((unsigned)(ntu * ntv), (unsigned)P);
         const float spv = chunk_samples_per_voxel(grid, det->step_mm, sh.chunk);
-        PMF_DISPATCH_MARCH(sh, CH, RPB, k_backproject<CH, RPB><<<gr, RPB, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, d_proj, vol_stride, acc, maxbits, bound_mult, spv));
+        PMF_DISPATCH_ADJOINT(sh, CH, RPB, {
+            constexpr int smem = (int)sizeof(int) * box_words<CH>();
+            cudaFuncSetAttribute(k_backproject<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_backproject<CH, RPB><<<gr, RPB, smem, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, d_proj, vol_stride, acc,
+                                                      maxbits, bound_mult, spv);
+        });
     }
     int64_t nb = (cells + 255) / 256;
     k_fixed_to_float_f<<<(unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks), 256, 0, s>>>(
@@ -479,7 +512,11 @@ pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items
         int ntl[kMaxItems];
         for (int i = 0; i < n; i++) ntl[i] = B.it[i].ntiles;
         const unsigned nc = persistent_ctas(total, ctas, sh.rays, ntl, n);
-        PMF_DISPATCH_MARCH(sh, CH, RPB, k_backproject_batched<CH, RPB><<<nc, RPB, 0, s>>>(B));
+        PMF_DISPATCH_ADJOINT(sh, CH, RPB, {
+            constexpr int smem = (int)sizeof(int) * box_words<CH>();
+            cudaFuncSetAttribute(k_backproject_batched<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_backproject_batched<CH, RPB><<<nc, RPB, smem, s>>>(B);
+        });
     }
     const int64_t nc = (maxcells + 255) / 256;
     k_fixed_to_float_batched<<<dim3((unsigned)(nc < 4 * kStreamBlocks ? nc : 4 * kStreamBlocks), (unsigned)n), 256, 0, s>>>(
@@ -493,7 +530,7 @@ PMF_DIAG_ACCESSOR(diag_backproject)
 
 pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes,
                               const MarchShape& sh, cudaStream_t s) {
-    if (!valid_shape(sh)) return set_error(PMF_EINVAL, "invalid march shape");
+    if (!valid_shape(sh, true)) return set_error(PMF_EINVAL, "invalid march shape");
     if (sh.form == 0)
         return backproject_grid(&it.grid, &it.det, it.P, it.views, it.d_proj, it.d_vol, it.vol_stride, accumulate,
                                 ws, ws_bytes, sh, s);

@@ -27,8 +27,9 @@ namespace {
 
 // Launch shapes (MarchShape): CH samples per chunk (the staged brick's length
 // along the rays) and RPB rays per CTA (a 16 x RPB/16 pixel tile, one ray per
-// thread).  The C entry points use 32 and 256; plans may pick others.
-constexpr int kBox = 6144;    // shared-memory box capacity (words)
+// thread).  The C entry points use 32 and 256 for the projector, 48 and 128
+// for the adjoint; plans may pick others.
+constexpr int kBox = 6144;    // the projector's shared-memory box capacity (words)
 constexpr int kPitch = 33;    // box row pitch: x = lane (box width <= 32), odd against bank conflicts
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -371,9 +372,7 @@ int max_samples_per_voxel(const pmf_grid* grid, float step) {
     return (int)floor(diag / (double)step) + 1;
 }
 
-bool valid_shape(const MarchShape& sh) {
-    return (sh.chunk == 16 || sh.chunk == 32) && (sh.rays == 128 || sh.rays == 256) && sh.form >= 0 && sh.form <= 16;
-}
+bool valid_shape(const MarchShape& sh, bool adjoint = false) { return valid_march_shape(sh, adjoint); }
 
 // (chunk, rays) -> template instantiation
 #define PMF_DISPATCH_MARCH(sh, CH, RPB, ...)                                                                  \

@@ -133,9 +133,7 @@ std::vector<std::string> read_lines(const char* path) {
     return out;
 }
 
-bool valid(const MarchShape& m) {
-    return m.form >= 0 && m.form <= 16 && (m.chunk == 16 || m.chunk == 32) && (m.rays == 128 || m.rays == 256);
-}
+bool valid(const MarchShape& m, bool adjoint) { return pmf::valid_march_shape(m, adjoint); }
 
 bool valid_tile(const int32_t* t) {
     return (t[0] == 8 || t[0] == 16) && t[1] == 8 && (t[2] == 8 || t[2] == 4);
@@ -149,7 +147,7 @@ bool cache_lookup(const char* path, const std::string& key, int sets, MarchShape
         MarchShape a, b;
         int used = 0;
         if (sscanf(s.c_str() + key.size(), " proj=%d,%d,%d backproj=%d,%d,%d%n", &a.form, &a.chunk, &a.rays, &b.form,
-                   &b.chunk, &b.rays, &used) != 6 || !valid(a) || !valid(b))
+                   &b.chunk, &b.rays, &used) != 6 || !valid(a, false) || !valid(b, true))
             continue;
         int32_t t[1 + PMF_MAX_LEVELS][3];
         memcpy(t, tile, sizeof(int32_t) * 3 * (size_t)sets);  // a line without vox= keeps the caller's tiles
@@ -547,10 +545,11 @@ pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path) {
     }
     pmf_status st = enqueue_step(p, s);  // fills W and dY
     // every (form, chunk, rays): forms 0 (grid) and 2-4 persistent CTAs per
-    // 1024 threads of an SM, bricks of 16 or 32 samples, 128 or 256 rays
+    // 1024 threads of an SM, bricks of 16 or 32 samples (the adjoint also 48
+    // and 64), 128 or 256 rays
     float best_fp = 3.0e38f, best_bp = 3.0e38f;
     MarchShape fp, bp;
-    for (int chunk : {32, 16})
+    for (int chunk : {32, 16, 48, 64})
         for (int rays : {256, 128})
             for (int form : {0, 1, 2, 4}) {
                 if (st != PMF_OK) break;
@@ -558,10 +557,13 @@ pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path) {
                 m.form = form == 0 ? 0 : form * (256 / rays);
                 m.chunk = chunk;
                 m.rays = rays;
-                p->fp = m;
-                float t = time_ms(s, 3, plan_project, p, st);
-                if (st == PMF_OK && t < best_fp) { best_fp = t; fp = m; }
-                if (st != PMF_OK) break;
+                float t;
+                if (chunk <= 32) {
+                    p->fp = m;
+                    t = time_ms(s, 3, plan_project, p, st);
+                    if (st == PMF_OK && t < best_fp) { best_fp = t; fp = m; }
+                    if (st != PMF_OK) break;
+                }
                 p->bp = m;
                 t = time_ms(s, 3, plan_backproject, p, st);
                 if (st == PMF_OK && t < best_bp) { best_bp = t; bp = m; }

@@ -76,8 +76,8 @@ pmf_status diag_splat(unsigned long long* out, int reset);
 
 // Launch shape of the ray marchers used by plans: form 0 is one CTA per
 // (view, pixel tile), k > 0 a persistent launch of k CTAs per SM; chunk (16 or
-// 32) is the number of samples per staged brick along the rays and rays (128
-// or 256) the rays per CTA.  Forms give identical results; chunk and rays
+// 32, and for the adjoint also 48 or 64) is the number of samples per staged
+// brick along the rays and rays (128 or 256) the rays per CTA.  Forms give identical results; chunk and rays
 // move the last bits (anchors, per-CTA fixed-point scale).
 struct MarchShape {
     int form = 0;
@@ -85,11 +85,21 @@ struct MarchShape {
     int rays = 256;
     int tma = 1;  // forward only: 1 stages fp32 boxes with bulk tensor copies when the layout allows, 0 never
 };
-// The adjoint's default: 128 rays per CTA (a 16x8 pixel tile).  Its rays have
+// The adjoint's default: 128 rays per CTA (a 16x8 pixel tile), whose rays have
 // closer sample ranges, so fewer lanes idle at the chunks where rays enter or
-// leave the volume; at the paper-scale geometry it is what the autotuner picks.
+// leave the volume, and 48-sample chunks, which halve the per-chunk work (box
+// set-up, barriers and the flush) against 32 while six CTAs of 128 still fit
+// an SM (measured at the paper-scale geometry: 7.87 -> 7.02 ms per 32 views;
+// 40 samples 7.59, 56 samples 7.23, 64 samples 7.70 at four CTAs per SM).
+// A launch shape the marchers take: the projector's chunks are 16 or 32
+// samples, the adjoint's may also be 48 or 64.
+inline bool valid_march_shape(const MarchShape& sh, bool adjoint) {
+    const bool chunk = sh.chunk == 16 || sh.chunk == 32 || (adjoint && (sh.chunk == 48 || sh.chunk == 64));
+    return chunk && (sh.rays == 128 || sh.rays == 256) && sh.form >= 0 && sh.form <= 16;
+}
 inline MarchShape default_backproject_shape() {
     MarchShape m;
+    m.chunk = 48;
     m.rays = 128;
     return m;
 }

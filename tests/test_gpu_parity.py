@@ -131,6 +131,26 @@ def test_voxelize_backward_matches_oracle(C, kappa):
         assert rel_l2(host(g_), r_) <= 1e-4, name
 
 
+@pytest.mark.parametrize("C", [2, 4])
+def test_voxelize_two_and_four_channels(C):
+    """The two- and four-channel forms against the oracle: the forward on the
+    default and the widest bin tile (same bits; at four channels its staged
+    records need more than 48 KB of shared memory) and the adjoint."""
+    grid = Grid(21, 18, 15, 2.0, 2.0, 2.0)
+    gs = _rand_gaussians(40 + C, grid, 80, 0.7, 3.0, C, 1.5)
+    g = gset(gs, 3.0)
+    base = pmf.gs_voxelize(grid, g)
+    assert torch.equal(base, pmf.gs_voxelize_tiled(grid, g, (16, 8, 8)))
+    ref = oracle.voxelize(grid, gs.mean, gs.scale, gs.quat, gs.value, 3.0)
+    amb, _ = tie_band(grid, gs, 3.0)
+    assert_voxels_match(host(base), ref, amb, TOL32)
+    d_out = np.random.default_rng(60 + C).normal(size=(C,) + grid.shape).astype(np.float32)
+    got = pmf.gs_voxelize_backward(grid, gset(gs, float("inf")), dev(d_out))
+    refb = oracle.voxelize_backward(grid, gs.mean, gs.scale, gs.quat, gs.value, d_out, float("inf"))
+    for name, g_, r_ in zip(("mean", "scale", "quat", "value"), got, refb):
+        assert rel_l2(host(g_), r_) <= 1e-4, name
+
+
 def test_voxelize_backward_accumulates():
     grid = Grid(8, 8, 8, 2.0, 2.0, 2.0)
     gs = gset(_rand_gaussians(9, grid, 10, 1.0, 2.0, 1), 3.0)

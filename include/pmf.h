@@ -600,9 +600,9 @@ pmf_status pmf_plan_tensors_get(const pmf_plan* plan, pmf_plan_tensors* out);
 /* Launch shapes the plan uses for the projector (proj) and its adjoint
  * (backproj), each int32[3] = {form, chunk, rays}: form 0 is one CTA per
  * (view, pixel tile) and k > 0 a persistent launch of k CTAs per SM; chunk
- * (16 or 32, and for the adjoint also 48 or 64) is the number of samples per
+ * (16, 32 or 48, and for the adjoint also 64) is the number of samples per
  * staged voxel brick along the rays; rays (128 or 256) the rays per CTA.
- * Defaults {0, 32, 256} (projector) and {0, 48, 128} (adjoint), or the
+ * Defaults {0, 48, 256} (projector) and {0, 48, 128} (adjoint), or the
  * autotuner's choice from tune_cache.  Forms give bit-identical results;
  * chunk and rays move the last bits (chunk anchors, per-CTA scales). */
 pmf_status pmf_plan_launch_forms(const pmf_plan* plan, int32_t* proj, int32_t* backproj);
@@ -617,8 +617,8 @@ pmf_status pmf_plan_voxel_tiles(const pmf_plan* plan, int32_t* tiles);
 pmf_status pmf_plan_destroy(pmf_plan* plan);
 
 /* Times the projector and its adjoint over launch shapes (forms 0, 1, 2, 4
- * CTAs per 1024 SM threads; chunks of 16 and 32 samples, for the adjoint also
- * 48 and 64; 128 and 256 rays per CTA) and each Gaussian set's voxelization over the bin tiles of
+ * CTAs per 1024 SM threads; chunks of 16, 32 and 48 samples, for the adjoint
+ * also 64; 128 and 256 rays per CTA) and each Gaussian set's voxelization over the bin tiles of
  * gs_voxelize_tiled, on desc's data (a temporary plan; CUDA events, best of 3
  * after a warm-up; the tile search allocates its own scratch), and records the
  * fastest of each in `cache_path` under a key made of the device name, SM

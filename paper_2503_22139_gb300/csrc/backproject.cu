@@ -192,7 +192,7 @@ __device__ __forceinline__ bool tile_mirror(const pmf_view& vw, int nu, int nv, 
     return dx * dy < 0.0f;
 }
 
-// Plane stride of the box: the smallest stride >= rows * kPitch that is 16
+// Plane stride of the box: the smallest stride >= rows * pitch that is 16
 // (mod 32), so cells one plane apart fall half a bank row apart.
 __device__ __forceinline__ int plane_stride(int rows, int pitch) {
     const int s = rows * pitch;

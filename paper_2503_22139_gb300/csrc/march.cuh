@@ -29,8 +29,6 @@ namespace {
 // along the rays) and RPB rays per CTA (a 16 x RPB/16 pixel tile, one ray per
 // thread).  The C entry points use 32 and 256 for the projector, 48 and 128
 // for the adjoint; plans may pick others.
-constexpr int kBox = 6144;    // the projector's shared-memory box capacity (words)
-constexpr int kPitch = 33;    // box row pitch: x = lane (box width <= 32), odd against bank conflicts
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Ray {
@@ -284,7 +282,6 @@ __device__ __forceinline__ bool chunk_begin(BoxState& bs, int sel, const Ray& r,
 struct Box {
     int lx, ly, lz, bx, by, bz;
     long long vol;
-    bool fits;  // width <= 32 and by * bz rows of kPitch words fit in kBox
 };
 
 __device__ __forceinline__ Box read_box(const BoxState& bs, int sel) {
@@ -293,14 +290,12 @@ __device__ __forceinline__ Box read_box(const BoxState& bs, int sel) {
     if (b.lx == INT_MAX) {
         b.bx = b.by = b.bz = 0;
         b.vol = 0;
-        b.fits = false;
         return b;
     }
     b.bx = bs.box[sel][3] - b.lx + 2;
     b.by = bs.box[sel][4] - b.ly + 2;
     b.bz = bs.box[sel][5] - b.lz + 2;
     b.vol = (long long)b.bx * b.by * b.bz;
-    b.fits = b.bx <= 32 && (long long)b.by * b.bz * kPitch <= kBox;
     return b;
 }
 

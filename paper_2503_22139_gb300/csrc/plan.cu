@@ -42,7 +42,7 @@ struct pmf_plan {
     size_t tv_bytes = 0;
     void* norm_ws = nullptr;
     size_t norm_bytes = 0;
-    pmf::MarchShape fp, bp = pmf::default_backproject_shape();  // launch shapes of the projector and its adjoint
+    pmf::MarchShape fp = pmf::default_project_shape(), bp = pmf::default_backproject_shape();  // launch shapes
     int32_t tile[1 + PMF_MAX_LEVELS][3] = {};  // voxelizer bin tile per Gaussian set (reference, then MBC levels)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -545,8 +545,8 @@ pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path) {
     }
     pmf_status st = enqueue_step(p, s);  // fills W and dY
     // every (form, chunk, rays): forms 0 (grid) and 2-4 persistent CTAs per
-    // 1024 threads of an SM, bricks of 16 or 32 samples (the adjoint also 48
-    // and 64), 128 or 256 rays
+    // 1024 threads of an SM, bricks of 16, 32 or 48 samples (the adjoint also
+    // 64), 128 or 256 rays
     float best_fp = 3.0e38f, best_bp = 3.0e38f;
     MarchShape fp, bp;
     for (int chunk : {32, 16, 48, 64})
@@ -558,7 +558,7 @@ pmf_status pmf_autotune(const pmf_batch_desc* desc, const char* cache_path) {
                 m.chunk = chunk;
                 m.rays = rays;
                 float t;
-                if (chunk <= 32) {
+                if (chunk <= 48) {
                     p->fp = m;
                     t = time_ms(s, 3, plan_project, p, st);
                     if (st == PMF_OK && t < best_fp) { best_fp = t; fp = m; }

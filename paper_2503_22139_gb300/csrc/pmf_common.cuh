@@ -75,8 +75,8 @@ pmf_status diag_backproject(unsigned long long* out, int reset);
 pmf_status diag_splat(unsigned long long* out, int reset);
 
 // Launch shape of the ray marchers used by plans: form 0 is one CTA per
-// (view, pixel tile), k > 0 a persistent launch of k CTAs per SM; chunk (16 or
-// 32, and for the adjoint also 48 or 64) is the number of samples per staged
+// (view, pixel tile), k > 0 a persistent launch of k CTAs per SM; chunk (16,
+// 32 or 48, and for the adjoint also 64) is the number of samples per staged
 // brick along the rays and rays (128 or 256) the rays per CTA.  Forms give identical results; chunk and rays
 // move the last bits (anchors, per-CTA fixed-point scale).
 struct MarchShape {
@@ -91,11 +91,20 @@ struct MarchShape {
 // set-up, barriers and the flush) against 32 while six CTAs of 128 still fit
 // an SM (measured at the paper-scale geometry: 7.87 -> 7.02 ms per 32 views;
 // 40 samples 7.59, 56 samples 7.23, 64 samples 7.70 at four CTAs per SM).
-// A launch shape the marchers take: the projector's chunks are 16 or 32
-// samples, the adjoint's may also be 48 or 64.
+// A launch shape the marchers take: the projector's chunks are 16, 32 or 48
+// samples, the adjoint's may also be 64.
 inline bool valid_march_shape(const MarchShape& sh, bool adjoint) {
-    const bool chunk = sh.chunk == 16 || sh.chunk == 32 || (adjoint && (sh.chunk == 48 || sh.chunk == 64));
+    const bool chunk = sh.chunk == 16 || sh.chunk == 32 || sh.chunk == 48 || (adjoint && sh.chunk == 64);
     return chunk && (sh.rays == 128 || sh.rays == 256) && sh.form >= 0 && sh.form <= 16;
+}
+// The projector's default: 256 rays per CTA and 48-sample chunks, staged by
+// bulk copies into a 52 KB box (measured at the paper-scale geometry: 4.05 ->
+// 3.69 ms per 32 views, the 32-sample chunks' 32 KB box also overflowing at
+// some view angles; 40 samples 3.78, 56 samples 3.74).
+inline MarchShape default_project_shape() {
+    MarchShape m;
+    m.chunk = 48;
+    return m;
 }
 inline MarchShape default_backproject_shape() {
     MarchShape m;

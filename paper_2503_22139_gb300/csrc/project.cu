@@ -13,7 +13,39 @@ namespace {
 
 // ----------------------------------------------------------------- forward
 
-// One 16x16 pixel tile of view p: every thread of the CTA calls it.
+// Capacity (floats) of the plain-staging box, in dynamic shared memory: a
+// 48-sample chunk's box at the paper geometry, with rows of 33 floats (65 when
+// the box is wider than 32 voxels, the same bank pattern).
+constexpr int kPlainBox = 13312;
+
+// The staged samples [j0, j1] of one ray on a box with rows PITCH floats apart
+// and planes sz floats apart (PITCH a template argument, so the corner offsets
+// are immediates).
+template <int PITCH>
+__device__ __forceinline__ void gather_samples(const Ray& r, const float* box, const Box& bx, int sz, int j0, int j1,
+                                               const int ib[3], const float fb[3], float& acc) {
+    // positions relative to the anchor cell; the box was bounded with the same
+    // expression, so every cell is inside it
+    constexpr int sy = PITCH;
+    const float syf = (float)sy, szf = (float)sz;
+    const float* qa = box + (ib[0] - bx.lx) + (ib[1] - bx.ly) * sy + (ib[2] - bx.lz) * sz;
+    float jf = (float)j0;
+    for (int j = j0; j <= j1; j++, jf += 1.0f) {
+        const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]), uz = fmaf(jf, r.dh[2], fb[2]);
+        const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
+        const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
+        const float* q = qa + (int)fmaf(flz, szf, fmaf(fly, syf, flx));
+        if (!PMF_DCHECK(q >= box && q + sz + sy + 1 < box + kPlainBox)) continue;
+        const float c000 = q[0], c100 = q[1], c010 = q[sy], c110 = q[sy + 1];
+        const float c001 = q[sz], c101 = q[sz + 1], c011 = q[sz + sy], c111 = q[sz + sy + 1];
+        const float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
+        const float a01 = fmaf(fx, c101 - c001, c001), a11 = fmaf(fx, c111 - c011, c011);
+        const float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
+        acc += fmaf(fz, b1 - b0, b0);  // into the tile's sum in sample order, as every path does
+    }
+}
+
+// One 16 x (RPB/16) pixel tile of view p: every thread of the CTA calls it.
 template <typename T, int CH, int RPB>
 __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int ntu, float step,
                                              const pmf_view* __restrict__ views, const T* __restrict__ vol,
@@ -42,12 +74,16 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
         const bool act = chunk_begin<CH>(bs, sel, r, live, M0, j0, j1, ib, fb);
         __syncthreads();
         const Box bx = read_box(bs, sel);
-        if (threadIdx.x == 0 && bx.vol > 0 && !bx.fits) diag_count(PMF_DIAG_PROJECT_BOX_FALLBACK);
-        if (bx.vol > 0 && bx.fits) {
-            // stage the box: lane = x, one warp per (y, z) row, zero outside the grid
-            {
-                const int x = bx.lx + lane;
-                const bool xin = lane < bx.bx && (unsigned)x < (unsigned)g.nx;
+        const int pitch = bx.bx <= 32 ? 33 : 65;
+        const int sz = pitch * bx.by;
+        const bool fits = bx.vol > 0 && bx.bx <= 64 && (long long)bx.bz * sz <= kPlainBox;
+        if (threadIdx.x == 0 && bx.vol > 0 && !fits) diag_count(PMF_DIAG_PROJECT_BOX_FALLBACK);
+        if (fits) {
+            // stage the box: lane = x (two passes when wider than 32), one warp
+            // per (y, z) row, zero outside the grid
+            for (int col = lane; col < bx.bx; col += 32) {
+                const int x = bx.lx + col;
+                const bool xin = (unsigned)x < (unsigned)g.nx;
                 for (int zz = 0; zz < bx.bz; zz++) {
                     const int z = bx.lz + zz;
                     const bool zin = (unsigned)z < (unsigned)g.nz;
@@ -56,33 +92,15 @@ __device__ __forceinline__ void project_tile(const GridD& g, int nu, int nv, int
                         float val = 0.0f;
                         if (xin && zin && (unsigned)y < (unsigned)g.ny)
                             val = Store<T>::ld(V, ((int64_t)z * g.ny + y) * g.nx + x);
-                        const int i = (zz * bx.by + yy) * kPitch + lane;
-                        if (PMF_DCHECK(i < kBox)) box[i] = val;
+                        const int i = zz * sz + yy * pitch + col;
+                        if (PMF_DCHECK(i < kPlainBox)) box[i] = val;
                     }
                 }
             }
             __syncthreads();
             if (act) {
-                // positions relative to the anchor cell; the box was bounded
-                // with the same expression, so every cell is inside it
-                const float syf = (float)kPitch, szf = (float)(kPitch * bx.by);
-                const int sy = kPitch, sz = kPitch * bx.by;
-                const float* qa = box + (ib[0] - bx.lx) + (ib[1] - bx.ly) * sy + (ib[2] - bx.lz) * sz;
-                float jf = (float)j0;
-                for (int j = j0; j <= j1; j++, jf += 1.0f) {
-                    const float ux = fmaf(jf, r.dh[0], fb[0]), uy = fmaf(jf, r.dh[1], fb[1]),
-                                uz = fmaf(jf, r.dh[2], fb[2]);
-                    const float flx = floorf(ux), fly = floorf(uy), flz = floorf(uz);
-                    const float fx = ux - flx, fy = uy - fly, fz = uz - flz;
-                    const float* q = qa + (int)fmaf(flz, szf, fmaf(fly, syf, flx));
-                    if (!PMF_DCHECK(q >= box && q + sz + sy + 1 < box + kBox)) continue;
-                    const float c000 = q[0], c100 = q[1], c010 = q[sy], c110 = q[sy + 1];
-                    const float c001 = q[sz], c101 = q[sz + 1], c011 = q[sz + sy], c111 = q[sz + sy + 1];
-                    const float a00 = fmaf(fx, c100 - c000, c000), a10 = fmaf(fx, c110 - c010, c010);
-                    const float a01 = fmaf(fx, c101 - c001, c001), a11 = fmaf(fx, c111 - c011, c011);
-                    const float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
-                    acc += fmaf(fz, b1 - b0, b0);
-                }
+                if (pitch == 33) gather_samples<33>(r, box, bx, sz, j0, j1, ib, fb, acc);
+                else gather_samples<65>(r, box, bx, sz, j0, j1, ib, fb, acc);
             }
         } else if (act) {
             // the staged loop's own positions and blend, so that every path
@@ -106,7 +124,7 @@ template <typename T, int CH, int RPB>
 __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project(GridD g, int nu, int nv, int ntu, float step,
                                                   const pmf_view* __restrict__ views, const T* __restrict__ vol,
                                                   int64_t vol_stride, float* __restrict__ proj) {
-    __shared__ float box[kBox];
+    extern __shared__ __align__(128) float box[];  // kPlainBox floats
     __shared__ BoxState bs;
     project_tile<T, CH, RPB>(g, nu, nv, ntu, step, views, vol, vol_stride, proj, blockIdx.y, blockIdx.x, box, bs);
 }
@@ -128,14 +146,16 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project(GridD g, int nu, in
 // the +16 is made by shifting odd planes' copies 16 voxels to the left in x:
 // plane z lands at z S - 16 (z & 1), and voxel (x, y, z) is always at
 // (x - x0) + 44 y + S z.  A box too wide for the shift uses S = 8k * 44;
-// one larger than kTmaBox falls back to bounds-checked global gathers.  The
+// one larger than kTmaBox falls back to bounds-checked global gathers (52 KB:
+// at the paper geometry no 48-sample chunk's box is larger, and four CTAs of
+// 256 rays, the register limit, still fit an SM).  The
 // wait is bounded (about one second of clock): a CTA that gives up counts
 // PMF_DIAG_TIMEOUT, waits once more for its copies, writes NaN to its pixels
 // and returns.
 constexpr int kTmaX = 44;                     // floats per staged row (one copy's x extent)
 constexpr int kTmaRows = 8;                   // rows per copy
 constexpr int kTmaSkew = 16;                  // extra plane stride (floats) of the conflict-free layout
-constexpr int kTmaBox = 8192;                 // staged floats (32 KB)
+constexpr int kTmaBox = 13312;                // staged floats (52 KB of dynamic shared memory)
 constexpr long long kTmaWaitCycles = 2000000000LL;
 constexpr long long kStallWaitCycles = 200000LL;  // the test hook's short limit (~0.1 ms)
 
@@ -308,7 +328,7 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_tma(GridD g, int nu
                                                                 const __grid_constant__ CUtensorMap map,
                                                                 const float* __restrict__ vol, int64_t vol_stride,
                                                                 float* __restrict__ proj) {
-    __shared__ __align__(128) float box[kTmaBox];
+    extern __shared__ __align__(128) float box[];  // kTmaBox floats
     __shared__ __align__(8) unsigned long long bar;
     __shared__ BoxState bs;
     if (threadIdx.x == 0) {
@@ -332,7 +352,7 @@ struct ProjBatchTma {
 
 template <int CH, int RPB>
 __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched_tma(const __grid_constant__ ProjBatchTma T) {
-    __shared__ __align__(128) float box[kTmaBox];
+    extern __shared__ __align__(128) float box[];  // kTmaBox floats
     __shared__ __align__(8) unsigned long long bar;
     __shared__ BoxState bs;
     if (threadIdx.x == 0) {
@@ -355,7 +375,7 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched_tma(const _
 
 template <typename T, int CH, int RPB>
 __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched(const __grid_constant__ ProjBatch B) {
-    __shared__ float box[kBox];
+    extern __shared__ __align__(128) float box[];  // kPlainBox floats
     __shared__ BoxState bs;
     for (int64_t w = blockIdx.x; w < B.total; w += gridDim.x) {
         const ProjItem it = B.it[find_item(B, w)];  // a copy: the tile code reads registers, not the parameter block
@@ -400,6 +420,19 @@ bool encode_volume_map(CUtensorMap* m, const float* vol, const pmf_grid* g, int3
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// (chunk, rays) -> the projector's kernels, whose chunks may also be 48
+// samples long
+#define PMF_DISPATCH_PROJ(sh, CH, RPB, ...)                                                                    \
+    switch ((sh).chunk * 1000 + (sh).rays) {                                                                \
+        case 48256: { constexpr int CH = 48, RPB = 256; __VA_ARGS__; break; }                               \
+        case 48128: { constexpr int CH = 48, RPB = 128; __VA_ARGS__; break; }                               \
+        case 32256: { constexpr int CH = 32, RPB = 256; __VA_ARGS__; break; }                               \
+        case 32128: { constexpr int CH = 32, RPB = 128; __VA_ARGS__; break; }                               \
+        case 16256: { constexpr int CH = 16, RPB = 256; __VA_ARGS__; break; }                               \
+        case 16128: { constexpr int CH = 16, RPB = 128; __VA_ARGS__; break; }                               \
+        default: return set_error(PMF_EINVAL, "unsupported march shape: chunk %d, rays %d", (sh).chunk, (sh).rays); \
+    }
+
 pmf_status project_grid(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
                         pmf_dtype dtype, const void* vol, int64_t vol_stride, float* proj, const MarchShape& sh,
                         cudaStream_t s) {
@@ -414,10 +447,18 @@ pmf_status project_grid(const pmf_grid* grid, const pmf_detector* det, int32_t P
     dim3 gr((unsigned)(ntu * ntv), (unsigned)P);
     CUtensorMap map;
     if (sh.tma && dtype == PMF_F32 && encode_volume_map(&map, (const float*)vol, grid, P, vol_stride)) {
-        PMF_DISPATCH_MARCH(sh, CH, RPB, k_project_tma<CH, RPB><<<gr, RPB, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, map, (const float*)vol, vol_stride, proj));
+        PMF_DISPATCH_PROJ(sh, CH, RPB, {
+            cudaFuncSetAttribute(k_project_tma<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kTmaBox * sizeof(float)));
+            k_project_tma<CH, RPB><<<gr, RPB, kTmaBox * sizeof(float), s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, map,
+                                                                           (const float*)vol, vol_stride, proj);
+        });
         return check_launch("conebeam_project");
     }
-    PMF_DISPATCH_MARCH(sh, CH, RPB, PMF_DISPATCH_DTYPE(dtype, T, k_project<T, CH, RPB><<<gr, RPB, 0, s>>>(g, det->nu, det->nv, ntu, det->step_mm, views, (const T*)vol, vol_stride, proj)));
+    PMF_DISPATCH_PROJ(sh, CH, RPB, PMF_DISPATCH_DTYPE(dtype, T, {
+        cudaFuncSetAttribute(k_project<T, CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kPlainBox * sizeof(float)));
+        k_project<T, CH, RPB><<<gr, RPB, kPlainBox * sizeof(float), s>>>(g, det->nu, det->nv, ntu, det->step_mm, views,
+                                                                        (const T*)vol, vol_stride, proj);
+    }));
     return check_launch("conebeam_project");
 }
 
@@ -454,11 +495,19 @@ pmf_status project_batched_impl(int32_t n, const pmf_project_item* items, pmf_dt
         }
         if (all) {
             tb.B = B;
-            PMF_DISPATCH_MARCH(sh, CH, RPB, k_project_batched_tma<CH, RPB><<<nc, RPB, 0, s>>>(tb));
+            PMF_DISPATCH_PROJ(sh, CH, RPB, {
+                cudaFuncSetAttribute(k_project_batched_tma<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kTmaBox * sizeof(float)));
+                k_project_batched_tma<CH, RPB><<<nc, RPB, kTmaBox * sizeof(float), s>>>(tb);
+            });
             return check_launch("conebeam_project_batched");
         }
     }
-    PMF_DISPATCH_MARCH(sh, CH, RPB, PMF_DISPATCH_DTYPE(dtype, T, k_project_batched<T, CH, RPB><<<nc, RPB, 0, s>>>(B)));
+    PMF_DISPATCH_PROJ(sh, CH, RPB, PMF_DISPATCH_DTYPE(dtype, T, {
+        cudaFuncSetAttribute(k_project_batched<T, CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kPlainBox * sizeof(float)));
+        k_project_batched<T, CH, RPB><<<nc, RPB, kPlainBox * sizeof(float), s>>>(B);
+    }));
     return check_launch("conebeam_project_batched");
 }
 
@@ -486,11 +535,11 @@ extern "C" {
 
 pmf_status conebeam_project(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
                             pmf_dtype dtype, const void* vol, int64_t vol_stride, float* proj, pmf_stream stream) {
-    return project_grid(grid, det, P, views, dtype, vol, vol_stride, proj, MarchShape{}, (cudaStream_t)stream);
+    return project_grid(grid, det, P, views, dtype, vol, vol_stride, proj, default_project_shape(), (cudaStream_t)stream);
 }
 
 pmf_status conebeam_project_batched(int32_t n, const pmf_project_item* items, pmf_dtype dtype, pmf_stream stream) {
-    return project_batched_impl(n, items, dtype, MarchShape{}, 0, (cudaStream_t)stream);
+    return project_batched_impl(n, items, dtype, default_project_shape(), 0, (cudaStream_t)stream);
 }
 
 pmf_status pmf_debug_stall_bulk_copies(int32_t on) {

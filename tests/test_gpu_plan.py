@@ -116,12 +116,12 @@ def test_autotune_cache_selects_launch_shapes(wl, tmp_path):
     assert tuned.voxel_tiles() == tiles and len(tiles) == 1 + len(mbc)
     assert all(t in pmf.ops.VOXEL_TILES for t in tiles)
     default = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.float32)
-    assert default.launch_forms() == ((0, 32, 256), (0, 48, 128))
+    assert default.launch_forms() == ((0, 48, 256), (0, 48, 128))
     assert default.voxel_tiles() == [(8, 8, 8)] * (1 + len(mbc))
     # the tiled voxelizer gives the same bits, so the tuned plan's voxel tiles
     # alone change nothing: force the tuned tiles with the default launch shapes
     cache_t = tmp_path / "tiles.txt"
-    cache_t.write_text(f"{key} proj=0,32,256 backproj=0,48,128 {vox_txt}\n")
+    cache_t.write_text(f"{key} proj=0,48,256 backproj=0,48,128 {vox_txt}\n")
     tiled = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.float32, tune_cache=str(cache_t))
     assert tiled.voxel_tiles() == tiles
     default.step(*b)
@@ -131,7 +131,7 @@ def test_autotune_cache_selects_launch_shapes(wl, tmp_path):
     torch.cuda.synchronize()
     _assert_same(base, _plan_outputs(tiled))
     tiled.close()
-    for fp, bp in [((2, 32, 256), (3, 48, 128)), ((0, 16, 256), (0, 64, 128)), ((4, 32, 128), (1, 16, 256))]:
+    for fp, bp in [((2, 48, 256), (3, 48, 128)), ((0, 16, 256), (0, 64, 128)), ((4, 32, 128), (1, 16, 256))]:
         cache.write_text(f"other-key proj=1,32,256 backproj=1,32,256\n{key} proj={','.join(map(str, fp))} "
                          f"backproj={','.join(map(str, bp))}\n")
         forced = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=wl.p, dtype=torch.float32, tune_cache=str(cache))
@@ -139,7 +139,7 @@ def test_autotune_cache_selects_launch_shapes(wl, tmp_path):
         forced.step(*b)
         torch.cuda.synchronize()
         got = _plan_outputs(forced)
-        if fp[1:] == (32, 256) and bp[1:] == (48, 128):
+        if fp[1:] == (48, 256) and bp[1:] == (48, 128):
             _assert_same(base, got)  # forms alone: bit-identical
         else:
             for k in base:

@@ -3,9 +3,9 @@
 // 32-bit fixed point (per-CTA scale); a warp's lanes take spread pixels and
 // start their chunk at staggered samples, so its simultaneous atomics land on
 // different voxels.  The box's bank layout follows the tile's rays: rows 33
-// words apart, x mirrored when the rays' x and y steps differ in sign, planes
-// a stride of 16 (mod 32) words apart, which keeps the cells of nearby
-// samples in different banks.  The box is then flushed with one 64-bit
+// words apart (65 for boxes wider than 32 voxels), x mirrored when the rays' x
+// and y steps differ in sign, planes a stride of 16 (mod 32) words apart,
+// which keeps the cells of nearby samples in different banks.  The box is then flushed with one 64-bit
 // fixed-point atomic per touched voxel (global scale 2^k from a provable
 // bound).  Integer sums are order independent, so the result is
 // bit-reproducible and independent of the layout.  A chunk whose box does not
@@ -199,6 +199,9 @@ __device__ __forceinline__ int plane_stride(int rows, int pitch) {
     return s + ((16 - (s & 31)) & 31);
 }
 
+// The samples j0..j1 of one ray of the chunk into a box with rows PITCH words
+// apart (a template argument, so the corner offsets are immediates) and NBOX
+// words in all.
 template <int PITCH, int NBOX>
 __device__ __forceinline__ void scatter_samples(const Ray& r, const Box& bx, int sz, bool mirror, float sxf, float gsb,
                                                 int j0, int j1, const int ib[3], const float fb[3], int* box) {

@@ -331,36 +331,68 @@ __global__ void __launch_bounds__(kThreads) k_warp_combine_bwd(GridD g, int L, i
 
 // ---------------------------------------------- tiled fused combine + warp
 //
-// A CTA owns a 32x4x4 voxel tile (256 threads, two voxels each: z and z+2),
-// keeps the coefficient table in shared memory and each voxel's MBC vectors
-// in registers for all P projections.  The adjoint scatters V's gradient into
-// a shared-memory box covering the tile plus a 4-voxel halo in 32-bit fixed
-// point (per-CTA scale, provable bound), flushed once per CTA with 64-bit
-// fixed-point atomics at the call's global scale; targets outside the halo go
-// straight to global memory.
+// A CTA owns a TX x TY x TZ voxel tile (two voxels per thread: z and
+// z + TZ / 2), keeps the coefficient table in shared memory and each voxel's
+// MBC vectors in registers for all P projections.  The adjoint scatters V's
+// gradient into a shared-memory box covering the tile plus a 4-voxel halo in
+// 32-bit fixed point (per-CTA scale, provable bound), flushed once per CTA
+// with 64-bit fixed-point atomics at the call's global scale; targets outside
+// the halo go straight to global memory.
+//
+// The forward takes an 8x8x4 tile (128 threads; a warp covers 8 x 4 voxels
+// of one plane): eight voxels along x leave few ragged tiles (a 200-voxel row
+// is 25 tiles, where 32-wide tiles left a quarter-full last column) and the
+// near-cubic tile keeps the staged halo small.  The adjoint keeps a 32x4x4
+// tile (256 threads, a warp per row): its per-CTA work (zeroing and flushing
+// the fixed-point box, the coefficient-gradient partials) is paid per tile,
+// and the smaller tile's share of it outweighed the ragged column.
 
-constexpr int kTX = 32, kTY = 4, kTZ = 4, kHalo = 4;
-constexpr int kBX = kTX + 2 * kHalo, kBY = kTY + 2 * kHalo, kBZ = kTZ + 2 * kHalo;
-constexpr int kBoxN = kBX * kBY * kBZ;
+constexpr int kHalo = 4;
 constexpr int kMaxPLTile = 512;  // P * L limit of the tiled path
+
+template <int TX_, int TY_, int TZ_, int PX_>
+struct TileGeom {
+    static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
+    static constexpr int THREADS = TX * TY * TZ / 2, WARPS = THREADS / 32;
+    static constexpr int BX = TX + 2 * kHalo, BY = TY + 2 * kHalo, BZ = TZ + 2 * kHalo;
+    static constexpr int PX = PX_;               // row pitch (elements) of the staged boxes
+    static constexpr int BOXN = PX * BY * BZ;    // elements of a staged box
+    static_assert(TZ % 2 == 0 && THREADS % 32 == 0 && PX >= BX, "tile shape");
+};
+// Forward: 16-pair rows (32 words), odd rows rotated by 8 pairs.  8-byte
+// shared loads are served per half-warp, and a half-warp of the forward reads
+// two adjacent rows of 8 pairs: the rotation puts them on complementary
+// halves of the 32 banks.
+using GeomFwd = TileGeom<8, 8, 4, 16>;
+using GeomBwd = TileGeom<32, 4, 4, 40>;
 
 struct TileIdx {
     int x0, y0, z0;
     int x, y, z[2];
+    int lx, ly, lz;  // box coordinates of the first voxel
 };
 
+template <class G>
 __device__ __forceinline__ TileIdx tile_idx(const GridD& g) {
-    const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
-    const int b = blockIdx.x;
+    const int ntx = (g.nx + G::TX - 1) / G::TX, nty = (g.ny + G::TY - 1) / G::TY;
+    const int b = blockIdx.x, tid = threadIdx.x;
     TileIdx t;
-    t.x0 = (b % ntx) * kTX;
-    t.y0 = ((b / ntx) % nty) * kTY;
-    t.z0 = (b / (ntx * nty)) * kTZ;
-    t.x = t.x0 + (threadIdx.x & 31);
-    t.y = t.y0 + ((threadIdx.x >> 5) & 3);
-    t.z[0] = t.z0 + (threadIdx.x >> 7);
-    t.z[1] = t.z[0] + 2;
+    t.x0 = (b % ntx) * G::TX;
+    t.y0 = ((b / ntx) % nty) * G::TY;
+    t.z0 = (b / (ntx * nty)) * G::TZ;
+    t.lx = tid % G::TX + kHalo;
+    t.ly = (tid / G::TX) % G::TY + kHalo;
+    t.lz = tid / (G::TX * G::TY) + kHalo;
+    t.x = t.x0 + t.lx - kHalo;
+    t.y = t.y0 + t.ly - kHalo;
+    t.z[0] = t.z0 + t.lz - kHalo;
+    t.z[1] = t.z[0] + G::TZ / 2;
     return t;
+}
+
+template <class G>
+int num_tiles(const GridD& g) {
+    return ((g.nx + G::TX - 1) / G::TX) * ((g.ny + G::TY - 1) / G::TY) * ((g.nz + G::TZ - 1) / G::TZ);
 }
 
 // a * b rounded once to the nearest integer, for |a b| < 2^22: the product is
@@ -369,52 +401,84 @@ __device__ __forceinline__ int round_prod_small(float a, float b) {
     return __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4b400000;
 }
 
-// The tile's box of ref (the 32x4x4 tile plus a kHalo-voxel halo) staged in
-// shared memory as (x, x+1) pairs: sv2[i] = (ref at box index i, ref one voxel
-// further along x), zero outside the grid.  Displaced samples whose cell lies
-// inside the box read their 8 corners as four aligned 8-byte loads instead of
-// going through L1/L2.  Each warp stages whole box rows: lane l loads x = l
-// and (for l < kBX - 32) x = 32 + l, and the right neighbour comes from the
-// next lane by a shuffle.
-template <typename T>
+// The tile's box of ref (the tile plus a kHalo-voxel halo) staged in shared
+// memory as (x, x+1) pairs: the pair of box voxel (x, row) = (ref there, ref
+// one voxel further along x), zero outside the grid, rows G::PX pairs apart.
+// Displaced samples whose cell lies inside the box read their 8 corners as
+// four aligned 8-byte loads instead of going through L1/L2.  A box row of 16
+// is staged by a half-warp and stored at x ^ 8 in odd rows (pair_col); a row
+// of 33 to 64 by a warp, lane l loading x = l and (for l < BX - 32)
+// x = 32 + l.  The right neighbour comes from the next lane by a shuffle;
+// the last pair of a row (never a lower cell corner) holds a zero.
+// Column of box x in a row of the pair box: rotated by 8 pairs in odd rows
+// of a 16-pair box (the row parity is the y parity, BY being even).
+template <class G>
+__device__ __forceinline__ int pair_col(int x, int row) {
+    if constexpr (G::BX == 16) {
+        static_assert(G::PX == 16 && G::BY % 2 == 0, "rotation of 16-pair rows");
+        return x ^ ((row & 1) << 3);
+    } else {
+        return x;
+    }
+}
+
+template <class G, typename T>
 __device__ __forceinline__ void stage_halo_pairs(const T* __restrict__ ref, const GridD& g, int bx0, int by0,
                                                  int bz0, float2* sv2) {
-    static_assert(kBX > 32 && kBX <= 64, "a box row spans one or two warp widths");
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int xa = bx0 + lane, xb = bx0 + 32 + lane;
-    const bool ina = (unsigned)xa < (unsigned)g.nx, inb = lane < kBX - 32 && (unsigned)xb < (unsigned)g.nx;
-    for (int row = warp; row < kBY * kBZ; row += nw) {
-        const int y = by0 + row % kBY, z = bz0 + row / kBY;
-        const bool inr = (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz;
-        const int64_t base = ((int64_t)z * g.ny + y) * g.nx;
-        const float va = inr && ina ? Store<T>::ld(ref, base + xa) : 0.0f;
-        const float vb = inr && inb ? Store<T>::ld(ref, base + xb) : 0.0f;
-        const float va1 = __shfl_down_sync(0xffffffffu, va, 1);
-        const float vb0 = __shfl_sync(0xffffffffu, vb, 0);
-        const float vb1 = __shfl_down_sync(0xffffffffu, vb, 1);
-        float2* r = sv2 + row * kBX;
-        r[lane] = make_float2(va, lane == 31 ? vb0 : va1);
-        if (lane < kBX - 32) r[32 + lane] = make_float2(vb, lane == kBX - 33 ? 0.0f : vb1);
+    constexpr int BX = G::BX, ROWS = G::BY * G::BZ;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (BX == 16) {
+        static_assert(ROWS % (2 * G::WARPS) == 0, "the same row count per warp");
+        const int xl = lane & 15, x = bx0 + xl;
+        const bool inx = (unsigned)x < (unsigned)g.nx;
+        for (int row = 2 * warp + (lane >> 4); row < ROWS; row += 2 * G::WARPS) {
+            const int y = by0 + row % G::BY, z = bz0 + row / G::BY;
+            const bool in = inx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz;
+            const float va = in ? Store<T>::ld(ref, ((int64_t)z * g.ny + y) * g.nx + x) : 0.0f;
+            const float va1 = __shfl_down_sync(0xffffffffu, va, 1);
+            sv2[row * G::PX + pair_col<G>(xl, row)] = make_float2(va, xl == BX - 1 ? 0.0f : va1);
+        }
+    } else {
+        static_assert(BX > 32 && BX <= 64, "a box row spans one or two warp widths");
+        const int xa = bx0 + lane, xb = bx0 + 32 + lane;
+        const bool ina = (unsigned)xa < (unsigned)g.nx, inb = lane < BX - 32 && (unsigned)xb < (unsigned)g.nx;
+        for (int row = warp; row < ROWS; row += G::WARPS) {
+            const int y = by0 + row % G::BY, z = bz0 + row / G::BY;
+            const bool inr = (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz;
+            const int64_t base = ((int64_t)z * g.ny + y) * g.nx;
+            const float va = inr && ina ? Store<T>::ld(ref, base + xa) : 0.0f;
+            const float vb = inr && inb ? Store<T>::ld(ref, base + xb) : 0.0f;
+            const float va1 = __shfl_down_sync(0xffffffffu, va, 1);
+            const float vb0 = __shfl_sync(0xffffffffu, vb, 0);
+            const float vb1 = __shfl_down_sync(0xffffffffu, vb, 1);
+            float2* r = sv2 + row * G::PX;
+            r[lane] = make_float2(va, lane == 31 ? vb0 : va1);
+            if (lane < BX - 32) r[32 + lane] = make_float2(vb, lane == BX - 33 ? 0.0f : vb1);
+        }
     }
 }
 
 // The 8 corners of the cell whose lower corner is box cell (rx, ry, rz), from
 // the pair box (the caller has checked that the cell lies inside the box).
+template <class G>
 __device__ __forceinline__ void corners8_pairs(const float2* sv2, int rx, int ry, int rz, float cv[8]) {
-    const int i = (rz * kBY + ry) * kBX + rx;
-    if (!PMF_DCHECK(i >= 0 && i + kBX * kBY + kBX < kBoxN)) {
+    constexpr int SY = G::PX, SZ = G::PX * G::BY;
+    const int r0 = rz * G::BY + ry;  // rows of the cell's y and y + 1 corners (and +BY for z + 1)
+    const int i0 = r0 * SY + pair_col<G>(rx, r0), i1 = (r0 + 1) * SY + pair_col<G>(rx, r0 + 1);
+    if (!PMF_DCHECK(i0 >= 0 && i1 >= 0 && i0 + SZ < G::BOXN && i1 + SZ < G::BOXN)) {
 #pragma unroll
         for (int c = 0; c < 8; c++) cv[c] = 0.0f;
         return;
     }
-    const float2* q = sv2 + i;
-    const float2 c00 = q[0], c10 = q[kBX], c01 = q[kBX * kBY], c11 = q[kBX * kBY + kBX];
+    const float2 c00 = sv2[i0], c10 = sv2[i1], c01 = sv2[i0 + SZ], c11 = sv2[i1 + SZ];
     cv[0] = c00.x; cv[1] = c00.y; cv[2] = c10.x; cv[3] = c10.y;
     cv[4] = c01.x; cv[5] = c01.y; cv[6] = c11.x; cv[7] = c11.y;
 }
 
+template <class G>
 __device__ __forceinline__ bool in_box(int rx, int ry, int rz) {
-    return (unsigned)rx < (unsigned)(kBX - 1) && (unsigned)ry < (unsigned)(kBY - 1) && (unsigned)rz < (unsigned)(kBZ - 1);
+    return (unsigned)rx < (unsigned)(G::BX - 1) && (unsigned)ry < (unsigned)(G::BY - 1) &&
+           (unsigned)rz < (unsigned)(G::BZ - 1);
 }
 
 // Box coordinate r = l + floor(t) of the lower cell corner and the fraction
@@ -436,20 +500,21 @@ __device__ __forceinline__ void stage_coeff4(const float* __restrict__ w, int PL
 }
 
 template <typename T, typename TO, int L>
-__global__ void __launch_bounds__(256, 3) k_wc_fwd_tile(GridD g, int P, const T* __restrict__ ref,
+__global__ void __launch_bounds__(GeomFwd::THREADS, 6) k_wc_fwd_tile(GridD g, int P, const T* __restrict__ ref,
                                                      const T* __restrict__ E, const float* __restrict__ w,
                                                      TO* __restrict__ W) {
+    using G = GeomFwd;
     extern __shared__ float4 smem_f4[];
     float4* sw4 = smem_f4;                          // [P][L] coefficients
-    float2* sv2 = (float2*)(smem_f4 + P * L);       // [kBZ][kBY][kBX] ref pairs
+    float2* sv2 = (float2*)(smem_f4 + P * L);       // [BZ][BY][PX] ref pairs
     stage_coeff4(w, P * L, sw4);
-    const TileIdx t = tile_idx(g);
-    stage_halo_pairs(ref, g, t.x0 - kHalo, t.y0 - kHalo, t.z0 - kHalo, sv2);
+    const TileIdx t = tile_idx<G>(g);
+    stage_halo_pairs<G>(ref, g, t.x0 - kHalo, t.y0 - kHalo, t.z0 - kHalo, sv2);
     __syncthreads();
     if (t.x >= g.nx || t.y >= g.ny) return;
     const int64_t N = g.n;
-    // box coordinates of the thread's voxels (z and z + 2)
-    const int lx = (threadIdx.x & 31) + kHalo, ly = ((threadIdx.x >> 5) & 3) + kHalo, lz = (threadIdx.x >> 7) + kHalo;
+    // box coordinates of the thread's voxels (z and z + TZ / 2)
+    const int lx = t.lx, ly = t.ly, lz = t.lz;
     bool in[2];
     float e[2][L][3];
     TO* out[2];
@@ -486,9 +551,10 @@ __global__ void __launch_bounds__(256, 3) k_wc_fwd_tile(GridD g, int P, const T*
             }
             const float tx = d0, ty = d1, tz = d2;
             float fx, fy, fz, cv[8];
-            const int rx = box_floor(tx, lx, fx), ry = box_floor(ty, ly, fy), rz = box_floor(tz, lz + 2 * h, fz);
-            if (in_box(rx, ry, rz)) {
-                corners8_pairs(sv2, rx, ry, rz, cv);
+            const int rx = box_floor(tx, lx, fx), ry = box_floor(ty, ly, fy);
+            const int rz = box_floor(tz, lz + h * (G::TZ / 2), fz);
+            if (in_box<G>(rx, ry, rz)) {
+                corners8_pairs<G>(sv2, rx, ry, rz, cv);
             } else {
                 int ox, oy, oz;
                 split_offset(tx, ox, fx);
@@ -559,27 +625,29 @@ __device__ __forceinline__ int exp_bits(float bound, int bits) {
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(256, 2) k_wc_bwd_tile(GridD g, int P, const T* __restrict__ ref,
+__global__ void __launch_bounds__(GeomBwd::THREADS, 2) k_wc_bwd_tile(GridD g, int P, const T* __restrict__ ref,
                                                         const T* __restrict__ E, const float* __restrict__ w,
                                                         const float* __restrict__ dW, float* d_mbc,
                                                         unsigned long long* acc, const unsigned* maxbits, float* part,
                                                         int accumulate) {
+    using G = GeomBwd;
     constexpr int K = 3 * L;  // coefficient-gradient values of one view
+    constexpr int SY = G::PX, SZ = G::PX * G::BY;
     extern __shared__ float4 smem_b4[];
     const int PL = P * L, PK = P * K;
     float4* sw4 = smem_b4;                         // [P][L] coefficients
-    float2* sv2 = (float2*)(sw4 + PL);             // [kBZ][kBY][kBX] ref pairs
-    int* box = (int*)(sv2 + kBoxN);                // [kBZ][kBY][kBX] fixed-point dV
-    float* swarp = (float*)(box + kBoxN);          // [8 warps][P][L][3]
-    __shared__ float red_sum[8];
+    float2* sv2 = (float2*)(sw4 + PL);             // [BZ][BY][PX] ref pairs
+    int* box = (int*)(sv2 + G::BOXN);              // [BZ][BY][PX] fixed-point dV
+    float* swarp = (float*)(box + G::BOXN);        // [warps][P][L][3]
+    __shared__ float red_sum[G::WARPS];
     __shared__ unsigned red_max;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     stage_coeff4(w, PL, sw4);
-    for (int i = threadIdx.x; i < kBoxN; i += 256) box[i] = 0;
-    for (int i = threadIdx.x; i < 8 * PK; i += 256) swarp[i] = 0.f;
+    for (int i = threadIdx.x; i < G::BOXN; i += G::THREADS) box[i] = 0;
+    for (int i = threadIdx.x; i < G::WARPS * PK; i += G::THREADS) swarp[i] = 0.f;
     if (threadIdx.x == 0) red_max = 0u;
-    const TileIdx t = tile_idx(g);
-    stage_halo_pairs(ref, g, t.x0 - kHalo, t.y0 - kHalo, t.z0 - kHalo, sv2);
+    const TileIdx t = tile_idx<G>(g);
+    stage_halo_pairs<G>(ref, g, t.x0 - kHalo, t.y0 - kHalo, t.z0 - kHalo, sv2);
     const int64_t N = g.n;
     bool in[2];
     int64_t v[2];
@@ -608,13 +676,13 @@ __global__ void __launch_bounds__(256, 2) k_wc_bwd_tile(GridD g, int P, const T*
     }
     __syncthreads();
     float stot = 0.f;
-    for (int i = 0; i < 8; i++) stot += red_sum[i];
+    for (int i = 0; i < G::WARPS; i++) stot += red_sum[i];
     const int kg = fixed_exponent(__uint_as_float(*maxbits) * (float)(N * P));
     const int kb = min(min(exp_bits(stot, 29), exp_bits(__uint_as_float(red_max), 21)), kg);
     const float sb = ldexpf(1.0f, kb), sg = ldexpf(1.0f, kg);
     const int shift = kg - kb;
     const int bx0 = t.x0 - kHalo, by0 = t.y0 - kHalo, bz0 = t.z0 - kHalo;
-    const int lx = lane + kHalo, ly = (warp & 3) + kHalo, lz = (warp >> 2) + kHalo;
+    const int lx = t.lx, ly = t.ly, lz = t.lz;
     const int slot = split_slot<K>(lane);
 
     bool halo_exit = false;
@@ -668,11 +736,12 @@ __global__ void __launch_bounds__(256, 2) k_wc_bwd_tile(GridD g, int P, const T*
             }
             const float tx = d0, ty = d1, tz = d2;
             Cell cl;
-            const int rx = box_floor(tx, lx, cl.fx), ry = box_floor(ty, ly, cl.fy), rz = box_floor(tz, lz + 2 * h, cl.fz);
-            const bool inside = in_box(rx, ry, rz);
+            const int rx = box_floor(tx, lx, cl.fx), ry = box_floor(ty, ly, cl.fy);
+            const int rz = box_floor(tz, lz + h * (G::TZ / 2), cl.fz);
+            const bool inside = in_box<G>(rx, ry, rz);
             float gx, gy, gz, cv[8];
             if (inside) {
-                corners8_pairs(sv2, rx, ry, rz, cv);
+                corners8_pairs<G>(sv2, rx, ry, rz, cv);
             } else {
                 int ox, oy, oz;
                 split_offset(tx, ox, cl.fx);
@@ -693,9 +762,8 @@ __global__ void __launch_bounds__(256, 2) k_wc_bwd_tile(GridD g, int P, const T*
             }
             // V's adjoint: the 8 trilinear corners, each weight times gw rounded
             // once to the CTA's fixed point
-            if (inside && PMF_DCHECK((rz * kBY + ry) * kBX + rx >= 0 &&
-                                     (rz * kBY + ry) * kBX + rx + kBX * kBY + kBX + 1 < kBoxN)) {
-                int* q = box + (rz * kBY + ry) * kBX + rx;
+            if (inside && PMF_DCHECK(rz * SZ + ry * SY + rx >= 0 && rz * SZ + ry * SY + rx + SZ + SY + 1 < G::BOXN)) {
+                int* q = box + rz * SZ + ry * SY + rx;
                 const float gz0 = gw * sb * (1.f - cl.fz), gz1 = gw * sb * cl.fz;
                 const float wyz[2][2] = {{gz0 * (1.f - cl.fy), gz0 * cl.fy}, {gz1 * (1.f - cl.fy), gz1 * cl.fy}};
                 const float wx0 = 1.f - cl.fx, wx1 = cl.fx;
@@ -703,7 +771,7 @@ __global__ void __launch_bounds__(256, 2) k_wc_bwd_tile(GridD g, int P, const T*
                 for (int dz = 0; dz < 2; dz++)
 #pragma unroll
                     for (int dy = 0; dy < 2; dy++) {
-                        int* r = q + (dz * kBY + dy) * kBX;
+                        int* r = q + dz * SZ + dy * SY;
                         atomicAdd(r, round_prod_small(wyz[dz][dy], wx0));
                         atomicAdd(r + 1, round_prod_small(wyz[dz][dy], wx1));
                     }
@@ -730,15 +798,15 @@ __global__ void __launch_bounds__(256, 2) k_wc_bwd_tile(GridD g, int P, const T*
             }
     }
     if (__syncthreads_or(halo_exit) && threadIdx.x == 0) diag_count(PMF_DIAG_WARP_HALO_EXIT);
-    for (int i = threadIdx.x; i < PK; i += 256) {
+    for (int i = threadIdx.x; i < PK; i += G::THREADS) {
         float r = 0.f;
-        for (int wi = 0; wi < 8; wi++) r += swarp[wi * PK + i];
+        for (int wi = 0; wi < G::WARPS; wi++) r += swarp[wi * PK + i];
         part[(int64_t)i * gridDim.x + blockIdx.x] = r;
     }
-    for (int i = threadIdx.x; i < kBoxN; i += 256) {
+    for (int i = threadIdx.x; i < G::BOXN; i += G::THREADS) {
         const int val = box[i];
-        if (val == 0) continue;
-        const int x = bx0 + i % kBX, y = by0 + (i / kBX) % kBY, z = bz0 + i / (kBX * kBY);
+        if (val == 0) continue;  // also the padding columns of a pitch wider than the box
+        const int x = bx0 + i % SY, y = by0 + (i / SY) % G::BY, z = bz0 + i / SZ;
         if ((unsigned)x < (unsigned)g.nx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz)
             atomicAdd(acc + ((int64_t)z * g.ny + y) * g.nx + x, (unsigned long long)((long long)val * (1ll << shift)));
     }
@@ -766,12 +834,8 @@ void launch_wc_bwd(unsigned nt, size_t smem, cudaStream_t s, const GridD& g, int
                    const float* coeff, const float* d_out, float* d_mbc, unsigned long long* acc,
                    const unsigned* maxbits, float* part, int accumulate) {
     cudaFuncSetAttribute(k_wc_bwd_tile<T, LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_wc_bwd_tile<T, LL><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, d_out, d_mbc, acc, maxbits,
+    k_wc_bwd_tile<T, LL><<<nt, GeomBwd::THREADS, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, d_out, d_mbc, acc, maxbits,
                                                 part, accumulate);
-}
-
-int num_tiles(const GridD& g) {
-    return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + kTZ - 1) / kTZ);
 }
 
 unsigned stream_blocks(int64_t work) {
@@ -896,15 +960,15 @@ template <typename T, typename TO, int LL>
 void launch_wc_fwd(unsigned nt, size_t smem, cudaStream_t s, const GridD& g, int P, const void* ref, const void* mbc,
                    const float* coeff, void* out) {
     cudaFuncSetAttribute(k_wc_fwd_tile<T, TO, LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_wc_fwd_tile<T, TO, LL><<<nt, 256, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out);
+    k_wc_fwd_tile<T, TO, LL><<<nt, GeomFwd::THREADS, smem, s>>>(g, P, (const T*)ref, (const T*)mbc, coeff, (TO*)out);
 }
 
 template <typename T, typename TO>
 pmf_status launch_warp_combine(const GridD& g, int32_t L, int32_t P, const void* ref, const void* mbc,
                                const float* coeff, void* out, cudaStream_t s) {
     if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
-        const size_t smem = sizeof(float4) * (size_t)(P * L) + sizeof(float2) * (size_t)kBoxN;
-        const unsigned nt = (unsigned)num_tiles(g);
+        const size_t smem = sizeof(float4) * (size_t)(P * L) + sizeof(float2) * (size_t)GeomFwd::BOXN;
+        const unsigned nt = (unsigned)num_tiles<GeomFwd>(g);
         switch (L) {
             case 1: launch_wc_fwd<T, TO, 1>(nt, smem, s, g, P, ref, mbc, coeff, out); break;
             case 2: launch_wc_fwd<T, TO, 2>(nt, smem, s, g, P, ref, mbc, coeff, out); break;
@@ -954,7 +1018,7 @@ pmf_status warp_combine_backward_workspace(const pmf_grid* grid, int32_t L, int3
     if (st != PMF_OK) return st;
     PMF_REQUIRE(bytes != nullptr && P >= 0 && L >= 1 && L <= kMaxL, "bad arguments");
     GridD g = make_grid(grid);
-    const size_t nb = (size_t)(num_tiles(g) > kStreamBlocks ? num_tiles(g) : kStreamBlocks);
+    const size_t nb = (size_t)(num_tiles<GeomBwd>(g) > kStreamBlocks ? num_tiles<GeomBwd>(g) : kStreamBlocks);
     *bytes = align_up(256) + align_up(sizeof(unsigned long long) * (size_t)g.n) +
              align_up(sizeof(float) * (size_t)P * L * 3 * nb);
     return PMF_OK;
@@ -984,9 +1048,9 @@ pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf
         k_absmax<<<stream_blocks(g.n * P), kThreads, 0, s>>>(d_out, g.n * P, maxbits);
         if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
             const int PL3 = P * L * 3;
-            const size_t smem2 = sizeof(float4) * (size_t)(P * L) + (sizeof(float2) + sizeof(int)) * (size_t)kBoxN +
-                                 sizeof(float) * (size_t)(8 * PL3);
-            const unsigned nt = (unsigned)num_tiles(g);
+            const size_t smem2 = sizeof(float4) * (size_t)(P * L) + (sizeof(float2) + sizeof(int)) * (size_t)GeomBwd::BOXN +
+                                 sizeof(float) * (size_t)(GeomBwd::WARPS * PL3);
+            const unsigned nt = (unsigned)num_tiles<GeomBwd>(g);
             PMF_DISPATCH_DTYPE(dtype, T, {
                 switch (L) {
                     case 1: launch_wc_bwd<T, 1>(nt, smem2, s, g, P, ref, mbc, coeff, d_out, d_mbc, acc, maxbits, part, accumulate); break;

@@ -409,6 +409,22 @@ __global__ void __launch_bounds__(RPB, 768 / RPB) k_backproject_batched(const __
     }
 }
 
+// One work item per CTA (the default launch): the same tile, without the
+// work-list loop.
+template <int CH, int RPB>
+__global__ void __launch_bounds__(RPB, 768 / RPB) k_backproject_batched1(const __grid_constant__ ProjBatch B) {
+    extern __shared__ int box[];  // box_words<CH>()
+    __shared__ BoxState bs;
+    __shared__ unsigned sgmax;
+    __shared__ float gsum[RPB / 32];
+    for (int i = threadIdx.x; i < box_words<CH>(); i += RPB) box[i] = 0;
+    const int64_t w = blockIdx.x;
+    const ProjItem it = B.it[find_item(B, w)];
+    const int local = (int)(w - it.begin);
+    backproject_tile<CH, RPB>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, it.dproj, it.vol_stride, it.acc, it.maxbits,
+                     it.bound_mult, it.spv, local / it.ntiles, local % it.ntiles, box, bs, sgmax, gsum);
+}
+
 // blockIdx.y = item
 __global__ void k_absmax_batched(const __grid_constant__ ProjBatch B) {
     const ProjItem& it = B.it[blockIdx.y];
@@ -517,8 +533,13 @@ pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items
         const unsigned nc = persistent_ctas(total, ctas, sh.rays, ntl, n);
         PMF_DISPATCH_ADJOINT(sh, CH, RPB, {
             constexpr int smem = (int)sizeof(int) * box_words<CH>();
-            cudaFuncSetAttribute(k_backproject_batched<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            k_backproject_batched<CH, RPB><<<nc, RPB, smem, s>>>(B);
+            if ((int64_t)nc == total) {
+                cudaFuncSetAttribute(k_backproject_batched1<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                k_backproject_batched1<CH, RPB><<<nc, RPB, smem, s>>>(B);
+            } else {
+                cudaFuncSetAttribute(k_backproject_batched<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                k_backproject_batched<CH, RPB><<<nc, RPB, smem, s>>>(B);
+            }
         });
     }
     const int64_t nc = (maxcells + 255) / 256;

@@ -302,10 +302,13 @@ __device__ __forceinline__ Box read_box(const BoxState& bs, int sel) {
 // ------------------------------------------------- batched (uneven) launches
 //
 // Several volumes -- different grids, detectors and view counts -- in one
-// persistent launch: work item w is tile (w - begin_i) % ntiles_i of view
-// (w - begin_i) / ntiles_i of item i, and each CTA walks the work items
-// round-robin.  A tile's arithmetic is the single-volume kernel's, so the
-// results equal per-volume launches bit for bit.
+// launch: work item w is tile (w - begin_i) % ntiles_i of view
+// (w - begin_i) / ntiles_i of item i.  By default each CTA runs one work item
+// (kernels without a work-list loop, which compile to the single-volume
+// kernels' code: the loop forms ran 0.5-1% slower per tile); a persistent
+// launch of fewer CTAs walks the work items round-robin.  A tile's arithmetic
+// is the single-volume kernel's, so the results equal per-volume launches bit
+// for bit.
 
 constexpr int kMaxItems = 16;
 

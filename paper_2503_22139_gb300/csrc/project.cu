@@ -386,6 +386,38 @@ __global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched(const __gri
     }
 }
 
+// One work item per CTA (the default launch): the same tiles, without the
+// work-list loop.
+template <int CH, int RPB>
+__global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched_tma1(const __grid_constant__ ProjBatchTma T) {
+    extern __shared__ __align__(128) float box[];  // kTmaBox floats
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ BoxState bs;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    const int64_t w = blockIdx.x;
+    const int i = find_item(T.B, w);
+    const ProjItem& it = T.B.it[i];
+    const int local = (int)(w - it.begin);
+    project_tile_tma<CH, RPB>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, &T.map[i], (const float*)it.vol,
+                              it.vol_stride, it.proj, local / it.ntiles, local % it.ntiles, box, &bar, bs, parity);
+}
+
+template <typename T, int CH, int RPB>
+__global__ void __launch_bounds__(RPB, 1024 / RPB) k_project_batched1(const __grid_constant__ ProjBatch B) {
+    extern __shared__ __align__(128) float box[];  // kPlainBox floats
+    __shared__ BoxState bs;
+    const int64_t w = blockIdx.x;
+    const ProjItem it = B.it[find_item(B, w)];
+    const int local = (int)(w - it.begin);
+    project_tile<T, CH, RPB>(it.g, it.nu, it.nv, it.ntu, it.step, it.views, (const T*)it.vol, it.vol_stride, it.proj,
+                    local / it.ntiles, local % it.ntiles, box, bs);
+}
+
 // cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -496,17 +528,29 @@ pmf_status project_batched_impl(int32_t n, const pmf_project_item* items, pmf_dt
         if (all) {
             tb.B = B;
             PMF_DISPATCH_PROJ(sh, CH, RPB, {
-                cudaFuncSetAttribute(k_project_batched_tma<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(kTmaBox * sizeof(float)));
-                k_project_batched_tma<CH, RPB><<<nc, RPB, kTmaBox * sizeof(float), s>>>(tb);
+                if ((int64_t)nc == total) {
+                    cudaFuncSetAttribute(k_project_batched_tma1<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kTmaBox * sizeof(float)));
+                    k_project_batched_tma1<CH, RPB><<<nc, RPB, kTmaBox * sizeof(float), s>>>(tb);
+                } else {
+                    cudaFuncSetAttribute(k_project_batched_tma<CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kTmaBox * sizeof(float)));
+                    k_project_batched_tma<CH, RPB><<<nc, RPB, kTmaBox * sizeof(float), s>>>(tb);
+                }
             });
             return check_launch("conebeam_project_batched");
         }
     }
     PMF_DISPATCH_PROJ(sh, CH, RPB, PMF_DISPATCH_DTYPE(dtype, T, {
-        cudaFuncSetAttribute(k_project_batched<T, CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kPlainBox * sizeof(float)));
-        k_project_batched<T, CH, RPB><<<nc, RPB, kPlainBox * sizeof(float), s>>>(B);
+        if ((int64_t)nc == total) {
+            cudaFuncSetAttribute(k_project_batched1<T, CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kPlainBox * sizeof(float)));
+            k_project_batched1<T, CH, RPB><<<nc, RPB, kPlainBox * sizeof(float), s>>>(B);
+        } else {
+            cudaFuncSetAttribute(k_project_batched<T, CH, RPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kPlainBox * sizeof(float)));
+            k_project_batched<T, CH, RPB><<<nc, RPB, kPlainBox * sizeof(float), s>>>(B);
+        }
     }));
     return check_launch("conebeam_project_batched");
 }

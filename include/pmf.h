@@ -268,6 +268,21 @@ pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf
                                  float* d_mbc, float* d_coeff, int accumulate, void* ws, size_t ws_bytes,
                                  pmf_stream stream);
 
+/* warp_combine_backward given the maximum of |d_out|: d_out_absmax_bits
+ * (device, 4 bytes, read on `stream`) holds max |d_out[.]| as the bits of the
+ * float with the sign cleared (0x7fffffff & bits; a NaN in d_out gives bits
+ * above those of +inf), as conebeam_project_backward_absmax writes it.  That
+ * maximum sets the fixed-point scale of d_ref; this call then skips its own
+ * pass over d_out, and with the exact maximum its results are bit-identical to
+ * warp_combine_backward's.  A larger value is a valid bound (d_ref then loses
+ * low-order bits); a smaller one can overflow the accumulator.  Workspace as
+ * warp_combine_backward_workspace.  PMF_EINVAL if d_out_absmax_bits is null. */
+pmf_status warp_combine_backward_bounded(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype,
+                                         const void* ref, const void* mbc, const float* coeff,
+                                         const float* d_out, const unsigned* d_out_absmax_bits, float* d_ref,
+                                         float* d_mbc, float* d_coeff, int accumulate, void* ws,
+                                         size_t ws_bytes, pmf_stream stream);
+
 /* ------------------------------------------- cone-beam projector (Eq. 6) */
 
 /* proj[p][b][a] = step * sum_{m >= 0} Trilin(vol_p, idx(src_p + m step r_pab)),
@@ -289,6 +304,18 @@ pmf_status conebeam_project_backward(const pmf_grid* grid, const pmf_detector* d
                                      const pmf_view* views, const float* d_proj, float* d_vol,
                                      int64_t vol_stride, int accumulate, void* ws, size_t ws_bytes,
                                      pmf_stream stream);
+
+/* conebeam_project_backward that also writes max |d_vol| over every element
+ * it writes (after accumulation) to d_vol_absmax_bits (device, 4 bytes, set on
+ * `stream`) as the bits of the float with the sign cleared, from the kernel
+ * that converts the accumulator, so a consumer that needs the bound
+ * (warp_combine_backward_bounded) does not read d_vol for it.  d_vol's values
+ * are those of conebeam_project_backward.  PMF_EINVAL if d_vol_absmax_bits is
+ * null. */
+pmf_status conebeam_project_backward_absmax(const pmf_grid* grid, const pmf_detector* det, int32_t P,
+                                            const pmf_view* views, const float* d_proj, float* d_vol,
+                                            int64_t vol_stride, int accumulate, void* ws, size_t ws_bytes,
+                                            unsigned* d_vol_absmax_bits, pmf_stream stream);
 
 /* ------------------------------------- batched, uneven projector launches */
 

@@ -113,9 +113,13 @@ SIGNATURES = {
     "warp_combine_mixed": [_G, _I32, _I32, ct.c_int, _P, _P, _P, ct.c_int, _P, _P],
     "warp_combine_backward_workspace": [_G, _I32, _I32, _SZ],
     "warp_combine_backward": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t, _P],
+    "warp_combine_backward_bounded": [_G, _I32, _I32, ct.c_int, _P, _P, _P, _P, _P, _P, _P, _P, ct.c_int, _P, ct.c_size_t,
+                                      _P],
     "conebeam_project": [_G, ct.POINTER(PmfDetector), _I32, _P, ct.c_int, _P, _I64, _P, _P],
     "conebeam_project_backward_workspace": [_G, _I32, _I64, _SZ],
     "conebeam_project_backward": [_G, ct.POINTER(PmfDetector), _I32, _P, _P, _P, _I64, ct.c_int, _P, ct.c_size_t, _P],
+    "conebeam_project_backward_absmax": [_G, ct.POINTER(PmfDetector), _I32, _P, _P, _P, _I64, ct.c_int, _P, ct.c_size_t,
+                                         _P, _P],
     "conebeam_project_batched": [_I32, ct.POINTER(PmfProjectItem), ct.c_int, _P],
     "conebeam_project_backward_batched_workspace": [_I32, ct.POINTER(PmfBackprojectItem), _SZ],
     "conebeam_project_backward_batched": [_I32, ct.POINTER(PmfBackprojectItem), ct.c_int, _P, ct.c_size_t, _P],

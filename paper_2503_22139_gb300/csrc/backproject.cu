@@ -379,17 +379,64 @@ __global__ void __launch_bounds__(RPB, 768 / RPB) k_backproject(GridD g, int nu,
                      blockIdx.y, blockIdx.x, box, bs, sgmax, gsum);
 }
 
+// The fixed-point accumulator to fp32 (added to out when accumulating).  MAX:
+// also the maximum of |out| over the written values, as abs_bits, into
+// *out_max (zeroed by the caller): the bound a consumer of out would
+// otherwise take in a pass of its own.  Blocks are whole warps.
+template <bool MAX>
 __global__ void k_fixed_to_float_f(const unsigned long long* __restrict__ acc, int64_t n, const unsigned* maxbits,
-                                   float bound_mult, float* out, int accumulate) {
+                                   float bound_mult, float* out, int accumulate, unsigned* out_max) {
     const float bound = __uint_as_float(*maxbits) * bound_mult;
     const int kexp = fixed_exponent(bound);
     const float inv = ldexpf(1.0f, -kexp);
     const bool bad = !isfinite(bound);
     if (bad && blockIdx.x == 0 && threadIdx.x == 0) diag_count(PMF_DIAG_NONFINITE);
+    unsigned m = 0u;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const float r = bad ? __int_as_float(0x7fc00000) : from_fixed(acc[t], inv);
-        out[t] = accumulate ? out[t] + r : r;
+        const float v = accumulate ? out[t] + r : r;
+        out[t] = v;
+        if (MAX) m = max(m, abs_bits(v));
     }
+    if (MAX) block_max_bits(m, out_max);
+}
+
+// Four values per thread and iteration: two 16-byte accumulator loads and one
+// 16-byte store (out 16-byte aligned); the n % 4 tail element by element.
+template <bool MAX>
+__global__ void k_fixed_to_float_f4(const unsigned long long* __restrict__ acc, int64_t n, const unsigned* maxbits,
+                                    float bound_mult, float* out, int accumulate, unsigned* out_max) {
+    const float bound = __uint_as_float(*maxbits) * bound_mult;
+    const int kexp = fixed_exponent(bound);
+    const float inv = ldexpf(1.0f, -kexp);
+    const bool bad = !isfinite(bound);
+    if (bad && blockIdx.x == 0 && threadIdx.x == 0) diag_count(PMF_DIAG_NONFINITE);
+    const float qnan = __int_as_float(0x7fc00000);
+    unsigned m = 0u;
+    const int64_t n4 = n >> 2, g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    const ulonglong2* a2 = (const ulonglong2*)acc;
+    float4* o4 = (float4*)out;
+    for (int64_t t = g0; t < n4; t += gs) {
+        const ulonglong2 p = a2[2 * t], q = a2[2 * t + 1];
+        float4 r;
+        r.x = bad ? qnan : from_fixed(p.x, inv);
+        r.y = bad ? qnan : from_fixed(p.y, inv);
+        r.z = bad ? qnan : from_fixed(q.x, inv);
+        r.w = bad ? qnan : from_fixed(q.y, inv);
+        if (accumulate) {
+            const float4 o = o4[t];
+            r.x = o.x + r.x; r.y = o.y + r.y; r.z = o.z + r.z; r.w = o.w + r.w;
+        }
+        o4[t] = r;
+        if (MAX) m = max(m, max(max(abs_bits(r.x), abs_bits(r.y)), max(abs_bits(r.z), abs_bits(r.w))));
+    }
+    for (int64_t t = 4 * n4 + g0; t < n; t += gs) {
+        const float r = bad ? qnan : from_fixed(acc[t], inv);
+        const float v = accumulate ? out[t] + r : r;
+        out[t] = v;
+        if (MAX) m = max(m, abs_bits(v));
+    }
+    if (MAX) block_max_bits(m, out_max);
 }
 
 template <int CH, int RPB>
@@ -431,22 +478,29 @@ __global__ void k_absmax_batched(const __grid_constant__ ProjBatch B) {
     absmax_bits(it.dproj, it.nq, it.maxbits);
 }
 
-__global__ void k_fixed_to_float_batched(const __grid_constant__ ProjBatch B, int accumulate) {
+// As k_fixed_to_float_f for every item (blockIdx.y = item); out_max takes the
+// maximum over all items.
+template <bool MAX>
+__global__ void k_fixed_to_float_batched(const __grid_constant__ ProjBatch B, int accumulate, unsigned* out_max) {
     const ProjItem& it = B.it[blockIdx.y];
     const float bound = __uint_as_float(*it.maxbits) * it.bound_mult;
     const int kexp = fixed_exponent(bound);
     const float inv = ldexpf(1.0f, -kexp);
     const bool bad = !isfinite(bound);
     if (bad && blockIdx.x == 0 && threadIdx.x == 0) diag_count(PMF_DIAG_NONFINITE);
+    unsigned m = 0u;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < it.cells; t += (int64_t)gridDim.x * blockDim.x) {
         const float r = bad ? __int_as_float(0x7fc00000) : from_fixed(it.acc[t], inv);
-        it.dvol[t] = accumulate ? it.dvol[t] + r : r;
+        const float v = accumulate ? it.dvol[t] + r : r;
+        it.dvol[t] = v;
+        if (MAX) m = max(m, abs_bits(v));
     }
+    if (MAX) block_max_bits(m, out_max);
 }
 
 pmf_status backproject_grid(const pmf_grid* grid, const pmf_detector* det, int32_t P, const pmf_view* views,
                             const float* d_proj, float* d_vol, int64_t vol_stride, int accumulate, void* ws,
-                            size_t ws_bytes, const MarchShape& sh, cudaStream_t s) {
+                            size_t ws_bytes, const MarchShape& sh, cudaStream_t s, unsigned* out_max = nullptr) {
     pmf_status st = check_proj(grid, det, P, views);
     if (st != PMF_OK) return st;
     PMF_REQUIRE(vol_stride >= 0, "vol_stride must be >= 0");
@@ -477,8 +531,15 @@ pmf_status backproject_grid(const pmf_grid* grid, const pmf_detector* det, int32
         });
     }
     int64_t nb = (cells + 255) / 256;
-    k_fixed_to_float_f<<<(unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks), 256, 0, s>>>(
-        acc, cells, maxbits, bound_mult, d_vol, accumulate);
+    if (out_max) cudaMemsetAsync(out_max, 0, sizeof(unsigned), s);
+    const unsigned ncv = (unsigned)(nb < 4 * kStreamBlocks ? nb : 4 * kStreamBlocks);
+    if (((uintptr_t)d_vol & 15) == 0) {
+        if (out_max) k_fixed_to_float_f4<true><<<ncv, 256, 0, s>>>(acc, cells, maxbits, bound_mult, d_vol, accumulate, out_max);
+        else k_fixed_to_float_f4<false><<<ncv, 256, 0, s>>>(acc, cells, maxbits, bound_mult, d_vol, accumulate, out_max);
+    } else {
+        if (out_max) k_fixed_to_float_f<true><<<ncv, 256, 0, s>>>(acc, cells, maxbits, bound_mult, d_vol, accumulate, out_max);
+        else k_fixed_to_float_f<false><<<ncv, 256, 0, s>>>(acc, cells, maxbits, bound_mult, d_vol, accumulate, out_max);
+    }
     return check_launch("conebeam_project_backward");
 }
 
@@ -489,7 +550,8 @@ size_t bp_item_bytes(const pmf_backproject_item& it) {
 }
 
 pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items, int accumulate, void* ws,
-                                    size_t ws_bytes, const MarchShape& sh, unsigned ctas, cudaStream_t s) {
+                                    size_t ws_bytes, const MarchShape& sh, unsigned ctas, cudaStream_t s,
+                                    unsigned* out_max = nullptr) {
     size_t need = 0;
     pmf_status st = conebeam_project_backward_batched_workspace(n, items, &need);
     if (st != PMF_OK) return st;
@@ -521,6 +583,7 @@ pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items
         maxcells = it.cells > maxcells ? it.cells : maxcells;
     }
     B.total = total;
+    if (out_max) cudaMemsetAsync(out_max, 0, sizeof(unsigned), s);
     if (n == 0) return PMF_OK;
     cudaMemsetAsync(ws, 0, need, s);
     if (maxq > 0) {
@@ -543,8 +606,9 @@ pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items
         });
     }
     const int64_t nc = (maxcells + 255) / 256;
-    k_fixed_to_float_batched<<<dim3((unsigned)(nc < 4 * kStreamBlocks ? nc : 4 * kStreamBlocks), (unsigned)n), 256, 0, s>>>(
-        B, accumulate);
+    const dim3 gc((unsigned)(nc < 4 * kStreamBlocks ? nc : 4 * kStreamBlocks), (unsigned)n);
+    if (out_max) k_fixed_to_float_batched<true><<<gc, 256, 0, s>>>(B, accumulate, out_max);
+    else k_fixed_to_float_batched<false><<<gc, 256, 0, s>>>(B, accumulate, out_max);
     return check_launch("conebeam_project_backward_batched");
 }
 
@@ -553,12 +617,12 @@ pmf_status backproject_batched_impl(int32_t n, const pmf_backproject_item* items
 PMF_DIAG_ACCESSOR(diag_backproject)
 
 pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes,
-                              const MarchShape& sh, cudaStream_t s) {
+                              const MarchShape& sh, cudaStream_t s, unsigned* out_max) {
     if (!valid_shape(sh, true)) return set_error(PMF_EINVAL, "invalid march shape");
     if (sh.form == 0)
         return backproject_grid(&it.grid, &it.det, it.P, it.views, it.d_proj, it.d_vol, it.vol_stride, accumulate,
-                                ws, ws_bytes, sh, s);
-    return backproject_batched_impl(1, &it, accumulate, ws, ws_bytes, sh, (unsigned)(sh.form * num_sms()), s);
+                                ws, ws_bytes, sh, s, out_max);
+    return backproject_batched_impl(1, &it, accumulate, ws, ws_bytes, sh, (unsigned)(sh.form * num_sms()), s, out_max);
 }
 
 }  // namespace pmf
@@ -583,6 +647,15 @@ pmf_status conebeam_project_backward(const pmf_grid* grid, const pmf_detector* d
     return backproject_grid(grid, det, P, views, d_proj, d_vol, vol_stride, accumulate, ws, ws_bytes,
                             default_backproject_shape(),
                             (cudaStream_t)stream);
+}
+
+pmf_status conebeam_project_backward_absmax(const pmf_grid* grid, const pmf_detector* det, int32_t P,
+                                            const pmf_view* views, const float* d_proj, float* d_vol,
+                                            int64_t vol_stride, int accumulate, void* ws, size_t ws_bytes,
+                                            unsigned* d_vol_absmax_bits, pmf_stream stream) {
+    PMF_REQUIRE(d_vol_absmax_bits != nullptr, "d_vol_absmax_bits is null");
+    return backproject_grid(grid, det, P, views, d_proj, d_vol, vol_stride, accumulate, ws, ws_bytes,
+                            default_backproject_shape(), (cudaStream_t)stream, d_vol_absmax_bits);
 }
 
 pmf_status conebeam_project_backward_batched_workspace(int32_t n, const pmf_backproject_item* items, size_t* bytes) {

@@ -26,6 +26,7 @@ struct pmf_plan {
     char* mem = nullptr;
     void *V = nullptr, *E = nullptr, *W = nullptr;
     float *Y = nullptr, *dY = nullptr, *dW = nullptr, *dV = nullptr, *dE = nullptr;
+    unsigned* dW_max = nullptr;  // max |dW| from the back-projector, the warp adjoint's fixed-point bound
     void* vox_ws[1 + PMF_MAX_LEVELS] = {};
     size_t vox_bytes[1 + PMF_MAX_LEVELS] = {};
     void* vb_ws[1 + PMF_MAX_LEVELS] = {};
@@ -208,7 +209,7 @@ pmf_status plan_project(pmf_plan* p, cudaStream_t s) {
 pmf_status plan_backproject(pmf_plan* p, cudaStream_t s) {
     const pmf_batch_desc& d = p->d;
     pmf_backproject_item it{d.grid, d.det, p->B, d.views, p->dY, p->dW, p->N};
-    return backproject_launch(it, 0, p->bp_ws, p->bp_bytes, p->bp, s);
+    return backproject_launch(it, 0, p->bp_ws, p->bp_bytes, p->bp, s, p->dW_max);
 }
 
 pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
@@ -234,8 +235,8 @@ pmf_status enqueue_step(pmf_plan* p, cudaStream_t s) {
         PMF_TRY(projection_dssim(p->B, d.det.nu, d.det.nv, p->Y, d.meas, d.ssim_range, d.lambda_ssim, d.loss, p->dY, 1,
                                  p->ssim_ws, p->ssim_bytes, ps));
     PMF_TRY(plan_backproject(p, s));
-    PMF_TRY(warp_combine_backward(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, p->dW, p->dV, p->dE, d.d_coeff,
-                                  0, p->wc_ws, p->wc_bytes, ps));
+    PMF_TRY(warp_combine_backward_bounded(&d.grid, p->L, p->B, d.dtype, p->V, p->E, d.coeff, p->dW, p->dW_max, p->dV,
+                                          p->dE, d.d_coeff, 0, p->wc_ws, p->wc_bytes, ps));
     if (eq14) {
         PMF_TRY(tv_loss(&d.grid, d.dtype, p->V, d.tv_size, d.tv_origin, d.lambda_tv, d.loss, p->dV, 1, p->tv_ws,
                         p->tv_bytes, ps));
@@ -327,6 +328,7 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     sz.push_back(B * N * 4);                  // dW
     sz.push_back(N * 4);                      // dV
     sz.push_back(L * 3 * N * 4);              // dE
+    sz.push_back(sizeof(unsigned));           // dW_max
     for (int i = 0; i < sets && st == PMF_OK; i++) {
         st = gs_voxelize_tiled_workspace(&d.grid, gset(d, i).n, cap[i], p->tile[i], &p->vox_bytes[i]);
         if (st == PMF_OK) st = gs_voxelize_backward_workspace(&d.grid, gset(d, i).n, gset(d, i).channels, &p->vb_bytes[i]);
@@ -374,6 +376,7 @@ pmf_status plan_create(const pmf_batch_desc* desc, pmf_plan** out) {
     p->dW = (float*)take();
     p->dV = (float*)take();
     p->dE = (float*)take();
+    p->dW_max = (unsigned*)take();
     for (int i = 0; i < sets; i++) p->vox_ws[i] = take();
     for (int i = 0; i < sets; i++) p->vb_ws[i] = take();
     p->bp_ws = take();

@@ -113,8 +113,10 @@ inline MarchShape default_backproject_shape() {
     return m;
 }
 pmf_status project_launch(const pmf_project_item& it, pmf_dtype dtype, const MarchShape& sh, cudaStream_t s);
+// out_max (optional, device): receives max |d_vol| as abs_bits (see
+// conebeam_project_backward_absmax).
 pmf_status backproject_launch(const pmf_backproject_item& it, int accumulate, void* ws, size_t ws_bytes,
-                              const MarchShape& sh, cudaStream_t s);
+                              const MarchShape& sh, cudaStream_t s, unsigned* out_max = nullptr);
 
 // ------------------------------------------------------- storage dtypes
 
@@ -298,6 +300,23 @@ __device__ __forceinline__ void absmax_bits(const float* __restrict__ x, int64_t
         m = max(m, abs_bits(__ldg(x + t)));
     m = __reduce_max_sync(0xffffffffu, m);
     if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// Block-wide maximum of the threads' m (abs bits) into *out: one atomic per
+// block, skipped when *out already holds at least the block's value (*out
+// only grows, so a stale read only costs an atomic).  Same-address atomics
+// from every warp of a large grid serialise in L2.  Every thread of the block
+// calls it; blocks are whole warps.
+__device__ __forceinline__ void block_max_bits(unsigned m, unsigned* out) {
+    __shared__ unsigned wmax[32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (int)(blockDim.x + 31) >> 5;
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (l == 0) wmax[w] = m;
+    __syncthreads();
+    if (w == 0) {
+        m = __reduce_max_sync(0xffffffffu, l < nw ? wmax[l] : 0u);
+        if (l == 0 && m > *(volatile unsigned*)out) atomicMax(out, m);
+    }
 }
 
 // --------------------------------------------------- block reductions

@@ -1024,9 +1024,17 @@ pmf_status warp_combine_backward_workspace(const pmf_grid* grid, int32_t L, int3
     return PMF_OK;
 }
 
-pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
-                                 const void* mbc, const float* coeff, const float* d_out, float* d_ref, float* d_mbc,
-                                 float* d_coeff, int accumulate, void* ws, size_t ws_bytes, pmf_stream stream) {
+}  // extern "C"
+
+namespace pmf {
+namespace {
+
+// The fused adjoint; out_bits (device, optional) holds max |d_out| as abs_bits,
+// computed by the producer of d_out, in place of this call's own pass over it.
+pmf_status wc_backward_impl(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
+                            const void* mbc, const float* coeff, const float* d_out, const unsigned* out_bits,
+                            float* d_ref, float* d_mbc, float* d_coeff, int accumulate, void* ws, size_t ws_bytes,
+                            pmf_stream stream) {
     pmf_status st = check_common(grid, P, dtype);
     if (st != PMF_OK) return st;
     PMF_REQUIRE(L >= 1 && L <= kMaxL, "L must be in [1, %d]", kMaxL);
@@ -1038,14 +1046,15 @@ pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf
     if (smem > 200 * 1024) return set_error(PMF_EUNSUPPORTED, "P*L too large for the fused adjoint (P*L <= %d)", (int)(200 * 1024 / (4 * 8 * 3)));
     GridD g = make_grid(grid);
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned* maxbits = (unsigned*)ws;
+    unsigned* ws_bits = (unsigned*)ws;
+    const unsigned* maxbits = out_bits && P > 0 ? out_bits : ws_bits;
     unsigned long long* acc = (unsigned long long*)((char*)ws + align_up(256));
     float* part = (float*)((char*)acc + align_up(sizeof(unsigned long long) * (size_t)g.n));
     cudaMemsetAsync(ws, 0, align_up(256) + align_up(sizeof(unsigned long long) * (size_t)g.n), s);
     if (P == 0) {
         if (!accumulate) cudaMemsetAsync(d_mbc, 0, sizeof(float) * (size_t)(L * 3 * g.n), s);
     } else {
-        k_absmax<<<stream_blocks(g.n * P), kThreads, 0, s>>>(d_out, g.n * P, maxbits);
+        if (!out_bits) k_absmax<<<stream_blocks(g.n * P), kThreads, 0, s>>>(d_out, g.n * P, ws_bits);
         if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
             const int PL3 = P * L * 3;
             const size_t smem2 = sizeof(float4) * (size_t)(P * L) + (sizeof(float2) + sizeof(int)) * (size_t)GeomBwd::BOXN +
@@ -1073,6 +1082,28 @@ pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf
     }
     k_fixed_to_float<<<stream_blocks(g.n), kThreads, 0, s>>>(acc, g.n, maxbits, (float)(g.n * (int64_t)P), d_ref, accumulate);
     return check_launch("warp_combine_backward");
+}
+
+}  // namespace
+}  // namespace pmf
+
+extern "C" {
+
+pmf_status warp_combine_backward(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
+                                 const void* mbc, const float* coeff, const float* d_out, float* d_ref, float* d_mbc,
+                                 float* d_coeff, int accumulate, void* ws, size_t ws_bytes, pmf_stream stream) {
+    return wc_backward_impl(grid, L, P, dtype, ref, mbc, coeff, d_out, nullptr, d_ref, d_mbc, d_coeff, accumulate, ws,
+                            ws_bytes, stream);
+}
+
+pmf_status warp_combine_backward_bounded(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtype dtype, const void* ref,
+                                         const void* mbc, const float* coeff, const float* d_out,
+                                         const unsigned* d_out_absmax_bits, float* d_ref, float* d_mbc,
+                                         float* d_coeff, int accumulate, void* ws, size_t ws_bytes,
+                                         pmf_stream stream) {
+    PMF_REQUIRE(d_out_absmax_bits != nullptr, "d_out_absmax_bits is null");
+    return wc_backward_impl(grid, L, P, dtype, ref, mbc, coeff, d_out, d_out_absmax_bits, d_ref, d_mbc, d_coeff,
+                            accumulate, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -398,7 +398,16 @@ def warp_combine_mixed(grid, ref, mbc, coeff, out_dtype=torch.float32, out=None)
     return out
 
 
-def warp_combine_backward(grid, ref, mbc, coeff, d_out, accumulate=False, grads=None, ws=None):
+def warp_combine_backward_bounded(grid, ref, mbc, coeff, d_out, d_out_absmax, accumulate=False, grads=None, ws=None):
+    """warp_combine_backward given max |d_out| (abs bits, device int32 [1])."""
+    return warp_combine_backward(grid, ref, mbc, coeff, d_out, accumulate=accumulate, grads=grads, ws=ws,
+                                 d_out_absmax=d_out_absmax)
+
+
+def warp_combine_backward(grid, ref, mbc, coeff, d_out, accumulate=False, grads=None, ws=None, d_out_absmax=None):
+    """d_out_absmax (optional, device int32 [1]): max |d_out| as written by
+    conebeam_project_backward(..., absmax=...); the call then skips its own
+    pass over d_out (warp_combine_backward_bounded)."""
     L = _lib.load()
     ref, mbc = _need(ref, "ref"), _need(mbc, "mbc")
     coeff = _need(coeff, "coeff", torch.float32)
@@ -411,6 +420,13 @@ def warp_combine_backward(grid, ref, mbc, coeff, d_out, accumulate=False, grads=
         grads = (torch.empty(ref.shape, dtype=torch.float32, device=ref.device),
                  torch.empty(mbc.shape, dtype=torch.float32, device=ref.device),
                  torch.empty(coeff.shape, dtype=torch.float32, device=ref.device))
+    if d_out_absmax is not None:
+        d_out_absmax = _need(d_out_absmax, "d_out_absmax", torch.int32)
+        check(L.warp_combine_backward_bounded(ct.byref(g), Lv, P, _DT[ref.dtype], _p(ref), _p(mbc), _p(coeff),
+                                              _p(d_out), _p(d_out_absmax), _p(grads[0]), _p(grads[1]), _p(grads[2]),
+                                              int(accumulate), _p(ws), ws.numel(), _stream()),
+              "warp_combine_backward_bounded")
+        return grads
     check(L.warp_combine_backward(ct.byref(g), Lv, P, _DT[ref.dtype], _p(ref), _p(mbc), _p(coeff), _p(d_out),
                                   _p(grads[0]), _p(grads[1]), _p(grads[2]), int(accumulate), _p(ws), ws.numel(),
                                   _stream()), "warp_combine_backward")
@@ -445,7 +461,11 @@ def conebeam_project(grid, det, views: torch.Tensor, vol: torch.Tensor, shared: 
 
 
 def conebeam_project_backward(grid, det, views, d_proj, shared: bool = False, accumulate=False, out=None,
-                              ws=None) -> torch.Tensor:
+                              ws=None, absmax=None) -> torch.Tensor:
+    """absmax (optional, device int32 [1]): receives max |out| as the bits of
+    the float with the sign cleared (conebeam_project_backward_absmax), the
+    bound warp_combine_backward(..., d_out_absmax=absmax) takes instead of a
+    pass of its own over out."""
     L = _lib.load()
     views = _need(views, "views", torch.float64)
     d_proj = _need(d_proj, "d_proj", torch.float32)
@@ -458,9 +478,23 @@ def conebeam_project_backward(grid, det, views, d_proj, shared: bool = False, ac
         ws = _ws(_size(L.conebeam_project_backward_workspace, ct.byref(g), P, stride), d_proj.device)
     if out is None:
         out = torch.empty(shape if shared else (P,) + shape, dtype=torch.float32, device=d_proj.device)
+    if absmax is not None:
+        absmax = _need(absmax, "absmax", torch.int32)
+        check(L.conebeam_project_backward_absmax(ct.byref(g), ct.byref(d), P, _p(views), _p(d_proj), _p(out), stride,
+                                                 int(accumulate), _p(ws), ws.numel(), _p(absmax), _stream()),
+              "conebeam_project_backward_absmax")
+        return out
     check(L.conebeam_project_backward(ct.byref(g), ct.byref(d), P, _p(views), _p(d_proj), _p(out), stride,
                                       int(accumulate), _p(ws), ws.numel(), _stream()), "conebeam_project_backward")
     return out
+
+
+def conebeam_project_backward_absmax(grid, det, views, d_proj, absmax, shared: bool = False, accumulate=False,
+                                     out=None, ws=None) -> torch.Tensor:
+    """conebeam_project_backward that also writes max |out| (abs bits) to
+    absmax (device int32 [1])."""
+    return conebeam_project_backward(grid, det, views, d_proj, shared=shared, accumulate=accumulate, out=out, ws=ws,
+                                     absmax=absmax)
 
 
 def conebeam_project_batched(items, out=None):

@@ -23,7 +23,9 @@ from .ops import Gaussians
 # kernels each entry point launches (memsets excluded): used for the launch count
 KERNELS = {
     "gs_voxelize": 4, "gs_voxelize_backward": 2, "warp_combine": 1, "conebeam_project": 1,
-    "projection_loss": 2, "conebeam_project_backward": 3, "warp_combine_backward": 4,
+    # warp_combine_backward as the step calls it: bounded by the back-projector's
+    # max |dW|, so without an abs-max pass of its own (4 launches unbounded)
+    "projection_loss": 2, "conebeam_project_backward": 3, "warp_combine_backward": 3,
     "projection_dssim": 3, "tv_loss": 2, "mbc_normality": 3,
     # rasterizer: frames, prep, 3 scan passes, fill, render; adjoint: frames, prep, sums, chain
     "gs_rasterize": 7, "gs_rasterize_backward": 4, "pmf_shift_means": 1,
@@ -75,6 +77,7 @@ class ForwardAdjoint:
         self.W = torch.empty((self.B,) + shape, dtype=w_dtype, device=dev)
         self.Y = torch.empty((self.B, det.nv, det.nu), dtype=torch.float32, device=dev)
         self.dW = torch.empty((self.B,) + shape, dtype=torch.float32, device=dev)
+        self.dW_max = torch.zeros(1, dtype=torch.int32, device=dev)  # max |dW| bits, from the back-projector
         self.g_ref = (torch.empty((ref.n, 3), device=dev), torch.empty((ref.n, 3), device=dev),
                       torch.empty((ref.n, 4), device=dev), torch.empty((ref.n, ref.channels), device=dev))
         self.g_mbc = [(torch.empty((m.n, 3), device=dev), torch.empty((m.n, 3), device=dev),
@@ -140,8 +143,9 @@ class ForwardAdjoint:
         if q is not None:
             ops.projection_dssim(self.Y, meas, q["data_range"], weight=q["lambda_ssim"], loss=loss, d_pred=dY,
                                  accumulate=True, ws=self.ssim_ws)
-        ops.conebeam_project_backward(g, det, views, dY, shared=False, out=self.dW, ws=self.bp_ws)
-        ops.warp_combine_backward(g, self.V[0], self.E, coeff, self.dW, grads=self.g_wc, ws=self.wc_ws)
+        ops.conebeam_project_backward(g, det, views, dY, shared=False, out=self.dW, ws=self.bp_ws, absmax=self.dW_max)
+        ops.warp_combine_backward(g, self.V[0], self.E, coeff, self.dW, grads=self.g_wc, ws=self.wc_ws,
+                                  d_out_absmax=self.dW_max)
         if q is not None:
             if tv_origin is not None and tv_origin.data_ptr() != self.tv_origin.data_ptr():
                 self.tv_origin.copy_(tv_origin, non_blocking=True)

@@ -163,3 +163,17 @@ def test_tiled_voxelizer_and_threshold_host_validation():
     for n, rank, scale in ((10, 10, 1.0), (10, -1, 1.0), (0, 0, 1.0), (10, 3, math.inf)):
         assert _status("gs_density_threshold", n, fake, scale, rank, fake, None) == -1, (n, rank, scale)
     assert _status("gs_density_threshold", 10, None, 1.0, 3, fake, None) == -1
+
+
+def test_fused_bound_entry_points_need_their_bound_pointer():
+    """conebeam_project_backward_absmax and warp_combine_backward_bounded
+    reject a null bound pointer on the host, before any device work."""
+    g = _lib.PmfGrid(8, 8, 8, 1.0, 1.0, 1.0)
+    d = _lib.PmfDetector(8, 8, 1.0)
+    fake = ct.c_void_p(256)
+    assert _status("conebeam_project_backward_absmax", ct.byref(g), ct.byref(d), 1, fake, fake, fake, 512, 0, fake,
+                   1 << 20, None, None) == -1
+    assert b"absmax" in _lib.load().pmf_last_error()
+    assert _status("warp_combine_backward_bounded", ct.byref(g), 3, 2, 0, fake, fake, fake, fake, None, fake, fake,
+                   fake, 0, fake, 1 << 20, None) == -1
+    assert b"absmax" in _lib.load().pmf_last_error()

@@ -339,32 +339,40 @@ __global__ void __launch_bounds__(kThreads) k_warp_combine_bwd(GridD g, int L, i
 // with 64-bit fixed-point atomics at the call's global scale; targets outside
 // the halo go straight to global memory.
 //
-// The forward takes an 8x8x4 tile (128 threads; a warp covers 8 x 4 voxels
-// of one plane): eight voxels along x leave few ragged tiles (a 200-voxel row
-// is 25 tiles, where 32-wide tiles left a quarter-full last column) and the
-// near-cubic tile keeps the staged halo small.  The adjoint keeps a 32x4x4
-// tile (256 threads, a warp per row): its per-CTA work (zeroing and flushing
-// the fixed-point box, the coefficient-gradient partials) is paid per tile,
-// and the smaller tile's share of it outweighed the ragged column.
+// Both take tiles eight voxels wide (a warp covers 8 x 4 voxels of one
+// plane): a 200-voxel row is 25 tiles, where 32-wide tiles left a
+// quarter-full last column whose warps paid full cost for 8 voxels.  The
+// forward takes an 8x8x4 tile (128 threads), which keeps the staged halo
+// small; the adjoint an 8x16x4 tile (256 threads), whose per-CTA work (zeroing
+// and flushing the fixed-point box, the coefficient-gradient partials) per
+// voxel matches the 32x4x4 tile's -- on an 8x8x4 tile that work, paid by twice
+// as many CTAs, outweighed the ragged column.
 
 constexpr int kHalo = 4;
 constexpr int kMaxPLTile = 512;  // P * L limit of the tiled path
 
-template <int TX_, int TY_, int TZ_, int PX_>
+template <int TX_, int TY_, int TZ_, int PX_, int IX_ = PX_>
 struct TileGeom {
     static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
     static constexpr int THREADS = TX * TY * TZ / 2, WARPS = THREADS / 32;
     static constexpr int BX = TX + 2 * kHalo, BY = TY + 2 * kHalo, BZ = TZ + 2 * kHalo;
-    static constexpr int PX = PX_;               // row pitch (elements) of the staged boxes
-    static constexpr int BOXN = PX * BY * BZ;    // elements of a staged box
-    static_assert(TZ % 2 == 0 && THREADS % 32 == 0 && PX >= BX, "tile shape");
+    static constexpr int PX = PX_;               // row pitch (pairs) of the staged ref box
+    static constexpr int BOXN = PX * BY * BZ;    // pairs of the staged ref box
+    static constexpr int IX = IX_;               // row pitch (words) of the adjoint's fixed-point box
+    static constexpr int IBOXN = IX * BY * BZ;
+    static_assert(TZ % 2 == 0 && THREADS % 32 == 0 && PX >= BX && IX >= BX, "tile shape");
 };
 // Forward: 16-pair rows (32 words), odd rows rotated by 8 pairs.  8-byte
 // shared loads are served per half-warp, and a half-warp of the forward reads
 // two adjacent rows of 8 pairs: the rotation puts them on complementary
 // halves of the 32 banks.
 using GeomFwd = TileGeom<8, 8, 4, 16>;
-using GeomBwd = TileGeom<32, 4, 4, 40>;
+// Adjoint: an 8x16x4 tile of 256 threads, the same CTA size as a 32x4x4 tile
+// (its per-CTA work per voxel unchanged) without a ragged x column on a
+// 200-voxel row; ragged y tiles leave whole warps outside the grid, which skip
+// the per-voxel work.  Fixed-point rows 24 words apart put a warp's four rows
+// of atomics on disjoint banks.
+using GeomBwd = TileGeom<8, 16, 4, 16, 24>;
 
 struct TileIdx {
     int x0, y0, z0;
@@ -632,18 +640,18 @@ __global__ void __launch_bounds__(GeomBwd::THREADS, 2) k_wc_bwd_tile(GridD g, in
                                                         int accumulate) {
     using G = GeomBwd;
     constexpr int K = 3 * L;  // coefficient-gradient values of one view
-    constexpr int SY = G::PX, SZ = G::PX * G::BY;
+    constexpr int SY = G::IX, SZ = G::IX * G::BY;  // fixed-point box strides
     extern __shared__ float4 smem_b4[];
     const int PL = P * L, PK = P * K;
     float4* sw4 = smem_b4;                         // [P][L] coefficients
     float2* sv2 = (float2*)(sw4 + PL);             // [BZ][BY][PX] ref pairs
-    int* box = (int*)(sv2 + G::BOXN);              // [BZ][BY][PX] fixed-point dV
-    float* swarp = (float*)(box + G::BOXN);        // [warps][P][L][3]
+    int* box = (int*)(sv2 + G::BOXN);              // [BZ][BY][IX] fixed-point dV
+    float* swarp = (float*)(box + G::IBOXN);       // [warps][P][L][3]
     __shared__ float red_sum[G::WARPS];
     __shared__ unsigned red_max;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     stage_coeff4(w, PL, sw4);
-    for (int i = threadIdx.x; i < G::BOXN; i += G::THREADS) box[i] = 0;
+    for (int i = threadIdx.x; i < G::IBOXN; i += G::THREADS) box[i] = 0;
     for (int i = threadIdx.x; i < G::WARPS * PK; i += G::THREADS) swarp[i] = 0.f;
     if (threadIdx.x == 0) red_max = 0u;
     const TileIdx t = tile_idx<G>(g);
@@ -762,7 +770,7 @@ __global__ void __launch_bounds__(GeomBwd::THREADS, 2) k_wc_bwd_tile(GridD g, in
             }
             // V's adjoint: the 8 trilinear corners, each weight times gw rounded
             // once to the CTA's fixed point
-            if (inside && PMF_DCHECK(rz * SZ + ry * SY + rx >= 0 && rz * SZ + ry * SY + rx + SZ + SY + 1 < G::BOXN)) {
+            if (inside && PMF_DCHECK(rz * SZ + ry * SY + rx >= 0 && rz * SZ + ry * SY + rx + SZ + SY + 1 < G::IBOXN)) {
                 int* q = box + rz * SZ + ry * SY + rx;
                 const float gz0 = gw * sb * (1.f - cl.fz), gz1 = gw * sb * cl.fz;
                 const float wyz[2][2] = {{gz0 * (1.f - cl.fy), gz0 * cl.fy}, {gz1 * (1.f - cl.fy), gz1 * cl.fy}};
@@ -803,7 +811,7 @@ __global__ void __launch_bounds__(GeomBwd::THREADS, 2) k_wc_bwd_tile(GridD g, in
         for (int wi = 0; wi < G::WARPS; wi++) r += swarp[wi * PK + i];
         part[(int64_t)i * gridDim.x + blockIdx.x] = r;
     }
-    for (int i = threadIdx.x; i < G::BOXN; i += G::THREADS) {
+    for (int i = threadIdx.x; i < G::IBOXN; i += G::THREADS) {
         const int val = box[i];
         if (val == 0) continue;  // also the padding columns of a pitch wider than the box
         const int x = bx0 + i % SY, y = by0 + (i / SY) % G::BY, z = bz0 + i / SZ;
@@ -1057,8 +1065,8 @@ pmf_status wc_backward_impl(const pmf_grid* grid, int32_t L, int32_t P, pmf_dtyp
         if (!out_bits) k_absmax<<<stream_blocks(g.n * P), kThreads, 0, s>>>(d_out, g.n * P, ws_bits);
         if (L <= 4 && (int64_t)P * L <= kMaxPLTile && g.n < ((int64_t)1 << 31)) {
             const int PL3 = P * L * 3;
-            const size_t smem2 = sizeof(float4) * (size_t)(P * L) + (sizeof(float2) + sizeof(int)) * (size_t)GeomBwd::BOXN +
-                                 sizeof(float) * (size_t)(GeomBwd::WARPS * PL3);
+            const size_t smem2 = sizeof(float4) * (size_t)(P * L) + sizeof(float2) * (size_t)GeomBwd::BOXN +
+                                 sizeof(int) * (size_t)GeomBwd::IBOXN + sizeof(float) * (size_t)(GeomBwd::WARPS * PL3);
             const unsigned nt = (unsigned)num_tiles<GeomBwd>(g);
             PMF_DISPATCH_DTYPE(dtype, T, {
                 switch (L) {

@@ -255,7 +255,7 @@ def test_combine_and_warp_backward_match_oracle():
 
 @pytest.mark.parametrize("L", [1, 2, 4])
 def test_fused_warp_tile_kernels_every_level_count(L):
-    """The tile kernels (8x8x4 forward, 32x4x4 adjoint) are instantiated per level count (L <= 4); each
+    """The tile kernels (8x8x4 forward, 8x16x4 adjoint) are instantiated per level count (L <= 4); each
     reduces its 3 L coefficient-gradient values per view across the warp by
     halving exchange, whose slot layout depends on 3 L.  Forward and adjoint of
     every instance against the oracle on a ragged grid."""
@@ -552,7 +552,7 @@ def test_projector_source_inside_volume():
 
 @pytest.mark.parametrize("L,std", [(3, 6.0), (1, 1.0), (4, 3.0)])
 def test_fused_warp_tiles_with_large_displacements(L, std):
-    """Ragged tiles (8x8x4 forward, 32x4x4 adjoint) and displacements well past the 4-voxel shared-memory
+    """Ragged tiles (8x8x4 forward, 8x16x4 adjoint) and displacements well past the 4-voxel shared-memory
     halo (std 6 mm at 2 mm voxels): both the box and the direct scatter paths."""
     grid = Grid(37, 9, 7, 2.0, 2.0, 2.0)
     rng = np.random.default_rng(40 + L)

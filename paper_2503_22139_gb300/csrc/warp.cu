@@ -362,16 +362,13 @@ struct TileGeom {
     static constexpr int IBOXN = IX * BY * BZ;
     static_assert(TZ % 2 == 0 && THREADS % 32 == 0 && PX >= BX && IX >= BX, "tile shape");
 };
-// Forward: 16-pair rows (32 words), odd rows rotated by 8 pairs.  8-byte
-// shared loads are served per half-warp, and a half-warp of the forward reads
-// two adjacent rows of 8 pairs: the rotation puts them on complementary
-// halves of the 32 banks.
+// Forward: 16-pair rows (32 words), odd rows rotated by 8 pairs (pair_col).
 using GeomFwd = TileGeom<8, 8, 4, 16>;
 // Adjoint: an 8x16x4 tile of 256 threads, the same CTA size as a 32x4x4 tile
 // (its per-CTA work per voxel unchanged) without a ragged x column on a
 // 200-voxel row; ragged y tiles leave whole warps outside the grid, which skip
-// the per-voxel work.  Fixed-point rows 24 words apart put a warp's four rows
-// of atomics on disjoint banks.
+// the per-voxel work.  Its pair box as the forward's; fixed-point rows 24
+// words apart put a warp's four rows of atomics on disjoint banks.
 using GeomBwd = TileGeom<8, 16, 4, 16, 24>;
 
 struct TileIdx {
@@ -409,60 +406,38 @@ __device__ __forceinline__ int round_prod_small(float a, float b) {
     return __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4b400000;
 }
 
-// The tile's box of ref (the tile plus a kHalo-voxel halo) staged in shared
-// memory as (x, x+1) pairs: the pair of box voxel (x, row) = (ref there, ref
-// one voxel further along x), zero outside the grid, rows G::PX pairs apart.
-// Displaced samples whose cell lies inside the box read their 8 corners as
-// four aligned 8-byte loads instead of going through L1/L2.  A box row of 16
-// is staged by a half-warp and stored at x ^ 8 in odd rows (pair_col); a row
-// of 33 to 64 by a warp, lane l loading x = l and (for l < BX - 32)
-// x = 32 + l.  The right neighbour comes from the next lane by a shuffle;
-// the last pair of a row (never a lower cell corner) holds a zero.
 // Column of box x in a row of the pair box: rotated by 8 pairs in odd rows
-// of a 16-pair box (the row parity is the y parity, BY being even).
+// (the row parity is the y parity, BY being even).  8-byte shared loads are
+// served per half-warp, and a half-warp reads two adjacent rows of 8 pairs:
+// the rotation puts them on complementary halves of the 32 banks.
 template <class G>
 __device__ __forceinline__ int pair_col(int x, int row) {
-    if constexpr (G::BX == 16) {
-        static_assert(G::PX == 16 && G::BY % 2 == 0, "rotation of 16-pair rows");
-        return x ^ ((row & 1) << 3);
-    } else {
-        return x;
-    }
+    static_assert(G::BX == 16 && G::PX == 16 && G::BY % 2 == 0, "rotation of 16-pair rows");
+    return x ^ ((row & 1) << 3);
 }
 
+// The tile's box of ref (the tile plus a kHalo-voxel halo) staged in shared
+// memory as (x, x+1) pairs: the pair of box voxel (x, row) = (ref there, ref
+// one voxel further along x), zero outside the grid, at column pair_col of
+// rows G::PX pairs apart.  Displaced samples whose cell lies inside the box
+// read their 8 corners as four aligned 8-byte loads instead of going through
+// L1/L2.  Each half-warp stages one 16-voxel box row, the right neighbour
+// coming from the next lane by a shuffle; the last pair of a row (never a
+// lower cell corner) holds a zero.
 template <class G, typename T>
 __device__ __forceinline__ void stage_halo_pairs(const T* __restrict__ ref, const GridD& g, int bx0, int by0,
                                                  int bz0, float2* sv2) {
     constexpr int BX = G::BX, ROWS = G::BY * G::BZ;
+    static_assert(BX == 16 && ROWS % (2 * G::WARPS) == 0, "half-warp rows, the same row count per warp");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if constexpr (BX == 16) {
-        static_assert(ROWS % (2 * G::WARPS) == 0, "the same row count per warp");
-        const int xl = lane & 15, x = bx0 + xl;
-        const bool inx = (unsigned)x < (unsigned)g.nx;
-        for (int row = 2 * warp + (lane >> 4); row < ROWS; row += 2 * G::WARPS) {
-            const int y = by0 + row % G::BY, z = bz0 + row / G::BY;
-            const bool in = inx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz;
-            const float va = in ? Store<T>::ld(ref, ((int64_t)z * g.ny + y) * g.nx + x) : 0.0f;
-            const float va1 = __shfl_down_sync(0xffffffffu, va, 1);
-            sv2[row * G::PX + pair_col<G>(xl, row)] = make_float2(va, xl == BX - 1 ? 0.0f : va1);
-        }
-    } else {
-        static_assert(BX > 32 && BX <= 64, "a box row spans one or two warp widths");
-        const int xa = bx0 + lane, xb = bx0 + 32 + lane;
-        const bool ina = (unsigned)xa < (unsigned)g.nx, inb = lane < BX - 32 && (unsigned)xb < (unsigned)g.nx;
-        for (int row = warp; row < ROWS; row += G::WARPS) {
-            const int y = by0 + row % G::BY, z = bz0 + row / G::BY;
-            const bool inr = (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz;
-            const int64_t base = ((int64_t)z * g.ny + y) * g.nx;
-            const float va = inr && ina ? Store<T>::ld(ref, base + xa) : 0.0f;
-            const float vb = inr && inb ? Store<T>::ld(ref, base + xb) : 0.0f;
-            const float va1 = __shfl_down_sync(0xffffffffu, va, 1);
-            const float vb0 = __shfl_sync(0xffffffffu, vb, 0);
-            const float vb1 = __shfl_down_sync(0xffffffffu, vb, 1);
-            float2* r = sv2 + row * G::PX;
-            r[lane] = make_float2(va, lane == 31 ? vb0 : va1);
-            if (lane < BX - 32) r[32 + lane] = make_float2(vb, lane == BX - 33 ? 0.0f : vb1);
-        }
+    const int xl = lane & 15, x = bx0 + xl;
+    const bool inx = (unsigned)x < (unsigned)g.nx;
+    for (int row = 2 * warp + (lane >> 4); row < ROWS; row += 2 * G::WARPS) {
+        const int y = by0 + row % G::BY, z = bz0 + row / G::BY;
+        const bool in = inx && (unsigned)y < (unsigned)g.ny && (unsigned)z < (unsigned)g.nz;
+        const float va = in ? Store<T>::ld(ref, ((int64_t)z * g.ny + y) * g.nx + x) : 0.0f;
+        const float va1 = __shfl_down_sync(0xffffffffu, va, 1);
+        sv2[row * G::PX + pair_col<G>(xl, row)] = make_float2(va, xl == BX - 1 ? 0.0f : va1);
     }
 }
 
@@ -523,8 +498,10 @@ __global__ void __launch_bounds__(GeomFwd::THREADS, 6) k_wc_fwd_tile(GridD g, in
     const int64_t N = g.n;
     // box coordinates of the thread's voxels (z and z + TZ / 2)
     const int lx = t.lx, ly = t.ly, lz = t.lz;
+    const f32x2 M2 = pack2(12582912.0f, 12582912.0f);
     bool in[2];
-    float e[2][L][3];
+    f32x2 exy[2][L];
+    float ez[2][L];
     TO* out[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -532,34 +509,46 @@ __global__ void __launch_bounds__(GeomFwd::THREADS, 6) k_wc_fwd_tile(GridD g, in
         const int64_t v = in[h] ? ((int64_t)t.z[h] * g.ny + t.y) * g.nx + t.x : 0;
         out[h] = W + v;
 #pragma unroll
-        for (int l = 0; l < L; l++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) e[h][l][a] = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + a) * N + v) : 0.0f;
-#pragma unroll
         for (int l = 0; l < L; l++) {  // MBC vectors in voxels: the displacement is then sum_l c e
-            e[h][l][0] *= g.ivx;
-            e[h][l][1] *= g.ivy;
-            e[h][l][2] *= g.ivz;
+            const float ex = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + 0) * N + v) : 0.0f;
+            const float ey = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + 1) * N + v) : 0.0f;
+            const float e_z = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + 2) * N + v) : 0.0f;
+            exy[h][l] = pack2(ex * g.ivx, ey * g.ivy);
+            ez[h][l] = e_z * g.ivz;
         }
     }
     for (int p = 0; p < P; p++) {
-        float4 c[L];
+        f32x2 cxy[L];
+        float cz[L];
 #pragma unroll
-        for (int l = 0; l < L; l++) c[l] = sw4[p * L + l];
+        for (int l = 0; l < L; l++) {
+            const float4 c = sw4[p * L + l];
+            cxy[l] = pack2(c.x, c.y);
+            cz[l] = c.z;
+        }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             // a voxel beyond the grid's last z plane (e = 0, no store) runs the
             // same code, so the loop has no branch on it
-            float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+            // the x and y displacements as one packed pair: their blend, and the
+            // round-down add and the fractions of box_floor, take one
+            // instruction for both (each half the scalar operation's bits)
+            f32x2 dxy = pack2(0.0f, 0.0f);
+            float dz = 0.0f;
 #pragma unroll
             for (int l = 0; l < L; l++) {
-                d0 = fmaf(c[l].x, e[h][l][0], d0);
-                d1 = fmaf(c[l].y, e[h][l][1], d1);
-                d2 = fmaf(c[l].z, e[h][l][2], d2);
+                dxy = fma2(cxy[l], exy[h][l], dxy);
+                dz = fmaf(cz[l], ez[h][l], dz);
             }
-            const float tx = d0, ty = d1, tz = d2;
+            const float tx = lo2(dxy), ty = hi2(dxy), tz = dz;
             float fx, fy, fz, cv[8];
-            const int rx = box_floor(tx, lx, fx), ry = box_floor(ty, ly, fy);
+            f32x2 tt;
+            asm("add.rm.f32x2 %0, %1, %2;" : "=l"(tt) : "l"(dxy), "l"(M2));
+            const f32x2 fxy = sub2(dxy, sub2(tt, M2));
+            fx = lo2(fxy);
+            fy = hi2(fxy);
+            const int rx = (int)((unsigned)__float_as_int(lo2(tt)) - (0x4b400000u - (unsigned)lx));
+            const int ry = (int)((unsigned)__float_as_int(hi2(tt)) - (0x4b400000u - (unsigned)ly));
             const int rz = box_floor(tz, lz + h * (G::TZ / 2), fz);
             if (in_box<G>(rx, ry, rz)) {
                 corners8_pairs<G>(sv2, rx, ry, rz, cv);
@@ -694,26 +683,24 @@ __global__ void __launch_bounds__(GeomBwd::THREADS, 2) k_wc_bwd_tile(GridD g, in
     const int slot = split_slot<K>(lane);
 
     bool halo_exit = false;
-    float e[2][L][3], gE[2][L][3];
-#pragma unroll
-    for (int h = 0; h < 2; h++)
-#pragma unroll
-        for (int l = 0; l < L; l++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                e[h][l][a] = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + a) * N + v[h]) : 0.f;
-                gE[h][l][a] = 0.f;
-            }
-    // MBC vectors in voxels (as in the forward); the per-view DVF gradient then
-    // stays in voxel units and the 1 / voxel factors are applied once at the end
+    // MBC vectors in voxels (as in the forward), x and y as packed pairs; the
+    // per-view DVF gradient then stays in voxel units and the 1 / voxel
+    // factors are applied once at the end
+    f32x2 exy[2][L], gExy[2][L];
+    float ez[2][L], gEz[2][L];
 #pragma unroll
     for (int h = 0; h < 2; h++)
 #pragma unroll
         for (int l = 0; l < L; l++) {
-            e[h][l][0] *= g.ivx;
-            e[h][l][1] *= g.ivy;
-            e[h][l][2] *= g.ivz;
+            const float ex = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + 0) * N + v[h]) : 0.f;
+            const float ey = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + 1) * N + v[h]) : 0.f;
+            const float e_z = in[h] ? Store<T>::ld(E, ((int64_t)l * 3 + 2) * N + v[h]) : 0.f;
+            exy[h][l] = pack2(ex * g.ivx, ey * g.ivy);
+            ez[h][l] = e_z * g.ivz;
+            gExy[h][l] = pack2(0.f, 0.f);
+            gEz[h][l] = 0.f;
         }
+    const f32x2 M2 = pack2(12582912.0f, 12582912.0f);
     // dW of the next view is loaded one view ahead
     float gw_next[2];
 #pragma unroll
@@ -725,26 +712,36 @@ __global__ void __launch_bounds__(GeomBwd::THREADS, 2) k_wc_bwd_tile(GridD g, in
             gwv[h] = gw_next[h];
             gw_next[h] = in[h] && p + 1 < P ? __ldg(dW + (int64_t)(p + 1) * N + v[h]) : 0.f;
         }
-        float4 c[L];
+        f32x2 cxy[L], cwxy[L];
+        float cz[L], cwz[L];
 #pragma unroll
-        for (int l = 0; l < L; l++) c[l] = sw4[p * L + l];
-        float cw[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) cw[k] = 0.f;
+        for (int l = 0; l < L; l++) {
+            const float4 c = sw4[p * L + l];
+            cxy[l] = pack2(c.x, c.y);
+            cz[l] = c.z;
+            cwxy[l] = pack2(0.f, 0.f);
+            cwz[l] = 0.f;
+        }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const float gw = gwv[h];
             if (gw == 0.f) continue;  // also every voxel outside the grid
-            float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+            f32x2 dxy = pack2(0.f, 0.f);
+            float dz = 0.0f;
 #pragma unroll
             for (int l = 0; l < L; l++) {
-                d0 = fmaf(c[l].x, e[h][l][0], d0);
-                d1 = fmaf(c[l].y, e[h][l][1], d1);
-                d2 = fmaf(c[l].z, e[h][l][2], d2);
+                dxy = fma2(cxy[l], exy[h][l], dxy);
+                dz = fmaf(cz[l], ez[h][l], dz);
             }
-            const float tx = d0, ty = d1, tz = d2;
+            const float tx = lo2(dxy), ty = hi2(dxy), tz = dz;
             Cell cl;
-            const int rx = box_floor(tx, lx, cl.fx), ry = box_floor(ty, ly, cl.fy);
+            f32x2 tt;
+            asm("add.rm.f32x2 %0, %1, %2;" : "=l"(tt) : "l"(dxy), "l"(M2));
+            const f32x2 fxy = sub2(dxy, sub2(tt, M2));
+            cl.fx = lo2(fxy);
+            cl.fy = hi2(fxy);
+            const int rx = (int)((unsigned)__float_as_int(lo2(tt)) - (0x4b400000u - (unsigned)lx));
+            const int ry = (int)((unsigned)__float_as_int(hi2(tt)) - (0x4b400000u - (unsigned)ly));
             const int rz = box_floor(tz, lz + h * (G::TZ / 2), cl.fz);
             const bool inside = in_box<G>(rx, ry, rz);
             float gx, gy, gz, cv[8];
@@ -759,14 +756,15 @@ __global__ void __launch_bounds__(GeomBwd::THREADS, 2) k_wc_bwd_tile(GridD g, in
                 corners8(ref, g, cl.i0, cl.j0, cl.k0, cv);
             }
             trilin8_grad(cv, cl, gx, gy, gz);
-            const float gd[3] = {gw * gx, gw * gy, gw * gz};  // dL/d(displacement in voxels)
+            // dL/d(displacement in voxels), x and y packed
+            const f32x2 gdxy = mul2(pack2(gw, gw), pack2(gx, gy));
+            const float gdz = gw * gz;
 #pragma unroll
             for (int l = 0; l < L; l++) {
-                gE[h][l][0] = fmaf(gd[0], c[l].x, gE[h][l][0]);
-                gE[h][l][1] = fmaf(gd[1], c[l].y, gE[h][l][1]);
-                gE[h][l][2] = fmaf(gd[2], c[l].z, gE[h][l][2]);
-#pragma unroll
-                for (int a = 0; a < 3; a++) cw[l * 3 + a] = fmaf(gd[a], e[h][l][a], cw[l * 3 + a]);
+                gExy[h][l] = fma2(gdxy, cxy[l], gExy[h][l]);
+                gEz[h][l] = fmaf(gdz, cz[l], gEz[h][l]);
+                cwxy[l] = fma2(gdxy, exy[h][l], cwxy[l]);
+                cwz[l] = fmaf(gdz, ez[h][l], cwz[l]);
             }
             // V's adjoint: the 8 trilinear corners, each weight times gw rounded
             // once to the CTA's fixed point
@@ -790,6 +788,13 @@ __global__ void __launch_bounds__(GeomBwd::THREADS, 2) k_wc_bwd_tile(GridD g, in
         }
         // coefficient gradient partials: halving warp reduction, then the
         // warp's own slot
+        float cw[K];
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            cw[3 * l] = lo2(cwxy[l]);
+            cw[3 * l + 1] = hi2(cwxy[l]);
+            cw[3 * l + 2] = cwz[l];
+        }
         SplitReduce<K, 16>::run(cw, lane);
         if (slot >= 0) swarp[warp * PK + p * K + slot] += cw[0];
     }
@@ -801,7 +806,8 @@ __global__ void __launch_bounds__(GeomBwd::THREADS, 2) k_wc_bwd_tile(GridD g, in
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 float* o = d_mbc + ((int64_t)l * 3 + a) * N + v[h];
-                const float ge = gE[h][l][a] * (a == 0 ? g.ivx : (a == 1 ? g.ivy : g.ivz));
+                const float gv = a == 0 ? lo2(gExy[h][l]) : (a == 1 ? hi2(gExy[h][l]) : gEz[h][l]);
+                const float ge = gv * (a == 0 ? g.ivx : (a == 1 ? g.ivy : g.ivz));
                 *o = accumulate ? *o + ge : ge;
             }
     }

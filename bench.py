@@ -428,26 +428,39 @@ def run_native(a):
     # end to end, through the C ABI: pinned host inputs -> device -> one
     # pmf_plan_step (the native step plan, replayed from a CUDA graph) ->
     # gradients and loss back to pinned host.  Every step copies its own inputs
-    # in and its gradients and loss out inside the timed region; as a data
-    # loader would, a copy stream moves step k+1's inputs (and step k-1's
-    # results) while step k computes, through two device staging sets.
+    # (the Gaussian sets' parameters and the batch) in and its gradients and
+    # loss out inside the timed region; as a data loader would, a copy stream
+    # moves step k+1's inputs (and step k-1's results) while step k computes,
+    # through two device staging sets.  The parameters live in one flat buffer
+    # and the plan's outputs in another (grads_flat), so each moves as one copy.
     e2e = None
     if not a.no_e2e:
-        eplan = pmf.Plan(wl.grid, wl.det, ref, mbc, batch=B, dtype=dt, kind=a.kind, use_graph=True, w_dtype=wdt)
-        params = [ref.mean, ref.scale, ref.quat, ref.value] + [t for m in mbc for t in (m.mean, m.scale, m.quat, m.value)]
-        h_par = [t.cpu().pin_memory() for t in params]
+        sets_in = [ref] + mbc
+        par_ts = [t for m in sets_in for t in (m.mean, m.scale, m.quat, m.value)]
+        offs, tot = [], 0
+        for t in par_ts:
+            offs.append(tot)
+            tot += (t.numel() + 63) // 64 * 64  # 256-byte boundaries
+        par_flat = torch.zeros(tot, dtype=torch.float32, device="cuda")
+        pv = [par_flat[o:o + t.numel()].view(t.shape) for o, t in zip(offs, par_ts)]
+        for v_, t in zip(pv, par_ts):
+            v_.copy_(t)
+        esets = [pmf.Gaussians(*pv[4 * i:4 * i + 4], m.kappa) for i, m in enumerate(sets_in)]
+        eplan = pmf.Plan(wl.grid, wl.det, esets[0], esets[1:], batch=B, dtype=dt, kind=a.kind, use_graph=True,
+                         w_dtype=wdt)
+        params = [par_flat]
+        h_par = [par_flat.cpu().pin_memory()]
         h_views = views_all.cpu().pin_memory()
         h_coeff = coeff_all.cpu().pin_memory()
         h_meas = meas_all.cpu().pin_memory()
-        outs = [t for grp in (eplan.g_ref, *eplan.g_mbc, (eplan.d_coeff,)) for t in grp]
+        outs = [eplan.grads_flat]  # every gradient and the loss
         h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
-        h_loss = torch.empty(1).pin_memory()
         st_par = [[torch.empty_like(t) for t in params] for _ in range(2)]
         st_in = [(torch.empty((B, 12), dtype=torch.float64, device="cuda"), torch.empty((B, L, 3), device="cuda"),
                   torch.empty((B, wl.det.nv, wl.det.nu), device="cuda")) for _ in range(2)]
-        st_out = [[torch.empty_like(t) for t in outs] + [torch.empty(1, device="cuda")] for _ in range(2)]
+        st_out = [[torch.empty_like(t) for t in outs] for _ in range(2)]
         h2d = sum(t.numel() * t.element_size() for t in h_par) + B * (12 * 8 + L * 3 * 4 + wl.det.q * 4)
-        d2h = sum(t.numel() * t.element_size() for t in h_out) + 4
+        d2h = sum(t.numel() * t.element_size() for t in h_out)
         cstream = torch.cuda.Stream()
         ev_in = [torch.cuda.Event() for _ in range(2)]
         ev_res = [torch.cuda.Event() for _ in range(2)]
@@ -474,15 +487,15 @@ def run_native(a):
                 stream.wait_event(ev_in[i])
                 for dst, src_ in zip(params, st_par[i]):
                     dst.copy_(src_, non_blocking=True)
-                lo = eplan.step(*st_in[i])
+                eplan.step(*st_in[i])
                 if k - 2 >= k0:
                     stream.wait_event(ev_out[i])  # step k - 2's results have left staging i
-                for dst, src_ in zip(st_out[i], outs + [lo]):
+                for dst, src_ in zip(st_out[i], outs):
                     dst.copy_(src_, non_blocking=True)
                 ev_res[i].record(stream)
                 with torch.cuda.stream(cstream):
                     cstream.wait_event(ev_res[i])
-                    for h, t in zip(h_out + [h_loss], st_out[i]):
+                    for h, t in zip(h_out, st_out[i]):
                         h.copy_(t, non_blocking=True)
                     ev_out[i].record(cstream)
             stream.wait_stream(cstream)

@@ -775,15 +775,22 @@ class _StepBuffers:
         self.views = torch.zeros((self.B, 12), dtype=torch.float64, device=dev)
         self.coeff = torch.zeros((self.B, self.L, 3), dtype=torch.float32, device=dev)
         self.meas = torch.zeros((self.B, gr.nv, gr.nu), dtype=torch.float32, device=dev)
-        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
-
-        def grads(gs):
-            return (torch.zeros((gs.n, 3), device=dev), torch.zeros((gs.n, 3), device=dev),
-                    torch.zeros((gs.n, 4), device=dev), torch.zeros((gs.n, gs.channels), device=dev))
-
-        self.g_ref = grads(ref)
-        self.g_mbc = [grads(m) for m in self.mbc]
-        self.d_coeff = torch.zeros((self.B, self.L, 3), dtype=torch.float32, device=dev)
+        # the step's outputs (every set's gradients, the coefficient gradient and
+        # the loss) as views of one fp32 allocation, each at a 256-byte
+        # boundary: a caller moves all of them with one copy of grads_flat
+        shapes = []
+        for gs in [ref] + list(self.mbc):
+            shapes += [(gs.n, 3), (gs.n, 3), (gs.n, 4), (gs.n, gs.channels)]
+        shapes += [(self.B, self.L, 3), (1,)]
+        offs, total = [], 0
+        for shp in shapes:
+            offs.append(total)
+            total += (math.prod(shp) + 63) // 64 * 64
+        self.grads_flat = torch.zeros(total, dtype=torch.float32, device=dev)
+        views = [self.grads_flat[o:o + math.prod(shp)].view(shp) for o, shp in zip(offs, shapes)]
+        self.g_ref = tuple(views[0:4])
+        self.g_mbc = [tuple(views[4 + 4 * l:8 + 4 * l]) for l in range(len(self.mbc))]
+        self.d_coeff, self.loss = views[-2], views[-1]
 
     def set_batch(self, views=None, coeff=None, meas=None, tv_origin=None) -> None:
         for dst, src in ((self.views, views), (self.coeff, coeff), (self.meas, meas)):
